@@ -1,0 +1,521 @@
+"""The paper's sharded layer programs, for the oracle (TEST INFRASTRUCTURE ONLY).
+
+Sec. 4 of the paper.  Every program here has two evaluators that share one plan:
+
+* ``*_slots``: the plan applied to cleartext float64 slot vectors, with ``np.roll`` as the
+  rotation (the slot simulator; it pins layouts, rotation sets and masks against plain
+  ``torch.nn.functional.conv2d`` / ``avg_pool2d`` without any encryption noise);
+* ``*_he``: the same plan on oracle ciphertexts (``oracle.ckks``).
+
+Layout (Sec. 4 "Sharding and Encrypting an Image", "Duplicating and Permuting Channels").
+Each channel's valid m x m pixels sit row-major in an M x M frame, M the next power of two
+(the paper's zero-padding suggestion for non-power-of-two sizes, Sec. 4), row stride M.
+A shard of N slots is cut into blocks of B = min(M^2, N) slots; block b of shard u holds the
+rows [row0, row0 + B/M) of one channel (or nothing).  A table (chan[u][b], row0[u][b]) is the
+metadata: it expresses image shards (B = M^2, z = N/M^2 channels per shard), channel shards
+(B = N, consecutive rows of one channel per shard), the duplication factor d (a channel in
+several blocks; tiled order c_0..c_{c-1} repeated d times) and the pooling permutation tau
+(chan[] in any order).
+"""
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+from .encode import encode
+
+
+# ============================================================================ layout
+@dataclass
+class Layout:
+    c: int                  # channels
+    m: int                  # valid side
+    M: int                  # frame side (row stride), power of two
+    N: int                  # slots per shard
+    B: int                  # slots per block
+    chan: np.ndarray        # [n_shards][nb] int: channel or -1
+    row0: np.ndarray        # [n_shards][nb] int: first frame row held by the block
+
+    @property
+    def n_shards(self):
+        return self.chan.shape[0]
+
+    @property
+    def nb(self):
+        return self.chan.shape[1]
+
+    @property
+    def rows_per_block(self):
+        return self.B // self.M
+
+    def copy(self):
+        return Layout(self.c, self.m, self.M, self.N, self.B, self.chan.copy(), self.row0.copy())
+
+
+def next_pow2(x):
+    return 1 << (int(x) - 1).bit_length()
+
+
+def image_layout(c, m, N):
+    """Initial layout of a c x m x m image (no permutation)."""
+    M = next_pow2(m)
+    if M * M <= N:
+        B = M * M
+        nb = N // B
+        if c * B <= N:                          # one shard, duplicated d = nb // c times
+            chan = np.full((1, nb), -1, dtype=np.int64)
+            d = nb // c
+            for b in range(d * c):
+                chan[0, b] = b % c
+        else:                                   # image shards, z = nb channels each
+            t = -(-c // nb)
+            chan = np.full((t, nb), -1, dtype=np.int64)
+            for f in range(c):
+                chan[f // nb, f % nb] = f
+        row0 = np.zeros_like(chan)
+    else:                                       # channel shards: N/M rows per shard
+        B = N
+        R = N // M
+        h = M // R                              # shards per channel
+        chan = np.zeros((c * h, 1), dtype=np.int64)
+        row0 = np.zeros((c * h, 1), dtype=np.int64)
+        for f in range(c):
+            for k in range(h):
+                chan[f * h + k, 0] = f
+                row0[f * h + k, 0] = k * R
+    return Layout(c, m, M, N, B, chan, row0)
+
+
+def slot_coords(lay: Layout, u: int):
+    """For every slot of shard u: (channel or -1, frame row y, column x, valid pixel?)."""
+    i = np.arange(lay.N)
+    b = i // lay.B
+    ch = lay.chan[u][b]
+    y = lay.row0[u][b] + (i % lay.B) // lay.M
+    x = i % lay.M
+    valid = (ch >= 0) & (y < lay.m) & (x < lay.m)
+    return ch, y, x, valid
+
+
+def pack(lay: Layout, img):
+    """img [c][m][m] -> slot vectors [n_shards][N]."""
+    img = np.asarray(img, dtype=np.float64)
+    out = np.zeros((lay.n_shards, lay.N))
+    for u in range(lay.n_shards):
+        ch, y, x, valid = slot_coords(lay, u)
+        out[u, valid] = img[ch[valid], y[valid], x[valid]]
+    return out
+
+
+def unpack(lay: Layout, slots, check_copies=False, atol=0.0):
+    """Slot vectors -> img [c][m][m] (first copy of every pixel)."""
+    img = np.full((lay.c, lay.m, lay.m), np.nan)
+    for u in range(lay.n_shards):
+        ch, y, x, valid = slot_coords(lay, u)
+        cur = img[ch[valid], y[valid], x[valid]]
+        vals = slots[u][valid]
+        if check_copies:
+            seen = ~np.isnan(cur)
+            assert np.all(np.abs(cur[seen] - vals[seen]) <= atol), "duplicate copies disagree"
+        fill = np.where(np.isnan(cur), vals, cur)
+        img[ch[valid], y[valid], x[valid]] = fill
+    assert not np.isnan(img).any(), "layout does not cover the image"
+    return img
+
+
+# ============================================================================ convolution
+@dataclass
+class ConvPlan:
+    lin: Layout
+    lout: Layout
+    terms: dict = field(default_factory=dict)    # v -> {(u, a): D float64 [N]}
+    bias: np.ndarray = None                      # [n_out][N], bias on valid output pixels
+
+    def amounts(self, u):
+        s = set()
+        for v in self.terms:
+            for (uu, a) in self.terms[v]:
+                if uu == u:
+                    s.add(a)
+        return sorted(s)
+
+    def n_rotations(self):
+        return sum(len([a for a in self.amounts(u) if a != 0]) for u in range(self.lin.n_shards))
+
+
+def conv_plan(lin: Layout, W, bias, pad):
+    """Stride-1 'same' convolution as sums of rotated, diagonal-weighted shards.
+
+    Eq. 1 (shift operator), Eqs. 2-5 (partial convolutions, rotation by r m^2), Eq. 6
+    (image shards), the duplication/permutation rule of Sec. 4 and Eq. 7 (channel shards),
+    written in one general form: for output slot i of shard v (channel o, pixel y, x), input
+    channel f and tap (k, l) the source pixel (y+k-pad, x+l-pad), if inside the image, is
+    read from the copy (u, slot j) of channel f holding that row; the amount is
+    a = (j - i) mod N and D_{u,v,a}[i] = W[o][f][k][l] (cross-correlation, as the paper's
+    S_{k,l} shifts rows up and columns left).  Among duplicated copies the one with the
+    smallest block offset (b_in - b_out) mod nb is used, which yields the paper's rotation
+    set {r m^2 + shift : 0 <= r < c}.
+    """
+    W = np.asarray(W, dtype=np.float64)
+    co, ci, kh, kw = W.shape
+    assert ci == lin.c
+    lout = image_layout(co, lin.m, lin.N)
+    assert lout.M == lin.M
+    plan = ConvPlan(lin, lout)
+    N = lin.N
+    # copies of each input channel: (u, b, row0)
+    copies = {f: [] for f in range(ci)}
+    for u in range(lin.n_shards):
+        for b in range(lin.nb):
+            f = lin.chan[u, b]
+            if f >= 0:
+                copies[f].append((u, b, lin.row0[u, b]))
+    R = lin.rows_per_block
+    for v in range(lout.n_shards):
+        ch, y, x, valid = slot_coords(lout, v)
+        i = np.arange(N)
+        b_out = i // lout.B
+        terms = {}
+        for f in range(ci):
+            for k in range(kh):
+                for l in range(kw):
+                    ys, xs = y + k - pad, x + l - pad
+                    ok = valid & (ys >= 0) & (ys < lin.m) & (xs >= 0) & (xs < lin.m)
+                    best_key = np.full(N, np.iinfo(np.int64).max)
+                    best_u = np.full(N, -1)
+                    best_j = np.full(N, -1)
+                    for (u, b, r0) in copies[f]:
+                        has = ok & (ys >= r0) & (ys < r0 + R)
+                        key = ((b - b_out) % lin.nb) * (lin.n_shards + 1) + u
+                        better = has & (key < best_key)
+                        j = b * lin.B + (ys - r0) * lin.M + xs
+                        best_key = np.where(better, key, best_key)
+                        best_u = np.where(better, u, best_u)
+                        best_j = np.where(better, j, best_j)
+                    sel = ok & (best_u >= 0)
+                    assert np.all(best_u[ok] >= 0), "source pixel missing from layout"
+                    if not sel.any():
+                        continue
+                    a = (best_j - i) % N
+                    wv = W[np.where(sel, ch, 0), f, k, l]
+                    keys = best_u[sel] * N + a[sel]
+                    idx = np.nonzero(sel)[0]
+                    for key in np.unique(keys):
+                        uu, aa = divmod(int(key), N)
+                        D = terms.setdefault((uu, aa), np.zeros(N))
+                        pos = idx[keys == key]
+                        assert np.all(D[pos] == 0.0), "two taps hit one diagonal entry"
+                        D[pos] = wv[pos]
+        plan.terms[v] = terms
+    bv = np.zeros((lout.n_shards, N))
+    if bias is not None:
+        bias = np.asarray(bias, dtype=np.float64)
+        for v in range(lout.n_shards):
+            ch, y, x, valid = slot_coords(lout, v)
+            bv[v, valid] = bias[ch[valid]]
+    plan.bias = bv
+    return plan
+
+
+def conv_slots(plan: ConvPlan, slots):
+    """Slot simulator: out_v = sum_{(u,a)} D_{u,v,a} * roll(in_u, -a) + bias."""
+    out = np.zeros((plan.lout.n_shards, plan.lin.N))
+    for v, terms in plan.terms.items():
+        for (u, a), D in terms.items():
+            out[v] += D * np.roll(slots[u], -a)
+        out[v] += plan.bias[v]
+    return out
+
+
+def conv_plaintexts(plan: ConvPlan, n, S):
+    """Integer plaintexts of every diagonal, encoded at scale S: {(u, v, a): int64 [n]}."""
+    return {(u, v, a): encode(D, n, S) for v, t in plan.terms.items() for (u, a), D in t.items()}
+
+
+def rotate_all(ctx, cts, amounts_of):
+    """Hoisted rotations {(u, a): ct} of every input shard by every amount it needs."""
+    R = {}
+    for u, ct in enumerate(cts):
+        am = amounts_of(u)
+        if not am:
+            continue
+        D = ctx.hoist(ct) if any(a != 0 for a in am) else None
+        for a in am:
+            if a != 0:
+                ctx.gen_rotation_key(a)
+            R[(u, a)] = ct.copy() if a == 0 else ctx.rotate_hoisted(ct, D, a)
+    return R
+
+
+def mac_rescale(ctx, R, terms, pts, level, scale_in):
+    """Rescale(sum_{(u,a)} pt_{u,a} * R_{u,a}): the fused pt x ct MAC of one output shard."""
+    mods, psis = ctx.mods(level), ctx.psis(level)
+    acc = [np.zeros((level + 1, ctx.n), dtype=np.uint64) for _ in range(2)]
+    for (u, a), pt in zip(terms, pts):
+        P = ctx.ntt(ctx.reduce_int(pt, mods), mods, psis).reshape(level + 1, ctx.n)
+        for k in range(2):
+            X = ctx.ntt(R[(u, a)].c[k], mods, psis).reshape(level + 1, ctx.n)
+            ctx.lib.orc_mac(acc[k], P, X, level + 1, ctx.n, mods)
+    from .ckks import Ciphertext
+    c = np.stack([ctx.intt(x, mods, psis).reshape(level + 1, ctx.n) for x in acc])
+    return ctx.rescale(Ciphertext(c, level, scale_in * ctx.q[level]))
+
+
+def conv_he(ctx, plan: ConvPlan, cts, pts=None, bias_pts=None):
+    """hconv2d on oracle ciphertexts (all inputs at one level and scale).
+
+    pts: optional {(u, v, a): int64 plaintext} at scale q_level (else encoded here);
+    bias_pts: optional {v: int64 plaintext} at the input scale (else encoded here).
+    """
+    level, scale = cts[0].level, cts[0].scale
+    assert all(c.level == level and c.scale == scale for c in cts)
+    if pts is None:
+        pts = conv_plaintexts(plan, ctx.n, float(ctx.q[level]))
+    R = rotate_all(ctx, cts, plan.amounts)
+    out = []
+    for v in range(plan.lout.n_shards):
+        keys = sorted(plan.terms[v].keys())
+        ct = mac_rescale(ctx, R, keys, [pts[(u, v, a)] for (u, a) in keys], level, scale)
+        bpt = bias_pts[v] if bias_pts is not None else encode(plan.bias[v], ctx.n, ct.scale)
+        ct.c[0] = ctx.add(ct.c[0], ctx.reduce_int(bpt, ctx.mods(ct.level)), ctx.mods(ct.level))
+        out.append(ct)
+    return out
+
+
+# ============================================================================ pooling
+@dataclass
+class PoolPlan:
+    lin: Layout
+    lout: Layout
+    pre: list            # amounts summed unmasked before downsampling (S stage)
+    h_terms: list        # [(amount, mask float64 [N])] horizontal reduction
+    v_terms: list        # [(amount, mask float64 [N])] vertical reduction
+    groups: list         # consolidation: list over output shards of [(input shard, amount)]
+    dup: list            # duplication amounts applied to the consolidated shard (incl. 0)
+
+
+def pool_plan(lin: Layout, weights=(0.25, 0.25, 0.25, 0.25), select_top_left=False):
+    """2x2 average pool (Sec. 4.2), or the stride-2 downsample when select_top_left.
+
+    S: W = X + rot_1 X + rot_M X + rot_{M+1} X      (the 2x2 ones convolution, unmasked)
+    H: Y = sum_{x'} mask_{x'} * rot_{x'}(W)          (Eq. 10, rotate-then-mask form)
+    V: Z = sum_{y'} mask_{y'} * rot_{3 y' M/2}(Y)     (Eq. 11)
+    C: consolidate 4 shards into one (Eq. 12), or duplicate when 1-2 shards remain (Eq. 13).
+    With select_top_left the S stage is skipped and the masks carry weight 1 (the paper's
+    strided convolution = unstrided convolution + downsampling, Sec. 4.1).
+    """
+    M, N, B, m = lin.M, lin.N, lin.B, lin.m
+    assert m % 2 == 0 and M >= 2
+    Mh = M // 2
+    Rb = lin.rows_per_block
+    assert Rb % 2 == 0 or Rb == 1
+    w = 1.0 if select_top_left else 0.25
+    pre = [] if select_top_left else [0, 1, M, M + 1]
+    i = np.arange(N)
+    loc = i % B
+    lr = loc // M                 # local row within the block
+    col = i % M
+    blk = i // B
+    h_terms = []
+    for xp in range(m // 2):
+        masks = np.zeros((lin.n_shards, N))
+        for u in range(lin.n_shards):
+            ch = lin.chan[u][blk]
+            y = lin.row0[u][blk] + lr
+            sel = (ch >= 0) & (y % 2 == 0) & (y < m) & (col == xp)
+            masks[u, sel] = w
+        h_terms.append((xp, masks))
+    v_terms = []
+    for yp in range(max(Rb // 2, 1)):
+        amount = 3 * yp * M // 2
+        masks = np.zeros((lin.n_shards, N))
+        for u in range(lin.n_shards):
+            ch = lin.chan[u][blk]
+            ynew = lin.row0[u][blk] // 2 + yp
+            sel = (ch >= 0) & (loc >= yp * Mh) & (loc < yp * Mh + m // 2) & (ynew < m // 2)
+            masks[u, sel] = 1.0
+        if masks.any():
+            v_terms.append((amount, masks))
+    # new layout: old block b of shard s -> new block 4b + q of output shard s // 4 (q = s % 4)
+    Bn = B // 4
+    nbn = N // Bn
+    t = lin.n_shards
+    n_out = -(-t // 4)
+    chan = np.full((n_out, nbn), -1, dtype=np.int64)
+    row0 = np.zeros((n_out, nbn), dtype=np.int64)
+    groups = []
+    for g in range(n_out):
+        grp = []
+        for q in range(4):
+            s = 4 * g + q
+            if s >= t:
+                break
+            grp.append((s, (-q * Bn) % N))
+            for b in range(lin.nb):
+                chan[g, 4 * b + q] = lin.chan[s, b]
+                row0[g, 4 * b + q] = lin.row0[s, b] // 2
+        groups.append(grp)
+    dup = [0]
+    if t in (1, 2):
+        f = 4 // t
+        step = t * Bn
+        dup = [(-k * step) % N for k in range(f)]
+        for k in range(1, f):
+            for b in range(nbn):
+                src = b - k * (step // Bn)
+                if src >= 0 and chan[0, src] >= 0 and chan[0, b] < 0:
+                    chan[0, b] = chan[0, src]
+                    row0[0, b] = row0[0, src]
+    lout = Layout(lin.c, m // 2, Mh, N, Bn, chan, row0)
+    return PoolPlan(lin, lout, pre, h_terms, v_terms, groups, dup)
+
+
+def pool_slots(plan: PoolPlan, slots):
+    out_sh = []
+    Z = []
+    for u in range(plan.lin.n_shards):
+        x = slots[u]
+        Wv = sum(np.roll(x, -a) for a in plan.pre) if plan.pre else x
+        Y = sum(mk[u] * np.roll(Wv, -a) for a, mk in plan.h_terms)
+        Z.append(sum(mk[u] * np.roll(Y, -a) for a, mk in plan.v_terms))
+    for grp in plan.groups:
+        S = sum(np.roll(Z[s], -a) for s, a in grp)
+        out_sh.append(S)
+    if len(plan.dup) > 1:
+        out_sh = [sum(np.roll(out_sh[0], -a) for a in plan.dup)]
+    return np.stack(out_sh)
+
+
+def _masked_stage(ctx, cts, terms, level):
+    """Rescale(sum_a Encode(mask_a, q_level) * rot_a(ct)) for every shard."""
+    out = []
+    for u, ct in enumerate(cts):
+        R = rotate_all(ctx, [ct], lambda _u: [a for a, _ in terms])
+        keys = [(0, a) for a, _ in terms]
+        pts = [encode(mk[u], ctx.n, float(ctx.q[level])) for _, mk in terms]
+        out.append(mac_rescale(ctx, R, keys, pts, level, ct.scale))
+    return out
+
+
+def pool_he(ctx, plan: PoolPlan, cts):
+    level = cts[0].level
+    Ws = []
+    for ct in cts:
+        if plan.pre:
+            R = rotate_all(ctx, [ct], lambda _u: plan.pre)
+            acc = R[(0, plan.pre[0])]
+            for a in plan.pre[1:]:
+                acc = ctx.add_ct(acc, R[(0, a)])
+            Ws.append(acc)
+        else:
+            Ws.append(ct)
+    Ys = _masked_stage(ctx, Ws, plan.h_terms, level)
+    Zs = _masked_stage(ctx, Ys, plan.v_terms, level - 1)
+    outs = []
+    for grp in plan.groups:
+        acc = None
+        for s, a in grp:
+            r = rotate_all(ctx, [Zs[s]], lambda _u: [a])[(0, a)]
+            acc = r if acc is None else ctx.add_ct(acc, r)
+        outs.append(acc)
+    if len(plan.dup) > 1:
+        R = rotate_all(ctx, [outs[0]], lambda _u: plan.dup)
+        acc = R[(0, plan.dup[0])]
+        for a in plan.dup[1:]:
+            acc = ctx.add_ct(acc, R[(0, a)])
+        outs = [acc]
+    return outs
+
+
+# ============================================================================ polynomial
+def cheb_nodes_coeffs(f, deg, lo, hi):
+    """Chebyshev interpolant of f on [lo, hi] at the deg+1 first-kind nodes (Appendix,
+    'Chebyshev Basis'): returns c_0..c_deg with p(x) = sum c_k T_k(t), t = (2x-lo-hi)/(hi-lo)."""
+    K = deg + 1
+    k = np.arange(K)
+    t = np.cos(np.pi * (k + 0.5) / K)
+    fx = np.array([f(0.5 * (hi - lo) * tt + 0.5 * (hi + lo)) for tt in t])
+    c = np.zeros(K)
+    for j in range(K):
+        c[j] = 2.0 / K * np.sum(fx * np.cos(j * np.pi * (k + 0.5) / K))
+    c[0] *= 0.5
+    return c
+
+
+def cheb_eval(c, x, lo, hi):
+    """p(x) = sum c_k T_k(t) with T_k(t) = cos(k arccos t) by the three-term recurrence."""
+    t = (2.0 * np.asarray(x, dtype=np.float64) - lo - hi) / (hi - lo)
+    T0, T1 = np.ones_like(t), t
+    acc = c[0] * T0 + (c[1] * T1 if len(c) > 1 else 0.0)
+    for k in range(2, len(c)):
+        T0, T1 = T1, 2.0 * t * T1 - T0
+        acc = acc + c[k] * T1
+    return acc
+
+
+def gelu(x):
+    return 0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0)))
+
+
+def relu(x):
+    return max(x, 0.0)
+
+
+def cheb_tree_slots(c, t):
+    """The paper's binary-tree recursion (Appendix, 'Chebyshev Polynomials'):
+    T_{2k} = 2 T_k^2 - 1, T_{2k+1} = 2 T_k T_{k+1} - T_1, then sum c_k T_k, on cleartext."""
+    T = {0: np.ones_like(t), 1: t}
+    for k in range(2, len(c)):
+        h = k // 2
+        T[k] = 2 * T[h] * T[h] - 1 if k % 2 == 0 else 2 * T[h] * T[h + 1] - T[1]
+    return sum(c[k] * T[k] for k in range(len(c)))
+
+
+def cheb_tree_he(ctx, ct, c, target_scale=None):
+    """Homomorphic sum c_k T_k(ct) with the binary-tree T_k and exact-scale constants.
+
+    T_1 = ct.  Products run through mul_relin (tensor, relinearise, rescale).  Every
+    subtraction of T_1 and the final linear combination re-target the scale exactly: a
+    ciphertext at scale s is multiplied by the integer round(c * S_target * q_l / s) at
+    level l and rescaled, so its scale becomes S_target (value error ~ 2^-40 relative).
+    The constant term is added as round(c_0 * scale) on coefficient 0.
+    """
+    target_scale = ctx.pr.scale if target_scale is None else target_scale
+    deg = len(c) - 1
+    T = {1: ct}
+
+    def retarget(x, level, scale_t):
+        """x (any scale) -> level `level`, scale exactly scale_t, costs one level."""
+        y = ctx.drop_to(x, level + 1)
+        K = int(round(scale_t * ctx.q[level + 1] / y.scale))
+        y = ctx.mul_int(y, K)
+        y = ctx.rescale(y)
+        y.scale = scale_t
+        return y
+
+    for k in range(2, deg + 1):
+        h = k // 2
+        if k % 2 == 0:
+            p = ctx.mul_relin(T[h], T[h])
+            p = ctx.mul_int(p, 2)
+            p = ctx.add_const_int(p, -int(round(p.scale)))
+        else:
+            a, b = T[h], T[h + 1]
+            lv = min(a.level, b.level)
+            p = ctx.mul_relin(ctx.drop_to(a, lv), ctx.drop_to(b, lv))
+            p = ctx.mul_int(p, 2)
+            t1 = retarget(T[1], p.level, p.scale)
+            p = ctx.sub_ct(p, t1)
+        T[k] = p
+    lmin = min(x.level for x in T.values())
+    acc = None
+    for k in range(1, deg + 1):
+        x = ctx.drop_to(T[k], lmin)
+        K = int(round(c[k] * target_scale * ctx.q[lmin] / x.scale))
+        y = ctx.mul_int(x, K)
+        y.scale = target_scale * ctx.q[lmin]
+        acc = y if acc is None else ctx.add_ct(acc, y)
+    acc = ctx.add_const_int(acc, int(round(c[0] * target_scale * ctx.q[lmin])))
+    out = ctx.rescale(acc)
+    out.scale = target_scale
+    return out

@@ -1,0 +1,162 @@
+"""Pins for the oracle's layer programs (Sec. 4) and polynomial routine (Appendix); no GPU."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import layers as Ly
+from oracle.params import TOY, Params
+from oracle.ckks import Context
+import workloads
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _conv_ref(x, W, b, pad):
+    return torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(W),
+                                      None if b is None else torch.tensor(b), padding=pad)[0].numpy()
+
+
+CASES = [  # (c_in, c_out, m, N, k, pad): single shard + dup, image shards, channel shards
+    (4, 4, 32, 4096, 3, 1),
+    (16, 16, 32, 32768, 3, 1),
+    (8, 8, 28, 2048, 3, 1),
+    (2, 3, 32, 512, 3, 1),
+    (3, 4, 32, 512, 7, 3),
+    (16, 8, 16, 1024, 3, 1),
+    (4, 4, 8, 64, 1, 0),
+]
+
+
+@pytest.mark.parametrize("c,co,m,N,k,pad", CASES)
+def test_conv_plan_equals_torch_conv2d(c, co, m, N, k, pad):
+    rng = np.random.default_rng(c * 100 + m)
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (co, c, k, k))
+    b = rng.uniform(-1, 1, co)
+    lin = Ly.image_layout(c, m, N)
+    plan = Ly.conv_plan(lin, W, b, pad)
+    img = Ly.unpack(plan.lout, Ly.conv_slots(plan, Ly.pack(lin, x)), check_copies=True, atol=1e-12)
+    assert np.abs(img - _conv_ref(x, W, b, pad)).max() < 1e-12
+
+
+def test_rotation_counts_match_the_paper():
+    # one full shard: c kappa^2 rotations including the identity (Sec. 4.1, Eqs. 4-5)
+    rng = np.random.default_rng(0)
+    p = Ly.conv_plan(Ly.image_layout(16, 32, 32768), rng.uniform(-1, 1, (16, 16, 3, 3)), None, 1)
+    assert p.n_rotations() == 16 * 9 - 1
+    # image shards: z kappa^2 amounts per input shard, shared by every output shard (Eq. 6)
+    p = Ly.conv_plan(Ly.image_layout(16, 16, 1024), rng.uniform(-1, 1, (16, 16, 3, 3)), None, 1)
+    assert [len(p.amounts(u)) for u in range(4)] == [4 * 9] * 4
+    # channel shards: one amount per tap, shared by own and neighbour shard (Eq. 7)
+    p = Ly.conv_plan(Ly.image_layout(2, 32, 512), rng.uniform(-1, 1, (2, 2, 3, 3)), None, 1)
+    assert all(len(p.amounts(u)) == 9 for u in range(p.lin.n_shards))
+    own_nbr = {(u, a) for v, t in p.terms.items() for (u, a) in t if u != v}
+    assert own_nbr  # some output shards read neighbour shards
+
+
+@pytest.mark.parametrize("c,m,N,sel", [(4, 32, 4096, False), (16, 32, 2048, False),
+                                        (8, 32, 2048, False), (2, 32, 512, False),
+                                        (2, 28, 512, False), (3, 32, 512, True),
+                                        (64, 56, 32768, False)])
+def test_pool_plan_equals_torch_avg_pool(c, m, N, sel):
+    rng = np.random.default_rng(m + c)
+    x = rng.uniform(0, 1, (c, m, m))
+    lin = Ly.image_layout(c, m, N)
+    plan = Ly.pool_plan(lin, select_top_left=sel)
+    img = Ly.unpack(plan.lout, Ly.pool_slots(plan, Ly.pack(lin, x)), check_copies=True,
+                    atol=1e-12)
+    ref = x[:, ::2, ::2] if sel else torch.nn.functional.avg_pool2d(torch.tensor(x)[None], 2)[0].numpy()
+    assert np.abs(img - ref).max() < 1e-12
+
+
+def test_pool_permutes_image_shards_but_not_channel_shards():
+    plan = Ly.pool_plan(Ly.image_layout(8, 32, 2048))
+    order = [int(c) for c in plan.lout.chan[0] if c >= 0]
+    assert sorted(order) == list(range(8)) and order != list(range(8))   # Fig. (consolidate)
+    plan = Ly.pool_plan(Ly.image_layout(2, 32, 512))                      # channel shards
+    ch = plan.lout.chan[0]
+    assert list(ch) == sorted(ch)                                         # order kept
+
+
+def test_strided_conv_is_conv_then_top_left_select():
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 1, (3, 32, 32))
+    W = rng.normal(0, 0.05, (4, 3, 7, 7))
+    lin = Ly.image_layout(3, 32, 512)
+    cp = Ly.conv_plan(lin, W, None, 3)
+    pp = Ly.pool_plan(cp.lout, select_top_left=True)
+    out = Ly.pool_slots(pp, Ly.conv_slots(cp, Ly.pack(lin, x)))
+    ref = torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(W), stride=2,
+                                     padding=3)[0].numpy()
+    assert np.abs(Ly.unpack(pp.lout, out) - ref).max() < 1e-12
+
+
+def test_chebyshev_nodes_table_from_the_paper():
+    rows = [l.split() for l in open(os.path.join(GOLD, "poly_approx_table.txt"))
+            if l.strip() and not l.startswith("#")]
+    xs = np.linspace(-16, 16, 100001)
+    for _, deg, relu_err, gelu_err in rows:
+        for f, want in ((Ly.relu, relu_err), (Ly.gelu, gelu_err)):
+            c = Ly.cheb_nodes_coeffs(f, int(deg), -16, 16)
+            err = np.abs(Ly.cheb_eval(c, xs, -16, 16) - np.array([f(v) for v in xs])).max()
+            assert round(err, 4) == float(want), (deg, f.__name__, err)
+
+
+def test_binary_tree_chebyshev_recursion_and_depth():
+    t = np.linspace(-1, 1, 1001)
+    c = np.random.default_rng(0).normal(size=60)
+    assert np.abs(Ly.cheb_tree_slots(c, t) - Ly.cheb_eval(c, t, -1, 1)).max() < 1e-10
+
+    # depth of T_k in the tree: T_1 = x at 0, T_k one level below its deeper operand
+    def depths(d):
+        dep = {1: 0}
+        for k in range(2, d + 1):
+            h = k // 2
+            dep[k] = 1 + (dep[h] if k % 2 == 0 else max(dep[h], dep[h + 1]))
+        return max(dep.values())
+    assert depths(59) == 6 and depths(27) == 5        # Appendix, Chebyshev polynomials
+
+
+@pytest.fixture(scope="module")
+def toy():
+    return Context(TOY)
+
+
+def test_toy_conv_decrypts_to_fp64_conv(toy):
+    wl = workloads.toy_conv(0)
+    lin = Ly.image_layout(4, 32, toy.N)
+    plan = Ly.conv_plan(lin, wl.W, wl.bias, wl.pad)
+    slots = Ly.pack(lin, wl.x)
+    cts = [toy.encrypt(slots[u], 3, nonce=u) for u in range(lin.n_shards)]
+    out = Ly.conv_he(toy, plan, cts)
+    img = Ly.unpack(plan.lout, np.stack([toy.decrypt(c) for c in out]))
+    ref = _conv_ref(wl.x, wl.W, wl.bias, wl.pad)
+    assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+    assert plan.n_rotations() == 35
+
+
+def test_toy_pool_decrypts_to_fp64_pool(toy):
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0, 1, (4, 32, 32))
+    lin = Ly.image_layout(4, 32, toy.N)
+    plan = Ly.pool_plan(lin)
+    cts = [toy.encrypt(Ly.pack(lin, x)[0], 3, nonce=5)]
+    out = Ly.pool_he(toy, plan, cts)
+    assert out[0].level == 1
+    img = Ly.unpack(plan.lout, np.stack([toy.decrypt(c) for c in out]))
+    ref = torch.nn.functional.avg_pool2d(torch.tensor(x)[None], 2)[0].numpy()
+    assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+
+
+def test_poly_gelu_he_matches_same_polynomial():
+    ctx = Context(Params(log_n=10, n_q=8, n_p=2, dnum=4, q0_bits=50, q_bits=40, p_bits=50,
+                         scale=2.0 ** 40, seed=1))
+    ctx.gen_relin_key()
+    z = np.random.default_rng(0).uniform(-1, 1, ctx.N)
+    c = Ly.cheb_nodes_coeffs(Ly.gelu, 16, -8, 8)
+    out = Ly.cheb_tree_he(ctx, ctx.encrypt(z, 7), c)
+    assert out.level == 2 and out.scale == 2.0 ** 40
+    ref = Ly.cheb_eval(c, 8 * z, -8, 8)
+    assert np.abs(ctx.decrypt(out) - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())

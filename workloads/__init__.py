@@ -1,0 +1,98 @@
+"""Seeded synthetic workloads shaped like the paper's CIFAR- and ImageNet-sized layers.
+
+This module only draws inputs (images, weights, folded BatchNorm affines, request arrival
+times).  It holds none of the homomorphic method's arithmetic, so both the CUDA path and the
+CPU oracle can take their inputs from it.  The paper evaluates on CIFAR-10/100 (32x32x3) and
+ImageNet-1k (224/128/256 pixels) with trained ResNets (Sec. 5.1-5.2); neither datasets nor
+weights exist here, so these seeded draws stand in for them with the same shapes and value
+ranges: pixels uniform in [0, 1], PyTorch's default conv initialisation, BatchNorm statistics
+taken from the plaintext convolution output (so pre-activations stay inside the polynomial's
+interval, the role the paper's kurtosis regularisation plays, Appendix).
+"""
+from dataclasses import dataclass
+import math
+
+import numpy as np
+
+GELU_BOUND = 8.0      # polynomial interval [-8, 8]; BN output is divided by it (folded)
+GELU_DEGREE = 16
+
+
+@dataclass
+class ConvLayer:
+    x: np.ndarray          # [c][m][m]
+    W: np.ndarray          # [co][ci][k][k], BN and 1/GELU_BOUND folded in when bn=True
+    bias: np.ndarray       # [co]
+    stride: int
+    pad: int
+    name: str
+
+
+def image(c, m, seed):
+    return np.random.default_rng(seed).uniform(0.0, 1.0, (c, m, m))
+
+
+def _plain_conv(x, W, pad):
+    import torch
+    return torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(W),
+                                      padding=pad)[0].numpy()
+
+
+def fold_bn(x, W, pad, bound=GELU_BOUND, eps=1e-5):
+    """gamma = 1, beta = 0, mu/sigma^2 from the plaintext conv output; divide by `bound`."""
+    y = _plain_conv(x, W, pad)
+    mu = y.mean(axis=(1, 2))
+    sd = np.sqrt(y.var(axis=(1, 2)) + eps)
+    Wf = W / (sd[:, None, None, None] * bound)
+    bf = -mu / (sd * bound)
+    return Wf, bf
+
+
+def toy_conv(seed=0):
+    """4x32x32 image, 3x3 conv 4->4, weights U[-1,1], bias 0, stride 1, pad 1."""
+    rng = np.random.default_rng(seed + 1)
+    return ConvLayer(image(4, 32, seed), rng.uniform(-1, 1, (4, 4, 3, 3)), np.zeros(4), 1, 1,
+                     "toy 4x32x32 conv3x3 4->4")
+
+
+def cifar_conv_bn(seed=0, c=16, m=32):
+    """16x32x32 image, 3x3 conv 16->16 (PyTorch default init), BN folded, /8 for the GELU."""
+    while True:
+        rng = np.random.default_rng(seed + 1)
+        x = image(c, m, seed)
+        bound = 1.0 / math.sqrt(c * 9)
+        W = rng.uniform(-bound, bound, (c, c, 3, 3))
+        Wf, bf = fold_bn(x, W, 1)
+        pre = _plain_conv(x, Wf, 1) + bf[:, None, None]
+        if np.abs(pre).max() <= 1.0:
+            return ConvLayer(x, Wf, bf, 1, 1, "cifar %dx%dx%d conv3x3+BN" % (c, m, m))
+        seed += 1000
+
+
+def imagenet_stem(seed=0):
+    """224x224x3 image, 7x7 conv 3->64, stride 2, pad 3, weights N(0, 0.05^2)."""
+    rng = np.random.default_rng(seed + 1)
+    return ConvLayer(image(3, 224, seed), rng.normal(0.0, 0.05, (64, 3, 7, 7)), np.zeros(64), 2,
+                     3, "imagenet stem 3x224x224 conv7x7/2 3->64")
+
+
+def resnet_block(seed=0, c=64, m=56):
+    """Basic block on 64x56x56: conv3x3-BN-GELU-conv3x3 (+ residual); BN folded per conv."""
+    x = image(c, m, seed)
+    rng = np.random.default_rng(seed + 1)
+    bound = 1.0 / math.sqrt(c * 9)
+    W1 = rng.uniform(-bound, bound, (c, c, 3, 3))
+    W2 = rng.uniform(-bound, bound, (c, c, 3, 3))
+    W1f, b1f = fold_bn(x, W1, 1)
+    return x, (W1f, b1f), (W2 / 8.0, np.zeros(c))
+
+
+def poisson_arrivals(n, rate, seed=0):
+    """Arrival times (seconds) of n requests at `rate` requests/second."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, n))
+
+
+def request_sizes(n, seed=0, sizes=(32, 64, 224), mix=(0.6, 0.3, 0.1)):
+    rng = np.random.default_rng(seed + 7)
+    return [int(s) for s in rng.choice(sizes, size=n, p=mix)]
