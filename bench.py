@@ -1,0 +1,289 @@
+"""Benchmark: one CIFAR-shaped encrypted layer at ring 2^16 on one GB300.
+
+Step = one pass of the whole hot path over one encrypted 16x32x32 image: hconv2d (3x3,
+16->16, BN folded, 143 hoisted rotations, 144-term fused MAC, rescale, bias) followed by the
+degree-16 Chebyshev GELU (15 relinearised products).  Parameters: n = 2^16, 20 ciphertext
+primes (50 + 19 x 40 bits), 5 special primes, dnum 4, scale 2^40, input level 19.  Keys
+(14.4 GB) and plaintexts (1.4 GB) are resident; every step streams them from HBM, so the
+working set is far larger than L2 and no flush is needed.
+
+Prints one JSON line (rank 0).  value = key switches per second (rotations + relins) over all
+ranks; ms_per_step = layer latency.  The batched mode is the headline; the plain
+per-ciphertext path is timed beside it.  N > 1 runs independent replicas (the layer does
+not shard across GPUs).  --impl reference times the CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HE conv-layer ms and key-switches/s at 2N=2^16 on 1 GB300, batched vs plain"
+WORKLOAD = "cifar layer: 16x32x32 conv3x3 16->16 + folded BN + degree-16 Chebyshev GELU, 2N=2^16, 20+5 primes"
+LEVEL = 19
+DEG = 16
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(sample_rotations=2):
+    """The oracle as it stands on this host's cores: hoisted rotations of the layer input at
+    the full ring (keys for them generated first, untimed)."""
+    import workloads
+    from oracle import layers as Ly
+    from oracle.ckks import Context
+    from oracle.params import C20
+    o = Context(C20)
+    wl = workloads.cifar_conv_bn(0)
+    lin = Ly.image_layout(16, 32, o.N)
+    ct = o.encrypt(Ly.pack(lin, wl.x)[0], LEVEL, nonce=1)
+    amounts = [1, 32][:sample_rotations]
+    for a in amounts:
+        o.gen_rotation_key(a)
+    t0 = time.perf_counter()
+    D = o.hoist(ct)
+    for a in amounts:
+        o.rotate_hoisted(ct, D, a)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": len(amounts) / dt, "unit": "key-switches/s", "cores": cores, "kind": "oracle",
+            "sample": "%d hoisted rotations (ModUp once, inner product, ModDown) of the layer input "
+                      "at n=2^16, level 19; %.1f s" % (len(amounts), dt)}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        pass
+    base = None
+    for _ in range(args.steps):
+        base = cpu_baseline(1)
+        steps.append(1.0 / base["value"])
+    ms = 1e3 * statistics.mean(steps)
+    line = {"impl": "reference", "metric": METRIC, "value": 1e3 / ms, "unit": "key-switches/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "reference": "CPU oracle, one hoisted "
+                                            "rotation of the layer input per step"},
+            "cpu_baseline": {"value": 1e3 / ms, "unit": "key-switches/s", "cores": base["cores"],
+                             "kind": "oracle", "sample": base["sample"]},
+            "e2e": {"value": 1e3 / ms, "unit": "key-switches/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--trace", default="ip", help="kernel whose launches the roofline uses")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    ws, rank, local = _dist()
+    import torch
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import workloads
+    from oracle import layers as Ly          # host-side packing and Chebyshev coefficients only
+    from oracle.params import C20
+    from paper_2306_09189_gb300 import hegpu as H
+
+    pr = C20
+    ctx = H.he_ctx_create(H.he_params(pr.log_n, pr.n_q, pr.n_p, pr.dnum, pr.q0_bits, pr.q_bits,
+                                      pr.p_bits, pr.scale, pr.seed))
+    info = H.he_ctx_info(ctx)
+    n, N = info["n"], info["slots"]
+    wl = workloads.cifar_conv_bn(0)
+    lin = Ly.image_layout(16, 32, N)
+    slots = Ly.pack(lin, wl.x)[0]
+    cheb = Ly.cheb_nodes_coeffs(Ly.gelu, DEG, -8, 8)
+    lay = H.he_layout_image(16, 32, N)
+    x = H.he_ct_alloc(ctx, LEVEL)
+    H.he_encrypt(ctx, slots, LEVEL, pr.scale, 1, x)
+    conv = H.he_conv_create(ctx, lay, wl.W, wl.bias, 1, 1, LEVEL, pr.scale)
+    rots = H.he_conv_rotations(conv)
+    H.he_keygen_rotations(ctx, rots)
+    H.he_keygen_relin(ctx)
+    y = H.he_ct_alloc(ctx, LEVEL - 1)
+    ks_per_step = len(rots) + (DEG - 1)
+    stream = torch.cuda.current_stream()
+
+    def step(mode):
+        H.he_conv_run(ctx, conv, [x], [y], mode, stream)
+        H.he_poly_eval(ctx, y, cheb, pr.scale, stream)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(mode, k, trace=None):
+        for _ in range(args.warmup):
+            step(mode)
+        barrier()
+        if trace:
+            H.he_trace_start(trace)
+        l0 = H.he_kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            step(mode)
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        launches = H.he_kernel_launches() - l0
+        tr = H.he_trace_stop() if trace else None
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / k, launches, tr
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms_b, launches_b, tr = timed(H.HE_BATCHED, args.steps, args.trace)
+    clk = clocks.stop()
+    ms_p, _, _ = timed(H.HE_PLAIN, max(1, args.steps // 2))
+
+    # end to end through the C ABI with host buffers: pinned host ciphertext in, result out
+    xin = H.he_ct_export_coeffs(ctx, x, n)
+    h_in = torch.empty(xin.size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64).reshape(xin.shape)
+    h_in[:] = xin
+    out_level = LEVEL - 1 - (DEG.bit_length() if DEG & (DEG - 1) else DEG.bit_length() - 1) - 1
+    out_shape = (2, out_level + 1, n)
+    h_out = torch.empty(int(np.prod(out_shape)), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    xe = H.he_ct_alloc(ctx, LEVEL)
+
+    def e2e_step():
+        H.he_ct_import_coeffs(xe, h_in, LEVEL, pr.scale, stream)
+        H.he_conv_run(ctx, conv, [xe], [y], H.HE_BATCHED, stream)
+        H.he_poly_eval(ctx, y, cheb, pr.scale, stream)
+        assert H.he_ct_level(y) == out_level
+        H.load().he_ct_export_coeffs(y, H._p(h_out, H.U64P), H.stream_ptr(stream))
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    barrier()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+
+    peaks, src = _peaks()
+    roof = None
+    if tr and tr["launches"]:
+        per_launch_ms = tr["ms"] / tr["launches"]
+        achieved = tr["bytes"] / tr["launches"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": args.trace, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": src, "launches": tr["launches"], "ms_per_launch": per_launch_ms,
+                "share_of_step": tr["ms"] / (ms_b * args.steps)}
+    mm_rate = H.he_bench_modmul(ctx, 152 * 8, 2048)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": ws * ks_per_step / (ms_b * 1e-3), "unit": "key-switches/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": "batched", "key_switches_per_step": ks_per_step,
+                       "rotations": int(len(rots)), "relins": DEG - 1, "input_level": LEVEL,
+                       "l2": "inputs larger than L2 (rotation keys %.1f GB streamed every step)" % (H.he_key_bytes(ctx) / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "plain": {"ms_per_step": ms_p, "value": ws * ks_per_step / (ms_p * 1e-3),
+                      "batched_speedup": ms_p / ms_b},
+            "e2e": {"value": ws * ks_per_step / (e2e_ms * 1e-3), "unit": "key-switches/s",
+                    "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(h_in.nbytes),
+                    "d2h_bytes_per_step": int(np.prod(out_shape) * 8)},
+            "gpu_launches": int(launches_b),
+            "roofline": roof,
+            "modmul_microbench_per_s": mm_rate,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(2)
+        print(json.dumps(line), flush=True)
+    H.he_conv_destroy(conv)
+    for c in (x, y, xe):
+        H.he_ct_free(c)
+    H.he_ctx_destroy(ctx)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,260 @@
+/*
+ * hegpu -- homomorphic convolution and average pooling over RNS-CKKS ciphertexts that hold a
+ * row-major packed image sharded across several ciphertexts, on one GB300 (sm_103a).
+ *
+ * Paper: "High-Resolution Convolutional Neural Networks on Homomorphically Encrypted Data via
+ * Sharding Ciphertexts" (arXiv 2306.09189).  Sec. 2 fixes the scheme: RNS-CKKS over
+ * R_Q = Z_Q[X]/(X^{2N}+1), N real slots per ciphertext, levels consumed by multiplications,
+ * slot rotations.  Sec. 4 gives the layer algorithms (shift operator Eq. 1, partial
+ * convolutions Eqs. 2-5, image shards Eq. 6, duplication/permutation metadata, channel
+ * shards Eq. 7, pooling Eqs. 10-13); the Appendix the Chebyshev-basis activation.
+ *
+ * Conventions for every entry point
+ *   - Return value: HE_OK (0) or a negative HE_E* code; he_last_error() gives a message
+ *     (thread-local).  No C++ exception crosses this boundary.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *     enqueued on it; host-pointer outputs are complete when the call returns.
+ *   - Ring degree n = 2^log_n (the paper's 2N), N = n/2 slots.  Level l means primes
+ *     q_0..q_l are live.  Ciphertexts live on the device in NTT form; the host exchange
+ *     format is coefficient form, residues in [0, q_i), layout [2][l+1][n] uint64.
+ *   - All ciphertext arithmetic is exact integer arithmetic mod the RNS primes (uint64
+ *     limbs); floating point appears only in encoding and in scale bookkeeping.
+ *   - One context is driven from one host thread and one stream at a time: the context owns
+ *     the scratch buffers that key switching uses.
+ *   - Device memory: the library allocates with cudaMalloc; he_ct_wrap lets a caller hand
+ *     in its own device buffer (for instance a torch tensor's storage).
+ */
+#ifndef HEGPU_H
+#define HEGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    HE_OK = 0,
+    HE_EINVAL = -1,    /* bad argument, shape or layout */
+    HE_ELEVEL = -2,    /* not enough levels left for the operation */
+    HE_EKEY = -3,      /* a rotation or relinearisation key is missing */
+    HE_ENOMEM = -4,    /* device or host allocation failed */
+    HE_ETIMEOUT = -5,  /* a bounded device wait gave up */
+    HE_ECUDA = -6,     /* CUDA runtime error */
+    HE_ESTATE = -7     /* object used in the wrong state (e.g. wrong context) */
+};
+
+enum { HE_PLAIN = 0, HE_BATCHED = 1 };
+enum { HE_RELIN_KEY = 0x7fffffff };   /* key id of the relinearisation key in he_key_export */
+
+typedef struct he_ctx he_ctx;
+typedef struct he_ct he_ct;
+typedef struct he_pt he_pt;
+typedef struct he_conv he_conv;
+typedef struct he_pool he_pool;
+typedef struct he_poly he_poly;
+
+/* Scheme parameters (Sec. 2; the paper uses ring 2^16 and 59-bit scales, Sec. 5.3).
+ * Prime rule: every prime = 1 mod 2n; primes of b bits are the largest such primes below
+ * 2^b in descending order, drawn in the order q_0 (q0_bits), p_0..p_{n_p-1} (p_bits),
+ * q_1..q_{n_q-1} (q_bits), each the next unused prime of its size.
+ * Key switching is hybrid with dnum digits of alpha = ceil(n_q/dnum) primes.
+ * seed keys the counter-based SplitMix64 generator that draws the secret, key and
+ * encryption randomness (stream ids in the design notes). */
+typedef struct {
+    int log_n;       /* 9..17 */
+    int n_q;         /* ciphertext primes, L = n_q - 1 */
+    int n_p;         /* special primes K */
+    int dnum;        /* key-switching digits */
+    int q0_bits, q_bits, p_bits;   /* each in [20, 61] */
+    double scale;    /* Delta */
+    uint64_t seed;
+} he_params;
+
+/* Image layout metadata (Sec. 4 "Sharding and Encrypting an Image", "Duplicating and
+ * Permuting Channels").  Each channel's valid m x m pixels sit row-major in an M x M frame
+ * (M = next power of two of m, row stride M).  A shard of N slots is cut into nb blocks of
+ * B = min(M*M, N) slots; block b of shard u holds the frame rows [row0, row0 + B/M) of
+ * channel chan[u*nb + b] (-1 = empty).  This single table expresses image shards, channel
+ * shards, the duplication factor d and the pooling permutation tau. */
+#define HE_MAX_BLOCKS 4096
+typedef struct {
+    int c, m, M, N, B;
+    int n_shards, nb;
+    int32_t chan[HE_MAX_BLOCKS];
+    int32_t row0[HE_MAX_BLOCKS];
+} he_layout;
+
+const char *he_last_error(void);
+
+/* Library build id and the number of kernels it launched so far (all contexts). */
+const char *he_version(void);
+uint64_t he_kernel_launches(void);
+
+/* Host only, no GPU needed: the prime chain the rule above gives, q[n_q] and p[n_p]. */
+int he_params_primes(const he_params *params, uint64_t *q, uint64_t *p);
+
+/* Host only: the initial layout of a c x m x m image over shards of N slots (no
+ * permutation; one shard with tiled duplication when c M^2 <= N, image shards when
+ * M^2 <= N < c M^2, channel shards of N/M rows when M^2 > N). */
+int he_layout_image(int c, int m, int N, he_layout *out);
+
+/* ------------------------------------------------------------------ context and keys */
+int he_ctx_create(const he_params *params, he_ctx **out);
+void he_ctx_destroy(he_ctx *ctx);
+/* n, N, L, K, dnum, alpha; q[L+1] and p[K] when the pointers are non-NULL. */
+int he_ctx_info(const he_ctx *ctx, int *n, int *slots, int *L, int *K, int *dnum, int *alpha,
+                uint64_t *q, uint64_t *p);
+
+/* Rotation keys for the left rotations rot[i] (slot j <- slot j + r; Galois element
+ * 5^(r mod N) mod 2n).  Keys already present are skipped.  Device resident, Montgomery
+ * NTT form, layout [dnum][2][L+1+K][n]. */
+int he_keygen_rotations(he_ctx *ctx, const int32_t *rot, size_t n_rot);
+/* Relinearisation key (switches s^2 to s). */
+int he_keygen_relin(he_ctx *ctx);
+int he_has_rotation_key(const he_ctx *ctx, int32_t rot);
+/* Key in coefficient form, host layout [dnum][2][L+1+K][n]; rot = HE_RELIN_KEY for relin. */
+int he_key_export(he_ctx *ctx, int32_t rot, uint64_t *host);
+/* Total bytes of device-resident keys. */
+size_t he_key_bytes(const he_ctx *ctx);
+
+/* ------------------------------------------------------------------ ciphertexts */
+int he_ct_alloc(he_ctx *ctx, int level, he_ct **out);
+/* Wrap caller-owned device memory of at least 2*(level+1)*n*8 bytes (not freed by us). */
+int he_ct_wrap(he_ctx *ctx, void *dev_ptr, size_t bytes, int level, he_ct **out);
+void he_ct_free(he_ct *ct);
+int he_ct_level(const he_ct *ct);
+double he_ct_scale(const he_ct *ct);
+int he_ct_set_scale(he_ct *ct, double scale);
+/* Device pointer of limb i of polynomial k (k in {0,1}). */
+void *he_ct_limb_ptr(const he_ct *ct, int k, int i);
+int he_ct_copy(he_ct *dst, const he_ct *src, void *stream);
+/* Drop the top limbs down to `level` (exact, no rescale). */
+int he_ct_drop_level(he_ct *ct, int level);
+
+/* Host coefficient form [2][level+1][n], residues in [0, q_i) -> device NTT form. */
+int he_ct_import_coeffs(he_ct *ct, const uint64_t *host, int level, double scale, void *stream);
+/* Device -> host coefficient form [2][level+1][n]. */
+int he_ct_export_coeffs(const he_ct *ct, uint64_t *host, void *stream);
+
+/* Secret-key encryption (test and client side; no security claim) of the integer message
+ * polynomial m[n]: (c0, c1) = (-a s + e + m, a) over Q_level, randomness keyed by nonce. */
+int he_encrypt_coeffs(he_ctx *ctx, const int64_t *m, int level, double scale, uint64_t nonce,
+                      he_ct *out, void *stream);
+/* Encode slots (canonical embedding, Sec. 2) at `scale`, then he_encrypt_coeffs. */
+int he_encrypt(he_ctx *ctx, const double *slots, size_t n_slots, int level, double scale,
+               uint64_t nonce, he_ct *out, void *stream);
+/* Decrypt and decode N slots.  Exact while |c0 + c1 s| < q_0 q_1 / 2 coefficient-wise. */
+int he_decrypt(he_ctx *ctx, const he_ct *ct, double *slots, size_t n_slots, void *stream);
+
+/* ------------------------------------------------------------------ plaintexts */
+/* Integer plaintext m[n] (coefficients) at `level`, stored for multiplication. */
+int he_pt_import_coeffs(he_ctx *ctx, const int64_t *m, int level, double scale, he_pt **out);
+int he_pt_encode(he_ctx *ctx, const double *slots, size_t n_slots, int level, double scale,
+                 he_pt **out);
+void he_pt_free(he_pt *pt);
+
+/* ------------------------------------------------------------------ primitives */
+/* Non-hoisted rotation by r (Sec. 4.1: a column shift is a rotation by 1, a row shift a
+ * rotation by m): out = (phi_g(c0) + ModDown(u0), ModDown(u1)),
+ * u = sum_j ModUp(phi_g(c1))_j * ksk_g[j].  out may not alias in. */
+int he_rotate(he_ctx *ctx, const he_ct *in, int32_t r, he_ct *out, void *stream);
+/* Hoisted rotations of one ciphertext by r[0..n_r-1]: ModUp(c1) once, then
+ * u = sum_j phi_g(ModUp(c1)_j) * ksk_g[j] per amount ("computed once and cached", Sec. 4.1).
+ * r = 0 copies.  out[i] must be allocated at in's level. */
+int he_rotate_hoisted(he_ctx *ctx, const he_ct *in, const int32_t *r, size_t n_r, he_ct **out,
+                      void *stream);
+/* acc = 0 at `level` with the given scale. */
+int he_ct_zero(he_ct *acc, int level, double scale, void *stream);
+/* acc += ct (.) pt  (plaintext x ciphertext multiply-accumulate, Sec. 4.1: mask and kernel
+ * weight merged on the plaintext side).  acc's scale becomes ct.scale * pt.scale. */
+int he_mul_pt_acc(he_ctx *ctx, he_ct *acc, const he_ct *ct, const he_pt *pt, void *stream);
+/* Drop q_l: c' = round(c / q_l) (centred representative of the top limb); scale /= q_l. */
+int he_rescale(he_ctx *ctx, he_ct *ct, void *stream);
+int he_add(he_ctx *ctx, he_ct *acc, const he_ct *b, void *stream);
+int he_sub(he_ctx *ctx, he_ct *acc, const he_ct *b, void *stream);
+/* ct *= c for an integer c given as a double holding an exact integer (|c| < 2^127). */
+int he_mul_int(he_ctx *ctx, he_ct *ct, double c, void *stream);
+/* c0 += c (constant polynomial) for an exact-integer double c. */
+int he_add_const_int(he_ctx *ctx, he_ct *ct, double c, void *stream);
+/* Tensor, relinearise, rescale (levels must match; Appendix, Chebyshev evaluation). */
+int he_mul_relin(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out, void *stream);
+
+/* ------------------------------------------------------------------ layers (Sec. 4) */
+/* Plan a stride-1 'same' convolution (cross-correlation, W[co][ci][kh][kw], bias[co] or
+ * NULL) for an input image with layout `in` at `level`: the rotation set and the diagonal
+ * plaintexts D_{u,v,a} that merge shift masks and kernel weights (Sec. 4.1 "combined
+ * non-homomorphically"), encoded at scale q_level, plus the bias encoded at the output
+ * scale in_scale.  stride 2 is the unstrided convolution followed by the top-left select
+ * of the pooling program (Sec. 4.1, last paragraph of "With a Single Shard").
+ * Rotation keys are not generated here: see he_conv_rotations. */
+int he_conv_create(he_ctx *ctx, const he_layout *in, const double *W, const double *bias,
+                   int co, int ci, int kh, int kw, int stride, int pad, int level,
+                   double in_scale, he_conv **out);
+void he_conv_destroy(he_conv *conv);
+int he_conv_out_layout(const he_conv *conv, he_layout *out);
+int he_conv_out_level(const he_conv *conv);
+/* Distinct non-zero rotation amounts the plan needs (all stages); returns the count,
+ * writes up to cap of them. */
+int he_conv_rotations(const he_conv *conv, int32_t *amounts, size_t cap);
+/* Number of diagonal terms of the stride-1 stage and their (u, v, a) in plan order
+ * (v, then u, then a ascending); diag (optional) receives [n_terms][N] doubles. */
+int he_conv_n_terms(const he_conv *conv);
+int he_conv_export_plan(const he_conv *conv, int32_t *u, int32_t *v, int32_t *a, double *diag);
+/* Replace the plan's encoded plaintexts by caller-given integer polynomials (plan order,
+ * [n_terms][n]) and bias plaintexts ([n_out][n]); used to run on plaintexts encoded
+ * elsewhere, e.g. for bit-exact comparison. */
+int he_conv_import_plaintexts(he_conv *conv, const int64_t *terms, const int64_t *bias);
+/* Run: out[v] (allocated by the caller at he_conv_out_level) for v < out layout n_shards.
+ * mode HE_PLAIN = per-ciphertext launches; HE_BATCHED = every rotation of a stage in one
+ * launch per kernel (keys read once per amount for all shards).  Same bits either way. */
+int he_conv_run(he_ctx *ctx, he_conv *conv, he_ct *const *in, he_ct **out, int mode,
+                void *stream);
+
+/* 2x2 average pool (Sec. 4.2): downsample (2x2 ones convolution, horizontal reduction
+ * Eq. 10, vertical reduction Eq. 11), consolidate 4 shards into one (Eq. 12, channel order
+ * permuted for image shards) or duplicate when 1-2 shards remain (Eq. 13).  Two levels. */
+int he_pool_create(he_ctx *ctx, const he_layout *in, int level, he_pool **out);
+void he_pool_destroy(he_pool *pool);
+int he_pool_out_layout(const he_pool *pool, he_layout *out);
+int he_pool_rotations(const he_pool *pool, int32_t *amounts, size_t cap);
+/* Replace the mask plaintexts by caller-given integer polynomials: h [n_h][n_shards][n] for
+ * the horizontal stage (column x' = 0, 1, ...) and v [n_v][n_shards][n] for the vertical
+ * stage (rows y' whose mask is not empty), the order the plan uses. */
+int he_pool_n_masks(const he_pool *pool, int *n_h, int *n_v);
+int he_pool_import_plaintexts(he_pool *pool, const int64_t *h, const int64_t *v);
+int he_pool_run(he_ctx *ctx, he_pool *pool, he_ct *const *in, he_ct **out, int mode,
+                void *stream);
+
+/* Chebyshev-basis polynomial sum_k c_k T_k(x) on a ciphertext holding x in [-1, 1]
+ * (Appendix: T_{2k} = 2 T_k^2 - 1, T_{2k+1} = 2 T_k T_{k+1} - T_1, exact-scale constants).
+ * Depth ceil(log2 deg) + 1; needs the relinearisation key.  io is replaced by the result
+ * (scale `target_scale`, level lowered by the depth). */
+int he_poly_eval(he_ctx *ctx, he_ct *io, const double *cheb, int deg, double target_scale,
+                 void *stream);
+
+/* Convenience wrappers: create, run, destroy. */
+int he_hconv2d(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, const double *W,
+               const double *bias, int co, int ci, int kh, int kw, int stride, int pad,
+               int mode, he_layout *out_layout, he_ct **out_cts, void *stream);
+int he_havgpool(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, he_layout *out_layout,
+                he_ct **out_cts, int mode, void *stream);
+
+/* ------------------------------------------------------------------ measurement */
+/* Per-kernel tracing.  he_trace_start(name) selects one kernel (e.g. "ip", "ntt", "mac",
+ * "modup", "moddown_fbc", "moddown_combine", "rescale"); every later launch of it is bracketed
+ * by CUDA events recorded on the stream it is launched on.  he_trace_stop synchronises those
+ * events and returns the summed device time, the launch count and the launches' algorithmic
+ * work: minimal bytes (inputs + keys + outputs, intermediates excluded) and modular products. */
+int he_trace_start(const char *kernel);
+int he_trace_stop(double *total_ms, uint64_t *launches, double *bytes, double *mulmods);
+
+/* Time the integer pipe: `iters` dependent 64-bit Montgomery products per thread over
+ * `blocks` x 256 threads; returns modular products per second (device-timed). */
+int he_bench_modmul(he_ctx *ctx, int blocks, int iters, double *mulmods_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

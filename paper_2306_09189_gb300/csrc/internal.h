@@ -1,0 +1,223 @@
+// Internal declarations shared by the hegpu translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/hegpu.h"
+
+typedef uint64_t u64;
+typedef unsigned __int128 u128;
+
+// ----------------------------------------------------------------------------- errors
+void he_set_error(const char *fmt, ...);
+#define HE_CHECK_CUDA(expr)                                                        \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess) {                                                   \
+            he_set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr,                \
+                         cudaGetErrorString(_e));                                  \
+            return HE_ECUDA;                                                       \
+        }                                                                          \
+    } while (0)
+#define HE_TRY(expr)                \
+    do {                            \
+        int _rc = (expr);           \
+        if (_rc != HE_OK) return _rc; \
+    } while (0)
+
+void he_count_launch(int k = 1);
+
+// Per-kernel tracing: while a kernel name is selected, every launch of that kernel is
+// bracketed by CUDA events on its own stream and its algorithmic work is accumulated.
+struct TraceScope {
+    bool on = false;
+    cudaStream_t s = 0;
+    cudaEvent_t b = nullptr;
+    double bytes = 0, mulmods = 0;
+    TraceScope(const char *name, cudaStream_t st, double bytes_, double mulmods_);
+    ~TraceScope();
+};
+
+// ----------------------------------------------------------------------------- tables
+// Every table is indexed by the global prime index: q_0..q_L are 0..L, p_k is L+1+k.
+struct KP {                  // kernel parameters passed by value
+    int n, logn, L, K;
+    const u64 *q;            // primes
+    const u64 *qinv;         // q^{-1} mod 2^64 (Montgomery)
+    const u64 *r2;           // 2^128 mod q (to Montgomery form)
+    const u64 *mu;           // floor(2^64 / q) (64-bit Barrett)
+    const u64 *tw, *tws;     // [np][n] psi^{brev(k)} and its Shoup companion
+    const u64 *itw, *itws;   // [np][n] psi^{-brev(k)} and Shoup
+    const u64 *ninv, *ninvs; // [np] n^{-1} and Shoup
+};
+
+// Fast-base-conversion table for one (source set -> target set) conversion.
+struct FbcTable {
+    int n_src, n_dst;
+    u64 *d;                  // device: [n_src] inv_hat, [n_src] inv_hat_shoup,
+                             //         [n_dst][n_src] hat (Montgomery), [n_dst][n_src] -hat (Mont)
+    std::vector<int> src_prime, dst_prime;   // global prime indices
+};
+
+struct DeviceKey {           // hybrid key-switching key, Montgomery NTT form
+    u64 *d = nullptr;        // [dnum][2][L+1+K][n]
+    int id = 0;
+};
+
+struct Scratch {             // grow-only device scratch owned by the context
+    u64 *p = nullptr;
+    size_t words = 0;
+    int ensure(size_t w);
+    ~Scratch();
+};
+
+// ----------------------------------------------------------------------------- objects
+struct he_ct {
+    he_ctx *ctx = nullptr;
+    u64 *d = nullptr;        // poly k, limb i at d + k*pstride + i*n   (NTT form)
+    size_t pstride = 0;      // words between the two polynomials
+    int cap = 0;             // allocated level
+    int level = 0;
+    double scale = 1.0;
+    bool owned = true;
+};
+
+struct he_pt {
+    he_ctx *ctx = nullptr;
+    u64 *d = nullptr;        // [level+1][n], Montgomery NTT form
+    int level = 0;
+    double scale = 1.0;
+};
+
+struct he_ctx {
+    he_params pr;
+    int n, logn, N, L, K, dnum, alpha, np;
+    std::vector<u64> primes;             // global order
+    std::vector<u64> psi;                // primitive 2n-th roots
+    KP kp;
+    u64 *d_tables = nullptr;
+    std::vector<u64> h_qinv, h_mu, h_r2;
+    // ModUp tables: [level][digit]; ModDown tables: [level]
+    std::vector<std::vector<FbcTable>> modup;
+    std::vector<FbcTable> moddown;
+    std::vector<u64> pinv, pinv_s;       // [L+1] P^{-1} mod q_i and Shoup
+    std::vector<u64> pmod;               // [L+1] P mod q_i
+    u64 *d_consts = nullptr;             // device copies of small per-level constant arrays
+    // secret key (this library also plays the client, for tests and benchmarks)
+    u64 *d_s = nullptr;                  // [L+1+K][n] NTT form, normal
+    std::map<int, DeviceKey> keys;       // key id (Galois element; 0 = relin) -> key
+    Scratch sc_digits, sc_u, sc_conv, sc_tmp, sc_tmp2;
+    size_t key_bytes = 0;
+};
+
+struct ntt_job {
+    u64 *base;               // poly p, limb l at base + p*poly_stride + l*n
+    size_t poly_stride;
+    int l0, nl;              // limbs [l0, l0+nl) of each poly
+    int nq;                  // limbs < nq use prime q_limb, limbs >= nq use p_(limb-nq)
+    int skip_alpha;          // if > 0: in poly p skip limbs [p*skip_alpha, min((p+1)*skip_alpha, nq))
+    int npoly;
+};
+
+// ----------------------------------------------------------------------------- kernels
+int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s);
+int k_reduce_int(const he_ctx *ctx, const int64_t *m, u64 *out, int nlimbs, int nq, bool mont,
+                 cudaStream_t s);
+int k_to_mont(const he_ctx *ctx, u64 *x, int nlimbs, int nq, int npoly, size_t pstride,
+              cudaStream_t s);
+int k_from_mont(const he_ctx *ctx, u64 *x, int nlimbs, int nq, int npoly, size_t pstride,
+                cudaStream_t s);
+int k_sample_uniform(const he_ctx *ctx, u64 seed, u64 stream, u64 *out, int nlimbs, int nq,
+                     cudaStream_t s);
+int k_sample_cbd(const he_ctx *ctx, u64 seed, u64 stream, int64_t *out, cudaStream_t s);
+int k_sample_ternary(const he_ctx *ctx, u64 seed, u64 stream, int64_t *out, cudaStream_t s);
+int k_permute(const he_ctx *ctx, const u64 *in, u64 *out, int nlimbs, u64 g, cudaStream_t s);
+int k_keygen_combine(const he_ctx *ctx, u64 *b, u64 *a, const u64 *e, const u64 *s_eval,
+                     const u64 *sp_eval, int digit, cudaStream_t s);
+int k_encrypt_combine(const he_ctx *ctx, u64 *c0, const u64 *a, const u64 *e, const u64 *m,
+                      int level, cudaStream_t s);
+int k_decrypt_dot(const he_ctx *ctx, const he_ct *ct, u64 *out, int nlimbs, cudaStream_t s);
+int k_add(const he_ctx *ctx, he_ct *acc, const he_ct *b, bool sub, cudaStream_t s);
+int k_mul_scalar(const he_ctx *ctx, he_ct *ct, const u64 *res /*device [l+1]*/, const u64 *shoup,
+                 cudaStream_t s);
+int k_add_const(const he_ctx *ctx, he_ct *ct, const u64 *res_dev, cudaStream_t s);
+int k_zero(u64 *p, size_t words, cudaStream_t s);
+int k_copy_limbs(u64 *dst, size_t dst_pstride, const u64 *src, size_t src_pstride,
+                 size_t words_per_poly, int npoly, cudaStream_t s);
+
+// Key switching.  D: [beta][level+1+K][n]; u: [2][level+1+K][n]; conv: [2][level+1][n].
+int k_modup(const he_ctx *ctx, const u64 *x_coef, const u64 *x_ntt, u64 *D, int level,
+            cudaStream_t s);
+struct ip_item {            // one key-switching inner product
+    const u64 *D;           // raised digits
+    const u64 *key;         // key [dnum][2][L+1+K][n]
+    u64 *u;                 // output [2][level+1+K][n]
+    u64 g;                  // automorphism applied to D on the fly (1 = none)
+    int beta;               // digits used at this level, ceil((level+1)/alpha)
+};
+int k_inner_product(const he_ctx *ctx, const ip_item *items_dev, int n_items, int level,
+                    cudaStream_t s);
+int k_moddown_fbc(const he_ctx *ctx, const u64 *u, u64 *conv, int level, int npoly,
+                  cudaStream_t s);
+struct md_item {            // out_c = base_c[phi_g] + (u_c - conv_c) * P^{-1}
+    const u64 *u;           // [2][level+1+K][n]
+    const u64 *conv;        // [2][level+1][n]
+    const u64 *base;        // NULL or ct (poly 0 at base, poly 1 at base + base_pstride)
+    size_t base_pstride;
+    int base_polys;         // 1: add base to out0 only; 2: add to both
+    u64 g;                  // automorphism on base reads (1 = none)
+    u64 *out;               // ct data
+    size_t out_pstride;
+};
+int k_moddown_combine(const he_ctx *ctx, const md_item *items_dev, int n_items, int level,
+                      cudaStream_t s);
+int k_rescale_prep(const he_ctx *ctx, const u64 *top_coef, size_t top_pstride, u64 *t, int level,
+                   cudaStream_t s);
+int k_rescale_combine(const he_ctx *ctx, he_ct *ct, const u64 *t, cudaStream_t s);
+struct mac_term {
+    const u64 *pt;          // [level+1][n] Montgomery
+    const u64 *ct;          // ct data
+    size_t ct_pstride;
+};
+int k_mac(const he_ctx *ctx, const mac_term *terms_dev, int n_terms, u64 *out, size_t out_pstride,
+          int level, bool accumulate, cudaStream_t s);
+int k_tensor(const he_ctx *ctx, const he_ct *a, const he_ct *b, u64 *d /*[3][l+1][n]*/,
+             cudaStream_t s);
+int k_inner_product_one(const he_ctx *ctx, const ip_item &it, int level, cudaStream_t s);
+int k_moddown_combine_one(const he_ctx *ctx, const md_item &it, int level, cudaStream_t s);
+int k_mac_one(const he_ctx *ctx, const mac_term &t, u64 *out, size_t out_pstride, int level,
+              bool accumulate, cudaStream_t s);
+int k_mul_scalar_v(const he_ctx *ctx, he_ct *ct, const u64 *res, const u64 *shoup, int polys,
+                   cudaStream_t s);
+int k_add_const_v(const he_ctx *ctx, he_ct *ct, const u64 *res, cudaStream_t s);
+int k_mul_pointwise(const he_ctx *ctx, const u64 *a, const u64 *b, u64 *out, int nlimbs,
+                    cudaStream_t s);
+double k_bench_modmul(const he_ctx *ctx, int blocks, int iters, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- host helpers
+u64 h_mulmod(u64 a, u64 b, u64 q);
+u64 h_powmod(u64 a, u64 e, u64 q);
+u64 h_invmod(u64 a, u64 q);
+u64 h_shoup(u64 w, u64 q);
+u64 h_galois(const he_ctx *ctx, int32_t r);
+int prime_index(const he_ctx *ctx, int limb, int nq);   // limb of a Q_l u P polynomial -> prime
+void encode_slots(const double *z, int n, double S, int64_t *m_out);
+void decode_coeffs(const double *m, int n, double S, double *z_out);
+int ensure_ct(he_ctx *ctx, he_ct *ct, int level);
+int keyswitch_core(he_ctx *ctx, const u64 *d_ntt, int level, const DeviceKey &key, u64 g_apply,
+                   const u64 *base, size_t base_pstride, int base_polys, u64 g_base, he_ct *out,
+                   cudaStream_t s);
+int get_key(he_ctx *ctx, int key_id, const DeviceKey **out);
+// IP + ModDown + combine for one rotation of the raised digits D (see context.cu)
+int ks_tail(he_ctx *c, const u64 *D, int level, const DeviceKey &key, u64 g_apply,
+            const u64 *base, size_t base_pstride, int base_polys, u64 g_base, u64 *out,
+            size_t out_pstride, cudaStream_t s);
+int k_add_raw(const he_ctx *ctx, u64 *a, size_t pa, const u64 *b, size_t pb, int nlimbs, int npoly,
+              bool sub, cudaStream_t s);
+int hoist_modup(he_ctx *ctx, const he_ct *in, u64 *D, cudaStream_t s);
+int upload_async(void *dst, const void *src, size_t bytes, cudaStream_t s);

@@ -1,0 +1,1047 @@
+// The paper's layer programs on sharded ciphertexts (Sec. 4): the host planner (layout
+// metadata, rotation sets, diagonal plaintexts, pooling masks) and the drivers that run the
+// key switches, the fused plaintext x ciphertext MAC and the rescales on the device.
+//
+// Two execution modes give the same bits: HE_PLAIN launches the key-switching kernels one
+// rotation at a time; HE_BATCHED raises every source once and puts every rotation of a stage
+// into one launch per kernel (inner product, ModDown, NTTs), in chunks sized to memory.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <thread>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace {
+
+// ================================================================================ layout
+struct Lay {
+    int c = 0, m = 0, M = 0, N = 0, B = 0, ns = 0, nb = 0;
+    std::vector<int> chan, row0;
+    int rows() const { return B / M; }
+};
+
+Lay from_c(const he_layout &l) {
+    Lay r;
+    r.c = l.c; r.m = l.m; r.M = l.M; r.N = l.N; r.B = l.B; r.ns = l.n_shards; r.nb = l.nb;
+    size_t cnt = (size_t)std::max(0, l.n_shards) * std::max(0, l.nb);
+    cnt = std::min<size_t>(cnt, HE_MAX_BLOCKS);
+    r.chan.assign(l.chan, l.chan + cnt);
+    r.row0.assign(l.row0, l.row0 + cnt);
+    return r;
+}
+
+int to_c(const Lay &r, he_layout *l) {
+    if ((size_t)r.ns * r.nb > HE_MAX_BLOCKS) {
+        he_set_error("layout needs %d blocks > HE_MAX_BLOCKS", r.ns * r.nb);
+        return HE_EINVAL;
+    }
+    memset(l, 0, sizeof(*l));
+    l->c = r.c; l->m = r.m; l->M = r.M; l->N = r.N; l->B = r.B; l->n_shards = r.ns; l->nb = r.nb;
+    for (size_t i = 0; i < r.chan.size(); i++) {
+        l->chan[i] = r.chan[i];
+        l->row0[i] = r.row0[i];
+    }
+    return HE_OK;
+}
+
+int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+int check_layout(const Lay &l, int N) {
+    bool ok = l.M > 0 && !(l.M & (l.M - 1)) && l.m >= 1 && l.m <= l.M && l.N == N && l.B > 0 &&
+              l.N % l.B == 0 && l.B % l.M == 0 && l.nb == l.N / l.B && l.ns >= 1 && l.c >= 1 &&
+              (size_t)l.ns * l.nb <= HE_MAX_BLOCKS;
+    if (!ok) {
+        he_set_error("inconsistent layout (frame, block or shard sizes)");
+        return HE_EINVAL;
+    }
+    for (size_t i = 0; i < l.chan.size(); i++)
+        if (l.chan[i] >= l.c || l.chan[i] < -1 || l.row0[i] < 0) {
+            he_set_error("layout table out of range");
+            return HE_EINVAL;
+        }
+    return HE_OK;
+}
+
+Lay image_layout(int c, int m, int N) {
+    Lay L;
+    L.c = c; L.m = m; L.M = next_pow2(m); L.N = N;
+    const int M = L.M;
+    if ((long long)M * M <= N) {
+        L.B = M * M;
+        L.nb = N / L.B;
+        if ((long long)c * L.B <= N) {              // one shard, tiled duplication
+            L.ns = 1;
+            L.chan.assign(L.nb, -1);
+            int d = L.nb / c;
+            for (int b = 0; b < d * c; b++) L.chan[b] = b % c;
+        } else {                                    // image shards
+            L.ns = (c + L.nb - 1) / L.nb;
+            L.chan.assign((size_t)L.ns * L.nb, -1);
+            for (int f = 0; f < c; f++) L.chan[f] = f;
+        }
+        L.row0.assign(L.chan.size(), 0);
+    } else {                                        // channel shards
+        L.B = N;
+        L.nb = 1;
+        const int R = N / M, h = M / R;
+        L.ns = c * h;
+        L.chan.resize(L.ns);
+        L.row0.resize(L.ns);
+        for (int f = 0; f < c; f++)
+            for (int k = 0; k < h; k++) {
+                L.chan[f * h + k] = f;
+                L.row0[f * h + k] = k * R;
+            }
+    }
+    return L;
+}
+
+struct SlotInfo {
+    int ch, y, x;
+    bool valid;
+};
+inline SlotInfo slot_info(const Lay &L, int u, int i) {
+    int b = i / L.B;
+    SlotInfo s;
+    s.ch = L.chan[(size_t)u * L.nb + b];
+    s.y = L.row0[(size_t)u * L.nb + b] + (i % L.B) / L.M;
+    s.x = i % L.M;
+    s.valid = s.ch >= 0 && s.y < L.m && s.x < L.m;
+    return s;
+}
+
+// ================================================================================ conv plan
+// For output slot i of shard v (channel o, pixel (y, x)), input channel f and tap (k, l), the
+// source pixel (y+k-pad, x+l-pad), when inside the image, is read from the copy of channel f
+// holding that row; among duplicated copies the smallest block offset (b_in - b_out) mod nb
+// wins, then the lowest shard.  Amount a = (j - i) mod N and D_{u,v,a}[i] = W[o][f][k][l]:
+// Eq. 1 (shift with its binary mask merged into the weight), Eqs. 2-5 (rotation by
+// r m^2 + shift), Eq. 6 (image shards), the tau/duplication indexing rule, Eq. 7 (channel
+// shards: own and neighbour shard share one amount).
+typedef std::map<long long, std::vector<double>> DiagMap;   // key u*N + a, ascending
+
+void plan_conv_v(const Lay &lin, const Lay &lout, const double *W, int ci, int kh, int kw,
+                 int pad, int v, DiagMap &out) {
+    const int N = lin.N;
+    struct Copy { int u, b, r0; };
+    std::vector<std::vector<Copy>> copies(ci);
+    for (int u = 0; u < lin.ns; u++)
+        for (int b = 0; b < lin.nb; b++) {
+            int f = lin.chan[(size_t)u * lin.nb + b];
+            if (f >= 0) copies[f].push_back({u, b, lin.row0[(size_t)u * lin.nb + b]});
+        }
+    const int R = lin.rows();
+    for (int i = 0; i < N; i++) {
+        SlotInfo so = slot_info(lout, v, i);
+        if (!so.valid) continue;
+        const int b_out = i / lout.B;
+        for (int f = 0; f < ci; f++)
+            for (int k = 0; k < kh; k++) {
+                const int ys = so.y + k - pad;
+                if (ys < 0 || ys >= lin.m) continue;
+                for (int l = 0; l < kw; l++) {
+                    const int xs = so.x + l - pad;
+                    if (xs < 0 || xs >= lin.m) continue;
+                    long long bestkey = -1, j = 0;
+                    int bu = -1;
+                    for (const Copy &cp : copies[f]) {
+                        if (ys < cp.r0 || ys >= cp.r0 + R) continue;
+                        long long key = (long long)(((cp.b - b_out) % lin.nb + lin.nb) % lin.nb) * (lin.ns + 1) + cp.u;
+                        if (bu < 0 || key < bestkey) {
+                            bestkey = key;
+                            j = (long long)cp.b * lin.B + (long long)(ys - cp.r0) * lin.M + xs;
+                            bu = cp.u;
+                        }
+                    }
+                    if (bu < 0) continue;
+                    const int a = (int)(((j - i) % N + N) % N);
+                    std::vector<double> &D = out[(long long)bu * N + a];
+                    if (D.empty()) D.assign(N, 0.0);
+                    D[i] = W[(((size_t)so.ch * ci + f) * kh + k) * kw + l];
+                }
+            }
+    }
+}
+
+// ================================================================================ pool plan
+// Sec. 4.2.  S: W = X + rot_1 X + rot_M X + rot_{M+1} X (2x2 ones convolution; skipped for the
+// stride-2 select).  H (Eq. 10): Y = sum_{x'} mask_{x'} rot_{x'}(W) on even valid rows, column
+// x'.  V (Eq. 11): Z = sum_{y'} mask_{y'} rot_{3 y' M / 2}(Y).  C (Eq. 12): shard 4g+q's old
+// block b becomes block 4b+q of output shard g (rotation right by q B/4).  Duplication
+// (Eq. 13) when 1 or 2 shards remain.
+struct PoolPlanH {
+    Lay lin, lout;
+    std::vector<int> pre, h_amt, v_amt;
+    std::vector<std::vector<std::vector<double>>> h_mask, v_mask;    // [amount][shard][N]
+    std::vector<std::vector<std::pair<int, int>>> groups;             // [out][(in shard, amount)]
+    std::vector<int> dup;                                             // incl. 0
+};
+
+int plan_pool(const Lay &lin, bool select, PoolPlanH &P) {
+    const int M = lin.M, N = lin.N, B = lin.B, m = lin.m;
+    if (m % 2 || M < 2 || lin.rows() % 2) {
+        he_set_error("pooling needs an even image side and an even number of rows per block");
+        return HE_EINVAL;
+    }
+    P.lin = lin;
+    const double w = select ? 1.0 : 0.25;
+    if (!select) P.pre = {0, 1, M, M + 1};
+    const int Mh = M / 2, Rb = lin.rows();
+    for (int xp = 0; xp < m / 2; xp++) {
+        std::vector<std::vector<double>> mk(lin.ns, std::vector<double>(N, 0.0));
+        for (int u = 0; u < lin.ns; u++)
+            for (int i = xp; i < N; i += M) {
+                int blk = i / B;
+                int ch = lin.chan[(size_t)u * lin.nb + blk];
+                int y = lin.row0[(size_t)u * lin.nb + blk] + (i % B) / M;
+                if (ch >= 0 && y % 2 == 0 && y < m) mk[u][i] = w;
+            }
+        P.h_amt.push_back(xp);
+        P.h_mask.push_back(std::move(mk));
+    }
+    for (int yp = 0; yp < Rb / 2; yp++) {
+        std::vector<std::vector<double>> mk(lin.ns, std::vector<double>(N, 0.0));
+        bool any = false;
+        for (int u = 0; u < lin.ns; u++)
+            for (int i = 0; i < N; i++) {
+                int blk = i / B, loc = i % B;
+                int ch = lin.chan[(size_t)u * lin.nb + blk];
+                int ynew = lin.row0[(size_t)u * lin.nb + blk] / 2 + yp;
+                if (ch >= 0 && loc >= yp * Mh && loc < yp * Mh + m / 2 && ynew < m / 2) {
+                    mk[u][i] = 1.0;
+                    any = true;
+                }
+            }
+        if (any) {
+            P.v_amt.push_back(3 * yp * M / 2);
+            P.v_mask.push_back(std::move(mk));
+        }
+    }
+    const int Bn = B / 4, nbn = N / Bn, t = lin.ns, nout = (t + 3) / 4;
+    Lay lo;
+    lo.c = lin.c; lo.m = m / 2; lo.M = Mh; lo.N = N; lo.B = Bn; lo.ns = nout; lo.nb = nbn;
+    lo.chan.assign((size_t)nout * nbn, -1);
+    lo.row0.assign((size_t)nout * nbn, 0);
+    for (int g = 0; g < nout; g++) {
+        std::vector<std::pair<int, int>> grp;
+        for (int q = 0; q < 4; q++) {
+            int s = 4 * g + q;
+            if (s >= t) break;
+            grp.push_back({s, ((-q * Bn) % N + N) % N});
+            for (int b = 0; b < lin.nb; b++) {
+                lo.chan[(size_t)g * nbn + 4 * b + q] = lin.chan[(size_t)s * lin.nb + b];
+                lo.row0[(size_t)g * nbn + 4 * b + q] = lin.row0[(size_t)s * lin.nb + b] / 2;
+            }
+        }
+        P.groups.push_back(grp);
+    }
+    P.dup = {0};
+    if (t == 1 || t == 2) {
+        const int f = 4 / t, step = t * Bn;
+        P.dup.clear();
+        for (int k = 0; k < f; k++) P.dup.push_back(((-k * step) % N + N) % N);
+        for (int k = 1; k < f; k++)
+            for (int b = 0; b < nbn; b++) {
+                int src = b - k * (step / Bn);
+                if (src >= 0 && lo.chan[src] >= 0 && lo.chan[b] < 0) {
+                    lo.chan[b] = lo.chan[src];
+                    lo.row0[b] = lo.row0[src];
+                }
+            }
+    }
+    P.lout = lo;
+    return HE_OK;
+}
+
+// ================================================================================ helpers
+template <class T>
+int dev_alloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return HE_OK;
+    if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        he_set_error("device allocation of %zu bytes failed", count * sizeof(T));
+        return HE_ENOMEM;
+    }
+    return HE_OK;
+}
+
+he_ct view(he_ctx *c, u64 *d, size_t ps, int level, double scale) {
+    he_ct t;
+    t.ctx = c; t.d = d; t.pstride = ps; t.level = level; t.cap = level; t.scale = scale; t.owned = false;
+    return t;
+}
+
+// Encode slot vectors at scale S (or take given integer plaintexts) and store them as
+// Montgomery NTT-form plaintexts at `level`, contiguous [count][level+1][n] from dst.
+int upload_plaintexts(he_ctx *c, const std::vector<const double *> &vecs, size_t count, double S,
+                      int level, u64 *dst, const int64_t *given) {
+    const int n = c->n;
+    const size_t pw = (size_t)(level + 1) * n;
+    int64_t *stage = (int64_t *)c->sc_tmp.p;
+    const size_t cap = std::max<size_t>(1, std::min<size_t>(64, c->sc_tmp.words / n));
+    std::vector<int64_t> host(cap * (size_t)n);
+    for (size_t b0 = 0; b0 < count; b0 += cap) {
+        const size_t nb = std::min(cap, count - b0);
+        if (given) {
+            memcpy(host.data(), given + b0 * n, nb * n * 8);
+        } else {
+            const unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+            std::vector<std::thread> th;
+            for (unsigned t = 0; t < nt; t++)
+                th.emplace_back([&, t]() {
+                    for (size_t i = t; i < nb; i += nt) encode_slots(vecs[b0 + i], n, S, host.data() + i * n);
+                });
+            for (auto &x : th) x.join();
+        }
+        HE_CHECK_CUDA(cudaMemcpy(stage, host.data(), nb * n * 8, cudaMemcpyHostToDevice));
+        for (size_t i = 0; i < nb; i++)
+            HE_TRY(k_reduce_int(c, stage + i * n, dst + (b0 + i) * pw, level + 1, level + 1, false, 0));
+        ntt_job j{dst + b0 * pw, pw, 0, level + 1, level + 1, 0, (int)nb};
+        HE_TRY(k_ntt(c, j, false, 0));
+        HE_TRY(k_to_mont(c, dst + b0 * pw, level + 1, level + 1, (int)nb, pw, 0));
+        HE_CHECK_CUDA(cudaStreamSynchronize(0));
+    }
+    return HE_OK;
+}
+
+// normal-form NTT addend at `level` from an integer polynomial
+int upload_addend(he_ctx *c, const int64_t *m, int level, u64 *dst) {
+    int64_t *stage = (int64_t *)c->sc_tmp.p;
+    HE_CHECK_CUDA(cudaMemcpy(stage, m, (size_t)c->n * 8, cudaMemcpyHostToDevice));
+    HE_TRY(k_reduce_int(c, stage, dst, level + 1, level + 1, false, 0));
+    ntt_job j{dst, 0, 0, level + 1, level + 1, 0, 1};
+    HE_TRY(k_ntt(c, j, false, 0));
+    HE_CHECK_CUDA(cudaStreamSynchronize(0));
+    return HE_OK;
+}
+
+size_t autotune_chunk(he_ctx *c, int level, size_t items) {
+    // one chunk's inner-product outputs and ModDown buffers stay under 4 GiB
+    size_t per = (size_t)(2 * (level + 1 + c->K) + 2 * (level + 1)) * c->n * 8;
+    size_t cap = std::max<size_t>(1, ((size_t)4 << 30) / per);
+    return std::max<size_t>(1, std::min(cap, items));
+}
+
+}  // namespace
+
+// ================================================================================ rotation sets
+// Hoisted rotations of several sources (ModUp of c1 once per source, Sec. 4.1 "computed once
+// and cached"), each by its own amounts, into destination buffers.
+struct RotSet {
+    he_ctx *c = nullptr;
+    int level = 0;
+    struct Src { u64 *d; size_t ps; };
+    struct Item { int src, amount; u64 g; u64 *dst; size_t ps; };
+    std::vector<Src> src;
+    std::vector<Item> items;                                   // non-zero amounts, by source
+    struct Copy { int src; u64 *dst; size_t ps; };
+    std::vector<Copy> copies;                                  // amount 0
+    std::vector<const DeviceKey *> keys;
+    size_t chunk = 0;
+    u64 *D_all = nullptr, *u_all = nullptr, *conv_all = nullptr;
+    ip_item *d_ip = nullptr;
+    md_item *d_md = nullptr;
+    bool batched_ready = false;
+
+    ~RotSet() {
+        cudaFree(D_all); cudaFree(u_all); cudaFree(conv_all); cudaFree(d_ip); cudaFree(d_md);
+    }
+    size_t nq() const { return (size_t)level + 1; }
+    size_t pw() const { return nq() * c->n; }
+    size_t ext() const { return (nq() + c->K) * c->n; }
+    int beta() const { return (level + c->alpha) / c->alpha; }
+
+    void add(int s, int amount, u64 *dst, size_t ps) {
+        u64 g = h_galois(c, amount);
+        if (g == 1) copies.push_back({s, dst, ps});
+        else items.push_back({s, amount, g, dst, ps});
+    }
+
+    int resolve_keys() {
+        keys.resize(items.size());
+        for (size_t i = 0; i < items.size(); i++) HE_TRY(get_key(c, (int)items[i].g, &keys[i]));
+        return HE_OK;
+    }
+
+    int prepare_batched() {
+        HE_TRY(resolve_keys());
+        if (batched_ready || items.empty()) { batched_ready = true; return HE_OK; }
+        chunk = autotune_chunk(c, level, items.size());
+        HE_TRY(dev_alloc(&D_all, src.size() * (size_t)beta() * ext()));
+        HE_TRY(dev_alloc(&u_all, chunk * 2 * ext()));
+        HE_TRY(dev_alloc(&conv_all, chunk * 2 * pw()));
+        std::vector<ip_item> ip(items.size());
+        std::vector<md_item> md(items.size());
+        for (size_t i = 0; i < items.size(); i++) {
+            const Item &it = items[i];
+            const size_t slot = i % chunk;
+            ip[i] = ip_item{D_all + (size_t)it.src * beta() * ext(), keys[i]->d,
+                            u_all + slot * 2 * ext(), it.g, beta()};
+            md[i] = md_item{u_all + slot * 2 * ext(), conv_all + slot * 2 * pw(), src[it.src].d,
+                            src[it.src].ps, 1, it.g, it.dst, it.ps};
+        }
+        HE_TRY(dev_alloc(&d_ip, ip.size()));
+        HE_TRY(dev_alloc(&d_md, md.size()));
+        HE_CHECK_CUDA(cudaMemcpy(d_ip, ip.data(), ip.size() * sizeof(ip_item), cudaMemcpyHostToDevice));
+        HE_CHECK_CUDA(cudaMemcpy(d_md, md.data(), md.size() * sizeof(md_item), cudaMemcpyHostToDevice));
+        batched_ready = true;
+        return HE_OK;
+    }
+
+    int run(int mode, cudaStream_t s) {
+        for (const Copy &cp : copies)
+            HE_TRY(k_copy_limbs(cp.dst, cp.ps, src[cp.src].d, src[cp.src].ps, pw(), 2, s));
+        if (items.empty()) return HE_OK;
+        if (keys.size() != items.size()) HE_TRY(resolve_keys());
+        if (mode == HE_PLAIN) {
+            int cur = -1;
+            for (size_t i = 0; i < items.size(); i++) {
+                const Item &it = items[i];
+                if (it.src != cur) {
+                    he_ct t = view(c, src[it.src].d, src[it.src].ps, level, 1.0);
+                    HE_TRY(hoist_modup(c, &t, c->sc_digits.p, s));
+                    cur = it.src;
+                }
+                HE_TRY(ks_tail(c, c->sc_digits.p, level, *keys[i], it.g, src[it.src].d, src[it.src].ps,
+                               1, it.g, it.dst, it.ps, s));
+            }
+            return HE_OK;
+        }
+        if (!batched_ready) HE_TRY(prepare_batched());
+        for (size_t u = 0; u < src.size(); u++) {
+            he_ct t = view(c, src[u].d, src[u].ps, level, 1.0);
+            HE_TRY(hoist_modup(c, &t, D_all + u * (size_t)beta() * ext(), s));
+        }
+        const int nqi = (int)nq();
+        for (size_t i0 = 0; i0 < items.size(); i0 += chunk) {
+            const int cnt = (int)std::min(chunk, items.size() - i0);
+            HE_TRY(k_inner_product(c, d_ip + i0, cnt, level, s));
+            ntt_job jp{u_all, ext(), nqi, c->K, nqi, 0, 2 * cnt};
+            HE_TRY(k_ntt(c, jp, true, s));
+            HE_TRY(k_moddown_fbc(c, u_all, conv_all, level, 2 * cnt, s));
+            ntt_job jc{conv_all, pw(), 0, nqi, nqi, 0, 2 * cnt};
+            HE_TRY(k_ntt(c, jc, false, s));
+            HE_TRY(k_moddown_combine(c, d_md + i0, cnt, level, s));
+        }
+        return HE_OK;
+    }
+};
+
+// ================================================================================ pooling
+struct he_pool {
+    he_ctx *c = nullptr;
+    PoolPlanH P;
+    int level = 0, ns = 0;
+    size_t pw0 = 0, pw1 = 0, pw2 = 0;
+    // buffers: X[ns] (pw0), W[ns] (pw0), Y[ns] (pw0: MAC at level, rescaled in place),
+    // Z[ns] (pw1), S[groups] (pw2); rotated copies per stage
+    u64 *X = nullptr, *Wb = nullptr, *Yb = nullptr, *Zb = nullptr, *Sb = nullptr;
+    u64 *rotS = nullptr, *rotH = nullptr, *rotV = nullptr, *rotC = nullptr, *rotD = nullptr;
+    RotSet rs_S, rs_H, rs_V, rs_C, rs_D;
+    u64 *hpts = nullptr, *vpts = nullptr;
+    std::vector<int> h_idx, v_idx;
+    int n_hpt = 0, n_vpt = 0;
+    mac_term *d_hterms = nullptr, *d_vterms = nullptr;
+    ~he_pool() {
+        cudaFree(X); cudaFree(Wb); cudaFree(Yb); cudaFree(Zb); cudaFree(Sb);
+        cudaFree(rotS); cudaFree(rotH); cudaFree(rotV); cudaFree(rotC); cudaFree(rotD);
+        cudaFree(hpts); cudaFree(vpts); cudaFree(d_hterms); cudaFree(d_vterms);
+    }
+};
+
+static int dedupe_upload(he_ctx *c, const std::vector<std::vector<std::vector<double>>> &mk, int ns,
+                         int lv, u64 **dst, std::vector<int> &idx, int &count) {
+    std::vector<const double *> uniq;
+    std::unordered_map<uint64_t, std::vector<int>> seen;
+    idx.assign(mk.size() * ns, -1);
+    for (size_t a = 0; a < mk.size(); a++)
+        for (int u = 0; u < ns; u++) {
+            const std::vector<double> &v = mk[a][u];
+            uint64_t h = 1469598103934665603ull;
+            for (int i = 0; i < c->N; i++) {
+                uint64_t bits;
+                memcpy(&bits, &v[i], 8);
+                h = (h ^ bits) * 1099511628211ull;
+            }
+            int found = -1;
+            for (int cand : seen[h])
+                if (!memcmp(uniq[cand], v.data(), (size_t)c->N * 8)) { found = cand; break; }
+            if (found < 0) {
+                found = (int)uniq.size();
+                uniq.push_back(v.data());
+                seen[h].push_back(found);
+            }
+            idx[a * ns + u] = found;
+        }
+    count = (int)uniq.size();
+    HE_TRY(dev_alloc(dst, (size_t)count * (lv + 1) * c->n));
+    return upload_plaintexts(c, uniq, uniq.size(), (double)c->primes[lv], lv, *dst, nullptr);
+}
+
+static int pool_build(he_ctx *c, const Lay &lin, int level, bool select, he_pool **out) {
+    if (level < 2) { he_set_error("pooling needs two levels"); return HE_ELEVEL; }
+    if (check_layout(lin, c->N) != HE_OK) return HE_EINVAL;
+    std::unique_ptr<he_pool> p(new he_pool());
+    p->c = c;
+    p->level = level;
+    HE_TRY(plan_pool(lin, select, p->P));
+    const PoolPlanH &P = p->P;
+    const int ns = lin.ns;
+    p->ns = ns;
+    p->pw0 = (size_t)(level + 1) * c->n;
+    p->pw1 = (size_t)level * c->n;
+    p->pw2 = (size_t)(level - 1) * c->n;
+    const size_t pw0 = p->pw0, pw1 = p->pw1, pw2 = p->pw2;
+    const size_t nS = P.pre.size(), nH = P.h_amt.size(), nV = P.v_amt.size(), nG = P.groups.size();
+    HE_TRY(dev_alloc(&p->X, (size_t)ns * 2 * pw0));
+    HE_TRY(dev_alloc(&p->Wb, (size_t)ns * 2 * pw0));
+    HE_TRY(dev_alloc(&p->Yb, (size_t)ns * 2 * pw0));
+    HE_TRY(dev_alloc(&p->Zb, (size_t)ns * 2 * pw1));
+    HE_TRY(dev_alloc(&p->Sb, nG * 2 * pw2));
+    HE_TRY(dev_alloc(&p->rotS, (size_t)ns * nS * 2 * pw0));
+    HE_TRY(dev_alloc(&p->rotH, (size_t)ns * nH * 2 * pw0));
+    HE_TRY(dev_alloc(&p->rotV, (size_t)ns * nV * 2 * pw1));
+    HE_TRY(dev_alloc(&p->rotC, (size_t)ns * 2 * pw2));
+    HE_TRY(dev_alloc(&p->rotD, P.dup.size() * 2 * pw2));
+    for (RotSet *rs : {&p->rs_S, &p->rs_H, &p->rs_V, &p->rs_C, &p->rs_D}) rs->c = c;
+    p->rs_S.level = level;
+    p->rs_H.level = level;
+    p->rs_V.level = level - 1;
+    p->rs_C.level = level - 2;
+    p->rs_D.level = level - 2;
+    u64 *hsrc = nS ? p->Wb : p->X;
+    for (int u = 0; u < ns; u++) {
+        p->rs_S.src.push_back({p->X + (size_t)u * 2 * pw0, pw0});
+        p->rs_H.src.push_back({hsrc + (size_t)u * 2 * pw0, pw0});
+        p->rs_V.src.push_back({p->Yb + (size_t)u * 2 * pw0, pw0});
+        p->rs_C.src.push_back({p->Zb + (size_t)u * 2 * pw1, pw1});
+        for (size_t a = 0; a < nS; a++) p->rs_S.add(u, P.pre[a], p->rotS + ((size_t)u * nS + a) * 2 * pw0, pw0);
+        for (size_t a = 0; a < nH; a++) p->rs_H.add(u, P.h_amt[a], p->rotH + ((size_t)u * nH + a) * 2 * pw0, pw0);
+        for (size_t a = 0; a < nV; a++) p->rs_V.add(u, P.v_amt[a], p->rotV + ((size_t)u * nV + a) * 2 * pw1, pw1);
+    }
+    for (size_t g = 0; g < nG; g++)
+        for (auto &e : P.groups[g]) p->rs_C.add(e.first, e.second, p->rotC + (size_t)e.first * 2 * pw2, pw2);
+    if (P.dup.size() > 1) {
+        p->rs_D.src.push_back({p->Sb, pw2});
+        for (size_t k = 0; k < P.dup.size(); k++) p->rs_D.add(0, P.dup[k], p->rotD + k * 2 * pw2, pw2);
+    }
+    HE_TRY(dedupe_upload(c, P.h_mask, ns, level, &p->hpts, p->h_idx, p->n_hpt));
+    HE_TRY(dedupe_upload(c, P.v_mask, ns, level - 1, &p->vpts, p->v_idx, p->n_vpt));
+    std::vector<mac_term> th, tv;
+    for (int u = 0; u < ns; u++) {
+        for (size_t a = 0; a < nH; a++)
+            th.push_back({p->hpts + (size_t)p->h_idx[a * ns + u] * pw0, p->rotH + ((size_t)u * nH + a) * 2 * pw0, pw0});
+        for (size_t a = 0; a < nV; a++)
+            tv.push_back({p->vpts + (size_t)p->v_idx[a * ns + u] * pw1, p->rotV + ((size_t)u * nV + a) * 2 * pw1, pw1});
+    }
+    HE_TRY(dev_alloc(&p->d_hterms, th.size()));
+    HE_TRY(dev_alloc(&p->d_vterms, tv.size()));
+    HE_CHECK_CUDA(cudaMemcpy(p->d_hterms, th.data(), th.size() * sizeof(mac_term), cudaMemcpyHostToDevice));
+    HE_CHECK_CUDA(cudaMemcpy(p->d_vterms, tv.data(), tv.size() * sizeof(mac_term), cudaMemcpyHostToDevice));
+    p->P.h_mask.clear();
+    p->P.v_mask.clear();
+    *out = p.release();
+    return HE_OK;
+}
+
+static int pool_run(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out, int mode, cudaStream_t s) {
+    const int ns = p->ns, lv = p->level;
+    const size_t pw0 = p->pw0, pw1 = p->pw1, pw2 = p->pw2;
+    const PoolPlanH &P = p->P;
+    const double scale = in[0]->scale;
+    for (int u = 0; u < ns; u++) {
+        if (!in[u] || in[u]->ctx != c || in[u]->level != lv || in[u]->scale != scale) {
+            he_set_error("pool input %d: level or scale mismatch", u);
+            return HE_ELEVEL;
+        }
+        HE_TRY(k_copy_limbs(p->X + (size_t)u * 2 * pw0, pw0, in[u]->d, in[u]->pstride, pw0, 2, s));
+    }
+    const size_t nS = P.pre.size(), nH = P.h_amt.size(), nV = P.v_amt.size();
+    if (nS) {                                                          // S
+        HE_TRY(p->rs_S.run(mode, s));
+        for (int u = 0; u < ns; u++) {
+            u64 *acc = p->Wb + (size_t)u * 2 * pw0;
+            HE_TRY(k_copy_limbs(acc, pw0, p->rotS + (size_t)u * nS * 2 * pw0, pw0, pw0, 2, s));
+            for (size_t a = 1; a < nS; a++)
+                HE_TRY(k_add_raw(c, acc, pw0, p->rotS + ((size_t)u * nS + a) * 2 * pw0, pw0, lv + 1, 2, false, s));
+        }
+    }
+    HE_TRY(p->rs_H.run(mode, s));                                      // H
+    double sH = scale;
+    for (int u = 0; u < ns; u++) {
+        u64 *y = p->Yb + (size_t)u * 2 * pw0;
+        HE_TRY(k_mac(c, p->d_hterms + (size_t)u * nH, (int)nH, y, pw0, lv, false, s));
+        he_ct t = view(c, y, pw0, lv, scale * (double)c->primes[lv]);
+        HE_TRY(he_rescale(c, &t, s));
+        sH = t.scale;
+    }
+    HE_TRY(p->rs_V.run(mode, s));                                      // V
+    double sV = sH;
+    for (int u = 0; u < ns; u++) {
+        u64 *z = p->Zb + (size_t)u * 2 * pw1;
+        HE_TRY(k_mac(c, p->d_vterms + (size_t)u * nV, (int)nV, z, pw1, lv - 1, false, s));
+        he_ct t = view(c, z, pw1, lv - 1, sH * (double)c->primes[lv - 1]);
+        HE_TRY(he_rescale(c, &t, s));
+        sV = t.scale;
+    }
+    HE_TRY(p->rs_C.run(mode, s));                                      // C
+    for (size_t g = 0; g < P.groups.size(); g++) {
+        u64 *acc = p->Sb + g * 2 * pw2;
+        const auto &grp = P.groups[g];
+        HE_TRY(k_copy_limbs(acc, pw2, p->rotC + (size_t)grp[0].first * 2 * pw2, pw2, pw2, 2, s));
+        for (size_t q = 1; q < grp.size(); q++)
+            HE_TRY(k_add_raw(c, acc, pw2, p->rotC + (size_t)grp[q].first * 2 * pw2, pw2, lv - 1, 2, false, s));
+    }
+    const int lo = lv - 2;
+    if (P.dup.size() > 1) {                                            // duplicate
+        HE_TRY(p->rs_D.run(mode, s));
+        HE_TRY(ensure_ct(c, out[0], lo));
+        HE_TRY(k_copy_limbs(out[0]->d, out[0]->pstride, p->rotD, pw2, pw2, 2, s));
+        for (size_t k = 1; k < P.dup.size(); k++)
+            HE_TRY(k_add_raw(c, out[0]->d, out[0]->pstride, p->rotD + k * 2 * pw2, pw2, lo + 1, 2, false, s));
+        out[0]->scale = sV;
+    } else {
+        for (size_t g = 0; g < P.groups.size(); g++) {
+            HE_TRY(ensure_ct(c, out[g], lo));
+            HE_TRY(k_copy_limbs(out[g]->d, out[g]->pstride, p->Sb + g * 2 * pw2, pw2, pw2, 2, s));
+            out[g]->scale = sV;
+        }
+    }
+    return HE_OK;
+}
+
+static int pool_prepare(he_pool *p, int mode) {
+    for (RotSet *rs : {&p->rs_S, &p->rs_H, &p->rs_V, &p->rs_C, &p->rs_D}) {
+        if (mode == HE_BATCHED) HE_TRY(rs->prepare_batched());
+        else HE_TRY(rs->resolve_keys());
+    }
+    return HE_OK;
+}
+
+static void collect_rotations(const he_pool *p, std::vector<int> &v) {
+    const PoolPlanH &P = p->P;
+    for (int a : P.pre) v.push_back(a);
+    for (int a : P.h_amt) v.push_back(a);
+    for (int a : P.v_amt) v.push_back(a);
+    for (auto &g : P.groups)
+        for (auto &e : g) v.push_back(e.second);
+    for (int a : P.dup) v.push_back(a);
+}
+
+extern "C" int he_pool_create(he_ctx *c, const he_layout *in, int level, he_pool **out) {
+    if (!c || !in || !out) { he_set_error("null argument"); return HE_EINVAL; }
+    if (level < 2 || level > c->L) { he_set_error("he_pool_create: level %d out of range", level); return HE_ELEVEL; }
+    return pool_build(c, from_c(*in), level, false, out);
+}
+extern "C" void he_pool_destroy(he_pool *p) {
+    if (p) { cudaDeviceSynchronize(); delete p; }
+}
+extern "C" int he_pool_out_layout(const he_pool *p, he_layout *out) {
+    if (!p || !out) return HE_EINVAL;
+    return to_c(p->P.lout, out);
+}
+static int distinct_nonzero(he_ctx *c, std::vector<int> v, int32_t *amounts, size_t cap) {
+    std::vector<int> r;
+    std::vector<u64> gs;
+    for (int a : v) {
+        u64 g = h_galois(c, a);
+        if (g == 1 || std::find(gs.begin(), gs.end(), g) != gs.end()) continue;
+        gs.push_back(g);
+        r.push_back(a);
+    }
+    for (size_t i = 0; i < r.size() && i < cap; i++) amounts[i] = r[i];
+    return (int)r.size();
+}
+extern "C" int he_pool_rotations(const he_pool *p, int32_t *amounts, size_t cap) {
+    if (!p) return HE_EINVAL;
+    std::vector<int> v;
+    collect_rotations(p, v);
+    return distinct_nonzero(p->c, v, amounts, cap);
+}
+extern "C" int he_pool_n_masks(const he_pool *p, int *n_h, int *n_v) {
+    if (!p) return HE_EINVAL;
+    if (n_h) *n_h = (int)p->P.h_amt.size();
+    if (n_v) *n_v = (int)p->P.v_amt.size();
+    return HE_OK;
+}
+
+static int import_masks(he_pool *p, const int64_t *m, size_t n_amt, const std::vector<int> &idx, int count,
+                        int lv, u64 *dst) {
+    he_ctx *c = p->c;
+    std::vector<int64_t> pick((size_t)count * c->n);
+    std::vector<char> done(count, 0);
+    for (size_t a = 0; a < n_amt; a++)
+        for (int u = 0; u < p->ns; u++) {
+            int k = idx[a * p->ns + u];
+            if (done[k]) continue;
+            memcpy(pick.data() + (size_t)k * c->n, m + (a * p->ns + u) * (size_t)c->n, (size_t)c->n * 8);
+            done[k] = 1;
+        }
+    std::vector<const double *> none;
+    return upload_plaintexts(c, none, (size_t)count, 0.0, lv, dst, pick.data());
+}
+
+extern "C" int he_pool_import_plaintexts(he_pool *p, const int64_t *h, const int64_t *v) {
+    if (!p) return HE_EINVAL;
+    if (h) HE_TRY(import_masks(p, h, p->P.h_amt.size(), p->h_idx, p->n_hpt, p->level, p->hpts));
+    if (v) HE_TRY(import_masks(p, v, p->P.v_amt.size(), p->v_idx, p->n_vpt, p->level - 1, p->vpts));
+    return HE_OK;
+}
+
+extern "C" int he_pool_run(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out, int mode, void *stream) {
+    if (!c || !p || !in || !out || p->c != c) { he_set_error("he_pool_run: bad argument"); return HE_EINVAL; }
+    HE_TRY(pool_prepare(p, mode));
+    return pool_run(c, p, in, out, mode, (cudaStream_t)stream);
+}
+
+// ================================================================================ convolution
+struct he_conv {
+    he_ctx *c = nullptr;
+    Lay lin, lout;
+    std::vector<double> W, bias;
+    int co = 0, ci = 0, kh = 0, kw = 0, pad = 0, stride = 1, level = 0;
+    double in_scale = 1.0, mid_scale = 1.0;
+    size_t pw = 0;
+    std::vector<int> tu, tv, ta;                 // terms in plan order
+    std::vector<int> term_off;                   // [n_out + 1]
+    std::map<long long, int> slot;               // u*N + a -> R slot
+    u64 *R = nullptr, *pts = nullptr, *bias_pts = nullptr, *acc = nullptr;
+    mac_term *d_terms = nullptr;
+    RotSet rot;
+    he_pool *pool = nullptr;
+    std::vector<he_ct *> mid;
+    ~he_conv() {
+        cudaFree(R); cudaFree(pts); cudaFree(bias_pts); cudaFree(d_terms); cudaFree(acc);
+        delete pool;
+        for (he_ct *x : mid) he_ct_free(x);
+    }
+};
+
+static int conv_bias_int(he_conv *cv, int v, double scale, std::vector<int64_t> &m) {
+    std::vector<double> z(cv->c->N, 0.0);
+    for (int i = 0; i < cv->c->N; i++) {
+        SlotInfo s = slot_info(cv->lout, v, i);
+        if (s.valid && !cv->bias.empty()) z[i] = cv->bias[s.ch];
+    }
+    m.resize(cv->c->n);
+    encode_slots(z.data(), cv->c->n, scale, m.data());
+    return HE_OK;
+}
+
+extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, const double *bias,
+                              int co, int ci, int kh, int kw, int stride, int pad, int level,
+                              double in_scale, he_conv **out) {
+    if (!c || !in || !W || !out || co < 1 || ci < 1 || kh < 1 || kw < 1 || pad < 0 ||
+        (stride != 1 && stride != 2)) {
+        he_set_error("he_conv_create: bad argument");
+        return HE_EINVAL;
+    }
+    const int need = stride == 1 ? 1 : 3;
+    if (level < need || level > c->L) { he_set_error("he_conv_create: level %d leaves too few levels", level); return HE_ELEVEL; }
+    Lay lin = from_c(*in);
+    HE_TRY(check_layout(lin, c->N));
+    if (lin.c != ci) { he_set_error("he_conv_create: layout has %d channels, W has %d", lin.c, ci); return HE_EINVAL; }
+    std::unique_ptr<he_conv> cv(new he_conv());
+    cv->c = c;
+    cv->lin = lin;
+    cv->lout = image_layout(co, lin.m, lin.N);
+    if (cv->lout.M != lin.M) { he_set_error("he_conv_create: output frame differs"); return HE_EINVAL; }
+    if ((size_t)cv->lout.ns * cv->lout.nb > HE_MAX_BLOCKS) { he_set_error("output layout too large"); return HE_EINVAL; }
+    cv->W.assign(W, W + (size_t)co * ci * kh * kw);
+    if (bias) cv->bias.assign(bias, bias + co);
+    cv->co = co; cv->ci = ci; cv->kh = kh; cv->kw = kw; cv->pad = pad; cv->stride = stride;
+    cv->level = level;
+    cv->in_scale = in_scale;
+    cv->mid_scale = in_scale * (double)c->primes[level] / (double)c->primes[level];
+    cv->pw = (size_t)(level + 1) * c->n;
+    const size_t pw = cv->pw;
+    // plan all output shards, keeping the diagonals of one shard at a time
+    std::vector<DiagMap> maps(cv->lout.ns);
+    size_t n_terms = 0;
+    for (int v = 0; v < cv->lout.ns; v++) {
+        plan_conv_v(lin, cv->lout, cv->W.data(), ci, kh, kw, pad, v, maps[v]);
+        n_terms += maps[v].size();
+    }
+    // R slots: every input shard's own copy (amount 0) first, then every rotation needed
+    for (int u = 0; u < lin.ns; u++) cv->slot[(long long)u * c->N] = u;
+    for (int v = 0; v < cv->lout.ns; v++)
+        for (auto &kv : maps[v])
+            if (!cv->slot.count(kv.first)) {
+                int id = (int)cv->slot.size();
+                cv->slot[kv.first] = id;
+            }
+    HE_TRY(dev_alloc(&cv->R, cv->slot.size() * 2 * pw));
+    HE_TRY(dev_alloc(&cv->pts, n_terms * pw));
+    HE_TRY(dev_alloc(&cv->bias_pts, (size_t)cv->lout.ns * level * c->n));
+    HE_TRY(dev_alloc(&cv->acc, (size_t)cv->lout.ns * 2 * pw));
+    // diagonal plaintexts at scale q_level
+    size_t t0 = 0;
+    cv->term_off.push_back(0);
+    for (int v = 0; v < cv->lout.ns; v++) {
+        std::vector<const double *> vecs;
+        for (auto &kv : maps[v]) {
+            cv->tu.push_back((int)(kv.first / c->N));
+            cv->tv.push_back(v);
+            cv->ta.push_back((int)(kv.first % c->N));
+            vecs.push_back(kv.second.data());
+        }
+        HE_TRY(upload_plaintexts(c, vecs, vecs.size(), (double)c->primes[level], level, cv->pts + t0 * pw, nullptr));
+        t0 += vecs.size();
+        cv->term_off.push_back((int)t0);
+        DiagMap().swap(maps[v]);
+    }
+    // bias at the output scale, normal NTT form at level - 1
+    for (int v = 0; v < cv->lout.ns; v++) {
+        std::vector<int64_t> m;
+        conv_bias_int(cv.get(), v, cv->mid_scale, m);
+        HE_TRY(upload_addend(c, m.data(), level - 1, cv->bias_pts + (size_t)v * level * c->n));
+    }
+    // MAC terms and rotation set
+    std::vector<mac_term> terms(n_terms);
+    for (size_t t = 0; t < n_terms; t++) {
+        int s = cv->slot[(long long)cv->tu[t] * c->N + cv->ta[t]];
+        terms[t] = mac_term{cv->pts + t * pw, cv->R + (size_t)s * 2 * pw, pw};
+    }
+    HE_TRY(dev_alloc(&cv->d_terms, n_terms));
+    HE_CHECK_CUDA(cudaMemcpy(cv->d_terms, terms.data(), n_terms * sizeof(mac_term), cudaMemcpyHostToDevice));
+    cv->rot.c = c;
+    cv->rot.level = level;
+    for (int u = 0; u < lin.ns; u++) cv->rot.src.push_back({cv->R + (size_t)u * 2 * pw, pw});
+    for (auto &kv : cv->slot) {
+        int u = (int)(kv.first / c->N), a = (int)(kv.first % c->N);
+        if (a != 0) cv->rot.add(u, a, cv->R + (size_t)kv.second * 2 * pw, pw);
+    }
+    if (stride == 2) {
+        HE_TRY(pool_build(c, cv->lout, level - 1, true, &cv->pool));
+        for (int v = 0; v < cv->lout.ns; v++) {
+            he_ct *m;
+            HE_TRY(he_ct_alloc(c, level - 1, &m));
+            cv->mid.push_back(m);
+        }
+    }
+    *out = cv.release();
+    return HE_OK;
+}
+
+extern "C" void he_conv_destroy(he_conv *cv) {
+    if (cv) { cudaDeviceSynchronize(); delete cv; }
+}
+extern "C" int he_conv_out_layout(const he_conv *cv, he_layout *out) {
+    if (!cv || !out) return HE_EINVAL;
+    return to_c(cv->pool ? cv->pool->P.lout : cv->lout, out);
+}
+extern "C" int he_conv_out_level(const he_conv *cv) {
+    if (!cv) return HE_EINVAL;
+    return cv->stride == 1 ? cv->level - 1 : cv->level - 3;
+}
+extern "C" int he_conv_rotations(const he_conv *cv, int32_t *amounts, size_t cap) {
+    if (!cv) return HE_EINVAL;
+    std::vector<int> v;
+    for (auto &kv : cv->slot) v.push_back((int)(kv.first % cv->c->N));
+    if (cv->pool) collect_rotations(cv->pool, v);
+    return distinct_nonzero(cv->c, v, amounts, cap);
+}
+extern "C" int he_conv_n_terms(const he_conv *cv) { return cv ? (int)cv->tu.size() : HE_EINVAL; }
+
+extern "C" int he_conv_export_plan(const he_conv *cv, int32_t *u, int32_t *v, int32_t *a, double *diag) {
+    if (!cv) return HE_EINVAL;
+    for (size_t t = 0; t < cv->tu.size(); t++) {
+        if (u) u[t] = cv->tu[t];
+        if (v) v[t] = cv->tv[t];
+        if (a) a[t] = cv->ta[t];
+    }
+    if (diag) {
+        const int N = cv->c->N;
+        size_t t = 0;
+        for (int vv = 0; vv < cv->lout.ns; vv++) {
+            DiagMap m;
+            plan_conv_v(cv->lin, cv->lout, cv->W.data(), cv->ci, cv->kh, cv->kw, cv->pad, vv, m);
+            for (auto &kv : m) memcpy(diag + (t++) * N, kv.second.data(), (size_t)N * 8);
+        }
+    }
+    return HE_OK;
+}
+
+extern "C" int he_conv_import_plaintexts(he_conv *cv, const int64_t *terms, const int64_t *bias) {
+    if (!cv) return HE_EINVAL;
+    he_ctx *c = cv->c;
+    if (terms) {
+        std::vector<const double *> none;
+        HE_TRY(upload_plaintexts(c, none, cv->tu.size(), 0.0, cv->level, cv->pts, terms));
+    }
+    if (bias)
+        for (int v = 0; v < cv->lout.ns; v++)
+            HE_TRY(upload_addend(c, bias + (size_t)v * c->n, cv->level - 1, cv->bias_pts + (size_t)v * cv->level * c->n));
+    return HE_OK;
+}
+
+extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out, int mode, void *stream) {
+    if (!c || !cv || !in || !out || cv->c != c || (mode != HE_PLAIN && mode != HE_BATCHED)) {
+        he_set_error("he_conv_run: bad argument");
+        return HE_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t pw = cv->pw;
+    const int lv = cv->level;
+    for (int u = 0; u < cv->lin.ns; u++) {
+        if (!in[u] || in[u]->ctx != c || in[u]->level != lv || in[u]->scale != cv->in_scale) {
+            he_set_error("he_conv_run: input shard %d is not at level %d / the planned scale", u, lv);
+            return HE_ELEVEL;
+        }
+        HE_TRY(k_copy_limbs(cv->R + (size_t)u * 2 * pw, pw, in[u]->d, in[u]->pstride, pw, 2, s));
+    }
+    if (mode == HE_BATCHED) HE_TRY(cv->rot.prepare_batched());
+    HE_TRY(cv->rot.run(mode, s));
+    he_ct **dst = cv->stride == 1 ? out : cv->mid.data();
+    for (int v = 0; v < cv->lout.ns; v++) {
+        // MAC over all (u, a) terms of output shard v, rescale, add the bias, hand out
+        u64 *a = cv->acc + (size_t)v * 2 * pw;
+        const int t0 = cv->term_off[v], t1 = cv->term_off[v + 1];
+        HE_TRY(k_mac(c, cv->d_terms + t0, t1 - t0, a, pw, lv, false, s));
+        he_ct t = view(c, a, pw, lv, cv->in_scale * (double)c->primes[lv]);
+        HE_TRY(he_rescale(c, &t, stream));
+        HE_TRY(k_add_raw(c, a, pw, cv->bias_pts + (size_t)v * lv * c->n, 0, lv, 1, false, s));
+        if (!dst[v] || dst[v]->ctx != c) { he_set_error("he_conv_run: output %d missing", v); return HE_EINVAL; }
+        HE_TRY(ensure_ct(c, dst[v], lv - 1));
+        HE_TRY(k_copy_limbs(dst[v]->d, dst[v]->pstride, a, pw, (size_t)lv * c->n, 2, s));
+        dst[v]->scale = t.scale;
+    }
+    if (cv->stride == 2) {
+        if (mode == HE_BATCHED) HE_TRY(pool_prepare(cv->pool, mode));
+        return pool_run(c, cv->pool, cv->mid.data(), out, mode, s);
+    }
+    return HE_OK;
+}
+
+// ================================================================================ polynomial
+// sum_k c_k T_k(x): T_{2k} = 2 T_k^2 - 1, T_{2k+1} = 2 T_k T_{k+1} - T_1 (Appendix), then the
+// linear combination with exact-scale integer constants round(c S_t q_l / s) at the lowest
+// level, the constant term round(c_0 S_t q_l) on coefficient 0, and one rescale.
+static int retarget(he_ctx *c, const he_ct *x, int level, double scale_t, he_ct *y, cudaStream_t s) {
+    HE_TRY(he_ct_copy(y, x, s));
+    HE_TRY(he_ct_drop_level(y, level + 1));
+    double K = std::nearbyint(scale_t * (double)c->primes[level + 1] / y->scale);
+    HE_TRY(he_mul_int(c, y, K, s));
+    HE_TRY(he_rescale(c, y, s));
+    y->scale = scale_t;
+    return HE_OK;
+}
+
+extern "C" int he_poly_eval(he_ctx *c, he_ct *io, const double *cheb, int deg, double target_scale, void *stream) {
+    if (!c || !io || !cheb || deg < 1 || deg > 64) { he_set_error("he_poly_eval: bad argument"); return HE_EINVAL; }
+    int depth = 0;
+    while ((1 << depth) < deg) depth++;
+    if (io->level < depth + 1) { he_set_error("he_poly_eval: needs %d levels", depth + 1); return HE_ELEVEL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<he_ct *> T(deg + 1, nullptr);
+    he_ct *tmpa = nullptr, *tmpb = nullptr, *t1 = nullptr, *acc = nullptr, *y = nullptr;
+    auto cleanup = [&]() {
+        for (he_ct *x : T) he_ct_free(x);
+        he_ct_free(tmpa); he_ct_free(tmpb); he_ct_free(t1); he_ct_free(acc); he_ct_free(y);
+    };
+    int rc = HE_OK;
+#define PTRY(e) do { rc = (e); if (rc != HE_OK) { cleanup(); return rc; } } while (0)
+    for (int k = 1; k <= deg; k++) PTRY(he_ct_alloc(c, io->level, &T[k]));
+    PTRY(he_ct_alloc(c, io->level, &tmpa));
+    PTRY(he_ct_alloc(c, io->level, &tmpb));
+    PTRY(he_ct_alloc(c, io->level, &t1));
+    PTRY(he_ct_alloc(c, io->level, &acc));
+    PTRY(he_ct_alloc(c, io->level, &y));
+    PTRY(he_ct_copy(T[1], io, stream));
+    for (int k = 2; k <= deg; k++) {
+        const int h = k / 2;
+        if (k % 2 == 0) {
+            PTRY(he_mul_relin(c, T[h], T[h], T[k], stream));
+            PTRY(he_mul_int(c, T[k], 2.0, stream));
+            PTRY(he_add_const_int(c, T[k], -std::nearbyint(T[k]->scale), stream));
+        } else {
+            const int lv = std::min(T[h]->level, T[h + 1]->level);
+            PTRY(he_ct_copy(tmpa, T[h], stream));
+            PTRY(he_ct_drop_level(tmpa, lv));
+            PTRY(he_ct_copy(tmpb, T[h + 1], stream));
+            PTRY(he_ct_drop_level(tmpb, lv));
+            PTRY(he_mul_relin(c, tmpa, tmpb, T[k], stream));
+            PTRY(he_mul_int(c, T[k], 2.0, stream));
+            PTRY(retarget(c, T[1], T[k]->level, T[k]->scale, t1, s));
+            PTRY(he_sub(c, T[k], t1, stream));
+        }
+    }
+    int lmin = T[1]->level;
+    for (int k = 2; k <= deg; k++) lmin = std::min(lmin, T[k]->level);
+    const double base = target_scale * (double)c->primes[lmin];
+    bool first = true;
+    for (int k = 1; k <= deg; k++) {
+        PTRY(he_ct_copy(y, T[k], stream));
+        PTRY(he_ct_drop_level(y, lmin));
+        double K = std::nearbyint(cheb[k] * target_scale * (double)c->primes[lmin] / y->scale);
+        PTRY(he_mul_int(c, y, K, stream));
+        y->scale = base;
+        if (first) { PTRY(he_ct_copy(acc, y, stream)); first = false; }
+        else PTRY(he_add(c, acc, y, stream));
+    }
+    PTRY(he_add_const_int(c, acc, std::nearbyint(cheb[0] * target_scale * (double)c->primes[lmin]), stream));
+    PTRY(he_rescale(c, acc, stream));
+    acc->scale = target_scale;
+    PTRY(he_ct_copy(io, acc, stream));
+#undef PTRY
+    cleanup();
+    return HE_OK;
+}
+
+// ================================================================================ wrappers
+static int keygen_for(he_ctx *c, const std::vector<int32_t> &amts) {
+    return he_keygen_rotations(c, amts.data(), amts.size());
+}
+
+extern "C" int he_hconv2d(he_ctx *c, const he_layout *in, he_ct *const *in_cts, const double *W,
+                          const double *bias, int co, int ci, int kh, int kw, int stride, int pad,
+                          int mode, he_layout *out_layout, he_ct **out_cts, void *stream) {
+    if (!c || !in || !in_cts || !out_cts) { he_set_error("null argument"); return HE_EINVAL; }
+    he_conv *cv = nullptr;
+    HE_TRY(he_conv_create(c, in, W, bias, co, ci, kh, kw, stride, pad, in_cts[0]->level, in_cts[0]->scale, &cv));
+    int n = he_conv_rotations(cv, nullptr, 0);
+    std::vector<int32_t> amts(std::max(n, 0));
+    he_conv_rotations(cv, amts.data(), amts.size());
+    int rc = keygen_for(c, amts);
+    if (rc == HE_OK && out_layout) rc = he_conv_out_layout(cv, out_layout);
+    if (rc == HE_OK) rc = he_conv_run(c, cv, in_cts, out_cts, mode, stream);
+    if (rc == HE_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = HE_ECUDA;
+    he_conv_destroy(cv);
+    return rc;
+}
+
+extern "C" int he_havgpool(he_ctx *c, const he_layout *in, he_ct *const *in_cts, he_layout *out_layout,
+                           he_ct **out_cts, int mode, void *stream) {
+    if (!c || !in || !in_cts || !out_cts) { he_set_error("null argument"); return HE_EINVAL; }
+    he_pool *p = nullptr;
+    HE_TRY(he_pool_create(c, in, in_cts[0]->level, &p));
+    int n = he_pool_rotations(p, nullptr, 0);
+    std::vector<int32_t> amts(std::max(n, 0));
+    he_pool_rotations(p, amts.data(), amts.size());
+    int rc = keygen_for(c, amts);
+    if (rc == HE_OK && out_layout) rc = he_pool_out_layout(p, out_layout);
+    if (rc == HE_OK) rc = he_pool_run(c, p, in_cts, out_cts, mode, stream);
+    if (rc == HE_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) rc = HE_ECUDA;
+    he_pool_destroy(p);
+    return rc;
+}
+
+extern "C" int he_layout_image(int c, int m, int N, he_layout *out) {
+    if (c < 1 || m < 2 || N < 4 || (N & (N - 1)) || !out) { he_set_error("he_layout_image: bad argument"); return HE_EINVAL; }
+    Lay L = image_layout(c, m, N);
+    if ((long long)L.M * L.M > N && (N % L.M != 0 || L.M % (N / L.M) != 0)) {
+        he_set_error("he_layout_image: frame does not tile the shard");
+        return HE_EINVAL;
+    }
+    return to_c(L, out);
+}

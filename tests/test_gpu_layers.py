@@ -1,0 +1,237 @@
+"""GPU parity of the layer programs (Sec. 4) against the oracle.
+
+Convolution and pooling run on plaintexts the oracle encoded (imported as integers), so the
+output limbs must equal the oracle's bit for bit, in both execution modes.  The Chebyshev
+evaluator needs no import (its constants are computed identically on both sides).  At the
+full 2^16 ring the CIFAR-shaped layer is checked by decryption against FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import layers as Ly
+from oracle.params import Params, TOY, C20
+from oracle.ckks import Context
+from oracle.encode import encode
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+MID = Params(log_n=12, n_q=6, n_p=2, dnum=3, q0_bits=50, q_bits=40, p_bits=50,
+             scale=2.0 ** 40, seed=5)
+
+
+@pytest.fixture(scope="module")
+def mid():
+    from tests._hegpu_util import GpuCtx
+    o = Context(MID)
+    g = GpuCtx(MID)
+    yield o, g
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def toy():
+    from tests._hegpu_util import GpuCtx
+    o = Context(TOY)
+    g = GpuCtx(TOY)
+    yield o, g
+    g.close()
+
+
+def _layout_of(lay_c):
+    chan, row0 = lay_c.tables()
+    return chan, row0
+
+
+def _gpu_conv(g, o, lin, W, bias, level, pad, plan, mode_list=(0, 1), stride=1):
+    from paper_2306_09189_gb300 import hegpu as H
+    lay = H.he_layout_image(lin.c, lin.m, o.N)
+    conv = H.he_conv_create(g.h, lay, W, bias, stride, pad, level, o.pr.scale)
+    H.he_keygen_rotations(g.h, H.he_conv_rotations(conv))
+    return conv
+
+
+def _conv_case(pair, c, co, m, k, pad, level, seed, bias=True):
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = pair
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (co, c, k, k))
+    b = rng.uniform(-1, 1, co) if bias else None
+    lin = Ly.image_layout(c, m, o.N)
+    plan = Ly.conv_plan(lin, W, b, pad)
+    slots = Ly.pack(lin, x)
+    cts = [o.encrypt(slots[u], level, nonce=seed * 100 + u) for u in range(lin.n_shards)]
+    pts = Ly.conv_plaintexts(plan, o.n, float(o.q[level]))
+    out_scale = o.pr.scale * o.q[level] / o.q[level]
+    bias_pts = {v: encode(plan.bias[v], o.n, out_scale) for v in range(plan.lout.n_shards)}
+    ref = Ly.conv_he(o, plan, cts, pts, bias_pts)
+
+    conv = _gpu_conv(g, o, lin, W, b, level, pad, plan)
+    # the planner's rotation set and diagonals equal the oracle's exactly
+    u, v, a, d = H.he_conv_export_plan(conv, o.N, with_diag=True)
+    keys = [(int(vv), int(uu), int(aa)) for uu, vv, aa in zip(u, v, a)]
+    want = [(vv, uu, aa) for vv in sorted(plan.terms) for (uu, aa) in sorted(plan.terms[vv])]
+    assert keys == want
+    for i, (vv, uu, aa) in enumerate(want):
+        assert np.array_equal(d[i], plan.terms[vv][(uu, aa)])
+    lay_out = H.he_conv_out_layout(conv)
+    chan, row0 = lay_out.tables()
+    assert np.array_equal(chan, plan.lout.chan) and np.array_equal(row0, plan.lout.row0)
+    H.he_conv_import_plaintexts(conv, np.stack([pts[(uu, vv, aa)] for (vv, uu, aa) in want]),
+                                np.stack([bias_pts[vv] for vv in range(plan.lout.n_shards)]))
+    ins = [g.upload(ct) for ct in cts]
+    for mode in (H.HE_PLAIN, H.HE_BATCHED):
+        outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
+        H.he_conv_run(g.h, conv, ins, outs, mode)
+        for oc, rc in zip(outs, ref):
+            assert H.he_ct_scale(oc) == rc.scale
+            assert_ct_equal(g.download(oc), rc)
+    H.he_conv_destroy(conv)
+    return ref, plan, x, W, b
+
+
+def test_conv_toy_bit_exact(toy):
+    wl = workloads.toy_conv(0)
+    o, g = toy
+    # the toy workload itself (bias 0) through the general case helper with its own draws
+    ref, plan, x, W, b = _conv_case(toy, 4, 4, 32, 3, 1, 3, seed=1, bias=False)
+    assert plan.n_rotations() == 35
+    dec = np.stack([o.decrypt(c) for c in ref])
+    img = Ly.unpack(plan.lout, dec)
+    want = torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(W), padding=1)[0].numpy()
+    assert np.abs(img - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+    assert wl.x.shape == (4, 32, 32)
+
+
+@pytest.mark.parametrize("c,co,m,k,pad", [(8, 8, 28, 3, 1), (2, 2, 56, 3, 1), (4, 2, 16, 5, 2),
+                                           (3, 2, 32, 7, 3)])
+def test_conv_sharded_bit_exact(mid, c, co, m, k, pad):
+    _conv_case(mid, c, co, m, k, pad, level=3, seed=c * 10 + m)
+
+
+@pytest.mark.parametrize("c,m", [(8, 32), (2, 32), (4, 32), (2, 64), (6, 28)])
+def test_pool_bit_exact(mid, c, m):
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = mid
+    level = 4
+    rng = np.random.default_rng(c + m)
+    x = rng.uniform(0, 1, (c, m, m))
+    lin = Ly.image_layout(c, m, o.N)
+    plan = Ly.pool_plan(lin)
+    slots = Ly.pack(lin, x)
+    cts = [o.encrypt(slots[u], level, nonce=500 + u) for u in range(lin.n_shards)]
+    ref = Ly.pool_he(o, plan, cts)
+    lay = H.he_layout_image(c, m, o.N)
+    pool = H.he_pool_create(g.h, lay, level)
+    H.he_keygen_rotations(g.h, H.he_pool_rotations(pool))
+    nh, nv = H.he_pool_n_masks(pool)
+    assert nh == len(plan.h_terms) and nv == len(plan.v_terms)
+    hm = np.stack([[encode(mk[u], o.n, float(o.q[level])) for u in range(lin.n_shards)]
+                   for _, mk in plan.h_terms])
+    vm = np.stack([[encode(mk[u], o.n, float(o.q[level - 1])) for u in range(lin.n_shards)]
+                   for _, mk in plan.v_terms])
+    H.he_pool_import_plaintexts(pool, hm, vm)
+    chan, row0 = H.he_pool_out_layout(pool).tables()
+    assert np.array_equal(chan, plan.lout.chan) and np.array_equal(row0, plan.lout.row0)
+    ins = [g.upload(ct) for ct in cts]
+    for mode in (H.HE_PLAIN, H.HE_BATCHED):
+        outs = [g.ct(level - 2) for _ in range(len(ref))]
+        H.he_pool_run(g.h, pool, ins, outs, mode)
+        for oc, rc in zip(outs, ref):
+            assert H.he_ct_scale(oc) == rc.scale
+            assert_ct_equal(g.download(oc), rc)
+    img = Ly.unpack(plan.lout, np.stack([o.decrypt(r) for r in ref]))
+    want = torch.nn.functional.avg_pool2d(torch.tensor(x)[None], 2)[0].numpy()
+    assert np.abs(img - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+    H.he_pool_destroy(pool)
+
+
+@pytest.mark.parametrize("deg,level", [(8, 5), (16, 5), (5, 4)])
+def test_poly_bit_exact(mid, deg, level):
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = mid
+    o.gen_relin_key()
+    H.he_keygen_relin(g.h)
+    z = np.random.default_rng(deg).uniform(-1, 1, o.N)
+    ct = o.encrypt(z, level, nonce=900 + deg)
+    c = Ly.cheb_nodes_coeffs(Ly.gelu, deg, -8, 8)
+    ref = Ly.cheb_tree_he(o, ct, c)
+    gc = g.upload(ct)
+    H.he_poly_eval(g.h, gc, c, o.pr.scale)
+    assert H.he_ct_level(gc) == ref.level and H.he_ct_scale(gc) == ref.scale
+    assert_ct_equal(g.download(gc), ref)
+
+
+def test_stride2_conv_decrypts_to_torch(mid):
+    from paper_2306_09189_gb300 import hegpu as H
+    o, g = mid
+    rng = np.random.default_rng(11)
+    c, co, m = 3, 4, 32
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.normal(0, 0.05, (co, c, 7, 7))
+    level = 5
+    lay = H.he_layout_image(c, m, o.N)
+    lin = Ly.image_layout(c, m, o.N)
+    slots = Ly.pack(lin, x)
+    ins = []
+    for u in range(lin.n_shards):
+        ct = g.ct(level)
+        H.he_encrypt(g.h, slots[u], level, o.pr.scale, 40 + u, ct)
+        ins.append(ct)
+    conv = H.he_conv_create(g.h, lay, W, None, 2, 3, level, o.pr.scale)
+    H.he_keygen_rotations(g.h, H.he_conv_rotations(conv))
+    lout = H.he_conv_out_layout(conv)
+    assert H.he_conv_out_level(conv) == level - 3
+    outs = [g.ct(level - 3) for _ in range(lout.n_shards)]
+    H.he_conv_run(g.h, conv, ins, outs, H.HE_BATCHED)
+    chan, row0 = lout.tables()
+    ol = Ly.Layout(lout.c, lout.m, lout.M, lout.N, lout.B, chan.astype(np.int64), row0.astype(np.int64))
+    img = Ly.unpack(ol, np.stack([H.he_decrypt(g.h, oc, o.N) for oc in outs]))
+    want = torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(W), stride=2, padding=3)[0].numpy()
+    assert img.shape == want.shape
+    assert np.abs(img - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+    H.he_conv_destroy(conv)
+
+
+def test_cifar_layer_full_ring():
+    """16x32x32 conv3x3 + folded BN + degree-16 GELU at n = 2^16, 20 primes (the headline layer)."""
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import GpuCtx
+    g = GpuCtx(C20)
+    try:
+        wl = workloads.cifar_conv_bn(0)
+        N, level = g.N, 19
+        lay = H.he_layout_image(16, 32, N)
+        lin = Ly.image_layout(16, 32, N)
+        slots = Ly.pack(lin, wl.x)
+        ct = g.ct(level)
+        H.he_encrypt(g.h, slots[0], level, C20.scale, 1, ct)
+        conv = H.he_conv_create(g.h, lay, wl.W, wl.bias, 1, 1, level, C20.scale)
+        rots = H.he_conv_rotations(conv)
+        assert len(rots) == 143
+        H.he_keygen_rotations(g.h, rots)
+        H.he_keygen_relin(g.h)
+        outs = {}
+        for mode in (H.HE_PLAIN, H.HE_BATCHED):
+            oc = g.ct(level - 1)
+            H.he_conv_run(g.h, conv, [ct], [oc], mode)
+            outs[mode] = g.download(oc)
+        assert np.array_equal(outs[0], outs[1])
+        ref = (torch.nn.functional.conv2d(torch.tensor(wl.x)[None], torch.tensor(wl.W), padding=1)[0].numpy()
+               + wl.bias[:, None, None])
+        img = Ly.unpack(lin, H.he_decrypt(g.h, oc, N)[None])
+        assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+        cheb = Ly.cheb_nodes_coeffs(Ly.gelu, workloads.GELU_DEGREE, -8, 8)
+        H.he_poly_eval(g.h, oc, cheb, C20.scale)
+        assert H.he_ct_level(oc) == level - 1 - 5
+        act = Ly.unpack(lin, H.he_decrypt(g.h, oc, N)[None])
+        want = Ly.cheb_eval(cheb, 8 * ref, -8, 8)
+        assert np.abs(act - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+        H.he_conv_destroy(conv)
+    finally:
+        g.close()
