@@ -145,6 +145,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--trace", default="ip", help="kernel whose launches the roofline uses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="profiling case: same ring, 2-channel 32x32 conv (17 rotations, ~2 GB of keys)")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="set up, warm up, then run one batched step between cudaProfilerStart/Stop")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -157,22 +161,17 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     import workloads
-    from oracle import layers as Ly          # host-side packing and Chebyshev coefficients only
-    from oracle.params import C20
     from paper_2306_09189_gb300 import hegpu as H
+    from paper_2306_09189_gb300 import host
 
-    pr = C20
-    ctx = H.he_ctx_create(H.he_params(pr.log_n, pr.n_q, pr.n_p, pr.dnum, pr.q0_bits, pr.q_bits,
-                                      pr.p_bits, pr.scale, pr.seed))
+    pr = host.cifar_params(seed=0)
+    ctx = H.he_ctx_create(pr)
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]
-    wl = workloads.cifar_conv_bn(0)
-    lin = Ly.image_layout(16, 32, N)
-    slots = Ly.pack(lin, wl.x)[0]
-    cheb = Ly.cheb_nodes_coeffs(Ly.gelu, DEG, -8, 8)
-    lay = H.he_layout_image(16, 32, N)
-    x = H.he_ct_alloc(ctx, LEVEL)
-    H.he_encrypt(ctx, slots, LEVEL, pr.scale, 1, x)
+    wl = workloads.cifar_conv_bn(0, c=2) if args.small else workloads.cifar_conv_bn(0)
+    lay = H.he_layout_image(wl.x.shape[0], 32, N)
+    cheb = host.chebyshev_coeffs(host.gelu, DEG, -8.0, 8.0)
+    x = host.encrypt_image(ctx, lay, wl.x, LEVEL, pr.scale, nonce0=1)[0]
     conv = H.he_conv_create(ctx, lay, wl.W, wl.bias, 1, 1, LEVEL, pr.scale)
     rots = H.he_conv_rotations(conv)
     H.he_keygen_rotations(ctx, rots)
@@ -212,6 +211,16 @@ def main():
             ms = float(t.item())
         return ms / k, launches, tr
 
+    if args.profile_step:
+        for _ in range(args.warmup):
+            step(H.HE_BATCHED)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step(H.HE_BATCHED)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return
+
     clocks = Clocks(local)
     clocks.start()
     ms_b, launches_b, tr = timed(H.HE_BATCHED, args.steps, args.trace)
@@ -222,7 +231,7 @@ def main():
     xin = H.he_ct_export_coeffs(ctx, x, n)
     h_in = torch.empty(xin.size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64).reshape(xin.shape)
     h_in[:] = xin
-    out_level = LEVEL - 1 - (DEG.bit_length() if DEG & (DEG - 1) else DEG.bit_length() - 1) - 1
+    out_level = LEVEL - 1 - ((DEG - 1).bit_length() + 1)      # conv, then ceil(log2 DEG) + 1
     out_shape = (2, out_level + 1, n)
     h_out = torch.empty(int(np.prod(out_shape)), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
     xe = H.he_ct_alloc(ctx, LEVEL)

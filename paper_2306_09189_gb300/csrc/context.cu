@@ -266,6 +266,7 @@ static int build_fbc(he_ctx *c, const std::vector<int> &src, const std::vector<i
 
 static void free_ctx(he_ctx *c) {
     if (!c) return;
+    for (he_ct *t : c->poly_tmp) he_ct_free(t);
     for (auto &lv : c->modup)
         for (auto &t : lv)
             if (t.d) cudaFree(t.d);
@@ -336,7 +337,14 @@ static int create(const he_params *pr, he_ctx **out) {
         ninv[t] = h_invmod((u64)n % qq, qq);
         ninvs[t] = h_shoup(ninv[t], qq);
     }
-    size_t words = 4 * (size_t)np + 4 * (size_t)np * n + 2 * (size_t)np;
+    std::vector<u64> tw2(2 * tw.size()), itw2(2 * tw.size());
+    for (size_t k = 0; k < tw.size(); k++) {
+        tw2[2 * k] = tw[k];
+        tw2[2 * k + 1] = tws[k];
+        itw2[2 * k] = itw[k];
+        itw2[2 * k + 1] = itws[k];
+    }
+    size_t words = 4 * (size_t)np + 8 * (size_t)np * n + 2 * (size_t)np;
     if (cudaMalloc(&c->d_tables, words * 8) != cudaSuccess) {
         cudaGetLastError();
         free_ctx(c);
@@ -364,6 +372,8 @@ static int create(const he_params *pr, he_ctx **out) {
     c->kp.itws = put(itws.data(), itws.size());
     c->kp.ninv = put(ninv.data(), np);
     c->kp.ninvs = put(ninvs.data(), np);
+    c->kp.tw2 = put(tw2.data(), tw2.size());
+    c->kp.itw2 = put(itw2.data(), itw2.size());
     // ---- base conversion tables
     c->modup.resize(c->L + 1);
     c->moddown.resize(c->L + 1);

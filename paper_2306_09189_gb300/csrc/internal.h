@@ -54,6 +54,7 @@ struct KP {                  // kernel parameters passed by value
     const u64 *tw, *tws;     // [np][n] psi^{brev(k)} and its Shoup companion
     const u64 *itw, *itws;   // [np][n] psi^{-brev(k)} and Shoup
     const u64 *ninv, *ninvs; // [np] n^{-1} and Shoup
+    const u64 *tw2, *itw2;   // [np][n] interleaved {w, w'} pairs of tw/tws and itw/itws
 };
 
 // Fast-base-conversion table for one (source set -> target set) conversion.
@@ -113,6 +114,7 @@ struct he_ctx {
     std::map<int, DeviceKey> keys;       // key id (Galois element; 0 = relin) -> key
     Scratch sc_digits, sc_u, sc_conv, sc_tmp, sc_tmp2;
     size_t key_bytes = 0;
+    std::vector<he_ct *> poly_tmp;       // reusable temporaries of he_poly_eval (level L)
 };
 
 struct ntt_job {

@@ -145,6 +145,167 @@ __global__ void __launch_bounds__(256) ntt_rows(KP kp, ntt_job job) {
     for (int k = 0; k < 8; k++) a[lane + 32 * k] = s[lane + 32 * k];
 }
 
+// ------------------------------------------------------------------------------ NTT, radix 16
+// Register-blocked form for 2^12 <= n <= 2^16 (R = n/256 rows of 256): every thread holds 16
+// words and runs four butterfly stages in registers per pass; the two passes of a phase
+// exchange through one shared-memory transpose.  Phase A (the log2 R stages whose distance is
+// a multiple of 256): pass 1 on rows r + (R/16) j, pass 2 on rows 16 r + e.  Phase B (the last
+// 8 stages, along 256-word rows): pass 1 on words l + 16 j, pass 2 on words 16 l + e.
+// Butterflies are lazy (Harvey): forward values stay in [0, 4q), inverse values in [0, 2q);
+// twiddles are read as {w, floor(w 2^64 / q)} pairs, one load per group of butterflies
+// sharing a twiddle.
+__device__ __forceinline__ void ct_lazy(u64 &X, u64 &Y, u64 w, u64 ws, u64 q, u64 q2) {
+    u64 x = X >= q2 ? X - q2 : X;
+    u64 t = Y * w - __umul64hi(Y, ws) * q;          // [0, 2q)
+    X = x + t;
+    Y = x - t + q2;
+}
+__device__ __forceinline__ void gs_lazy(u64 &X, u64 &Y, u64 w, u64 ws, u64 q, u64 q2) {
+    u64 s = X + Y;
+    s = s >= q2 ? s - q2 : s;
+    u64 d = X - Y + q2;
+    Y = d * w - __umul64hi(d, ws) * q;              // [0, 2q)
+    X = s;
+}
+
+// stage with butterfly distance `half` words inside x[16]; element j has NTT index
+// base + (j << ls); all butterflies of a group of 2*half consecutive j share one twiddle.
+template <bool INV, int H>
+__device__ __forceinline__ void reg_stage(u64 (&x)[16], int base, int ls, int logn,
+                                          const ulonglong2 *__restrict__ W, u64 q, u64 q2) {
+    constexpr int half = 1 << H;
+    const int sh = ls + H + 1;
+    const int m = (1 << logn) >> sh;
+    const int i0 = base >> sh;
+#pragma unroll
+    for (int g = 0; g < (8 >> H); g++) {
+        const ulonglong2 w = W[m + i0 + g];
+#pragma unroll
+        for (int k = 0; k < half; k++) {
+            const int j = g * 2 * half + k;
+            if (INV) gs_lazy(x[j], x[j + half], w.x, w.y, q, q2);
+            else ct_lazy(x[j], x[j + half], w.x, w.y, q, q2);
+        }
+    }
+}
+
+// CT stages H = 3..lo (forward) or GS stages lo..3 (inverse), lo in [0, 4]
+template <bool INV>
+__device__ __forceinline__ void reg_pass(u64 (&x)[16], int base, int ls, int logn, int nstages,
+                                         const ulonglong2 *__restrict__ W, u64 q, u64 q2) {
+    if (!INV) {
+        if (nstages >= 4) reg_stage<false, 3>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 3) reg_stage<false, 2>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 2) reg_stage<false, 1>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 1) reg_stage<false, 0>(x, base, ls, logn, W, q, q2);
+    } else {
+        if (nstages >= 1) reg_stage<true, 0>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 2) reg_stage<true, 1>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 3) reg_stage<true, 2>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 4) reg_stage<true, 3>(x, base, ls, logn, W, q, q2);
+    }
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(256) ntt16_cols(KP kp, ntt_job job) {
+    __shared__ u64 sm[4096];
+    const int p = blockIdx.z;
+    const int limb = job_limb(job, blockIdx.y, p);
+    if (limb < 0) return;
+    const int pr = prime_of(kp, limb, job.nq);
+    const u64 q = kp.q[pr], q2 = 2 * q;
+    const int lr = kp.logn - 8;                      // R = 2^lr rows, 4 <= lr <= 8
+    const int R16 = 1 << (lr - 4);
+    const int ltc = 12 - lr, TC = 1 << ltc;           // columns per block
+    const int t = threadIdx.x, tc = t & (TC - 1), r = t >> ltc;
+    const int c = blockIdx.x * TC + tc;
+    u64 *a = job.base + (size_t)p * job.poly_stride + (size_t)limb * kp.n;
+    const ulonglong2 *W = (const ulonglong2 *)(INV ? kp.itw2 : kp.tw2) + (size_t)pr * kp.n;
+    const int n2 = lr - 4;                           // pass-2 stages
+    u64 x[16];
+    if (!INV) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) x[j] = a[(size_t)(r + R16 * j) * ROW + c];
+        reg_pass<false>(x, r * ROW + c, lr + 4, kp.logn, 4, W, q, q2);
+#pragma unroll
+        for (int j = 0; j < 16; j++) sm[(r + R16 * j) * TC + tc] = x[j];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = sm[(16 * r + e) * TC + tc];
+        reg_pass<false>(x, 16 * r * ROW + c, 8, kp.logn, n2, W, q, q2);
+#pragma unroll
+        for (int e = 0; e < 16; e++) a[(size_t)(16 * r + e) * ROW + c] = x[e];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = a[(size_t)(16 * r + e) * ROW + c];
+        reg_pass<true>(x, 16 * r * ROW + c, 8, kp.logn, n2, W, q, q2);
+#pragma unroll
+        for (int e = 0; e < 16; e++) sm[(16 * r + e) * TC + tc] = x[e];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 16; j++) x[j] = sm[(r + R16 * j) * TC + tc];
+        reg_pass<true>(x, r * ROW + c, lr + 4, kp.logn, 4, W, q, q2);
+        const u64 ni = kp.ninv[pr], nis = kp.ninvs[pr];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            u64 v = x[j] * ni - __umul64hi(x[j], nis) * q;
+            a[(size_t)(r + R16 * j) * ROW + c] = v >= q ? v - q : v;
+        }
+    }
+}
+
+__device__ __forceinline__ int pad17(int k) { return k + (k >> 4); }
+
+template <bool INV>
+__global__ void __launch_bounds__(256) ntt16_rows(KP kp, ntt_job job) {
+    __shared__ u64 sm[16][272];
+    const int p = blockIdx.z;
+    const int limb = job_limb(job, blockIdx.y, p);
+    if (limb < 0) return;
+    const int pr = prime_of(kp, limb, job.nq);
+    const u64 q = kp.q[pr], q2 = 2 * q;
+    const int t = threadIdx.x, rl = t >> 4, l = t & 15;
+    const int row = blockIdx.x * 16 + rl;
+    u64 *a = job.base + (size_t)p * job.poly_stride + (size_t)limb * kp.n + (size_t)row * ROW;
+    const ulonglong2 *W = (const ulonglong2 *)(INV ? kp.itw2 : kp.tw2) + (size_t)pr * kp.n;
+    u64 *s = sm[rl];
+    u64 x[16];
+    if (!INV) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) x[j] = a[l + 16 * j];
+        reg_pass<false>(x, row * ROW + l, 4, kp.logn, 4, W, q, q2);
+#pragma unroll
+        for (int j = 0; j < 16; j++) s[pad17(l + 16 * j)] = x[j];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = s[pad17(16 * l + e)];
+        reg_pass<false>(x, row * ROW + 16 * l, 0, kp.logn, 4, W, q, q2);
+#pragma unroll
+        for (int e = 0; e < 16; e++) {
+            u64 v = x[e] >= q2 ? x[e] - q2 : x[e];
+            s[pad17(16 * l + e)] = v >= q ? v - q : v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 16; j++) a[l + 16 * j] = s[pad17(l + 16 * j)];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; j++) s[pad17(l + 16 * j)] = a[l + 16 * j];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 16; e++) x[e] = s[pad17(16 * l + e)];
+        reg_pass<true>(x, row * ROW + 16 * l, 0, kp.logn, 4, W, q, q2);
+#pragma unroll
+        for (int e = 0; e < 16; e++) s[pad17(16 * l + e)] = x[e];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 16; j++) x[j] = s[pad17(l + 16 * j)];
+        reg_pass<true>(x, row * ROW + l, 4, kp.logn, 4, W, q, q2);
+#pragma unroll
+        for (int j = 0; j < 16; j++) a[l + 16 * j] = x[j];
+    }
+}
+
 // ------------------------------------------------------------------------------ sampling
 __global__ void sample_uniform_kernel(KP kp, u64 seed, u64 stream, u64 *out, int nq) {
     const int k = blockIdx.x * TB + threadIdx.x;
@@ -514,6 +675,24 @@ __global__ void bench_modmul_kernel(u64 q, u64 qinv, int iters, u64 *sink) {
 int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
     if (job.nl <= 0 || job.npoly <= 0) return HE_OK;
     const int R = ctx->n / ROW;
+    if (ctx->logn >= 12 && ctx->logn <= 16) {
+        const double limbs = (double)job.nl * job.npoly;
+        TraceScope tr("ntt", s, limbs * 2.0 * ctx->n * 8, limbs * (ctx->n / 2) * ctx->logn);
+        const int TC = 4096 / R;
+        dim3 gA(ROW / TC, job.nl, job.npoly), gB(R / 16, job.nl, job.npoly);
+        if (!inverse) {
+            ntt16_cols<false><<<gA, 256, 0, s>>>(ctx->kp, job);
+            LAUNCH_CHECK();
+            ntt16_rows<false><<<gB, 256, 0, s>>>(ctx->kp, job);
+            LAUNCH_CHECK();
+        } else {
+            ntt16_rows<true><<<gB, 256, 0, s>>>(ctx->kp, job);
+            LAUNCH_CHECK();
+            ntt16_cols<true><<<gA, 256, 0, s>>>(ctx->kp, job);
+            LAUNCH_CHECK();
+        }
+        return HE_OK;
+    }
     dim3 gA(ROW / NTT_TC, job.nl, job.npoly), gB((R + 7) / 8, job.nl, job.npoly);
     size_t smA = (size_t)R * NTT_TC * sizeof(u64);
     const double limbs = (double)job.nl * job.npoly;

@@ -943,20 +943,19 @@ extern "C" int he_poly_eval(he_ctx *c, he_ct *io, const double *cheb, int deg, d
     while ((1 << depth) < deg) depth++;
     if (io->level < depth + 1) { he_set_error("he_poly_eval: needs %d levels", depth + 1); return HE_ELEVEL; }
     cudaStream_t s = (cudaStream_t)stream;
+    // temporaries live in the context (allocated once at the top level, reused every call)
+    const size_t need = (size_t)deg + 6;
+    while (c->poly_tmp.size() < need) {
+        he_ct *t = nullptr;
+        HE_TRY(he_ct_alloc(c, c->L, &t));
+        c->poly_tmp.push_back(t);
+    }
     std::vector<he_ct *> T(deg + 1, nullptr);
-    he_ct *tmpa = nullptr, *tmpb = nullptr, *t1 = nullptr, *acc = nullptr, *y = nullptr;
-    auto cleanup = [&]() {
-        for (he_ct *x : T) he_ct_free(x);
-        he_ct_free(tmpa); he_ct_free(tmpb); he_ct_free(t1); he_ct_free(acc); he_ct_free(y);
-    };
+    for (int k = 1; k <= deg; k++) T[k] = c->poly_tmp[k - 1];
+    he_ct *tmpa = c->poly_tmp[deg], *tmpb = c->poly_tmp[deg + 1], *t1 = c->poly_tmp[deg + 2];
+    he_ct *acc = c->poly_tmp[deg + 3], *y = c->poly_tmp[deg + 4];
     int rc = HE_OK;
-#define PTRY(e) do { rc = (e); if (rc != HE_OK) { cleanup(); return rc; } } while (0)
-    for (int k = 1; k <= deg; k++) PTRY(he_ct_alloc(c, io->level, &T[k]));
-    PTRY(he_ct_alloc(c, io->level, &tmpa));
-    PTRY(he_ct_alloc(c, io->level, &tmpb));
-    PTRY(he_ct_alloc(c, io->level, &t1));
-    PTRY(he_ct_alloc(c, io->level, &acc));
-    PTRY(he_ct_alloc(c, io->level, &y));
+#define PTRY(e) do { rc = (e); if (rc != HE_OK) return rc; } while (0)
     PTRY(he_ct_copy(T[1], io, stream));
     for (int k = 2; k <= deg; k++) {
         const int h = k / 2;
@@ -994,7 +993,6 @@ extern "C" int he_poly_eval(he_ctx *c, he_ct *io, const double *cheb, int deg, d
     acc->scale = target_scale;
     PTRY(he_ct_copy(io, acc, stream));
 #undef PTRY
-    cleanup();
     return HE_OK;
 }
 

@@ -228,3 +228,29 @@ def test_full_ring_rotation_bit_exact(pair20, level):
     assert np.abs(H.he_decrypt(g.h, out, o.N) - np.roll(z, -33)).max() < 2.0 ** -20
     H.he_rescale(g.h, c)
     assert_ct_equal(g.download(c), o.rescale(ct))
+
+
+@pytest.mark.parametrize("log_n", [10, 11, 13])
+def test_small_ring_rotation_and_relin_bit_exact(log_n):
+    """Rings below 2^12 take the shared-memory radix-2 NTT; 2^13 the radix-16 one."""
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import GpuCtx, assert_ct_equal
+    pr = Params(log_n=log_n, n_q=4, n_p=2, dnum=2, q0_bits=50, q_bits=40, p_bits=50,
+                scale=2.0 ** 40, seed=9)
+    o = Context(pr)
+    g = GpuCtx(pr)
+    try:
+        ct, z = _rand_ct(o, 3, 300 + log_n)
+        ct2, _ = _rand_ct(o, 3, 400 + log_n)
+        o.gen_rotation_key(7)
+        o.gen_relin_key()
+        H.he_keygen_rotations(g.h, [7])
+        H.he_keygen_relin(g.h)
+        out = g.ct(3)
+        H.he_rotate(g.h, g.upload(ct), 7, out)
+        assert_ct_equal(g.download(out), o.rotate(ct, 7))
+        m = g.ct(3)
+        H.he_mul_relin(g.h, g.upload(ct), g.upload(ct2), m)
+        assert_ct_equal(g.download(m), o.mul_relin(ct, ct2))
+    finally:
+        g.close()
