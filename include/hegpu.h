@@ -241,6 +241,19 @@ int he_hconv2d(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, const dou
 int he_havgpool(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, he_layout *out_layout,
                 he_ct **out_cts, int mode, void *stream);
 
+/* Rescale without allocating anything: the same result as he_rescale, bit for bit, for
+ * callers that must not allocate device memory after set-up (their device memory is owned
+ * entirely by another allocator, or a memory cap forbids driver allocations).  The paper
+ * has no counterpart; this is a property of this library's memory handling.
+ * Its scratch is a fixed device array inside the library (24 MiB, 3 * 2^20 words), held on
+ * every GPU that loads the library until the process exits; it rejects a ciphertext whose
+ * 2 * level * n exceeds that with HE_EINVAL.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current: make that first
+ * call before any stream capture.  All calls share the one array and every call overwrites
+ * it completely before reading it; calls whose work overlaps on the GPU (different streams,
+ * or different host threads) race on it and must be serialised by the caller. */
+int he_rescale_noalloc(he_ctx *ctx, he_ct *ct, void *stream);
+
 /* ------------------------------------------------------------------ measurement */
 /* Per-kernel tracing.  he_trace_start(name) selects one kernel (e.g. "ip", "ntt", "mac",
  * "modup", "moddown_fbc", "moddown_combine", "rescale"); every later launch of it is bracketed

@@ -113,6 +113,7 @@ _SIGS = {
     "he_havgpool": (c_int, [c_vp, ctypes.POINTER(he_layout), ctypes.POINTER(c_vp), ctypes.POINTER(he_layout),
                             ctypes.POINTER(c_vp), c_int, c_vp]),
     "he_bench_modmul": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_double)]),
+    "he_rescale_noalloc": (c_int, [c_vp, c_vp, c_vp]),
     "he_trace_start": (c_int, [ctypes.c_char_p]),
     "he_trace_stop": (c_int, [ctypes.POINTER(c_double), ctypes.POINTER(c_u64), ctypes.POINTER(c_double),
                               ctypes.POINTER(c_double)]),
@@ -337,6 +338,10 @@ def he_mul_pt_acc(ctx, acc, ct, pt, stream=None):
 
 def he_rescale(ctx, ct, stream=None):
     _check(load().he_rescale(ctx, ct, stream_ptr(stream)))
+
+
+def he_rescale_noalloc(ctx, ct, stream=None):
+    _check(load().he_rescale_noalloc(ctx, ct, stream_ptr(stream)))
 
 
 def he_add(ctx, acc, b, stream=None):
