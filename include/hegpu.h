@@ -45,7 +45,11 @@ enum {
     HE_ESTATE = -7     /* object used in the wrong state (e.g. wrong context) */
 };
 
-enum { HE_PLAIN = 0, HE_BATCHED = 1 };
+/* Execution modes of the layer programs.  HE_PLAIN and HE_BATCHED give identical bits (one
+ * ModDown per rotation).  HE_FUSED moves the weighted sum of each output shard inside the
+ * ModDown (inner product and plaintext MAC fused over Q u P, one ModDown per output shard);
+ * it decrypts to the same layer with different bits. */
+enum { HE_PLAIN = 0, HE_BATCHED = 1, HE_FUSED = 2 };
 enum { HE_RELIN_KEY = 0x7fffffff };   /* key id of the relinearisation key in he_key_export */
 
 typedef struct he_ctx he_ctx;
@@ -208,7 +212,9 @@ int he_conv_export_plan(const he_conv *conv, int32_t *u, int32_t *v, int32_t *a,
 int he_conv_import_plaintexts(he_conv *conv, const int64_t *terms, const int64_t *bias);
 /* Run: out[v] (allocated by the caller at he_conv_out_level) for v < out layout n_shards.
  * mode HE_PLAIN = per-ciphertext launches; HE_BATCHED = every rotation of a stage in one
- * launch per kernel (keys read once per amount for all shards).  Same bits either way. */
+ * launch per kernel; these two give the same bits.  HE_FUSED = for each group of output
+ * shards one kernel streams every rotation key once, forms the inner products and their
+ * plaintext-weighted sums over Q u P in registers, then one ModDown per output shard. */
 int he_conv_run(he_ctx *ctx, he_conv *conv, he_ct *const *in, he_ct **out, int mode,
                 void *stream);
 

@@ -282,6 +282,64 @@ def conv_he(ctx, plan: ConvPlan, cts, pts=None, bias_pts=None):
     return out
 
 
+def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None):
+    """hconv2d with one ModDown per output shard ("double hoisting").
+
+    Same plan and plaintexts as conv_he.  A hoisted rotation is
+    R_a = (phi_a(c0) + ModDown(u0_a), ModDown(u1_a)), u_a = sum_j phi_a(D_j) * ksk_a[j] over
+    Q u P.  Here the weighted sum moves inside the ModDown: for output shard v
+        out_v = Rescale( (B0, B1) + ModDown( sum_{(u,a), a != 0} pt_{u,v,a} * u_a ) )
+    with B0 = sum_{(u,a)} pt_{u,v,a} * phi_a(c0_u) and B1 = sum_{(u,0)} pt_{u,v,0} * c1_u, the
+    plaintext reduced modulo every prime of Q u P.  It decrypts like conv_he (one ModDown
+    rounding per output instead of one per rotation) but the bits differ.
+    """
+    from .ckks import Ciphertext
+    level, scale = cts[0].level, cts[0].scale
+    assert all(c.level == level and c.scale == scale for c in cts)
+    if pts is None:
+        pts = conv_plaintexts(plan, ctx.n, float(ctx.q[level]))
+    mq, pq = ctx.mods(level), ctx.psis(level)
+    me, pe = ctx.mods(level, True), ctx.psis(level, True)
+    nq, ne, n = level + 1, len(me), ctx.n
+    D = {}
+    for u, ct in enumerate(cts):
+        if any(a != 0 for a in plan.amounts(u)):
+            D[u] = ctx.hoist(ct)
+    c_eval = [[ctx.ntt(ct.c[k], mq, pq).reshape(nq, n) for k in range(2)] for ct in cts]
+    out = []
+    for v in range(plan.lout.n_shards):
+        acc = [np.zeros((ne, n), dtype=np.uint64) for _ in range(2)]
+        base = [np.zeros((nq, n), dtype=np.uint64) for _ in range(2)]
+        for (u, a) in sorted(plan.terms[v].keys()):
+            pt = pts[(u, v, a)]
+            Pq = ctx.ntt(ctx.reduce_int(pt, mq), mq, pq).reshape(nq, n)
+            if a == 0:
+                for k in range(2):
+                    ctx.lib.orc_mac(base[k], Pq, c_eval[u][k], nq, n, mq)
+                continue
+            g = ctx.galois(a)
+            ctx.gen_rotation_key(a)
+            c0g = ctx.automorph_eval(c_eval[u][0], g).reshape(nq, n)
+            ctx.lib.orc_mac(base[0], Pq, c0g, nq, n, mq)
+            Pe = ctx.ntt(ctx.reduce_int(pt, me), me, pe).reshape(ne, n)
+            keys = ctx._key_limbs(g, level)
+            for k in range(2):
+                uk = np.zeros((ne, n), dtype=np.uint64)
+                for j, Dj in enumerate(D[u]):
+                    ctx.lib.orc_mac(uk, ctx.automorph_eval(Dj, g).reshape(ne, n),
+                                    np.ascontiguousarray(keys[j][k]), ne, n, me)
+                ctx.lib.orc_mac(acc[k], Pe, uk, ne, n, me)
+        c = []
+        for k in range(2):
+            y = ctx.moddown(ctx.intt(acc[k], me, pe).reshape(ne, n), level)
+            c.append(ctx.add(ctx.intt(base[k], mq, pq).reshape(nq, n), y, mq))
+        ct = ctx.rescale(Ciphertext(np.stack(c), level, scale * ctx.q[level]))
+        bpt = bias_pts[v] if bias_pts is not None else encode(plan.bias[v], ctx.n, ct.scale)
+        ct.c[0] = ctx.add(ct.c[0], ctx.reduce_int(bpt, ctx.mods(ct.level)), ctx.mods(ct.level))
+        out.append(ct)
+    return out
+
+
 # ============================================================================ pooling
 @dataclass
 class PoolPlan:

@@ -267,6 +267,7 @@ static int build_fbc(he_ctx *c, const std::vector<int> &src, const std::vector<i
 static void free_ctx(he_ctx *c) {
     if (!c) return;
     for (he_ct *t : c->poly_tmp) he_ct_free(t);
+    if (c->poly_block) cudaFree(c->poly_block);
     for (auto &lv : c->modup)
         for (auto &t : lv)
             if (t.d) cudaFree(t.d);
@@ -917,7 +918,7 @@ extern "C" int he_sub(he_ctx *c, he_ct *acc, const he_ct *b, void *stream) {
 }
 
 // exact integer held by a double -> residue mod q
-static bool int_residue(double v, u64 q, u64 *out) {
+bool int_residue(double v, u64 q, u64 *out) {
     if (!(std::fabs(v) < 1.7e38) || v != std::nearbyint(v)) return false;
     bool neg = v < 0;
     double a = neg ? -v : v;

@@ -114,7 +114,9 @@ struct he_ctx {
     std::map<int, DeviceKey> keys;       // key id (Galois element; 0 = relin) -> key
     Scratch sc_digits, sc_u, sc_conv, sc_tmp, sc_tmp2;
     size_t key_bytes = 0;
-    std::vector<he_ct *> poly_tmp;       // reusable temporaries of he_poly_eval (level L)
+    std::vector<he_ct *> poly_tmp;       // reusable temporaries of he_poly_eval (level L), views
+    u64 *poly_block = nullptr;           // one allocation holding them at a uniform stride
+    Scratch sc_relin;                    // batched relinearisation buffers
 };
 
 struct ntt_job {
@@ -122,8 +124,10 @@ struct ntt_job {
     size_t poly_stride;
     int l0, nl;              // limbs [l0, l0+nl) of each poly
     int nq;                  // limbs < nq use prime q_limb, limbs >= nq use p_(limb-nq)
-    int skip_alpha;          // if > 0: in poly p skip limbs [p*skip_alpha, min((p+1)*skip_alpha, nq))
+    int skip_alpha;          // if > 0: in poly p skip limbs [j*skip_alpha, min((j+1)*skip_alpha, nq)),
+                             // j = p mod skip_mod (j = p when skip_mod is 0)
     int npoly;
+    int skip_mod;
 };
 
 // ----------------------------------------------------------------------------- kernels
@@ -192,6 +196,10 @@ int k_tensor(const he_ctx *ctx, const he_ct *a, const he_ct *b, u64 *d /*[3][l+1
              cudaStream_t s);
 int k_inner_product_one(const he_ctx *ctx, const ip_item &it, int level, cudaStream_t s);
 int k_moddown_combine_one(const he_ctx *ctx, const md_item &it, int level, cudaStream_t s);
+// up to HE_INLINE_ITEMS items passed by value (no device table, no upload)
+#define HE_INLINE_ITEMS 8
+int k_inner_product_inline(const he_ctx *ctx, const ip_item *items, int n, int level, cudaStream_t s);
+int k_moddown_combine_inline(const he_ctx *ctx, const md_item *items, int n, int level, cudaStream_t s);
 int k_mac_one(const he_ctx *ctx, const mac_term &t, u64 *out, size_t out_pstride, int level,
               bool accumulate, cudaStream_t s);
 int k_mul_scalar_v(const he_ctx *ctx, he_ct *ct, const u64 *res, const u64 *shoup, int polys,
@@ -199,6 +207,24 @@ int k_mul_scalar_v(const he_ctx *ctx, he_ct *ct, const u64 *res, const u64 *shou
 int k_add_const_v(const he_ctx *ctx, he_ct *ct, const u64 *res, cudaStream_t s);
 int k_mul_pointwise(const he_ctx *ctx, const u64 *a, const u64 *b, u64 *out, int nlimbs,
                     cudaStream_t s);
+// Fused inner product + MAC in the raised basis (one ModDown per output afterwards).
+#define HE_FUSED_MAXV 4
+struct fused_item {
+    const u64 *D;           // raised digits of the source [beta][l+1+K][n]; null when amount 0
+    const u64 *key;         // key [dnum][2][L+1+K][n]; null when amount 0
+    const u64 *src;         // source ciphertext data (c0, c1 at src + src_ps), level l
+    size_t src_ps;
+    u64 g;                  // Galois element (1 when amount 0)
+    int beta;
+    const u64 *pt[HE_FUSED_MAXV];   // per output of the group: [l+1+K][n] Montgomery, or null
+};
+// acc [V][2][l+1+K][n] = sum pt * u_item (normal form); base [V][2][l+1][n] = sum pt * phi(c0)
+// (and pt * c1 for amount-0 items)
+int k_ipmac(const he_ctx *ctx, const fused_item *items_dev, int n_items, int V, int level,
+            u64 *acc, u64 *base, cudaStream_t s);
+int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u64 *res, int n,
+              const u64 *cst, int level, u64 *out, size_t out_ps, cudaStream_t s);
+int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s);
 double k_bench_modmul(const he_ctx *ctx, int blocks, int iters, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- host helpers
@@ -211,6 +237,7 @@ int prime_index(const he_ctx *ctx, int limb, int nq);   // limb of a Q_l u P pol
 void encode_slots(const double *z, int n, double S, int64_t *m_out);
 void decode_coeffs(const double *m, int n, double S, double *z_out);
 int ensure_ct(he_ctx *ctx, he_ct *ct, int level);
+bool int_residue(double v, u64 q, u64 *out);   // exact-integer double -> residue mod q
 int keyswitch_core(he_ctx *ctx, const u64 *d_ntt, int level, const DeviceKey &key, u64 g_apply,
                    const u64 *base, size_t base_pstride, int base_polys, u64 g_base, he_ct *out,
                    cudaStream_t s);

@@ -4,6 +4,9 @@
 // coefficient index of one limb, so every global access is a coalesced 8-byte stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <string.h>
+
 #include "internal.h"
 #include "modarith.cuh"
 
@@ -20,6 +23,7 @@ __device__ __forceinline__ int prime_of(const KP &kp, int limb, int nq) {
 __device__ __forceinline__ int job_limb(const ntt_job &j, int y, int p) {
     int s0 = 0, s1 = 0;
     if (j.skip_alpha > 0) {
+        if (j.skip_mod > 0) p %= j.skip_mod;
         s0 = p * j.skip_alpha;
         s1 = min(s0 + j.skip_alpha, j.nq);
         if (s0 >= j.nq) s0 = s1 = 0;
@@ -207,7 +211,7 @@ __device__ __forceinline__ void reg_pass(u64 (&x)[16], int base, int ls, int log
 }
 
 template <bool INV>
-__global__ void __launch_bounds__(256) ntt16_cols(KP kp, ntt_job job) {
+__global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job) {
     __shared__ u64 sm[4096];
     const int p = blockIdx.z;
     const int limb = job_limb(job, blockIdx.y, p);
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(256) ntt16_cols(KP kp, ntt_job job) {
 __device__ __forceinline__ int pad17(int k) { return k + (k >> 4); }
 
 template <bool INV>
-__global__ void __launch_bounds__(256) ntt16_rows(KP kp, ntt_job job) {
+__global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job) {
     __shared__ u64 sm[16][272];
     const int p = blockIdx.z;
     const int limb = job_limb(job, blockIdx.y, p);
@@ -500,10 +504,17 @@ __global__ void __launch_bounds__(TB) modup_kernel(KP kp, ModupArgs A) {
 
 // ------------------------------------------------------------------------------ inner product
 // u_c[t][k] = sum_j D_j[t][phi_g(k)] * ksk[j][c][t'][k]   (key in Montgomery form -> normal)
-__global__ void __launch_bounds__(TB) ip_kernel(KP kp, const ip_item *items, ip_item one, int level) {
+struct IpInline {
+    ip_item it[HE_INLINE_ITEMS];
+};
+struct MdInline {
+    md_item it[HE_INLINE_ITEMS];
+};
+
+__global__ void __launch_bounds__(TB) ip_kernel(KP kp, const ip_item *items, IpInline inl, int level) {
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
-    const ip_item it = items ? items[blockIdx.z] : one;
+    const ip_item it = items ? items[blockIdx.z] : inl.it[blockIdx.z];
     const int nq = level + 1;
     const int ext = nq + kp.K;
     const int kl = t < nq ? t : kp.L + 1 + (t - nq);     // key limb = global prime index
@@ -556,12 +567,12 @@ __global__ void __launch_bounds__(TB) moddown_fbc_kernel(KP kp, const u64 *u, u6
 }
 
 // out_c[i][k] = base_c[i][phi_g(k)] + (u_c[i][k] - conv_c[i][k]) * P^-1
-__global__ void __launch_bounds__(TB) moddown_combine_kernel(KP kp, const md_item *items, md_item one,
+__global__ void __launch_bounds__(TB) moddown_combine_kernel(KP kp, const md_item *items, MdInline inl,
                                                              int level, const u64 *pinv,
                                                              const u64 *pinvs) {
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y;
-    const md_item it = items ? items[blockIdx.z] : one;
+    const md_item it = items ? items[blockIdx.z] : inl.it[blockIdx.z];
     const int nq = level + 1;
     const int ext = nq + kp.K;
     const u64 q = kp.q[i];
@@ -628,6 +639,115 @@ __global__ void __launch_bounds__(TB) mac_kernel(KP kp, const mac_term *terms, m
     }
     out[off] = r0;
     out[out_pstride + off] = r1;
+}
+
+// ------------------------------------------------------------------------------ fused IP + MAC
+// For every coefficient k of limb t of Q_l u P and every item (source shard u, amount a):
+//   u_c = REDC(sum_j D_j[t][phi_a(k)] * ksk_a[j][c][t][k])          (inner product, normal form)
+//   acc_c[v] += pt_v[t][k] * u_c                                       (Montgomery pt -> one REDC)
+// and on the Q limbs base_0[v] += pt_v * c0[phi_a(k)] (+ base_1[v] += pt_v * c1 for a = 0).
+// Rotated ciphertexts are never written: key, plaintext and the gathered digits feed
+// 128-bit accumulators directly.
+// Two coefficients per thread: for Galois elements g = 1 mod 4 the NTT-domain automorphism
+// maps the aligned pair (k, k^1) onto an aligned pair (phi(k), phi(k)^1), so every gather is a
+// full 16-byte load and every key / plaintext / output access a 16-byte vector access.
+__device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *(const ulonglong2 *)p; }
+__device__ __forceinline__ void st2(u64 *p, u64 a, u64 b) { *(ulonglong2 *)p = make_ulonglong2(a, b); }
+
+template <int V>
+__global__ void __launch_bounds__(TB) ipmac_kernel(KP kp, const fused_item *items, int n_items,
+                                                   int level, u64 *acc, u64 *base) {
+    const int k = 2 * (blockIdx.x * TB + threadIdx.x);
+    const int t = blockIdx.y;
+    const int nq = level + 1;
+    const int ext = nq + kp.K;
+    const int kl = t < nq ? t : kp.L + 1 + (t - nq);
+    const u64 q = kp.q[kl], qi = kp.qinv[kl];
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    const size_t off = (size_t)t * kp.n + k;
+    u128 a0[V][2], a1[V][2], b0[V][2], b1[V][2];
+#pragma unroll
+    for (int v = 0; v < V; v++)
+#pragma unroll
+        for (int e = 0; e < 2; e++) a0[v][e] = a1[v][e] = b0[v][e] = b1[v][e] = 0;
+    for (int i = 0; i < n_items; i++) {
+        const fused_item &it = items[i];
+        const int ks = it.g == 1 ? k : autom_index(k, it.g, kp.logn);
+        const int sw = ks & 1, kb = ks & ~1;
+        ulonglong2 p[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) p[v] = it.pt[v] ? ld2(it.pt[v] + off) : make_ulonglong2(0, 0);
+        if (it.key) {
+            u128 s0[2] = {0, 0}, s1[2] = {0, 0};
+            for (int j = 0; j < it.beta; j++) {
+                const ulonglong2 d = ld2(it.D + ((size_t)j * ext + t) * kp.n + kb);
+                const u64 d0 = sw ? d.y : d.x, d1 = sw ? d.x : d.y;
+                const u64 *kp0 = it.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+                const ulonglong2 k0 = ld2(kp0), k1 = ld2(kp0 + kstride);
+                s0[0] += (u128)d0 * k0.x;
+                s0[1] += (u128)d1 * k0.y;
+                s1[0] += (u128)d0 * k1.x;
+                s1[1] += (u128)d1 * k1.y;
+            }
+            const u64 u00 = redc(s0[0], q, qi), u01 = redc(s0[1], q, qi);
+            const u64 u10 = redc(s1[0], q, qi), u11 = redc(s1[1], q, qi);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                a0[v][0] += (u128)p[v].x * u00;
+                a0[v][1] += (u128)p[v].y * u01;
+                a1[v][0] += (u128)p[v].x * u10;
+                a1[v][1] += (u128)p[v].y * u11;
+            }
+        }
+        if (t < nq) {
+            const ulonglong2 cc = ld2(it.src + (size_t)t * kp.n + kb);
+            const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
+            ulonglong2 c1 = make_ulonglong2(0, 0);
+            if (!it.key) c1 = ld2(it.src + it.src_ps + off);
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                b0[v][0] += (u128)p[v].x * c00;
+                b0[v][1] += (u128)p[v].y * c01;
+                b1[v][0] += (u128)p[v].x * c1.x;
+                b1[v][1] += (u128)p[v].y * c1.y;
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        st2(acc + ((size_t)(2 * v) * ext) * kp.n + off, redc(a0[v][0], q, qi), redc(a0[v][1], q, qi));
+        st2(acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
+        if (t < nq) {
+            st2(base + ((size_t)(2 * v) * nq) * kp.n + off, redc(b0[v][0], q, qi), redc(b0[v][1], q, qi));
+            st2(base + ((size_t)(2 * v + 1) * nq) * kp.n + off, redc(b1[v][0], q, qi), redc(b1[v][1], q, qi));
+        }
+    }
+}
+
+// acc = sum_terms K_term * x_term (+ c on poly 0) over limbs 0..level, x of any higher level
+// (the drop is implicit); per-limb residues of the integer constants are passed by value.
+#define HE_LC_MAX 20
+#define HE_LC_LIMBS 24
+struct LincombArgs {
+    const u64 *x[HE_LC_MAX];
+    size_t ps[HE_LC_MAX];
+    u64 res[HE_LC_MAX][HE_LC_LIMBS];
+    u64 cst[HE_LC_LIMBS];
+    int n_terms;
+};
+__global__ void lincomb_kernel(KP kp, LincombArgs A, u64 *out, size_t out_ps) {
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int i = blockIdx.y;
+    const int c = blockIdx.z;
+    const u64 q = kp.q[i], qi = kp.qinv[i], r2 = kp.r2[i];
+    u128 acc = 0;
+    for (int t = 0; t < A.n_terms; t++) {
+        const u64 x = A.x[t][c * A.ps[t] + (size_t)i * kp.n + k];
+        acc += (u128)x * to_mont(A.res[t][i], q, qi, r2);
+    }
+    u64 r = redc(acc, q, qi);
+    if (c == 0) r = add_mod(r, A.cst[i], q);
+    out[c * out_ps + (size_t)i * kp.n + k] = r;
 }
 
 __global__ void tensor_kernel(KP kp, const u64 *a, size_t pa, const u64 *b, size_t pb, u64 *d,
@@ -852,17 +972,26 @@ static double ip_mulmods(const he_ctx *ctx, int level, int items) {
 int k_inner_product(const he_ctx *ctx, const ip_item *items_dev, int n_items, int level,
                     cudaStream_t s) {
     TraceScope tr("ip", s, ip_bytes(ctx, level, n_items), ip_mulmods(ctx, level, n_items));
-    ip_kernel<<<dim3(ctx->n / TB, level + 1 + ctx->K, n_items), TB, 0, s>>>(ctx->kp, items_dev, ip_item{},
+    ip_kernel<<<dim3(ctx->n / TB, level + 1 + ctx->K, n_items), TB, 0, s>>>(ctx->kp, items_dev, IpInline{},
                                                                              level);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
-int k_inner_product_one(const he_ctx *ctx, const ip_item &it, int level, cudaStream_t s) {
-    TraceScope tr("ip", s, ip_bytes(ctx, level, 1), ip_mulmods(ctx, level, 1));
-    ip_kernel<<<dim3(ctx->n / TB, level + 1 + ctx->K, 1), TB, 0, s>>>(ctx->kp, nullptr, it, level);
-    LAUNCH_CHECK();
+int k_inner_product_inline(const he_ctx *ctx, const ip_item *items, int n, int level, cudaStream_t s) {
+    for (int i0 = 0; i0 < n; i0 += HE_INLINE_ITEMS) {
+        const int cnt = std::min(HE_INLINE_ITEMS, n - i0);
+        IpInline inl;
+        for (int i = 0; i < cnt; i++) inl.it[i] = items[i0 + i];
+        TraceScope tr("ip", s, ip_bytes(ctx, level, cnt), ip_mulmods(ctx, level, cnt));
+        ip_kernel<<<dim3(ctx->n / TB, level + 1 + ctx->K, cnt), TB, 0, s>>>(ctx->kp, nullptr, inl, level);
+        LAUNCH_CHECK();
+    }
     return HE_OK;
+}
+
+int k_inner_product_one(const he_ctx *ctx, const ip_item &it, int level, cudaStream_t s) {
+    return k_inner_product_inline(ctx, &it, 1, level, s);
 }
 
 int k_moddown_fbc(const he_ctx *ctx, const u64 *u, u64 *conv, int level, int npoly,
@@ -885,19 +1014,29 @@ int k_moddown_combine(const he_ctx *ctx, const md_item *items_dev, int n_items, 
     const u64 *pinvs = pinv + (ctx->L + 1);
     TraceScope tr("moddown_combine", s, (double)n_items * (level + 1) * ctx->n * 8 * 7, (double)n_items * (level + 1) * ctx->n * 2);
     moddown_combine_kernel<<<dim3(ctx->n / TB, level + 1, n_items), TB, 0, s>>>(
-        ctx->kp, items_dev, md_item{}, level, pinv, pinvs);
+        ctx->kp, items_dev, MdInline{}, level, pinv, pinvs);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
-int k_moddown_combine_one(const he_ctx *ctx, const md_item &it, int level, cudaStream_t s) {
+int k_moddown_combine_inline(const he_ctx *ctx, const md_item *items, int n, int level, cudaStream_t s) {
     const u64 *pinv = ctx->d_consts + ctx->np;
     const u64 *pinvs = pinv + (ctx->L + 1);
-    TraceScope tr("moddown_combine", s, (double)(level + 1) * ctx->n * 8 * 7, (double)(level + 1) * ctx->n * 2);
-    moddown_combine_kernel<<<dim3(ctx->n / TB, level + 1, 1), TB, 0, s>>>(ctx->kp, nullptr, it, level,
-                                                                         pinv, pinvs);
-    LAUNCH_CHECK();
+    for (int i0 = 0; i0 < n; i0 += HE_INLINE_ITEMS) {
+        const int cnt = std::min(HE_INLINE_ITEMS, n - i0);
+        MdInline inl;
+        for (int i = 0; i < cnt; i++) inl.it[i] = items[i0 + i];
+        TraceScope tr("moddown_combine", s, (double)cnt * (level + 1) * ctx->n * 8 * 7,
+                      (double)cnt * (level + 1) * ctx->n * 2);
+        moddown_combine_kernel<<<dim3(ctx->n / TB, level + 1, cnt), TB, 0, s>>>(ctx->kp, nullptr, inl, level,
+                                                                               pinv, pinvs);
+        LAUNCH_CHECK();
+    }
     return HE_OK;
+}
+
+int k_moddown_combine_one(const he_ctx *ctx, const md_item &it, int level, cudaStream_t s) {
+    return k_moddown_combine_inline(ctx, &it, 1, level, s);
 }
 
 int k_rescale_prep(const he_ctx *ctx, const u64 *top, size_t top_pstride, u64 *t, int level,
@@ -962,6 +1101,63 @@ int k_mul_pointwise(const he_ctx *ctx, const u64 *a, const u64 *b, u64 *out, int
 int k_tensor(const he_ctx *ctx, const he_ct *a, const he_ct *b, u64 *d, cudaStream_t s) {
     tensor_kernel<<<dim3(ctx->n / TB, a->level + 1), TB, 0, s>>>(ctx->kp, a->d, a->pstride, b->d, b->pstride, d,
                                                                 a->level);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+int k_ipmac(const he_ctx *ctx, const fused_item *items_dev, int n_items, int V, int level,
+            u64 *acc, u64 *base, cudaStream_t s) {
+    const int ext = level + 1 + ctx->K;
+    const double beta = (level + ctx->alpha) / ctx->alpha;
+    // algorithmic bytes: per rotation the key (2 beta limbs) and V plaintexts over Q u P, the
+    // digits once, the outputs once
+    TraceScope tr("ipmac", s, (double)ext * ctx->n * 8 * ((double)n_items * (2 * beta + V) + beta + 2.0 * V) +
+                                  (double)(level + 1) * ctx->n * 8 * (2.0 + 2.0 * V),
+                  (double)n_items * ext * ctx->n * (2 * beta + 2.0 * V));
+    dim3 g(ctx->n / (2 * TB), ext);
+    switch (V) {
+        case 1: ipmac_kernel<1><<<g, TB, 0, s>>>(ctx->kp, items_dev, n_items, level, acc, base); break;
+        case 2: ipmac_kernel<2><<<g, TB, 0, s>>>(ctx->kp, items_dev, n_items, level, acc, base); break;
+        case 4: ipmac_kernel<4><<<g, TB, 0, s>>>(ctx->kp, items_dev, n_items, level, acc, base); break;
+        default: he_set_error("k_ipmac: V must be 1, 2 or 4"); return HE_EINVAL;
+    }
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u64 *res /*[n][24]*/, int n,
+              const u64 *cst /*[24]*/, int level, u64 *out, size_t out_ps, cudaStream_t s) {
+    if (n < 1 || n > HE_LC_MAX || level + 1 > HE_LC_LIMBS) {
+        he_set_error("lincomb: at most %d terms of at most %d limbs", HE_LC_MAX, HE_LC_LIMBS);
+        return HE_EINVAL;
+    }
+    LincombArgs A;
+    memset(&A, 0, sizeof(A));
+    for (int t = 0; t < n; t++) {
+        A.x[t] = x[t];
+        A.ps[t] = ps[t];
+        for (int i = 0; i <= level; i++) A.res[t][i] = res[t * HE_LC_LIMBS + i];
+    }
+    for (int i = 0; i <= level; i++) A.cst[i] = cst[i];
+    A.n_terms = n;
+    lincomb_kernel<<<dim3(ctx->n / TB, level + 1, 2), TB, 0, s>>>(ctx->kp, A, out, out_ps);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+// rescale of m ciphertexts laid out at a uniform stride (poly p of ct i at base + (2i + p) ps)
+int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s) {
+    ntt_job top{base, ps, level, 1, level + 1, 0, 2 * m, 0};
+    HE_TRY(k_ntt(ctx, top, true, s));
+    rescale_prep_kernel<<<dim3(ctx->n / TB, level, 2 * m), TB, 0, s>>>(ctx->kp, base + (size_t)level * ctx->n, ps, t, level);
+    LAUNCH_CHECK();
+    ntt_job tj{t, (size_t)level * ctx->n, 0, level, level, 0, 2 * m, 0};
+    HE_TRY(k_ntt(ctx, tj, false, s));
+    const u64 *cb = ctx->d_consts + ctx->np + 2 * (ctx->L + 1);
+    const u64 *inv = cb + (size_t)level * 2 * (ctx->L + 1);
+    const u64 *invs = inv + (ctx->L + 1);
+    TraceScope tr("rescale", s, (double)m * level * ctx->n * 8 * 6, (double)m * level * ctx->n * 2);
+    rescale_combine_kernel<<<dim3(ctx->n / TB, level, 2 * m), TB, 0, s>>>(ctx->kp, base, ps, t, level, inv, invs);
     LAUNCH_CHECK();
     return HE_OK;
 }

@@ -284,9 +284,10 @@ he_ct view(he_ctx *c, u64 *d, size_t ps, int level, double scale) {
 // Encode slot vectors at scale S (or take given integer plaintexts) and store them as
 // Montgomery NTT-form plaintexts at `level`, contiguous [count][level+1][n] from dst.
 int upload_plaintexts(he_ctx *c, const std::vector<const double *> &vecs, size_t count, double S,
-                      int level, u64 *dst, const int64_t *given) {
+                      int level, u64 *dst, const int64_t *given, bool ext = false) {
     const int n = c->n;
-    const size_t pw = (size_t)(level + 1) * n;
+    const int nl = level + 1 + (ext ? c->K : 0);         // limbs stored: Q_l, or Q_l u P
+    const size_t pw = (size_t)nl * n;
     int64_t *stage = (int64_t *)c->sc_tmp.p;
     const size_t cap = std::max<size_t>(1, std::min<size_t>(64, c->sc_tmp.words / n));
     std::vector<int64_t> host(cap * (size_t)n);
@@ -305,10 +306,10 @@ int upload_plaintexts(he_ctx *c, const std::vector<const double *> &vecs, size_t
         }
         HE_CHECK_CUDA(cudaMemcpy(stage, host.data(), nb * n * 8, cudaMemcpyHostToDevice));
         for (size_t i = 0; i < nb; i++)
-            HE_TRY(k_reduce_int(c, stage + i * n, dst + (b0 + i) * pw, level + 1, level + 1, false, 0));
-        ntt_job j{dst + b0 * pw, pw, 0, level + 1, level + 1, 0, (int)nb};
+            HE_TRY(k_reduce_int(c, stage + i * n, dst + (b0 + i) * pw, nl, level + 1, false, 0));
+        ntt_job j{dst + b0 * pw, pw, 0, nl, level + 1, 0, (int)nb};
         HE_TRY(k_ntt(c, j, false, 0));
-        HE_TRY(k_to_mont(c, dst + b0 * pw, level + 1, level + 1, (int)nb, pw, 0));
+        HE_TRY(k_to_mont(c, dst + b0 * pw, nl, level + 1, (int)nb, pw, 0));
         HE_CHECK_CUDA(cudaStreamSynchronize(0));
     }
     return HE_OK;
@@ -715,13 +716,28 @@ struct he_conv {
     std::vector<int> tu, tv, ta;                 // terms in plan order
     std::vector<int> term_off;                   // [n_out + 1]
     std::map<long long, int> slot;               // u*N + a -> R slot
+    size_t pe = 0;                               // plaintext stride: Q_l u P limbs
     u64 *R = nullptr, *pts = nullptr, *bias_pts = nullptr, *acc = nullptr;
     mac_term *d_terms = nullptr;
     RotSet rot;
     he_pool *pool = nullptr;
     std::vector<he_ct *> mid;
+    // HE_FUSED resources (built on first use)
+    struct FusedGroup {
+        int V = 1;
+        std::vector<int> outs;                   // output shards of the group
+        fused_item *d_items = nullptr;
+        int n_items = 0;
+        md_item *d_md = nullptr;
+    };
+    std::vector<FusedGroup> fgroups;
+    u64 *D_all = nullptr, *facc = nullptr, *fbase = nullptr, *fconv = nullptr;
+    std::vector<int> hoisted;                    // sources with at least one rotation
+    int fused_V = 0;
     ~he_conv() {
         cudaFree(R); cudaFree(pts); cudaFree(bias_pts); cudaFree(d_terms); cudaFree(acc);
+        for (auto &g : fgroups) { cudaFree(g.d_items); cudaFree(g.d_md); }
+        cudaFree(D_all); cudaFree(facc); cudaFree(fbase); cudaFree(fconv);
         delete pool;
         for (he_ct *x : mid) he_ct_free(x);
     }
@@ -764,7 +780,8 @@ extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, c
     cv->in_scale = in_scale;
     cv->mid_scale = in_scale * (double)c->primes[level] / (double)c->primes[level];
     cv->pw = (size_t)(level + 1) * c->n;
-    const size_t pw = cv->pw;
+    cv->pe = (size_t)(level + 1 + c->K) * c->n;
+    const size_t pw = cv->pw, pe = cv->pe;
     // plan all output shards, keeping the diagonals of one shard at a time
     std::vector<DiagMap> maps(cv->lout.ns);
     size_t n_terms = 0;
@@ -781,7 +798,7 @@ extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, c
                 cv->slot[kv.first] = id;
             }
     HE_TRY(dev_alloc(&cv->R, cv->slot.size() * 2 * pw));
-    HE_TRY(dev_alloc(&cv->pts, n_terms * pw));
+    HE_TRY(dev_alloc(&cv->pts, n_terms * pe));
     HE_TRY(dev_alloc(&cv->bias_pts, (size_t)cv->lout.ns * level * c->n));
     HE_TRY(dev_alloc(&cv->acc, (size_t)cv->lout.ns * 2 * pw));
     // diagonal plaintexts at scale q_level
@@ -795,7 +812,8 @@ extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, c
             cv->ta.push_back((int)(kv.first % c->N));
             vecs.push_back(kv.second.data());
         }
-        HE_TRY(upload_plaintexts(c, vecs, vecs.size(), (double)c->primes[level], level, cv->pts + t0 * pw, nullptr));
+        HE_TRY(upload_plaintexts(c, vecs, vecs.size(), (double)c->primes[level], level, cv->pts + t0 * pe, nullptr,
+                                 true));
         t0 += vecs.size();
         cv->term_off.push_back((int)t0);
         DiagMap().swap(maps[v]);
@@ -810,7 +828,7 @@ extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, c
     std::vector<mac_term> terms(n_terms);
     for (size_t t = 0; t < n_terms; t++) {
         int s = cv->slot[(long long)cv->tu[t] * c->N + cv->ta[t]];
-        terms[t] = mac_term{cv->pts + t * pw, cv->R + (size_t)s * 2 * pw, pw};
+        terms[t] = mac_term{cv->pts + t * pe, cv->R + (size_t)s * 2 * pw, pw};
     }
     HE_TRY(dev_alloc(&cv->d_terms, n_terms));
     HE_CHECK_CUDA(cudaMemcpy(cv->d_terms, terms.data(), n_terms * sizeof(mac_term), cudaMemcpyHostToDevice));
@@ -877,7 +895,7 @@ extern "C" int he_conv_import_plaintexts(he_conv *cv, const int64_t *terms, cons
     he_ctx *c = cv->c;
     if (terms) {
         std::vector<const double *> none;
-        HE_TRY(upload_plaintexts(c, none, cv->tu.size(), 0.0, cv->level, cv->pts, terms));
+        HE_TRY(upload_plaintexts(c, none, cv->tu.size(), 0.0, cv->level, cv->pts, terms, true));
     }
     if (bias)
         for (int v = 0; v < cv->lout.ns; v++)
@@ -885,8 +903,99 @@ extern "C" int he_conv_import_plaintexts(he_conv *cv, const int64_t *terms, cons
     return HE_OK;
 }
 
+// Output groups of up to V shards; each group's items are the (u, a) pairs any of its
+// outputs uses, ordered by source shard so one shard's raised digits stay hot in L2.
+static int conv_prepare_fused(he_conv *cv) {
+    if (!cv->fgroups.empty()) return HE_OK;
+    he_ctx *c = cv->c;
+    const int lv = cv->level, nq = lv + 1, ext = nq + c->K, n_out = cv->lout.ns;
+    const size_t pw = cv->pw, pe = cv->pe;
+    const int beta = (lv + c->alpha) / c->alpha;
+    int V = n_out >= 4 ? 4 : (n_out >= 2 ? 2 : 1);
+    cv->fused_V = V;
+    std::map<long long, int> term_index;          // (u*N + a)*n_out + v -> term
+    for (size_t t = 0; t < cv->tu.size(); t++)
+        term_index[((long long)cv->tu[t] * c->N + cv->ta[t]) * n_out + cv->tv[t]] = (int)t;
+    std::vector<char> rot(cv->lin.ns, 0);
+    for (size_t t = 0; t < cv->tu.size(); t++)
+        if (cv->ta[t] != 0) rot[cv->tu[t]] = 1;
+    std::vector<int> hslot(cv->lin.ns, -1);
+    for (int u = 0; u < cv->lin.ns; u++)
+        if (rot[u]) { hslot[u] = (int)cv->hoisted.size(); cv->hoisted.push_back(u); }
+    HE_TRY(dev_alloc(&cv->D_all, cv->hoisted.size() * (size_t)beta * ext * c->n));
+    HE_TRY(dev_alloc(&cv->facc, (size_t)V * 2 * ext * c->n));
+    HE_TRY(dev_alloc(&cv->fbase, (size_t)V * 2 * nq * c->n));
+    HE_TRY(dev_alloc(&cv->fconv, (size_t)V * 2 * nq * c->n));
+    for (int v0 = 0; v0 < n_out; v0 += V) {
+        he_conv::FusedGroup G;
+        G.V = V;
+        for (int v = v0; v < std::min(n_out, v0 + V); v++) G.outs.push_back(v);
+        std::map<long long, fused_item> items;    // key u*N + a, ascending
+        for (size_t vi = 0; vi < G.outs.size(); vi++) {
+            const int v = G.outs[vi];
+            for (int t = cv->term_off[v]; t < cv->term_off[v + 1]; t++) {
+                const int u = cv->tu[t], a = cv->ta[t];
+                const long long key = (long long)u * c->N + a;
+                auto it = items.find(key);
+                if (it == items.end()) {
+                    fused_item fi;
+                    memset(&fi, 0, sizeof(fi));
+                    fi.src = cv->R + (size_t)u * 2 * pw;
+                    fi.src_ps = pw;
+                    fi.g = h_galois(c, a);
+                    fi.beta = beta;
+                    if (fi.g != 1) {
+                        const DeviceKey *k;
+                        HE_TRY(get_key(c, (int)fi.g, &k));
+                        fi.key = k->d;
+                        fi.D = cv->D_all + (size_t)hslot[u] * beta * ext * c->n;
+                    }
+                    it = items.emplace(key, fi).first;
+                }
+                it->second.pt[vi] = cv->pts + (size_t)t * pe;
+            }
+        }
+        std::vector<fused_item> hv;
+        for (auto &kv : items) hv.push_back(kv.second);
+        G.n_items = (int)hv.size();
+        HE_TRY(dev_alloc(&G.d_items, hv.size()));
+        HE_CHECK_CUDA(cudaMemcpy(G.d_items, hv.data(), hv.size() * sizeof(fused_item), cudaMemcpyHostToDevice));
+        std::vector<md_item> md;
+        for (size_t vi = 0; vi < G.outs.size(); vi++)
+            md.push_back(md_item{cv->facc + vi * 2 * ext * c->n, cv->fconv + vi * 2 * nq * c->n,
+                                 cv->fbase + vi * 2 * nq * c->n, (size_t)nq * c->n, 2, 1,
+                                 cv->acc + (size_t)G.outs[vi] * 2 * pw, pw});
+        HE_TRY(dev_alloc(&G.d_md, md.size()));
+        HE_CHECK_CUDA(cudaMemcpy(G.d_md, md.data(), md.size() * sizeof(md_item), cudaMemcpyHostToDevice));
+        cv->fgroups.push_back(G);
+    }
+    return HE_OK;
+}
+
+static int conv_run_fused(he_conv *cv, cudaStream_t s) {
+    he_ctx *c = cv->c;
+    const int lv = cv->level, nq = lv + 1, ext = nq + c->K;
+    const int beta = (lv + c->alpha) / c->alpha;
+    for (size_t h = 0; h < cv->hoisted.size(); h++) {
+        const int u = cv->hoisted[h];
+        he_ct t = view(c, cv->R + (size_t)u * 2 * cv->pw, cv->pw, lv, 1.0);
+        HE_TRY(hoist_modup(c, &t, cv->D_all + h * (size_t)beta * ext * c->n, s));
+    }
+    for (auto &G : cv->fgroups) {
+        const int V = G.V, nv = (int)G.outs.size();
+        HE_TRY(k_ipmac(c, G.d_items, G.n_items, V, lv, cv->facc, cv->fbase, s));
+        ntt_job jp{cv->facc, (size_t)ext * c->n, nq, c->K, nq, 0, 2 * nv};
+        HE_TRY(k_ntt(c, jp, true, s));
+        HE_TRY(k_moddown_fbc(c, cv->facc, cv->fconv, lv, 2 * nv, s));
+        ntt_job jc{cv->fconv, (size_t)nq * c->n, 0, nq, nq, 0, 2 * nv};
+        HE_TRY(k_ntt(c, jc, false, s));
+        HE_TRY(k_moddown_combine(c, G.d_md, nv, lv, s));
+    }
+    return HE_OK;
+}
+
 extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out, int mode, void *stream) {
-    if (!c || !cv || !in || !out || cv->c != c || (mode != HE_PLAIN && mode != HE_BATCHED)) {
+    if (!c || !cv || !in || !out || cv->c != c || (mode != HE_PLAIN && mode != HE_BATCHED && mode != HE_FUSED)) {
         he_set_error("he_conv_run: bad argument");
         return HE_EINVAL;
     }
@@ -900,14 +1009,20 @@ extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out
         }
         HE_TRY(k_copy_limbs(cv->R + (size_t)u * 2 * pw, pw, in[u]->d, in[u]->pstride, pw, 2, s));
     }
-    if (mode == HE_BATCHED) HE_TRY(cv->rot.prepare_batched());
-    HE_TRY(cv->rot.run(mode, s));
+    if (mode == HE_FUSED) {
+        HE_TRY(conv_prepare_fused(cv));
+        HE_TRY(conv_run_fused(cv, s));
+    } else {
+        if (mode == HE_BATCHED) HE_TRY(cv->rot.prepare_batched());
+        HE_TRY(cv->rot.run(mode, s));
+    }
     he_ct **dst = cv->stride == 1 ? out : cv->mid.data();
     for (int v = 0; v < cv->lout.ns; v++) {
-        // MAC over all (u, a) terms of output shard v, rescale, add the bias, hand out
+        // MAC over all (u, a) terms of output shard v (fused mode: already in acc), rescale,
+        // add the bias, hand out
         u64 *a = cv->acc + (size_t)v * 2 * pw;
         const int t0 = cv->term_off[v], t1 = cv->term_off[v + 1];
-        HE_TRY(k_mac(c, cv->d_terms + t0, t1 - t0, a, pw, lv, false, s));
+        if (mode != HE_FUSED) HE_TRY(k_mac(c, cv->d_terms + t0, t1 - t0, a, pw, lv, false, s));
         he_ct t = view(c, a, pw, lv, cv->in_scale * (double)c->primes[lv]);
         HE_TRY(he_rescale(c, &t, stream));
         HE_TRY(k_add_raw(c, a, pw, cv->bias_pts + (size_t)v * lv * c->n, 0, lv, 1, false, s));
@@ -917,16 +1032,85 @@ extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out
         dst[v]->scale = t.scale;
     }
     if (cv->stride == 2) {
-        if (mode == HE_BATCHED) HE_TRY(pool_prepare(cv->pool, mode));
-        return pool_run(c, cv->pool, cv->mid.data(), out, mode, s);
+        const int pm = mode == HE_FUSED ? HE_BATCHED : mode;
+        HE_TRY(pool_prepare(cv->pool, pm));
+        return pool_run(c, cv->pool, cv->mid.data(), out, pm, s);
     }
     return HE_OK;
 }
 
 // ================================================================================ polynomial
+// Relinearised products of several ciphertext pairs at one level in one set of launches per
+// kernel: tensor, ModUp of every d2, one inner-product launch with the relinearisation key
+// (read once per launch for all pairs), one ModDown pipeline, then the rescales.  Each
+// product gets exactly the bits he_mul_relin gives it.
+static int relin_batch(he_ctx *c, const std::vector<const he_ct *> &A, const std::vector<const he_ct *> &B,
+                       const std::vector<he_ct *> &out, cudaStream_t s) {
+    const int m = (int)A.size();
+    if (m == 0) return HE_OK;
+    const int l = A[0]->level;
+    for (int i = 0; i < m; i++)
+        if (A[i]->level != l || B[i]->level != l) { he_set_error("relin_batch: levels differ"); return HE_ELEVEL; }
+    if (l < 1) { he_set_error("relin_batch: no level left"); return HE_ELEVEL; }
+    const DeviceKey *key;
+    HE_TRY(get_key(c, 0, &key));
+    const int nq = l + 1, ext = nq + c->K, beta = (l + c->alpha) / c->alpha;
+    const size_t n = c->n, wq = (size_t)nq * n, we = (size_t)ext * n;
+    const size_t per = 3 * wq + wq + (size_t)beta * we + 2 * we + 2 * wq + 2 * wq;
+    HE_TRY(c->sc_relin.ensure((size_t)m * per));
+    u64 *d = c->sc_relin.p;                       // [m][3][nq][n]
+    u64 *xc = d + (size_t)m * 3 * wq;             // [m][nq][n]
+    u64 *D = xc + (size_t)m * wq;                 // [m][beta][ext][n]
+    u64 *u = D + (size_t)m * beta * we;           // [m][2][ext][n]
+    u64 *conv = u + (size_t)m * 2 * we;           // [m][2][nq][n]
+    u64 *rt = conv + (size_t)m * 2 * wq;          // [m][2][nq][n] rescale scratch
+    for (int i = 0; i < m; i++) {
+        he_ct ta = *A[i], tb = *B[i];
+        HE_TRY(k_tensor(c, &ta, &tb, d + (size_t)i * 3 * wq, s));
+    }
+    HE_TRY(k_copy_limbs(xc, wq, d + 2 * wq, 3 * wq, wq, m, s));
+    ntt_job ji{xc, wq, 0, nq, nq, 0, m, 0};
+    HE_TRY(k_ntt(c, ji, true, s));
+    for (int i = 0; i < m; i++)
+        HE_TRY(k_modup(c, xc + i * wq, d + (size_t)i * 3 * wq + 2 * wq, D + (size_t)i * beta * we, l, s));
+    ntt_job jd{D, we, 0, ext, nq, c->alpha, beta * m, beta};
+    HE_TRY(k_ntt(c, jd, false, s));
+    std::vector<ip_item> ip(m);
+    std::vector<md_item> md(m);
+    for (int i = 0; i < m; i++) {
+        HE_TRY(ensure_ct(c, out[i], l));
+        ip[i] = ip_item{D + (size_t)i * beta * we, key->d, u + (size_t)i * 2 * we, 1, beta};
+        md[i] = md_item{u + (size_t)i * 2 * we, conv + (size_t)i * 2 * wq, d + (size_t)i * 3 * wq, wq, 2, 1,
+                        out[i]->d, out[i]->pstride};
+    }
+    HE_TRY(k_inner_product_inline(c, ip.data(), m, l, s));
+    ntt_job jp{u, we, nq, c->K, nq, 0, 2 * m, 0};
+    HE_TRY(k_ntt(c, jp, true, s));
+    HE_TRY(k_moddown_fbc(c, u, conv, l, 2 * m, s));
+    ntt_job jc{conv, wq, 0, nq, nq, 0, 2 * m, 0};
+    HE_TRY(k_ntt(c, jc, false, s));
+    HE_TRY(k_moddown_combine_inline(c, md.data(), m, l, s));
+    bool uniform = true;
+    for (int i = 1; i < m; i++)
+        uniform = uniform && out[i]->pstride == out[0]->pstride && out[i]->d == out[0]->d + 2 * (size_t)i * out[0]->pstride;
+    if (uniform) HE_TRY(k_rescale_many(c, out[0]->d, out[0]->pstride, m, l, rt, s));
+    for (int i = 0; i < m; i++) {
+        out[i]->scale = A[i]->scale * B[i]->scale;
+        if (uniform) {
+            out[i]->level = l - 1;
+            out[i]->scale = out[i]->scale / (double)c->primes[l];
+        } else {
+            HE_TRY(he_rescale(c, out[i], s));
+        }
+    }
+    return HE_OK;
+}
+
 // sum_k c_k T_k(x): T_{2k} = 2 T_k^2 - 1, T_{2k+1} = 2 T_k T_{k+1} - T_1 (Appendix), then the
 // linear combination with exact-scale integer constants round(c S_t q_l / s) at the lowest
-// level, the constant term round(c_0 S_t q_l) on coefficient 0, and one rescale.
+// level, the constant term round(c_0 S_t q_l) on coefficient 0, and one rescale.  All T_k of
+// one tree depth read operands of lower depth at one common level, so each depth is one
+// batched relinearisation.
 static int retarget(he_ctx *c, const he_ct *x, int level, double scale_t, he_ct *y, cudaStream_t s) {
     HE_TRY(he_ct_copy(y, x, s));
     HE_TRY(he_ct_drop_level(y, level + 1));
@@ -944,56 +1128,99 @@ extern "C" int he_poly_eval(he_ctx *c, he_ct *io, const double *cheb, int deg, d
     if (io->level < depth + 1) { he_set_error("he_poly_eval: needs %d levels", depth + 1); return HE_ELEVEL; }
     cudaStream_t s = (cudaStream_t)stream;
     // temporaries live in the context (allocated once at the top level, reused every call)
-    const size_t need = (size_t)deg + 6;
-    while (c->poly_tmp.size() < need) {
-        he_ct *t = nullptr;
-        HE_TRY(he_ct_alloc(c, c->L, &t));
-        c->poly_tmp.push_back(t);
+    const size_t need = 2 * (size_t)deg + 4;
+    if (c->poly_tmp.size() < need) {
+        for (he_ct *t : c->poly_tmp) he_ct_free(t);
+        c->poly_tmp.clear();
+        if (c->poly_block) cudaFree(c->poly_block);
+        c->poly_block = nullptr;
+        const size_t ps = (size_t)(c->L + 1) * c->n;
+        HE_TRY(dev_alloc(&c->poly_block, need * 2 * ps));
+        for (size_t i = 0; i < need; i++) {
+            he_ct *t = nullptr;
+            HE_TRY(he_ct_wrap(c, c->poly_block + i * 2 * ps, 2 * ps * 8, c->L, &t));
+            c->poly_tmp.push_back(t);
+        }
     }
-    std::vector<he_ct *> T(deg + 1, nullptr);
+    std::vector<he_ct *> T(deg + 1, nullptr), opA(deg + 1, nullptr), opB(deg + 1, nullptr);
     for (int k = 1; k <= deg; k++) T[k] = c->poly_tmp[k - 1];
-    he_ct *tmpa = c->poly_tmp[deg], *tmpb = c->poly_tmp[deg + 1], *t1 = c->poly_tmp[deg + 2];
-    he_ct *acc = c->poly_tmp[deg + 3], *y = c->poly_tmp[deg + 4];
-    int rc = HE_OK;
-#define PTRY(e) do { rc = (e); if (rc != HE_OK) return rc; } while (0)
-    PTRY(he_ct_copy(T[1], io, stream));
-    for (int k = 2; k <= deg; k++) {
-        const int h = k / 2;
-        if (k % 2 == 0) {
-            PTRY(he_mul_relin(c, T[h], T[h], T[k], stream));
-            PTRY(he_mul_int(c, T[k], 2.0, stream));
-            PTRY(he_add_const_int(c, T[k], -std::nearbyint(T[k]->scale), stream));
-        } else {
-            const int lv = std::min(T[h]->level, T[h + 1]->level);
-            PTRY(he_ct_copy(tmpa, T[h], stream));
-            PTRY(he_ct_drop_level(tmpa, lv));
-            PTRY(he_ct_copy(tmpb, T[h + 1], stream));
-            PTRY(he_ct_drop_level(tmpb, lv));
-            PTRY(he_mul_relin(c, tmpa, tmpb, T[k], stream));
-            PTRY(he_mul_int(c, T[k], 2.0, stream));
-            PTRY(retarget(c, T[1], T[k]->level, T[k]->scale, t1, s));
-            PTRY(he_sub(c, T[k], t1, stream));
+    for (int k = 2; k <= deg; k++) opA[k] = c->poly_tmp[deg + k - 2];
+    he_ct *t1 = c->poly_tmp[2 * deg], *acc = c->poly_tmp[2 * deg + 1], *y = c->poly_tmp[2 * deg + 2];
+    HE_TRY(he_ct_copy(T[1], io, stream));
+    for (int d = 1; d <= depth; d++) {
+        const int k0 = (1 << (d - 1)) + 1, k1 = std::min(deg, 1 << d);
+        std::vector<const he_ct *> A, B;
+        std::vector<he_ct *> O;
+        for (int k = k0; k <= k1; k++) {
+            const int h = k / 2;
+            if (k % 2 == 0) {
+                A.push_back(T[h]);
+                B.push_back(T[h]);
+            } else {
+                // depth never decreases with k, so T_{h+1} already sits at the common level and
+                // only a copy of T_h is dropped to it
+                const int lv = T[h + 1]->level;
+                if (T[h]->level < lv) { he_set_error("he_poly_eval: operand levels out of order"); return HE_ESTATE; }
+                HE_TRY(he_ct_copy(opA[k], T[h], stream));
+                HE_TRY(he_ct_drop_level(opA[k], lv));
+                A.push_back(opA[k]);
+                B.push_back(T[h + 1]);
+            }
+            O.push_back(T[k]);
+        }
+        HE_TRY(relin_batch(c, A, B, O, s));
+        for (int k = k0; k <= k1; k++) {
+            HE_TRY(he_mul_int(c, T[k], 2.0, stream));
+            if (k % 2 == 0) {
+                HE_TRY(he_add_const_int(c, T[k], -std::nearbyint(T[k]->scale), stream));
+            } else {
+                HE_TRY(retarget(c, T[1], T[k]->level, T[k]->scale, t1, s));
+                HE_TRY(he_sub(c, T[k], t1, stream));
+            }
         }
     }
     int lmin = T[1]->level;
     for (int k = 2; k <= deg; k++) lmin = std::min(lmin, T[k]->level);
     const double base = target_scale * (double)c->primes[lmin];
+    const double cst = std::nearbyint(cheb[0] * target_scale * (double)c->primes[lmin]);
+    if (deg <= 20 && lmin + 1 <= 24) {
+        // one pass: acc = sum_k K_k T_k + c_0 (same integers and sums as the term-by-term form)
+        std::vector<const u64 *> xs(deg);
+        std::vector<size_t> pss(deg);
+        std::vector<u64> res((size_t)deg * 24, 0), cres(24, 0);
+        for (int k = 1; k <= deg; k++) {
+            const double K = std::nearbyint(cheb[k] * target_scale * (double)c->primes[lmin] / T[k]->scale);
+            xs[k - 1] = T[k]->d;
+            pss[k - 1] = T[k]->pstride;
+            for (int i = 0; i <= lmin; i++)
+                if (!int_residue(K, c->primes[i], &res[(size_t)(k - 1) * 24 + i])) {
+                    he_set_error("he_poly_eval: constant is not an exact integer");
+                    return HE_EINVAL;
+                }
+        }
+        for (int i = 0; i <= lmin; i++)
+            if (!int_residue(cst, c->primes[i], &cres[i])) { he_set_error("he_poly_eval: bad constant"); return HE_EINVAL; }
+        HE_TRY(ensure_ct(c, acc, lmin));
+        HE_TRY(k_lincomb(c, xs.data(), pss.data(), res.data(), deg, cres.data(), lmin, acc->d, acc->pstride, s));
+        acc->scale = base;
+        HE_TRY(he_rescale(c, acc, stream));
+        acc->scale = target_scale;
+        return he_ct_copy(io, acc, stream);
+    }
     bool first = true;
     for (int k = 1; k <= deg; k++) {
-        PTRY(he_ct_copy(y, T[k], stream));
-        PTRY(he_ct_drop_level(y, lmin));
+        HE_TRY(he_ct_copy(y, T[k], stream));
+        HE_TRY(he_ct_drop_level(y, lmin));
         double K = std::nearbyint(cheb[k] * target_scale * (double)c->primes[lmin] / y->scale);
-        PTRY(he_mul_int(c, y, K, stream));
+        HE_TRY(he_mul_int(c, y, K, stream));
         y->scale = base;
-        if (first) { PTRY(he_ct_copy(acc, y, stream)); first = false; }
-        else PTRY(he_add(c, acc, y, stream));
+        if (first) { HE_TRY(he_ct_copy(acc, y, stream)); first = false; }
+        else HE_TRY(he_add(c, acc, y, stream));
     }
-    PTRY(he_add_const_int(c, acc, std::nearbyint(cheb[0] * target_scale * (double)c->primes[lmin]), stream));
-    PTRY(he_rescale(c, acc, stream));
+    HE_TRY(he_add_const_int(c, acc, std::nearbyint(cheb[0] * target_scale * (double)c->primes[lmin]), stream));
+    HE_TRY(he_rescale(c, acc, stream));
     acc->scale = target_scale;
-    PTRY(he_ct_copy(io, acc, stream));
-#undef PTRY
-    return HE_OK;
+    return he_ct_copy(io, acc, stream);
 }
 
 // ================================================================================ wrappers

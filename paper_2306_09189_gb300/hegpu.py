@@ -12,7 +12,7 @@ import numpy as np
 from . import build as _build
 
 HE_OK, HE_EINVAL, HE_ELEVEL, HE_EKEY, HE_ENOMEM, HE_ETIMEOUT, HE_ECUDA, HE_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
-HE_PLAIN, HE_BATCHED = 0, 1
+HE_PLAIN, HE_BATCHED, HE_FUSED = 0, 1, 2
 HE_RELIN_KEY = 0x7FFFFFFF
 HE_MAX_BLOCKS = 4096
 

@@ -89,6 +89,13 @@ def _conv_case(pair, c, co, m, k, pad, level, seed, bias=True):
         for oc, rc in zip(outs, ref):
             assert H.he_ct_scale(oc) == rc.scale
             assert_ct_equal(g.download(oc), rc)
+    # one ModDown per output shard: equals the oracle's raised-basis restatement
+    ref_raised = Ly.conv_he_raised(o, plan, cts, pts, bias_pts)
+    outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
+    H.he_conv_run(g.h, conv, ins, outs, H.HE_FUSED)
+    for oc, rc in zip(outs, ref_raised):
+        assert H.he_ct_scale(oc) == rc.scale
+        assert_ct_equal(g.download(oc), rc)
     H.he_conv_destroy(conv)
     return ref, plan, x, W, b
 
@@ -107,7 +114,7 @@ def test_conv_toy_bit_exact(toy):
 
 
 @pytest.mark.parametrize("c,co,m,k,pad", [(8, 8, 28, 3, 1), (2, 2, 56, 3, 1), (4, 2, 16, 5, 2),
-                                           (3, 2, 32, 7, 3)])
+                                           (3, 2, 32, 7, 3), (16, 24, 16, 3, 1)])
 def test_conv_sharded_bit_exact(mid, c, co, m, k, pad):
     _conv_case(mid, c, co, m, k, pad, level=3, seed=c * 10 + m)
 
@@ -217,15 +224,15 @@ def test_cifar_layer_full_ring():
         H.he_keygen_rotations(g.h, rots)
         H.he_keygen_relin(g.h)
         outs = {}
-        for mode in (H.HE_PLAIN, H.HE_BATCHED):
+        for mode in (H.HE_PLAIN, H.HE_BATCHED, H.HE_FUSED):
             oc = g.ct(level - 1)
             H.he_conv_run(g.h, conv, [ct], [oc], mode)
             outs[mode] = g.download(oc)
+            ref = (torch.nn.functional.conv2d(torch.tensor(wl.x)[None], torch.tensor(wl.W), padding=1)[0].numpy()
+                   + wl.bias[:, None, None])
+            img = Ly.unpack(lin, H.he_decrypt(g.h, oc, N)[None])
+            assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
         assert np.array_equal(outs[0], outs[1])
-        ref = (torch.nn.functional.conv2d(torch.tensor(wl.x)[None], torch.tensor(wl.W), padding=1)[0].numpy()
-               + wl.bias[:, None, None])
-        img = Ly.unpack(lin, H.he_decrypt(g.h, oc, N)[None])
-        assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
         cheb = Ly.cheb_nodes_coeffs(Ly.gelu, workloads.GELU_DEGREE, -8, 8)
         H.he_poly_eval(g.h, oc, cheb, C20.scale)
         assert H.he_ct_level(oc) == level - 1 - 5

@@ -160,3 +160,36 @@ def test_poly_gelu_he_matches_same_polynomial():
     assert out.level == 2 and out.scale == 2.0 ** 40
     ref = Ly.cheb_eval(c, 8 * z, -8, 8)
     assert np.abs(ctx.decrypt(out) - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+
+
+def test_toy_conv_raised_basis_decrypts_to_fp64_conv(toy):
+    # one ModDown per output shard: different bits from conv_he, same decryption
+    wl = workloads.toy_conv(0)
+    lin = Ly.image_layout(4, 32, toy.N)
+    plan = Ly.conv_plan(lin, wl.W, np.linspace(-1, 1, 4), wl.pad)
+    slots = Ly.pack(lin, wl.x)
+    cts = [toy.encrypt(slots[u], 3, nonce=u) for u in range(lin.n_shards)]
+    a = Ly.conv_he(toy, plan, cts)
+    b = Ly.conv_he_raised(toy, plan, cts)
+    assert not np.array_equal(a[0].c, b[0].c)
+    ref = _conv_ref(wl.x, wl.W, np.linspace(-1, 1, 4), wl.pad)
+    for out in (a, b):
+        img = Ly.unpack(plan.lout, np.stack([toy.decrypt(c) for c in out]))
+        assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+
+
+def test_raised_basis_conv_on_image_shards():
+    ctx = Context(Params(log_n=11, n_q=4, n_p=2, dnum=2, q0_bits=50, q_bits=40, p_bits=50,
+                         scale=2.0 ** 40, seed=4))
+    rng = np.random.default_rng(8)
+    x = rng.uniform(0, 1, (8, 16, 16))
+    W = rng.uniform(-1, 1, (4, 8, 3, 3))
+    lin = Ly.image_layout(8, 16, ctx.N)
+    assert lin.n_shards == 2
+    plan = Ly.conv_plan(lin, W, None, 1)
+    slots = Ly.pack(lin, x)
+    cts = [ctx.encrypt(slots[u], 3, nonce=u) for u in range(2)]
+    out = Ly.conv_he_raised(ctx, plan, cts)
+    img = Ly.unpack(plan.lout, np.stack([ctx.decrypt(c) for c in out]))
+    ref = _conv_ref(x, W, None, 1)
+    assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
