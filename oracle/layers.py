@@ -282,50 +282,47 @@ def conv_he(ctx, plan: ConvPlan, cts, pts=None, bias_pts=None):
     return out
 
 
-def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None):
-    """hconv2d with one ModDown per output shard ("double hoisting").
+def raised_stage(ctx, srcs, terms_by_v):
+    """Weighted hoisted rotations with one ModDown per output ("double hoisting").
 
-    Same plan and plaintexts as conv_he.  A hoisted rotation is
-    R_a = (phi_a(c0) + ModDown(u0_a), ModDown(u1_a)), u_a = sum_j phi_a(D_j) * ksk_a[j] over
-    Q u P.  Here the weighted sum moves inside the ModDown: for output shard v
-        out_v = Rescale( (B0, B1) + ModDown( sum_{(u,a), a != 0} pt_{u,v,a} * u_a ) )
-    with B0 = sum_{(u,a)} pt_{u,v,a} * phi_a(c0_u) and B1 = sum_{(u,0)} pt_{u,v,0} * c1_u, the
-    plaintext reduced modulo every prime of Q u P.  It decrypts like conv_he (one ModDown
-    rounding per output instead of one per rotation) but the bits differ.
+    out_v = (B0, B1) + ModDown( sum_{(s, a), a != 0} pt * u_{s,a} ),  where for source s
+    rotated by a the hoisted inner product is u_{s,a} = sum_j phi_a(D_j(s)) * ksk_a[j] over
+    Q u P, B0 = sum_{(s,a)} pt * phi_a(c0_s) and B1 = sum_{(s,0)} pt * c1_s.  pt is an integer
+    plaintext reduced modulo every prime of Q u P, or None for the integer 1.  All sources share
+    one level; outputs are returned unrescaled, scale = source scale (times the plaintext scale,
+    applied by the caller).
     """
     from .ckks import Ciphertext
-    level, scale = cts[0].level, cts[0].scale
-    assert all(c.level == level and c.scale == scale for c in cts)
-    if pts is None:
-        pts = conv_plaintexts(plan, ctx.n, float(ctx.q[level]))
+    level = srcs[0].level
+    assert all(c.level == level for c in srcs)
     mq, pq = ctx.mods(level), ctx.psis(level)
     me, pe = ctx.mods(level, True), ctx.psis(level, True)
     nq, ne, n = level + 1, len(me), ctx.n
-    D = {}
-    for u, ct in enumerate(cts):
-        if any(a != 0 for a in plan.amounts(u)):
-            D[u] = ctx.hoist(ct)
-    c_eval = [[ctx.ntt(ct.c[k], mq, pq).reshape(nq, n) for k in range(2)] for ct in cts]
-    out = []
-    for v in range(plan.lout.n_shards):
+    one = np.zeros(n, dtype=np.int64)
+    one[0] = 1
+    rotated = {s for terms in terms_by_v.values() for (s, a, _) in terms if a % ctx.N != 0}
+    D = {s: ctx.hoist(srcs[s]) for s in sorted(rotated)}
+    c_eval = [[ctx.ntt(ct.c[k], mq, pq).reshape(nq, n) for k in range(2)] for ct in srcs]
+    out = {}
+    for v in sorted(terms_by_v):
         acc = [np.zeros((ne, n), dtype=np.uint64) for _ in range(2)]
         base = [np.zeros((nq, n), dtype=np.uint64) for _ in range(2)]
-        for (u, a) in sorted(plan.terms[v].keys()):
-            pt = pts[(u, v, a)]
+        for (s, a, pt) in terms_by_v[v]:
+            pt = one if pt is None else pt
             Pq = ctx.ntt(ctx.reduce_int(pt, mq), mq, pq).reshape(nq, n)
-            if a == 0:
+            if a % ctx.N == 0:
                 for k in range(2):
-                    ctx.lib.orc_mac(base[k], Pq, c_eval[u][k], nq, n, mq)
+                    ctx.lib.orc_mac(base[k], Pq, c_eval[s][k], nq, n, mq)
                 continue
             g = ctx.galois(a)
             ctx.gen_rotation_key(a)
-            c0g = ctx.automorph_eval(c_eval[u][0], g).reshape(nq, n)
+            c0g = ctx.automorph_eval(c_eval[s][0], g).reshape(nq, n)
             ctx.lib.orc_mac(base[0], Pq, c0g, nq, n, mq)
             Pe = ctx.ntt(ctx.reduce_int(pt, me), me, pe).reshape(ne, n)
             keys = ctx._key_limbs(g, level)
             for k in range(2):
                 uk = np.zeros((ne, n), dtype=np.uint64)
-                for j, Dj in enumerate(D[u]):
+                for j, Dj in enumerate(D[s]):
                     ctx.lib.orc_mac(uk, ctx.automorph_eval(Dj, g).reshape(ne, n),
                                     np.ascontiguousarray(keys[j][k]), ne, n, me)
                 ctx.lib.orc_mac(acc[k], Pe, uk, ne, n, me)
@@ -333,7 +330,23 @@ def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None):
         for k in range(2):
             y = ctx.moddown(ctx.intt(acc[k], me, pe).reshape(ne, n), level)
             c.append(ctx.add(ctx.intt(base[k], mq, pq).reshape(nq, n), y, mq))
-        ct = ctx.rescale(Ciphertext(np.stack(c), level, scale * ctx.q[level]))
+        out[v] = Ciphertext(np.stack(c), level, srcs[0].scale)
+    return [out[v] for v in sorted(out)]
+
+
+def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None):
+    """hconv2d with one ModDown per output shard (raised_stage), then rescale and bias.
+    Same plan and plaintexts as conv_he; decrypts like it, different bits."""
+    level, scale = cts[0].level, cts[0].scale
+    assert all(c.level == level and c.scale == scale for c in cts)
+    if pts is None:
+        pts = conv_plaintexts(plan, ctx.n, float(ctx.q[level]))
+    terms = {v: [(u, a, pts[(u, v, a)]) for (u, a) in sorted(plan.terms[v].keys())]
+             for v in range(plan.lout.n_shards)}
+    out = []
+    for v, acc in enumerate(raised_stage(ctx, cts, terms)):
+        acc.scale = scale * ctx.q[level]
+        ct = ctx.rescale(acc)
         bpt = bias_pts[v] if bias_pts is not None else encode(plan.bias[v], ctx.n, ct.scale)
         ct.c[0] = ctx.add(ct.c[0], ctx.reduce_int(bpt, ctx.mods(ct.level)), ctx.mods(ct.level))
         out.append(ct)
@@ -453,6 +466,37 @@ def _masked_stage(ctx, cts, terms, level):
         pts = [encode(mk[u], ctx.n, float(ctx.q[level])) for _, mk in terms]
         out.append(mac_rescale(ctx, R, keys, pts, level, ct.scale))
     return out
+
+
+def pool_he_raised(ctx, plan: PoolPlan, cts, h_pts=None, v_pts=None):
+    """havgpool with every stage (ones-sum, H, V, consolidate, duplicate) as a raised_stage:
+    one ModDown per output shard per stage.  h_pts/v_pts: optional integer masks
+    [amount][shard] (else encoded here at q_l and q_{l-1})."""
+    level = cts[0].level
+    ns = plan.lin.n_shards
+    if h_pts is None:
+        h_pts = [[encode(mk[u], ctx.n, float(ctx.q[level])) for u in range(ns)] for _, mk in plan.h_terms]
+    if v_pts is None:
+        v_pts = [[encode(mk[u], ctx.n, float(ctx.q[level - 1])) for u in range(ns)] for _, mk in plan.v_terms]
+    W = cts
+    if plan.pre:
+        W = raised_stage(ctx, cts, {u: [(u, a, None) for a in plan.pre] for u in range(ns)})
+    Y = raised_stage(ctx, W, {u: [(u, a, h_pts[i][u]) for i, (a, _) in enumerate(plan.h_terms)]
+                              for u in range(ns)})
+    Y2 = []
+    for y in Y:
+        y.scale = W[0].scale * ctx.q[level]
+        Y2.append(ctx.rescale(y))
+    Z = raised_stage(ctx, Y2, {u: [(u, a, v_pts[i][u]) for i, (a, _) in enumerate(plan.v_terms)]
+                               for u in range(ns)})
+    Z2 = []
+    for z in Z:
+        z.scale = Y2[0].scale * ctx.q[level - 1]
+        Z2.append(ctx.rescale(z))
+    S = raised_stage(ctx, Z2, {g: [(s, a, None) for s, a in grp] for g, grp in enumerate(plan.groups)})
+    if len(plan.dup) > 1:
+        S = raised_stage(ctx, [S[0]], {0: [(0, a, None) for a in plan.dup]})
+    return S
 
 
 def pool_he(ctx, plan: PoolPlan, cts):

@@ -208,20 +208,28 @@ int k_add_const_v(const he_ctx *ctx, he_ct *ct, const u64 *res, cudaStream_t s);
 int k_mul_pointwise(const he_ctx *ctx, const u64 *a, const u64 *b, u64 *out, int nlimbs,
                     cudaStream_t s);
 // Fused inner product + MAC in the raised basis (one ModDown per output afterwards).
-#define HE_FUSED_MAXV 4
-struct fused_item {
-    const u64 *D;           // raised digits of the source [beta][l+1+K][n]; null when amount 0
-    const u64 *key;         // key [dnum][2][L+1+K][n]; null when amount 0
-    const u64 *src;         // source ciphertext data (c0, c1 at src + src_ps), level l
-    size_t src_ps;
-    u64 g;                  // Galois element (1 when amount 0)
-    int beta;
-    const u64 *pt[HE_FUSED_MAXV];   // per output of the group: [l+1+K][n] Montgomery, or null
+// Amount-major form: every rotation key is read once and applied to every source shard that
+// uses that amount.  A plaintext pointer equal to HE_PT_ONE stands for the integer 1.
+#define HE_PT_ONE ((const u64 *)1)
+struct fsrc {
+    const u64 *D;           // raised digits [beta][l+1+K][n] (null when the source is never rotated)
+    const u64 *src;         // ciphertext data (c0, c1 at src + ps), level l
+    size_t ps;
 };
-// acc [V][2][l+1+K][n] = sum pt * u_item (normal form); base [V][2][l+1][n] = sum pt * phi(c0)
-// (and pt * c1 for amount-0 items)
-int k_ipmac(const he_ctx *ctx, const fused_item *items_dev, int n_items, int V, int level,
-            u64 *acc, u64 *base, cudaStream_t s);
+struct famt {
+    const u64 *key;         // null for amount 0
+    u64 g;
+    int e0, e1;             // entries [e0, e1)
+};
+struct fent {
+    const u64 *D;           // the source's raised digits, or null
+    const u64 *src;         // the source's ciphertext data
+    size_t ps;
+    const u64 *pt[2];       // per output of the group (V <= 2): plaintext, HE_PT_ONE or null
+    int s;                  // source index (host bookkeeping)
+};
+int k_ipmac2(const he_ctx *ctx, const fsrc *srcs, const famt *amts, int n_amt, const fent *ents, int V,
+             int level, u64 *acc, u64 *base, double bytes, double mulmods, cudaStream_t s);
 int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u64 *res, int n,
               const u64 *cst, int level, u64 *out, size_t out_ps, cudaStream_t s);
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s);

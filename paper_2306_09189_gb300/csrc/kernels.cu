@@ -642,27 +642,26 @@ __global__ void __launch_bounds__(TB) mac_kernel(KP kp, const mac_term *terms, m
 }
 
 // ------------------------------------------------------------------------------ fused IP + MAC
-// For every coefficient k of limb t of Q_l u P and every item (source shard u, amount a):
-//   u_c = REDC(sum_j D_j[t][phi_a(k)] * ksk_a[j][c][t][k])          (inner product, normal form)
-//   acc_c[v] += pt_v[t][k] * u_c                                       (Montgomery pt -> one REDC)
-// and on the Q limbs base_0[v] += pt_v * c0[phi_a(k)] (+ base_1[v] += pt_v * c1 for a = 0).
-// Rotated ciphertexts are never written: key, plaintext and the gathered digits feed
-// 128-bit accumulators directly.
 // Two coefficients per thread: for Galois elements g = 1 mod 4 the NTT-domain automorphism
 // maps the aligned pair (k, k^1) onto an aligned pair (phi(k), phi(k)^1), so every gather is a
 // full 16-byte load and every key / plaintext / output access a 16-byte vector access.
 __device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *(const ulonglong2 *)p; }
 __device__ __forceinline__ void st2(u64 *p, u64 a, u64 b) { *(ulonglong2 *)p = make_ulonglong2(a, b); }
 
-template <int V>
-__global__ void __launch_bounds__(TB) ipmac_kernel(KP kp, const fused_item *items, int n_items,
-                                                   int level, u64 *acc, u64 *base) {
+// Amount-major fused inner product + MAC.  For each amount the thread loads its key words
+// once (two coefficients, beta digits, both polynomials) and applies them to every source
+// shard that uses the amount; V <= 2 outputs per group.
+template <int V, int B>
+__global__ void __launch_bounds__(TB) ipmac2_kernel(KP kp, const fsrc *srcs, const famt *amts, int n_amt,
+                                                    const fent *ents, int level, int beta,
+                                                    u64 *acc, u64 *base) {
     const int k = 2 * (blockIdx.x * TB + threadIdx.x);
     const int t = blockIdx.y;
     const int nq = level + 1;
     const int ext = nq + kp.K;
     const int kl = t < nq ? t : kp.L + 1 + (t - nq);
-    const u64 q = kp.q[kl], qi = kp.qinv[kl];
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 one = to_mont(1, q, qi, r2);
     const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
     const size_t off = (size_t)t * kp.n + k;
     u128 a0[V][2], a1[V][2], b0[V][2], b1[V][2];
@@ -670,46 +669,63 @@ __global__ void __launch_bounds__(TB) ipmac_kernel(KP kp, const fused_item *item
     for (int v = 0; v < V; v++)
 #pragma unroll
         for (int e = 0; e < 2; e++) a0[v][e] = a1[v][e] = b0[v][e] = b1[v][e] = 0;
-    for (int i = 0; i < n_items; i++) {
-        const fused_item &it = items[i];
-        const int ks = it.g == 1 ? k : autom_index(k, it.g, kp.logn);
+    for (int i = 0; i < n_amt; i++) {
+        const famt A = amts[i];
+        const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
         const int sw = ks & 1, kb = ks & ~1;
-        ulonglong2 p[V];
+        ulonglong2 kk0[B], kk1[B];
+        if (A.key) {
 #pragma unroll
-        for (int v = 0; v < V; v++) p[v] = it.pt[v] ? ld2(it.pt[v] + off) : make_ulonglong2(0, 0);
-        if (it.key) {
-            u128 s0[2] = {0, 0}, s1[2] = {0, 0};
-            for (int j = 0; j < it.beta; j++) {
-                const ulonglong2 d = ld2(it.D + ((size_t)j * ext + t) * kp.n + kb);
-                const u64 d0 = sw ? d.y : d.x, d1 = sw ? d.x : d.y;
-                const u64 *kp0 = it.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
-                const ulonglong2 k0 = ld2(kp0), k1 = ld2(kp0 + kstride);
-                s0[0] += (u128)d0 * k0.x;
-                s0[1] += (u128)d1 * k0.y;
-                s1[0] += (u128)d0 * k1.x;
-                s1[1] += (u128)d1 * k1.y;
-            }
-            const u64 u00 = redc(s0[0], q, qi), u01 = redc(s0[1], q, qi);
-            const u64 u10 = redc(s1[0], q, qi), u11 = redc(s1[1], q, qi);
-#pragma unroll
-            for (int v = 0; v < V; v++) {
-                a0[v][0] += (u128)p[v].x * u00;
-                a0[v][1] += (u128)p[v].y * u01;
-                a1[v][0] += (u128)p[v].x * u10;
-                a1[v][1] += (u128)p[v].y * u11;
-            }
+            for (int j = 0; j < B; j++)
+                if (j < beta) {
+                    const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+                    kk0[j] = ld2(kp0);
+                    kk1[j] = ld2(kp0 + kstride);
+                }
         }
-        if (t < nq) {
-            const ulonglong2 cc = ld2(it.src + (size_t)t * kp.n + kb);
-            const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
-            ulonglong2 c1 = make_ulonglong2(0, 0);
-            if (!it.key) c1 = ld2(it.src + it.src_ps + off);
+        for (int e = A.e0; e < A.e1; e++) {
+            const fent E = ents[e];
+            const fsrc S{E.D, E.src, E.ps};
+            ulonglong2 p[V];
 #pragma unroll
             for (int v = 0; v < V; v++) {
-                b0[v][0] += (u128)p[v].x * c00;
-                b0[v][1] += (u128)p[v].y * c01;
-                b1[v][0] += (u128)p[v].x * c1.x;
-                b1[v][1] += (u128)p[v].y * c1.y;
+                const u64 *pp = E.pt[v];
+                p[v] = pp == HE_PT_ONE ? make_ulonglong2(one, one) : (pp ? ld2(pp + off) : make_ulonglong2(0, 0));
+            }
+            if (A.key) {
+                u128 s0[2] = {0, 0}, s1[2] = {0, 0};
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        const ulonglong2 d = ld2(S.D + ((size_t)j * ext + t) * kp.n + kb);
+                        const u64 d0 = sw ? d.y : d.x, d1 = sw ? d.x : d.y;
+                        s0[0] += (u128)d0 * kk0[j].x;
+                        s0[1] += (u128)d1 * kk0[j].y;
+                        s1[0] += (u128)d0 * kk1[j].x;
+                        s1[1] += (u128)d1 * kk1[j].y;
+                    }
+                const u64 u00 = redc(s0[0], q, qi), u01 = redc(s0[1], q, qi);
+                const u64 u10 = redc(s1[0], q, qi), u11 = redc(s1[1], q, qi);
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    a0[v][0] += (u128)p[v].x * u00;
+                    a0[v][1] += (u128)p[v].y * u01;
+                    a1[v][0] += (u128)p[v].x * u10;
+                    a1[v][1] += (u128)p[v].y * u11;
+                }
+            }
+            if (t < nq) {
+                const ulonglong2 cc = ld2(S.src + (size_t)t * kp.n + kb);
+                const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
+                ulonglong2 c1 = make_ulonglong2(0, 0);
+                if (!A.key) c1 = ld2(S.src + S.ps + off);
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    b0[v][0] += (u128)p[v].x * c00;
+                    b0[v][1] += (u128)p[v].y * c01;
+                    b1[v][0] += (u128)p[v].x * c1.x;
+                    b1[v][1] += (u128)p[v].y * c1.y;
+                }
             }
         }
     }
@@ -1105,22 +1121,18 @@ int k_tensor(const he_ctx *ctx, const he_ct *a, const he_ct *b, u64 *d, cudaStre
     return HE_OK;
 }
 
-int k_ipmac(const he_ctx *ctx, const fused_item *items_dev, int n_items, int V, int level,
-            u64 *acc, u64 *base, cudaStream_t s) {
+int k_ipmac2(const he_ctx *ctx, const fsrc *srcs, const famt *amts, int n_amt, const fent *ents, int V,
+             int level, u64 *acc, u64 *base, double bytes, double mulmods, cudaStream_t s) {
     const int ext = level + 1 + ctx->K;
-    const double beta = (level + ctx->alpha) / ctx->alpha;
-    // algorithmic bytes: per rotation the key (2 beta limbs) and V plaintexts over Q u P, the
-    // digits once, the outputs once
-    TraceScope tr("ipmac", s, (double)ext * ctx->n * 8 * ((double)n_items * (2 * beta + V) + beta + 2.0 * V) +
-                                  (double)(level + 1) * ctx->n * 8 * (2.0 + 2.0 * V),
-                  (double)n_items * ext * ctx->n * (2 * beta + 2.0 * V));
+    const int beta = (level + ctx->alpha) / ctx->alpha;
+    if (beta > 8) { he_set_error("fused key switching: at most 8 digits"); return HE_EINVAL; }
     dim3 g(ctx->n / (2 * TB), ext);
-    switch (V) {
-        case 1: ipmac_kernel<1><<<g, TB, 0, s>>>(ctx->kp, items_dev, n_items, level, acc, base); break;
-        case 2: ipmac_kernel<2><<<g, TB, 0, s>>>(ctx->kp, items_dev, n_items, level, acc, base); break;
-        case 4: ipmac_kernel<4><<<g, TB, 0, s>>>(ctx->kp, items_dev, n_items, level, acc, base); break;
-        default: he_set_error("k_ipmac: V must be 1, 2 or 4"); return HE_EINVAL;
-    }
+    TraceScope tr("ipmac", s, bytes, mulmods);
+#define IPM2(VV, BB) ipmac2_kernel<VV, BB><<<g, TB, 0, s>>>(ctx->kp, srcs, amts, n_amt, ents, level, beta, acc, base)
+    if (V == 1) { if (beta <= 4) IPM2(1, 4); else IPM2(1, 8); }
+    else if (V == 2) { if (beta <= 4) IPM2(2, 4); else IPM2(2, 8); }
+    else { he_set_error("k_ipmac2: V must be 1 or 2"); return HE_EINVAL; }
+#undef IPM2
     LAUNCH_CHECK();
     return HE_OK;
 }

@@ -438,6 +438,148 @@ struct RotSet {
     }
 };
 
+// ================================================================================ fused stages
+// One stage of weighted hoisted rotations: out_v = sum_{(s, a)} pt_{v,s,a} (.) rot_a(src_s),
+// evaluated in the raised basis: every rotation's inner product is accumulated with its
+// plaintext over Q u P (keys read once per amount and output group) and each output takes one
+// ModDown.  Outputs are left unrescaled at the stage level.
+struct FusedStage {
+    he_ctx *c = nullptr;
+    int level = 0;
+    struct Src { u64 *d; size_t ps; bool rotated; };
+    std::vector<Src> srcs;
+    struct Term { int v, s, a; const u64 *pt; };
+    std::vector<Term> terms;
+    std::vector<std::pair<u64 *, size_t>> outs;      // output data and poly stride
+    struct Group {
+        int V = 1, n_amt = 0;
+        std::vector<int> outs;
+        fsrc *d_src = nullptr;
+        famt *d_amt = nullptr;
+        fent *d_ent = nullptr;
+        md_item *d_md = nullptr;
+        double bytes = 0, mulmods = 0;
+    };
+    std::vector<Group> groups;
+    std::vector<int> hslot;                           // source -> slot in D_all (-1: not rotated)
+    u64 *D_all = nullptr, *facc = nullptr, *fbase = nullptr, *fconv = nullptr;
+    bool ready = false;
+
+    ~FusedStage() {
+        for (auto &g : groups) { cudaFree(g.d_src); cudaFree(g.d_amt); cudaFree(g.d_ent); cudaFree(g.d_md); }
+        cudaFree(D_all); cudaFree(facc); cudaFree(fbase); cudaFree(fconv);
+    }
+    int add_src(u64 *d, size_t ps) { srcs.push_back({d, ps, false}); return (int)srcs.size() - 1; }
+    int add_out(u64 *d, size_t ps) { outs.push_back({d, ps}); return (int)outs.size() - 1; }
+    void add_term(int v, int s, int a, const u64 *pt) { terms.push_back({v, s, ((a % c->N) + c->N) % c->N, pt}); }
+
+    int build() {
+        if (ready) return HE_OK;
+        const int nq = level + 1, ext = nq + c->K, beta = (level + c->alpha) / c->alpha;
+        const size_t n = c->n;
+        for (auto &t : terms)
+            if (h_galois(c, t.a) != 1) srcs[t.s].rotated = true;
+        hslot.assign(srcs.size(), -1);
+        int nh = 0;
+        for (size_t i = 0; i < srcs.size(); i++)
+            if (srcs[i].rotated) hslot[i] = nh++;
+        HE_TRY(dev_alloc(&D_all, (size_t)nh * beta * ext * n));
+        const int nout = (int)outs.size();
+        const int V = nout >= 2 ? 2 : 1;
+        HE_TRY(dev_alloc(&facc, (size_t)V * 2 * ext * n));
+        HE_TRY(dev_alloc(&fbase, (size_t)V * 2 * nq * n));
+        HE_TRY(dev_alloc(&fconv, (size_t)V * 2 * nq * n));
+        std::vector<fsrc> hs(srcs.size());
+        for (size_t i = 0; i < srcs.size(); i++)
+            hs[i] = fsrc{hslot[i] >= 0 ? D_all + (size_t)hslot[i] * beta * ext * n : nullptr, srcs[i].d, srcs[i].ps};
+        for (int v0 = 0; v0 < nout; v0 += V) {
+            Group G;
+            G.V = V;
+            for (int v = v0; v < std::min(nout, v0 + V); v++) G.outs.push_back(v);
+            // amount -> source -> per-output plaintexts
+            std::map<int, std::map<int, fent>> m;
+            for (auto &t : terms) {
+                int vi = -1;
+                for (size_t k = 0; k < G.outs.size(); k++)
+                    if (G.outs[k] == t.v) vi = (int)k;
+                if (vi < 0) continue;
+                fent &e = m[t.a][t.s];
+                e.s = t.s;
+                if (e.pt[vi]) { he_set_error("fused stage: duplicate term"); return HE_EINVAL; }
+                e.pt[vi] = t.pt;
+            }
+            std::vector<famt> ha;
+            std::vector<fent> he;
+            double bytes = 0, mm = 0;
+            for (auto &am : m) {
+                famt A;
+                A.g = h_galois(c, am.first);
+                A.key = nullptr;
+                if (A.g != 1) {
+                    const DeviceKey *k;
+                    HE_TRY(get_key(c, (int)A.g, &k));
+                    A.key = k->d;
+                    bytes += (double)2 * beta * ext * n * 8;
+                }
+                A.e0 = (int)he.size();
+                for (auto &se : am.second) {
+                    fent E = se.second;
+                    E.D = hs[E.s].D;
+                    E.src = hs[E.s].src;
+                    E.ps = hs[E.s].ps;
+                    he.push_back(E);
+                    for (int vi = 0; vi < V; vi++)
+                        if (se.second.pt[vi] && se.second.pt[vi] != HE_PT_ONE) bytes += (double)(A.key ? ext : nq) * n * 8;
+                    mm += (double)(A.key ? ext : nq) * n * (A.key ? 2 * beta + 2 * V : 2 * V);
+                }
+                A.e1 = (int)he.size();
+                ha.push_back(A);
+            }
+            bytes += (double)nh * beta * ext * n * 8 + (double)srcs.size() * 2 * nq * n * 8 +
+                     (double)G.outs.size() * 2 * (ext + nq) * n * 8;
+            G.bytes = bytes;
+            G.mulmods = mm;
+            G.n_amt = (int)ha.size();
+            HE_TRY(dev_alloc(&G.d_src, hs.size()));
+            HE_TRY(dev_alloc(&G.d_amt, std::max<size_t>(1, ha.size())));
+            HE_TRY(dev_alloc(&G.d_ent, std::max<size_t>(1, he.size())));
+            HE_CHECK_CUDA(cudaMemcpy(G.d_src, hs.data(), hs.size() * sizeof(fsrc), cudaMemcpyHostToDevice));
+            if (!ha.empty()) HE_CHECK_CUDA(cudaMemcpy(G.d_amt, ha.data(), ha.size() * sizeof(famt), cudaMemcpyHostToDevice));
+            if (!he.empty()) HE_CHECK_CUDA(cudaMemcpy(G.d_ent, he.data(), he.size() * sizeof(fent), cudaMemcpyHostToDevice));
+            std::vector<md_item> md;
+            for (size_t vi = 0; vi < G.outs.size(); vi++)
+                md.push_back(md_item{facc + vi * 2 * ext * n, fconv + vi * 2 * nq * n, fbase + vi * 2 * nq * n,
+                                     (size_t)nq * n, 2, 1, outs[G.outs[vi]].first, outs[G.outs[vi]].second});
+            HE_TRY(dev_alloc(&G.d_md, md.size()));
+            HE_CHECK_CUDA(cudaMemcpy(G.d_md, md.data(), md.size() * sizeof(md_item), cudaMemcpyHostToDevice));
+            groups.push_back(G);
+        }
+        ready = true;
+        return HE_OK;
+    }
+
+    int run(cudaStream_t s) {
+        HE_TRY(build());
+        const int nq = level + 1, ext = nq + c->K, beta = (level + c->alpha) / c->alpha;
+        for (size_t i = 0; i < srcs.size(); i++)
+            if (hslot[i] >= 0) {
+                he_ct t = view(c, srcs[i].d, srcs[i].ps, level, 1.0);
+                HE_TRY(hoist_modup(c, &t, D_all + (size_t)hslot[i] * beta * ext * c->n, s));
+            }
+        for (auto &G : groups) {
+            const int nv = (int)G.outs.size();
+            HE_TRY(k_ipmac2(c, G.d_src, G.d_amt, G.n_amt, G.d_ent, G.V, level, facc, fbase, G.bytes, G.mulmods, s));
+            ntt_job jp{facc, (size_t)ext * c->n, nq, c->K, nq, 0, 2 * nv, 0};
+            HE_TRY(k_ntt(c, jp, true, s));
+            HE_TRY(k_moddown_fbc(c, facc, fconv, level, 2 * nv, s));
+            ntt_job jc{fconv, (size_t)nq * c->n, 0, nq, nq, 0, 2 * nv, 0};
+            HE_TRY(k_ntt(c, jc, false, s));
+            HE_TRY(k_moddown_combine(c, G.d_md, nv, level, s));
+        }
+        return HE_OK;
+    }
+};
+
 // ================================================================================ pooling
 struct he_pool {
     he_ctx *c = nullptr;
@@ -449,10 +591,12 @@ struct he_pool {
     u64 *X = nullptr, *Wb = nullptr, *Yb = nullptr, *Zb = nullptr, *Sb = nullptr;
     u64 *rotS = nullptr, *rotH = nullptr, *rotV = nullptr, *rotC = nullptr, *rotD = nullptr;
     RotSet rs_S, rs_H, rs_V, rs_C, rs_D;
-    u64 *hpts = nullptr, *vpts = nullptr;
+    u64 *hpts = nullptr, *vpts = nullptr;     // masks over Q_l u P (stride pe0 / pe1)
+    size_t pe0 = 0, pe1 = 0;
     std::vector<int> h_idx, v_idx;
     int n_hpt = 0, n_vpt = 0;
     mac_term *d_hterms = nullptr, *d_vterms = nullptr;
+    FusedStage f_S, f_H, f_V, f_C, f_D;     // HE_FUSED stages (built on first use)
     ~he_pool() {
         cudaFree(X); cudaFree(Wb); cudaFree(Yb); cudaFree(Zb); cudaFree(Sb);
         cudaFree(rotS); cudaFree(rotH); cudaFree(rotV); cudaFree(rotC); cudaFree(rotD);
@@ -462,6 +606,7 @@ struct he_pool {
 
 static int dedupe_upload(he_ctx *c, const std::vector<std::vector<std::vector<double>>> &mk, int ns,
                          int lv, u64 **dst, std::vector<int> &idx, int &count) {
+    // stored over Q_lv u P so the fused stages can use them; the plain MAC reads the Q limbs
     std::vector<const double *> uniq;
     std::unordered_map<uint64_t, std::vector<int>> seen;
     idx.assign(mk.size() * ns, -1);
@@ -485,8 +630,8 @@ static int dedupe_upload(he_ctx *c, const std::vector<std::vector<std::vector<do
             idx[a * ns + u] = found;
         }
     count = (int)uniq.size();
-    HE_TRY(dev_alloc(dst, (size_t)count * (lv + 1) * c->n));
-    return upload_plaintexts(c, uniq, uniq.size(), (double)c->primes[lv], lv, *dst, nullptr);
+    HE_TRY(dev_alloc(dst, (size_t)count * (lv + 1 + c->K) * c->n));
+    return upload_plaintexts(c, uniq, uniq.size(), (double)c->primes[lv], lv, *dst, nullptr, true);
 }
 
 static int pool_build(he_ctx *c, const Lay &lin, int level, bool select, he_pool **out) {
@@ -502,6 +647,8 @@ static int pool_build(he_ctx *c, const Lay &lin, int level, bool select, he_pool
     p->pw0 = (size_t)(level + 1) * c->n;
     p->pw1 = (size_t)level * c->n;
     p->pw2 = (size_t)(level - 1) * c->n;
+    p->pe0 = (size_t)(level + 1 + c->K) * c->n;
+    p->pe1 = (size_t)(level + c->K) * c->n;
     const size_t pw0 = p->pw0, pw1 = p->pw1, pw2 = p->pw2;
     const size_t nS = P.pre.size(), nH = P.h_amt.size(), nV = P.v_amt.size(), nG = P.groups.size();
     HE_TRY(dev_alloc(&p->X, (size_t)ns * 2 * pw0));
@@ -541,9 +688,9 @@ static int pool_build(he_ctx *c, const Lay &lin, int level, bool select, he_pool
     std::vector<mac_term> th, tv;
     for (int u = 0; u < ns; u++) {
         for (size_t a = 0; a < nH; a++)
-            th.push_back({p->hpts + (size_t)p->h_idx[a * ns + u] * pw0, p->rotH + ((size_t)u * nH + a) * 2 * pw0, pw0});
+            th.push_back({p->hpts + (size_t)p->h_idx[a * ns + u] * p->pe0, p->rotH + ((size_t)u * nH + a) * 2 * pw0, pw0});
         for (size_t a = 0; a < nV; a++)
-            tv.push_back({p->vpts + (size_t)p->v_idx[a * ns + u] * pw1, p->rotV + ((size_t)u * nV + a) * 2 * pw1, pw1});
+            tv.push_back({p->vpts + (size_t)p->v_idx[a * ns + u] * p->pe1, p->rotV + ((size_t)u * nV + a) * 2 * pw1, pw1});
     }
     HE_TRY(dev_alloc(&p->d_hterms, th.size()));
     HE_TRY(dev_alloc(&p->d_vterms, tv.size()));
@@ -555,7 +702,10 @@ static int pool_build(he_ctx *c, const Lay &lin, int level, bool select, he_pool
     return HE_OK;
 }
 
+static int pool_run_fused(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out, cudaStream_t s);
+
 static int pool_run(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out, int mode, cudaStream_t s) {
+    if (mode == HE_FUSED) return pool_run_fused(c, p, in, out, s);
     const int ns = p->ns, lv = p->level;
     const size_t pw0 = p->pw0, pw1 = p->pw1, pw2 = p->pw2;
     const PoolPlanH &P = p->P;
@@ -621,7 +771,94 @@ static int pool_run(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out, int mo
     return HE_OK;
 }
 
+static int pool_prepare_fused(he_pool *p) {
+    if (p->f_H.c) return HE_OK;
+    he_ctx *c = p->c;
+    const int ns = p->ns, lv = p->level;
+    const PoolPlanH &P = p->P;
+    const size_t pw0 = p->pw0, pw1 = p->pw1, pw2 = p->pw2;
+    const size_t nH = P.h_amt.size(), nV = P.v_amt.size();
+    for (FusedStage *f : {&p->f_S, &p->f_H, &p->f_V, &p->f_C, &p->f_D}) f->c = c;
+    p->f_S.level = p->f_H.level = lv;
+    p->f_V.level = lv - 1;
+    p->f_C.level = p->f_D.level = lv - 2;
+    u64 *hsrc = P.pre.empty() ? p->X : p->Wb;
+    for (int u = 0; u < ns; u++) {
+        p->f_S.add_src(p->X + (size_t)u * 2 * pw0, pw0);
+        p->f_S.add_out(p->Wb + (size_t)u * 2 * pw0, pw0);
+        for (int a : P.pre) p->f_S.add_term(u, u, a, HE_PT_ONE);
+        p->f_H.add_src(hsrc + (size_t)u * 2 * pw0, pw0);
+        p->f_H.add_out(p->Yb + (size_t)u * 2 * pw0, pw0);
+        for (size_t a = 0; a < nH; a++)
+            p->f_H.add_term(u, u, P.h_amt[a], p->hpts + (size_t)p->h_idx[a * ns + u] * p->pe0);
+        p->f_V.add_src(p->Yb + (size_t)u * 2 * pw0, pw0);
+        p->f_V.add_out(p->Zb + (size_t)u * 2 * pw1, pw1);
+        for (size_t a = 0; a < nV; a++)
+            p->f_V.add_term(u, u, P.v_amt[a], p->vpts + (size_t)p->v_idx[a * ns + u] * p->pe1);
+        p->f_C.add_src(p->Zb + (size_t)u * 2 * pw1, pw1);
+    }
+    for (size_t g = 0; g < P.groups.size(); g++) {
+        p->f_C.add_out(p->Sb + g * 2 * pw2, pw2);
+        for (auto &e : P.groups[g]) p->f_C.add_term((int)g, e.first, e.second, HE_PT_ONE);
+    }
+    if (P.dup.size() > 1) {
+        p->f_D.add_src(p->Sb, pw2);
+        p->f_D.add_out(p->rotD, pw2);
+        for (int a : P.dup) p->f_D.add_term(0, 0, a, HE_PT_ONE);
+        HE_TRY(p->f_D.build());
+    }
+    if (!P.pre.empty()) HE_TRY(p->f_S.build());
+    HE_TRY(p->f_H.build());
+    HE_TRY(p->f_V.build());
+    return p->f_C.build();
+}
+
+static int pool_run_fused(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out, cudaStream_t s) {
+    const int ns = p->ns, lv = p->level;
+    const size_t pw0 = p->pw0, pw1 = p->pw1, pw2 = p->pw2;
+    const PoolPlanH &P = p->P;
+    const double scale = in[0]->scale;
+    for (int u = 0; u < ns; u++) {
+        if (!in[u] || in[u]->ctx != c || in[u]->level != lv || in[u]->scale != scale) {
+            he_set_error("pool input %d: level or scale mismatch", u);
+            return HE_ELEVEL;
+        }
+        HE_TRY(k_copy_limbs(p->X + (size_t)u * 2 * pw0, pw0, in[u]->d, in[u]->pstride, pw0, 2, s));
+    }
+    if (!P.pre.empty()) HE_TRY(p->f_S.run(s));
+    HE_TRY(p->f_H.run(s));
+    double sH = scale;
+    for (int u = 0; u < ns; u++) {
+        he_ct t = view(c, p->Yb + (size_t)u * 2 * pw0, pw0, lv, scale * (double)c->primes[lv]);
+        HE_TRY(he_rescale(c, &t, s));
+        sH = t.scale;
+    }
+    HE_TRY(p->f_V.run(s));
+    double sV = sH;
+    for (int u = 0; u < ns; u++) {
+        he_ct t = view(c, p->Zb + (size_t)u * 2 * pw1, pw1, lv - 1, sH * (double)c->primes[lv - 1]);
+        HE_TRY(he_rescale(c, &t, s));
+        sV = t.scale;
+    }
+    HE_TRY(p->f_C.run(s));
+    const int lo = lv - 2;
+    if (P.dup.size() > 1) {
+        HE_TRY(p->f_D.run(s));
+        HE_TRY(ensure_ct(c, out[0], lo));
+        HE_TRY(k_copy_limbs(out[0]->d, out[0]->pstride, p->rotD, pw2, pw2, 2, s));
+        out[0]->scale = sV;
+    } else {
+        for (size_t g = 0; g < P.groups.size(); g++) {
+            HE_TRY(ensure_ct(c, out[g], lo));
+            HE_TRY(k_copy_limbs(out[g]->d, out[g]->pstride, p->Sb + g * 2 * pw2, pw2, pw2, 2, s));
+            out[g]->scale = sV;
+        }
+    }
+    return HE_OK;
+}
+
 static int pool_prepare(he_pool *p, int mode) {
+    if (mode == HE_FUSED) return pool_prepare_fused(p);
     for (RotSet *rs : {&p->rs_S, &p->rs_H, &p->rs_V, &p->rs_C, &p->rs_D}) {
         if (mode == HE_BATCHED) HE_TRY(rs->prepare_batched());
         else HE_TRY(rs->resolve_keys());
@@ -689,7 +926,7 @@ static int import_masks(he_pool *p, const int64_t *m, size_t n_amt, const std::v
             done[k] = 1;
         }
     std::vector<const double *> none;
-    return upload_plaintexts(c, none, (size_t)count, 0.0, lv, dst, pick.data());
+    return upload_plaintexts(c, none, (size_t)count, 0.0, lv, dst, pick.data(), true);
 }
 
 extern "C" int he_pool_import_plaintexts(he_pool *p, const int64_t *h, const int64_t *v) {
@@ -700,7 +937,10 @@ extern "C" int he_pool_import_plaintexts(he_pool *p, const int64_t *h, const int
 }
 
 extern "C" int he_pool_run(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out, int mode, void *stream) {
-    if (!c || !p || !in || !out || p->c != c) { he_set_error("he_pool_run: bad argument"); return HE_EINVAL; }
+    if (!c || !p || !in || !out || p->c != c || mode < HE_PLAIN || mode > HE_FUSED) {
+        he_set_error("he_pool_run: bad argument");
+        return HE_EINVAL;
+    }
     HE_TRY(pool_prepare(p, mode));
     return pool_run(c, p, in, out, mode, (cudaStream_t)stream);
 }
@@ -722,22 +962,9 @@ struct he_conv {
     RotSet rot;
     he_pool *pool = nullptr;
     std::vector<he_ct *> mid;
-    // HE_FUSED resources (built on first use)
-    struct FusedGroup {
-        int V = 1;
-        std::vector<int> outs;                   // output shards of the group
-        fused_item *d_items = nullptr;
-        int n_items = 0;
-        md_item *d_md = nullptr;
-    };
-    std::vector<FusedGroup> fgroups;
-    u64 *D_all = nullptr, *facc = nullptr, *fbase = nullptr, *fconv = nullptr;
-    std::vector<int> hoisted;                    // sources with at least one rotation
-    int fused_V = 0;
+    FusedStage fused;                            // HE_FUSED: built on first use
     ~he_conv() {
         cudaFree(R); cudaFree(pts); cudaFree(bias_pts); cudaFree(d_terms); cudaFree(acc);
-        for (auto &g : fgroups) { cudaFree(g.d_items); cudaFree(g.d_md); }
-        cudaFree(D_all); cudaFree(facc); cudaFree(fbase); cudaFree(fconv);
         delete pool;
         for (he_ct *x : mid) he_ct_free(x);
     }
@@ -903,95 +1130,15 @@ extern "C" int he_conv_import_plaintexts(he_conv *cv, const int64_t *terms, cons
     return HE_OK;
 }
 
-// Output groups of up to V shards; each group's items are the (u, a) pairs any of its
-// outputs uses, ordered by source shard so one shard's raised digits stay hot in L2.
 static int conv_prepare_fused(he_conv *cv) {
-    if (!cv->fgroups.empty()) return HE_OK;
-    he_ctx *c = cv->c;
-    const int lv = cv->level, nq = lv + 1, ext = nq + c->K, n_out = cv->lout.ns;
-    const size_t pw = cv->pw, pe = cv->pe;
-    const int beta = (lv + c->alpha) / c->alpha;
-    int V = n_out >= 4 ? 4 : (n_out >= 2 ? 2 : 1);
-    cv->fused_V = V;
-    std::map<long long, int> term_index;          // (u*N + a)*n_out + v -> term
-    for (size_t t = 0; t < cv->tu.size(); t++)
-        term_index[((long long)cv->tu[t] * c->N + cv->ta[t]) * n_out + cv->tv[t]] = (int)t;
-    std::vector<char> rot(cv->lin.ns, 0);
-    for (size_t t = 0; t < cv->tu.size(); t++)
-        if (cv->ta[t] != 0) rot[cv->tu[t]] = 1;
-    std::vector<int> hslot(cv->lin.ns, -1);
-    for (int u = 0; u < cv->lin.ns; u++)
-        if (rot[u]) { hslot[u] = (int)cv->hoisted.size(); cv->hoisted.push_back(u); }
-    HE_TRY(dev_alloc(&cv->D_all, cv->hoisted.size() * (size_t)beta * ext * c->n));
-    HE_TRY(dev_alloc(&cv->facc, (size_t)V * 2 * ext * c->n));
-    HE_TRY(dev_alloc(&cv->fbase, (size_t)V * 2 * nq * c->n));
-    HE_TRY(dev_alloc(&cv->fconv, (size_t)V * 2 * nq * c->n));
-    for (int v0 = 0; v0 < n_out; v0 += V) {
-        he_conv::FusedGroup G;
-        G.V = V;
-        for (int v = v0; v < std::min(n_out, v0 + V); v++) G.outs.push_back(v);
-        std::map<long long, fused_item> items;    // key u*N + a, ascending
-        for (size_t vi = 0; vi < G.outs.size(); vi++) {
-            const int v = G.outs[vi];
-            for (int t = cv->term_off[v]; t < cv->term_off[v + 1]; t++) {
-                const int u = cv->tu[t], a = cv->ta[t];
-                const long long key = (long long)u * c->N + a;
-                auto it = items.find(key);
-                if (it == items.end()) {
-                    fused_item fi;
-                    memset(&fi, 0, sizeof(fi));
-                    fi.src = cv->R + (size_t)u * 2 * pw;
-                    fi.src_ps = pw;
-                    fi.g = h_galois(c, a);
-                    fi.beta = beta;
-                    if (fi.g != 1) {
-                        const DeviceKey *k;
-                        HE_TRY(get_key(c, (int)fi.g, &k));
-                        fi.key = k->d;
-                        fi.D = cv->D_all + (size_t)hslot[u] * beta * ext * c->n;
-                    }
-                    it = items.emplace(key, fi).first;
-                }
-                it->second.pt[vi] = cv->pts + (size_t)t * pe;
-            }
-        }
-        std::vector<fused_item> hv;
-        for (auto &kv : items) hv.push_back(kv.second);
-        G.n_items = (int)hv.size();
-        HE_TRY(dev_alloc(&G.d_items, hv.size()));
-        HE_CHECK_CUDA(cudaMemcpy(G.d_items, hv.data(), hv.size() * sizeof(fused_item), cudaMemcpyHostToDevice));
-        std::vector<md_item> md;
-        for (size_t vi = 0; vi < G.outs.size(); vi++)
-            md.push_back(md_item{cv->facc + vi * 2 * ext * c->n, cv->fconv + vi * 2 * nq * c->n,
-                                 cv->fbase + vi * 2 * nq * c->n, (size_t)nq * c->n, 2, 1,
-                                 cv->acc + (size_t)G.outs[vi] * 2 * pw, pw});
-        HE_TRY(dev_alloc(&G.d_md, md.size()));
-        HE_CHECK_CUDA(cudaMemcpy(G.d_md, md.data(), md.size() * sizeof(md_item), cudaMemcpyHostToDevice));
-        cv->fgroups.push_back(G);
-    }
-    return HE_OK;
-}
-
-static int conv_run_fused(he_conv *cv, cudaStream_t s) {
-    he_ctx *c = cv->c;
-    const int lv = cv->level, nq = lv + 1, ext = nq + c->K;
-    const int beta = (lv + c->alpha) / c->alpha;
-    for (size_t h = 0; h < cv->hoisted.size(); h++) {
-        const int u = cv->hoisted[h];
-        he_ct t = view(c, cv->R + (size_t)u * 2 * cv->pw, cv->pw, lv, 1.0);
-        HE_TRY(hoist_modup(c, &t, cv->D_all + h * (size_t)beta * ext * c->n, s));
-    }
-    for (auto &G : cv->fgroups) {
-        const int V = G.V, nv = (int)G.outs.size();
-        HE_TRY(k_ipmac(c, G.d_items, G.n_items, V, lv, cv->facc, cv->fbase, s));
-        ntt_job jp{cv->facc, (size_t)ext * c->n, nq, c->K, nq, 0, 2 * nv};
-        HE_TRY(k_ntt(c, jp, true, s));
-        HE_TRY(k_moddown_fbc(c, cv->facc, cv->fconv, lv, 2 * nv, s));
-        ntt_job jc{cv->fconv, (size_t)nq * c->n, 0, nq, nq, 0, 2 * nv};
-        HE_TRY(k_ntt(c, jc, false, s));
-        HE_TRY(k_moddown_combine(c, G.d_md, nv, lv, s));
-    }
-    return HE_OK;
+    FusedStage &F = cv->fused;
+    if (F.c) return HE_OK;
+    F.c = cv->c;
+    F.level = cv->level;
+    for (int u = 0; u < cv->lin.ns; u++) F.add_src(cv->R + (size_t)u * 2 * cv->pw, cv->pw);
+    for (int v = 0; v < cv->lout.ns; v++) F.add_out(cv->acc + (size_t)v * 2 * cv->pw, cv->pw);
+    for (size_t t = 0; t < cv->tu.size(); t++) F.add_term(cv->tv[t], cv->tu[t], cv->ta[t], cv->pts + t * cv->pe);
+    return F.build();
 }
 
 extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out, int mode, void *stream) {
@@ -1011,7 +1158,7 @@ extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out
     }
     if (mode == HE_FUSED) {
         HE_TRY(conv_prepare_fused(cv));
-        HE_TRY(conv_run_fused(cv, s));
+        HE_TRY(cv->fused.run(s));
     } else {
         if (mode == HE_BATCHED) HE_TRY(cv->rot.prepare_batched());
         HE_TRY(cv->rot.run(mode, s));
@@ -1032,9 +1179,8 @@ extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out
         dst[v]->scale = t.scale;
     }
     if (cv->stride == 2) {
-        const int pm = mode == HE_FUSED ? HE_BATCHED : mode;
-        HE_TRY(pool_prepare(cv->pool, pm));
-        return pool_run(c, cv->pool, cv->mid.data(), out, pm, s);
+        HE_TRY(pool_prepare(cv->pool, mode));
+        return pool_run(c, cv->pool, cv->mid.data(), out, mode, s);
     }
     return HE_OK;
 }

@@ -151,9 +151,17 @@ def test_pool_bit_exact(mid, c, m):
         for oc, rc in zip(outs, ref):
             assert H.he_ct_scale(oc) == rc.scale
             assert_ct_equal(g.download(oc), rc)
-    img = Ly.unpack(plan.lout, np.stack([o.decrypt(r) for r in ref]))
+    # every stage with one ModDown per output shard: equals the oracle's raised-basis pool
+    ref_r = Ly.pool_he_raised(o, plan, cts, list(hm), list(vm))
+    outs = [g.ct(level - 2) for _ in range(len(ref_r))]
+    H.he_pool_run(g.h, pool, ins, outs, H.HE_FUSED)
+    for oc, rc in zip(outs, ref_r):
+        assert H.he_ct_scale(oc) == rc.scale
+        assert_ct_equal(g.download(oc), rc)
     want = torch.nn.functional.avg_pool2d(torch.tensor(x)[None], 2)[0].numpy()
-    assert np.abs(img - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+    for r in (ref, ref_r):
+        img = Ly.unpack(plan.lout, np.stack([o.decrypt(c) for c in r]))
+        assert np.abs(img - want).max() <= 2.0 ** -20 * (want.max() - want.min())
     H.he_pool_destroy(pool)
 
 
@@ -194,14 +202,15 @@ def test_stride2_conv_decrypts_to_torch(mid):
     H.he_keygen_rotations(g.h, H.he_conv_rotations(conv))
     lout = H.he_conv_out_layout(conv)
     assert H.he_conv_out_level(conv) == level - 3
-    outs = [g.ct(level - 3) for _ in range(lout.n_shards)]
-    H.he_conv_run(g.h, conv, ins, outs, H.HE_BATCHED)
     chan, row0 = lout.tables()
     ol = Ly.Layout(lout.c, lout.m, lout.M, lout.N, lout.B, chan.astype(np.int64), row0.astype(np.int64))
-    img = Ly.unpack(ol, np.stack([H.he_decrypt(g.h, oc, o.N) for oc in outs]))
     want = torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(W), stride=2, padding=3)[0].numpy()
-    assert img.shape == want.shape
-    assert np.abs(img - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+    for mode in (H.HE_BATCHED, H.HE_FUSED):
+        outs = [g.ct(level - 3) for _ in range(lout.n_shards)]
+        H.he_conv_run(g.h, conv, ins, outs, mode)
+        img = Ly.unpack(ol, np.stack([H.he_decrypt(g.h, oc, o.N) for oc in outs]))
+        assert img.shape == want.shape
+        assert np.abs(img - want).max() <= 2.0 ** -20 * (want.max() - want.min())
     H.he_conv_destroy(conv)
 
 

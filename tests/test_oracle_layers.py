@@ -193,3 +193,16 @@ def test_raised_basis_conv_on_image_shards():
     img = Ly.unpack(plan.lout, np.stack([ctx.decrypt(c) for c in out]))
     ref = _conv_ref(x, W, None, 1)
     assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+
+
+def test_toy_pool_raised_basis_decrypts_to_fp64_pool(toy):
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0, 1, (4, 32, 32))
+    lin = Ly.image_layout(4, 32, toy.N)
+    plan = Ly.pool_plan(lin)
+    cts = [toy.encrypt(Ly.pack(lin, x)[0], 3, nonce=5)]
+    out = Ly.pool_he_raised(toy, plan, cts)
+    assert out[0].level == 1 and not np.array_equal(out[0].c, Ly.pool_he(toy, plan, cts)[0].c)
+    img = Ly.unpack(plan.lout, np.stack([toy.decrypt(c) for c in out]))
+    ref = torch.nn.functional.avg_pool2d(torch.tensor(x)[None], 2)[0].numpy()
+    assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
