@@ -38,6 +38,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(ms, ws):
+    """The job's time: the max of a per-rank time over all ranks (NCCL on GPUs, gloo on CPU)."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step_per_rank, ms_per_step, ws):
+    """Whole-job throughput: the units every rank processed / the job's time (weak scaling)."""
+    return ws * units_per_step_per_rank / (ms_per_step * 1e-3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -137,6 +154,161 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+BLOCK_LEVELS = (8, 12, 16, 19)
+BLOCK_WORKLOAD = ("resnet basic block: 64x56x56 (64x64 frame, 8 shards of 8 channels), conv3x3+BN, "
+                  "degree-16 Chebyshev GELU, conv3x3, residual; batch of 4 images at input levels "
+                  "8/12/16/19, 2N=2^16, 20+5 primes")
+
+
+def run_block(args, ws, rank, local):
+    """The batched form: one ResNet basic block over a batch of images at mixed levels.  Each
+    conv of the batch is ONE fused-kernel launch over all images (groups of every image and
+    level side by side); the GELU runs per ciphertext; the whole step is one CUDA graph."""
+    import torch
+    import workloads
+    from paper_2306_09189_gb300 import hegpu as H
+    from paper_2306_09189_gb300 import host
+    pr = host.cifar_params(seed=0)
+    ctx = H.he_ctx_create(pr)
+    H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
+                                                   "tma": H.HE_KEY_STREAM_TMA}[args.key_stream])
+    info = H.he_ctx_info(ctx)
+    n, N = info["n"], info["slots"]
+    q = info["q"]
+    x0, (W1, b1), (W2, b2) = workloads.resnet_block(0)
+    c, m = x0.shape[0], x0.shape[1]
+    imgs = [x0] + [workloads.image(c, m, 10 + i) for i in range(len(BLOCK_LEVELS) - 1)]
+    top1, top2 = 19, 19 - 1 - (DEG - 1).bit_length() - 1
+    t_setup = time.perf_counter()
+    lay = H.he_layout_image(c, m, N)
+    conv1 = H.he_conv_create(ctx, lay, W1, b1, 1, 1, top1, pr.scale)
+    lay1 = H.he_conv_out_layout(conv1)
+    conv2 = H.he_conv_create(ctx, lay1, W2, b2, 1, 1, top2, pr.scale)
+    lay2 = H.he_conv_out_layout(conv2)
+    H.he_keygen_rotations(ctx, sorted(set(H.he_conv_rotations(conv1)) | set(H.he_conv_rotations(conv2))))
+    H.he_keygen_relin(ctx)
+    cheb = host.chebyshev_coeffs(host.gelu, DEG, -8.0, 8.0)
+    ns1, ns2 = lay.n_shards, lay1.n_shards
+    xs = []
+    for i, (img, lv) in enumerate(zip(imgs, BLOCK_LEVELS)):
+        xs += host.encrypt_image(ctx, lay, img, lv, pr.scale, nonce0=100 * i)
+    y1 = [H.he_ct_alloc(ctx, top1 - 1) for _ in range(len(BLOCK_LEVELS) * ns1)]
+    y2 = [H.he_ct_alloc(ctx, top2 - 1) for _ in range(len(BLOCK_LEVELS) * ns2)]
+    # GELU output scale chosen so that conv2's output lands on the input's scale (residual)
+    tgt = [pr.scale * float(q[lv - 1 - (DEG - 1).bit_length() - 1]) / float(q[top2]) for lv in BLOCK_LEVELS]
+    setup_s = time.perf_counter() - t_setup
+
+    def rot_count(conv):
+        u, v, a, _ = H.he_conv_export_plan(conv, N)
+        return len({(int(uu), int(aa)) for uu, aa in zip(u, a) if int(aa) % N != 0})
+    ks_per_step = len(BLOCK_LEVELS) * (rot_count(conv1) + rot_count(conv2) + ns1 * (DEG - 1))
+    pt_bytes = sum(H.he_conv_n_terms(cv) * (lv + 1 + info["K"]) * n * 8 for cv, lv in ((conv1, top1), (conv2, top2)))
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def step(mode):
+        H.he_conv_run_batch(ctx, conv1, xs, y1, len(BLOCK_LEVELS), mode, stream)
+        for i in range(len(BLOCK_LEVELS)):
+            for v in range(ns1):
+                H.he_poly_eval(ctx, y1[i * ns1 + v], cheb, tgt[i], stream)
+        H.he_conv_run_batch(ctx, conv2, y1, y2, len(BLOCK_LEVELS), mode, stream)
+        for i in range(len(BLOCK_LEVELS)):
+            for v in range(ns2):
+                H.he_add(ctx, y2[i * ns2 + v], xs[i * ns1 + v], stream)
+
+    step(H.HE_FUSED)
+    torch.cuda.synchronize()
+    H.he_graph_begin(ctx, stream)
+    step(H.HE_FUSED)
+    graph = H.he_graph_end(ctx, stream)
+
+    def timed(mode, k, trace=None):
+        for _ in range(args.warmup if mode == H.HE_FUSED else 1):
+            if mode == H.HE_FUSED:
+                H.he_graph_launch(graph, stream)
+            else:
+                step(mode)
+        torch.cuda.synchronize()
+        gk = None
+        if trace:
+            H.he_trace_start(trace)
+        if mode == H.HE_FUSED:
+            H.he_graph_begin(ctx, stream)
+            for _ in range(k):
+                step(mode)
+            gk = H.he_graph_end(ctx, stream)
+        l0 = H.he_kernel_launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if gk is not None:
+            H.he_graph_launch(gk, stream)
+        else:
+            for _ in range(k):
+                step(mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1), ws) / k
+        launches = H.he_kernel_launches() - l0
+        tr = H.he_trace_stop() if trace else None
+        if gk is not None:
+            H.he_graph_destroy(gk)
+        return ms, launches, tr
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms_f, launches_f, tr = timed(H.HE_FUSED, args.steps, args.trace)
+    clk = clocks.stop()
+    # sampled output check: image 0 (input level 8), decrypted, against the FP64 block with
+    # the same polynomial
+    from numpy.polynomial import chebyshev as C
+    t1 = torch.nn.functional.conv2d(torch.tensor(imgs[0])[None], torch.tensor(W1), padding=1)[0].numpy() + b1[:, None, None]
+    g1 = C.chebval(t1, cheb)
+    want = torch.nn.functional.conv2d(torch.tensor(g1)[None], torch.tensor(W2), padding=1)[0].numpy() + b2[:, None, None] + imgs[0]
+    got = host.decrypt_image(ctx, lay2, y2[:ns2])
+    err = float(np.abs(got - want).max() / (want.max() - want.min()))
+    ms_p, _, _ = timed(H.HE_PLAIN, 1)
+    peaks, src = _peaks()
+    roof = None
+    if tr and tr["launches"]:
+        per_launch_ms = tr["ms"] / tr["launches"]
+        achieved = tr["bytes"] / tr["launches"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": args.trace, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                "launches": tr["launches"], "ms_per_launch": per_launch_ms,
+                "share_of_step": tr["ms"] / (ms_f * args.steps)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": job_value(ks_per_step, ms_f, ws), "unit": "key-switches/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_f,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic",
+                "config": {"workload": BLOCK_WORKLOAD, "input_levels": list(BLOCK_LEVELS),
+                           "key_switches_per_step": ks_per_step, "images": len(BLOCK_LEVELS),
+                           "mode": "each conv of the batch is one fused launch over all images and levels",
+                           "cuda_graph": True, "key_stream": args.key_stream,
+                           "autotuner": H.he_ctx_tuning_log(ctx).strip().splitlines(),
+                           "setup_s": setup_s,
+                           "l2": "inputs larger than L2 (%.1f GB of keys, %.1f GB of plaintexts)"
+                                 % (H.he_key_bytes(ctx) / 1e9, pt_bytes / 1e9),
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "plain": {"ms_per_step": ms_p, "value": ws * ks_per_step / (ms_p * 1e-3),
+                          "batched_speedup": ms_p / ms_f,
+                          "note": "image by image, per-ciphertext key switches, same plaintexts"},
+                "check": {"image": 0, "input_level": BLOCK_LEVELS[0], "max_err_rel_range": err,
+                          "tolerance": 2.0 ** -20},
+                "gpu_launches": int(launches_f), "roofline": roof, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    H.he_ctx_check(ctx, stream)
+    H.he_graph_destroy(graph)
+    H.he_conv_destroy(conv1)
+    H.he_conv_destroy(conv2)
+    for ct in xs + y1 + y2:
+        H.he_ct_free(ct)
+    H.he_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -149,6 +321,12 @@ def main():
                     help="profiling case: same ring, 2-channel 32x32 conv (17 rotations, ~2 GB of keys)")
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, warm up, then run one batched step between cudaProfilerStart/Stop")
+    ap.add_argument("--key-stream", default="auto", choices=["auto", "ldg", "tma"],
+                    help="how the fused kernel brings key words on chip: autotuned (default), "
+                         "vector loads, or a TMA tile pipeline")
+    ap.add_argument("--no-graph", action="store_true", help="launch the fused step eagerly, not as a CUDA graph")
+    ap.add_argument("--workload", default="cifar-layer", choices=["cifar-layer", "resnet-block"],
+                    help="cifar-layer: the headline layer; resnet-block: the batched mixed-level block")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -160,12 +338,19 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    if args.workload == "resnet-block":
+        run_block(args, ws, rank, local)
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
     import workloads
     from paper_2306_09189_gb300 import hegpu as H
     from paper_2306_09189_gb300 import host
 
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
+    H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
+                                                   "tma": H.HE_KEY_STREAM_TMA}[args.key_stream])
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]
     wl = workloads.cifar_conv_bn(0, c=2) if args.small else workloads.cifar_conv_bn(0)
@@ -178,7 +363,9 @@ def main():
     H.he_keygen_relin(ctx)
     y = H.he_ct_alloc(ctx, LEVEL - 1)
     ks_per_step = len(rots) + (DEG - 1)
-    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()             # a created stream: the default one cannot be captured
+    torch.cuda.set_stream(stream)
 
     def step(mode):
         H.he_conv_run(ctx, conv, [x], [y], mode, stream)
@@ -189,31 +376,56 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # the fused step as one CUDA graph (its first run builds, autotunes and allocates)
+    step(H.HE_FUSED)
+    torch.cuda.synchronize()
+    H.he_graph_begin(ctx, stream)
+    step(H.HE_FUSED)
+    graph = H.he_graph_end(ctx, stream)
+
+    def run(mode):
+        if mode == H.HE_FUSED and not args.no_graph:
+            H.he_graph_launch(graph, stream)
+        else:
+            step(mode)
+
     def timed(mode, k, trace=None):
         for _ in range(args.warmup):
-            step(mode)
+            run(mode)
         barrier()
-        if trace:
+        graph_k = None
+        if mode == H.HE_FUSED and not args.no_graph:
+            # the K timed steps as one graph (captured while tracing: the traced kernel's
+            # launches inside it carry their own event nodes)
+            if trace:
+                H.he_trace_start(trace)
+            H.he_graph_begin(ctx, stream)
+            for _ in range(k):
+                step(mode)
+            graph_k = H.he_graph_end(ctx, stream)
+        elif trace:
             H.he_trace_start(trace)
         l0 = H.he_kernel_launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(k):
-            step(mode)
+        if graph_k is not None:
+            H.he_graph_launch(graph_k, stream)
+        else:
+            for _ in range(k):
+                step(mode)
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
         launches = H.he_kernel_launches() - l0
         tr = H.he_trace_stop() if trace else None
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        if graph_k is not None:
+            H.he_graph_destroy(graph_k)
+        ms = max_over_ranks(ms, ws)
         return ms / k, launches, tr
 
     if args.profile_step:
         for _ in range(args.warmup):
-            step(H.HE_FUSED)
+            run(H.HE_FUSED)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         step(H.HE_FUSED)
@@ -237,10 +449,23 @@ def main():
     h_out = torch.empty(int(np.prod(out_shape)), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
     xe = H.he_ct_alloc(ctx, LEVEL)
 
-    def e2e_step():
-        H.he_ct_import_coeffs(xe, h_in, LEVEL, pr.scale, stream)
+    def e2e_body():
         H.he_conv_run(ctx, conv, [xe], [y], H.HE_FUSED, stream)
         H.he_poly_eval(ctx, y, cheb, pr.scale, stream)
+
+    H.he_ct_import_coeffs(xe, h_in, LEVEL, pr.scale, stream)
+    e2e_body()
+    torch.cuda.synchronize()
+    H.he_graph_begin(ctx, stream)
+    e2e_body()
+    graph_e2e = H.he_graph_end(ctx, stream)
+
+    def e2e_step():
+        H.he_ct_import_coeffs(xe, h_in, LEVEL, pr.scale, stream)
+        if args.no_graph:
+            e2e_body()
+        else:
+            H.he_graph_launch(graph_e2e, stream)
         assert H.he_ct_level(y) == out_level
         H.load().he_ct_export_coeffs(y, H._p(h_out, H.U64P), H.stream_ptr(stream))
 
@@ -266,14 +491,16 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": ws * ks_per_step / (ms_b * 1e-3), "unit": "key-switches/s",
+            "metric": METRIC, "value": job_value(ks_per_step, ms_b, ws), "unit": "key-switches/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": "batched+fused: every rotation key streamed once "
                                                       "into a raised-basis MAC, one ModDown per output; "
                                                       "relinearisations batched per tree depth",
-                       "key_switches_per_step": ks_per_step,
+                       "key_switches_per_step": ks_per_step, "key_stream": args.key_stream,
+                       "cuda_graph": not args.no_graph,
+                       "autotuner": H.he_ctx_tuning_log(ctx).strip().splitlines(),
                        "rotations": int(len(rots)), "relins": DEG - 1, "input_level": LEVEL,
                        "l2": "inputs larger than L2 (rotation keys %.1f GB streamed every step)" % (H.he_key_bytes(ctx) / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single"},
@@ -293,6 +520,9 @@ def main():
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(2)
         print(json.dumps(line), flush=True)
+    H.he_ctx_check(ctx, stream)
+    H.he_graph_destroy(graph)
+    H.he_graph_destroy(graph_e2e)
     H.he_conv_destroy(conv)
     for c in (x, y, xe):
         H.he_ct_free(c)

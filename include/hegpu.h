@@ -63,7 +63,8 @@ typedef struct he_poly he_poly;
  * Prime rule: every prime = 1 mod 2n; primes of b bits are the largest such primes below
  * 2^b in descending order, drawn in the order q_0 (q0_bits), p_0..p_{n_p-1} (p_bits),
  * q_1..q_{n_q-1} (q_bits), each the next unused prime of its size.
- * Key switching is hybrid with dnum digits of alpha = ceil(n_q/dnum) primes.
+ * Key switching is hybrid with dnum digits of alpha = ceil(n_q/dnum) primes; he_ctx_create
+ * rejects sets whose special-prime product P is smaller than the largest digit modulus.
  * seed keys the counter-based SplitMix64 generator that draws the secret, key and
  * encryption randomness (stream ids in the design notes). */
 typedef struct {
@@ -82,7 +83,7 @@ typedef struct {
  * B = min(M*M, N) slots; block b of shard u holds the frame rows [row0, row0 + B/M) of
  * channel chan[u*nb + b] (-1 = empty).  This single table expresses image shards, channel
  * shards, the duplication factor d and the pooling permutation tau. */
-#define HE_MAX_BLOCKS 4096
+#define HE_MAX_BLOCKS 32768   /* N / 1 for N = 2^15 slots: any frame of a 2^16 ring */
 typedef struct {
     int c, m, M, N, B;
     int n_shards, nb;
@@ -107,6 +108,62 @@ int he_layout_image(int c, int m, int N, he_layout *out);
 /* ------------------------------------------------------------------ context and keys */
 int he_ctx_create(const he_params *params, he_ctx **out);
 void he_ctx_destroy(he_ctx *ctx);
+/* A context that shares everything read-only with `parent` (tables, secret, every key,
+ * including keys generated later) but owns its own key-switching scratch, so that work on
+ * several streams can proceed at once: one fork per concurrent stream.  Destroy forks
+ * before their parent. */
+int he_ctx_fork(he_ctx *parent, he_ctx **out);
+/* Synchronise `stream` and report whether any bounded device wait of this context gave up
+ * since the last check (HE_ETIMEOUT; the work since then is invalid) or a CUDA error
+ * occurred (HE_ECUDA).  Clears the timeout flag. */
+int he_ctx_check(he_ctx *ctx, void *stream);
+/* Per-context tuning options (values are ints; a fork starts with its parent's values).
+ * HE_OPT_KEY_STREAM selects how the fused key-switch + MAC kernel brings key words on chip:
+ *   HE_KEY_STREAM_LDG (0): 16-byte vector loads straight into registers;
+ *   HE_KEY_STREAM_TMA (1): cp.async.bulk copies into a double-buffered shared-memory tile,
+ *     signalled by mbarriers with bounded waits (a wait that gives up is reported by
+ *     he_ctx_check as HE_ETIMEOUT).  Used for up to 4 digits; otherwise the LDG form runs;
+ *   HE_KEY_STREAM_SPLIT (3): the split form: the raised inner product of every (source,
+ *     amount) is written to HBM once (each key read once), then a raised-basis MAC forms the
+ *     plaintext-weighted sums of 4 outputs per pass; amounts go in chunks of at most 2 GB of
+ *     inner products.  Cheaper than the fused kernel when a stage has many output shards;
+ *   HE_KEY_STREAM_AUTO (2, default): on the first run of each fused launch an autotuner times
+ *     every eligible candidate (fused kernel: key stream x outputs per key pass; split form,
+ *     when device memory allows) and keeps the fastest (he_ctx_tuning_log lists them).
+ * Every choice gives the same bits.  Returns HE_EINVAL for an unknown option or value. */
+#define HE_OPT_KEY_STREAM 1
+#define HE_KEY_STREAM_LDG 0
+#define HE_KEY_STREAM_TMA 1
+#define HE_KEY_STREAM_AUTO 2
+#define HE_KEY_STREAM_SPLIT 3
+int he_ctx_set_option(he_ctx *ctx, int option, int value);
+int he_ctx_get_option(const he_ctx *ctx, int option, int *value);
+/* The autotuner's decisions so far (one line per tuned stage: the candidates' times and the
+ * choice), NUL-terminated into buf[cap]; returns the length needed (excluding the NUL). */
+size_t he_ctx_tuning_log(const he_ctx *ctx, char *buf, size_t cap);
+
+/* CUDA graphs.  he_graph_begin starts capturing `stream` (thread-local capture mode); every
+ * library call made on that stream by this thread until he_graph_end is recorded instead of
+ * run.  Calls that would allocate device memory or synchronise (the first run of a layer,
+ * encryption, export) fail with HE_ESTATE while capturing: run the step once before
+ * capturing it.  Host-side ciphertext metadata (level, scale) is updated at capture time
+ * exactly as a real run would, and a replay reproduces the captured device work bit for bit.
+ * The stream must be a created stream (the default stream cannot be captured: HE_EINVAL).
+ * he_graph_end returns the instantiated graph (caller owns it; he_graph_destroy frees it). */
+typedef struct he_graph he_graph;
+int he_graph_begin(he_ctx *ctx, void *stream);
+int he_graph_end(he_ctx *ctx, void *stream, he_graph **out);
+int he_graph_launch(he_graph *graph, void *stream);
+/* Kernels one launch of the graph runs. */
+uint64_t he_graph_kernels(const he_graph *graph);
+void he_graph_destroy(he_graph *graph);
+
+/* Failure-path self-test (no fault involved): launches one warp that waits, with the same
+ * bound as the key-tile pipeline, on an mbarrier nothing arrives on.  The wait gives up after
+ * 250 ms of wall time, records the timeout in the context's error word and returns; the next
+ * he_ctx_check reports HE_ETIMEOUT and clears it, and the context stays usable. */
+int he_selftest_bounded_wait(he_ctx *ctx, void *stream);
+
 /* n, N, L, K, dnum, alpha; q[L+1] and p[K] when the pointers are non-NULL. */
 int he_ctx_info(const he_ctx *ctx, int *n, int *slots, int *L, int *K, int *dnum, int *alpha,
                 uint64_t *q, uint64_t *p);
@@ -176,6 +233,9 @@ int he_ct_zero(he_ct *acc, int level, double scale, void *stream);
 int he_mul_pt_acc(he_ctx *ctx, he_ct *acc, const he_ct *ct, const he_pt *pt, void *stream);
 /* Drop q_l: c' = round(c / q_l) (centred representative of the top limb); scale /= q_l. */
 int he_rescale(he_ctx *ctx, he_ct *ct, void *stream);
+/* acc += b (he_sub: acc -= b) limb-wise.  b may sit at a higher level than acc: only its limbs
+ * q_0..q_l are read, which is b dropped to acc's level (exact; the residual connection of a
+ * ResNet block adds its input this way).  acc keeps its scale. */
 int he_add(he_ctx *ctx, he_ct *acc, const he_ct *b, void *stream);
 int he_sub(he_ctx *ctx, he_ct *acc, const he_ct *b, void *stream);
 /* ct *= c for an integer c given as a double holding an exact integer (|c| < 2^127). */
@@ -217,6 +277,26 @@ int he_conv_import_plaintexts(he_conv *conv, const int64_t *terms, const int64_t
  * plaintext-weighted sums over Q u P in registers, then one ModDown per output shard. */
 int he_conv_run(he_ctx *ctx, he_conv *conv, he_ct *const *in, he_ct **out, int mode,
                 void *stream);
+/* A batch of n_img images through one stride-1 convolution (Sec. 4.1 applied per image):
+ * in[i * n_in + u] is shard u of image i, out[i * n_out + v] receives output shard v.  Each
+ * image may sit at its own level l_i in 1..the layer's level (all its shards at one level and
+ * scale): the plaintexts encoded for the layer's level serve every lower level, so image i's
+ * output has scale in_scale_i * q_L' / q_{l_i} (L' = the layer's level) at level l_i - 1, and
+ * its bias is encoded at that scale on first use (or imported, he_conv_import_bias).  In
+ * HE_FUSED mode every image's key switches and MACs run in one fused-kernel launch (groups of
+ * all images and levels side by side, each key read from DRAM once for the batch); HE_PLAIN
+ * and HE_BATCHED run image by image.  Buffers are kept for the last level signature; a new
+ * signature allocates (not allowed inside a graph capture). */
+int he_conv_run_batch(he_ctx *ctx, he_conv *conv, he_ct *const *in, he_ct **out, int n_img, int mode,
+                      void *stream);
+/* Bias plaintexts ([n_out][n] integers) for images at `level` whose output scale is out_scale
+ * (bit-exact comparison against another encoder). */
+int he_conv_import_bias(he_conv *conv, int level, double out_scale, const int64_t *bias);
+
+/* A copy of a convolution plan for another context of the same root (he_ctx_fork): it shares
+ * the plan and the resident plaintexts, and owns its run buffers, so forks run concurrently
+ * on their own streams.  Destroy forks before the original. */
+int he_conv_fork(const he_conv *conv, he_ctx *ctx, he_conv **out);
 
 /* 2x2 average pool (Sec. 4.2): downsample (2x2 ones convolution, horizontal reduction
  * Eq. 10, vertical reduction Eq. 11), consolidate 4 shards into one (Eq. 12, channel order
@@ -224,6 +304,8 @@ int he_conv_run(he_ctx *ctx, he_conv *conv, he_ct *const *in, he_ct **out, int m
 int he_pool_create(he_ctx *ctx, const he_layout *in, int level, he_pool **out);
 void he_pool_destroy(he_pool *pool);
 int he_pool_out_layout(const he_pool *pool, he_layout *out);
+/* Fork of a pooling plan for another context of the same root (shares the mask plaintexts). */
+int he_pool_fork(const he_pool *pool, he_ctx *ctx, he_pool **out);
 int he_pool_rotations(const he_pool *pool, int32_t *amounts, size_t cap);
 /* Replace the mask plaintexts by caller-given integer polynomials: h [n_h][n_shards][n] for
  * the horizontal stage (column x' = 0, 1, ...) and v [n_v][n_shards][n] for the vertical
@@ -261,11 +343,13 @@ int he_havgpool(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, he_layou
 int he_rescale_noalloc(he_ctx *ctx, he_ct *ct, void *stream);
 
 /* ------------------------------------------------------------------ measurement */
-/* Per-kernel tracing.  he_trace_start(name) selects one kernel (e.g. "ip", "ntt", "mac",
+/* Per-kernel tracing.  he_trace_start(name) selects one kernel (e.g. "ipmac", "ip", "ntt", "mac",
  * "modup", "moddown_fbc", "moddown_combine", "rescale"); every later launch of it is bracketed
  * by CUDA events recorded on the stream it is launched on.  he_trace_stop synchronises those
  * events and returns the summed device time, the launch count and the launches' algorithmic
- * work: minimal bytes (inputs + keys + outputs, intermediates excluded) and modular products. */
+ * work: minimal bytes (inputs + keys + outputs, intermediates excluded) and modular products.
+ * Launches recorded into a CUDA graph while tracing get their events as external event-record
+ * nodes: launch such a graph once before he_trace_stop (a later launch re-records them). */
 int he_trace_start(const char *kernel);
 int he_trace_stop(double *total_ms, uint64_t *launches, double *bytes, double *mulmods);
 

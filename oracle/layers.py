@@ -247,8 +247,9 @@ def rotate_all(ctx, cts, amounts_of):
     return R
 
 
-def mac_rescale(ctx, R, terms, pts, level, scale_in):
-    """Rescale(sum_{(u,a)} pt_{u,a} * R_{u,a}): the fused pt x ct MAC of one output shard."""
+def mac_rescale(ctx, R, terms, pts, level, scale_in, pt_scale=None):
+    """Rescale(sum_{(u,a)} pt_{u,a} * R_{u,a}): the fused pt x ct MAC of one output shard.
+    pt_scale: the plaintexts' encoding scale (default q_level, which keeps the scale exact)."""
     mods, psis = ctx.mods(level), ctx.psis(level)
     acc = [np.zeros((level + 1, ctx.n), dtype=np.uint64) for _ in range(2)]
     for (u, a), pt in zip(terms, pts):
@@ -258,14 +259,17 @@ def mac_rescale(ctx, R, terms, pts, level, scale_in):
             ctx.lib.orc_mac(acc[k], P, X, level + 1, ctx.n, mods)
     from .ckks import Ciphertext
     c = np.stack([ctx.intt(x, mods, psis).reshape(level + 1, ctx.n) for x in acc])
-    return ctx.rescale(Ciphertext(c, level, scale_in * ctx.q[level]))
+    S = float(ctx.q[level]) if pt_scale is None else pt_scale
+    return ctx.rescale(Ciphertext(c, level, scale_in * S))
 
 
-def conv_he(ctx, plan: ConvPlan, cts, pts=None, bias_pts=None):
+def conv_he(ctx, plan: ConvPlan, cts, pts=None, bias_pts=None, pt_scale=None):
     """hconv2d on oracle ciphertexts (all inputs at one level and scale).
 
     pts: optional {(u, v, a): int64 plaintext} at scale q_level (else encoded here);
     bias_pts: optional {v: int64 plaintext} at the input scale (else encoded here).
+    pt_scale: the scale pts were encoded at, when they were encoded for another (higher)
+    level: an integer plaintext is the same at every level, only its residues are fewer.
     """
     level, scale = cts[0].level, cts[0].scale
     assert all(c.level == level and c.scale == scale for c in cts)
@@ -275,7 +279,7 @@ def conv_he(ctx, plan: ConvPlan, cts, pts=None, bias_pts=None):
     out = []
     for v in range(plan.lout.n_shards):
         keys = sorted(plan.terms[v].keys())
-        ct = mac_rescale(ctx, R, keys, [pts[(u, v, a)] for (u, a) in keys], level, scale)
+        ct = mac_rescale(ctx, R, keys, [pts[(u, v, a)] for (u, a) in keys], level, scale, pt_scale)
         bpt = bias_pts[v] if bias_pts is not None else encode(plan.bias[v], ctx.n, ct.scale)
         ct.c[0] = ctx.add(ct.c[0], ctx.reduce_int(bpt, ctx.mods(ct.level)), ctx.mods(ct.level))
         out.append(ct)
@@ -334,9 +338,10 @@ def raised_stage(ctx, srcs, terms_by_v):
     return [out[v] for v in sorted(out)]
 
 
-def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None):
+def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None, pt_scale=None):
     """hconv2d with one ModDown per output shard (raised_stage), then rescale and bias.
-    Same plan and plaintexts as conv_he; decrypts like it, different bits."""
+    Same plan and plaintexts as conv_he; decrypts like it, different bits.  pt_scale as in
+    conv_he."""
     level, scale = cts[0].level, cts[0].scale
     assert all(c.level == level and c.scale == scale for c in cts)
     if pts is None:
@@ -345,7 +350,7 @@ def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None):
              for v in range(plan.lout.n_shards)}
     out = []
     for v, acc in enumerate(raised_stage(ctx, cts, terms)):
-        acc.scale = scale * ctx.q[level]
+        acc.scale = scale * (float(ctx.q[level]) if pt_scale is None else pt_scale)
         ct = ctx.rescale(acc)
         bpt = bias_pts[v] if bias_pts is not None else encode(plan.bias[v], ctx.n, ct.scale)
         ct.c[0] = ctx.add(ct.c[0], ctx.reduce_int(bpt, ctx.mods(ct.level)), ctx.mods(ct.level))

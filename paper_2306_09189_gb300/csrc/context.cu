@@ -20,7 +20,21 @@ void he_set_error(const char *fmt, ...) {
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
 }
-void he_count_launch(int k) { g_launches += (uint64_t)k; }
+static thread_local bool g_capturing = false;
+static thread_local uint64_t g_captured = 0;    // kernels recorded by this thread's capture
+void he_count_launch(int k) {
+    if (g_capturing) g_captured += (uint64_t)k;  // recorded, not run: counted per replay
+    else g_launches += (uint64_t)k;
+}
+
+bool he_capturing() { return g_capturing; }
+static thread_local bool g_capture_failed = false;
+int he_capture_guard(const char *what) {
+    if (!g_capturing) return HE_OK;
+    g_capture_failed = true;                     // the graph would be incomplete: discard it
+    he_set_error("%s during graph capture: run the step once before capturing it", what);
+    return HE_ESTATE;
+}
 
 // ================================================================================ tracing
 #include <mutex>
@@ -35,6 +49,12 @@ struct Tracer {
 } g_tr;
 }  // namespace
 
+// Inside a graph capture the two events become external event-record nodes of the graph, so
+// a graph captured while tracing (launched once before he_trace_stop) is timed per kernel too.
+static cudaError_t trace_record(cudaEvent_t e, cudaStream_t s) {
+    return g_capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
 TraceScope::TraceScope(const char *name, cudaStream_t st, double bytes_, double mulmods_)
     : s(st), bytes(bytes_), mulmods(mulmods_) {
     if (!g_tr.on) return;
@@ -42,13 +62,13 @@ TraceScope::TraceScope(const char *name, cudaStream_t st, double bytes_, double 
     if (!g_tr.on || g_tr.name != name) return;
     on = true;
     cudaEventCreate(&b);
-    cudaEventRecord(b, s);
+    trace_record(b, s);
 }
 TraceScope::~TraceScope() {
     if (!on) return;
     cudaEvent_t e;
     cudaEventCreate(&e);
-    cudaEventRecord(e, s);
+    trace_record(e, s);
     std::lock_guard<std::mutex> lk(g_tr.mu);
     g_tr.recs.push_back({b, e});
     g_tr.bytes += bytes;
@@ -212,6 +232,7 @@ u64 h_galois(const he_ctx *ctx, int32_t r) {
 // ================================================================================ scratch
 int Scratch::ensure(size_t w) {
     if (w <= words) return HE_OK;
+    HE_TRY(he_capture_guard("scratch allocation"));
     if (p) cudaFree(p);
     p = nullptr;
     words = 0;
@@ -268,6 +289,11 @@ static void free_ctx(he_ctx *c) {
     if (!c) return;
     for (he_ct *t : c->poly_tmp) he_ct_free(t);
     if (c->poly_block) cudaFree(c->poly_block);
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->parent) {                       // a fork owns only its scratch
+        delete c;
+        return;
+    }
     for (auto &lv : c->modup)
         for (auto &t : lv)
             if (t.d) cudaFree(t.d);
@@ -295,6 +321,23 @@ static int create(const he_params *pr, he_ctx **out) {
         cudaGetLastError();
         he_set_error("no CUDA device: this library has no CPU fallback");
         return HE_ECUDA;
+    }
+    {
+        // hybrid key switching divides by P = prod p_k; P must exceed every digit's modulus
+        // (a product of alpha ciphertext primes) or the switching noise swamps the message
+        const int alpha = (pr->n_q + pr->dnum - 1) / pr->dnum;
+        double bits_P = 0, worst = 0;
+        for (u64 x : p) bits_P += std::log2((double)x);
+        for (int j = 0; j * alpha < pr->n_q; j++) {
+            double b = 0;
+            for (int i = j * alpha; i < std::min(pr->n_q, (j + 1) * alpha); i++) b += std::log2((double)q[i]);
+            worst = std::max(worst, b);
+        }
+        if (bits_P < worst) {
+            he_set_error("parameters: the special primes give %.0f bits, below the largest key-switching "
+                         "digit (%.0f bits); raise n_p or dnum", bits_P, worst);
+            return HE_EINVAL;
+        }
     }
     he_ctx *c = new he_ctx();
     c->pr = *pr;
@@ -442,6 +485,13 @@ static int create(const he_params *pr, he_ctx **out) {
         he_set_error("secret allocation failed");
         return HE_ENOMEM;
     }
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s_int);
+        free_ctx(c);
+        he_set_error("error-word allocation failed");
+        return HE_ENOMEM;
+    }
     rc = k_sample_ternary(c, pr->seed, 1, s_int, 0);
     if (rc == HE_OK) rc = k_reduce_int(c, s_int, c->d_s, np, Q, false, 0);
     if (rc == HE_OK) rc = ntt_poly(c, c->d_s, 0, 0, np, Q, 1, false, 0);
@@ -486,6 +536,7 @@ static int gen_key(he_ctx *c, int id, const u64 *sp_eval, cudaStream_t s) {
     const size_t limbs = (size_t)np * n;
     DeviceKey key;
     key.id = id;
+    HE_TRY(he_capture_guard("key generation"));
     if (cudaMalloc(&key.d, (size_t)c->dnum * 2 * limbs * 8) != cudaSuccess) {
         cudaGetLastError();
         he_set_error("key allocation failed (%zu bytes)", (size_t)c->dnum * 2 * limbs * 8);
@@ -510,8 +561,8 @@ static int gen_key(he_ctx *c, int id, const u64 *sp_eval, cudaStream_t s) {
         cudaFree(key.d);
         return rc;
     }
-    c->keys[id] = key;
-    c->key_bytes += (size_t)c->dnum * 2 * limbs * 8;
+    c->root()->keys[id] = key;
+    c->root()->key_bytes += (size_t)c->dnum * 2 * limbs * 8;
     return HE_OK;
 }
 
@@ -521,7 +572,7 @@ extern "C" int he_keygen_rotations(he_ctx *c, const int32_t *rot, size_t n_rot) 
     u64 *sp = c->sc_tmp2.p;      // [np][n]
     for (size_t i = 0; i < n_rot; i++) {
         u64 g = h_galois(c, rot[i]);
-        if (g == 1 || c->keys.count((int)g)) continue;
+        if (g == 1 || c->root()->keys.count((int)g)) continue;
         HE_TRY(k_permute(c, c->d_s, sp, c->np, g, s));
         HE_TRY(gen_key(c, (int)g, sp, s));
     }
@@ -531,7 +582,7 @@ extern "C" int he_keygen_rotations(he_ctx *c, const int32_t *rot, size_t n_rot) 
 
 extern "C" int he_keygen_relin(he_ctx *c) {
     if (!c) { he_set_error("null context"); return HE_EINVAL; }
-    if (c->keys.count(0)) return HE_OK;
+    if (c->root()->keys.count(0)) return HE_OK;
     u64 *sp = c->sc_tmp2.p;
     HE_TRY(k_mul_pointwise(c, c->d_s, c->d_s, sp, c->np, 0));
     HE_TRY(gen_key(c, 0, sp, 0));
@@ -542,12 +593,13 @@ extern "C" int he_keygen_relin(he_ctx *c) {
 extern "C" int he_has_rotation_key(const he_ctx *c, int32_t rot) {
     if (!c) return 0;
     u64 g = h_galois(c, rot);
-    return g == 1 || c->keys.count((int)g) ? 1 : 0;
+    return g == 1 || c->root()->keys.count((int)g) ? 1 : 0;
 }
 
 int get_key(he_ctx *c, int id, const DeviceKey **out) {
-    auto it = c->keys.find(id);
-    if (it == c->keys.end()) {
+    auto &keys = c->root()->keys;
+    auto it = keys.find(id);
+    if (it == keys.end()) {
         he_set_error(id == 0 ? "relinearisation key missing" : "rotation key for Galois element %d missing", id);
         return HE_EKEY;
     }
@@ -574,7 +626,171 @@ extern "C" int he_key_export(he_ctx *c, int32_t rot, uint64_t *host) {
     return HE_OK;
 }
 
-extern "C" size_t he_key_bytes(const he_ctx *c) { return c ? c->key_bytes : 0; }
+extern "C" size_t he_key_bytes(const he_ctx *c) { return c ? c->root()->key_bytes : 0; }
+
+extern "C" int he_ctx_fork(he_ctx *parent, he_ctx **out) {
+    if (!parent || !out) { he_set_error("he_ctx_fork: null argument"); return HE_EINVAL; }
+    he_ctx *r = parent->root();
+    he_ctx *c = new he_ctx();
+    c->pr = r->pr;
+    c->n = r->n; c->logn = r->logn; c->N = r->N; c->L = r->L; c->K = r->K;
+    c->dnum = r->dnum; c->alpha = r->alpha; c->np = r->np;
+    c->primes = r->primes; c->psi = r->psi; c->kp = r->kp;
+    c->d_tables = r->d_tables;
+    c->h_qinv = r->h_qinv; c->h_mu = r->h_mu; c->h_r2 = r->h_r2;
+    c->modup = r->modup; c->moddown = r->moddown;
+    c->pinv = r->pinv; c->pinv_s = r->pinv_s; c->pmod = r->pmod;
+    c->d_consts = r->d_consts;
+    c->d_s = r->d_s;
+    c->key_stream = parent->key_stream;
+    c->parent = r;
+    const size_t ext = (size_t)(c->L + 1 + c->K) * c->n;
+    int rc = c->sc_digits.ensure((size_t)c->dnum * ext);
+    if (rc == HE_OK) rc = c->sc_u.ensure(2 * ext);
+    if (rc == HE_OK) rc = c->sc_conv.ensure(2 * (size_t)(c->L + 1) * c->n);
+    if (rc == HE_OK) rc = c->sc_tmp.ensure(3 * ext);
+    if (rc == HE_OK) rc = c->sc_tmp2.ensure(ext);
+    if (rc == HE_OK && (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+                        cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)) {
+        cudaGetLastError();
+        c->d_err = nullptr;
+        rc = HE_ENOMEM;
+    }
+    if (rc != HE_OK) { free_ctx(c); return rc; }
+    *out = c;
+    return HE_OK;
+}
+
+extern "C" int he_ctx_check(he_ctx *c, void *stream) {
+    if (!c) { he_set_error("null context"); return HE_EINVAL; }
+    HE_CHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    HE_CHECK_CUDA(cudaGetLastError());
+    int e = 0;
+    HE_CHECK_CUDA(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        cudaMemset(c->d_err, 0, sizeof(int));
+        he_set_error("a bounded device wait gave up (key-tile pipeline); results of the work since "
+                     "the last check are invalid");
+        return HE_ETIMEOUT;
+    }
+    return HE_OK;
+}
+
+extern "C" int he_selftest_bounded_wait(he_ctx *c, void *stream) {
+    if (!c) { he_set_error("null context"); return HE_EINVAL; }
+    return k_selftest_bounded_wait(c, (cudaStream_t)stream);
+}
+
+extern "C" int he_ctx_set_option(he_ctx *c, int option, int value) {
+    if (!c) { he_set_error("null context"); return HE_EINVAL; }
+    if (option == HE_OPT_KEY_STREAM &&
+        (value == HE_KEY_STREAM_LDG || value == HE_KEY_STREAM_TMA || value == HE_KEY_STREAM_AUTO ||
+         value == HE_KEY_STREAM_SPLIT)) {
+        c->key_stream = value;
+        return HE_OK;
+    }
+    he_set_error("he_ctx_set_option: unknown option %d or value %d", option, value);
+    return HE_EINVAL;
+}
+
+extern "C" int he_ctx_get_option(const he_ctx *c, int option, int *value) {
+    if (!c || !value) { he_set_error("he_ctx_get_option: null argument"); return HE_EINVAL; }
+    if (option == HE_OPT_KEY_STREAM) { *value = c->key_stream; return HE_OK; }
+    he_set_error("he_ctx_get_option: unknown option %d", option);
+    return HE_EINVAL;
+}
+
+void he_tune_note(he_ctx *c, const std::string &line) {
+    he_ctx *r = c->root();
+    std::lock_guard<std::mutex> lk(r->tune_mu);
+    r->tune_log.push_back(line);
+}
+
+extern "C" size_t he_ctx_tuning_log(const he_ctx *cc, char *buf, size_t cap) {
+    if (!cc) return 0;
+    he_ctx *r = const_cast<he_ctx *>(cc)->root();
+    std::lock_guard<std::mutex> lk(r->tune_mu);
+    std::string all;
+    for (auto &l : r->tune_log) all += l + "\n";
+    if (buf && cap) {
+        const size_t m = std::min(cap - 1, all.size());
+        memcpy(buf, all.data(), m);
+        buf[m] = 0;
+    }
+    return all.size();
+}
+
+// ================================================================================ graphs
+struct he_graph {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t e = nullptr;
+    uint64_t kernels = 0;
+};
+
+extern "C" int he_graph_begin(he_ctx *c, void *stream) {
+    if (!c) { he_set_error("null context"); return HE_EINVAL; }
+    if (g_capturing) { he_set_error("he_graph_begin: already capturing"); return HE_ESTATE; }
+    if (!stream || stream == (void *)cudaStreamLegacy || stream == (void *)cudaStreamPerThread) {
+        he_set_error("he_graph_begin: the default stream cannot be captured; use a created stream");
+        return HE_EINVAL;
+    }
+    HE_CHECK_CUDA(cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    g_captured = 0;
+    g_capture_failed = false;
+    return HE_OK;
+}
+
+extern "C" int he_graph_end(he_ctx *c, void *stream, he_graph **out) {
+    if (!c || !out) { he_set_error("he_graph_end: null argument"); return HE_EINVAL; }
+    if (!g_capturing) { he_set_error("he_graph_end: not capturing"); return HE_ESTATE; }
+    g_capturing = false;
+    const uint64_t captured = g_captured;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture((cudaStream_t)stream, &g);
+    if (e != cudaSuccess || !g) {
+        cudaGetLastError();
+        he_set_error("he_graph_end: capture failed (%s); a call inside it was not capturable",
+                     cudaGetErrorString(e));
+        if (g) cudaGraphDestroy(g);
+        return HE_ECUDA;
+    }
+    if (g_capture_failed) {
+        cudaGraphDestroy(g);
+        he_set_error("he_graph_end: a call during the capture failed (see its error); graph discarded");
+        return HE_ESTATE;
+    }
+    he_graph *h = new he_graph();
+    h->g = g;
+    h->kernels = captured;
+    if (cudaGraphInstantiate(&h->e, g, 0) != cudaSuccess ||
+        cudaGraphUpload(h->e, (cudaStream_t)stream) != cudaSuccess) {   // first launch pays no upload
+        cudaGetLastError();
+        if (h->e) cudaGraphExecDestroy(h->e);
+        cudaGraphDestroy(g);
+        delete h;
+        he_set_error("he_graph_end: instantiation failed");
+        return HE_ECUDA;
+    }
+    *out = h;
+    return HE_OK;
+}
+
+extern "C" int he_graph_launch(he_graph *h, void *stream) {
+    if (!h) { he_set_error("null graph"); return HE_EINVAL; }
+    HE_CHECK_CUDA(cudaGraphLaunch(h->e, (cudaStream_t)stream));
+    g_launches += h->kernels;
+    return HE_OK;
+}
+
+extern "C" uint64_t he_graph_kernels(const he_graph *h) { return h ? h->kernels : 0; }
+
+extern "C" void he_graph_destroy(he_graph *h) {
+    if (!h) return;
+    if (h->e) cudaGraphExecDestroy(h->e);
+    if (h->g) cudaGraphDestroy(h->g);
+    delete h;
+}
 
 // ================================================================================ ciphertexts
 extern "C" int he_ct_alloc(he_ctx *c, int level, he_ct **out) {
@@ -583,6 +799,7 @@ extern "C" int he_ct_alloc(he_ctx *c, int level, he_ct **out) {
     ct->ctx = c;
     ct->cap = ct->level = level;
     ct->pstride = (size_t)(level + 1) * c->n;
+    if (he_capturing()) { delete ct; return he_capture_guard("ciphertext allocation"); }
     if (cudaMalloc(&ct->d, 2 * ct->pstride * 8) != cudaSuccess) {
         cudaGetLastError();
         delete ct;
@@ -908,12 +1125,13 @@ extern "C" int he_rescale(he_ctx *c, he_ct *ct, void *stream) {
     return HE_OK;
 }
 
+// b may sit above acc's level: its limbs q_0..q_l are b at level l (dropping limbs is exact)
 extern "C" int he_add(he_ctx *c, he_ct *acc, const he_ct *b, void *stream) {
-    if (!c || !acc || !b || acc->level != b->level) { he_set_error("he_add: level mismatch"); return HE_ELEVEL; }
+    if (!c || !acc || !b || acc->level > b->level) { he_set_error("he_add: addend below the accumulator's level"); return HE_ELEVEL; }
     return k_add(c, acc, b, false, (cudaStream_t)stream);
 }
 extern "C" int he_sub(he_ctx *c, he_ct *acc, const he_ct *b, void *stream) {
-    if (!c || !acc || !b || acc->level != b->level) { he_set_error("he_sub: level mismatch"); return HE_ELEVEL; }
+    if (!c || !acc || !b || acc->level > b->level) { he_set_error("he_sub: operand below the accumulator's level"); return HE_ELEVEL; }
     return k_add(c, acc, b, true, (cudaStream_t)stream);
 }
 

@@ -5,6 +5,7 @@
 
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -19,6 +20,7 @@ void he_set_error(const char *fmt, ...);
     do {                                                                           \
         cudaError_t _e = (expr);                                                   \
         if (_e != cudaSuccess) {                                                   \
+            cudaGetLastError();  /* do not leave the error for a later launch check */ \
             he_set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr,                \
                          cudaGetErrorString(_e));                                  \
             return HE_ECUDA;                                                       \
@@ -31,6 +33,10 @@ void he_set_error(const char *fmt, ...);
     } while (0)
 
 void he_count_launch(int k = 1);
+// True while this thread is capturing a CUDA graph (he_graph_begin .. he_graph_end): no device
+// allocation, synchronous copy or event timing may happen then.
+bool he_capturing();
+int he_capture_guard(const char *what);    // HE_ESTATE with a message when capturing
 
 // Per-kernel tracing: while a kernel name is selected, every launch of that kernel is
 // bracketed by CUDA events on its own stream and its algorithmic work is accumulated.
@@ -114,6 +120,13 @@ struct he_ctx {
     std::map<int, DeviceKey> keys;       // key id (Galois element; 0 = relin) -> key
     Scratch sc_digits, sc_u, sc_conv, sc_tmp, sc_tmp2;
     size_t key_bytes = 0;
+    int *d_err = nullptr;                // set by a bounded device wait that gave up
+    int key_stream = HE_KEY_STREAM_AUTO; // HE_OPT_KEY_STREAM
+    std::mutex tune_mu;                  // root only: the autotuner's log
+    std::vector<std::string> tune_log;
+    he_ctx *parent = nullptr;            // forks share tables, secret and keys with their root
+    he_ctx *root() { return parent ? parent : this; }
+    const he_ctx *root() const { return parent ? parent : this; }
     std::vector<he_ct *> poly_tmp;       // reusable temporaries of he_poly_eval (level L), views
     u64 *poly_block = nullptr;           // one allocation holding them at a uniform stride
     Scratch sc_relin;                    // batched relinearisation buffers
@@ -211,25 +224,66 @@ int k_mul_pointwise(const he_ctx *ctx, const u64 *a, const u64 *b, u64 *out, int
 // Amount-major form: every rotation key is read once and applied to every source shard that
 // uses that amount.  A plaintext pointer equal to HE_PT_ONE stands for the integer 1.
 #define HE_PT_ONE ((const u64 *)1)
-struct fsrc {
-    const u64 *D;           // raised digits [beta][l+1+K][n] (null when the source is never rotated)
-    const u64 *src;         // ciphertext data (c0, c1 at src + ps), level l
-    size_t ps;
-};
 struct famt {
     const u64 *key;         // null for amount 0
     u64 g;
     int e0, e1;             // entries [e0, e1)
 };
 struct fent {
-    const u64 *D;           // the source's raised digits, or null
-    const u64 *src;         // the source's ciphertext data
+    const u64 *D;           // the source's raised digits [beta][l+1+K][n], or null
+    const u64 *src;         // the source's ciphertext data (c0, c1 at src + ps), level l
     size_t ps;
     const u64 *pt[2];       // per output of the group (V <= 2): plaintext, HE_PT_ONE or null
     int s;                  // source index (host bookkeeping)
 };
-int k_ipmac2(const he_ctx *ctx, const fsrc *srcs, const famt *amts, int n_amt, const fent *ents, int V,
-             int level, u64 *acc, u64 *base, double bytes, double mulmods, cudaStream_t s);
+// One group of a fused launch: V outputs of one item (an image's layer stage at level l).
+// Plaintexts hold pt_level + 1 q-limbs then the K p-limbs, pt_level >= l, so one plaintext
+// set encoded for the top level also serves items at every lower level.
+struct fgrp {
+    const famt *amts;
+    const fent *ents;
+    int n_amt, level, beta, pt_level;
+    u64 *acc;               // [2V][l+1+K][n]  raised-basis inner products x plaintexts
+    u64 *base;              // [2V][l+1][n]    plaintext x rotated c0 (and unrotated c1)
+};
+// One launch over n_grp groups (any mix of levels): the grid walks global primes, and the
+// groups sharing a (coefficient tile, prime) are adjacent in launch order, so each key and
+// plaintext word is fetched from DRAM once and served to the other groups from L2.
+// form: HE_KEY_STREAM_LDG or HE_KEY_STREAM_TMA (TMA needs beta <= 4 in every group).
+int k_ipmac(const he_ctx *ctx, const fgrp *grps_dev, int n_grp, int V, int max_beta, double bytes,
+            double mulmods, int form, cudaStream_t s);
+// Split form of a fused stage (same bits): (1) the raised inner product u_{s,a} of every
+// (source, amount) is written to HBM once (amount-major: each key read once per launch), then
+// (2) a raised-basis MAC forms sum pt (.) u over Q u P for HE_RV outputs per pass.  Cheaper
+// than the fused kernel when many output groups would each recompute the inner products.
+#define HE_RV 4
+struct uent {
+    const u64 *D;           // the source's raised digits
+    u64 *U;                 // output [2][l+1+K][n]
+};
+struct ugrp {               // inner products of one stage (one image at one level)
+    const famt *amts;       // keyed amounts; entries index uent
+    const uent *ents;
+    int n_amt, level, beta;
+};
+struct rterm {
+    const u64 *U;           // raised inner product of (s, a), null for amount 0
+    const u64 *src;         // source ciphertext (c0, c1 at src + ps)
+    size_t ps;
+    u64 g;                  // Galois element of a (gathers c0)
+    const u64 *pt[HE_RV];   // per output of the group: plaintext, HE_PT_ONE or null
+};
+struct rgrp {               // HE_RV outputs of one stage
+    const rterm *terms;
+    int n_terms, level, pt_level;
+    int accumulate;         // add to acc/base (mod q) instead of overwriting: later amount chunks
+    u64 *acc;               // [2 HE_RV][l+1+K][n]
+    u64 *base;              // [2 HE_RV][l+1][n]
+};
+int k_ip_amounts(const he_ctx *ctx, const ugrp *grps_dev, int n_grp, int max_beta, double bytes, cudaStream_t s);
+int k_rmac(const he_ctx *ctx, const rgrp *grps_dev, int n_grp, double bytes, double mulmods, cudaStream_t s);
+void he_tune_note(he_ctx *ctx, const std::string &line);
+int k_selftest_bounded_wait(const he_ctx *ctx, cudaStream_t s);
 int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u64 *res, int n,
               const u64 *cst, int level, u64 *out, size_t out_ps, cudaStream_t s);
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s);

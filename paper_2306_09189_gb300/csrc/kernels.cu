@@ -648,29 +648,82 @@ __global__ void __launch_bounds__(TB) mac_kernel(KP kp, const mac_term *terms, m
 __device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *(const ulonglong2 *)p; }
 __device__ __forceinline__ void st2(u64 *p, u64 a, u64 b) { *(ulonglong2 *)p = make_ulonglong2(a, b); }
 
+// L2 residency: the key and plaintext streams are read once per launch, while the raised
+// digits and the source ciphertext are gathered again for every rotation amount.  Streaming
+// loads carry an evict-first policy and gathers an evict-last one, so the gathered working set
+// (one source: beta (l+1+K) n words, 52 MB at n = 2^16, l = 19) stays in the 126 MB L2
+// instead of being flushed by gigabytes of keys.
+__device__ __forceinline__ u64 policy_evict_first() {
+    u64 p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ u64 policy_evict_last() {
+    u64 p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ ulonglong2 ld2_hint(const u64 *p, u64 pol) {
+    ulonglong2 r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
+                 : "=l"(r.x), "=l"(r.y) : "l"(p), "l"(pol));
+    return r;
+}
+
+// Block -> (group, coefficient tile, limb).  blockIdx.x = tile * n_grp + group, so the groups
+// that read the same key / plaintext words run side by side; blockIdx.y is the global prime
+// index.  Returns false for a q-prime above the group's level (nothing to do there).  t is the
+// limb's index in the group's Q_l u P layout, ptl its index in the plaintexts' layout.
+__device__ __forceinline__ bool grp_pos(const KP &kp, const fgrp *grps, int n_grp, fgrp &P, int &tile, int &t,
+                                        int &ptl) {
+    const int g = blockIdx.x % n_grp;
+    tile = blockIdx.x / n_grp;
+    P = grps[g];
+    const int kl = blockIdx.y;
+    if (kl <= kp.L) {
+        if (kl > P.level) return false;
+        t = ptl = kl;
+    } else {
+        t = P.level + 1 + (kl - kp.L - 1);
+        ptl = P.pt_level + 1 + (kl - kp.L - 1);
+    }
+    return true;
+}
+
 // Amount-major fused inner product + MAC.  For each amount the thread loads its key words
 // once (two coefficients, beta digits, both polynomials) and applies them to every source
-// shard that uses the amount; V <= 2 outputs per group.
+// shard that uses the amount; V <= 2 outputs per group.  The next amount's descriptors are
+// fetched while the current one computes, so each amount costs one memory round trip.
 template <int V, int B>
-__global__ void __launch_bounds__(TB) ipmac2_kernel(KP kp, const fsrc *srcs, const famt *amts, int n_amt,
-                                                    const fent *ents, int level, int beta,
-                                                    u64 *acc, u64 *base) {
-    const int k = 2 * (blockIdx.x * TB + threadIdx.x);
-    const int t = blockIdx.y;
-    const int nq = level + 1;
+__global__ void __launch_bounds__(TB, (V == 1 && B == 4) ? 2 : 1) ipmac_kernel(KP kp, const fgrp *grps, int n_grp) {
+    fgrp P;
+    int tile, t, ptl;
+    if (!grp_pos(kp, grps, n_grp, P, tile, t, ptl)) return;
+    const int k = 2 * (tile * TB + threadIdx.x);
+    const int kl = blockIdx.y;
+    const int nq = P.level + 1;
     const int ext = nq + kp.K;
-    const int kl = t < nq ? t : kp.L + 1 + (t - nq);
+    const int beta = P.beta;
     const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
     const u64 one = to_mont(1, q, qi, r2);
     const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
-    const size_t off = (size_t)t * kp.n + k;
+    const size_t off = (size_t)t * kp.n + k, ptoff = (size_t)ptl * kp.n + k;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
     u128 a0[V][2], a1[V][2], b0[V][2], b1[V][2];
 #pragma unroll
     for (int v = 0; v < V; v++)
 #pragma unroll
         for (int e = 0; e < 2; e++) a0[v][e] = a1[v][e] = b0[v][e] = b1[v][e] = 0;
+    const int n_amt = P.n_amt;
+    famt A = n_amt > 0 ? P.amts[0] : famt{};
+    fent E = (n_amt > 0 && A.e0 < A.e1) ? P.ents[A.e0] : fent{};
     for (int i = 0; i < n_amt; i++) {
-        const famt A = amts[i];
+        famt An{};
+        fent En{};
+        if (i + 1 < n_amt) {
+            An = P.amts[i + 1];
+            if (An.e0 < An.e1) En = P.ents[An.e0];
+        }
         const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
         const int sw = ks & 1, kb = ks & ~1;
         ulonglong2 kk0[B], kk1[B];
@@ -679,25 +732,24 @@ __global__ void __launch_bounds__(TB) ipmac2_kernel(KP kp, const fsrc *srcs, con
             for (int j = 0; j < B; j++)
                 if (j < beta) {
                     const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
-                    kk0[j] = ld2(kp0);
-                    kk1[j] = ld2(kp0 + kstride);
+                    kk0[j] = ld2_hint(kp0, stream);
+                    kk1[j] = ld2_hint(kp0 + kstride, stream);
                 }
         }
         for (int e = A.e0; e < A.e1; e++) {
-            const fent E = ents[e];
-            const fsrc S{E.D, E.src, E.ps};
+            if (e > A.e0) E = P.ents[e];
             ulonglong2 p[V];
 #pragma unroll
             for (int v = 0; v < V; v++) {
                 const u64 *pp = E.pt[v];
-                p[v] = pp == HE_PT_ONE ? make_ulonglong2(one, one) : (pp ? ld2(pp + off) : make_ulonglong2(0, 0));
+                p[v] = pp == HE_PT_ONE ? make_ulonglong2(one, one) : (pp ? ld2_hint(pp + ptoff, stream) : make_ulonglong2(0, 0));
             }
             if (A.key) {
                 u128 s0[2] = {0, 0}, s1[2] = {0, 0};
 #pragma unroll
                 for (int j = 0; j < B; j++)
                     if (j < beta) {
-                        const ulonglong2 d = ld2(S.D + ((size_t)j * ext + t) * kp.n + kb);
+                        const ulonglong2 d = ld2_hint(E.D + ((size_t)j * ext + t) * kp.n + kb, keep);
                         const u64 d0 = sw ? d.y : d.x, d1 = sw ? d.x : d.y;
                         s0[0] += (u128)d0 * kk0[j].x;
                         s0[1] += (u128)d1 * kk0[j].y;
@@ -715,10 +767,10 @@ __global__ void __launch_bounds__(TB) ipmac2_kernel(KP kp, const fsrc *srcs, con
                 }
             }
             if (t < nq) {
-                const ulonglong2 cc = ld2(S.src + (size_t)t * kp.n + kb);
+                const ulonglong2 cc = ld2_hint(E.src + (size_t)t * kp.n + kb, keep);
                 const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
                 ulonglong2 c1 = make_ulonglong2(0, 0);
-                if (!A.key) c1 = ld2(S.src + S.ps + off);
+                if (!A.key) c1 = ld2_hint(E.src + E.ps + off, keep);
 #pragma unroll
                 for (int v = 0; v < V; v++) {
                     b0[v][0] += (u128)p[v].x * c00;
@@ -728,14 +780,207 @@ __global__ void __launch_bounds__(TB) ipmac2_kernel(KP kp, const fsrc *srcs, con
                 }
             }
         }
+        A = An;
+        E = En;
     }
 #pragma unroll
     for (int v = 0; v < V; v++) {
-        st2(acc + ((size_t)(2 * v) * ext) * kp.n + off, redc(a0[v][0], q, qi), redc(a0[v][1], q, qi));
-        st2(acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
+        st2(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, redc(a0[v][0], q, qi), redc(a0[v][1], q, qi));
+        st2(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
         if (t < nq) {
-            st2(base + ((size_t)(2 * v) * nq) * kp.n + off, redc(b0[v][0], q, qi), redc(b0[v][1], q, qi));
-            st2(base + ((size_t)(2 * v + 1) * nq) * kp.n + off, redc(b1[v][0], q, qi), redc(b1[v][1], q, qi));
+            st2(P.base + ((size_t)(2 * v) * nq) * kp.n + off, redc(b0[v][0], q, qi), redc(b0[v][1], q, qi));
+            st2(P.base + ((size_t)(2 * v + 1) * nq) * kp.n + off, redc(b1[v][0], q, qi), redc(b1[v][1], q, qi));
+        }
+    }
+}
+
+// ---- TMA-pipelined form: each keyed amount's key tile (2 beta limb segments of 512 words)
+// is copied by cp.async.bulk into a ring of TMA_STAGES shared-memory stages, each signalled
+// by its own mbarrier; thread 0 keeps TMA_STAGES - 1 tiles in flight ahead of the block, so
+// the key stream's latency is covered without holding key words in registers.  Every wait
+// is bounded: on timeout the kernel sets *err, waits (bounded) for its copies in flight and
+// returns.
+constexpr int TMA_TILE = 512;                 // coefficients per block (two per thread)
+constexpr int TMA_STAGES = 3;                 // ring depth (3 x 32 KB at beta = 4: 2 blocks per SM)
+constexpr long long WAIT_LIMIT = 1ll << 24;   // try_wait polls before giving up, at most
+constexpr unsigned long long WAIT_NS = 250000000ull;   // and at most 250 ms of wall time
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned phase) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(phase) : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Gives up after WAIT_NS of wall time (checked every 64 polls) or WAIT_LIMIT polls.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned phase) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < WAIT_LIMIT; it++) {
+        if (mbar_try(bar, phase)) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > WAIT_NS) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load(unsigned dst, const void *src, unsigned bytes, unsigned bar, u64 pol) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar), "l"(pol) : "memory");
+}
+
+template <int V>
+__global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, int n_grp, int *err) {
+    constexpr int NS = TMA_STAGES;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    fgrp P;
+    int tile, t, ptl;
+    if (!grp_pos(kp, grps, n_grp, P, tile, t, ptl)) return;   // block-uniform
+    const int beta = P.beta, n_amt = P.n_amt;
+    const famt *amts = P.amts;
+    const fent *ents = P.ents;
+    u64 *kbuf = (u64 *)smem_raw;                               // [NS stages][2 beta][TMA_TILE]
+    const int seg = 2 * beta;
+    uint64_t *bars = (uint64_t *)(kbuf + (size_t)NS * seg * TMA_TILE);
+    const int k0 = tile * TMA_TILE;
+    const int k = k0 + 2 * threadIdx.x;
+    const int kl = blockIdx.y;
+    const int nq = P.level + 1;
+    const int ext = nq + kp.K;
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 one = to_mont(1, q, qi, r2);
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    const size_t off = (size_t)t * kp.n + k, ptoff = (size_t)ptl * kp.n + k;
+    const unsigned tile_bytes = TMA_TILE * 8;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    if (*(volatile int *)err) return;              // an earlier block already gave up: results invalid
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < NS; st++) mbar_init(smem_u32(&bars[st]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // producer (thread 0): copy the key tile of amount i into stage st
+    auto issue = [&](int i, int st) {
+        const unsigned bar = smem_u32(&bars[st]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, (unsigned)seg * tile_bytes);
+        const u64 *kb = amts[i].key + (size_t)kl * kp.n + k0;
+        for (int sgi = 0; sgi < seg; sgi++)
+            tma_load(smem_u32(kbuf + ((size_t)st * seg + sgi) * TMA_TILE), kb + (size_t)sgi * kstride, tile_bytes, bar,
+                     stream);
+    };
+    int next = 0, issued = 0, used = 0;            // next keyed amount to issue; counts of keyed amounts
+    while (next < n_amt && !amts[next].key) next++;
+    while (issued < NS - 1 && next < n_amt) {      // prologue: NS - 1 tiles in flight
+        if (threadIdx.x == 0) issue(next, issued % NS);
+        issued++;
+        next++;
+        while (next < n_amt && !amts[next].key) next++;
+    }
+    u128 a0[V][2], a1[V][2], b0[V][2], b1[V][2];
+#pragma unroll
+    for (int v = 0; v < V; v++)
+#pragma unroll
+        for (int e = 0; e < 2; e++) a0[v][e] = a1[v][e] = b0[v][e] = b1[v][e] = 0;
+    bool failed = false;
+    for (int i = 0; i < n_amt; i++) {
+        const famt A = amts[i];
+        const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
+        const int sw = ks & 1, kb = ks & ~1;
+        const u64 *kt = nullptr;
+        bool ok = true;
+        if (A.key) {
+            const int st = used % NS;
+            // refill the stage the block released at the end of the previous keyed amount
+            if (next < n_amt) {
+                if (threadIdx.x == 0) issue(next, issued % NS);
+                issued++;
+                next++;
+                while (next < n_amt && !amts[next].key) next++;
+            }
+            ok = mbar_wait_bounded(smem_u32(&bars[st]), (used / NS) & 1);
+            kt = kbuf + (size_t)st * seg * TMA_TILE + 2 * threadIdx.x;
+        }
+        for (int e = A.e0; e < A.e1; e++) {
+            const fent E = ents[e];
+            ulonglong2 p[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const u64 *pp = E.pt[v];
+                p[v] = pp == HE_PT_ONE ? make_ulonglong2(one, one) : (pp ? ld2_hint(pp + ptoff, stream) : make_ulonglong2(0, 0));
+            }
+            if (A.key) {
+                u128 s0[2] = {0, 0}, s1[2] = {0, 0};
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (j < beta) {
+                        const ulonglong2 d = ld2_hint(E.D + ((size_t)j * ext + t) * kp.n + kb, keep);
+                        const u64 d0 = sw ? d.y : d.x, d1 = sw ? d.x : d.y;
+                        const ulonglong2 k0v = *(const ulonglong2 *)(kt + (size_t)(2 * j) * TMA_TILE);
+                        const ulonglong2 k1v = *(const ulonglong2 *)(kt + (size_t)(2 * j + 1) * TMA_TILE);
+                        s0[0] += (u128)d0 * k0v.x;
+                        s0[1] += (u128)d1 * k0v.y;
+                        s1[0] += (u128)d0 * k1v.x;
+                        s1[1] += (u128)d1 * k1v.y;
+                    }
+                const u64 u00 = redc(s0[0], q, qi), u01 = redc(s0[1], q, qi);
+                const u64 u10 = redc(s1[0], q, qi), u11 = redc(s1[1], q, qi);
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    a0[v][0] += (u128)p[v].x * u00;
+                    a0[v][1] += (u128)p[v].y * u01;
+                    a1[v][0] += (u128)p[v].x * u10;
+                    a1[v][1] += (u128)p[v].y * u11;
+                }
+            }
+            if (t < nq) {
+                const ulonglong2 cc = ld2_hint(E.src + (size_t)t * kp.n + kb, keep);
+                const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
+                ulonglong2 c1 = make_ulonglong2(0, 0);
+                if (!A.key) c1 = ld2_hint(E.src + E.ps + off, keep);
+#pragma unroll
+                for (int v = 0; v < V; v++) {
+                    b0[v][0] += (u128)p[v].x * c00;
+                    b0[v][1] += (u128)p[v].y * c01;
+                    b1[v][0] += (u128)p[v].x * c1.x;
+                    b1[v][1] += (u128)p[v].y * c1.y;
+                }
+            }
+        }
+        if (A.key) {
+            used++;
+            // one barrier per keyed amount: it releases the stage for the refill issued next
+            // round and makes the timeout decision block-uniform (a thread whose wait gave up
+            // computed on stale words; the vote discards the block's results)
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+        }
+    }
+    if (failed) {
+        // record it, then let the copies still in flight land (bounded) before the block's
+        // shared memory goes away
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        for (int u = used - 1; u < issued; u++) mbar_wait_bounded(smem_u32(&bars[u % NS]), (u / NS) & 1);
+        return;
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+        st2(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, redc(a0[v][0], q, qi), redc(a0[v][1], q, qi));
+        st2(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
+        if (t < nq) {
+            st2(P.base + ((size_t)(2 * v) * nq) * kp.n + off, redc(b0[v][0], q, qi), redc(b0[v][1], q, qi));
+            st2(P.base + ((size_t)(2 * v + 1) * nq) * kp.n + off, redc(b1[v][0], q, qi), redc(b1[v][1], q, qi));
         }
     }
 }
@@ -1121,18 +1366,216 @@ int k_tensor(const he_ctx *ctx, const he_ct *a, const he_ct *b, u64 *d, cudaStre
     return HE_OK;
 }
 
-int k_ipmac2(const he_ctx *ctx, const fsrc *srcs, const famt *amts, int n_amt, const fent *ents, int V,
-             int level, u64 *acc, u64 *base, double bytes, double mulmods, cudaStream_t s) {
-    const int ext = level + 1 + ctx->K;
-    const int beta = (level + ctx->alpha) / ctx->alpha;
-    if (beta > 8) { he_set_error("fused key switching: at most 8 digits"); return HE_EINVAL; }
-    dim3 g(ctx->n / (2 * TB), ext);
+int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta, double bytes, double mulmods,
+            int form, cudaStream_t s) {
+    if (n_grp <= 0) return HE_OK;
+    if (max_beta > 8) { he_set_error("fused key switching: at most 8 digits"); return HE_EINVAL; }
+    if (V != 1 && V != 2) { he_set_error("k_ipmac: V must be 1 or 2"); return HE_EINVAL; }
+    const int primes = ctx->L + 1 + ctx->K;
     TraceScope tr("ipmac", s, bytes, mulmods);
-#define IPM2(VV, BB) ipmac2_kernel<VV, BB><<<g, TB, 0, s>>>(ctx->kp, srcs, amts, n_amt, ents, level, beta, acc, base)
-    if (V == 1) { if (beta <= 4) IPM2(1, 4); else IPM2(1, 8); }
-    else if (V == 2) { if (beta <= 4) IPM2(2, 4); else IPM2(2, 8); }
-    else { he_set_error("k_ipmac2: V must be 1 or 2"); return HE_EINVAL; }
-#undef IPM2
+    if (form == HE_KEY_STREAM_TMA && max_beta <= 4 && ctx->d_err) {
+        // TMA-pipelined form: TMA_STAGES stages of 2*beta key segments of TMA_TILE words + mbarriers
+        const size_t smem = TMA_STAGES * ((size_t)(2 * max_beta) * TMA_TILE * 8 + 8);
+        const int smem_max = TMA_STAGES * (2 * 4 * TMA_TILE * 8 + 8);
+        static const bool attr_ok =                       // thread-safe one-time opt-in
+            cudaFuncSetAttribute(ipmac_tma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(ipmac_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) ==
+                cudaSuccess;
+        if (!attr_ok) { he_set_error("fused kernel: shared-memory opt-in failed"); return HE_ECUDA; }
+        dim3 gt((unsigned)(ctx->n / TMA_TILE) * n_grp, primes);
+        if (V == 1)
+            ipmac_tma_kernel<1><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, ctx->d_err);
+        else
+            ipmac_tma_kernel<2><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, ctx->d_err);
+        LAUNCH_CHECK();
+        return HE_OK;
+    }
+    dim3 g((unsigned)(ctx->n / (2 * TB)) * n_grp, primes);
+#define IPM(VV, BB) ipmac_kernel<VV, BB><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp)
+    if (V == 1) { if (max_beta <= 4) IPM(1, 4); else IPM(1, 8); }
+    else { if (max_beta <= 4) IPM(2, 4); else IPM(2, 8); }
+#undef IPM
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+// ---- split form: amount-major inner products, then the raised-basis MAC
+// One coefficient per thread.  Block -> (group, tile, prime) as in grp_pos.
+__device__ __forceinline__ bool lvl_pos(const KP &kp, int level, int &t) {
+    const int kl = blockIdx.y;
+    if (kl <= kp.L) {
+        if (kl > level) return false;
+        t = kl;
+    } else {
+        t = level + 1 + (kl - kp.L - 1);
+    }
+    return true;
+}
+
+template <int B>
+__global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps, int n_grp) {
+    const ugrp P = grps[blockIdx.x % n_grp];
+    const int tile = blockIdx.x / n_grp;
+    int t;
+    if (!lvl_pos(kp, P.level, t)) return;
+    const int k = tile * TB + threadIdx.x;
+    const int kl = blockIdx.y;
+    const int ext = P.level + 1 + kp.K;
+    const int beta = P.beta;
+    const u64 q = kp.q[kl], qi = kp.qinv[kl];
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    for (int i = 0; i < P.n_amt; i++) {
+        const famt A = P.amts[i];
+        const int ks = autom_index(k, A.g, kp.logn);
+        u64 k0[B], k1[B];
+#pragma unroll
+        for (int j = 0; j < B; j++)
+            if (j < beta) {
+                const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+                asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(k0[j]) : "l"(kp0), "l"(stream));
+                asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(k1[j]) : "l"(kp0 + kstride), "l"(stream));
+            }
+        for (int e = A.e0; e < A.e1; e++) {
+            const uent E = P.ents[e];
+            u128 a0 = 0, a1 = 0;
+#pragma unroll
+            for (int j = 0; j < B; j++)
+                if (j < beta) {
+                    u64 d;
+                    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;"
+                                 : "=l"(d) : "l"(E.D + ((size_t)j * ext + t) * kp.n + ks), "l"(keep));
+                    a0 += (u128)d * k0[j];
+                    a1 += (u128)d * k1[j];
+                }
+            E.U[(size_t)t * kp.n + k] = redc(a0, q, qi);
+            E.U[((size_t)ext + t) * kp.n + k] = redc(a1, q, qi);
+        }
+    }
+}
+
+__device__ __forceinline__ u64 ld_hint(const u64 *p, u64 pol) {
+    u64 r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+    return r;
+}
+
+// acc_v = sum_terms pt_v (.) U (Q u P), base_v = sum_terms pt_v (.) phi(c0) (+ pt_v (.) c1 for the
+// amount-0 terms) over Q; HE_RV outputs per thread, the next term's words loaded while the
+// current one is accumulated.
+__global__ void __launch_bounds__(TB) rmac_kernel(KP kp, const rgrp *grps, int n_grp) {
+    constexpr int RV = HE_RV;
+    const rgrp P = grps[blockIdx.x % n_grp];
+    const int tile = blockIdx.x / n_grp;
+    int t;
+    if (!lvl_pos(kp, P.level, t)) return;
+    const int k = tile * TB + threadIdx.x;
+    const int kl = blockIdx.y;
+    const int nq = P.level + 1, ext = nq + kp.K;
+    const int ptl = kl <= kp.L ? kl : P.pt_level + 1 + (kl - kp.L - 1);
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 one = to_mont(1, q, qi, r2);
+    const size_t off = (size_t)t * kp.n + k, ptoff = (size_t)ptl * kp.n + k;
+    const bool isq = t < nq;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    u128 a0[RV], a1[RV], b0[RV], b1[RV];
+#pragma unroll
+    for (int v = 0; v < RV; v++) a0[v] = a1[v] = b0[v] = b1[v] = 0;
+    // words of term i: u0, u1 (raised), c0 (gathered), c1 (amount 0), pt[RV]
+    auto fetch = [&](int i, u64 &u0, u64 &u1, u64 &c0, u64 &c1, u64 (&p)[RV]) {
+        const rterm T = P.terms[i];
+        u0 = u1 = c0 = c1 = 0;
+        if (T.U) {
+            u0 = ld_hint(T.U + off, stream);
+            u1 = ld_hint(T.U + (size_t)ext * kp.n + off, stream);
+        }
+        if (isq) {
+            const int ks = T.g == 1 ? k : autom_index(k, T.g, kp.logn);
+            c0 = ld_hint(T.src + (size_t)t * kp.n + ks, keep);
+            if (!T.U) c1 = ld_hint(T.src + T.ps + off, keep);
+        }
+#pragma unroll
+        for (int v = 0; v < RV; v++) {
+            const u64 *pp = T.pt[v];
+            p[v] = pp == HE_PT_ONE ? one : (pp ? ld_hint(pp + ptoff, stream) : 0);
+        }
+    };
+    u64 u0, u1, c0, c1, p[RV];
+    if (P.n_terms > 0) fetch(0, u0, u1, c0, c1, p);
+    for (int i = 0; i < P.n_terms; i++) {
+        u64 nu0 = 0, nu1 = 0, nc0 = 0, nc1 = 0, np_[RV];
+#pragma unroll
+        for (int v = 0; v < RV; v++) np_[v] = 0;
+        if (i + 1 < P.n_terms) fetch(i + 1, nu0, nu1, nc0, nc1, np_);
+#pragma unroll
+        for (int v = 0; v < RV; v++) {
+            a0[v] += (u128)p[v] * u0;
+            a1[v] += (u128)p[v] * u1;
+            b0[v] += (u128)p[v] * c0;
+            b1[v] += (u128)p[v] * c1;
+        }
+        u0 = nu0; u1 = nu1; c0 = nc0; c1 = nc1;
+#pragma unroll
+        for (int v = 0; v < RV; v++) p[v] = np_[v];
+    }
+    // a later chunk of amounts adds its partial sums modulo q: same residues as one pass
+    auto put = [&](u64 *dst, u128 acc) {
+        u64 r = redc(acc, q, qi);
+        if (P.accumulate) {
+            r += *dst;
+            if (r >= q) r -= q;
+        }
+        *dst = r;
+    };
+#pragma unroll
+    for (int v = 0; v < RV; v++) {
+        put(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, a0[v]);
+        put(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, a1[v]);
+        if (isq) {
+            put(P.base + ((size_t)(2 * v) * nq) * kp.n + off, b0[v]);
+            put(P.base + ((size_t)(2 * v + 1) * nq) * kp.n + off, b1[v]);
+        }
+    }
+}
+
+int k_ip_amounts(const he_ctx *ctx, const ugrp *grps, int n_grp, int max_beta, double bytes, cudaStream_t s) {
+    if (n_grp <= 0) return HE_OK;
+    if (max_beta > 8) { he_set_error("inner products: at most 8 digits"); return HE_EINVAL; }
+    TraceScope tr("ip_amounts", s, bytes, 0);
+    dim3 g((unsigned)(ctx->n / TB) * n_grp, ctx->L + 1 + ctx->K);
+    if (max_beta <= 4) ip_amounts_kernel<4><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp);
+    else ip_amounts_kernel<8><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+int k_rmac(const he_ctx *ctx, const rgrp *grps, int n_grp, double bytes, double mulmods, cudaStream_t s) {
+    if (n_grp <= 0) return HE_OK;
+    TraceScope tr("rmac", s, bytes, mulmods);
+    dim3 g((unsigned)(ctx->n / TB) * n_grp, ctx->L + 1 + ctx->K);
+    rmac_kernel<<<g, TB, 0, s>>>(ctx->kp, grps, n_grp);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+// Failure-path self-test: one warp waits (bounded, like the key-tile pipeline) on an mbarrier
+// that nothing will ever arrive on; the wait gives up, the kernel records the timeout in the
+// context's error word and returns, leaving the context usable.
+__global__ void bounded_wait_selftest_kernel(int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(smem_u32(&bar), 0);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+int k_selftest_bounded_wait(const he_ctx *ctx, cudaStream_t s) {
+    if (!ctx->d_err) { he_set_error("context has no error word"); return HE_ESTATE; }
+    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(ctx->d_err);
     LAUNCH_CHECK();
     return HE_OK;
 }

@@ -12,6 +12,8 @@
 #include <cmath>
 #include <thread>
 #include <unordered_map>
+#include <set>
+#include <tuple>
 
 #include "internal.h"
 
@@ -266,6 +268,7 @@ template <class T>
 int dev_alloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) return HE_OK;
+    HE_TRY(he_capture_guard("device allocation"));
     if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -442,67 +445,125 @@ struct RotSet {
 // One stage of weighted hoisted rotations: out_v = sum_{(s, a)} pt_{v,s,a} (.) rot_a(src_s),
 // evaluated in the raised basis: every rotation's inner product is accumulated with its
 // plaintext over Q u P (keys read once per amount and output group) and each output takes one
-// ModDown.  Outputs are left unrescaled at the stage level.
+// ModDown.  Outputs are left unrescaled at the stage level.  A stage's groups (V outputs
+// each) go into a FusedLaunch, which may also carry the groups of other stages (other images,
+// other levels) so that all of them are served by one kernel launch.
+struct FusedLaunch;
+
 struct FusedStage {
     he_ctx *c = nullptr;
     int level = 0;
+    int pt_level = -1;                                // layout of the plaintexts (default: level)
     struct Src { u64 *d; size_t ps; bool rotated; };
     std::vector<Src> srcs;
     struct Term { int v, s, a; const u64 *pt; };
     std::vector<Term> terms;
     std::vector<std::pair<u64 *, size_t>> outs;      // output data and poly stride
     struct Group {
-        int V = 1, n_amt = 0;
         std::vector<int> outs;
-        fsrc *d_src = nullptr;
         famt *d_amt = nullptr;
         fent *d_ent = nullptr;
-        md_item *d_md = nullptr;
+        fgrp desc{};
         double bytes = 0, mulmods = 0;
     };
-    std::vector<Group> groups;
+    std::vector<Group> groups;                        // for outputs-per-key-pass Vg
     std::vector<int> hslot;                           // source -> slot in D_all (-1: not rotated)
-    u64 *D_all = nullptr, *facc = nullptr, *fbase = nullptr, *fconv = nullptr;
+    u64 *D_all = nullptr;
+    u64 *facc = nullptr, *fbase = nullptr, *fconv = nullptr;   // [nout][2][ext|nq|nq][n]
+    md_item *d_md = nullptr;
     bool ready = false;
+    int Vg = 0;
+    std::string name = "stage";
+    std::unique_ptr<FusedLaunch> own;                 // launch of this stage alone
+    // split form: chunks of keyed amounts (inner products into U, then the raised MAC)
+    struct Chunk {
+        famt *d_amt = nullptr;
+        uent *d_ent = nullptr;
+        ugrp udesc{};
+        std::vector<rterm *> d_terms;                 // per output group of HE_RV
+        std::vector<rgrp> rdesc;
+        double ubytes = 0, rbytes = 0, rmm = 0;
+    };
+    std::vector<Chunk> chunks;
+    u64 *U = nullptr;                                 // [slots][2][ext][n] of the largest chunk
+    bool split_ready = false;
 
-    ~FusedStage() {
-        for (auto &g : groups) { cudaFree(g.d_src); cudaFree(g.d_amt); cudaFree(g.d_ent); cudaFree(g.d_md); }
-        cudaFree(D_all); cudaFree(facc); cudaFree(fbase); cudaFree(fconv);
+    ~FusedStage();
+    void free_split() {
+        for (auto &ch : chunks) {
+            cudaFree(ch.d_amt); cudaFree(ch.d_ent);
+            for (auto *t : ch.d_terms) cudaFree(t);
+        }
+        chunks.clear();
+        cudaFree(U);
+        U = nullptr;
+        split_ready = false;
+    }
+    size_t split_bytes() const;                       // device memory the split form needs
+    int build_split(size_t cap_bytes);
+    void free_groups() {
+        for (auto &g : groups) { cudaFree(g.d_amt); cudaFree(g.d_ent); }
+        groups.clear();
+        Vg = 0;
     }
     int add_src(u64 *d, size_t ps) { srcs.push_back({d, ps, false}); return (int)srcs.size() - 1; }
     int add_out(u64 *d, size_t ps) { outs.push_back({d, ps}); return (int)outs.size() - 1; }
     void add_term(int v, int s, int a, const u64 *pt) { terms.push_back({v, s, ((a % c->N) + c->N) % c->N, pt}); }
+    int nq() const { return level + 1; }
+    int ext() const { return level + 1 + c->K; }
+    int beta() const { return (level + c->alpha) / c->alpha; }
 
     int build() {
         if (ready) return HE_OK;
-        const int nq = level + 1, ext = nq + c->K, beta = (level + c->alpha) / c->alpha;
-        const size_t n = c->n;
+        if (pt_level < 0) pt_level = level;
+        if (pt_level < level || pt_level > c->L) { he_set_error("fused stage: plaintext level below the stage"); return HE_EINVAL; }
+        const size_t n = c->n, nout = outs.size();
         for (auto &t : terms)
             if (h_galois(c, t.a) != 1) srcs[t.s].rotated = true;
         hslot.assign(srcs.size(), -1);
         int nh = 0;
         for (size_t i = 0; i < srcs.size(); i++)
             if (srcs[i].rotated) hslot[i] = nh++;
-        HE_TRY(dev_alloc(&D_all, (size_t)nh * beta * ext * n));
-        const int nout = (int)outs.size();
-        const int V = nout >= 2 ? 2 : 1;
-        HE_TRY(dev_alloc(&facc, (size_t)V * 2 * ext * n));
-        HE_TRY(dev_alloc(&fbase, (size_t)V * 2 * nq * n));
-        HE_TRY(dev_alloc(&fconv, (size_t)V * 2 * nq * n));
-        std::vector<fsrc> hs(srcs.size());
+        HE_TRY(dev_alloc(&D_all, (size_t)nh * beta() * ext() * n));
+        // room for whole groups: a group whose last outputs are absent still stores their (zero)
+        // accumulators, so the output count is padded to a multiple of every group width (2, HE_RV)
+        const size_t nslot = (nout + HE_RV - 1) / HE_RV * HE_RV;
+        HE_TRY(dev_alloc(&facc, nslot * 2 * ext() * n));
+        HE_TRY(dev_alloc(&fbase, nslot * 2 * nq() * n));
+        HE_TRY(dev_alloc(&fconv, nslot * 2 * nq() * n));
+        std::vector<md_item> md;
+        for (size_t v = 0; v < nout; v++)
+            md.push_back(md_item{facc + v * 2 * ext() * n, fconv + v * 2 * nq() * n, fbase + v * 2 * nq() * n,
+                                 (size_t)nq() * n, 2, 1, outs[v].first, outs[v].second});
+        HE_TRY(dev_alloc(&d_md, std::max<size_t>(1, md.size())));
+        if (!md.empty()) HE_CHECK_CUDA(cudaMemcpy(d_md, md.data(), md.size() * sizeof(md_item), cudaMemcpyHostToDevice));
+        ready = true;
+        return HE_OK;
+    }
+
+    // Groups of V outputs, each one group of the fused kernel: every key is streamed once for
+    // the group's V outputs (and, through L2, for the neighbouring groups of the same launch).
+    int build_groups(int V) {
+        HE_TRY(build());
+        if (V == Vg && !groups.empty()) return HE_OK;
+        free_groups();
+        Vg = V;
+        const int nq_ = nq(), ext_ = ext(), beta_ = beta();
+        const size_t n = c->n;
+        int nh = 0;
+        for (int h : hslot) nh += h >= 0;
+        std::vector<const u64 *> Dp(srcs.size());
         for (size_t i = 0; i < srcs.size(); i++)
-            hs[i] = fsrc{hslot[i] >= 0 ? D_all + (size_t)hslot[i] * beta * ext * n : nullptr, srcs[i].d, srcs[i].ps};
+            Dp[i] = hslot[i] >= 0 ? D_all + (size_t)hslot[i] * beta_ * ext_ * n : nullptr;
+        const int nout = (int)outs.size();
         for (int v0 = 0; v0 < nout; v0 += V) {
             Group G;
-            G.V = V;
             for (int v = v0; v < std::min(nout, v0 + V); v++) G.outs.push_back(v);
             // amount -> source -> per-output plaintexts
             std::map<int, std::map<int, fent>> m;
             for (auto &t : terms) {
-                int vi = -1;
-                for (size_t k = 0; k < G.outs.size(); k++)
-                    if (G.outs[k] == t.v) vi = (int)k;
-                if (vi < 0) continue;
+                if (t.v < v0 || t.v >= v0 + V) continue;
+                const int vi = t.v - v0;
                 fent &e = m[t.a][t.s];
                 e.s = t.s;
                 if (e.pt[vi]) { he_set_error("fused stage: duplicate term"); return HE_EINVAL; }
@@ -519,66 +580,428 @@ struct FusedStage {
                     const DeviceKey *k;
                     HE_TRY(get_key(c, (int)A.g, &k));
                     A.key = k->d;
-                    bytes += (double)2 * beta * ext * n * 8;
+                    bytes += (double)2 * beta_ * ext_ * n * 8;
                 }
                 A.e0 = (int)he.size();
                 for (auto &se : am.second) {
                     fent E = se.second;
-                    E.D = hs[E.s].D;
-                    E.src = hs[E.s].src;
-                    E.ps = hs[E.s].ps;
+                    E.D = Dp[E.s];
+                    E.src = srcs[E.s].d;
+                    E.ps = srcs[E.s].ps;
                     he.push_back(E);
                     for (int vi = 0; vi < V; vi++)
-                        if (se.second.pt[vi] && se.second.pt[vi] != HE_PT_ONE) bytes += (double)(A.key ? ext : nq) * n * 8;
-                    mm += (double)(A.key ? ext : nq) * n * (A.key ? 2 * beta + 2 * V : 2 * V);
+                        if (se.second.pt[vi] && se.second.pt[vi] != HE_PT_ONE) bytes += (double)(A.key ? ext_ : nq_) * n * 8;
+                    mm += (double)(A.key ? ext_ : nq_) * n * (A.key ? 2 * beta_ + 2 * V : 2 * V);
                 }
                 A.e1 = (int)he.size();
                 ha.push_back(A);
             }
-            bytes += (double)nh * beta * ext * n * 8 + (double)srcs.size() * 2 * nq * n * 8 +
-                     (double)G.outs.size() * 2 * (ext + nq) * n * 8;
+            bytes += (double)nh * beta_ * ext_ * n * 8 / std::max(1, (nout + V - 1) / V) +
+                     (double)srcs.size() * 2 * nq_ * n * 8 / std::max(1, (nout + V - 1) / V) +
+                     (double)G.outs.size() * 2 * (ext_ + nq_) * n * 8;
             G.bytes = bytes;
             G.mulmods = mm;
-            G.n_amt = (int)ha.size();
-            HE_TRY(dev_alloc(&G.d_src, hs.size()));
             HE_TRY(dev_alloc(&G.d_amt, std::max<size_t>(1, ha.size())));
             HE_TRY(dev_alloc(&G.d_ent, std::max<size_t>(1, he.size())));
-            HE_CHECK_CUDA(cudaMemcpy(G.d_src, hs.data(), hs.size() * sizeof(fsrc), cudaMemcpyHostToDevice));
             if (!ha.empty()) HE_CHECK_CUDA(cudaMemcpy(G.d_amt, ha.data(), ha.size() * sizeof(famt), cudaMemcpyHostToDevice));
             if (!he.empty()) HE_CHECK_CUDA(cudaMemcpy(G.d_ent, he.data(), he.size() * sizeof(fent), cudaMemcpyHostToDevice));
-            std::vector<md_item> md;
-            for (size_t vi = 0; vi < G.outs.size(); vi++)
-                md.push_back(md_item{facc + vi * 2 * ext * n, fconv + vi * 2 * nq * n, fbase + vi * 2 * nq * n,
-                                     (size_t)nq * n, 2, 1, outs[G.outs[vi]].first, outs[G.outs[vi]].second});
-            HE_TRY(dev_alloc(&G.d_md, md.size()));
-            HE_CHECK_CUDA(cudaMemcpy(G.d_md, md.data(), md.size() * sizeof(md_item), cudaMemcpyHostToDevice));
+            G.desc = fgrp{G.d_amt, G.d_ent, (int)ha.size(), level, beta_, pt_level,
+                          facc + (size_t)v0 * 2 * ext_ * n, fbase + (size_t)v0 * 2 * nq_ * n};
             groups.push_back(G);
         }
-        ready = true;
+        return HE_OK;
+    }
+
+    int hoist(cudaStream_t s) {
+        for (size_t i = 0; i < srcs.size(); i++)
+            if (hslot[i] >= 0) {
+                he_ct t = view(c, srcs[i].d, srcs[i].ps, level, 1.0);
+                HE_TRY(hoist_modup(c, &t, D_all + (size_t)hslot[i] * beta() * ext() * c->n, s));
+            }
+        return HE_OK;
+    }
+
+    // one ModDown pipeline for every output of the stage
+    int moddown(cudaStream_t s) {
+        const int nv = (int)outs.size();
+        if (nv == 0) return HE_OK;
+        ntt_job jp{facc, (size_t)ext() * c->n, nq(), c->K, nq(), 0, 2 * nv, 0};
+        HE_TRY(k_ntt(c, jp, true, s));
+        HE_TRY(k_moddown_fbc(c, facc, fconv, level, 2 * nv, s));
+        ntt_job jc{fconv, (size_t)nq() * c->n, 0, nq(), nq(), 0, 2 * nv, 0};
+        HE_TRY(k_ntt(c, jc, false, s));
+        return k_moddown_combine(c, d_md, nv, level, s);
+    }
+
+    int run(cudaStream_t s);
+};
+
+// One fused-kernel launch over the groups of one or more stages.  Autotuner: the candidates
+// (outputs per key pass V, key stream) give the same bits, so the first run times each one's
+// launch (one warm-up pass, then the best of two timed passes, CUDA events on the launch's
+// stream) and keeps the fastest.  Needs the raised digits in place: called after the hoisted
+// ModUps of the first run.
+struct FusedLaunch {
+    he_ctx *c = nullptr;
+    std::vector<FusedStage *> st;
+    fgrp *d_grps = nullptr;
+    int G = 0, V = 0, max_beta = 0;
+    int form = HE_KEY_STREAM_LDG;
+    bool tuned = false;
+    bool use_split = false;                           // split form chosen by the autotuner
+    double bytes = 0, mulmods = 0;
+    std::string name;
+    // split form: per amount chunk, the inner-product and raised-MAC group tables
+    std::vector<ugrp *> d_ugrps;
+    std::vector<rgrp *> d_rgrps;
+    std::vector<int> n_ugrp, n_rgrp;
+    std::vector<double> ubytes, rbytes, rmm;
+    bool split_built = false;
+
+    ~FusedLaunch() { cudaFree(d_grps); free_split_tables(); }
+    void free_split_tables() {
+        for (auto *p : d_ugrps) cudaFree(p);
+        for (auto *p : d_rgrps) cudaFree(p);
+        d_ugrps.clear(); d_rgrps.clear(); n_ugrp.clear(); n_rgrp.clear();
+        ubytes.clear(); rbytes.clear(); rmm.clear();
+        split_built = false;
+    }
+    int vmax() const {
+        for (auto *f : st)
+            if (f->outs.size() >= 2) return 2;
+        return 1;
+    }
+
+    int build(int Vsel) {
+        if (Vsel == V && d_grps) return HE_OK;
+        std::vector<fgrp> h;
+        bytes = mulmods = 0;
+        max_beta = 0;
+        for (auto *f : st) {
+            HE_TRY(f->build_groups(Vsel));
+            for (auto &g : f->groups) {
+                h.push_back(g.desc);
+                bytes += g.bytes;
+                mulmods += g.mulmods;
+            }
+            max_beta = std::max(max_beta, f->beta());
+        }
+        cudaFree(d_grps);
+        d_grps = nullptr;
+        HE_TRY(dev_alloc(&d_grps, std::max<size_t>(1, h.size())));
+        if (!h.empty()) HE_CHECK_CUDA(cudaMemcpy(d_grps, h.data(), h.size() * sizeof(fgrp), cudaMemcpyHostToDevice));
+        G = (int)h.size();
+        V = Vsel;
+        return HE_OK;
+    }
+
+    size_t split_need() const {
+        size_t b = 0;
+        for (auto *f : st) b += f->split_bytes();
+        return b;
+    }
+
+    int build_split() {
+        if (split_built) return HE_OK;
+        size_t nch = 0;
+        for (auto *f : st) {
+            HE_TRY(f->build_split((size_t)2 << 30));
+            nch = std::max(nch, f->chunks.size());
+        }
+        for (size_t ci = 0; ci < nch; ci++) {
+            std::vector<ugrp> hu;
+            std::vector<rgrp> hr;
+            double ub = 0, rb = 0, mm = 0;
+            for (auto *f : st) {
+                if (ci >= f->chunks.size()) continue;
+                auto &ch = f->chunks[ci];
+                hu.push_back(ch.udesc);
+                for (auto &r : ch.rdesc) hr.push_back(r);
+                ub += ch.ubytes;
+                rb += ch.rbytes;
+                mm += ch.rmm;
+            }
+            ugrp *du = nullptr;
+            rgrp *dr = nullptr;
+            HE_TRY(dev_alloc(&du, std::max<size_t>(1, hu.size())));
+            HE_TRY(dev_alloc(&dr, std::max<size_t>(1, hr.size())));
+            if (!hu.empty()) HE_CHECK_CUDA(cudaMemcpy(du, hu.data(), hu.size() * sizeof(ugrp), cudaMemcpyHostToDevice));
+            if (!hr.empty()) HE_CHECK_CUDA(cudaMemcpy(dr, hr.data(), hr.size() * sizeof(rgrp), cudaMemcpyHostToDevice));
+            d_ugrps.push_back(du);
+            d_rgrps.push_back(dr);
+            n_ugrp.push_back((int)hu.size());
+            n_rgrp.push_back((int)hr.size());
+            ubytes.push_back(ub);
+            rbytes.push_back(rb);
+            rmm.push_back(mm);
+        }
+        split_built = true;
+        return HE_OK;
+    }
+
+    int launch(int fm, cudaStream_t s) { return k_ipmac(c, d_grps, G, V, max_beta, bytes, mulmods, fm, s); }
+    int launch_split(cudaStream_t s) {
+        int mb = 0;
+        for (auto *f : st) mb = std::max(mb, f->beta());
+        for (size_t ci = 0; ci < d_ugrps.size(); ci++) {
+            HE_TRY(k_ip_amounts(c, d_ugrps[ci], n_ugrp[ci], mb, ubytes[ci], s));
+            HE_TRY(k_rmac(c, d_rgrps[ci], n_rgrp[ci], rbytes[ci], rmm[ci], s));
+        }
+        return HE_OK;
+    }
+
+    // candidates: the fused kernel (V outputs per key pass, key stream) and the split form
+    int tune(cudaStream_t s) {
+        std::vector<int> forms = {HE_KEY_STREAM_LDG};
+        if (max_beta <= 4 && c->d_err) forms.push_back(HE_KEY_STREAM_TMA);
+        std::vector<int> Vs = {vmax()};
+        if (vmax() == 2) Vs.push_back(1);
+        bool try_split = false;
+        if (!he_capturing()) {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && split_need() + ((size_t)4 << 30) < fr) try_split = true;
+            cudaGetLastError();
+        }
+        if ((forms.size() == 1 && Vs.size() == 1 && !try_split) || he_capturing()) {
+            // nothing to choose, or no timing possible inside a graph capture: keep the built
+            // groups (a captured graph refers to them, so they are never rebuilt afterwards)
+            form = forms[0];
+            tuned = true;
+            return HE_OK;
+        }
+        cudaEvent_t e0, e1;
+        HE_CHECK_CUDA(cudaEventCreate(&e0));
+        HE_CHECK_CUDA(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int bestV = Vs[0], bestF = forms[0];
+        bool bestSplit = false;
+        char line[640];
+        int pos = snprintf(line, sizeof(line), "%s (%zu stage(s), level %d, %zu outputs):", name.c_str(), st.size(),
+                           st.empty() ? 0 : st[0]->level, st.empty() ? (size_t)0 : st[0]->outs.size());
+        int rc = HE_OK;
+        // time fn() once warm, best of two
+        auto time_it = [&](auto fn, float &t) -> int {
+            t = 1e30f;
+            HE_TRY(fn());
+            for (int rep = 0; rep < 2; rep++) {
+                float ms = 0;
+                if (cudaEventRecord(e0, s) != cudaSuccess) { cudaGetLastError(); he_set_error("autotuner: event"); return HE_ECUDA; }
+                HE_TRY(fn());
+                if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                    cudaGetLastError();
+                    he_set_error("autotuner: event timing failed");
+                    return HE_ECUDA;
+                }
+                t = std::min(t, ms);
+            }
+            return HE_OK;
+        };
+        for (int Vc : Vs) {
+            if ((rc = build(Vc)) != HE_OK) break;
+            for (int fm : forms) {
+                float t;
+                if ((rc = time_it([&]() { return launch(fm, s); }, t)) != HE_OK) break;
+                if (pos < (int)sizeof(line))
+                    pos += snprintf(line + pos, sizeof(line) - pos, " V=%d %s %.3f ms;", Vc,
+                                    fm == HE_KEY_STREAM_TMA ? "tma" : "ldg", t);
+                if (t < best) { best = t; bestV = Vc; bestF = fm; bestSplit = false; }
+            }
+            if (rc != HE_OK) break;
+        }
+        if (rc == HE_OK && try_split) {
+            float t;
+            rc = build_split();
+            if (rc == HE_OK) rc = time_it([&]() { return launch_split(s); }, t);
+            if (rc == HE_OK) {
+                if (pos < (int)sizeof(line))
+                    pos += snprintf(line + pos, sizeof(line) - pos, " split (%zu chunk(s)) %.3f ms;", d_ugrps.size(), t);
+                if (t < best) { best = t; bestSplit = true; }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        HE_TRY(rc);
+        if (bestSplit) {
+            use_split = true;
+            cudaFree(d_grps);                         // the fused tables are not needed
+            d_grps = nullptr;
+        } else {
+            HE_TRY(build(bestV));
+            form = bestF;
+            if (split_built) {                        // give the split form's memory back
+                free_split_tables();
+                for (auto *f : st) f->free_split();
+            }
+        }
+        tuned = true;
+        if (pos < (int)sizeof(line)) {
+            if (bestSplit) snprintf(line + pos, sizeof(line) - pos, " -> split");
+            else snprintf(line + pos, sizeof(line) - pos, " -> V=%d %s", bestV, bestF == HE_KEY_STREAM_TMA ? "tma" : "ldg");
+        }
+        he_tune_note(c, line);
         return HE_OK;
     }
 
     int run(cudaStream_t s) {
-        HE_TRY(build());
-        const int nq = level + 1, ext = nq + c->K, beta = (level + c->alpha) / c->alpha;
-        for (size_t i = 0; i < srcs.size(); i++)
-            if (hslot[i] >= 0) {
-                he_ct t = view(c, srcs[i].d, srcs[i].ps, level, 1.0);
-                HE_TRY(hoist_modup(c, &t, D_all + (size_t)hslot[i] * beta * ext * c->n, s));
-            }
-        for (auto &G : groups) {
-            const int nv = (int)G.outs.size();
-            HE_TRY(k_ipmac2(c, G.d_src, G.d_amt, G.n_amt, G.d_ent, G.V, level, facc, fbase, G.bytes, G.mulmods, s));
-            ntt_job jp{facc, (size_t)ext * c->n, nq, c->K, nq, 0, 2 * nv, 0};
-            HE_TRY(k_ntt(c, jp, true, s));
-            HE_TRY(k_moddown_fbc(c, facc, fconv, level, 2 * nv, s));
-            ntt_job jc{fconv, (size_t)nq * c->n, 0, nq, nq, 0, 2 * nv, 0};
-            HE_TRY(k_ntt(c, jc, false, s));
-            HE_TRY(k_moddown_combine(c, G.d_md, nv, level, s));
+        const int opt = c->key_stream;
+        for (auto *f : st) HE_TRY(f->hoist(s));
+        if (opt == HE_KEY_STREAM_SPLIT) {                       // explicit split form
+            HE_TRY(build_split());
+            HE_TRY(launch_split(s));
+        } else if (opt != HE_KEY_STREAM_AUTO) {                 // explicit fused form
+            if (!d_grps) HE_TRY(build(V ? V : vmax()));
+            HE_TRY(launch(opt, s));
+        } else {
+            if (!d_grps && !use_split) HE_TRY(build(vmax()));
+            if (!tuned) HE_TRY(tune(s));
+            if (use_split) HE_TRY(launch_split(s));
+            else HE_TRY(launch(form, s));
         }
+        for (auto *f : st) HE_TRY(f->moddown(s));
         return HE_OK;
     }
 };
+
+// Amount chunks of the split form: each chunk's inner products fit in cap_bytes of U.
+static std::vector<std::vector<std::pair<int, std::vector<int>>>> split_plan(
+    const FusedStage &f, size_t slot_bytes, size_t cap_bytes) {
+    // keyed amount -> sources, in amount order
+    std::map<int, std::set<int>> am;
+    for (auto &t : f.terms)
+        if (h_galois(f.c, t.a) != 1) am[t.a].insert(t.s);
+    std::vector<std::vector<std::pair<int, std::vector<int>>>> out(1);
+    size_t used = 0;
+    for (auto &kv : am) {
+        const size_t need = kv.second.size() * slot_bytes;
+        if (used + need > cap_bytes && !out.back().empty()) {
+            out.emplace_back();
+            used = 0;
+        }
+        out.back().push_back({kv.first, std::vector<int>(kv.second.begin(), kv.second.end())});
+        used += need;
+    }
+    return out;
+}
+
+size_t FusedStage::split_bytes() const {
+    const size_t slot = (size_t)2 * ext() * c->n * 8;
+    size_t best = 0;
+    for (auto &ch : split_plan(*this, slot, (size_t)2 << 30)) {
+        size_t k = 0;
+        for (auto &a : ch) k += a.second.size();
+        best = std::max(best, k * slot);
+    }
+    return best;
+}
+
+int FusedStage::build_split(size_t cap_bytes) {
+    if (split_ready) return HE_OK;
+    HE_TRY(build());
+    const int nq_ = nq(), ext_ = ext(), beta_ = beta();
+    const size_t n = c->n, slot = (size_t)2 * ext_ * n;
+    std::vector<const u64 *> Dp(srcs.size());
+    for (size_t i = 0; i < srcs.size(); i++)
+        Dp[i] = hslot[i] >= 0 ? D_all + (size_t)hslot[i] * beta_ * ext_ * n : nullptr;
+    auto plan = split_plan(*this, slot * 8, cap_bytes);
+    size_t max_slots = 0;
+    for (auto &ch : plan) {
+        size_t k = 0;
+        for (auto &a : ch) k += a.second.size();
+        max_slots = std::max(max_slots, k);
+    }
+    HE_TRY(dev_alloc(&U, std::max<size_t>(1, max_slots) * slot));
+    // term lookup: (v, s, a) -> plaintext
+    std::map<std::tuple<int, int, int>, const u64 *> pt_of;
+    for (auto &t : terms) pt_of[std::make_tuple(t.v, t.s, t.a)] = t.pt;
+    const int nout = (int)outs.size();
+    for (size_t ci = 0; ci < plan.size(); ci++) {
+        Chunk ch;
+        std::vector<famt> ha;
+        std::vector<uent> he;
+        std::map<std::pair<int, int>, u64 *> uslot;   // (a, s) -> U slot
+        for (auto &a : plan[ci]) {
+            famt A;
+            A.g = h_galois(c, a.first);
+            const DeviceKey *k;
+            HE_TRY(get_key(c, (int)A.g, &k));
+            A.key = k->d;
+            A.e0 = (int)he.size();
+            for (int sidx : a.second) {
+                u64 *u = U + he.size() * slot;
+                he.push_back(uent{Dp[sidx], u});
+                uslot[{a.first, sidx}] = u;
+            }
+            A.e1 = (int)he.size();
+            ha.push_back(A);
+            ch.ubytes += (double)2 * beta_ * ext_ * n * 8 + (double)(A.e1 - A.e0) * slot * 8;
+        }
+        HE_TRY(dev_alloc(&ch.d_amt, std::max<size_t>(1, ha.size())));
+        HE_TRY(dev_alloc(&ch.d_ent, std::max<size_t>(1, he.size())));
+        if (!ha.empty()) HE_CHECK_CUDA(cudaMemcpy(ch.d_amt, ha.data(), ha.size() * sizeof(famt), cudaMemcpyHostToDevice));
+        if (!he.empty()) HE_CHECK_CUDA(cudaMemcpy(ch.d_ent, he.data(), he.size() * sizeof(uent), cudaMemcpyHostToDevice));
+        ch.udesc = ugrp{ch.d_amt, ch.d_ent, (int)ha.size(), level, beta_};
+        // raised MAC terms per group of HE_RV outputs: this chunk's (a, s) pairs, plus the
+        // amount-0 terms in chunk 0
+        for (int v0 = 0; v0 < nout; v0 += HE_RV) {
+            std::map<std::pair<int, int>, rterm> tm;
+            for (auto &t : terms) {
+                if (t.v < v0 || t.v >= v0 + HE_RV) continue;
+                const bool keyed = h_galois(c, t.a) != 1;
+                u64 *u = nullptr;
+                if (keyed) {
+                    auto it = uslot.find({t.a, t.s});
+                    if (it == uslot.end()) continue;          // another chunk
+                    u = it->second;
+                } else if (ci != 0) {
+                    continue;
+                }
+                rterm &r = tm[{t.a, t.s}];
+                r.U = u;
+                r.src = srcs[t.s].d;
+                r.ps = srcs[t.s].ps;
+                r.g = h_galois(c, t.a);
+                r.pt[t.v - v0] = t.pt;
+            }
+            std::vector<rterm> ht;
+            for (auto &kv : tm) ht.push_back(kv.second);
+            rterm *d = nullptr;
+            HE_TRY(dev_alloc(&d, std::max<size_t>(1, ht.size())));
+            if (!ht.empty()) HE_CHECK_CUDA(cudaMemcpy(d, ht.data(), ht.size() * sizeof(rterm), cudaMemcpyHostToDevice));
+            ch.d_terms.push_back(d);
+            ch.rdesc.push_back(rgrp{d, (int)ht.size(), level, pt_level, ci > 0 ? 1 : 0,
+                                    facc + (size_t)v0 * 2 * ext_ * n, fbase + (size_t)v0 * 2 * nq_ * n});
+            for (auto &r : ht) {
+                ch.rbytes += (r.U ? slot * 8.0 : 0) + (double)2 * nq_ * n * 8;
+                for (int v = 0; v < HE_RV; v++)
+                    if (r.pt[v] && r.pt[v] != HE_PT_ONE) ch.rbytes += (double)(r.U ? ext_ : nq_) * n * 8;
+                ch.rmm += (double)4 * HE_RV * ext_ * n;
+            }
+            ch.rbytes += (double)std::min(HE_RV, nout - v0) * 2 * (ext_ + nq_) * n * 8;
+        }
+        chunks.push_back(std::move(ch));
+    }
+    split_ready = true;
+    return HE_OK;
+}
+
+FusedStage::~FusedStage() {
+    own.reset();
+    free_split();
+    free_groups();
+    cudaFree(D_all); cudaFree(facc); cudaFree(fbase); cudaFree(fconv); cudaFree(d_md);
+}
+
+int FusedStage::run(cudaStream_t s) {
+    HE_TRY(build());
+    if (!own) {
+        own.reset(new FusedLaunch());
+        own->c = c;
+        own->st = {this};
+        own->name = name;
+    }
+    return own->run(s);
+}
 
 // ================================================================================ pooling
 struct he_pool {
@@ -597,10 +1020,13 @@ struct he_pool {
     int n_hpt = 0, n_vpt = 0;
     mac_term *d_hterms = nullptr, *d_vterms = nullptr;
     FusedStage f_S, f_H, f_V, f_C, f_D;     // HE_FUSED stages (built on first use)
+    bool shared_masks = false;               // forks share the parent's mask plaintexts
+    bool rot_ready = false;                  // per-rotation buffers of HE_PLAIN / HE_BATCHED
     ~he_pool() {
         cudaFree(X); cudaFree(Wb); cudaFree(Yb); cudaFree(Zb); cudaFree(Sb);
         cudaFree(rotS); cudaFree(rotH); cudaFree(rotV); cudaFree(rotC); cudaFree(rotD);
-        cudaFree(hpts); cudaFree(vpts); cudaFree(d_hterms); cudaFree(d_vterms);
+        cudaFree(d_hterms); cudaFree(d_vterms);
+        if (!shared_masks) { cudaFree(hpts); cudaFree(vpts); }
     }
 };
 
@@ -634,33 +1060,31 @@ static int dedupe_upload(he_ctx *c, const std::vector<std::vector<std::vector<do
     return upload_plaintexts(c, uniq, uniq.size(), (double)c->primes[lv], lv, *dst, nullptr, true);
 }
 
-static int pool_build(he_ctx *c, const Lay &lin, int level, bool select, he_pool **out) {
-    if (level < 2) { he_set_error("pooling needs two levels"); return HE_ELEVEL; }
-    if (check_layout(lin, c->N) != HE_OK) return HE_EINVAL;
-    std::unique_ptr<he_pool> p(new he_pool());
-    p->c = c;
-    p->level = level;
-    HE_TRY(plan_pool(lin, select, p->P));
+// stage buffers every mode uses
+static int pool_runtime(he_pool *p) {
     const PoolPlanH &P = p->P;
-    const int ns = lin.ns;
-    p->ns = ns;
-    p->pw0 = (size_t)(level + 1) * c->n;
-    p->pw1 = (size_t)level * c->n;
-    p->pw2 = (size_t)(level - 1) * c->n;
-    p->pe0 = (size_t)(level + 1 + c->K) * c->n;
-    p->pe1 = (size_t)(level + c->K) * c->n;
+    const int ns = p->ns;
+    HE_TRY(dev_alloc(&p->X, (size_t)ns * 2 * p->pw0));
+    HE_TRY(dev_alloc(&p->Wb, (size_t)ns * 2 * p->pw0));
+    HE_TRY(dev_alloc(&p->Yb, (size_t)ns * 2 * p->pw0));
+    HE_TRY(dev_alloc(&p->Zb, (size_t)ns * 2 * p->pw1));
+    HE_TRY(dev_alloc(&p->Sb, P.groups.size() * 2 * p->pw2));
+    HE_TRY(dev_alloc(&p->rotD, P.dup.size() * 2 * p->pw2));
+    return HE_OK;
+}
+
+// buffers, rotation sets and MAC tables of the per-rotation modes (HE_PLAIN / HE_BATCHED)
+static int pool_rot_runtime(he_pool *p) {
+    if (p->rot_ready) return HE_OK;
+    he_ctx *c = p->c;
+    const PoolPlanH &P = p->P;
+    const int ns = p->ns, level = p->level;
     const size_t pw0 = p->pw0, pw1 = p->pw1, pw2 = p->pw2;
     const size_t nS = P.pre.size(), nH = P.h_amt.size(), nV = P.v_amt.size(), nG = P.groups.size();
-    HE_TRY(dev_alloc(&p->X, (size_t)ns * 2 * pw0));
-    HE_TRY(dev_alloc(&p->Wb, (size_t)ns * 2 * pw0));
-    HE_TRY(dev_alloc(&p->Yb, (size_t)ns * 2 * pw0));
-    HE_TRY(dev_alloc(&p->Zb, (size_t)ns * 2 * pw1));
-    HE_TRY(dev_alloc(&p->Sb, nG * 2 * pw2));
     HE_TRY(dev_alloc(&p->rotS, (size_t)ns * nS * 2 * pw0));
     HE_TRY(dev_alloc(&p->rotH, (size_t)ns * nH * 2 * pw0));
     HE_TRY(dev_alloc(&p->rotV, (size_t)ns * nV * 2 * pw1));
     HE_TRY(dev_alloc(&p->rotC, (size_t)ns * 2 * pw2));
-    HE_TRY(dev_alloc(&p->rotD, P.dup.size() * 2 * pw2));
     for (RotSet *rs : {&p->rs_S, &p->rs_H, &p->rs_V, &p->rs_C, &p->rs_D}) rs->c = c;
     p->rs_S.level = level;
     p->rs_H.level = level;
@@ -683,8 +1107,6 @@ static int pool_build(he_ctx *c, const Lay &lin, int level, bool select, he_pool
         p->rs_D.src.push_back({p->Sb, pw2});
         for (size_t k = 0; k < P.dup.size(); k++) p->rs_D.add(0, P.dup[k], p->rotD + k * 2 * pw2, pw2);
     }
-    HE_TRY(dedupe_upload(c, P.h_mask, ns, level, &p->hpts, p->h_idx, p->n_hpt));
-    HE_TRY(dedupe_upload(c, P.v_mask, ns, level - 1, &p->vpts, p->v_idx, p->n_vpt));
     std::vector<mac_term> th, tv;
     for (int u = 0; u < ns; u++) {
         for (size_t a = 0; a < nH; a++)
@@ -696,8 +1118,50 @@ static int pool_build(he_ctx *c, const Lay &lin, int level, bool select, he_pool
     HE_TRY(dev_alloc(&p->d_vterms, tv.size()));
     HE_CHECK_CUDA(cudaMemcpy(p->d_hterms, th.data(), th.size() * sizeof(mac_term), cudaMemcpyHostToDevice));
     HE_CHECK_CUDA(cudaMemcpy(p->d_vterms, tv.data(), tv.size() * sizeof(mac_term), cudaMemcpyHostToDevice));
+    p->rot_ready = true;
+    return HE_OK;
+}
+
+static void pool_sizes(he_pool *p, he_ctx *c, int level) {
+    p->c = c;
+    p->level = level;
+    p->pw0 = (size_t)(level + 1) * c->n;
+    p->pw1 = (size_t)level * c->n;
+    p->pw2 = (size_t)(level - 1) * c->n;
+    p->pe0 = (size_t)(level + 1 + c->K) * c->n;
+    p->pe1 = (size_t)(level + c->K) * c->n;
+}
+
+static int pool_build(he_ctx *c, const Lay &lin, int level, bool select, he_pool **out) {
+    if (level < 2) { he_set_error("pooling needs two levels"); return HE_ELEVEL; }
+    if (check_layout(lin, c->N) != HE_OK) return HE_EINVAL;
+    std::unique_ptr<he_pool> p(new he_pool());
+    pool_sizes(p.get(), c, level);
+    HE_TRY(plan_pool(lin, select, p->P));
+    p->ns = lin.ns;
+    HE_TRY(dedupe_upload(c, p->P.h_mask, p->ns, level, &p->hpts, p->h_idx, p->n_hpt));
+    HE_TRY(dedupe_upload(c, p->P.v_mask, p->ns, level - 1, &p->vpts, p->v_idx, p->n_vpt));
     p->P.h_mask.clear();
     p->P.v_mask.clear();
+    HE_TRY(pool_runtime(p.get()));
+    *out = p.release();
+    return HE_OK;
+}
+
+static int pool_fork(const he_pool *src, he_ctx *c, he_pool **out) {
+    if (c->root() != src->c->root()) { he_set_error("fork: contexts do not share a root"); return HE_ESTATE; }
+    std::unique_ptr<he_pool> p(new he_pool());
+    pool_sizes(p.get(), c, src->level);
+    p->P = src->P;
+    p->ns = src->ns;
+    p->hpts = src->hpts;
+    p->vpts = src->vpts;
+    p->h_idx = src->h_idx;
+    p->v_idx = src->v_idx;
+    p->n_hpt = src->n_hpt;
+    p->n_vpt = src->n_vpt;
+    p->shared_masks = true;
+    HE_TRY(pool_runtime(p.get()));
     *out = p.release();
     return HE_OK;
 }
@@ -779,6 +1243,13 @@ static int pool_prepare_fused(he_pool *p) {
     const size_t pw0 = p->pw0, pw1 = p->pw1, pw2 = p->pw2;
     const size_t nH = P.h_amt.size(), nV = P.v_amt.size();
     for (FusedStage *f : {&p->f_S, &p->f_H, &p->f_V, &p->f_C, &p->f_D}) f->c = c;
+    char nm[64];
+    const char *tag[5] = {"S (ones conv)", "H (horizontal)", "V (vertical)", "C (consolidate)", "D (duplicate)"};
+    FusedStage *fs[5] = {&p->f_S, &p->f_H, &p->f_V, &p->f_C, &p->f_D};
+    for (int k = 0; k < 5; k++) {
+        snprintf(nm, sizeof(nm), "pool %dx%d %s", p->P.lin.m, p->P.lin.m, tag[k]);
+        fs[k]->name = nm;
+    }
     p->f_S.level = p->f_H.level = lv;
     p->f_V.level = lv - 1;
     p->f_C.level = p->f_D.level = lv - 2;
@@ -859,6 +1330,7 @@ static int pool_run_fused(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out, 
 
 static int pool_prepare(he_pool *p, int mode) {
     if (mode == HE_FUSED) return pool_prepare_fused(p);
+    HE_TRY(pool_rot_runtime(p));
     for (RotSet *rs : {&p->rs_S, &p->rs_H, &p->rs_V, &p->rs_C, &p->rs_D}) {
         if (mode == HE_BATCHED) HE_TRY(rs->prepare_batched());
         else HE_TRY(rs->resolve_keys());
@@ -946,6 +1418,7 @@ extern "C" int he_pool_run(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out,
 }
 
 // ================================================================================ convolution
+struct ConvBatch;
 struct he_conv {
     he_ctx *c = nullptr;
     Lay lin, lout;
@@ -955,19 +1428,23 @@ struct he_conv {
     size_t pw = 0;
     std::vector<int> tu, tv, ta;                 // terms in plan order
     std::vector<int> term_off;                   // [n_out + 1]
-    std::map<long long, int> slot;               // u*N + a -> R slot
+    std::map<long long, int> slot;               // u*N + a -> rotation slot (amount != 0)
     size_t pe = 0;                               // plaintext stride: Q_l u P limbs
-    u64 *R = nullptr, *pts = nullptr, *bias_pts = nullptr, *acc = nullptr;
+    u64 *R = nullptr;                            // [n_in][2][pw] input copies
+    u64 *Rrot = nullptr;                         // [slots][2][pw] rotations (per-rotation modes)
+    u64 *pts = nullptr, *bias_pts = nullptr, *acc = nullptr;
     mac_term *d_terms = nullptr;
     RotSet rot;
+    bool rot_ready = false, shared_pts = false;
     he_pool *pool = nullptr;
     std::vector<he_ct *> mid;
     FusedStage fused;                            // HE_FUSED: built on first use
-    ~he_conv() {
-        cudaFree(R); cudaFree(pts); cudaFree(bias_pts); cudaFree(d_terms); cudaFree(acc);
-        delete pool;
-        for (he_ct *x : mid) he_ct_free(x);
+    std::unique_ptr<ConvBatch> batch;            // he_conv_run_batch: buffers of the last signature
+    std::map<std::pair<int, uint64_t>, u64 *> bias_by;   // (level, output scale) -> bias addends
+    u64 *rot_ptr(int u, int a) {
+        return a == 0 ? R + (size_t)u * 2 * pw : Rrot + (size_t)slot[(long long)u * c->N + a] * 2 * pw;
     }
+    ~he_conv();
 };
 
 static int conv_bias_int(he_conv *cv, int v, double scale, std::vector<int64_t> &m) {
@@ -979,6 +1456,74 @@ static int conv_bias_int(he_conv *cv, int v, double scale, std::vector<int64_t> 
     m.resize(cv->c->n);
     encode_slots(z.data(), cv->c->n, scale, m.data());
     return HE_OK;
+}
+
+// buffers every mode uses: input copies, accumulators, the stride-2 select stage
+static int conv_runtime(he_conv *cv, const he_pool *pool_src = nullptr) {
+    he_ctx *c = cv->c;
+    HE_TRY(dev_alloc(&cv->R, (size_t)cv->lin.ns * 2 * cv->pw));
+    HE_TRY(dev_alloc(&cv->acc, (size_t)cv->lout.ns * 2 * cv->pw));
+    if (cv->stride == 2) {
+        if (pool_src) HE_TRY(pool_fork(pool_src, c, &cv->pool));
+        else HE_TRY(pool_build(c, cv->lout, cv->level - 1, true, &cv->pool));
+        for (int v = 0; v < cv->lout.ns; v++) {
+            he_ct *m;
+            HE_TRY(he_ct_alloc(c, cv->level - 1, &m));
+            cv->mid.push_back(m);
+        }
+    }
+    return HE_OK;
+}
+
+// rotation buffers, MAC tables and rotation set of the per-rotation modes
+static int conv_rot_runtime(he_conv *cv) {
+    if (cv->rot_ready) return HE_OK;
+    he_ctx *c = cv->c;
+    const size_t pw = cv->pw, n_terms = cv->tu.size();
+    HE_TRY(dev_alloc(&cv->Rrot, cv->slot.size() * 2 * pw));
+    std::vector<mac_term> terms(n_terms);
+    for (size_t t = 0; t < n_terms; t++)
+        terms[t] = mac_term{cv->pts + t * cv->pe, cv->rot_ptr(cv->tu[t], cv->ta[t]), pw};
+    HE_TRY(dev_alloc(&cv->d_terms, n_terms));
+    HE_CHECK_CUDA(cudaMemcpy(cv->d_terms, terms.data(), n_terms * sizeof(mac_term), cudaMemcpyHostToDevice));
+    cv->rot.c = c;
+    cv->rot.level = cv->level;
+    for (int u = 0; u < cv->lin.ns; u++) cv->rot.src.push_back({cv->R + (size_t)u * 2 * pw, pw});
+    for (auto &kv : cv->slot) {
+        int u = (int)(kv.first / c->N), a = (int)(kv.first % c->N);
+        cv->rot.add(u, a, cv->Rrot + (size_t)kv.second * 2 * pw, pw);
+    }
+    cv->rot_ready = true;
+    return HE_OK;
+}
+
+static int conv_fork(const he_conv *src, he_ctx *c, he_conv **out) {
+    if (c->root() != src->c->root()) { he_set_error("fork: contexts do not share a root"); return HE_ESTATE; }
+    std::unique_ptr<he_conv> cv(new he_conv());
+    cv->c = c;
+    cv->lin = src->lin; cv->lout = src->lout; cv->W = src->W; cv->bias = src->bias;
+    cv->co = src->co; cv->ci = src->ci; cv->kh = src->kh; cv->kw = src->kw; cv->pad = src->pad;
+    cv->stride = src->stride; cv->level = src->level;
+    cv->in_scale = src->in_scale; cv->mid_scale = src->mid_scale;
+    cv->pw = src->pw; cv->pe = src->pe;
+    cv->tu = src->tu; cv->tv = src->tv; cv->ta = src->ta; cv->term_off = src->term_off;
+    cv->slot = src->slot;
+    cv->pts = src->pts;
+    cv->bias_pts = src->bias_pts;
+    cv->shared_pts = true;
+    HE_TRY(conv_runtime(cv.get(), src->pool));
+    *out = cv.release();
+    return HE_OK;
+}
+
+extern "C" int he_conv_fork(const he_conv *src, he_ctx *ctx, he_conv **out) {
+    if (!src || !ctx || !out) { he_set_error("he_conv_fork: null argument"); return HE_EINVAL; }
+    return conv_fork(src, ctx, out);
+}
+
+extern "C" int he_pool_fork(const he_pool *src, he_ctx *ctx, he_pool **out) {
+    if (!src || !ctx || !out) { he_set_error("he_pool_fork: null argument"); return HE_EINVAL; }
+    return pool_fork(src, ctx, out);
 }
 
 extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, const double *bias,
@@ -1016,18 +1561,15 @@ extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, c
         plan_conv_v(lin, cv->lout, cv->W.data(), ci, kh, kw, pad, v, maps[v]);
         n_terms += maps[v].size();
     }
-    // R slots: every input shard's own copy (amount 0) first, then every rotation needed
-    for (int u = 0; u < lin.ns; u++) cv->slot[(long long)u * c->N] = u;
+    // rotation slots: every (u, a) with a != 0 that some output needs
     for (int v = 0; v < cv->lout.ns; v++)
         for (auto &kv : maps[v])
-            if (!cv->slot.count(kv.first)) {
+            if (kv.first % c->N != 0 && !cv->slot.count(kv.first)) {
                 int id = (int)cv->slot.size();
                 cv->slot[kv.first] = id;
             }
-    HE_TRY(dev_alloc(&cv->R, cv->slot.size() * 2 * pw));
     HE_TRY(dev_alloc(&cv->pts, n_terms * pe));
     HE_TRY(dev_alloc(&cv->bias_pts, (size_t)cv->lout.ns * level * c->n));
-    HE_TRY(dev_alloc(&cv->acc, (size_t)cv->lout.ns * 2 * pw));
     // diagonal plaintexts at scale q_level
     size_t t0 = 0;
     cv->term_off.push_back(0);
@@ -1051,29 +1593,7 @@ extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, c
         conv_bias_int(cv.get(), v, cv->mid_scale, m);
         HE_TRY(upload_addend(c, m.data(), level - 1, cv->bias_pts + (size_t)v * level * c->n));
     }
-    // MAC terms and rotation set
-    std::vector<mac_term> terms(n_terms);
-    for (size_t t = 0; t < n_terms; t++) {
-        int s = cv->slot[(long long)cv->tu[t] * c->N + cv->ta[t]];
-        terms[t] = mac_term{cv->pts + t * pe, cv->R + (size_t)s * 2 * pw, pw};
-    }
-    HE_TRY(dev_alloc(&cv->d_terms, n_terms));
-    HE_CHECK_CUDA(cudaMemcpy(cv->d_terms, terms.data(), n_terms * sizeof(mac_term), cudaMemcpyHostToDevice));
-    cv->rot.c = c;
-    cv->rot.level = level;
-    for (int u = 0; u < lin.ns; u++) cv->rot.src.push_back({cv->R + (size_t)u * 2 * pw, pw});
-    for (auto &kv : cv->slot) {
-        int u = (int)(kv.first / c->N), a = (int)(kv.first % c->N);
-        if (a != 0) cv->rot.add(u, a, cv->R + (size_t)kv.second * 2 * pw, pw);
-    }
-    if (stride == 2) {
-        HE_TRY(pool_build(c, cv->lout, level - 1, true, &cv->pool));
-        for (int v = 0; v < cv->lout.ns; v++) {
-            he_ct *m;
-            HE_TRY(he_ct_alloc(c, level - 1, &m));
-            cv->mid.push_back(m);
-        }
-    }
+    HE_TRY(conv_runtime(cv.get()));
     *out = cv.release();
     return HE_OK;
 }
@@ -1135,6 +1655,9 @@ static int conv_prepare_fused(he_conv *cv) {
     if (F.c) return HE_OK;
     F.c = cv->c;
     F.level = cv->level;
+    char nm[96];
+    snprintf(nm, sizeof(nm), "conv %d->%d %dx%d k%dx%d", cv->ci, cv->co, cv->lin.m, cv->lin.m, cv->kh, cv->kw);
+    F.name = nm;
     for (int u = 0; u < cv->lin.ns; u++) F.add_src(cv->R + (size_t)u * 2 * cv->pw, cv->pw);
     for (int v = 0; v < cv->lout.ns; v++) F.add_out(cv->acc + (size_t)v * 2 * cv->pw, cv->pw);
     for (size_t t = 0; t < cv->tu.size(); t++) F.add_term(cv->tv[t], cv->tu[t], cv->ta[t], cv->pts + t * cv->pe);
@@ -1160,6 +1683,7 @@ extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out
         HE_TRY(conv_prepare_fused(cv));
         HE_TRY(cv->fused.run(s));
     } else {
+        HE_TRY(conv_rot_runtime(cv));
         if (mode == HE_BATCHED) HE_TRY(cv->rot.prepare_batched());
         HE_TRY(cv->rot.run(mode, s));
     }
@@ -1181,6 +1705,208 @@ extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out
     if (cv->stride == 2) {
         HE_TRY(pool_prepare(cv->pool, mode));
         return pool_run(c, cv->pool, cv->mid.data(), out, mode, s);
+    }
+    return HE_OK;
+}
+
+// ================================================================================ image batches
+// Several images through one convolution, each at its own level l_i <= the layer's level
+// (the plaintexts, encoded once for the layer's level, serve every lower level: an integer
+// plaintext's residues mod q_0..q_l and P are a subset of the stored ones).  In HE_FUSED mode
+// every image's rotations, inner products and MACs run in ONE fused-kernel launch whose groups
+// span all images and levels; the per-rotation modes run image by image.
+struct ConvSlot {                                // one image of a batch: buffers at its level
+    int level = 0;
+    size_t pw = 0;
+    u64 *R = nullptr, *acc = nullptr, *Rrot = nullptr;
+    mac_term *d_terms = nullptr;
+    RotSet rot;
+    bool rot_ready = false;
+    FusedStage fused;
+    ~ConvSlot() { cudaFree(R); cudaFree(acc); cudaFree(Rrot); cudaFree(d_terms); }
+};
+struct ConvBatch {
+    std::vector<int> levels;
+    std::vector<std::unique_ptr<ConvSlot>> slots;
+    std::unique_ptr<FusedLaunch> launch;
+};
+
+he_conv::~he_conv() {
+    batch.reset();
+    for (auto &kv : bias_by) cudaFree(kv.second);
+    cudaFree(R); cudaFree(Rrot); cudaFree(d_terms); cudaFree(acc);
+    if (!shared_pts) { cudaFree(pts); cudaFree(bias_pts); }
+    delete pool;
+    for (he_ct *x : mid) he_ct_free(x);
+}
+
+static int conv_batch_build(he_conv *cv, const std::vector<int> &levels) {
+    he_ctx *c = cv->c;
+    HE_TRY(he_capture_guard("a new batch signature"));
+    std::unique_ptr<ConvBatch> B(new ConvBatch());
+    B->levels = levels;
+    B->launch.reset(new FusedLaunch());
+    B->launch->c = c;
+    char nm[128];
+    snprintf(nm, sizeof(nm), "conv %d->%d %dx%d k%dx%d batch of %zu", cv->ci, cv->co, cv->lin.m, cv->lin.m, cv->kh,
+             cv->kw, levels.size());
+    B->launch->name = nm;
+    for (size_t i = 0; i < levels.size(); i++) {
+        std::unique_ptr<ConvSlot> S(new ConvSlot());
+        const int l = levels[i];
+        S->level = l;
+        S->pw = (size_t)(l + 1) * c->n;
+        HE_TRY(dev_alloc(&S->R, (size_t)cv->lin.ns * 2 * S->pw));
+        HE_TRY(dev_alloc(&S->acc, (size_t)cv->lout.ns * 2 * S->pw));
+        FusedStage &F = S->fused;
+        F.c = c;
+        F.level = l;
+        F.pt_level = cv->level;
+        F.name = std::string(nm) + " image " + std::to_string(i);
+        for (int u = 0; u < cv->lin.ns; u++) F.add_src(S->R + (size_t)u * 2 * S->pw, S->pw);
+        for (int v = 0; v < cv->lout.ns; v++) F.add_out(S->acc + (size_t)v * 2 * S->pw, S->pw);
+        for (size_t t = 0; t < cv->tu.size(); t++) F.add_term(cv->tv[t], cv->tu[t], cv->ta[t], cv->pts + t * cv->pe);
+        HE_TRY(F.build());
+        B->launch->st.push_back(&F);
+        B->slots.push_back(std::move(S));
+    }
+    cv->batch.reset(B.release());
+    return HE_OK;
+}
+
+// rotation buffers and MAC tables of one image for the per-rotation modes
+static int conv_slot_rot(he_conv *cv, ConvSlot &S) {
+    if (S.rot_ready) return HE_OK;
+    he_ctx *c = cv->c;
+    const size_t pw = S.pw, n_terms = cv->tu.size();
+    std::map<long long, int> slot = cv->slot;
+    HE_TRY(dev_alloc(&S.Rrot, slot.size() * 2 * pw));
+    auto rptr = [&](int u, int a) {
+        return a == 0 ? S.R + (size_t)u * 2 * pw : S.Rrot + (size_t)slot[(long long)u * c->N + a] * 2 * pw;
+    };
+    std::vector<mac_term> terms(n_terms);
+    for (size_t t = 0; t < n_terms; t++) terms[t] = mac_term{cv->pts + t * cv->pe, rptr(cv->tu[t], cv->ta[t]), pw};
+    HE_TRY(dev_alloc(&S.d_terms, n_terms));
+    HE_CHECK_CUDA(cudaMemcpy(S.d_terms, terms.data(), n_terms * sizeof(mac_term), cudaMemcpyHostToDevice));
+    S.rot.c = c;
+    S.rot.level = S.level;
+    for (int u = 0; u < cv->lin.ns; u++) S.rot.src.push_back({S.R + (size_t)u * 2 * pw, pw});
+    for (auto &kv : slot) {
+        int u = (int)(kv.first / c->N), a = (int)(kv.first % c->N);
+        S.rot.add(u, a, S.Rrot + (size_t)kv.second * 2 * pw, pw);
+    }
+    S.rot_ready = true;
+    return HE_OK;
+}
+
+static uint64_t scale_bits(double x) {
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    return b;
+}
+
+// bias addends [n_out][l][n] at level l - 1 and the given output scale (encoded on first use)
+static int conv_bias_for(he_conv *cv, int l, double out_scale, const u64 **out) {
+    auto key = std::make_pair(l, scale_bits(out_scale));
+    auto it = cv->bias_by.find(key);
+    if (it == cv->bias_by.end()) {
+        HE_TRY(he_capture_guard("bias encoding for a new level or scale"));
+        u64 *d;
+        HE_TRY(dev_alloc(&d, (size_t)cv->lout.ns * l * cv->c->n));
+        for (int v = 0; v < cv->lout.ns; v++) {
+            std::vector<int64_t> m;
+            conv_bias_int(cv, v, out_scale, m);
+            int rc = upload_addend(cv->c, m.data(), l - 1, d + (size_t)v * l * cv->c->n);
+            if (rc != HE_OK) { cudaFree(d); return rc; }
+        }
+        it = cv->bias_by.emplace(key, d).first;
+    }
+    *out = it->second;
+    return HE_OK;
+}
+
+extern "C" int he_conv_import_bias(he_conv *cv, int level, double out_scale, const int64_t *bias) {
+    if (!cv || !bias || level < 1 || level > cv->level) { he_set_error("he_conv_import_bias: bad argument"); return HE_EINVAL; }
+    auto key = std::make_pair(level, scale_bits(out_scale));
+    auto it = cv->bias_by.find(key);
+    u64 *d;
+    if (it != cv->bias_by.end()) d = it->second;
+    else {
+        HE_TRY(dev_alloc(&d, (size_t)cv->lout.ns * level * cv->c->n));
+        cv->bias_by.emplace(key, d);
+    }
+    for (int v = 0; v < cv->lout.ns; v++)
+        HE_TRY(upload_addend(cv->c, bias + (size_t)v * cv->c->n, level - 1, d + (size_t)v * level * cv->c->n));
+    return HE_OK;
+}
+
+extern "C" int he_conv_run_batch(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out, int n_img, int mode,
+                                 void *stream) {
+    if (!c || !cv || !in || !out || cv->c != c || n_img < 1 ||
+        (mode != HE_PLAIN && mode != HE_BATCHED && mode != HE_FUSED)) {
+        he_set_error("he_conv_run_batch: bad argument");
+        return HE_EINVAL;
+    }
+    if (cv->stride != 1) { he_set_error("he_conv_run_batch: stride-1 convolutions only"); return HE_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ni = cv->lin.ns, no = cv->lout.ns;
+    std::vector<int> levels(n_img);
+    for (int i = 0; i < n_img; i++) {
+        const he_ct *x0 = in[(size_t)i * ni];
+        if (!x0 || x0->ctx != c) { he_set_error("he_conv_run_batch: image %d input missing", i); return HE_EINVAL; }
+        levels[i] = x0->level;
+        if (levels[i] < 1 || levels[i] > cv->level) {
+            he_set_error("he_conv_run_batch: image %d at level %d, the layer takes 1..%d", i, levels[i], cv->level);
+            return HE_ELEVEL;
+        }
+        for (int u = 0; u < ni; u++) {
+            const he_ct *x = in[(size_t)i * ni + u];
+            if (!x || x->ctx != c || x->level != levels[i] || x->scale != x0->scale) {
+                he_set_error("he_conv_run_batch: image %d shard %d differs in level or scale", i, u);
+                return HE_ELEVEL;
+            }
+        }
+    }
+    if (!cv->batch || cv->batch->levels != levels) HE_TRY(conv_batch_build(cv, levels));
+    ConvBatch &B = *cv->batch;
+    for (int i = 0; i < n_img; i++) {
+        ConvSlot &S = *B.slots[i];
+        for (int u = 0; u < ni; u++) {
+            const he_ct *x = in[(size_t)i * ni + u];
+            HE_TRY(k_copy_limbs(S.R + (size_t)u * 2 * S.pw, S.pw, x->d, x->pstride, S.pw, 2, s));
+        }
+    }
+    if (mode == HE_FUSED) {
+        HE_TRY(B.launch->run(s));
+    } else {
+        for (int i = 0; i < n_img; i++) {
+            ConvSlot &S = *B.slots[i];
+            HE_TRY(conv_slot_rot(cv, S));
+            if (mode == HE_BATCHED) HE_TRY(S.rot.prepare_batched());
+            HE_TRY(S.rot.run(mode, s));
+        }
+    }
+    const double S_pt = (double)c->primes[cv->level];
+    for (int i = 0; i < n_img; i++) {
+        ConvSlot &S = *B.slots[i];
+        const int l = S.level;
+        const double in_scale = in[(size_t)i * ni]->scale;
+        const double out_scale = in_scale * S_pt / (double)c->primes[l];
+        const u64 *bias;
+        HE_TRY(conv_bias_for(cv, l, out_scale, &bias));
+        for (int v = 0; v < no; v++) {
+            u64 *a = S.acc + (size_t)v * 2 * S.pw;
+            const int t0 = cv->term_off[v], t1 = cv->term_off[v + 1];
+            if (mode != HE_FUSED) HE_TRY(k_mac(c, S.d_terms + t0, t1 - t0, a, S.pw, l, false, s));
+            he_ct t = view(c, a, S.pw, l, in_scale * S_pt);
+            HE_TRY(he_rescale(c, &t, stream));
+            HE_TRY(k_add_raw(c, a, S.pw, bias + (size_t)v * l * c->n, 0, l, 1, false, s));
+            he_ct *d = out[(size_t)i * no + v];
+            if (!d || d->ctx != c) { he_set_error("he_conv_run_batch: output %d of image %d missing", v, i); return HE_EINVAL; }
+            HE_TRY(ensure_ct(c, d, l - 1));
+            HE_TRY(k_copy_limbs(d->d, d->pstride, a, S.pw, (size_t)l * c->n, 2, s));
+            d->scale = t.scale;
+        }
     }
     return HE_OK;
 }

@@ -14,7 +14,9 @@ from . import build as _build
 HE_OK, HE_EINVAL, HE_ELEVEL, HE_EKEY, HE_ENOMEM, HE_ETIMEOUT, HE_ECUDA, HE_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 HE_PLAIN, HE_BATCHED, HE_FUSED = 0, 1, 2
 HE_RELIN_KEY = 0x7FFFFFFF
-HE_MAX_BLOCKS = 4096
+HE_MAX_BLOCKS = 32768
+HE_OPT_KEY_STREAM = 1
+HE_KEY_STREAM_LDG, HE_KEY_STREAM_TMA, HE_KEY_STREAM_AUTO, HE_KEY_STREAM_SPLIT = 0, 1, 2, 3
 
 c_int, c_double, c_size_t, c_u64, c_i32, c_vp = (ctypes.c_int, ctypes.c_double, ctypes.c_size_t,
                                                  ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p)
@@ -56,6 +58,17 @@ _SIGS = {
     "he_layout_image": (c_int, [c_int, c_int, c_int, ctypes.POINTER(he_layout)]),
     "he_ctx_create": (c_int, [ctypes.POINTER(he_params), ctypes.POINTER(c_vp)]),
     "he_ctx_destroy": (None, [c_vp]),
+    "he_ctx_fork": (c_int, [c_vp, ctypes.POINTER(c_vp)]),
+    "he_ctx_check": (c_int, [c_vp, c_vp]),
+    "he_ctx_set_option": (c_int, [c_vp, c_int, c_int]),
+    "he_ctx_get_option": (c_int, [c_vp, c_int, ctypes.POINTER(c_int)]),
+    "he_ctx_tuning_log": (c_size_t, [c_vp, ctypes.c_char_p, c_size_t]),
+    "he_selftest_bounded_wait": (c_int, [c_vp, c_vp]),
+    "he_graph_begin": (c_int, [c_vp, c_vp]),
+    "he_graph_end": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
+    "he_graph_launch": (c_int, [c_vp, c_vp]),
+    "he_graph_kernels": (c_u64, [c_vp]),
+    "he_graph_destroy": (None, [c_vp]),
     "he_ctx_info": (c_int, [c_vp] + [ctypes.POINTER(c_int)] * 6 + [U64P, U64P]),
     "he_keygen_rotations": (c_int, [c_vp, I32P, c_size_t]),
     "he_keygen_relin": (c_int, [c_vp]),
@@ -92,6 +105,7 @@ _SIGS = {
     "he_conv_create": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_int, c_int,
                                c_int, c_int, c_int, c_double, ctypes.POINTER(c_vp)]),
     "he_conv_destroy": (None, [c_vp]),
+    "he_conv_fork": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "he_conv_out_layout": (c_int, [c_vp, ctypes.POINTER(he_layout)]),
     "he_conv_out_level": (c_int, [c_vp]),
     "he_conv_rotations": (c_int, [c_vp, I32P, c_size_t]),
@@ -99,8 +113,11 @@ _SIGS = {
     "he_conv_export_plan": (c_int, [c_vp, I32P, I32P, I32P, F64P]),
     "he_conv_import_plaintexts": (c_int, [c_vp, I64P, I64P]),
     "he_conv_run": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_vp]),
+    "he_conv_run_batch": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_int, c_vp]),
+    "he_conv_import_bias": (c_int, [c_vp, c_int, c_double, I64P]),
     "he_pool_create": (c_int, [c_vp, ctypes.POINTER(he_layout), c_int, ctypes.POINTER(c_vp)]),
     "he_pool_destroy": (None, [c_vp]),
+    "he_pool_fork": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "he_pool_out_layout": (c_int, [c_vp, ctypes.POINTER(he_layout)]),
     "he_pool_rotations": (c_int, [c_vp, I32P, c_size_t]),
     "he_pool_n_masks": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
@@ -203,6 +220,59 @@ def he_ctx_create(params: he_params):
 
 def he_ctx_destroy(ctx):
     load().he_ctx_destroy(ctx)
+
+
+def he_ctx_check(ctx, stream=None):
+    _check(load().he_ctx_check(ctx, stream_ptr(stream)))
+
+
+def he_ctx_set_option(ctx, option, value):
+    _check(load().he_ctx_set_option(ctx, option, value))
+
+
+def he_ctx_get_option(ctx, option):
+    v = c_int()
+    _check(load().he_ctx_get_option(ctx, option, ctypes.byref(v)))
+    return v.value
+
+
+def he_ctx_tuning_log(ctx):
+    n = load().he_ctx_tuning_log(ctx, None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    load().he_ctx_tuning_log(ctx, buf, n + 1)
+    return buf.value.decode()
+
+
+def he_selftest_bounded_wait(ctx, stream=None):
+    _check(load().he_selftest_bounded_wait(ctx, stream_ptr(stream)))
+
+
+def he_graph_begin(ctx, stream=None):
+    _check(load().he_graph_begin(ctx, stream_ptr(stream)))
+
+
+def he_graph_end(ctx, stream=None):
+    g = c_vp()
+    _check(load().he_graph_end(ctx, stream_ptr(stream), ctypes.byref(g)))
+    return g
+
+
+def he_graph_launch(graph, stream=None):
+    _check(load().he_graph_launch(graph, stream_ptr(stream)))
+
+
+def he_graph_kernels(graph):
+    return int(load().he_graph_kernels(graph))
+
+
+def he_graph_destroy(graph):
+    load().he_graph_destroy(graph)
+
+
+def he_ctx_fork(ctx):
+    h = c_vp()
+    _check(load().he_ctx_fork(ctx, ctypes.byref(h)))
+    return h
 
 
 def he_ctx_info(ctx):
@@ -379,6 +449,12 @@ def he_conv_destroy(conv):
     load().he_conv_destroy(conv)
 
 
+def he_conv_fork(conv, ctx):
+    h = c_vp()
+    _check(load().he_conv_fork(conv, ctx, ctypes.byref(h)))
+    return h
+
+
 def he_conv_out_layout(conv):
     lay = he_layout()
     _check(load().he_conv_out_layout(conv, ctypes.byref(lay)))
@@ -420,6 +496,16 @@ def he_conv_run(ctx, conv, ins, outs, mode=HE_PLAIN, stream=None):
     _check(load().he_conv_run(ctx, conv, _vp_array(ins), _vp_array(outs), mode, stream_ptr(stream)))
 
 
+def he_conv_run_batch(ctx, conv, ins, outs, n_img, mode=HE_FUSED, stream=None):
+    """ins: n_img * n_in shards (image-major); outs: n_img * n_out."""
+    _check(load().he_conv_run_batch(ctx, conv, _vp_array(ins), _vp_array(outs), n_img, mode, stream_ptr(stream)))
+
+
+def he_conv_import_bias(conv, level, out_scale, bias):
+    b = np.ascontiguousarray(bias, dtype=np.int64)
+    _check(load().he_conv_import_bias(conv, level, out_scale, _p(b, I64P)))
+
+
 def he_pool_create(ctx, layout, level):
     h = c_vp()
     _check(load().he_pool_create(ctx, ctypes.byref(layout), level, ctypes.byref(h)))
@@ -428,6 +514,12 @@ def he_pool_create(ctx, layout, level):
 
 def he_pool_destroy(pool):
     load().he_pool_destroy(pool)
+
+
+def he_pool_fork(pool, ctx):
+    h = c_vp()
+    _check(load().he_pool_fork(pool, ctx, ctypes.byref(h)))
+    return h
 
 
 def he_pool_out_layout(pool):

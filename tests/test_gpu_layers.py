@@ -90,12 +90,17 @@ def _conv_case(pair, c, co, m, k, pad, level, seed, bias=True):
             assert H.he_ct_scale(oc) == rc.scale
             assert_ct_equal(g.download(oc), rc)
     # one ModDown per output shard: equals the oracle's raised-basis restatement
+    # (both ways of streaming key words into the fused kernel give these bits)
     ref_raised = Ly.conv_he_raised(o, plan, cts, pts, bias_pts)
-    outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
-    H.he_conv_run(g.h, conv, ins, outs, H.HE_FUSED)
-    for oc, rc in zip(outs, ref_raised):
-        assert H.he_ct_scale(oc) == rc.scale
-        assert_ct_equal(g.download(oc), rc)
+    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_SPLIT):
+        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
+        outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
+        H.he_conv_run(g.h, conv, ins, outs, H.HE_FUSED)
+        H.he_ctx_check(g.h)
+        for oc, rc in zip(outs, ref_raised):
+            assert H.he_ct_scale(oc) == rc.scale
+            assert_ct_equal(g.download(oc), rc)
+    H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_LDG)
     H.he_conv_destroy(conv)
     return ref, plan, x, W, b
 
@@ -153,11 +158,15 @@ def test_pool_bit_exact(mid, c, m):
             assert_ct_equal(g.download(oc), rc)
     # every stage with one ModDown per output shard: equals the oracle's raised-basis pool
     ref_r = Ly.pool_he_raised(o, plan, cts, list(hm), list(vm))
-    outs = [g.ct(level - 2) for _ in range(len(ref_r))]
-    H.he_pool_run(g.h, pool, ins, outs, H.HE_FUSED)
-    for oc, rc in zip(outs, ref_r):
-        assert H.he_ct_scale(oc) == rc.scale
-        assert_ct_equal(g.download(oc), rc)
+    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_SPLIT):
+        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
+        outs = [g.ct(level - 2) for _ in range(len(ref_r))]
+        H.he_pool_run(g.h, pool, ins, outs, H.HE_FUSED)
+        H.he_ctx_check(g.h)
+        for oc, rc in zip(outs, ref_r):
+            assert H.he_ct_scale(oc) == rc.scale
+            assert_ct_equal(g.download(oc), rc)
+    H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_LDG)
     want = torch.nn.functional.avg_pool2d(torch.tensor(x)[None], 2)[0].numpy()
     for r in (ref, ref_r):
         img = Ly.unpack(plan.lout, np.stack([o.decrypt(c) for c in r]))
@@ -242,6 +251,14 @@ def test_cifar_layer_full_ring():
             img = Ly.unpack(lin, H.he_decrypt(g.h, oc, N)[None])
             assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
         assert np.array_equal(outs[0], outs[1])
+        # the TMA key-tile pipeline and the split form reproduce the fused output at full size
+        for ks in (H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_SPLIT):
+            H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
+            ot = g.ct(level - 1)
+            H.he_conv_run(g.h, conv, [ct], [ot], H.HE_FUSED)
+            H.he_ctx_check(g.h)
+            assert np.array_equal(g.download(ot), outs[H.HE_FUSED])
+        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_LDG)
         cheb = Ly.cheb_nodes_coeffs(Ly.gelu, workloads.GELU_DEGREE, -8, 8)
         H.he_poly_eval(g.h, oc, cheb, C20.scale)
         assert H.he_ct_level(oc) == level - 1 - 5

@@ -96,3 +96,27 @@ def poisson_arrivals(n, rate, seed=0):
 def request_sizes(n, seed=0, sizes=(32, 64, 224), mix=(0.6, 0.3, 0.1)):
     rng = np.random.default_rng(seed + 7)
     return [int(s) for s in rng.choice(sizes, size=n, p=mix)]
+
+
+def serving_stack(seed=0, widths=(4, 16, 32, 64, 64), m=32, bound=GELU_BOUND, deg=GELU_DEGREE):
+    """Weights of the 4 x [conv3x3 + folded BN, GELU, 2x2 avg-pool] serving stack.
+
+    PyTorch default conv init; BatchNorm statistics of every layer taken from a seeded m x m
+    image pushed through the plaintext stack (conv, BN, exact GELU, avg-pool) and divided by
+    `bound`, so the pre-activations of uniform images stay inside [-1, 1].  Returns
+    [(W, b)] per layer."""
+    import torch
+    rng = np.random.default_rng(seed + 11)
+    x = image(widths[0], m, seed + 5)
+    x[3:] = 0.0                                  # 3 colour channels padded to 4
+    layers = []
+    for li in range(len(widths) - 1):
+        ci, co = widths[li], widths[li + 1]
+        lim = 1.0 / math.sqrt(ci * 9)
+        W = rng.uniform(-lim, lim, (co, ci, 3, 3))
+        Wf, bf = fold_bn(x, W, 1, bound=bound)
+        layers.append((Wf, bf))
+        y = torch.tensor(_plain_conv(x, Wf, 1) + bf[:, None, None])
+        y = torch.nn.functional.gelu(y * bound)
+        x = torch.nn.functional.avg_pool2d(y[None], 2)[0].numpy()
+    return layers
