@@ -116,7 +116,8 @@ def cpu_baseline(sample_rotations=2):
     wl = workloads.cifar_conv_bn(0)
     lin = Ly.image_layout(16, 32, o.N)
     ct = o.encrypt(Ly.pack(lin, wl.x)[0], LEVEL, nonce=1)
-    amounts = [1, 32][:sample_rotations]
+    amounts = [1, 32, 31, 33, 63, 64, 65, 95, 96, 97, 127, 128][:sample_rotations]
+    amounts += [2 + i for i in range(max(0, sample_rotations - len(amounts)))]
     for a in amounts:
         o.gen_rotation_key(a)
     t0 = time.perf_counter()
@@ -171,14 +172,19 @@ def run_block(args, ws, rank, local):
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
-                                                   "tma": H.HE_KEY_STREAM_TMA}[args.key_stream])
+                                                   "tma": H.HE_KEY_STREAM_TMA,
+                                                   "split": H.HE_KEY_STREAM_SPLIT}[args.key_stream])
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]
     q = info["q"]
-    x0, (W1, b1), (W2, b2) = workloads.resnet_block(0)
+    # --small: the profiling case (16 channels = 2 shards, two images at levels 8 and 12,
+    # layer planned at level 12: a few GB on the device)
+    levels = (8, 12) if args.small else BLOCK_LEVELS
+    x0, (W1, b1), (W2, b2) = workloads.resnet_block(0, c=16 if args.small else 64)
     c, m = x0.shape[0], x0.shape[1]
-    imgs = [x0] + [workloads.image(c, m, 10 + i) for i in range(len(BLOCK_LEVELS) - 1)]
-    top1, top2 = 19, 19 - 1 - (DEG - 1).bit_length() - 1
+    imgs = [x0] + [workloads.image(c, m, 10 + i) for i in range(len(levels) - 1)]
+    top1 = max(levels)
+    top2 = top1 - 1 - (DEG - 1).bit_length() - 1
     t_setup = time.perf_counter()
     lay = H.he_layout_image(c, m, N)
     conv1 = H.he_conv_create(ctx, lay, W1, b1, 1, 1, top1, pr.scale)
@@ -190,30 +196,34 @@ def run_block(args, ws, rank, local):
     cheb = host.chebyshev_coeffs(host.gelu, DEG, -8.0, 8.0)
     ns1, ns2 = lay.n_shards, lay1.n_shards
     xs = []
-    for i, (img, lv) in enumerate(zip(imgs, BLOCK_LEVELS)):
+    for i, (img, lv) in enumerate(zip(imgs, levels)):
         xs += host.encrypt_image(ctx, lay, img, lv, pr.scale, nonce0=100 * i)
-    y1 = [H.he_ct_alloc(ctx, top1 - 1) for _ in range(len(BLOCK_LEVELS) * ns1)]
-    y2 = [H.he_ct_alloc(ctx, top2 - 1) for _ in range(len(BLOCK_LEVELS) * ns2)]
+    y1 = [H.he_ct_alloc(ctx, top1 - 1) for _ in range(len(levels) * ns1)]
+    y2 = [H.he_ct_alloc(ctx, top2 - 1) for _ in range(len(levels) * ns2)]
     # GELU output scale chosen so that conv2's output lands on the input's scale (residual)
-    tgt = [pr.scale * float(q[lv - 1 - (DEG - 1).bit_length() - 1]) / float(q[top2]) for lv in BLOCK_LEVELS]
+    tgt = [pr.scale * float(q[lv - 1 - (DEG - 1).bit_length() - 1]) / float(q[top2]) for lv in levels]
+    tgt_all = [t for t in tgt for _ in range(lay.n_shards)]
     setup_s = time.perf_counter() - t_setup
 
     def rot_count(conv):
         u, v, a, _ = H.he_conv_export_plan(conv, N)
         return len({(int(uu), int(aa)) for uu, aa in zip(u, a) if int(aa) % N != 0})
-    ks_per_step = len(BLOCK_LEVELS) * (rot_count(conv1) + rot_count(conv2) + ns1 * (DEG - 1))
+    ks_per_step = len(levels) * (rot_count(conv1) + rot_count(conv2) + ns1 * (DEG - 1))
     pt_bytes = sum(H.he_conv_n_terms(cv) * (lv + 1 + info["K"]) * n * 8 for cv, lv in ((conv1, top1), (conv2, top2)))
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
 
     def step(mode):
-        H.he_conv_run_batch(ctx, conv1, xs, y1, len(BLOCK_LEVELS), mode, stream)
-        for i in range(len(BLOCK_LEVELS)):
-            for v in range(ns1):
-                H.he_poly_eval(ctx, y1[i * ns1 + v], cheb, tgt[i], stream)
-        H.he_conv_run_batch(ctx, conv2, y1, y2, len(BLOCK_LEVELS), mode, stream)
-        for i in range(len(BLOCK_LEVELS)):
+        H.he_conv_run_batch(ctx, conv1, xs, y1, len(levels), mode, stream)
+        if mode == H.HE_PLAIN:                   # the per-ciphertext path
+            for i in range(len(levels)):
+                for v in range(ns1):
+                    H.he_poly_eval(ctx, y1[i * ns1 + v], cheb, tgt[i], stream)
+        else:                                    # every ciphertext of a level through the tree together
+            H.he_poly_eval_many(ctx, y1, cheb, tgt_all, stream)
+        H.he_conv_run_batch(ctx, conv2, y1, y2, len(levels), mode, stream)
+        for i in range(len(levels)):
             for v in range(ns2):
                 H.he_add(ctx, y2[i * ns2 + v], xs[i * ns1 + v], stream)
 
@@ -257,9 +267,20 @@ def run_block(args, ws, rank, local):
             H.he_graph_destroy(gk)
         return ms, launches, tr
 
+    if args.profile_step:
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        step(H.HE_FUSED)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return
+    # the roofline follows the kernel that carries the key switches of this step
+    trace = args.trace
+    if trace == "ipmac" and ("-> split" in H.he_ctx_tuning_log(ctx) or args.key_stream == "split"):
+        trace = "rmac"
     clocks = Clocks(local)
     clocks.start()
-    ms_f, launches_f, tr = timed(H.HE_FUSED, args.steps, args.trace)
+    ms_f, launches_f, tr = timed(H.HE_FUSED, args.steps, trace)
     clk = clocks.stop()
     # sampled output check: image 0 (input level 8), decrypted, against the FP64 block with
     # the same polynomial
@@ -275,7 +296,7 @@ def run_block(args, ws, rank, local):
     if tr and tr["launches"]:
         per_launch_ms = tr["ms"] / tr["launches"]
         achieved = tr["bytes"] / tr["launches"] / (per_launch_ms * 1e-3) / 1e9
-        roof = {"kernel": args.trace, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+        roof = {"kernel": trace, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
                 "launches": tr["launches"], "ms_per_launch": per_launch_ms,
                 "share_of_step": tr["ms"] / (ms_f * args.steps)}
@@ -284,8 +305,9 @@ def run_block(args, ws, rank, local):
                 "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_f,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
                 "data": "synthetic",
-                "config": {"workload": BLOCK_WORKLOAD, "input_levels": list(BLOCK_LEVELS),
-                           "key_switches_per_step": ks_per_step, "images": len(BLOCK_LEVELS),
+                "config": {"workload": BLOCK_WORKLOAD if not args.small else "profiling case: " + BLOCK_WORKLOAD.replace("64x56x56", "16x56x56"),
+                           "input_levels": list(levels),
+                           "key_switches_per_step": ks_per_step, "images": len(levels),
                            "mode": "each conv of the batch is one fused launch over all images and levels",
                            "cuda_graph": True, "key_stream": args.key_stream,
                            "autotuner": H.he_ctx_tuning_log(ctx).strip().splitlines(),
@@ -296,7 +318,7 @@ def run_block(args, ws, rank, local):
                 "plain": {"ms_per_step": ms_p, "value": ws * ks_per_step / (ms_p * 1e-3),
                           "batched_speedup": ms_p / ms_f,
                           "note": "image by image, per-ciphertext key switches, same plaintexts"},
-                "check": {"image": 0, "input_level": BLOCK_LEVELS[0], "max_err_rel_range": err,
+                "check": {"image": 0, "input_level": levels[0], "max_err_rel_range": err,
                           "tolerance": 2.0 ** -20},
                 "gpu_launches": int(launches_f), "roofline": roof, "clocks": clk}
         print(json.dumps(line), flush=True)
@@ -321,9 +343,9 @@ def main():
                     help="profiling case: same ring, 2-channel 32x32 conv (17 rotations, ~2 GB of keys)")
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, warm up, then run one batched step between cudaProfilerStart/Stop")
-    ap.add_argument("--key-stream", default="auto", choices=["auto", "ldg", "tma"],
-                    help="how the fused kernel brings key words on chip: autotuned (default), "
-                         "vector loads, or a TMA tile pipeline")
+    ap.add_argument("--key-stream", default="auto", choices=["auto", "ldg", "tma", "split"],
+                    help="key-switch + MAC form: autotuned (default), the fused kernel with vector "
+                         "loads or a TMA tile pipeline, or the split form (inner products, then MAC)")
     ap.add_argument("--no-graph", action="store_true", help="launch the fused step eagerly, not as a CUDA graph")
     ap.add_argument("--workload", default="cifar-layer", choices=["cifar-layer", "resnet-block"],
                     help="cifar-layer: the headline layer; resnet-block: the batched mixed-level block")
@@ -350,7 +372,8 @@ def main():
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
-                                                   "tma": H.HE_KEY_STREAM_TMA}[args.key_stream])
+                                                   "tma": H.HE_KEY_STREAM_TMA,
+                                                   "split": H.HE_KEY_STREAM_SPLIT}[args.key_stream])
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]
     wl = workloads.cifar_conv_bn(0, c=2) if args.small else workloads.cifar_conv_bn(0)
@@ -518,7 +541,7 @@ def main():
             "clocks": clk,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(2)
+            line["cpu_baseline"] = cpu_baseline(48)          # ~10-15 s of oracle work
         print(json.dumps(line), flush=True)
     H.he_ctx_check(ctx, stream)
     H.he_graph_destroy(graph)

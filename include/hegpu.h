@@ -256,6 +256,20 @@ int he_mul_relin(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out, void *
 int he_conv_create(he_ctx *ctx, const he_layout *in, const double *W, const double *bias,
                    int co, int ci, int kh, int kw, int stride, int pad, int level,
                    double in_scale, he_conv **out);
+/* The same convolution in the factored two-stage form for an input in channel shards (each
+ * shard holds consecutive rows of one channel, channels in order; Sec. 4.1 "With Channel
+ * Shards", Eq. 7): stage 1 forms Y_{f,h,t} = sum_{h'} B_{h,h',t} (.) rot_{a_t}(X_{f,h'}) with
+ * binary masks B (own and neighbouring shard of tap t share the amount a_t) encoded at scale
+ * q_level, and rescales; stage 2 weights them with the integer scalars round(w q_{level-1})
+ * (round half away from zero), rescales, and adds the bias.  Two levels (four with stride 2)
+ * instead of one, and at most 2 H T mask plaintexts (H shards per channel, T taps) instead of
+ * co ci H T diagonals, which is what makes high-resolution channel-shard layers fit in HBM.
+ * For this form he_conv_n_terms counts the masks and he_conv_export_plan returns, per mask,
+ * u = source shard h', v = shard h, a = a_t and the mask; he_conv_import_plaintexts takes the
+ * masks [n_masks][n] and the bias [n_out][n] (at level - 2).  Not available for batches and forks. */
+int he_conv_create_factored(he_ctx *ctx, const he_layout *in, const double *W, const double *bias,
+                            int co, int ci, int kh, int kw, int stride, int pad, int level,
+                            double in_scale, he_conv **out);
 void he_conv_destroy(he_conv *conv);
 int he_conv_out_layout(const he_conv *conv, he_layout *out);
 int he_conv_out_level(const he_conv *conv);
@@ -321,6 +335,11 @@ int he_pool_run(he_ctx *ctx, he_pool *pool, he_ct *const *in, he_ct **out, int m
  * (scale `target_scale`, level lowered by the depth). */
 int he_poly_eval(he_ctx *ctx, he_ct *io, const double *cheb, int deg, double target_scale,
                  void *stream);
+/* The same polynomial on m ciphertexts (any levels; target_scales[m]): the ones at one level go
+ * through the tree together, each tree depth one batched relinearisation for all of them.  Each
+ * ciphertext gets exactly the bits he_poly_eval gives it. */
+int he_poly_eval_many(he_ctx *ctx, he_ct *const *io, int m, const double *cheb, int deg,
+                      const double *target_scales, void *stream);
 
 /* Convenience wrappers: create, run, destroy. */
 int he_hconv2d(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, const double *W,

@@ -32,6 +32,8 @@ The two roundings are centred on purpose: a [0, q) (floor) choice adds a bias of
 2^-20 accuracy target.
   mult         (a0 b0, a0 b1 + a1 b0, a1 b1), relinearise with s' = s^2, rescale
 """
+import math
+
 import numpy as np
 
 from . import _lib
@@ -195,6 +197,12 @@ class Context:
     # ------------------------------------------------------------ keys
     def _gen_ksk(self, key_id, s_prime_int):
         """Hybrid key-switching key for s' (integer polynomial), eval form over Q_L u P."""
+        # hybrid key switching needs P at least as large as every digit's modulus: the
+        # inner product's error grows with the digit modulus and ModDown divides it by P
+        P = math.prod(self.p)
+        for dig in self.digits(self.L):
+            if math.prod(self.q[i] for i in dig) > P:
+                raise ValueError("special modulus P smaller than a digit modulus")
         L = self.L
         mods = self.mods(L, True)
         psis = self.psis(L, True)

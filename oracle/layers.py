@@ -358,6 +358,148 @@ def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None, pt_scale=None):
     return out
 
 
+# ============================================================================ factored conv
+@dataclass
+class FactoredPlan:
+    """Channel-shard convolution in two stages (Eq. 7 with the weights taken out of the masks).
+
+    Every shard holds R = N/M consecutive rows of one channel, H = M/R shards per channel.  For
+    tap t = (k, l) the source pixel of an output slot lies in the same shard or in a
+    neighbouring one, always at the same rotation amount a_t = ((k - pad) M + (l - pad)) mod N
+    (the shared amount of Eq. 7).  Stage 1 forms, per input channel f, shard h and tap t,
+        Y_{f,h,t} = sum_{h'} B_{h,h',t} (.) rot_{a_t}(X_{f,h'})
+    with binary masks B that depend on (h, h', t) only (every channel has the same geometry);
+    stage 2 weights them with integer scalars:
+        out_{o,h} = sum_{f,t} round(W[o][f][t] q) Y_{f,h,t} / q + bias.
+    Two levels instead of one; mask plaintexts number 2 H T at most instead of co ci H T."""
+    lin: Layout
+    lout: Layout
+    H: int                    # shards per channel
+    pad: int
+    taps: list                # [(k, l)]
+    amounts: list             # a_t per tap
+    masks: dict               # (h, h_src, t) -> float64 [N] in {0, 1}
+    W: np.ndarray             # [co][ci][kh][kw]
+    bias: np.ndarray          # [n_out][N]
+
+    def sources(self, f, h, t):
+        """[(input shard, mask key)] summed into Y_{f,h,t}."""
+        return [(f * self.H + hs, key) for key in sorted(self.masks) if key[0] == h and key[2] == t
+                for hs in [key[1]]]
+
+
+def conv_plan_factored(lin: Layout, W, bias, pad):
+    W = np.asarray(W, dtype=np.float64)
+    co, ci, kh, kw = W.shape
+    assert ci == lin.c and lin.nb == 1 and lin.B == lin.N, "channel shards only"
+    M, N, R = lin.M, lin.N, lin.rows_per_block
+    H = M // R
+    assert lin.n_shards == ci * H
+    lout = image_layout(co, lin.m, N)
+    i = np.arange(N)
+    taps = [(k, l) for k in range(kh) for l in range(kw)]
+    amounts, masks = [], {}
+    for t, (k, l) in enumerate(taps):
+        a = ((k - pad) * M + (l - pad)) % N
+        amounts.append(a)
+        for h in range(H):
+            ch, y, x, valid = slot_coords(lout, h)      # shard h of output channel 0
+            ys, xs = y + k - pad, x + l - pad
+            ok = valid & (ys >= 0) & (ys < lin.m) & (xs >= 0) & (xs < lin.m)
+            hs = np.where(ok, ys // R, -1)
+            j = (ys - hs * R) * M + xs
+            assert np.all(((j - i) % N)[ok] == a), "own and neighbour reads share the amount"
+            for h_src in np.unique(hs[ok]):
+                masks[(h, int(h_src), t)] = (ok & (hs == h_src)).astype(np.float64)
+    bv = np.zeros((lout.n_shards, N))
+    if bias is not None:
+        bias = np.asarray(bias, dtype=np.float64)
+        for v in range(lout.n_shards):
+            ch, y, x, valid = slot_coords(lout, v)
+            bv[v, valid] = bias[ch[valid]]
+    return FactoredPlan(lin, lout, H, pad, taps, amounts, masks, W, bv)
+
+
+def factored_slots(plan: FactoredPlan, slots):
+    """Slot simulator of both stages (float64 weights)."""
+    co, ci = plan.W.shape[:2]
+    H, N = plan.H, plan.lin.N
+    out = np.zeros((plan.lout.n_shards, N))
+    for f in range(ci):
+        for h in range(H):
+            for t, (k, l) in enumerate(plan.taps):
+                Y = np.zeros(N)
+                for (u, key) in plan.sources(f, h, t):
+                    Y += plan.masks[key] * np.roll(slots[u], -plan.amounts[t])
+                for o in range(co):
+                    out[o * H + h] += plan.W[o, f, k, l] * Y
+    return out + plan.bias
+
+
+def round_half_away(x):
+    return int(math.copysign(math.floor(abs(x) + 0.5), x))
+
+
+def factored_scalars(plan: FactoredPlan, q):
+    """Stage-2 integer weights round(W[o][f][t] q), [co][ci][T] python ints."""
+    co, ci = plan.W.shape[:2]
+    return [[[round_half_away(float(plan.W[o, f, k, l]) * float(q)) for (k, l) in plan.taps]
+             for f in range(ci)] for o in range(co)]
+
+
+def mask_plaintexts(plan: FactoredPlan, n, S):
+    """Integer plaintexts of the masks at scale S: {(h, h_src, t): int64 [n]}."""
+    return {key: encode(m, n, S) for key, m in plan.masks.items()}
+
+
+def conv_he_factored(ctx, plan: FactoredPlan, cts, mask_pts=None, bias_pts=None, raised=False):
+    """Both stages on oracle ciphertexts (inputs at one level l, scale s): stage 1 at level l
+    (masks at scale q_l, rescale), stage 2 with integer scalars round(w q_{l-1}) (rescale),
+    then the bias: output at level l - 2.  raised=True takes stage 1 with one ModDown per Y
+    (raised_stage) instead of one per rotation; different bits, same decryption."""
+    from .ckks import Ciphertext
+    level, scale = cts[0].level, cts[0].scale
+    assert all(c.level == level and c.scale == scale for c in cts)
+    co, ci = plan.W.shape[:2]
+    H, T = plan.H, len(plan.taps)
+    if mask_pts is None:
+        mask_pts = mask_plaintexts(plan, ctx.n, float(ctx.q[level]))
+    ykeys = [(f, h, t) for f in range(ci) for h in range(H) for t in range(T)]
+    Y = {}
+    if raised:
+        terms = {y: [(u, plan.amounts[t], mask_pts[key]) for (u, key) in plan.sources(f, h, t)]
+                 for y, (f, h, t) in enumerate(ykeys)}
+        outs = raised_stage(ctx, cts, terms)
+        for y, key in enumerate(ykeys):
+            outs[y].scale = scale * float(ctx.q[level])
+            Y[key] = ctx.rescale(outs[y])
+    else:
+        R = rotate_all(ctx, cts, lambda u: sorted({plan.amounts[t] for t in range(T)}))
+        for (f, h, t) in ykeys:
+            src = plan.sources(f, h, t)
+            Y[(f, h, t)] = mac_rescale(ctx, R, [(u, plan.amounts[t]) for (u, _) in src],
+                                       [mask_pts[key] for (_, key) in src], level, scale)
+    l1 = level - 1
+    mods = ctx.mods(l1)
+    Wt = factored_scalars(plan, ctx.q[l1])
+    out = []
+    for o in range(co):
+        for h in range(H):
+            acc = [np.zeros((l1 + 1, ctx.n), dtype=np.uint64) for _ in range(2)]
+            for f in range(ci):
+                for t in range(T):
+                    w = np.array([Wt[o][f][t] % int(q) for q in mods], dtype=np.uint64)
+                    y = Y[(f, h, t)]
+                    for k in range(2):
+                        acc[k] = ctx.add(acc[k], ctx.mul_scalar(y.c[k], w, mods), mods)
+            ct = ctx.rescale(Ciphertext(np.stack(acc), l1, Y[(0, h, 0)].scale * float(ctx.q[l1])))
+            v = o * H + h
+            bpt = bias_pts[v] if bias_pts is not None else encode(plan.bias[v], ctx.n, ct.scale)
+            ct.c[0] = ctx.add(ct.c[0], ctx.reduce_int(bpt, ctx.mods(ct.level)), ctx.mods(ct.level))
+            out.append(ct)
+    return out
+
+
 # ============================================================================ pooling
 @dataclass
 class PoolPlan:

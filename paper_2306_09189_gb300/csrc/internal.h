@@ -243,46 +243,49 @@ struct fgrp {
     const famt *amts;
     const fent *ents;
     int n_amt, level, beta, pt_level;
-    u64 *acc;               // [2V][l+1+K][n]  raised-basis inner products x plaintexts
-    u64 *base;              // [2V][l+1][n]    plaintext x rotated c0 (and unrotated c1)
+    int nv;                 // outputs present in this group (<= V); only these are stored
+    u64 *acc;               // [2V][l+1+K][n]  raised-basis (folded) inner products x plaintexts
 };
 // One launch over n_grp groups (any mix of levels): the grid walks global primes, and the
 // groups sharing a (coefficient tile, prime) are adjacent in launch order, so each key and
 // plaintext word is fetched from DRAM once and served to the other groups from L2.
 // form: HE_KEY_STREAM_LDG or HE_KEY_STREAM_TMA (TMA needs beta <= 4 in every group).
 int k_ipmac(const he_ctx *ctx, const fgrp *grps_dev, int n_grp, int V, int max_beta, double bytes,
-            double mulmods, int form, cudaStream_t s);
-// Split form of a fused stage (same bits): (1) the raised inner product u_{s,a} of every
-// (source, amount) is written to HBM once (amount-major: each key read once per launch), then
-// (2) a raised-basis MAC forms sum pt (.) u over Q u P for HE_RV outputs per pass.  Cheaper
+            double mulmods, int form, cudaStream_t s);   // acc only: the base folds in (see kernels.cu)
+// Split form of a fused stage (same bits): (1) the raised inner product of every (source,
+// amount), with [P]_q phi_a(c0) folded into its first polynomial (and [P]_q (c0, c1) for
+// amount 0), is written to HBM once (amount-major: each key read once per launch); then
+// (2) a raised-basis MAC forms sum pt (.) U over Q u P for HE_RV outputs per pass.  Cheaper
 // than the fused kernel when many output groups would each recompute the inner products.
-#define HE_RV 4
+#define HE_RV 8
 struct uent {
-    const u64 *D;           // the source's raised digits
+    const u64 *D;           // the source's raised digits (keyed amounts)
     u64 *U;                 // output [2][l+1+K][n]
+    const u64 *src;         // the source ciphertext (c0, c1 at src + ps)
+    size_t ps;
 };
 struct ugrp {               // inner products of one stage (one image at one level)
-    const famt *amts;       // keyed amounts; entries index uent
+    const famt *amts;       // amounts (key null for amount 0); entries index uent
     const uent *ents;
     int n_amt, level, beta;
 };
 struct rterm {
-    const u64 *U;           // raised inner product of (s, a), null for amount 0
-    const u64 *src;         // source ciphertext (c0, c1 at src + ps)
-    size_t ps;
-    u64 g;                  // Galois element of a (gathers c0)
+    const u64 *U;           // folded raised inner product of (s, a)
     const u64 *pt[HE_RV];   // per output of the group: plaintext, HE_PT_ONE or null
 };
 struct rgrp {               // HE_RV outputs of one stage
     const rterm *terms;
     int n_terms, level, pt_level;
-    int accumulate;         // add to acc/base (mod q) instead of overwriting: later amount chunks
+    int nv;                 // outputs present in this group (<= HE_RV); only these are stored
+    int accumulate;         // add to acc (mod q) instead of overwriting: later amount chunks
     u64 *acc;               // [2 HE_RV][l+1+K][n]
-    u64 *base;              // [2 HE_RV][l+1][n]
 };
 int k_ip_amounts(const he_ctx *ctx, const ugrp *grps_dev, int n_grp, int max_beta, double bytes, cudaStream_t s);
 int k_rmac(const he_ctx *ctx, const rgrp *grps_dev, int n_grp, double bytes, double mulmods, cudaStream_t s);
 void he_tune_note(he_ctx *ctx, const std::string &line);
+// factored channel-shard conv, stage 2 (see kernels.cu); Y ct j at Y + j ystride, poly c at + c yps
+int k_smac(const he_ctx *ctx, const u64 *Y, size_t ystride, size_t yps, const u64 *Wm, int co, int ci, int H, int T,
+           int level, u64 *out, size_t ostride, size_t ops, cudaStream_t s);
 int k_selftest_bounded_wait(const he_ctx *ctx, cudaStream_t s);
 int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u64 *res, int n,
               const u64 *cst, int level, u64 *out, size_t out_ps, cudaStream_t s);

@@ -694,8 +694,13 @@ __device__ __forceinline__ bool grp_pos(const KP &kp, const fgrp *grps, int n_gr
 // once (two coefficients, beta digits, both polynomials) and applies them to every source
 // shard that uses the amount; V <= 2 outputs per group.  The next amount's descriptors are
 // fetched while the current one computes, so each amount costs one memory round trip.
+//
+// The unrotated part folds into the raised sum: on a q-limb, u_0 += [P]_q phi(c0) and, for
+// amount 0, u = [P]_q (c0, c1).  ModDown(acc + P b) = ModDown(acc) + b exactly (P b vanishes
+// mod every p), so the outputs need no separate base sums and the ModDown adds nothing else.
 template <int V, int B>
-__global__ void __launch_bounds__(TB, (V == 1 && B == 4) ? 2 : 1) ipmac_kernel(KP kp, const fgrp *grps, int n_grp) {
+__global__ void __launch_bounds__(TB, (V == 1 && B == 4) ? 2 : 1) ipmac_kernel(KP kp, const fgrp *grps, int n_grp,
+                                                                               const u64 *pmod) {
     fgrp P;
     int tile, t, ptl;
     if (!grp_pos(kp, grps, n_grp, P, tile, t, ptl)) return;
@@ -704,16 +709,18 @@ __global__ void __launch_bounds__(TB, (V == 1 && B == 4) ? 2 : 1) ipmac_kernel(K
     const int nq = P.level + 1;
     const int ext = nq + kp.K;
     const int beta = P.beta;
+    const bool isq = t < nq;
     const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
     const u64 one = to_mont(1, q, qi, r2);
+    const u64 Pm = isq ? to_mont(pmod[kl], q, qi, r2) : 0;     // [P]_q in Montgomery form
     const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
     const size_t off = (size_t)t * kp.n + k, ptoff = (size_t)ptl * kp.n + k;
     const u64 stream = policy_evict_first(), keep = policy_evict_last();
-    u128 a0[V][2], a1[V][2], b0[V][2], b1[V][2];
+    u128 a0[V][2], a1[V][2];
 #pragma unroll
     for (int v = 0; v < V; v++)
 #pragma unroll
-        for (int e = 0; e < 2; e++) a0[v][e] = a1[v][e] = b0[v][e] = b1[v][e] = 0;
+        for (int e = 0; e < 2; e++) a0[v][e] = a1[v][e] = 0;
     const int n_amt = P.n_amt;
     famt A = n_amt > 0 ? P.amts[0] : famt{};
     fent E = (n_amt > 0 && A.e0 < A.e1) ? P.ents[A.e0] : fent{};
@@ -744,6 +751,12 @@ __global__ void __launch_bounds__(TB, (V == 1 && B == 4) ? 2 : 1) ipmac_kernel(K
                 const u64 *pp = E.pt[v];
                 p[v] = pp == HE_PT_ONE ? make_ulonglong2(one, one) : (pp ? ld2_hint(pp + ptoff, stream) : make_ulonglong2(0, 0));
             }
+            ulonglong2 cc = make_ulonglong2(0, 0), c1 = make_ulonglong2(0, 0);
+            if (isq) {
+                cc = ld2_hint(E.src + (size_t)t * kp.n + kb, keep);
+                if (!A.key) c1 = ld2_hint(E.src + E.ps + off, keep);
+            }
+            u64 u00 = 0, u01 = 0, u10 = 0, u11 = 0;
             if (A.key) {
                 u128 s0[2] = {0, 0}, s1[2] = {0, 0};
 #pragma unroll
@@ -756,42 +769,37 @@ __global__ void __launch_bounds__(TB, (V == 1 && B == 4) ? 2 : 1) ipmac_kernel(K
                         s1[0] += (u128)d0 * kk1[j].x;
                         s1[1] += (u128)d1 * kk1[j].y;
                     }
-                const u64 u00 = redc(s0[0], q, qi), u01 = redc(s0[1], q, qi);
-                const u64 u10 = redc(s1[0], q, qi), u11 = redc(s1[1], q, qi);
-#pragma unroll
-                for (int v = 0; v < V; v++) {
-                    a0[v][0] += (u128)p[v].x * u00;
-                    a0[v][1] += (u128)p[v].y * u01;
-                    a1[v][0] += (u128)p[v].x * u10;
-                    a1[v][1] += (u128)p[v].y * u11;
+                u00 = redc(s0[0], q, qi);
+                u01 = redc(s0[1], q, qi);
+                u10 = redc(s1[0], q, qi);
+                u11 = redc(s1[1], q, qi);
+            }
+            if (isq) {
+                const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
+                u00 = add_mod(u00, mul_mont(c00, Pm, q, qi), q);
+                u01 = add_mod(u01, mul_mont(c01, Pm, q, qi), q);
+                if (!A.key) {
+                    u10 = mul_mont(c1.x, Pm, q, qi);
+                    u11 = mul_mont(c1.y, Pm, q, qi);
                 }
             }
-            if (t < nq) {
-                const ulonglong2 cc = ld2_hint(E.src + (size_t)t * kp.n + kb, keep);
-                const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
-                ulonglong2 c1 = make_ulonglong2(0, 0);
-                if (!A.key) c1 = ld2_hint(E.src + E.ps + off, keep);
 #pragma unroll
-                for (int v = 0; v < V; v++) {
-                    b0[v][0] += (u128)p[v].x * c00;
-                    b0[v][1] += (u128)p[v].y * c01;
-                    b1[v][0] += (u128)p[v].x * c1.x;
-                    b1[v][1] += (u128)p[v].y * c1.y;
-                }
+            for (int v = 0; v < V; v++) {
+                a0[v][0] += (u128)p[v].x * u00;
+                a0[v][1] += (u128)p[v].y * u01;
+                a1[v][0] += (u128)p[v].x * u10;
+                a1[v][1] += (u128)p[v].y * u11;
             }
         }
         A = An;
         E = En;
     }
 #pragma unroll
-    for (int v = 0; v < V; v++) {
-        st2(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, redc(a0[v][0], q, qi), redc(a0[v][1], q, qi));
-        st2(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
-        if (t < nq) {
-            st2(P.base + ((size_t)(2 * v) * nq) * kp.n + off, redc(b0[v][0], q, qi), redc(b0[v][1], q, qi));
-            st2(P.base + ((size_t)(2 * v + 1) * nq) * kp.n + off, redc(b1[v][0], q, qi), redc(b1[v][1], q, qi));
+    for (int v = 0; v < V; v++)
+        if (v < P.nv) {
+            st2(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, redc(a0[v][0], q, qi), redc(a0[v][1], q, qi));
+            st2(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
         }
-    }
 }
 
 // ---- TMA-pipelined form: each keyed amount's key tile (2 beta limb segments of 512 words)
@@ -839,7 +847,8 @@ __device__ __forceinline__ void tma_load(unsigned dst, const void *src, unsigned
 }
 
 template <int V>
-__global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, int n_grp, int *err) {
+__global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, int n_grp, int *err,
+                                                       const u64 *pmod) {
     constexpr int NS = TMA_STAGES;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     fgrp P;
@@ -858,6 +867,8 @@ __global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, 
     const int ext = nq + kp.K;
     const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
     const u64 one = to_mont(1, q, qi, r2);
+    const bool isq = t < nq;
+    const u64 Pm = isq ? to_mont(pmod[kl], q, qi, r2) : 0;     // [P]_q in Montgomery form
     const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
     const size_t off = (size_t)t * kp.n + k, ptoff = (size_t)ptl * kp.n + k;
     const unsigned tile_bytes = TMA_TILE * 8;
@@ -886,11 +897,11 @@ __global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, 
         next++;
         while (next < n_amt && !amts[next].key) next++;
     }
-    u128 a0[V][2], a1[V][2], b0[V][2], b1[V][2];
+    u128 a0[V][2], a1[V][2];
 #pragma unroll
     for (int v = 0; v < V; v++)
 #pragma unroll
-        for (int e = 0; e < 2; e++) a0[v][e] = a1[v][e] = b0[v][e] = b1[v][e] = 0;
+        for (int e = 0; e < 2; e++) a0[v][e] = a1[v][e] = 0;
     bool failed = false;
     for (int i = 0; i < n_amt; i++) {
         const famt A = amts[i];
@@ -918,6 +929,12 @@ __global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, 
                 const u64 *pp = E.pt[v];
                 p[v] = pp == HE_PT_ONE ? make_ulonglong2(one, one) : (pp ? ld2_hint(pp + ptoff, stream) : make_ulonglong2(0, 0));
             }
+            ulonglong2 cc = make_ulonglong2(0, 0), c1 = make_ulonglong2(0, 0);
+            if (isq) {
+                cc = ld2_hint(E.src + (size_t)t * kp.n + kb, keep);
+                if (!A.key) c1 = ld2_hint(E.src + E.ps + off, keep);
+            }
+            u64 u00 = 0, u01 = 0, u10 = 0, u11 = 0;
             if (A.key) {
                 u128 s0[2] = {0, 0}, s1[2] = {0, 0};
 #pragma unroll
@@ -932,28 +949,26 @@ __global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, 
                         s1[0] += (u128)d0 * k1v.x;
                         s1[1] += (u128)d1 * k1v.y;
                     }
-                const u64 u00 = redc(s0[0], q, qi), u01 = redc(s0[1], q, qi);
-                const u64 u10 = redc(s1[0], q, qi), u11 = redc(s1[1], q, qi);
-#pragma unroll
-                for (int v = 0; v < V; v++) {
-                    a0[v][0] += (u128)p[v].x * u00;
-                    a0[v][1] += (u128)p[v].y * u01;
-                    a1[v][0] += (u128)p[v].x * u10;
-                    a1[v][1] += (u128)p[v].y * u11;
+                u00 = redc(s0[0], q, qi);
+                u01 = redc(s0[1], q, qi);
+                u10 = redc(s1[0], q, qi);
+                u11 = redc(s1[1], q, qi);
+            }
+            if (isq) {                             // fold [P]_q phi(c0) (and [P]_q c1 at amount 0)
+                const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
+                u00 = add_mod(u00, mul_mont(c00, Pm, q, qi), q);
+                u01 = add_mod(u01, mul_mont(c01, Pm, q, qi), q);
+                if (!A.key) {
+                    u10 = mul_mont(c1.x, Pm, q, qi);
+                    u11 = mul_mont(c1.y, Pm, q, qi);
                 }
             }
-            if (t < nq) {
-                const ulonglong2 cc = ld2_hint(E.src + (size_t)t * kp.n + kb, keep);
-                const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
-                ulonglong2 c1 = make_ulonglong2(0, 0);
-                if (!A.key) c1 = ld2_hint(E.src + E.ps + off, keep);
 #pragma unroll
-                for (int v = 0; v < V; v++) {
-                    b0[v][0] += (u128)p[v].x * c00;
-                    b0[v][1] += (u128)p[v].y * c01;
-                    b1[v][0] += (u128)p[v].x * c1.x;
-                    b1[v][1] += (u128)p[v].y * c1.y;
-                }
+            for (int v = 0; v < V; v++) {
+                a0[v][0] += (u128)p[v].x * u00;
+                a0[v][1] += (u128)p[v].y * u01;
+                a1[v][0] += (u128)p[v].x * u10;
+                a1[v][1] += (u128)p[v].y * u11;
             }
         }
         if (A.key) {
@@ -975,14 +990,11 @@ __global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, 
         return;
     }
 #pragma unroll
-    for (int v = 0; v < V; v++) {
-        st2(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, redc(a0[v][0], q, qi), redc(a0[v][1], q, qi));
-        st2(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
-        if (t < nq) {
-            st2(P.base + ((size_t)(2 * v) * nq) * kp.n + off, redc(b0[v][0], q, qi), redc(b0[v][1], q, qi));
-            st2(P.base + ((size_t)(2 * v + 1) * nq) * kp.n + off, redc(b1[v][0], q, qi), redc(b1[v][1], q, qi));
+    for (int v = 0; v < V; v++)
+        if (v < P.nv) {
+            st2(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, redc(a0[v][0], q, qi), redc(a0[v][1], q, qi));
+            st2(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
         }
-    }
 }
 
 // acc = sum_terms K_term * x_term (+ c on poly 0) over limbs 0..level, x of any higher level
@@ -1385,14 +1397,14 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
         if (!attr_ok) { he_set_error("fused kernel: shared-memory opt-in failed"); return HE_ECUDA; }
         dim3 gt((unsigned)(ctx->n / TMA_TILE) * n_grp, primes);
         if (V == 1)
-            ipmac_tma_kernel<1><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, ctx->d_err);
+            ipmac_tma_kernel<1><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, ctx->d_err, ctx->d_consts);
         else
-            ipmac_tma_kernel<2><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, ctx->d_err);
+            ipmac_tma_kernel<2><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, ctx->d_err, ctx->d_consts);
         LAUNCH_CHECK();
         return HE_OK;
     }
     dim3 g((unsigned)(ctx->n / (2 * TB)) * n_grp, primes);
-#define IPM(VV, BB) ipmac_kernel<VV, BB><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp)
+#define IPM(VV, BB) ipmac_kernel<VV, BB><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp, ctx->d_consts)
     if (V == 1) { if (max_beta <= 4) IPM(1, 4); else IPM(1, 8); }
     else { if (max_beta <= 4) IPM(2, 4); else IPM(2, 8); }
 #undef IPM
@@ -1413,58 +1425,70 @@ __device__ __forceinline__ bool lvl_pos(const KP &kp, int level, int &t) {
     return true;
 }
 
-template <int B>
-__global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps, int n_grp) {
-    const ugrp P = grps[blockIdx.x % n_grp];
-    const int tile = blockIdx.x / n_grp;
-    int t;
-    if (!lvl_pos(kp, P.level, t)) return;
-    const int k = tile * TB + threadIdx.x;
-    const int kl = blockIdx.y;
-    const int ext = P.level + 1 + kp.K;
-    const int beta = P.beta;
-    const u64 q = kp.q[kl], qi = kp.qinv[kl];
-    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
-    const u64 stream = policy_evict_first(), keep = policy_evict_last();
-    for (int i = 0; i < P.n_amt; i++) {
-        const famt A = P.amts[i];
-        const int ks = autom_index(k, A.g, kp.logn);
-        u64 k0[B], k1[B];
-#pragma unroll
-        for (int j = 0; j < B; j++)
-            if (j < beta) {
-                const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
-                asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(k0[j]) : "l"(kp0), "l"(stream));
-                asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(k1[j]) : "l"(kp0 + kstride), "l"(stream));
-            }
-        for (int e = A.e0; e < A.e1; e++) {
-            const uent E = P.ents[e];
-            u128 a0 = 0, a1 = 0;
-#pragma unroll
-            for (int j = 0; j < B; j++)
-                if (j < beta) {
-                    u64 d;
-                    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;"
-                                 : "=l"(d) : "l"(E.D + ((size_t)j * ext + t) * kp.n + ks), "l"(keep));
-                    a0 += (u128)d * k0[j];
-                    a1 += (u128)d * k1[j];
-                }
-            E.U[(size_t)t * kp.n + k] = redc(a0, q, qi);
-            E.U[((size_t)ext + t) * kp.n + k] = redc(a1, q, qi);
-        }
-    }
-}
-
 __device__ __forceinline__ u64 ld_hint(const u64 *p, u64 pol) {
     u64 r;
     asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
     return r;
 }
 
-// acc_v = sum_terms pt_v (.) U (Q u P), base_v = sum_terms pt_v (.) phi(c0) (+ pt_v (.) c1 for the
-// amount-0 terms) over Q; HE_RV outputs per thread, the next term's words loaded while the
-// current one is accumulated.
-__global__ void __launch_bounds__(TB) rmac_kernel(KP kp, const rgrp *grps, int n_grp) {
+template <int B>
+__global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps, int n_grp, const u64 *pmod) {
+    const ugrp P = grps[blockIdx.x % n_grp];
+    const int tile = blockIdx.x / n_grp;
+    int t;
+    if (!lvl_pos(kp, P.level, t)) return;
+    const int k = tile * TB + threadIdx.x;
+    const int kl = blockIdx.y;
+    const int nq = P.level + 1, ext = nq + kp.K;
+    const int beta = P.beta;
+    const bool isq = t < nq;
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 Pm = isq ? to_mont(pmod[kl], q, qi, r2) : 0;
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    const size_t off = (size_t)t * kp.n + k;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    for (int i = 0; i < P.n_amt; i++) {
+        const famt A = P.amts[i];
+        const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
+        u64 k0[B], k1[B];
+        if (A.key) {
+#pragma unroll
+            for (int j = 0; j < B; j++)
+                if (j < beta) {
+                    const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+                    k0[j] = ld_hint(kp0, stream);
+                    k1[j] = ld_hint(kp0 + kstride, stream);
+                }
+        }
+        for (int e = A.e0; e < A.e1; e++) {
+            const uent E = P.ents[e];
+            u64 u0 = 0, u1 = 0;
+            if (A.key) {
+                u128 a0 = 0, a1 = 0;
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        const u64 d = ld_hint(E.D + ((size_t)j * ext + t) * kp.n + ks, keep);
+                        a0 += (u128)d * k0[j];
+                        a1 += (u128)d * k1[j];
+                    }
+                u0 = redc(a0, q, qi);
+                u1 = redc(a1, q, qi);
+            }
+            if (isq) {                              // fold [P]_q phi(c0) (and [P]_q c1 at amount 0)
+                u0 = add_mod(u0, mul_mont(ld_hint(E.src + off - k + ks, keep), Pm, q, qi), q);
+                if (!A.key) u1 = mul_mont(ld_hint(E.src + E.ps + off, keep), Pm, q, qi);
+            }
+            E.U[off] = u0;
+            E.U[(size_t)ext * kp.n + off] = u1;
+        }
+    }
+}
+
+// acc_v = sum_terms pt_v (.) U over Q u P for HE_RV outputs per thread (one coefficient); absent
+// outputs are skipped (block-uniform); the next term's words are loaded while the current one
+// is accumulated.
+__global__ void __launch_bounds__(TB, 2) rmac_kernel(KP kp, const rgrp *grps, int n_grp) {
     constexpr int RV = HE_RV;
     const rgrp P = grps[blockIdx.x % n_grp];
     const int tile = blockIdx.x / n_grp;
@@ -1477,45 +1501,37 @@ __global__ void __launch_bounds__(TB) rmac_kernel(KP kp, const rgrp *grps, int n
     const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
     const u64 one = to_mont(1, q, qi, r2);
     const size_t off = (size_t)t * kp.n + k, ptoff = (size_t)ptl * kp.n + k;
-    const bool isq = t < nq;
-    const u64 stream = policy_evict_first(), keep = policy_evict_last();
-    u128 a0[RV], a1[RV], b0[RV], b1[RV];
+    const u64 stream = policy_evict_first();
+    u128 a0[RV], a1[RV];
 #pragma unroll
-    for (int v = 0; v < RV; v++) a0[v] = a1[v] = b0[v] = b1[v] = 0;
-    // words of term i: u0, u1 (raised), c0 (gathered), c1 (amount 0), pt[RV]
-    auto fetch = [&](int i, u64 &u0, u64 &u1, u64 &c0, u64 &c1, u64 (&p)[RV]) {
+    for (int v = 0; v < RV; v++) a0[v] = a1[v] = 0;
+    auto fetch = [&](int i, u64 &u0, u64 &u1, u64 (&p)[RV]) {
         const rterm T = P.terms[i];
-        u0 = u1 = c0 = c1 = 0;
-        if (T.U) {
-            u0 = ld_hint(T.U + off, stream);
-            u1 = ld_hint(T.U + (size_t)ext * kp.n + off, stream);
-        }
-        if (isq) {
-            const int ks = T.g == 1 ? k : autom_index(k, T.g, kp.logn);
-            c0 = ld_hint(T.src + (size_t)t * kp.n + ks, keep);
-            if (!T.U) c1 = ld_hint(T.src + T.ps + off, keep);
-        }
+        u0 = ld_hint(T.U + off, stream);
+        u1 = ld_hint(T.U + (size_t)ext * kp.n + off, stream);
 #pragma unroll
         for (int v = 0; v < RV; v++) {
             const u64 *pp = T.pt[v];
             p[v] = pp == HE_PT_ONE ? one : (pp ? ld_hint(pp + ptoff, stream) : 0);
         }
     };
-    u64 u0, u1, c0, c1, p[RV];
-    if (P.n_terms > 0) fetch(0, u0, u1, c0, c1, p);
+    u64 u0 = 0, u1 = 0, p[RV];
+#pragma unroll
+    for (int v = 0; v < RV; v++) p[v] = 0;
+    if (P.n_terms > 0) fetch(0, u0, u1, p);
     for (int i = 0; i < P.n_terms; i++) {
-        u64 nu0 = 0, nu1 = 0, nc0 = 0, nc1 = 0, np_[RV];
+        u64 nu0 = 0, nu1 = 0, np_[RV];
 #pragma unroll
         for (int v = 0; v < RV; v++) np_[v] = 0;
-        if (i + 1 < P.n_terms) fetch(i + 1, nu0, nu1, nc0, nc1, np_);
+        if (i + 1 < P.n_terms) fetch(i + 1, nu0, nu1, np_);
 #pragma unroll
-        for (int v = 0; v < RV; v++) {
-            a0[v] += (u128)p[v] * u0;
-            a1[v] += (u128)p[v] * u1;
-            b0[v] += (u128)p[v] * c0;
-            b1[v] += (u128)p[v] * c1;
-        }
-        u0 = nu0; u1 = nu1; c0 = nc0; c1 = nc1;
+        for (int v = 0; v < RV; v++)
+            if (P.terms[i].pt[v]) {                 // block-uniform
+                a0[v] += (u128)p[v] * u0;
+                a1[v] += (u128)p[v] * u1;
+            }
+        u0 = nu0;
+        u1 = nu1;
 #pragma unroll
         for (int v = 0; v < RV; v++) p[v] = np_[v];
     }
@@ -1529,14 +1545,11 @@ __global__ void __launch_bounds__(TB) rmac_kernel(KP kp, const rgrp *grps, int n
         *dst = r;
     };
 #pragma unroll
-    for (int v = 0; v < RV; v++) {
-        put(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, a0[v]);
-        put(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, a1[v]);
-        if (isq) {
-            put(P.base + ((size_t)(2 * v) * nq) * kp.n + off, b0[v]);
-            put(P.base + ((size_t)(2 * v + 1) * nq) * kp.n + off, b1[v]);
+    for (int v = 0; v < RV; v++)
+        if (v < P.nv) {
+            put(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, a0[v]);
+            put(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, a1[v]);
         }
-    }
 }
 
 int k_ip_amounts(const he_ctx *ctx, const ugrp *grps, int n_grp, int max_beta, double bytes, cudaStream_t s) {
@@ -1544,8 +1557,8 @@ int k_ip_amounts(const he_ctx *ctx, const ugrp *grps, int n_grp, int max_beta, d
     if (max_beta > 8) { he_set_error("inner products: at most 8 digits"); return HE_EINVAL; }
     TraceScope tr("ip_amounts", s, bytes, 0);
     dim3 g((unsigned)(ctx->n / TB) * n_grp, ctx->L + 1 + ctx->K);
-    if (max_beta <= 4) ip_amounts_kernel<4><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp);
-    else ip_amounts_kernel<8><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp);
+    if (max_beta <= 4) ip_amounts_kernel<4><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp, ctx->d_consts);
+    else ip_amounts_kernel<8><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp, ctx->d_consts);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1555,6 +1568,62 @@ int k_rmac(const he_ctx *ctx, const rgrp *grps, int n_grp, double bytes, double 
     TraceScope tr("rmac", s, bytes, mulmods);
     dim3 g((unsigned)(ctx->n / TB) * n_grp, ctx->L + 1 + ctx->K);
     rmac_kernel<<<g, TB, 0, s>>>(ctx->kp, grps, n_grp);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+// ---- factored channel-shard conv, stage 2: integer-scalar weighting of the masked rotations
+// out[o H + h][c][i][k] = sum_{f, t} Wm[i][o][f T + t] * Y[(f H + h) T + t][c][i][k]   (mod q_i)
+// Wm holds the scalars' residues in Montgomery form, so one REDC of the 128-bit sum gives the
+// result.  SM_OB outputs per thread (one coefficient); the block's weights sit in shared memory.
+constexpr int SM_OB = 16;
+
+__global__ void __launch_bounds__(TB) smac_kernel(KP kp, const u64 *Y, size_t ystride, size_t yps, const u64 *Wm,
+                                                  int co, int nin, int H, int T, u64 *out, size_t ostride,
+                                                  size_t ops) {
+    extern __shared__ u64 wsm[];                                   // [SM_OB][nin]
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int i = blockIdx.y >> 1, c = blockIdx.y & 1;             // limb, polynomial
+    const int h = blockIdx.z % H, o0 = (blockIdx.z / H) * SM_OB;
+    const u64 q = kp.q[i], qi = kp.qinv[i];
+    const int nob = min(SM_OB, co - o0);
+    for (int x = threadIdx.x; x < nob * nin; x += TB) {
+        const int ob = x / nin, kk = x % nin;
+        wsm[x] = Wm[((size_t)i * co + o0 + ob) * nin + kk];
+    }
+    __syncthreads();
+    u128 acc[SM_OB];
+#pragma unroll
+    for (int ob = 0; ob < SM_OB; ob++) acc[ob] = 0;
+    const u64 stream = policy_evict_first();
+    for (int kk = 0; kk < nin; kk++) {
+        const int f = kk / T, t = kk % T;
+        const u64 y = ld_hint(Y + ((size_t)(f * H + h) * T + t) * ystride + c * yps + (size_t)i * kp.n + k, stream);
+#pragma unroll
+        for (int ob = 0; ob < SM_OB; ob++)
+            if (ob < nob) acc[ob] += (u128)y * wsm[ob * nin + kk];
+    }
+#pragma unroll
+    for (int ob = 0; ob < SM_OB; ob++)
+        if (ob < nob) out[(size_t)((o0 + ob) * H + h) * ostride + c * ops + (size_t)i * kp.n + k] = redc(acc[ob], q, qi);
+}
+
+int k_smac(const he_ctx *ctx, const u64 *Y, size_t ystride, size_t yps, const u64 *Wm, int co, int ci, int H, int T,
+           int level, u64 *out, size_t ostride, size_t ops, cudaStream_t s) {
+    const int nin = ci * T;
+    const size_t smem = (size_t)SM_OB * nin * 8;
+    if (smem > 200 * 1024) { he_set_error("factored conv: %d inputs per output exceed shared memory", nin); return HE_EINVAL; }
+    if (smem > 48 * 1024) {
+        static const bool ok = cudaFuncSetAttribute(smac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    200 * 1024) == cudaSuccess;
+        if (!ok) { he_set_error("factored conv: shared-memory opt-in failed"); return HE_ECUDA; }
+    }
+    const double nl = level + 1;
+    TraceScope tr("smac", s, (double)(H * ci * T) * 2 * nl * ctx->n * 8 * ((co + SM_OB - 1) / SM_OB) +
+                                 (double)co * H * 2 * nl * ctx->n * 8,
+                  (double)co * H * ci * T * 2 * nl * ctx->n);
+    dim3 g(ctx->n / TB, 2 * (level + 1), H * ((co + SM_OB - 1) / SM_OB));
+    smac_kernel<<<g, TB, smem, s>>>(ctx->kp, Y, ystride, yps, Wm, co, nin, H, T, out, ostride, ops);
     LAUNCH_CHECK();
     return HE_OK;
 }

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <thread>
 #include <unordered_map>
@@ -469,7 +470,7 @@ struct FusedStage {
     std::vector<Group> groups;                        // for outputs-per-key-pass Vg
     std::vector<int> hslot;                           // source -> slot in D_all (-1: not rotated)
     u64 *D_all = nullptr;
-    u64 *facc = nullptr, *fbase = nullptr, *fconv = nullptr;   // [nout][2][ext|nq|nq][n]
+    u64 *facc = nullptr, *fconv = nullptr;            // [nout][2][ext|nq][n]
     md_item *d_md = nullptr;
     bool ready = false;
     int Vg = 0;
@@ -525,16 +526,15 @@ struct FusedStage {
         for (size_t i = 0; i < srcs.size(); i++)
             if (srcs[i].rotated) hslot[i] = nh++;
         HE_TRY(dev_alloc(&D_all, (size_t)nh * beta() * ext() * n));
-        // room for whole groups: a group whose last outputs are absent still stores their (zero)
-        // accumulators, so the output count is padded to a multiple of every group width (2, HE_RV)
-        const size_t nslot = (nout + HE_RV - 1) / HE_RV * HE_RV;
+        // a group stores only the outputs it has (fgrp.nv, rgrp.nv): no padding needed
+        const size_t nslot = nout;
         HE_TRY(dev_alloc(&facc, nslot * 2 * ext() * n));
-        HE_TRY(dev_alloc(&fbase, nslot * 2 * nq() * n));
         HE_TRY(dev_alloc(&fconv, nslot * 2 * nq() * n));
+        // the unrotated parts are folded into the raised sums, so the ModDown adds no base
         std::vector<md_item> md;
         for (size_t v = 0; v < nout; v++)
-            md.push_back(md_item{facc + v * 2 * ext() * n, fconv + v * 2 * nq() * n, fbase + v * 2 * nq() * n,
-                                 (size_t)nq() * n, 2, 1, outs[v].first, outs[v].second});
+            md.push_back(md_item{facc + v * 2 * ext() * n, fconv + v * 2 * nq() * n, nullptr, 0, 0, 1,
+                                 outs[v].first, outs[v].second});
         HE_TRY(dev_alloc(&d_md, std::max<size_t>(1, md.size())));
         if (!md.empty()) HE_CHECK_CUDA(cudaMemcpy(d_md, md.data(), md.size() * sizeof(md_item), cudaMemcpyHostToDevice));
         ready = true;
@@ -598,15 +598,15 @@ struct FusedStage {
             }
             bytes += (double)nh * beta_ * ext_ * n * 8 / std::max(1, (nout + V - 1) / V) +
                      (double)srcs.size() * 2 * nq_ * n * 8 / std::max(1, (nout + V - 1) / V) +
-                     (double)G.outs.size() * 2 * (ext_ + nq_) * n * 8;
+                     (double)G.outs.size() * 2 * ext_ * n * 8;
             G.bytes = bytes;
             G.mulmods = mm;
             HE_TRY(dev_alloc(&G.d_amt, std::max<size_t>(1, ha.size())));
             HE_TRY(dev_alloc(&G.d_ent, std::max<size_t>(1, he.size())));
             if (!ha.empty()) HE_CHECK_CUDA(cudaMemcpy(G.d_amt, ha.data(), ha.size() * sizeof(famt), cudaMemcpyHostToDevice));
             if (!he.empty()) HE_CHECK_CUDA(cudaMemcpy(G.d_ent, he.data(), he.size() * sizeof(fent), cudaMemcpyHostToDevice));
-            G.desc = fgrp{G.d_amt, G.d_ent, (int)ha.size(), level, beta_, pt_level,
-                          facc + (size_t)v0 * 2 * ext_ * n, fbase + (size_t)v0 * 2 * nq_ * n};
+            G.desc = fgrp{G.d_amt, G.d_ent, (int)ha.size(), level, beta_, pt_level, (int)G.outs.size(),
+                          facc + (size_t)v0 * 2 * ext_ * n};
             groups.push_back(G);
         }
         return HE_OK;
@@ -867,9 +867,8 @@ struct FusedLaunch {
 static std::vector<std::vector<std::pair<int, std::vector<int>>>> split_plan(
     const FusedStage &f, size_t slot_bytes, size_t cap_bytes) {
     // keyed amount -> sources, in amount order
-    std::map<int, std::set<int>> am;
-    for (auto &t : f.terms)
-        if (h_galois(f.c, t.a) != 1) am[t.a].insert(t.s);
+    std::map<int, std::set<int>> am;                  // amount 0 (no key) comes first
+    for (auto &t : f.terms) am[h_galois(f.c, t.a) == 1 ? 0 : t.a].insert(t.s);
     std::vector<std::vector<std::pair<int, std::vector<int>>>> out(1);
     size_t used = 0;
     for (auto &kv : am) {
@@ -911,9 +910,6 @@ int FusedStage::build_split(size_t cap_bytes) {
         max_slots = std::max(max_slots, k);
     }
     HE_TRY(dev_alloc(&U, std::max<size_t>(1, max_slots) * slot));
-    // term lookup: (v, s, a) -> plaintext
-    std::map<std::tuple<int, int, int>, const u64 *> pt_of;
-    for (auto &t : terms) pt_of[std::make_tuple(t.v, t.s, t.a)] = t.pt;
     const int nout = (int)outs.size();
     for (size_t ci = 0; ci < plan.size(); ci++) {
         Chunk ch;
@@ -923,44 +919,38 @@ int FusedStage::build_split(size_t cap_bytes) {
         for (auto &a : plan[ci]) {
             famt A;
             A.g = h_galois(c, a.first);
-            const DeviceKey *k;
-            HE_TRY(get_key(c, (int)A.g, &k));
-            A.key = k->d;
+            A.key = nullptr;
+            if (A.g != 1) {
+                const DeviceKey *k;
+                HE_TRY(get_key(c, (int)A.g, &k));
+                A.key = k->d;
+                ch.ubytes += (double)2 * beta_ * ext_ * n * 8;
+            }
             A.e0 = (int)he.size();
             for (int sidx : a.second) {
                 u64 *u = U + he.size() * slot;
-                he.push_back(uent{Dp[sidx], u});
+                he.push_back(uent{Dp[sidx], u, srcs[sidx].d, srcs[sidx].ps});
                 uslot[{a.first, sidx}] = u;
             }
             A.e1 = (int)he.size();
             ha.push_back(A);
-            ch.ubytes += (double)2 * beta_ * ext_ * n * 8 + (double)(A.e1 - A.e0) * slot * 8;
+            ch.ubytes += (double)(A.e1 - A.e0) * slot * 8;
         }
         HE_TRY(dev_alloc(&ch.d_amt, std::max<size_t>(1, ha.size())));
         HE_TRY(dev_alloc(&ch.d_ent, std::max<size_t>(1, he.size())));
         if (!ha.empty()) HE_CHECK_CUDA(cudaMemcpy(ch.d_amt, ha.data(), ha.size() * sizeof(famt), cudaMemcpyHostToDevice));
         if (!he.empty()) HE_CHECK_CUDA(cudaMemcpy(ch.d_ent, he.data(), he.size() * sizeof(uent), cudaMemcpyHostToDevice));
         ch.udesc = ugrp{ch.d_amt, ch.d_ent, (int)ha.size(), level, beta_};
-        // raised MAC terms per group of HE_RV outputs: this chunk's (a, s) pairs, plus the
-        // amount-0 terms in chunk 0
+        // raised MAC terms per group of HE_RV outputs: this chunk's (a, s) pairs
         for (int v0 = 0; v0 < nout; v0 += HE_RV) {
             std::map<std::pair<int, int>, rterm> tm;
             for (auto &t : terms) {
                 if (t.v < v0 || t.v >= v0 + HE_RV) continue;
-                const bool keyed = h_galois(c, t.a) != 1;
-                u64 *u = nullptr;
-                if (keyed) {
-                    auto it = uslot.find({t.a, t.s});
-                    if (it == uslot.end()) continue;          // another chunk
-                    u = it->second;
-                } else if (ci != 0) {
-                    continue;
-                }
-                rterm &r = tm[{t.a, t.s}];
-                r.U = u;
-                r.src = srcs[t.s].d;
-                r.ps = srcs[t.s].ps;
-                r.g = h_galois(c, t.a);
+                const int a = h_galois(c, t.a) == 1 ? 0 : t.a;
+                auto it = uslot.find({a, t.s});
+                if (it == uslot.end()) continue;              // another chunk
+                rterm &r = tm[{a, t.s}];
+                r.U = it->second;
                 r.pt[t.v - v0] = t.pt;
             }
             std::vector<rterm> ht;
@@ -969,15 +959,17 @@ int FusedStage::build_split(size_t cap_bytes) {
             HE_TRY(dev_alloc(&d, std::max<size_t>(1, ht.size())));
             if (!ht.empty()) HE_CHECK_CUDA(cudaMemcpy(d, ht.data(), ht.size() * sizeof(rterm), cudaMemcpyHostToDevice));
             ch.d_terms.push_back(d);
-            ch.rdesc.push_back(rgrp{d, (int)ht.size(), level, pt_level, ci > 0 ? 1 : 0,
-                                    facc + (size_t)v0 * 2 * ext_ * n, fbase + (size_t)v0 * 2 * nq_ * n});
+            ch.rdesc.push_back(rgrp{d, (int)ht.size(), level, pt_level, std::min(HE_RV, nout - v0), ci > 0 ? 1 : 0,
+                                    facc + (size_t)v0 * 2 * ext_ * n});
             for (auto &r : ht) {
-                ch.rbytes += (r.U ? slot * 8.0 : 0) + (double)2 * nq_ * n * 8;
+                ch.rbytes += slot * 8.0;
                 for (int v = 0; v < HE_RV; v++)
-                    if (r.pt[v] && r.pt[v] != HE_PT_ONE) ch.rbytes += (double)(r.U ? ext_ : nq_) * n * 8;
-                ch.rmm += (double)4 * HE_RV * ext_ * n;
+                    if (r.pt[v]) {
+                        if (r.pt[v] != HE_PT_ONE) ch.rbytes += (double)ext_ * n * 8;
+                        ch.rmm += (double)2 * ext_ * n;
+                    }
             }
-            ch.rbytes += (double)std::min(HE_RV, nout - v0) * 2 * (ext_ + nq_) * n * 8;
+            ch.rbytes += (double)std::min(HE_RV, nout - v0) * 2 * ext_ * n * 8;
         }
         chunks.push_back(std::move(ch));
     }
@@ -989,7 +981,7 @@ FusedStage::~FusedStage() {
     own.reset();
     free_split();
     free_groups();
-    cudaFree(D_all); cudaFree(facc); cudaFree(fbase); cudaFree(fconv); cudaFree(d_md);
+    cudaFree(D_all); cudaFree(facc); cudaFree(fconv); cudaFree(d_md);
 }
 
 int FusedStage::run(cudaStream_t s) {
@@ -1419,6 +1411,7 @@ extern "C" int he_pool_run(he_ctx *c, he_pool *p, he_ct *const *in, he_ct **out,
 
 // ================================================================================ convolution
 struct ConvBatch;
+struct FactoredConv;
 struct he_conv {
     he_ctx *c = nullptr;
     Lay lin, lout;
@@ -1440,6 +1433,7 @@ struct he_conv {
     std::vector<he_ct *> mid;
     FusedStage fused;                            // HE_FUSED: built on first use
     std::unique_ptr<ConvBatch> batch;            // he_conv_run_batch: buffers of the last signature
+    std::unique_ptr<FactoredConv> fc;            // set: the factored channel-shard form
     std::map<std::pair<int, uint64_t>, u64 *> bias_by;   // (level, output scale) -> bias addends
     u64 *rot_ptr(int u, int a) {
         return a == 0 ? R + (size_t)u * 2 * pw : Rrot + (size_t)slot[(long long)u * c->N + a] * 2 * pw;
@@ -1457,6 +1451,269 @@ static int conv_bias_int(he_conv *cv, int v, double scale, std::vector<int64_t> 
     encode_slots(z.data(), cv->c->n, scale, m.data());
     return HE_OK;
 }
+
+// ================================================================================ factored conv
+// Channel-shard convolution in two stages (Eq. 7 with the weights taken out of the masks):
+// stage 1  Y_{f,h,t} = sum_{h'} B_{h,h',t} (.) rot_{a_t}(X_{f,h'})   binary masks at scale q_l,
+//          rescale;
+// stage 2  out_{o,h} = sum_{f,t} round(W[o][f][t] q_{l-1}) Y_{f,h,t}   integer scalars, rescale,
+//          bias.
+// Every shard holds R = N/M rows of one channel (H = M/R shards per channel); own and
+// neighbour reads of a tap share the amount a_t = ((k - pad) M + (l - pad)) mod N, and the masks
+// depend on (h, h', t) only, so there are at most 2 H T of them instead of co ci H T diagonals.
+struct FactoredConv {
+    int H = 0, T = 0, nY = 0, n_masks = 0;
+    std::vector<int> amt;                        // per tap
+    std::vector<std::array<int, 3>> mkey;        // (h, h_src, t), sorted
+    u64 *masks = nullptr;                        // [n_masks][l+1+K][n] Montgomery NTT, scale q_l
+    u64 *Wm = nullptr;                           // [l][co][ci T] Montgomery residues (limbs 0..l-1)
+    u64 *Y = nullptr;                            // [nY][2][pw] stage-1 outputs
+    u64 *rt = nullptr;                           // rescale scratch [2 max(nY, n_out)][l][n]
+    std::vector<int> yoff, ts, ta, tm;           // stage-1 terms per Y: source, amount, mask
+    FusedStage fy;                               // HE_FUSED stage 1
+    RotSet ry;                                   // per-rotation stage 1
+    u64 *Rrot = nullptr;
+    std::map<int, int> rslot;                    // (u * N + a) -> rotation slot
+    mac_term *d_terms = nullptr;
+    bool rot_ready = false;
+    ~FactoredConv() { cudaFree(masks); cudaFree(Wm); cudaFree(Y); cudaFree(rt); cudaFree(Rrot); cudaFree(d_terms); }
+};
+
+// the masks B_{h,h',t} (sorted by key) and the tap amounts
+static int factored_masks(const he_conv *cv, std::vector<std::array<int, 3>> &keys,
+                          std::vector<std::vector<double>> &mvals, std::vector<int> &amt) {
+    const Lay &L = cv->lin;
+    const int M = L.M, N = L.N, R = L.rows(), H = M / R;
+    std::map<std::array<int, 3>, std::vector<double>> mk;
+    amt.clear();
+    for (int k = 0; k < cv->kh; k++)
+        for (int l = 0; l < cv->kw; l++) {
+            const int t = k * cv->kw + l;
+            const int a = (int)((((long long)(k - cv->pad) * M + (l - cv->pad)) % N + N) % N);
+            amt.push_back(a);
+            for (int h = 0; h < H; h++)
+                for (int i = 0; i < N; i++) {
+                    SlotInfo si = slot_info(cv->lout, h, i);      // shard h of output channel 0
+                    const int ys = si.y + k - cv->pad, xs = si.x + l - cv->pad;
+                    if (!si.valid || ys < 0 || ys >= L.m || xs < 0 || xs >= L.m) continue;
+                    const int hs = ys / R;
+                    const int j = (ys - hs * R) * M + xs;
+                    if (((j - i) % N + N) % N != a) { he_set_error("factored conv: amounts disagree"); return HE_ESTATE; }
+                    auto &v = mk[{h, hs, t}];
+                    if (v.empty()) v.assign(N, 0.0);
+                    v[i] = 1.0;
+                }
+        }
+    keys.clear();
+    mvals.clear();
+    for (auto &kv : mk) {
+        keys.push_back(kv.first);
+        mvals.push_back(std::move(kv.second));
+    }
+    return HE_OK;
+}
+
+static int factored_plan(he_conv *cv, std::vector<std::vector<double>> &mvals) {
+    he_ctx *c = cv->c;
+    FactoredConv &F = *cv->fc;
+    const Lay &L = cv->lin;
+    F.H = L.M / L.rows();
+    F.T = cv->kh * cv->kw;
+    F.nY = cv->ci * F.H * F.T;
+    HE_TRY(factored_masks(cv, F.mkey, mvals, F.amt));
+    F.n_masks = (int)F.mkey.size();
+    // stage-1 terms per Y = (f, h, t)
+    for (int f = 0; f < cv->ci; f++)
+        for (int h = 0; h < F.H; h++)
+            for (int t = 0; t < F.T; t++) {
+                F.yoff.push_back((int)F.ts.size());
+                for (int m = 0; m < F.n_masks; m++)
+                    if (F.mkey[m][0] == h && F.mkey[m][2] == t) {
+                        F.ts.push_back(f * F.H + F.mkey[m][1]);
+                        F.ta.push_back(F.amt[t]);
+                        F.tm.push_back(m);
+                    }
+            }
+    F.yoff.push_back((int)F.ts.size());
+    // stage-2 scalars round(w q_{l-1}), residues mod q_0..q_{l-1} in Montgomery form
+    const int l1 = cv->level - 1, nin = cv->ci * F.T;
+    std::vector<u64> wm((size_t)(l1 + 1) * cv->co * nin);
+    const double ql1 = (double)c->primes[l1];
+    for (int o = 0; o < cv->co; o++)
+        for (int f = 0; f < cv->ci; f++)
+            for (int t = 0; t < F.T; t++) {
+                const double w = cv->W[(((size_t)o * cv->ci + f) * cv->kh + t / cv->kw) * cv->kw + t % cv->kw];
+                const double r = std::round(w * ql1);               // half away from zero
+                if (!(std::fabs(r) < 9.0e18)) { he_set_error("factored conv: weight too large"); return HE_EINVAL; }
+                const long long wi = (long long)r;
+                for (int i = 0; i <= l1; i++) {
+                    const u64 q = c->primes[i];
+                    const u64 res = wi >= 0 ? (u64)wi % q : (q - (u64)(-wi) % q) % q;
+                    wm[((size_t)i * cv->co + o) * nin + f * F.T + t] = (u64)(((u128)res << 64) % q);
+                }
+            }
+    HE_TRY(dev_alloc(&F.Wm, wm.size()));
+    HE_CHECK_CUDA(cudaMemcpy(F.Wm, wm.data(), wm.size() * 8, cudaMemcpyHostToDevice));
+    return HE_OK;
+}
+
+static int factored_runtime(he_conv *cv) {
+    he_ctx *c = cv->c;
+    FactoredConv &F = *cv->fc;
+    const size_t pw = cv->pw;
+    HE_TRY(dev_alloc(&cv->R, (size_t)cv->lin.ns * 2 * pw));
+    HE_TRY(dev_alloc(&F.Y, (size_t)F.nY * 2 * pw));
+    HE_TRY(dev_alloc(&cv->acc, (size_t)cv->lout.ns * 2 * pw));
+    HE_TRY(dev_alloc(&F.rt, (size_t)2 * std::max(F.nY, cv->lout.ns) * cv->level * c->n));
+    if (cv->stride == 2) {
+        HE_TRY(pool_build(c, cv->lout, cv->level - 2, true, &cv->pool));
+        for (int v = 0; v < cv->lout.ns; v++) {
+            he_ct *m;
+            HE_TRY(he_ct_alloc(c, cv->level - 2, &m));
+            cv->mid.push_back(m);
+        }
+    }
+    return HE_OK;
+}
+
+static int factored_prepare(he_conv *cv, int mode) {
+    he_ctx *c = cv->c;
+    FactoredConv &F = *cv->fc;
+    const size_t pw = cv->pw;
+    const size_t pe = (size_t)(cv->level + 1 + c->K) * c->n;
+    if (mode == HE_FUSED) {
+        if (F.fy.c) return HE_OK;
+        F.fy.c = c;
+        F.fy.level = cv->level;
+        char nm[96];
+        snprintf(nm, sizeof(nm), "factored conv %d->%d %dx%d k%dx%d masks", cv->ci, cv->co, cv->lin.m, cv->lin.m,
+                 cv->kh, cv->kw);
+        F.fy.name = nm;
+        for (int u = 0; u < cv->lin.ns; u++) F.fy.add_src(cv->R + (size_t)u * 2 * pw, pw);
+        for (int y = 0; y < F.nY; y++) F.fy.add_out(F.Y + (size_t)y * 2 * pw, pw);
+        for (int y = 0; y < F.nY; y++)
+            for (int x = F.yoff[y]; x < F.yoff[y + 1]; x++) F.fy.add_term(y, F.ts[x], F.ta[x], F.masks + (size_t)F.tm[x] * pe);
+        return F.fy.build();
+    }
+    if (F.rot_ready) return HE_OK;
+    for (size_t x = 0; x < F.ts.size(); x++)
+        if (F.ta[x] != 0) F.rslot.emplace(F.ts[x] * c->N + F.ta[x], (int)F.rslot.size());
+    HE_TRY(dev_alloc(&F.Rrot, F.rslot.size() * 2 * pw));
+    std::vector<mac_term> terms(F.ts.size());
+    for (size_t x = 0; x < F.ts.size(); x++) {
+        const u64 *src = F.ta[x] == 0 ? cv->R + (size_t)F.ts[x] * 2 * pw
+                                      : F.Rrot + (size_t)F.rslot[F.ts[x] * c->N + F.ta[x]] * 2 * pw;
+        terms[x] = mac_term{F.masks + (size_t)F.tm[x] * pe, src, pw};
+    }
+    HE_TRY(dev_alloc(&F.d_terms, std::max<size_t>(1, terms.size())));
+    if (!terms.empty()) HE_CHECK_CUDA(cudaMemcpy(F.d_terms, terms.data(), terms.size() * sizeof(mac_term), cudaMemcpyHostToDevice));
+    F.ry.c = c;
+    F.ry.level = cv->level;
+    for (int u = 0; u < cv->lin.ns; u++) F.ry.src.push_back({cv->R + (size_t)u * 2 * pw, pw});
+    for (auto &kv : F.rslot) F.ry.add(kv.first / c->N, kv.first % c->N, F.Rrot + (size_t)kv.second * 2 * pw, pw);
+    F.rot_ready = true;
+    return HE_OK;
+}
+
+static int factored_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out, int mode, cudaStream_t s) {
+    FactoredConv &F = *cv->fc;
+    const size_t pw = cv->pw;
+    const int lv = cv->level;
+    for (int u = 0; u < cv->lin.ns; u++) {
+        if (!in[u] || in[u]->ctx != c || in[u]->level != lv || in[u]->scale != cv->in_scale) {
+            he_set_error("he_conv_run: input shard %d is not at level %d / the planned scale", u, lv);
+            return HE_ELEVEL;
+        }
+        HE_TRY(k_copy_limbs(cv->R + (size_t)u * 2 * pw, pw, in[u]->d, in[u]->pstride, pw, 2, s));
+    }
+    HE_TRY(factored_prepare(cv, mode));
+    // stage 1: masked rotations, then one batched rescale of every Y
+    if (mode == HE_FUSED) {
+        HE_TRY(F.fy.run(s));
+    } else {
+        if (mode == HE_BATCHED) HE_TRY(F.ry.prepare_batched());
+        HE_TRY(F.ry.run(mode, s));
+        for (int y = 0; y < F.nY; y++)
+            HE_TRY(k_mac(c, F.d_terms + F.yoff[y], F.yoff[y + 1] - F.yoff[y], F.Y + (size_t)y * 2 * pw, pw, lv, false, s));
+    }
+    HE_TRY(k_rescale_many(c, F.Y, pw, F.nY, lv, F.rt, s));
+    const double y_scale = cv->in_scale * (double)c->primes[lv] / (double)c->primes[lv];
+    // stage 2: integer scalars, rescale, bias
+    const int l1 = lv - 1;
+    HE_TRY(k_smac(c, F.Y, 2 * pw, pw, F.Wm, cv->co, cv->ci, F.H, F.T, l1, cv->acc, 2 * pw, pw, s));
+    HE_TRY(k_rescale_many(c, cv->acc, pw, cv->lout.ns, l1, F.rt, s));
+    const double o_scale = y_scale * (double)c->primes[l1] / (double)c->primes[l1];
+    he_ct **dst = cv->stride == 1 ? out : cv->mid.data();
+    for (int v = 0; v < cv->lout.ns; v++) {
+        u64 *a = cv->acc + (size_t)v * 2 * pw;
+        HE_TRY(k_add_raw(c, a, pw, cv->bias_pts + (size_t)v * (lv - 1) * c->n, 0, lv - 1, 1, false, s));
+        if (!dst[v] || dst[v]->ctx != c) { he_set_error("he_conv_run: output %d missing", v); return HE_EINVAL; }
+        HE_TRY(ensure_ct(c, dst[v], lv - 2));
+        HE_TRY(k_copy_limbs(dst[v]->d, dst[v]->pstride, a, pw, (size_t)(lv - 1) * c->n, 2, s));
+        dst[v]->scale = o_scale;
+    }
+    if (cv->stride == 2) {
+        HE_TRY(pool_prepare(cv->pool, mode));
+        return pool_run(c, cv->pool, cv->mid.data(), out, mode, s);
+    }
+    return HE_OK;
+}
+
+extern "C" int he_conv_create_factored(he_ctx *c, const he_layout *in, const double *W, const double *bias, int co,
+                                       int ci, int kh, int kw, int stride, int pad, int level, double in_scale,
+                                       he_conv **out) {
+    if (!c || !in || !W || !out || co < 1 || ci < 1 || kh < 1 || kw < 1 || pad < 0 ||
+        (stride != 1 && stride != 2)) {
+        he_set_error("he_conv_create_factored: bad argument");
+        return HE_EINVAL;
+    }
+    const int need = stride == 1 ? 2 : 4;
+    if (level < need || level > c->L) { he_set_error("he_conv_create_factored: level %d leaves too few levels", level); return HE_ELEVEL; }
+    Lay lin = from_c(*in);
+    HE_TRY(check_layout(lin, c->N));
+    if (lin.c != ci) { he_set_error("he_conv_create_factored: layout has %d channels, W has %d", lin.c, ci); return HE_EINVAL; }
+    if (lin.nb != 1 || lin.B != lin.N || lin.ns != ci * (lin.M / lin.rows())) {
+        he_set_error("he_conv_create_factored: the input must be in channel shards (each shard rows of one channel)");
+        return HE_EINVAL;
+    }
+    for (int u = 0; u < lin.ns; u++)
+        if (lin.chan[u] != u / (lin.M / lin.rows()) || lin.row0[u] != (u % (lin.M / lin.rows())) * lin.rows()) {
+            he_set_error("he_conv_create_factored: shards must hold channels in order, rows in order");
+            return HE_EINVAL;
+        }
+    std::unique_ptr<he_conv> cv(new he_conv());
+    cv->c = c;
+    cv->lin = lin;
+    cv->lout = image_layout(co, lin.m, lin.N);
+    cv->W.assign(W, W + (size_t)co * ci * kh * kw);
+    if (bias) cv->bias.assign(bias, bias + co);
+    cv->co = co; cv->ci = ci; cv->kh = kh; cv->kw = kw; cv->pad = pad; cv->stride = stride;
+    cv->level = level;
+    cv->in_scale = in_scale;
+    cv->pw = (size_t)(level + 1) * c->n;
+    cv->pe = (size_t)(level + 1 + c->K) * c->n;
+    cv->fc.reset(new FactoredConv());
+    FactoredConv &F = *cv->fc;
+    std::vector<std::vector<double>> mvals;
+    HE_TRY(factored_plan(cv.get(), mvals));
+    HE_TRY(dev_alloc(&F.masks, (size_t)F.n_masks * cv->pe));
+    std::vector<const double *> vecs;
+    for (auto &v : mvals) vecs.push_back(v.data());
+    HE_TRY(upload_plaintexts(c, vecs, vecs.size(), (double)c->primes[level], level, F.masks, nullptr, true));
+    // bias at the output scale, normal NTT form at level - 2
+    const double y_scale = in_scale * (double)c->primes[level] / (double)c->primes[level];
+    const double o_scale = y_scale * (double)c->primes[level - 1] / (double)c->primes[level - 1];
+    HE_TRY(dev_alloc(&cv->bias_pts, (size_t)cv->lout.ns * (level - 1) * c->n));
+    for (int v = 0; v < cv->lout.ns; v++) {
+        std::vector<int64_t> m;
+        conv_bias_int(cv.get(), v, o_scale, m);
+        HE_TRY(upload_addend(c, m.data(), level - 2, cv->bias_pts + (size_t)v * (level - 1) * c->n));
+    }
+    HE_TRY(factored_runtime(cv.get()));
+    *out = cv.release();
+    return HE_OK;
+}
+
 
 // buffers every mode uses: input copies, accumulators, the stride-2 select stage
 static int conv_runtime(he_conv *cv, const he_pool *pool_src = nullptr) {
@@ -1499,6 +1756,7 @@ static int conv_rot_runtime(he_conv *cv) {
 
 static int conv_fork(const he_conv *src, he_ctx *c, he_conv **out) {
     if (c->root() != src->c->root()) { he_set_error("fork: contexts do not share a root"); return HE_ESTATE; }
+    if (src->fc) { he_set_error("fork: not available for the factored form"); return HE_EINVAL; }
     std::unique_ptr<he_conv> cv(new he_conv());
     cv->c = c;
     cv->lin = src->lin; cv->lout = src->lout; cv->W = src->W; cv->bias = src->bias;
@@ -1607,19 +1865,37 @@ extern "C" int he_conv_out_layout(const he_conv *cv, he_layout *out) {
 }
 extern "C" int he_conv_out_level(const he_conv *cv) {
     if (!cv) return HE_EINVAL;
+    if (cv->fc) return cv->stride == 1 ? cv->level - 2 : cv->level - 4;
     return cv->stride == 1 ? cv->level - 1 : cv->level - 3;
 }
 extern "C" int he_conv_rotations(const he_conv *cv, int32_t *amounts, size_t cap) {
     if (!cv) return HE_EINVAL;
     std::vector<int> v;
     for (auto &kv : cv->slot) v.push_back((int)(kv.first % cv->c->N));
+    if (cv->fc) v.insert(v.end(), cv->fc->amt.begin(), cv->fc->amt.end());
     if (cv->pool) collect_rotations(cv->pool, v);
     return distinct_nonzero(cv->c, v, amounts, cap);
 }
-extern "C" int he_conv_n_terms(const he_conv *cv) { return cv ? (int)cv->tu.size() : HE_EINVAL; }
+extern "C" int he_conv_n_terms(const he_conv *cv) {
+    if (!cv) return HE_EINVAL;
+    return cv->fc ? cv->fc->n_masks : (int)cv->tu.size();
+}
 
 extern "C" int he_conv_export_plan(const he_conv *cv, int32_t *u, int32_t *v, int32_t *a, double *diag) {
     if (!cv) return HE_EINVAL;
+    if (cv->fc) {                               // masks: u = source shard h', v = shard h, a = a_t
+        std::vector<std::array<int, 3>> keys;
+        std::vector<std::vector<double>> mv;
+        std::vector<int> amt;
+        HE_TRY(factored_masks(cv, keys, mv, amt));
+        for (size_t m = 0; m < keys.size(); m++) {
+            if (u) u[m] = keys[m][1];
+            if (v) v[m] = keys[m][0];
+            if (a) a[m] = amt[keys[m][2]];
+            if (diag) memcpy(diag + m * (size_t)cv->c->N, mv[m].data(), (size_t)cv->c->N * 8);
+        }
+        return HE_OK;
+    }
     for (size_t t = 0; t < cv->tu.size(); t++) {
         if (u) u[t] = cv->tu[t];
         if (v) v[t] = cv->tv[t];
@@ -1640,6 +1916,15 @@ extern "C" int he_conv_export_plan(const he_conv *cv, int32_t *u, int32_t *v, in
 extern "C" int he_conv_import_plaintexts(he_conv *cv, const int64_t *terms, const int64_t *bias) {
     if (!cv) return HE_EINVAL;
     he_ctx *c = cv->c;
+    if (cv->fc) {                               // masks [n_masks][n] at scale q_l, bias at l - 2
+        std::vector<const double *> none;
+        if (terms) HE_TRY(upload_plaintexts(c, none, cv->fc->n_masks, 0.0, cv->level, cv->fc->masks, terms, true));
+        if (bias)
+            for (int v = 0; v < cv->lout.ns; v++)
+                HE_TRY(upload_addend(c, bias + (size_t)v * c->n, cv->level - 2,
+                                     cv->bias_pts + (size_t)v * (cv->level - 1) * c->n));
+        return HE_OK;
+    }
     if (terms) {
         std::vector<const double *> none;
         HE_TRY(upload_plaintexts(c, none, cv->tu.size(), 0.0, cv->level, cv->pts, terms, true));
@@ -1664,11 +1949,14 @@ static int conv_prepare_fused(he_conv *cv) {
     return F.build();
 }
 
+static int factored_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out, int mode, cudaStream_t s);
+
 extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out, int mode, void *stream) {
     if (!c || !cv || !in || !out || cv->c != c || (mode != HE_PLAIN && mode != HE_BATCHED && mode != HE_FUSED)) {
         he_set_error("he_conv_run: bad argument");
         return HE_EINVAL;
     }
+    if (cv->fc) return factored_run(c, cv, in, out, mode, (cudaStream_t)stream);
     cudaStream_t s = (cudaStream_t)stream;
     const size_t pw = cv->pw;
     const int lv = cv->level;
@@ -1733,6 +2021,7 @@ struct ConvBatch {
 
 he_conv::~he_conv() {
     batch.reset();
+    fc.reset();
     for (auto &kv : bias_by) cudaFree(kv.second);
     cudaFree(R); cudaFree(Rrot); cudaFree(d_terms); cudaFree(acc);
     if (!shared_pts) { cudaFree(pts); cudaFree(bias_pts); }
@@ -1847,7 +2136,7 @@ extern "C" int he_conv_run_batch(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct
         he_set_error("he_conv_run_batch: bad argument");
         return HE_EINVAL;
     }
-    if (cv->stride != 1) { he_set_error("he_conv_run_batch: stride-1 convolutions only"); return HE_EINVAL; }
+    if (cv->stride != 1 || cv->fc) { he_set_error("he_conv_run_batch: stride-1 diagonal convolutions only"); return HE_EINVAL; }
     cudaStream_t s = (cudaStream_t)stream;
     const int ni = cv->lin.ns, no = cv->lout.ns;
     std::vector<int> levels(n_img);
@@ -1993,106 +2282,167 @@ static int retarget(he_ctx *c, const he_ct *x, int level, double scale_t, he_ct 
     return HE_OK;
 }
 
+// Temporaries of the polynomial evaluator: `need` ciphertexts at level L in one allocation,
+// kept in the context and reused by every call.
+static int poly_temps(he_ctx *c, size_t need) {
+    if (c->poly_tmp.size() >= need) return HE_OK;
+    HE_TRY(he_capture_guard("polynomial temporaries"));
+    for (he_ct *t : c->poly_tmp) he_ct_free(t);
+    c->poly_tmp.clear();
+    if (c->poly_block) cudaFree(c->poly_block);
+    c->poly_block = nullptr;
+    const size_t ps = (size_t)(c->L + 1) * c->n;
+    HE_TRY(dev_alloc(&c->poly_block, need * 2 * ps));
+    for (size_t i = 0; i < need; i++) {
+        he_ct *t = nullptr;
+        HE_TRY(he_ct_wrap(c, c->poly_block + i * 2 * ps, 2 * ps * 8, c->L, &t));
+        c->poly_tmp.push_back(t);
+    }
+    return HE_OK;
+}
+
+// The Chebyshev tree on m ciphertexts at one level, side by side: every tree depth is one
+// batched relinearisation over all of them (relin_batch), and each ciphertext gets exactly the
+// bits the one-ciphertext evaluation gives it.  Temporaries poly_tmp[t0 .. t0 + m (2 deg + 4)).
+static int poly_eval_group(he_ctx *c, const std::vector<he_ct *> &io, const double *cheb, int deg,
+                           const std::vector<double> &tgt, size_t t0, cudaStream_t s) {
+    const int m = (int)io.size();
+    const size_t per = 2 * (size_t)deg + 4;
+    int depth = 0;
+    while ((1 << depth) < deg) depth++;
+    std::vector<std::vector<he_ct *>> T(m), opA(m);
+    std::vector<he_ct *> t1(m), acc(m), y(m);
+    for (int j = 0; j < m; j++) {
+        he_ct **tp = c->poly_tmp.data() + t0 + (size_t)j * per;
+        T[j].assign(deg + 1, nullptr);
+        opA[j].assign(deg + 1, nullptr);
+        for (int k = 1; k <= deg; k++) T[j][k] = tp[k - 1];
+        for (int k = 2; k <= deg; k++) opA[j][k] = tp[deg + k - 2];
+        t1[j] = tp[2 * deg];
+        acc[j] = tp[2 * deg + 1];
+        y[j] = tp[2 * deg + 2];
+        HE_TRY(he_ct_copy(T[j][1], io[j], s));
+    }
+    for (int d = 1; d <= depth; d++) {
+        const int k0 = (1 << (d - 1)) + 1, k1 = std::min(deg, 1 << d);
+        std::vector<const he_ct *> A, B;
+        std::vector<he_ct *> O;
+        for (int j = 0; j < m; j++)
+            for (int k = k0; k <= k1; k++) {
+                const int h = k / 2;
+                if (k % 2 == 0) {
+                    A.push_back(T[j][h]);
+                    B.push_back(T[j][h]);
+                } else {
+                    // depth never decreases with k, so T_{h+1} already sits at the common level
+                    // and only a copy of T_h is dropped to it
+                    const int lv = T[j][h + 1]->level;
+                    if (T[j][h]->level < lv) { he_set_error("he_poly_eval: operand levels out of order"); return HE_ESTATE; }
+                    HE_TRY(he_ct_copy(opA[j][k], T[j][h], s));
+                    HE_TRY(he_ct_drop_level(opA[j][k], lv));
+                    A.push_back(opA[j][k]);
+                    B.push_back(T[j][h + 1]);
+                }
+                O.push_back(T[j][k]);
+            }
+        HE_TRY(relin_batch(c, A, B, O, s));
+        for (int j = 0; j < m; j++)
+            for (int k = k0; k <= k1; k++) {
+                HE_TRY(he_mul_int(c, T[j][k], 2.0, s));
+                if (k % 2 == 0) {
+                    HE_TRY(he_add_const_int(c, T[j][k], -std::nearbyint(T[j][k]->scale), s));
+                } else {
+                    HE_TRY(retarget(c, T[j][1], T[j][k]->level, T[j][k]->scale, t1[j], s));
+                    HE_TRY(he_sub(c, T[j][k], t1[j], s));
+                }
+            }
+    }
+    for (int j = 0; j < m; j++) {
+        const double target_scale = tgt[j];
+        int lmin = T[j][1]->level;
+        for (int k = 2; k <= deg; k++) lmin = std::min(lmin, T[j][k]->level);
+        const double base = target_scale * (double)c->primes[lmin];
+        const double cst = std::nearbyint(cheb[0] * target_scale * (double)c->primes[lmin]);
+        if (deg <= 20 && lmin + 1 <= 24) {
+            // one pass: acc = sum_k K_k T_k + c_0 (same integers and sums as the term-by-term form)
+            std::vector<const u64 *> xs(deg);
+            std::vector<size_t> pss(deg);
+            std::vector<u64> res((size_t)deg * 24, 0), cres(24, 0);
+            for (int k = 1; k <= deg; k++) {
+                const double K = std::nearbyint(cheb[k] * target_scale * (double)c->primes[lmin] / T[j][k]->scale);
+                xs[k - 1] = T[j][k]->d;
+                pss[k - 1] = T[j][k]->pstride;
+                for (int i = 0; i <= lmin; i++)
+                    if (!int_residue(K, c->primes[i], &res[(size_t)(k - 1) * 24 + i])) {
+                        he_set_error("he_poly_eval: constant is not an exact integer");
+                        return HE_EINVAL;
+                    }
+            }
+            for (int i = 0; i <= lmin; i++)
+                if (!int_residue(cst, c->primes[i], &cres[i])) { he_set_error("he_poly_eval: bad constant"); return HE_EINVAL; }
+            HE_TRY(ensure_ct(c, acc[j], lmin));
+            HE_TRY(k_lincomb(c, xs.data(), pss.data(), res.data(), deg, cres.data(), lmin, acc[j]->d, acc[j]->pstride, s));
+            acc[j]->scale = base;
+            HE_TRY(he_rescale(c, acc[j], s));
+            acc[j]->scale = target_scale;
+            HE_TRY(he_ct_copy(io[j], acc[j], s));
+            continue;
+        }
+        bool first = true;
+        for (int k = 1; k <= deg; k++) {
+            HE_TRY(he_ct_copy(y[j], T[j][k], s));
+            HE_TRY(he_ct_drop_level(y[j], lmin));
+            double K = std::nearbyint(cheb[k] * target_scale * (double)c->primes[lmin] / y[j]->scale);
+            HE_TRY(he_mul_int(c, y[j], K, s));
+            y[j]->scale = base;
+            if (first) { HE_TRY(he_ct_copy(acc[j], y[j], s)); first = false; }
+            else HE_TRY(he_add(c, acc[j], y[j], s));
+        }
+        HE_TRY(he_add_const_int(c, acc[j], cst, s));
+        HE_TRY(he_rescale(c, acc[j], s));
+        acc[j]->scale = target_scale;
+        HE_TRY(he_ct_copy(io[j], acc[j], s));
+    }
+    return HE_OK;
+}
+
 extern "C" int he_poly_eval(he_ctx *c, he_ct *io, const double *cheb, int deg, double target_scale, void *stream) {
     if (!c || !io || !cheb || deg < 1 || deg > 64) { he_set_error("he_poly_eval: bad argument"); return HE_EINVAL; }
     int depth = 0;
     while ((1 << depth) < deg) depth++;
     if (io->level < depth + 1) { he_set_error("he_poly_eval: needs %d levels", depth + 1); return HE_ELEVEL; }
-    cudaStream_t s = (cudaStream_t)stream;
-    // temporaries live in the context (allocated once at the top level, reused every call)
-    const size_t need = 2 * (size_t)deg + 4;
-    if (c->poly_tmp.size() < need) {
-        for (he_ct *t : c->poly_tmp) he_ct_free(t);
-        c->poly_tmp.clear();
-        if (c->poly_block) cudaFree(c->poly_block);
-        c->poly_block = nullptr;
-        const size_t ps = (size_t)(c->L + 1) * c->n;
-        HE_TRY(dev_alloc(&c->poly_block, need * 2 * ps));
-        for (size_t i = 0; i < need; i++) {
-            he_ct *t = nullptr;
-            HE_TRY(he_ct_wrap(c, c->poly_block + i * 2 * ps, 2 * ps * 8, c->L, &t));
-            c->poly_tmp.push_back(t);
-        }
+    HE_TRY(poly_temps(c, 2 * (size_t)deg + 4));
+    return poly_eval_group(c, {io}, cheb, deg, {target_scale}, 0, (cudaStream_t)stream);
+}
+
+extern "C" int he_poly_eval_many(he_ctx *c, he_ct *const *io, int m, const double *cheb, int deg,
+                                 const double *target_scales, void *stream) {
+    if (!c || !io || m < 1 || !cheb || !target_scales || deg < 1 || deg > 64) {
+        he_set_error("he_poly_eval_many: bad argument");
+        return HE_EINVAL;
     }
-    std::vector<he_ct *> T(deg + 1, nullptr), opA(deg + 1, nullptr), opB(deg + 1, nullptr);
-    for (int k = 1; k <= deg; k++) T[k] = c->poly_tmp[k - 1];
-    for (int k = 2; k <= deg; k++) opA[k] = c->poly_tmp[deg + k - 2];
-    he_ct *t1 = c->poly_tmp[2 * deg], *acc = c->poly_tmp[2 * deg + 1], *y = c->poly_tmp[2 * deg + 2];
-    HE_TRY(he_ct_copy(T[1], io, stream));
-    for (int d = 1; d <= depth; d++) {
-        const int k0 = (1 << (d - 1)) + 1, k1 = std::min(deg, 1 << d);
-        std::vector<const he_ct *> A, B;
-        std::vector<he_ct *> O;
-        for (int k = k0; k <= k1; k++) {
-            const int h = k / 2;
-            if (k % 2 == 0) {
-                A.push_back(T[h]);
-                B.push_back(T[h]);
-            } else {
-                // depth never decreases with k, so T_{h+1} already sits at the common level and
-                // only a copy of T_h is dropped to it
-                const int lv = T[h + 1]->level;
-                if (T[h]->level < lv) { he_set_error("he_poly_eval: operand levels out of order"); return HE_ESTATE; }
-                HE_TRY(he_ct_copy(opA[k], T[h], stream));
-                HE_TRY(he_ct_drop_level(opA[k], lv));
-                A.push_back(opA[k]);
-                B.push_back(T[h + 1]);
-            }
-            O.push_back(T[k]);
-        }
-        HE_TRY(relin_batch(c, A, B, O, s));
-        for (int k = k0; k <= k1; k++) {
-            HE_TRY(he_mul_int(c, T[k], 2.0, stream));
-            if (k % 2 == 0) {
-                HE_TRY(he_add_const_int(c, T[k], -std::nearbyint(T[k]->scale), stream));
-            } else {
-                HE_TRY(retarget(c, T[1], T[k]->level, T[k]->scale, t1, s));
-                HE_TRY(he_sub(c, T[k], t1, stream));
-            }
-        }
+    int depth = 0;
+    while ((1 << depth) < deg) depth++;
+    std::map<int, std::vector<int>> by_level;
+    for (int j = 0; j < m; j++) {
+        if (!io[j] || io[j]->ctx != c) { he_set_error("he_poly_eval_many: ciphertext %d missing", j); return HE_EINVAL; }
+        if (io[j]->level < depth + 1) { he_set_error("he_poly_eval: needs %d levels", depth + 1); return HE_ELEVEL; }
+        by_level[io[j]->level].push_back(j);
     }
-    int lmin = T[1]->level;
-    for (int k = 2; k <= deg; k++) lmin = std::min(lmin, T[k]->level);
-    const double base = target_scale * (double)c->primes[lmin];
-    const double cst = std::nearbyint(cheb[0] * target_scale * (double)c->primes[lmin]);
-    if (deg <= 20 && lmin + 1 <= 24) {
-        // one pass: acc = sum_k K_k T_k + c_0 (same integers and sums as the term-by-term form)
-        std::vector<const u64 *> xs(deg);
-        std::vector<size_t> pss(deg);
-        std::vector<u64> res((size_t)deg * 24, 0), cres(24, 0);
-        for (int k = 1; k <= deg; k++) {
-            const double K = std::nearbyint(cheb[k] * target_scale * (double)c->primes[lmin] / T[k]->scale);
-            xs[k - 1] = T[k]->d;
-            pss[k - 1] = T[k]->pstride;
-            for (int i = 0; i <= lmin; i++)
-                if (!int_residue(K, c->primes[i], &res[(size_t)(k - 1) * 24 + i])) {
-                    he_set_error("he_poly_eval: constant is not an exact integer");
-                    return HE_EINVAL;
-                }
+    const size_t per = 2 * (size_t)deg + 4;
+    HE_TRY(poly_temps(c, (size_t)m * per));
+    size_t t0 = 0;
+    for (auto &kv : by_level) {
+        std::vector<he_ct *> grp;
+        std::vector<double> tg;
+        for (int j : kv.second) {
+            grp.push_back(io[j]);
+            tg.push_back(target_scales[j]);
         }
-        for (int i = 0; i <= lmin; i++)
-            if (!int_residue(cst, c->primes[i], &cres[i])) { he_set_error("he_poly_eval: bad constant"); return HE_EINVAL; }
-        HE_TRY(ensure_ct(c, acc, lmin));
-        HE_TRY(k_lincomb(c, xs.data(), pss.data(), res.data(), deg, cres.data(), lmin, acc->d, acc->pstride, s));
-        acc->scale = base;
-        HE_TRY(he_rescale(c, acc, stream));
-        acc->scale = target_scale;
-        return he_ct_copy(io, acc, stream);
+        HE_TRY(poly_eval_group(c, grp, cheb, deg, tg, t0, (cudaStream_t)stream));
+        t0 += grp.size() * per;
     }
-    bool first = true;
-    for (int k = 1; k <= deg; k++) {
-        HE_TRY(he_ct_copy(y, T[k], stream));
-        HE_TRY(he_ct_drop_level(y, lmin));
-        double K = std::nearbyint(cheb[k] * target_scale * (double)c->primes[lmin] / y->scale);
-        HE_TRY(he_mul_int(c, y, K, stream));
-        y->scale = base;
-        if (first) { HE_TRY(he_ct_copy(acc, y, stream)); first = false; }
-        else HE_TRY(he_add(c, acc, y, stream));
-    }
-    HE_TRY(he_add_const_int(c, acc, std::nearbyint(cheb[0] * target_scale * (double)c->primes[lmin]), stream));
-    HE_TRY(he_rescale(c, acc, stream));
-    acc->scale = target_scale;
-    return he_ct_copy(io, acc, stream);
+    return HE_OK;
 }
 
 // ================================================================================ wrappers

@@ -104,6 +104,8 @@ _SIGS = {
     "he_mul_relin": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "he_conv_create": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_int, c_int,
                                c_int, c_int, c_int, c_double, ctypes.POINTER(c_vp)]),
+    "he_conv_create_factored": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_int, c_int,
+                                        c_int, c_int, c_int, c_double, ctypes.POINTER(c_vp)]),
     "he_conv_destroy": (None, [c_vp]),
     "he_conv_fork": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "he_conv_out_layout": (c_int, [c_vp, ctypes.POINTER(he_layout)]),
@@ -124,6 +126,7 @@ _SIGS = {
     "he_pool_import_plaintexts": (c_int, [c_vp, I64P, I64P]),
     "he_pool_run": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_vp]),
     "he_poly_eval": (c_int, [c_vp, c_vp, F64P, c_int, c_double, c_vp]),
+    "he_poly_eval_many": (c_int, [c_vp, ctypes.POINTER(c_vp), c_int, F64P, c_int, F64P, c_vp]),
     "he_hconv2d": (c_int, [c_vp, ctypes.POINTER(he_layout), ctypes.POINTER(c_vp), F64P, F64P, c_int, c_int,
                            c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(he_layout),
                            ctypes.POINTER(c_vp), c_vp]),
@@ -445,6 +448,16 @@ def he_conv_create(ctx, layout, W, bias, stride, pad, level, in_scale):
     return h
 
 
+def he_conv_create_factored(ctx, layout, W, bias, stride, pad, level, in_scale):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    co, ci, kh, kw = W.shape
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
+    h = c_vp()
+    _check(load().he_conv_create_factored(ctx, ctypes.byref(layout), _p(W, F64P), None if b is None else _p(b, F64P),
+                                          co, ci, kh, kw, stride, pad, level, in_scale, ctypes.byref(h)))
+    return h
+
+
 def he_conv_destroy(conv):
     load().he_conv_destroy(conv)
 
@@ -550,6 +563,13 @@ def he_pool_import_plaintexts(pool, h=None, v=None):
 
 def he_pool_run(ctx, pool, ins, outs, mode=HE_PLAIN, stream=None):
     _check(load().he_pool_run(ctx, pool, _vp_array(ins), _vp_array(outs), mode, stream_ptr(stream)))
+
+
+def he_poly_eval_many(ctx, cts, cheb, target_scales, stream=None):
+    c = np.ascontiguousarray(cheb, dtype=np.float64)
+    t = np.ascontiguousarray(target_scales, dtype=np.float64)
+    _check(load().he_poly_eval_many(ctx, _vp_array(cts), len(cts), _p(c, F64P), c.size - 1, _p(t, F64P),
+                                    stream_ptr(stream)))
 
 
 def he_poly_eval(ctx, ct, cheb, target_scale, stream=None):

@@ -99,8 +99,11 @@ class Worker:
         for i, (stage, (conv, pool)) in enumerate(zip(st.stages, fs)):
             outc = b["conv%d" % i]
             H.he_conv_run(self.ctx, conv, cur, outc, mode, s)
-            for ct in outc:
-                H.he_poly_eval(self.ctx, ct, st.cheb, st.scale, s)
+            if mode == H.HE_PLAIN:
+                for ct in outc:
+                    H.he_poly_eval(self.ctx, ct, st.cheb, st.scale, s)
+            else:                                  # all shards of the layer through the tree together
+                H.he_poly_eval_many(self.ctx, outc, st.cheb, [st.scale] * len(outc), s)
             outp = b["pool%d" % i]
             H.he_pool_run(self.ctx, pool, outc, outp, mode, s)
             cur = outp

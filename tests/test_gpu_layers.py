@@ -268,3 +268,103 @@ def test_cifar_layer_full_ring():
         H.he_conv_destroy(conv)
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("c,co,m,k,pad", [(2, 3, 64, 3, 1), (3, 2, 64, 7, 3), (1, 4, 56, 5, 2)])
+def test_factored_conv_bit_exact(mid, c, co, m, k, pad):
+    """Channel-shard conv in the factored two-stage form: masks, then integer scalars."""
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = mid
+    level = 4
+    rng = np.random.default_rng(c * 31 + k)
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (co, c, k, k))
+    b = rng.uniform(-1, 1, co)
+    lin = Ly.image_layout(c, m, o.N)
+    plan = Ly.conv_plan_factored(lin, W, b, pad)
+    mpts = Ly.mask_plaintexts(plan, o.n, float(o.q[level]))
+    cts = [o.encrypt(s, level, nonce=800 + u) for u, s in enumerate(Ly.pack(lin, x))]
+    y_scale = o.pr.scale * float(o.q[level]) / float(o.q[level])
+    out_scale = y_scale * float(o.q[level - 1]) / float(o.q[level - 1])
+    bias = {v: encode(plan.bias[v], o.n, out_scale) for v in range(plan.lout.n_shards)}
+    ref_p = Ly.conv_he_factored(o, plan, cts, mpts, bias, raised=False)
+    ref_r = Ly.conv_he_factored(o, plan, cts, mpts, bias, raised=True)
+    lay = H.he_layout_image(c, m, o.N)
+    conv = H.he_conv_create_factored(g.h, lay, W, b, 1, pad, level, o.pr.scale)
+    H.he_keygen_rotations(g.h, H.he_conv_rotations(conv))
+    assert H.he_conv_out_level(conv) == level - 2
+    u, v, a, d = H.he_conv_export_plan(conv, o.N, with_diag=True)
+    keys = sorted(plan.masks)
+    assert len(keys) == len(u)
+    for i, (h, hs, t) in enumerate(keys):
+        assert (v[i], u[i], a[i]) == (h, hs, plan.amounts[t])
+        assert np.array_equal(d[i], plan.masks[(h, hs, t)])
+    H.he_conv_import_plaintexts(conv, np.stack([mpts[key] for key in keys]),
+                                np.stack([bias[vv] for vv in range(plan.lout.n_shards)]))
+    ins = [g.upload(ct) for ct in cts]
+    runs = [(H.HE_PLAIN, H.HE_KEY_STREAM_AUTO, ref_p), (H.HE_BATCHED, H.HE_KEY_STREAM_AUTO, ref_p),
+            (H.HE_FUSED, H.HE_KEY_STREAM_LDG, ref_r), (H.HE_FUSED, H.HE_KEY_STREAM_TMA, ref_r),
+            (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT, ref_r)]
+    for mode, ks, ref in runs:
+        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
+        outs = [g.ct(level - 2) for _ in range(plan.lout.n_shards)]
+        H.he_conv_run(g.h, conv, ins, outs, mode)
+        H.he_ctx_check(g.h)
+        for oc, rc in zip(outs, ref):
+            assert H.he_ct_scale(oc) == rc.scale
+            assert_ct_equal(g.download(oc), rc)
+    H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_AUTO)
+    want = torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(W), torch.tensor(b), padding=pad)[0].numpy()
+    img = Ly.unpack(plan.lout, np.stack([o.decrypt(ct) for ct in ref_r]))
+    assert np.abs(img - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+    H.he_conv_destroy(conv)
+
+
+def test_factored_stride2_conv_decrypts_to_torch(mid):
+    """The stem's shape in small: channel-shard input, 7x7 stride 2 in the factored form."""
+    from paper_2306_09189_gb300 import hegpu as H
+    o, g = mid
+    rng = np.random.default_rng(17)
+    c, co, m, level = 3, 4, 64, 5
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.normal(0, 0.05, (co, c, 7, 7))
+    lay = H.he_layout_image(c, m, o.N)
+    lin = Ly.image_layout(c, m, o.N)
+    ins = []
+    for u, s in enumerate(Ly.pack(lin, x)):
+        ct = g.ct(level)
+        H.he_encrypt(g.h, s, level, o.pr.scale, 60 + u, ct)
+        ins.append(ct)
+    conv = H.he_conv_create_factored(g.h, lay, W, None, 2, 3, level, o.pr.scale)
+    H.he_keygen_rotations(g.h, H.he_conv_rotations(conv))
+    lout = H.he_conv_out_layout(conv)
+    assert H.he_conv_out_level(conv) == level - 4
+    chan, row0 = lout.tables()
+    ol = Ly.Layout(lout.c, lout.m, lout.M, lout.N, lout.B, chan.astype(np.int64), row0.astype(np.int64))
+    want = torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(W), stride=2, padding=3)[0].numpy()
+    for mode in (H.HE_BATCHED, H.HE_FUSED):
+        outs = [g.ct(level - 4) for _ in range(lout.n_shards)]
+        H.he_conv_run(g.h, conv, ins, outs, mode)
+        img = Ly.unpack(ol, np.stack([H.he_decrypt(g.h, oc, o.N) for oc in outs]))
+        assert img.shape == want.shape
+        assert np.abs(img - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+    H.he_conv_destroy(conv)
+
+
+def test_poly_eval_many_equals_oracle_per_ciphertext(mid):
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = mid
+    o.gen_relin_key()
+    H.he_keygen_relin(g.h)
+    c = Ly.cheb_nodes_coeffs(Ly.gelu, 8, -8, 8)
+    rng = np.random.default_rng(77)
+    levels = [5, 4, 5, 4]
+    cts = [o.encrypt(rng.uniform(-1, 1, o.N), lv, nonce=950 + i) for i, lv in enumerate(levels)]
+    refs = [Ly.cheb_tree_he(o, ct, c) for ct in cts]
+    gcs = [g.upload(ct) for ct in cts]
+    H.he_poly_eval_many(g.h, gcs, c, [o.pr.scale] * len(gcs))
+    for gc, ref in zip(gcs, refs):
+        assert H.he_ct_level(gc) == ref.level and H.he_ct_scale(gc) == ref.scale
+        assert_ct_equal(g.download(gc), ref)

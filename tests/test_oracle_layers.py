@@ -206,3 +206,103 @@ def test_toy_pool_raised_basis_decrypts_to_fp64_pool(toy):
     img = Ly.unpack(plan.lout, np.stack([toy.decrypt(c) for c in out]))
     ref = torch.nn.functional.avg_pool2d(torch.tensor(x)[None], 2)[0].numpy()
     assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+
+
+def _small_ctx():
+    return Context(Params(log_n=10, n_q=4, n_p=2, dnum=2, q0_bits=50, q_bits=40, p_bits=50,
+                          scale=2.0 ** 40, seed=11))
+
+
+def test_raised_stage_single_rotation_is_the_hoisted_rotation():
+    # one term, plaintext 1, amount a: (phi(c0), 0) + ModDown(u_a) is exactly the hoisted
+    # rotation, which is pinned against np.roll elsewhere
+    ctx = _small_ctx()
+    z = np.random.default_rng(3).uniform(-1, 1, ctx.N)
+    ct = ctx.encrypt(z, 3, nonce=9)
+    for a in (1, 5, ctx.N - 3):
+        ctx.gen_rotation_key(a)
+        out = Ly.raised_stage(ctx, [ct], {0: [(0, a, None)]})[0]
+        ref = ctx.rotate_hoisted(ct, ctx.hoist(ct), a)
+        assert np.array_equal(out.c, ref.c)
+
+
+def test_raised_stage_without_rotations_is_the_direct_mac():
+    # only amount-0 terms: nothing is raised, the ModDown adds zero, the result is sum pt * ct
+    ctx = _small_ctx()
+    rng = np.random.default_rng(4)
+    cts = [ctx.encrypt(rng.uniform(-1, 1, ctx.N), 3, nonce=20 + i) for i in range(2)]
+    pts = [rng.integers(-2 ** 20, 2 ** 20, ctx.n) for _ in range(2)]
+    out = Ly.raised_stage(ctx, cts, {0: [(0, 0, pts[0]), (1, 0, pts[1])]})[0]
+    mods, psis = ctx.mods(3), ctx.psis(3)
+    want = []
+    for k in range(2):
+        acc = np.zeros((4, ctx.n), dtype=np.uint64)
+        for ct, pt in zip(cts, pts):
+            P = ctx.ntt(ctx.reduce_int(pt, mods), mods, psis).reshape(4, ctx.n)
+            X = ctx.ntt(ct.c[k], mods, psis).reshape(4, ctx.n)
+            ctx.lib.orc_mac(acc, P, X, 4, ctx.n, mods)
+        want.append(ctx.intt(acc, mods, psis).reshape(4, ctx.n))
+    assert np.array_equal(out.c, np.stack(want))
+
+
+def test_plaintexts_encoded_for_a_higher_level_serve_a_lower_one():
+    # a conv planned at level 3 (plaintexts at scale q_3) applied to an input at level 2:
+    # the output scale is scale * q_3 / q_2 and it still decrypts to the FP64 convolution
+    ctx = _small_ctx()
+    rng = np.random.default_rng(6)
+    x = rng.uniform(0, 1, (2, 16, 16))
+    W = rng.uniform(-1, 1, (2, 2, 3, 3))
+    b = rng.uniform(-1, 1, 2)
+    lin = Ly.image_layout(2, 16, ctx.N)
+    plan = Ly.conv_plan(lin, W, b, 1)
+    S = float(ctx.q[3])
+    pts = Ly.conv_plaintexts(plan, ctx.n, S)
+    cts = [ctx.encrypt(Ly.pack(lin, x)[u], 2, nonce=30 + u) for u in range(lin.n_shards)]
+    ref = _conv_ref(x, W, b, 1)
+    for f in (Ly.conv_he, Ly.conv_he_raised):
+        out = f(ctx, plan, cts, pts, pt_scale=S)
+        assert out[0].level == 1 and out[0].scale == ctx.pr.scale * S / float(ctx.q[2])
+        img = Ly.unpack(plan.lout, np.stack([ctx.decrypt(c) for c in out]))
+        assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+
+
+@pytest.mark.parametrize("c,co,m,N,k,pad", [(3, 4, 32, 512, 3, 1), (2, 2, 32, 256, 7, 3), (3, 2, 28, 256, 5, 2),
+                                           (1, 3, 64, 1024, 3, 1)])
+def test_factored_plan_equals_torch_conv2d(c, co, m, N, k, pad):
+    rng = np.random.default_rng(c * 7 + m)
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (co, c, k, k))
+    b = rng.uniform(-1, 1, co)
+    lin = Ly.image_layout(c, m, N)
+    plan = Ly.conv_plan_factored(lin, W, b, pad)
+    img = Ly.unpack(plan.lout, Ly.factored_slots(plan, Ly.pack(lin, x)))
+    assert np.abs(img - _conv_ref(x, W, b, pad)).max() < 1e-12
+    # own shard plus at most one neighbour per (shard, tap): the masks number <= 2 H T, and a
+    # tap whose rows stay inside one shard has only the own mask there
+    assert len(plan.masks) <= 2 * plan.H * k * k
+    assert set(plan.amounts) == {((kk - pad) * lin.M + (ll - pad)) % N for kk in range(k) for ll in range(k)}
+
+
+def test_factored_scalars_round_half_away():
+    assert Ly.round_half_away(2.5) == 3 and Ly.round_half_away(-2.5) == -3
+    assert Ly.round_half_away(-0.49) == 0 and Ly.round_half_away(7.0) == 7
+
+
+@pytest.mark.parametrize("raised", [False, True])
+def test_factored_conv_he_decrypts_to_fp64(raised):
+    ctx = Context(Params(log_n=10, n_q=5, n_p=2, dnum=3, q0_bits=50, q_bits=40, p_bits=50,
+                         scale=2.0 ** 40, seed=12))
+    rng = np.random.default_rng(13)
+    c, co, m, k, pad = 2, 3, 32, 3, 1
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (co, c, k, k))
+    b = rng.uniform(-1, 1, co)
+    lin = Ly.image_layout(c, m, ctx.N)
+    plan = Ly.conv_plan_factored(lin, W, b, pad)
+    assert plan.H == 2
+    cts = [ctx.encrypt(s, 4, nonce=40 + u) for u, s in enumerate(Ly.pack(lin, x))]
+    out = Ly.conv_he_factored(ctx, plan, cts, raised=raised)
+    assert out[0].level == 2
+    img = Ly.unpack(plan.lout, np.stack([ctx.decrypt(ct) for ct in out]))
+    ref = _conv_ref(x, W, b, pad)
+    assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())

@@ -111,3 +111,13 @@ def test_key_switching_key_decrypts_to_gadget(ctx):
             e = (v[i].astype(object) - np.asarray(gad, dtype=object)) % m
             e = np.where(e > m // 2, e - m, e).astype(np.int64)
             assert np.abs(e).max() <= 21
+
+
+def test_special_modulus_below_a_digit_is_rejected():
+    # digits of 3 primes (~130 bits) against P of 2 primes (~100 bits): key switching would
+    # not be correct, key generation refuses the set (the library refuses the context)
+    ctx = Context(Params(log_n=10, n_q=5, n_p=2, dnum=2, q0_bits=50, q_bits=40, p_bits=50, scale=2.0 ** 40, seed=1))
+    with pytest.raises(ValueError):
+        ctx.gen_rotation_key(1)
+    with pytest.raises(ValueError):
+        ctx.gen_relin_key()
