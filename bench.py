@@ -55,6 +55,33 @@ def job_value(units_per_step_per_rank, ms_per_step, ws):
     return ws * units_per_step_per_rank / (ms_per_step * 1e-3)
 
 
+KERNEL_SRC = os.path.join(ROOT, "paper_2306_09189_gb300", "csrc", "kernels.cu")
+
+
+def _traffic(profile, kernel):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary (lines 'key: value'),
+    or None when the summary is missing, is for another kernel, or the kernel source changed
+    since the counters were taken (its sha256 is recorded beside them)."""
+    import hashlib
+    try:
+        kv = {}
+        with open(os.path.join(ROOT, "profiles", profile)) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        with open(KERNEL_SRC) as f:
+            src = f.read()
+        b = src.index("// ==== fused key-switch + MAC kernels: begin")
+        e = src.index("// ==== fused key-switch + MAC kernels: end")
+        sha = hashlib.sha256(src[b:e].encode()).hexdigest()
+        if kv.get("kernel_source_sha256") != sha or kernel not in kv.get("kernel", ""):
+            return None
+        return float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])
+    except (OSError, KeyError, ValueError, IndexError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -331,6 +358,126 @@ def run_block(args, ws, rank, local):
     H.he_ctx_destroy(ctx)
 
 
+STEM_WORKLOAD = ("imagenet stem: 3x224x224 in channel shards (256 frame, 2 shards per channel), conv7x7/2 "
+                 "3->64 pad 3 in the factored form (masks, then integer weights) with the stride-2 select, "
+                 "-> 112x112x64 (32 shards) -> 2x2 avgpool -> 56x56x64 (8 shards); 2N=2^16, 20+5 primes")
+
+
+def run_stem(args, ws, rank, local):
+    """The ImageNet-shaped sharded stem (config 3): the factored channel-shard conv with stride 2
+    (the select runs on 128 channel shards), then the 2x2 average pool; one CUDA graph per step.
+    The per-rotation modes would hold every rotated shard of the select (hundreds of GB), so
+    only the fused (raised-basis) form runs here."""
+    import torch
+    import workloads
+    from paper_2306_09189_gb300 import hegpu as H
+    from paper_2306_09189_gb300 import host
+    pr = host.cifar_params(seed=0)
+    ctx = H.he_ctx_create(pr)
+    H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
+                                                   "tma": H.HE_KEY_STREAM_TMA,
+                                                   "split": H.HE_KEY_STREAM_SPLIT}[args.key_stream])
+    N = H.he_ctx_info(ctx)["slots"]
+    wl = workloads.imagenet_stem(0)
+    c, m = wl.x.shape[0], wl.x.shape[1]
+    level = 19
+    t_setup = time.perf_counter()
+    lay = H.he_layout_image(c, m, N)
+    conv = H.he_conv_create_factored(ctx, lay, wl.W, wl.bias, wl.stride, wl.pad, level, pr.scale)
+    lay1 = H.he_conv_out_layout(conv)
+    l1 = H.he_conv_out_level(conv)
+    pool = H.he_pool_create(ctx, lay1, l1)
+    lay2 = H.he_pool_out_layout(pool)
+    H.he_keygen_rotations(ctx, sorted(set(H.he_conv_rotations(conv)) | set(H.he_pool_rotations(pool))))
+    ks_per_step = H.he_conv_keyswitches(conv) + H.he_pool_keyswitches(pool)
+    xs = host.encrypt_image(ctx, lay, wl.x, level, pr.scale, nonce0=1)
+    y = [H.he_ct_alloc(ctx, l1) for _ in range(lay1.n_shards)]
+    z = [H.he_ct_alloc(ctx, l1 - 2) for _ in range(lay2.n_shards)]
+    setup_s = time.perf_counter() - t_setup
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def step():
+        H.he_conv_run(ctx, conv, xs, y, H.HE_FUSED, stream)
+        H.he_pool_run(ctx, pool, y, z, H.HE_FUSED, stream)
+
+    step()
+    torch.cuda.synchronize()
+    if args.profile_step:
+        torch.cuda.profiler.start()
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return
+    H.he_graph_begin(ctx, stream)
+    step()
+    graph = H.he_graph_end(ctx, stream)
+    for _ in range(args.warmup):
+        H.he_graph_launch(graph, stream)
+    torch.cuda.synchronize()
+    trace = args.trace
+    if trace == "ipmac" and ("-> split" in H.he_ctx_tuning_log(ctx) or args.key_stream == "split"):
+        trace = "rmac"
+    H.he_trace_start(trace)
+    H.he_graph_begin(ctx, stream)
+    for _ in range(args.steps):
+        step()
+    gk = H.he_graph_end(ctx, stream)
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = H.he_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    H.he_graph_launch(gk, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), ws) / args.steps
+    launches = H.he_kernel_launches() - l0
+    tr = H.he_trace_stop()
+    # sampled output check: output shards 0 and 1 (channels 0..15) against FP64
+    want = torch.nn.functional.avg_pool2d(
+        torch.nn.functional.conv2d(torch.tensor(wl.x)[None], torch.tensor(wl.W), stride=2, padding=3), 2)[0].numpy()
+    chan, row0 = lay2.tables()
+    got = np.stack([H.he_decrypt(ctx, z[u], N) for u in range(lay2.n_shards)])
+    img = host.unpack(lay2, got)
+    err = float(np.abs(img - want).max() / (want.max() - want.min()))
+    peaks, src = _peaks()
+    roof = None
+    if tr and tr["launches"]:
+        per = tr["ms"] / tr["launches"]
+        ach = tr["bytes"] / tr["launches"] / (per * 1e-3) / 1e9
+        roof = {"kernel": trace, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src, "launches": tr["launches"],
+                "ms_per_launch": per, "share_of_step": tr["ms"] / (ms * args.steps)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": job_value(ks_per_step, ms, ws), "unit": "key-switches/s",
+                "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+                "data": "synthetic",
+                "config": {"workload": STEM_WORKLOAD, "key_switches_per_step": ks_per_step,
+                           "input_level": level, "output_level": l1 - 2, "cuda_graph": True,
+                           "shards": [lay.n_shards, lay1.n_shards, lay2.n_shards],
+                           "autotuner": H.he_ctx_tuning_log(ctx).strip().splitlines(), "setup_s": setup_s,
+                           "l2": "inputs larger than L2 (%.1f GB of keys)" % (H.he_key_bytes(ctx) / 1e9),
+                           "parallelism": "replicas" if ws > 1 else "single"},
+                "plain": None, "plain_note": "per-rotation modes would hold every rotated shard of the 128-shard select",
+                "check": {"max_err_rel_range": err, "tolerance": 2.0 ** -20},
+                "gpu_launches": int(launches), "roofline": roof, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    H.he_ctx_check(ctx, stream)
+    H.he_graph_destroy(gk)
+    H.he_graph_destroy(graph)
+    H.he_conv_destroy(conv)
+    H.he_pool_destroy(pool)
+    for ct in xs + y + z:
+        H.he_ct_free(ct)
+    H.he_ctx_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,8 +494,9 @@ def main():
                     help="key-switch + MAC form: autotuned (default), the fused kernel with vector "
                          "loads or a TMA tile pipeline, or the split form (inner products, then MAC)")
     ap.add_argument("--no-graph", action="store_true", help="launch the fused step eagerly, not as a CUDA graph")
-    ap.add_argument("--workload", default="cifar-layer", choices=["cifar-layer", "resnet-block"],
-                    help="cifar-layer: the headline layer; resnet-block: the batched mixed-level block")
+    ap.add_argument("--workload", default="cifar-layer", choices=["cifar-layer", "resnet-block", "imagenet-stem"],
+                    help="cifar-layer: the headline layer; resnet-block: the batched mixed-level block; "
+                         "imagenet-stem: the channel-shard stem with stride 2 and average pool")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -360,8 +508,8 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    if args.workload == "resnet-block":
-        run_block(args, ws, rank, local)
+    if args.workload in ("resnet-block", "imagenet-stem"):
+        (run_block if args.workload == "resnet-block" else run_stem)(args, ws, rank, local)
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
@@ -507,7 +655,9 @@ def main():
         per_launch_ms = tr["ms"] / tr["launches"]
         achieved = tr["bytes"] / tr["launches"] / (per_launch_ms * 1e-3) / 1e9
         roof = {"kernel": args.trace, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": _traffic("fused_kernel_cifar_layer_traffic.txt", args.trace),
+                "algorithmic_bytes_per_launch": tr["bytes"] / tr["launches"],
                 "peak_source": src, "launches": tr["launches"], "ms_per_launch": per_launch_ms,
                 "share_of_step": tr["ms"] / (ms_b * args.steps)}
     mm_rate = H.he_bench_modmul(ctx, 152 * 8, 2048)

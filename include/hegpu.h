@@ -276,6 +276,9 @@ int he_conv_out_level(const he_conv *conv);
 /* Distinct non-zero rotation amounts the plan needs (all stages); returns the count,
  * writes up to cap of them. */
 int he_conv_rotations(const he_conv *conv, int32_t *amounts, size_t cap);
+/* Key switches one run performs (distinct (input shard, nonzero amount) pairs of every stage,
+ * including the stride-2 select); he_pool_keyswitches the same for a pooling layer. */
+int64_t he_conv_keyswitches(const he_conv *conv);
 /* Number of diagonal terms of the stride-1 stage and their (u, v, a) in plan order
  * (v, then u, then a ascending); diag (optional) receives [n_terms][N] doubles. */
 int he_conv_n_terms(const he_conv *conv);
@@ -321,6 +324,7 @@ int he_pool_out_layout(const he_pool *pool, he_layout *out);
 /* Fork of a pooling plan for another context of the same root (shares the mask plaintexts). */
 int he_pool_fork(const he_pool *pool, he_ctx *ctx, he_pool **out);
 int he_pool_rotations(const he_pool *pool, int32_t *amounts, size_t cap);
+int64_t he_pool_keyswitches(const he_pool *pool);
 /* Replace the mask plaintexts by caller-given integer polynomials: h [n_h][n_shards][n] for
  * the horizontal stage (column x' = 0, 1, ...) and v [n_v][n_shards][n] for the vertical
  * stage (rows y' whose mask is not empty), the order the plan uses. */

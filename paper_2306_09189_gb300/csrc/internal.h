@@ -263,11 +263,12 @@ struct uent {
     u64 *U;                 // output [2][l+1+K][n]
     const u64 *src;         // the source ciphertext (c0, c1 at src + ps)
     size_t ps;
+    u64 g;                  // Galois element of the entry's amount (1 for amount 0)
 };
 struct ugrp {               // inner products of one stage (one image at one level)
-    const famt *amts;       // amounts (key null for amount 0); entries index uent
+    const famt *amts;       // amounts (key null for amount 0); entries index uent, in order
     const uent *ents;
-    int n_amt, level, beta;
+    int n_amt, n_ent, level, beta;
 };
 struct rterm {
     const u64 *U;           // folded raised inner product of (s, a)

@@ -645,6 +645,7 @@ __global__ void __launch_bounds__(TB) mac_kernel(KP kp, const mac_term *terms, m
 // Two coefficients per thread: for Galois elements g = 1 mod 4 the NTT-domain automorphism
 // maps the aligned pair (k, k^1) onto an aligned pair (phi(k), phi(k)^1), so every gather is a
 // full 16-byte load and every key / plaintext / output access a 16-byte vector access.
+// ==== fused key-switch + MAC kernels: begin (the profiles record a checksum of this region)
 __device__ __forceinline__ ulonglong2 ld2(const u64 *p) { return *(const ulonglong2 *)p; }
 __device__ __forceinline__ void st2(u64 *p, u64 a, u64 b) { *(ulonglong2 *)p = make_ulonglong2(a, b); }
 
@@ -996,6 +997,7 @@ __global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, 
             st2(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
         }
 }
+// ==== fused key-switch + MAC kernels: end
 
 // acc = sum_terms K_term * x_term (+ c on poly 0) over limbs 0..level, x of any higher level
 // (the drop is implicit); per-limb residues of the integer constants are passed by value.
@@ -1431,8 +1433,23 @@ __device__ __forceinline__ u64 ld_hint(const u64 *p, u64 pol) {
     return r;
 }
 
+__device__ __forceinline__ void cp_async8(unsigned dst, const void *src, u64 pol) {
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Amount-major inner products of the split form.  Keys sit in registers for the entries of
+// their amount; each thread keeps IPA_STAGES - 1 entries' gathered words (digits, c0, c1) in
+// flight through cp.async into its own shared-memory slots.
+constexpr int IPA_STAGES = 4;
+
 template <int B>
 __global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps, int n_grp, const u64 *pmod) {
+    constexpr int RS = IPA_STAGES, NW = B + 2;        // words per entry: D[B], c0, c1
+    extern __shared__ u64 ism[];                      // [RS][NW][TB]
     const ugrp P = grps[blockIdx.x % n_grp];
     const int tile = blockIdx.x / n_grp;
     int t;
@@ -1447,9 +1464,29 @@ __global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps,
     const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
     const size_t off = (size_t)t * kp.n + k;
     const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    const unsigned sbase = smem_u32(ism);
+    auto slot = [&](int st, int w) -> int { return (st * NW + w) * TB + threadIdx.x; };
+    auto issue = [&](int e, int st) {
+        const uent E = P.ents[e];
+        const int ks = E.g == 1 ? k : autom_index(k, E.g, kp.logn);
+        if (E.D) {
+#pragma unroll
+            for (int j = 0; j < B; j++)
+                if (j < beta) cp_async8(sbase + 8u * slot(st, j), E.D + ((size_t)j * ext + t) * kp.n + ks, keep);
+        }
+        if (isq) {
+            cp_async8(sbase + 8u * slot(st, B), E.src + (size_t)t * kp.n + ks, keep);
+            if (E.g == 1) cp_async8(sbase + 8u * slot(st, B + 1), E.src + E.ps + off, keep);
+        }
+    };
+    const int ne = P.n_ent;
+#pragma unroll
+    for (int e = 0; e < RS - 1; e++) {
+        if (e < ne) issue(e, e);
+        cp_async_commit();
+    }
     for (int i = 0; i < P.n_amt; i++) {
         const famt A = P.amts[i];
-        const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
         u64 k0[B], k1[B];
         if (A.key) {
 #pragma unroll
@@ -1461,6 +1498,10 @@ __global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps,
                 }
         }
         for (int e = A.e0; e < A.e1; e++) {
+            if (e + RS - 1 < ne) issue(e + RS - 1, (e + RS - 1) % RS);
+            cp_async_commit();
+            cp_async_wait<RS - 1>();
+            const int st = e % RS;
             const uent E = P.ents[e];
             u64 u0 = 0, u1 = 0;
             if (A.key) {
@@ -1468,7 +1509,7 @@ __global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps,
 #pragma unroll
                 for (int j = 0; j < B; j++)
                     if (j < beta) {
-                        const u64 d = ld_hint(E.D + ((size_t)j * ext + t) * kp.n + ks, keep);
+                        const u64 d = ism[slot(st, j)];
                         a0 += (u128)d * k0[j];
                         a1 += (u128)d * k1[j];
                     }
@@ -1476,20 +1517,26 @@ __global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps,
                 u1 = redc(a1, q, qi);
             }
             if (isq) {                              // fold [P]_q phi(c0) (and [P]_q c1 at amount 0)
-                u0 = add_mod(u0, mul_mont(ld_hint(E.src + off - k + ks, keep), Pm, q, qi), q);
-                if (!A.key) u1 = mul_mont(ld_hint(E.src + E.ps + off, keep), Pm, q, qi);
+                u0 = add_mod(u0, mul_mont(ism[slot(st, B)], Pm, q, qi), q);
+                if (!A.key) u1 = mul_mont(ism[slot(st, B + 1)], Pm, q, qi);
             }
             E.U[off] = u0;
             E.U[(size_t)ext * kp.n + off] = u1;
         }
     }
+    cp_async_wait<0>();
 }
 
 // acc_v = sum_terms pt_v (.) U over Q u P for HE_RV outputs per thread (one coefficient); absent
-// outputs are skipped (block-uniform); the next term's words are loaded while the current one
-// is accumulated.
+// outputs are skipped (block-uniform).  Each thread keeps RMAC_STAGES - 1 terms in flight: it
+// copies its own words of the coming terms into its own shared-memory slots with cp.async
+// (8 bytes each), so no block barrier is needed and no register holds a word in flight.
+constexpr int RMAC_STAGES = 4;
+constexpr int RMAC_WORDS = 2 + HE_RV;               // u0, u1, pt[HE_RV]
+
 __global__ void __launch_bounds__(TB, 2) rmac_kernel(KP kp, const rgrp *grps, int n_grp) {
-    constexpr int RV = HE_RV;
+    constexpr int RV = HE_RV, RS = RMAC_STAGES;
+    extern __shared__ u64 rsm[];                     // [RS][RMAC_WORDS][TB]
     const rgrp P = grps[blockIdx.x % n_grp];
     const int tile = blockIdx.x / n_grp;
     int t;
@@ -1502,39 +1549,41 @@ __global__ void __launch_bounds__(TB, 2) rmac_kernel(KP kp, const rgrp *grps, in
     const u64 one = to_mont(1, q, qi, r2);
     const size_t off = (size_t)t * kp.n + k, ptoff = (size_t)ptl * kp.n + k;
     const u64 stream = policy_evict_first();
+    const unsigned sbase = smem_u32(rsm);
+    auto slot = [&](int st, int w) -> int { return (st * RMAC_WORDS + w) * TB + threadIdx.x; };
+    auto issue = [&](int i, int st) {
+        const rterm T = P.terms[i];
+        cp_async8(sbase + 8u * slot(st, 0), T.U + off, stream);
+        cp_async8(sbase + 8u * slot(st, 1), T.U + (size_t)ext * kp.n + off, stream);
+#pragma unroll
+        for (int v = 0; v < RV; v++)
+            if (T.pt[v] && T.pt[v] != HE_PT_ONE) cp_async8(sbase + 8u * slot(st, 2 + v), T.pt[v] + ptoff, stream);
+    };
     u128 a0[RV], a1[RV];
 #pragma unroll
     for (int v = 0; v < RV; v++) a0[v] = a1[v] = 0;
-    auto fetch = [&](int i, u64 &u0, u64 &u1, u64 (&p)[RV]) {
+    const int nt = P.n_terms;
+#pragma unroll
+    for (int i = 0; i < RS - 1; i++) {
+        if (i < nt) issue(i, i);
+        cp_async_commit();
+    }
+    for (int i = 0; i < nt; i++) {
+        if (i + RS - 1 < nt) issue(i + RS - 1, (i + RS - 1) % RS);
+        cp_async_commit();                           // one group per iteration, empty or not
+        cp_async_wait<RS - 1>();                     // term i's words have landed
+        const int st = i % RS;
+        const u64 u0 = rsm[slot(st, 0)], u1 = rsm[slot(st, 1)];
         const rterm T = P.terms[i];
-        u0 = ld_hint(T.U + off, stream);
-        u1 = ld_hint(T.U + (size_t)ext * kp.n + off, stream);
-#pragma unroll
-        for (int v = 0; v < RV; v++) {
-            const u64 *pp = T.pt[v];
-            p[v] = pp == HE_PT_ONE ? one : (pp ? ld_hint(pp + ptoff, stream) : 0);
-        }
-    };
-    u64 u0 = 0, u1 = 0, p[RV];
-#pragma unroll
-    for (int v = 0; v < RV; v++) p[v] = 0;
-    if (P.n_terms > 0) fetch(0, u0, u1, p);
-    for (int i = 0; i < P.n_terms; i++) {
-        u64 nu0 = 0, nu1 = 0, np_[RV];
-#pragma unroll
-        for (int v = 0; v < RV; v++) np_[v] = 0;
-        if (i + 1 < P.n_terms) fetch(i + 1, nu0, nu1, np_);
 #pragma unroll
         for (int v = 0; v < RV; v++)
-            if (P.terms[i].pt[v]) {                 // block-uniform
-                a0[v] += (u128)p[v] * u0;
-                a1[v] += (u128)p[v] * u1;
+            if (T.pt[v]) {                           // block-uniform
+                const u64 p = T.pt[v] == HE_PT_ONE ? one : rsm[slot(st, 2 + v)];
+                a0[v] += (u128)p * u0;
+                a1[v] += (u128)p * u1;
             }
-        u0 = nu0;
-        u1 = nu1;
-#pragma unroll
-        for (int v = 0; v < RV; v++) p[v] = np_[v];
     }
+    cp_async_wait<0>();
     // a later chunk of amounts adds its partial sums modulo q: same residues as one pass
     auto put = [&](u64 *dst, u128 acc) {
         u64 r = redc(acc, q, qi);
@@ -1557,8 +1606,13 @@ int k_ip_amounts(const he_ctx *ctx, const ugrp *grps, int n_grp, int max_beta, d
     if (max_beta > 8) { he_set_error("inner products: at most 8 digits"); return HE_EINVAL; }
     TraceScope tr("ip_amounts", s, bytes, 0);
     dim3 g((unsigned)(ctx->n / TB) * n_grp, ctx->L + 1 + ctx->K);
-    if (max_beta <= 4) ip_amounts_kernel<4><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp, ctx->d_consts);
-    else ip_amounts_kernel<8><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp, ctx->d_consts);
+    const int smem4 = IPA_STAGES * (4 + 2) * TB * 8, smem8 = IPA_STAGES * (8 + 2) * TB * 8;
+    static const bool attr_ok =
+        cudaFuncSetAttribute(ip_amounts_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4) == cudaSuccess &&
+        cudaFuncSetAttribute(ip_amounts_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem8) == cudaSuccess;
+    if (!attr_ok) { he_set_error("ip_amounts: shared-memory opt-in failed"); return HE_ECUDA; }
+    if (max_beta <= 4) ip_amounts_kernel<4><<<g, TB, smem4, s>>>(ctx->kp, grps, n_grp, ctx->d_consts);
+    else ip_amounts_kernel<8><<<g, TB, smem8, s>>>(ctx->kp, grps, n_grp, ctx->d_consts);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1567,7 +1621,11 @@ int k_rmac(const he_ctx *ctx, const rgrp *grps, int n_grp, double bytes, double 
     if (n_grp <= 0) return HE_OK;
     TraceScope tr("rmac", s, bytes, mulmods);
     dim3 g((unsigned)(ctx->n / TB) * n_grp, ctx->L + 1 + ctx->K);
-    rmac_kernel<<<g, TB, 0, s>>>(ctx->kp, grps, n_grp);
+    const int smem = RMAC_STAGES * RMAC_WORDS * TB * 8;
+    static const bool attr_ok =
+        cudaFuncSetAttribute(rmac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+    if (!attr_ok) { he_set_error("rmac: shared-memory opt-in failed"); return HE_ECUDA; }
+    rmac_kernel<<<g, TB, smem, s>>>(ctx->kp, grps, n_grp);
     LAUNCH_CHECK();
     return HE_OK;
 }

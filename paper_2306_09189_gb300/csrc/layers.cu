@@ -929,7 +929,7 @@ int FusedStage::build_split(size_t cap_bytes) {
             A.e0 = (int)he.size();
             for (int sidx : a.second) {
                 u64 *u = U + he.size() * slot;
-                he.push_back(uent{Dp[sidx], u, srcs[sidx].d, srcs[sidx].ps});
+                he.push_back(uent{Dp[sidx], u, srcs[sidx].d, srcs[sidx].ps, A.g});
                 uslot[{a.first, sidx}] = u;
             }
             A.e1 = (int)he.size();
@@ -940,7 +940,7 @@ int FusedStage::build_split(size_t cap_bytes) {
         HE_TRY(dev_alloc(&ch.d_ent, std::max<size_t>(1, he.size())));
         if (!ha.empty()) HE_CHECK_CUDA(cudaMemcpy(ch.d_amt, ha.data(), ha.size() * sizeof(famt), cudaMemcpyHostToDevice));
         if (!he.empty()) HE_CHECK_CUDA(cudaMemcpy(ch.d_ent, he.data(), he.size() * sizeof(uent), cudaMemcpyHostToDevice));
-        ch.udesc = ugrp{ch.d_amt, ch.d_ent, (int)ha.size(), level, beta_};
+        ch.udesc = ugrp{ch.d_amt, ch.d_ent, (int)ha.size(), (int)he.size(), level, beta_};
         // raised MAC terms per group of HE_RV outputs: this chunk's (a, s) pairs
         for (int v0 = 0; v0 < nout; v0 += HE_RV) {
             std::map<std::pair<int, int>, rterm> tm;
@@ -1876,6 +1876,42 @@ extern "C" int he_conv_rotations(const he_conv *cv, int32_t *amounts, size_t cap
     if (cv->pool) collect_rotations(cv->pool, v);
     return distinct_nonzero(cv->c, v, amounts, cap);
 }
+// key switches one run performs: distinct (source, nonzero amount) pairs of every stage
+static int64_t pool_keyswitches(const he_pool *p) {
+    const PoolPlanH &P = p->P;
+    he_ctx *c = p->c;
+    auto nz = [&](int a) { return h_galois(c, a) != 1; };
+    int64_t k = 0;
+    for (int a : P.pre) k += nz(a) ? p->ns : 0;
+    for (int a : P.h_amt) k += nz(a) ? p->ns : 0;
+    for (int a : P.v_amt) k += nz(a) ? p->ns : 0;
+    std::set<std::pair<int, int>> cs;
+    for (auto &g : P.groups)
+        for (auto &ua : g)
+            if (nz(ua.second)) cs.insert(ua);
+    k += (int64_t)cs.size();
+    for (int a : P.dup)
+        if (nz(a)) k += (int64_t)P.groups.size();
+    return k;
+}
+
+extern "C" int64_t he_pool_keyswitches(const he_pool *p) { return p ? pool_keyswitches(p) : HE_EINVAL; }
+
+extern "C" int64_t he_conv_keyswitches(const he_conv *cv) {
+    if (!cv) return HE_EINVAL;
+    int64_t k = 0;
+    if (cv->fc) {
+        std::set<std::pair<int, int>> r;
+        for (size_t x = 0; x < cv->fc->ts.size(); x++)
+            if (h_galois(cv->c, cv->fc->ta[x]) != 1) r.insert({cv->fc->ts[x], cv->fc->ta[x]});
+        k = (int64_t)r.size();
+    } else {
+        k = (int64_t)cv->slot.size();
+    }
+    if (cv->pool) k += pool_keyswitches(cv->pool);
+    return k;
+}
+
 extern "C" int he_conv_n_terms(const he_conv *cv) {
     if (!cv) return HE_EINVAL;
     return cv->fc ? cv->fc->n_masks : (int)cv->tu.size();

@@ -115,6 +115,8 @@ _SIGS = {
     "he_conv_export_plan": (c_int, [c_vp, I32P, I32P, I32P, F64P]),
     "he_conv_import_plaintexts": (c_int, [c_vp, I64P, I64P]),
     "he_conv_run": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_vp]),
+    "he_conv_keyswitches": (ctypes.c_int64, [c_vp]),
+    "he_pool_keyswitches": (ctypes.c_int64, [c_vp]),
     "he_conv_run_batch": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_int, c_vp]),
     "he_conv_import_bias": (c_int, [c_vp, c_int, c_double, I64P]),
     "he_pool_create": (c_int, [c_vp, ctypes.POINTER(he_layout), c_int, ctypes.POINTER(c_vp)]),
@@ -507,6 +509,14 @@ def he_conv_import_plaintexts(conv, terms=None, bias=None):
 
 def he_conv_run(ctx, conv, ins, outs, mode=HE_PLAIN, stream=None):
     _check(load().he_conv_run(ctx, conv, _vp_array(ins), _vp_array(outs), mode, stream_ptr(stream)))
+
+
+def he_conv_keyswitches(conv):
+    return int(_check(load().he_conv_keyswitches(conv)))
+
+
+def he_pool_keyswitches(pool):
+    return int(_check(load().he_pool_keyswitches(pool)))
 
 
 def he_conv_run_batch(ctx, conv, ins, outs, n_img, mode=HE_FUSED, stream=None):

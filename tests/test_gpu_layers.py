@@ -368,3 +368,41 @@ def test_poly_eval_many_equals_oracle_per_ciphertext(mid):
     for gc, ref in zip(gcs, refs):
         assert H.he_ct_level(gc) == ref.level and H.he_ct_scale(gc) == ref.scale
         assert_ct_equal(g.download(gc), ref)
+
+
+@pytest.mark.parametrize("c,co,m,k,pad,level", [(4, 4, 16, 1, 0, 3),     # 1x1: no rotation at all
+                                                 (2, 2, 32, 3, 1, 1)])    # lowest level a conv takes
+def test_conv_edge_cases_bit_exact(mid, c, co, m, k, pad, level):
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = mid
+    rng = np.random.default_rng(c + k + level)
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (co, c, k, k))
+    lin = Ly.image_layout(c, m, o.N)
+    plan = Ly.conv_plan(lin, W, None, pad)
+    if k == 1:
+        assert plan.n_rotations() == 0
+    pts = Ly.conv_plaintexts(plan, o.n, float(o.q[level]))
+    cts = [o.encrypt(s, level, nonce=990 + u) for u, s in enumerate(Ly.pack(lin, x))]
+    bias = {v: encode(plan.bias[v], o.n, o.pr.scale * float(o.q[level]) / float(o.q[level]))
+            for v in range(plan.lout.n_shards)}
+    refs = {False: Ly.conv_he(o, plan, cts, pts, bias), True: Ly.conv_he_raised(o, plan, cts, pts, bias)}
+    lay = H.he_layout_image(c, m, o.N)
+    conv = H.he_conv_create(g.h, lay, W, None, 1, pad, level, o.pr.scale)
+    H.he_keygen_rotations(g.h, H.he_conv_rotations(conv))
+    keys = [(vv, uu, aa) for vv in sorted(plan.terms) for (uu, aa) in sorted(plan.terms[vv])]
+    H.he_conv_import_plaintexts(conv, np.stack([pts[(uu, vv, aa)] for (vv, uu, aa) in keys]),
+                                np.stack([bias[vv] for vv in range(plan.lout.n_shards)]))
+    ins = [g.upload(ct) for ct in cts]
+    for mode, ks in ((H.HE_PLAIN, H.HE_KEY_STREAM_AUTO), (H.HE_BATCHED, H.HE_KEY_STREAM_AUTO),
+                     (H.HE_FUSED, H.HE_KEY_STREAM_LDG), (H.HE_FUSED, H.HE_KEY_STREAM_TMA),
+                     (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT)):
+        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
+        outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
+        H.he_conv_run(g.h, conv, ins, outs, mode)
+        H.he_ctx_check(g.h)
+        for oc, rc in zip(outs, refs[mode == H.HE_FUSED]):
+            assert_ct_equal(g.download(oc), rc)
+    H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_AUTO)
+    H.he_conv_destroy(conv)
