@@ -123,6 +123,9 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  *   HE_KEY_STREAM_TMA (1): cp.async.bulk copies into a double-buffered shared-memory tile,
  *     signalled by mbarriers with bounded waits (a wait that gives up is reported by
  *     he_ctx_check as HE_ETIMEOUT).  Used for up to 4 digits; otherwise the LDG form runs;
+ *   HE_KEY_STREAM_CP (4): every word of an (amount, source) item (key words, gathered digits,
+ *     plaintexts, source words) copied by each thread with cp.async into its own shared-memory
+ *     slots, two items ahead of the one it computes (no block barrier).  Up to 4 digits;
  *   HE_KEY_STREAM_SPLIT (3): the split form: the raised inner product of every (source,
  *     amount) is written to HBM once (each key read once), then a raised-basis MAC forms the
  *     plaintext-weighted sums of 4 outputs per pass; amounts go in chunks of at most 2 GB of
@@ -136,6 +139,7 @@ int he_ctx_check(he_ctx *ctx, void *stream);
 #define HE_KEY_STREAM_TMA 1
 #define HE_KEY_STREAM_AUTO 2
 #define HE_KEY_STREAM_SPLIT 3
+#define HE_KEY_STREAM_CP 4
 int he_ctx_set_option(he_ctx *ctx, int option, int value);
 int he_ctx_get_option(const he_ctx *ctx, int option, int *value);
 /* The autotuner's decisions so far (one line per tuned stage: the candidates' times and the

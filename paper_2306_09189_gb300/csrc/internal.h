@@ -251,7 +251,7 @@ struct fgrp {
 // plaintext word is fetched from DRAM once and served to the other groups from L2.
 // form: HE_KEY_STREAM_LDG or HE_KEY_STREAM_TMA (TMA needs beta <= 4 in every group).
 int k_ipmac(const he_ctx *ctx, const fgrp *grps_dev, int n_grp, int V, int max_beta, double bytes,
-            double mulmods, int form, cudaStream_t s);   // acc only: the base folds in (see kernels.cu)
+            double mulmods, int form, int gb, cudaStream_t s);       // gb: groups per batch (0: all)   // acc only: the base folds in (see kernels.cu)
 // Split form of a fused stage (same bits): (1) the raised inner product of every (source,
 // amount), with [P]_q phi_a(c0) folded into its first polynomial (and [P]_q (c0, c1) for
 // amount 0), is written to HBM once (amount-major: each key read once per launch); then

@@ -671,14 +671,20 @@ __device__ __forceinline__ ulonglong2 ld2_hint(const u64 *p, u64 pol) {
     return r;
 }
 
-// Block -> (group, coefficient tile, limb).  blockIdx.x = tile * n_grp + group, so the groups
-// that read the same key / plaintext words run side by side; blockIdx.y is the global prime
-// index.  Returns false for a q-prime above the group's level (nothing to do there).  t is the
-// limb's index in the group's Q_l u P layout, ptl its index in the plaintexts' layout.
-__device__ __forceinline__ bool grp_pos(const KP &kp, const fgrp *grps, int n_grp, fgrp &P, int &tile, int &t,
-                                        int &ptl) {
-    const int g = blockIdx.x % n_grp;
-    tile = blockIdx.x / n_grp;
+// Block -> (group, coefficient tile, limb).  Groups go in batches of gb: blockIdx.x walks the
+// batch's groups fastest, then the coefficient tiles, then the batches, so the groups sharing a
+// (tile, prime) run side by side (each key and plaintext word comes from DRAM once per batch)
+// while a batch's raised digits stay in L2 across all tiles (gb = n_grp: every group side by
+// side; a smaller gb keeps the gathered working set small).  blockIdx.y is the global prime.
+// Returns false for a q-prime above the group's level or a padding block past the last group.
+// t is the limb's index in the group's Q_l u P layout, ptl its index in the plaintexts' layout.
+__device__ __forceinline__ bool grp_pos(const KP &kp, const fgrp *grps, int n_grp, int gb, fgrp &P, int &tile,
+                                        int &t, int &ptl) {
+    const int n_tiles = kp.n / 512;
+    const int g_in = blockIdx.x % gb, rest = blockIdx.x / gb;
+    tile = rest % n_tiles;
+    const int g = (rest / n_tiles) * gb + g_in;
+    if (g >= n_grp) return false;
     P = grps[g];
     const int kl = blockIdx.y;
     if (kl <= kp.L) {
@@ -701,10 +707,10 @@ __device__ __forceinline__ bool grp_pos(const KP &kp, const fgrp *grps, int n_gr
 // mod every p), so the outputs need no separate base sums and the ModDown adds nothing else.
 template <int V, int B>
 __global__ void __launch_bounds__(TB, (V == 1 && B == 4) ? 2 : 1) ipmac_kernel(KP kp, const fgrp *grps, int n_grp,
-                                                                               const u64 *pmod) {
+                                                                               int gb, const u64 *pmod) {
     fgrp P;
     int tile, t, ptl;
-    if (!grp_pos(kp, grps, n_grp, P, tile, t, ptl)) return;
+    if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl)) return;
     const int k = 2 * (tile * TB + threadIdx.x);
     const int kl = blockIdx.y;
     const int nq = P.level + 1;
@@ -848,13 +854,13 @@ __device__ __forceinline__ void tma_load(unsigned dst, const void *src, unsigned
 }
 
 template <int V>
-__global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, int n_grp, int *err,
+__global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, int n_grp, int gb, int *err,
                                                        const u64 *pmod) {
     constexpr int NS = TMA_STAGES;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     fgrp P;
     int tile, t, ptl;
-    if (!grp_pos(kp, grps, n_grp, P, tile, t, ptl)) return;   // block-uniform
+    if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl)) return;   // block-uniform
     const int beta = P.beta, n_amt = P.n_amt;
     const famt *amts = P.amts;
     const fent *ents = P.ents;
@@ -990,6 +996,159 @@ __global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, 
         for (int u = used - 1; u < issued; u++) mbar_wait_bounded(smem_u32(&bars[u % NS]), (u / NS) & 1);
         return;
     }
+#pragma unroll
+    for (int v = 0; v < V; v++)
+        if (v < P.nv) {
+            st2(P.acc + ((size_t)(2 * v) * ext) * kp.n + off, redc(a0[v][0], q, qi), redc(a0[v][1], q, qi));
+            st2(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
+        }
+}
+
+// ---- cp.async form: every word an (amount, entry) item needs (its amount's key words at the
+// amount's first entry, the gathered digit pairs, plaintext pairs, c0 and c1) is copied by the
+// thread itself, 16 bytes at a time, into its own shared-memory slots, CP_STAGES - 1 items ahead
+// of the one it computes: no block barrier, no register holds a word in flight.
+constexpr int CP_STAGES = 3;
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, u64 pol) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int V>
+__global__ void __launch_bounds__(TB) ipmac_cp_kernel(KP kp, const fgrp *grps, int n_grp, int gb, const u64 *pmod) {
+    constexpr int RS = CP_STAGES, B = 4;
+    constexpr int NW = 2 * B + B + V + 2;            // 16-byte words per item: keys, D, pt, c0, c1
+    extern __shared__ ulonglong2 csm[];              // [RS][NW][TB]
+    fgrp P;
+    int tile, t, ptl;
+    if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl)) return;
+    const int k = 2 * (tile * TB + threadIdx.x);
+    const int kl = blockIdx.y;
+    const int nq = P.level + 1;
+    const int ext = nq + kp.K;
+    const int beta = P.beta;
+    const bool isq = t < nq;
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 one = to_mont(1, q, qi, r2);
+    const u64 Pm = isq ? to_mont(pmod[kl], q, qi, r2) : 0;
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    const size_t off = (size_t)t * kp.n + k, ptoff = (size_t)ptl * kp.n + k;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    const unsigned sbase = smem_u32(csm);
+    auto slot = [&](int st, int w) -> int { return (st * NW + w) * TB + threadIdx.x; };
+    // items are (amount, entry) pairs in order; item e belongs to amount am[e]
+    const int n_amt = P.n_amt;
+    const int n_item = n_amt > 0 ? P.amts[n_amt - 1].e1 : 0;
+    // producer state: the item to issue next and its amount
+    int pi = 0, pa = 0;
+    auto issue = [&](int st) {
+        while (pa < n_amt && pi >= P.amts[pa].e1) pa++;
+        const famt A = P.amts[pa];
+        const fent E = P.ents[pi];
+        const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
+        const int kb = ks & ~1;
+        if (A.key) {
+            if (pi == A.e0) {
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+                        cp_async16(sbase + 16u * slot(st, 2 * j), kp0, stream);
+                        cp_async16(sbase + 16u * slot(st, 2 * j + 1), kp0 + kstride, stream);
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < B; j++)
+                if (j < beta) cp_async16(sbase + 16u * slot(st, 2 * B + j), E.D + ((size_t)j * ext + t) * kp.n + kb, keep);
+        }
+#pragma unroll
+        for (int v = 0; v < V; v++)
+            if (E.pt[v] && E.pt[v] != HE_PT_ONE) cp_async16(sbase + 16u * slot(st, 3 * B + v), E.pt[v] + ptoff, stream);
+        if (isq) {
+            cp_async16(sbase + 16u * slot(st, 3 * B + V), E.src + (size_t)t * kp.n + kb, keep);
+            if (!A.key) cp_async16(sbase + 16u * slot(st, 3 * B + V + 1), E.src + E.ps + off, keep);
+        }
+        pi++;
+    };
+    u128 a0[V][2], a1[V][2];
+#pragma unroll
+    for (int v = 0; v < V; v++)
+#pragma unroll
+        for (int e = 0; e < 2; e++) a0[v][e] = a1[v][e] = 0;
+#pragma unroll
+    for (int i = 0; i < RS - 1; i++) {
+        if (pi < n_item) issue(i);
+        cp_commit();
+    }
+    ulonglong2 kk0[B], kk1[B];
+    int e = 0;
+    for (int i = 0; i < n_amt; i++) {
+        const famt A = P.amts[i];
+        const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
+        const int sw = ks & 1;
+        for (; e < A.e1; e++) {
+            if (pi < n_item) issue((e + RS - 1) % RS);
+            cp_commit();
+            cp_wait<RS - 1>();
+            const int st = e % RS;
+            const fent E = P.ents[e];
+            if (A.key && e == A.e0) {
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        kk0[j] = csm[slot(st, 2 * j)];
+                        kk1[j] = csm[slot(st, 2 * j + 1)];
+                    }
+            }
+            ulonglong2 p[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const u64 *pp = E.pt[v];
+                p[v] = pp == HE_PT_ONE ? make_ulonglong2(one, one) : (pp ? csm[slot(st, 3 * B + v)] : make_ulonglong2(0, 0));
+            }
+            u64 u00 = 0, u01 = 0, u10 = 0, u11 = 0;
+            if (A.key) {
+                u128 s0[2] = {0, 0}, s1[2] = {0, 0};
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        const ulonglong2 d = csm[slot(st, 2 * B + j)];
+                        const u64 d0 = sw ? d.y : d.x, d1 = sw ? d.x : d.y;
+                        s0[0] += (u128)d0 * kk0[j].x;
+                        s0[1] += (u128)d1 * kk0[j].y;
+                        s1[0] += (u128)d0 * kk1[j].x;
+                        s1[1] += (u128)d1 * kk1[j].y;
+                    }
+                u00 = redc(s0[0], q, qi);
+                u01 = redc(s0[1], q, qi);
+                u10 = redc(s1[0], q, qi);
+                u11 = redc(s1[1], q, qi);
+            }
+            if (isq) {                               // fold [P]_q phi(c0) (and [P]_q c1 at amount 0)
+                const ulonglong2 cc = csm[slot(st, 3 * B + V)];
+                const u64 c00 = sw ? cc.y : cc.x, c01 = sw ? cc.x : cc.y;
+                u00 = add_mod(u00, mul_mont(c00, Pm, q, qi), q);
+                u01 = add_mod(u01, mul_mont(c01, Pm, q, qi), q);
+                if (!A.key) {
+                    const ulonglong2 c1 = csm[slot(st, 3 * B + V + 1)];
+                    u10 = mul_mont(c1.x, Pm, q, qi);
+                    u11 = mul_mont(c1.y, Pm, q, qi);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                a0[v][0] += (u128)p[v].x * u00;
+                a0[v][1] += (u128)p[v].y * u01;
+                a1[v][0] += (u128)p[v].x * u10;
+                a1[v][1] += (u128)p[v].y * u11;
+            }
+        }
+    }
+    cp_wait<0>();
 #pragma unroll
     for (int v = 0; v < V; v++)
         if (v < P.nv) {
@@ -1381,8 +1540,10 @@ int k_tensor(const he_ctx *ctx, const he_ct *a, const he_ct *b, u64 *d, cudaStre
 }
 
 int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta, double bytes, double mulmods,
-            int form, cudaStream_t s) {
+            int form, int gb, cudaStream_t s) {
     if (n_grp <= 0) return HE_OK;
+    if (gb <= 0 || gb > n_grp) gb = n_grp;
+    const unsigned gx = (unsigned)((n_grp + gb - 1) / gb) * gb * (ctx->n / 512);
     if (max_beta > 8) { he_set_error("fused key switching: at most 8 digits"); return HE_EINVAL; }
     if (V != 1 && V != 2) { he_set_error("k_ipmac: V must be 1 or 2"); return HE_EINVAL; }
     const int primes = ctx->L + 1 + ctx->K;
@@ -1397,16 +1558,31 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
             cudaFuncSetAttribute(ipmac_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max) ==
                 cudaSuccess;
         if (!attr_ok) { he_set_error("fused kernel: shared-memory opt-in failed"); return HE_ECUDA; }
-        dim3 gt((unsigned)(ctx->n / TMA_TILE) * n_grp, primes);
+        dim3 gt(gx, primes);
         if (V == 1)
-            ipmac_tma_kernel<1><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, ctx->d_err, ctx->d_consts);
+            ipmac_tma_kernel<1><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
         else
-            ipmac_tma_kernel<2><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, ctx->d_err, ctx->d_consts);
+            ipmac_tma_kernel<2><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
         LAUNCH_CHECK();
         return HE_OK;
     }
-    dim3 g((unsigned)(ctx->n / (2 * TB)) * n_grp, primes);
-#define IPM(VV, BB) ipmac_kernel<VV, BB><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp, ctx->d_consts)
+    if (form == HE_KEY_STREAM_CP && max_beta <= 4) {
+        const size_t smem1 = (size_t)CP_STAGES * (2 * 4 + 4 + 1 + 2) * TB * 16;
+        const size_t smem2 = (size_t)CP_STAGES * (2 * 4 + 4 + 2 + 2) * TB * 16;
+        static const bool attr_ok =
+            cudaFuncSetAttribute(ipmac_cp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(ipmac_cp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2) ==
+                cudaSuccess;
+        if (!attr_ok) { he_set_error("fused kernel: shared-memory opt-in failed"); return HE_ECUDA; }
+        dim3 gc(gx, primes);
+        if (V == 1) ipmac_cp_kernel<1><<<gc, TB, smem1, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else ipmac_cp_kernel<2><<<gc, TB, smem2, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        LAUNCH_CHECK();
+        return HE_OK;
+    }
+    dim3 g(gx, primes);
+#define IPM(VV, BB) ipmac_kernel<VV, BB><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts)
     if (V == 1) { if (max_beta <= 4) IPM(1, 4); else IPM(1, 8); }
     else { if (max_beta <= 4) IPM(2, 4); else IPM(2, 8); }
 #undef IPM

@@ -641,11 +641,16 @@ struct FusedStage {
 // launch (one warm-up pass, then the best of two timed passes, CUDA events on the launch's
 // stream) and keeps the fastest.  Needs the raised digits in place: called after the hoisted
 // ModUps of the first run.
+static const char *form_name(int fm) {
+    return fm == HE_KEY_STREAM_TMA ? "tma" : fm == HE_KEY_STREAM_CP ? "cp" : "ldg";
+}
+
 struct FusedLaunch {
     he_ctx *c = nullptr;
     std::vector<FusedStage *> st;
     fgrp *d_grps = nullptr;
     int G = 0, V = 0, max_beta = 0;
+    int gb = 0;                                       // groups per batch of the block schedule (0: all)
     int form = HE_KEY_STREAM_LDG;
     bool tuned = false;
     bool use_split = false;                           // split form chosen by the autotuner
@@ -739,7 +744,7 @@ struct FusedLaunch {
         return HE_OK;
     }
 
-    int launch(int fm, cudaStream_t s) { return k_ipmac(c, d_grps, G, V, max_beta, bytes, mulmods, fm, s); }
+    int launch(int fm, cudaStream_t s) { return k_ipmac(c, d_grps, G, V, max_beta, bytes, mulmods, fm, gb, s); }
     int launch_split(cudaStream_t s) {
         int mb = 0;
         for (auto *f : st) mb = std::max(mb, f->beta());
@@ -754,6 +759,7 @@ struct FusedLaunch {
     int tune(cudaStream_t s) {
         std::vector<int> forms = {HE_KEY_STREAM_LDG};
         if (max_beta <= 4 && c->d_err) forms.push_back(HE_KEY_STREAM_TMA);
+        if (max_beta <= 4) forms.push_back(HE_KEY_STREAM_CP);
         std::vector<int> Vs = {vmax()};
         if (vmax() == 2) Vs.push_back(1);
         bool try_split = false;
@@ -775,7 +781,7 @@ struct FusedLaunch {
         float best = 1e30f;
         int bestV = Vs[0], bestF = forms[0];
         bool bestSplit = false;
-        char line[640];
+        char line[1024];
         int pos = snprintf(line, sizeof(line), "%s (%zu stage(s), level %d, %zu outputs):", name.c_str(), st.size(),
                            st.empty() ? 0 : st[0]->level, st.empty() ? (size_t)0 : st[0]->outs.size());
         int rc = HE_OK;
@@ -803,11 +809,27 @@ struct FusedLaunch {
                 float t;
                 if ((rc = time_it([&]() { return launch(fm, s); }, t)) != HE_OK) break;
                 if (pos < (int)sizeof(line))
-                    pos += snprintf(line + pos, sizeof(line) - pos, " V=%d %s %.3f ms;", Vc,
-                                    fm == HE_KEY_STREAM_TMA ? "tma" : "ldg", t);
+                    pos += snprintf(line + pos, sizeof(line) - pos, " V=%d %s %.3f ms;", Vc, form_name(fm), t);
                 if (t < best) { best = t; bestV = Vc; bestF = fm; bestSplit = false; }
             }
             if (rc != HE_OK) break;
+        }
+        // shard schedule: batches of groups small enough for their gathered digits to stay in L2
+        int bestGb = 0;
+        if (rc == HE_OK) rc = build(bestV);
+        if (rc == HE_OK && G > 8) {
+            for (int gbc : {16, 4}) {
+                if (gbc >= G) continue;
+                float t;
+                gb = gbc;
+                rc = time_it([&]() { return launch(bestF, s); }, t);
+                gb = 0;
+                if (rc != HE_OK) break;
+                if (pos < (int)sizeof(line))
+                    pos += snprintf(line + pos, sizeof(line) - pos, " V=%d %s gb=%d %.3f ms;", bestV,
+                                    form_name(bestF), gbc, t);
+                if (t < best) { best = t; bestGb = gbc; }
+            }
         }
         if (rc == HE_OK && try_split) {
             float t;
@@ -829,6 +851,7 @@ struct FusedLaunch {
         } else {
             HE_TRY(build(bestV));
             form = bestF;
+            gb = bestGb;
             if (split_built) {                        // give the split form's memory back
                 free_split_tables();
                 for (auto *f : st) f->free_split();
@@ -837,7 +860,8 @@ struct FusedLaunch {
         tuned = true;
         if (pos < (int)sizeof(line)) {
             if (bestSplit) snprintf(line + pos, sizeof(line) - pos, " -> split");
-            else snprintf(line + pos, sizeof(line) - pos, " -> V=%d %s", bestV, bestF == HE_KEY_STREAM_TMA ? "tma" : "ldg");
+            else snprintf(line + pos, sizeof(line) - pos, " -> V=%d %s gb=%d", bestV, form_name(bestF),
+                          bestGb ? bestGb : G);
         }
         he_tune_note(c, line);
         return HE_OK;

@@ -92,7 +92,7 @@ def _conv_case(pair, c, co, m, k, pad, level, seed, bias=True):
     # one ModDown per output shard: equals the oracle's raised-basis restatement
     # (both ways of streaming key words into the fused kernel give these bits)
     ref_raised = Ly.conv_he_raised(o, plan, cts, pts, bias_pts)
-    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_SPLIT):
+    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_SPLIT):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
         H.he_conv_run(g.h, conv, ins, outs, H.HE_FUSED)
@@ -158,7 +158,7 @@ def test_pool_bit_exact(mid, c, m):
             assert_ct_equal(g.download(oc), rc)
     # every stage with one ModDown per output shard: equals the oracle's raised-basis pool
     ref_r = Ly.pool_he_raised(o, plan, cts, list(hm), list(vm))
-    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_SPLIT):
+    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_SPLIT):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 2) for _ in range(len(ref_r))]
         H.he_pool_run(g.h, pool, ins, outs, H.HE_FUSED)
@@ -252,7 +252,7 @@ def test_cifar_layer_full_ring():
             assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
         assert np.array_equal(outs[0], outs[1])
         # the TMA key-tile pipeline and the split form reproduce the fused output at full size
-        for ks in (H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_SPLIT):
+        for ks in (H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_SPLIT):
             H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
             ot = g.ct(level - 1)
             H.he_conv_run(g.h, conv, [ct], [ot], H.HE_FUSED)
@@ -305,7 +305,7 @@ def test_factored_conv_bit_exact(mid, c, co, m, k, pad):
     ins = [g.upload(ct) for ct in cts]
     runs = [(H.HE_PLAIN, H.HE_KEY_STREAM_AUTO, ref_p), (H.HE_BATCHED, H.HE_KEY_STREAM_AUTO, ref_p),
             (H.HE_FUSED, H.HE_KEY_STREAM_LDG, ref_r), (H.HE_FUSED, H.HE_KEY_STREAM_TMA, ref_r),
-            (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT, ref_r)]
+            (H.HE_FUSED, H.HE_KEY_STREAM_CP, ref_r), (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT, ref_r)]
     for mode, ks, ref in runs:
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 2) for _ in range(plan.lout.n_shards)]
@@ -370,7 +370,8 @@ def test_poly_eval_many_equals_oracle_per_ciphertext(mid):
         assert_ct_equal(g.download(gc), ref)
 
 
-@pytest.mark.parametrize("c,co,m,k,pad,level", [(4, 4, 16, 1, 0, 3),     # 1x1: no rotation at all
+@pytest.mark.parametrize("c,co,m,k,pad,level", [(1, 1, 16, 1, 0, 3),     # 1x1, one channel: no rotation
+                                                 (4, 4, 16, 1, 0, 3),     # 1x1 across channels
                                                  (2, 2, 32, 3, 1, 1)])    # lowest level a conv takes
 def test_conv_edge_cases_bit_exact(mid, c, co, m, k, pad, level):
     from paper_2306_09189_gb300 import hegpu as H
@@ -381,7 +382,7 @@ def test_conv_edge_cases_bit_exact(mid, c, co, m, k, pad, level):
     W = rng.uniform(-1, 1, (co, c, k, k))
     lin = Ly.image_layout(c, m, o.N)
     plan = Ly.conv_plan(lin, W, None, pad)
-    if k == 1:
+    if k == 1 and c == 1:
         assert plan.n_rotations() == 0
     pts = Ly.conv_plaintexts(plan, o.n, float(o.q[level]))
     cts = [o.encrypt(s, level, nonce=990 + u) for u, s in enumerate(Ly.pack(lin, x))]
@@ -397,7 +398,7 @@ def test_conv_edge_cases_bit_exact(mid, c, co, m, k, pad, level):
     ins = [g.upload(ct) for ct in cts]
     for mode, ks in ((H.HE_PLAIN, H.HE_KEY_STREAM_AUTO), (H.HE_BATCHED, H.HE_KEY_STREAM_AUTO),
                      (H.HE_FUSED, H.HE_KEY_STREAM_LDG), (H.HE_FUSED, H.HE_KEY_STREAM_TMA),
-                     (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT)):
+                     (H.HE_FUSED, H.HE_KEY_STREAM_CP), (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT)):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
         H.he_conv_run(g.h, conv, ins, outs, mode)
