@@ -123,6 +123,8 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  *   HE_KEY_STREAM_TMA (1): cp.async.bulk copies into a double-buffered shared-memory tile,
  *     signalled by mbarriers with bounded waits (a wait that gives up is reported by
  *     he_ctx_check as HE_ETIMEOUT).  Used for up to 4 digits; otherwise the LDG form runs;
+ *   HE_KEY_STREAM_LDG1 (5): vector loads with one coefficient per thread: fewer registers per
+ *     thread, three blocks per SM;
  *   HE_KEY_STREAM_CP (4): every word of an (amount, source) item (key words, gathered digits,
  *     plaintexts, source words) copied by each thread with cp.async into its own shared-memory
  *     slots, two items ahead of the one it computes (no block barrier).  Up to 4 digits;
@@ -140,6 +142,7 @@ int he_ctx_check(he_ctx *ctx, void *stream);
 #define HE_KEY_STREAM_AUTO 2
 #define HE_KEY_STREAM_SPLIT 3
 #define HE_KEY_STREAM_CP 4
+#define HE_KEY_STREAM_LDG1 5
 int he_ctx_set_option(he_ctx *ctx, int option, int value);
 int he_ctx_get_option(const he_ctx *ctx, int option, int *value);
 /* The autotuner's decisions so far (one line per tuned stage: the candidates' times and the

@@ -664,6 +664,12 @@ __device__ __forceinline__ u64 policy_evict_last() {
     asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
+__device__ __forceinline__ u64 ld_hint(const u64 *p, u64 pol) {
+    u64 r;
+    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
+    return r;
+}
+
 __device__ __forceinline__ ulonglong2 ld2_hint(const u64 *p, u64 pol) {
     ulonglong2 r;
     asm volatile("ld.global.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
@@ -679,8 +685,8 @@ __device__ __forceinline__ ulonglong2 ld2_hint(const u64 *p, u64 pol) {
 // Returns false for a q-prime above the group's level or a padding block past the last group.
 // t is the limb's index in the group's Q_l u P layout, ptl its index in the plaintexts' layout.
 __device__ __forceinline__ bool grp_pos(const KP &kp, const fgrp *grps, int n_grp, int gb, fgrp &P, int &tile,
-                                        int &t, int &ptl) {
-    const int n_tiles = kp.n / 512;
+                                        int &t, int &ptl, int tile_coeffs = 512) {
+    const int n_tiles = kp.n / tile_coeffs;
     const int g_in = blockIdx.x % gb, rest = blockIdx.x / gb;
     tile = rest % n_tiles;
     const int g = (rest / n_tiles) * gb + g_in;
@@ -1156,6 +1162,97 @@ __global__ void __launch_bounds__(TB) ipmac_cp_kernel(KP kp, const fgrp *grps, i
             st2(P.acc + ((size_t)(2 * v + 1) * ext) * kp.n + off, redc(a1[v][0], q, qi), redc(a1[v][1], q, qi));
         }
 }
+
+// ---- one-coefficient form: each thread handles one coefficient (8-byte loads), so a thread
+// holds half the key, digit and accumulator words of the pair form and three blocks fit on an
+// SM (24 warps to cover the key stream's latency).  Same arithmetic, same bits.
+template <int V, int B>
+__global__ void __launch_bounds__(TB, 3) ipmac1_kernel(KP kp, const fgrp *grps, int n_grp, int gb, const u64 *pmod) {
+    fgrp P;
+    int tile, t, ptl;
+    if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl, TB)) return;
+    const int k = tile * TB + threadIdx.x;
+    const int kl = blockIdx.y;
+    const int nq = P.level + 1;
+    const int ext = nq + kp.K;
+    const int beta = P.beta;
+    const bool isq = t < nq;
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 one = to_mont(1, q, qi, r2);
+    const u64 Pm = isq ? to_mont(pmod[kl], q, qi, r2) : 0;
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    const size_t off = (size_t)t * kp.n + k, ptoff = (size_t)ptl * kp.n + k;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    u128 a0[V], a1[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) a0[v] = a1[v] = 0;
+    const int n_amt = P.n_amt;
+    famt A = n_amt > 0 ? P.amts[0] : famt{};
+    fent E = (n_amt > 0 && A.e0 < A.e1) ? P.ents[A.e0] : fent{};
+    for (int i = 0; i < n_amt; i++) {
+        famt An{};
+        fent En{};
+        if (i + 1 < n_amt) {
+            An = P.amts[i + 1];
+            if (An.e0 < An.e1) En = P.ents[An.e0];
+        }
+        const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
+        u64 k0[B], k1[B];
+        if (A.key) {
+#pragma unroll
+            for (int j = 0; j < B; j++)
+                if (j < beta) {
+                    const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+                    k0[j] = ld_hint(kp0, stream);
+                    k1[j] = ld_hint(kp0 + kstride, stream);
+                }
+        }
+        for (int e = A.e0; e < A.e1; e++) {
+            if (e > A.e0) E = P.ents[e];
+            u64 p[V];
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                const u64 *pp = E.pt[v];
+                p[v] = pp == HE_PT_ONE ? one : (pp ? ld_hint(pp + ptoff, stream) : 0);
+            }
+            u64 c0 = 0, c1 = 0;
+            if (isq) {
+                c0 = ld_hint(E.src + (size_t)t * kp.n + ks, keep);
+                if (!A.key) c1 = ld_hint(E.src + E.ps + off, keep);
+            }
+            u64 u0 = 0, u1 = 0;
+            if (A.key) {
+                u128 s0 = 0, s1 = 0;
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        const u64 d = ld_hint(E.D + ((size_t)j * ext + t) * kp.n + ks, keep);
+                        s0 += (u128)d * k0[j];
+                        s1 += (u128)d * k1[j];
+                    }
+                u0 = redc(s0, q, qi);
+                u1 = redc(s1, q, qi);
+            }
+            if (isq) {                               // fold [P]_q phi(c0) (and [P]_q c1 at amount 0)
+                u0 = add_mod(u0, mul_mont(c0, Pm, q, qi), q);
+                if (!A.key) u1 = mul_mont(c1, Pm, q, qi);
+            }
+#pragma unroll
+            for (int v = 0; v < V; v++) {
+                a0[v] += (u128)p[v] * u0;
+                a1[v] += (u128)p[v] * u1;
+            }
+        }
+        A = An;
+        E = En;
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++)
+        if (v < P.nv) {
+            P.acc[((size_t)(2 * v) * ext) * kp.n + off] = redc(a0[v], q, qi);
+            P.acc[((size_t)(2 * v + 1) * ext) * kp.n + off] = redc(a1[v], q, qi);
+        }
+}
 // ==== fused key-switch + MAC kernels: end
 
 // acc = sum_terms K_term * x_term (+ c on poly 0) over limbs 0..level, x of any higher level
@@ -1566,6 +1663,15 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
         LAUNCH_CHECK();
         return HE_OK;
     }
+    if (form == HE_KEY_STREAM_LDG1) {
+        dim3 g1((unsigned)((n_grp + gb - 1) / gb) * gb * (ctx->n / TB), primes);
+#define IPM1(VV, BB) ipmac1_kernel<VV, BB><<<g1, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts)
+        if (V == 1) { if (max_beta <= 4) IPM1(1, 4); else IPM1(1, 8); }
+        else { if (max_beta <= 4) IPM1(2, 4); else IPM1(2, 8); }
+#undef IPM1
+        LAUNCH_CHECK();
+        return HE_OK;
+    }
     if (form == HE_KEY_STREAM_CP && max_beta <= 4) {
         const size_t smem1 = (size_t)CP_STAGES * (2 * 4 + 4 + 1 + 2) * TB * 16;
         const size_t smem2 = (size_t)CP_STAGES * (2 * 4 + 4 + 2 + 2) * TB * 16;
@@ -1601,12 +1707,6 @@ __device__ __forceinline__ bool lvl_pos(const KP &kp, int level, int &t) {
         t = level + 1 + (kl - kp.L - 1);
     }
     return true;
-}
-
-__device__ __forceinline__ u64 ld_hint(const u64 *p, u64 pol) {
-    u64 r;
-    asm volatile("ld.global.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(r) : "l"(p), "l"(pol));
-    return r;
 }
 
 __device__ __forceinline__ void cp_async8(unsigned dst, const void *src, u64 pol) {
@@ -1813,9 +1913,10 @@ int k_rmac(const he_ctx *ctx, const rgrp *grps, int n_grp, double bytes, double 
 constexpr int SM_OB = 16;
 
 __global__ void __launch_bounds__(TB) smac_kernel(KP kp, const u64 *Y, size_t ystride, size_t yps, const u64 *Wm,
-                                                  int co, int nin, int H, int T, u64 *out, size_t ostride,
+                                                  int co, int ci, int H, int T, u64 *out, size_t ostride,
                                                   size_t ops) {
     extern __shared__ u64 wsm[];                                   // [SM_OB][nin]
+    const int nin = ci * T;
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y >> 1, c = blockIdx.y & 1;             // limb, polynomial
     const int h = blockIdx.z % H, o0 = (blockIdx.z / H) * SM_OB;
@@ -1830,12 +1931,22 @@ __global__ void __launch_bounds__(TB) smac_kernel(KP kp, const u64 *Y, size_t ys
 #pragma unroll
     for (int ob = 0; ob < SM_OB; ob++) acc[ob] = 0;
     const u64 stream = policy_evict_first();
-    for (int kk = 0; kk < nin; kk++) {
-        const int f = kk / T, t = kk % T;
-        const u64 y = ld_hint(Y + ((size_t)(f * H + h) * T + t) * ystride + c * yps + (size_t)i * kp.n + k, stream);
+    constexpr int U = 4;                                           // inputs in flight per thread
+    for (int f = 0; f < ci; f++) {
+        const u64 *yb = Y + (size_t)(f * H + h) * T * ystride + c * yps + (size_t)i * kp.n + k;
+        const u64 *wf = wsm + f * T;
+        for (int t = 0; t < T; t += U) {
+            u64 y[U];
 #pragma unroll
-        for (int ob = 0; ob < SM_OB; ob++)
-            if (ob < nob) acc[ob] += (u128)y * wsm[ob * nin + kk];
+            for (int u = 0; u < U; u++) y[u] = t + u < T ? ld_hint(yb + (size_t)(t + u) * ystride, stream) : 0;
+#pragma unroll
+            for (int u = 0; u < U; u++)
+                if (t + u < T) {
+#pragma unroll
+                    for (int ob = 0; ob < SM_OB; ob++)
+                        if (ob < nob) acc[ob] += (u128)y[u] * wf[ob * nin + t + u];
+                }
+        }
     }
 #pragma unroll
     for (int ob = 0; ob < SM_OB; ob++)
@@ -1857,7 +1968,7 @@ int k_smac(const he_ctx *ctx, const u64 *Y, size_t ystride, size_t yps, const u6
                                  (double)co * H * 2 * nl * ctx->n * 8,
                   (double)co * H * ci * T * 2 * nl * ctx->n);
     dim3 g(ctx->n / TB, 2 * (level + 1), H * ((co + SM_OB - 1) / SM_OB));
-    smac_kernel<<<g, TB, smem, s>>>(ctx->kp, Y, ystride, yps, Wm, co, nin, H, T, out, ostride, ops);
+    smac_kernel<<<g, TB, smem, s>>>(ctx->kp, Y, ystride, yps, Wm, co, ci, H, T, out, ostride, ops);
     LAUNCH_CHECK();
     return HE_OK;
 }

@@ -642,7 +642,7 @@ struct FusedStage {
 // stream) and keeps the fastest.  Needs the raised digits in place: called after the hoisted
 // ModUps of the first run.
 static const char *form_name(int fm) {
-    return fm == HE_KEY_STREAM_TMA ? "tma" : fm == HE_KEY_STREAM_CP ? "cp" : "ldg";
+    return fm == HE_KEY_STREAM_TMA ? "tma" : fm == HE_KEY_STREAM_CP ? "cp" : fm == HE_KEY_STREAM_LDG1 ? "ldg1" : "ldg";
 }
 
 struct FusedLaunch {
@@ -760,6 +760,7 @@ struct FusedLaunch {
         std::vector<int> forms = {HE_KEY_STREAM_LDG};
         if (max_beta <= 4 && c->d_err) forms.push_back(HE_KEY_STREAM_TMA);
         if (max_beta <= 4) forms.push_back(HE_KEY_STREAM_CP);
+        forms.push_back(HE_KEY_STREAM_LDG1);
         std::vector<int> Vs = {vmax()};
         if (vmax() == 2) Vs.push_back(1);
         bool try_split = false;

@@ -92,7 +92,8 @@ def _conv_case(pair, c, co, m, k, pad, level, seed, bias=True):
     # one ModDown per output shard: equals the oracle's raised-basis restatement
     # (both ways of streaming key words into the fused kernel give these bits)
     ref_raised = Ly.conv_he_raised(o, plan, cts, pts, bias_pts)
-    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_SPLIT):
+    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_LDG1,
+               H.HE_KEY_STREAM_SPLIT):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
         H.he_conv_run(g.h, conv, ins, outs, H.HE_FUSED)
@@ -158,7 +159,8 @@ def test_pool_bit_exact(mid, c, m):
             assert_ct_equal(g.download(oc), rc)
     # every stage with one ModDown per output shard: equals the oracle's raised-basis pool
     ref_r = Ly.pool_he_raised(o, plan, cts, list(hm), list(vm))
-    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_SPLIT):
+    for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_LDG1,
+               H.HE_KEY_STREAM_SPLIT):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 2) for _ in range(len(ref_r))]
         H.he_pool_run(g.h, pool, ins, outs, H.HE_FUSED)
@@ -252,7 +254,7 @@ def test_cifar_layer_full_ring():
             assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
         assert np.array_equal(outs[0], outs[1])
         # the TMA key-tile pipeline and the split form reproduce the fused output at full size
-        for ks in (H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_SPLIT):
+        for ks in (H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_LDG1, H.HE_KEY_STREAM_SPLIT):
             H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
             ot = g.ct(level - 1)
             H.he_conv_run(g.h, conv, [ct], [ot], H.HE_FUSED)
@@ -305,7 +307,8 @@ def test_factored_conv_bit_exact(mid, c, co, m, k, pad):
     ins = [g.upload(ct) for ct in cts]
     runs = [(H.HE_PLAIN, H.HE_KEY_STREAM_AUTO, ref_p), (H.HE_BATCHED, H.HE_KEY_STREAM_AUTO, ref_p),
             (H.HE_FUSED, H.HE_KEY_STREAM_LDG, ref_r), (H.HE_FUSED, H.HE_KEY_STREAM_TMA, ref_r),
-            (H.HE_FUSED, H.HE_KEY_STREAM_CP, ref_r), (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT, ref_r)]
+            (H.HE_FUSED, H.HE_KEY_STREAM_CP, ref_r), (H.HE_FUSED, H.HE_KEY_STREAM_LDG1, ref_r),
+            (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT, ref_r)]
     for mode, ks, ref in runs:
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 2) for _ in range(plan.lout.n_shards)]
@@ -398,7 +401,8 @@ def test_conv_edge_cases_bit_exact(mid, c, co, m, k, pad, level):
     ins = [g.upload(ct) for ct in cts]
     for mode, ks in ((H.HE_PLAIN, H.HE_KEY_STREAM_AUTO), (H.HE_BATCHED, H.HE_KEY_STREAM_AUTO),
                      (H.HE_FUSED, H.HE_KEY_STREAM_LDG), (H.HE_FUSED, H.HE_KEY_STREAM_TMA),
-                     (H.HE_FUSED, H.HE_KEY_STREAM_CP), (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT)):
+                     (H.HE_FUSED, H.HE_KEY_STREAM_CP), (H.HE_FUSED, H.HE_KEY_STREAM_LDG1),
+                     (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT)):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
         H.he_conv_run(g.h, conv, ins, outs, mode)
