@@ -720,6 +720,140 @@ def cheb_tree_slots(c, t):
     return sum(c[k] * T[k] for k in range(len(c)))
 
 
+def cheb_ps_params(deg):
+    """Paterson-Stockmeyer split for degree deg: baby steps T_1..T_k (k a power of two near
+    sqrt((deg + 1) / 2)) and giant steps T_k, T_2k, T_4k, ... <= deg."""
+    k = 2
+    while k * k < (deg + 1) // 2:
+        k *= 2
+    giants = []
+    g = k
+    while g <= deg:
+        giants.append(g)
+        g *= 2
+    return k, giants
+
+
+def cheb_divide(c, G):
+    """Chebyshev division p = q T_G + r (deg p < 2G): with T_G T_j = (T_{G+j} + T_{|G-j|}) / 2,
+    q_0 = c_G, q_j = 2 c_{G+j} (j >= 1), r_i = c_i - c_{2G-i} for i < G (c beyond deg p is 0)."""
+    d = len(c) - 1
+    q = [c[G]] + [2.0 * c[G + j] for j in range(1, d - G + 1)]
+    r = [c[i] - (c[2 * G - i] if 2 * G - i <= d and i >= 1 else 0.0) for i in range(G)]
+    return q, r
+
+
+def cheb_ps_slots(c, t):
+    """Paterson-Stockmeyer evaluation of sum c_k T_k(t) on cleartext (same recursion as the HE form)."""
+    deg = len(c) - 1
+    k, giants = cheb_ps_params(deg)
+    T = {0: np.ones_like(t), 1: t}
+    for j in range(2, max([k] + giants) + 1):
+        if j <= k or j in giants:
+            h = j // 2
+            T[j] = 2 * T[h] * T[h] - 1 if j % 2 == 0 else 2 * T[h] * T[h + 1] - T[1]
+
+    def ev(cc):
+        d = len(cc) - 1
+        if d < k:
+            return sum(cc[i] * T[i] for i in range(d + 1))
+        G = max(g for g in giants if g <= d)
+        q, r = cheb_divide(cc, G)
+        return ev(q) * T[G] + ev(r)
+    return ev(list(c))
+
+
+def cheb_ps_he(ctx, ct, c, target_scale=None):
+    """Homomorphic Paterson-Stockmeyer evaluation of sum c_k T_k(ct) in the Chebyshev basis.
+
+    Baby steps T_1..T_k and giant steps T_k, T_2k, ... come from the binary-tree recursion
+    (the same products and exact-scale re-targeting as cheb_tree_he).  ev(p, l, s) returns p at
+    level l and scale s (the scale of a product is s' = s_q s_G / q_{l+1}, within rounding of s):
+      * deg p < k (or p = q_0 T_G + r with a constant quotient and deg r < k): one exact-scale
+        linear combination sum round(c_i s q_{l+1} / s_i) T_i at level l + 1, then a rescale; a
+        constant quotient with a larger remainder adds q_0 T_G (one combination) to ev(r, l, s);
+      * otherwise p = q T_G + r: Q = ev(q, l + 1, s q_{l+1} / s_G), then mul_relin(Q, T_G) lands at
+        level l with scale s', and r is evaluated to exactly (l, s') and added.
+    The output level is the highest the recursion allows."""
+    target_scale = ctx.pr.scale if target_scale is None else target_scale
+    deg = len(c) - 1
+    k, giants = cheb_ps_params(deg)
+    T = {1: ct}
+
+    def retarget(x, level, scale_t):
+        y = ctx.drop_to(x, level + 1)
+        K = int(round(scale_t * ctx.q[level + 1] / y.scale))
+        y = ctx.mul_int(y, K)
+        y = ctx.rescale(y)
+        y.scale = scale_t
+        return y
+
+    for j in range(2, max([k] + giants) + 1):
+        if not (j <= k or j in giants):
+            continue
+        h = j // 2
+        if j % 2 == 0:
+            p = ctx.mul_relin(T[h], T[h])
+            p = ctx.mul_int(p, 2)
+            p = ctx.add_const_int(p, -int(round(p.scale)))
+        else:
+            a, b = T[h], T[h + 1]
+            lv = min(a.level, b.level)
+            p = ctx.mul_relin(ctx.drop_to(a, lv), ctx.drop_to(b, lv))
+            p = ctx.mul_int(p, 2)
+            t1 = retarget(T[1], p.level, p.scale)
+            p = ctx.sub_ct(p, t1)
+        T[j] = p
+
+    def lincomb(terms, c0, level, scale):
+        """sum_(coef, T) round(coef scale q_{l+1} / s_T) T + round(c0 scale q_{l+1}), rescaled to (l, scale)."""
+        acc = None
+        for coef, x in terms:
+            y = ctx.drop_to(x, level + 1)
+            K = int(round(coef * scale * ctx.q[level + 1] / y.scale))
+            y = ctx.mul_int(y, K)
+            y.scale = scale * ctx.q[level + 1]
+            acc = y if acc is None else ctx.add_ct(acc, y)
+        acc = ctx.add_const_int(acc, int(round(c0 * scale * ctx.q[level + 1])))
+        out = ctx.rescale(acc)
+        out.scale = scale
+        return out
+
+    def need(cc):
+        """levels consumed below the input level by ev(cc)"""
+        d = len(cc) - 1
+        depth = lambda i: (i - 1).bit_length()
+        if d < k:
+            return 1 + max([depth(i) for i in range(1, d + 1)] + [0])
+        G = max(g for g in giants if g <= d)
+        q, r = cheb_divide(cc, G)
+        if len(q) == 1 and G - 1 < k:
+            return 1 + max([depth(G)] + [depth(i) for i in range(1, G)])
+        if len(q) == 1:
+            return max(1 + depth(G), need(r))
+        return max(need(q) + 1, depth(G) + 1, need(r))
+
+    def ev(cc, level, scale):
+        d = len(cc) - 1
+        if d < k:
+            return lincomb([(cc[i], T[i]) for i in range(1, d + 1)], cc[0], level, scale)
+        G = max(g for g in giants if g <= d)
+        q, r = cheb_divide(cc, G)
+        if len(q) == 1 and G - 1 < k:          # q_0 T_G + r in one combination (r a leaf)
+            return lincomb([(cc_i, T[i]) for i, cc_i in enumerate(r) if i >= 1] + [(q[0], T[G])], r[0],
+                           level, scale)
+        if len(q) == 1:                        # scalar q_0 T_G plus the recursion on r, same (l, s)
+            return ctx.add_ct(ev(r, level, scale), lincomb([(q[0], T[G])], 0.0, level, scale))
+        TG = ctx.drop_to(T[G], level + 1)
+        Q = ev(q, level + 1, scale * ctx.q[level + 1] / TG.scale)
+        prod = ctx.mul_relin(ctx.drop_to(Q, level + 1), TG)
+        return ctx.add_ct(prod, ev(r, level, prod.scale))
+
+    out_level = ct.level - need(list(c))
+    assert out_level >= 0, "not enough levels"
+    return ev(list(c), out_level, target_scale)
+
+
 def cheb_tree_he(ctx, ct, c, target_scale=None):
     """Homomorphic sum c_k T_k(ct) with the binary-tree T_k and exact-scale constants.
 

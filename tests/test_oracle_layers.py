@@ -306,3 +306,58 @@ def test_factored_conv_he_decrypts_to_fp64(raised):
     img = Ly.unpack(plan.lout, np.stack([ctx.decrypt(ct) for ct in out]))
     ref = _conv_ref(x, W, b, pad)
     assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+
+
+@pytest.mark.parametrize("deg", [5, 8, 16, 27, 59])
+def test_paterson_stockmeyer_slots_equal_chebyshev_sum(deg):
+    c = Ly.cheb_nodes_coeffs(Ly.gelu, deg, -8, 8)
+    t = np.linspace(-1, 1, 513)
+    assert np.abs(Ly.cheb_ps_slots(c, t) - Ly.cheb_eval(c, 8 * t, -8, 8)).max() < 1e-12
+
+
+def test_chebyshev_division_identity():
+    # p = q T_G + r exactly (T_G T_j = (T_{G+j} + T_{|G-j|}) / 2), deg r < G
+    rng = np.random.default_rng(3)
+    t = np.linspace(-1, 1, 257)
+    for d, G in ((16, 16), (15, 8), (59, 32), (31, 16), (9, 8)):
+        c = rng.normal(size=d + 1)
+        q, r = Ly.cheb_divide(list(c), G)
+        assert len(r) == G and len(q) == d - G + 1
+        TG = np.cos(G * np.arccos(t))
+        lhs = Ly.cheb_eval(c, t, -1, 1)
+        rhs = Ly.cheb_eval(q, t, -1, 1) * TG + Ly.cheb_eval(r, t, -1, 1)
+        assert np.abs(lhs - rhs).max() < 1e-11
+
+
+@pytest.fixture(scope="module")
+def deep():
+    ctx = Context(Params(log_n=10, n_q=10, n_p=3, dnum=4, q0_bits=50, q_bits=40, p_bits=50,
+                         scale=2.0 ** 40, seed=21))
+    ctx.gen_relin_key()
+    return ctx
+
+
+@pytest.mark.parametrize("deg,depth", [(59, 6), (27, 5), (16, 5)])
+def test_paterson_stockmeyer_he_depth_and_accuracy(deep, deg, depth):
+    """The paper evaluates the degree-59 GELU at depth 6 and degree 27 at depth 5 (Appendix):
+    the Paterson-Stockmeyer recursion reaches exactly those depths, with fewer products than
+    the binary tree, and decrypts to the same polynomial."""
+    ctx = deep
+    c = Ly.cheb_nodes_coeffs(Ly.gelu, deg, -8, 8)
+    z = np.random.default_rng(deg).uniform(-1, 1, ctx.N)
+    ct = ctx.encrypt(z, 9, nonce=deg)
+    count = [0]
+    orig = ctx.mul_relin
+
+    def counted(a, b):
+        count[0] += 1
+        return orig(a, b)
+    ctx.mul_relin = counted
+    try:
+        out = Ly.cheb_ps_he(ctx, ct, c)
+    finally:
+        ctx.mul_relin = orig
+    assert ct.level - out.level == depth
+    assert count[0] < deg - 1
+    ref = Ly.cheb_eval(c, 8 * z, -8, 8)
+    assert np.abs(ctx.decrypt(out) - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
