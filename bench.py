@@ -211,7 +211,8 @@ def run_block(args, ws, rank, local):
     c, m = x0.shape[0], x0.shape[1]
     imgs = [x0] + [workloads.image(c, m, 10 + i) for i in range(len(levels) - 1)]
     top1 = max(levels)
-    top2 = top1 - 1 - (DEG - 1).bit_length() - 1
+    gdepth = host.ps_depth(DEG) if args.poly == "ps" else (DEG - 1).bit_length() + 1
+    top2 = top1 - 1 - gdepth
     t_setup = time.perf_counter()
     lay = H.he_layout_image(c, m, N)
     conv1 = H.he_conv_create(ctx, lay, W1, b1, 1, 1, top1, pr.scale)
@@ -228,14 +229,15 @@ def run_block(args, ws, rank, local):
     y1 = [H.he_ct_alloc(ctx, top1 - 1) for _ in range(len(levels) * ns1)]
     y2 = [H.he_ct_alloc(ctx, top2 - 1) for _ in range(len(levels) * ns2)]
     # GELU output scale chosen so that conv2's output lands on the input's scale (residual)
-    tgt = [pr.scale * float(q[lv - 1 - (DEG - 1).bit_length() - 1]) / float(q[top2]) for lv in levels]
+    tgt = [pr.scale * float(q[lv - 1 - gdepth]) / float(q[top2]) for lv in levels]
     tgt_all = [t for t in tgt for _ in range(lay.n_shards)]
     setup_s = time.perf_counter() - t_setup
 
     def rot_count(conv):
         u, v, a, _ = H.he_conv_export_plan(conv, N)
         return len({(int(uu), int(aa)) for uu, aa in zip(u, a) if int(aa) % N != 0})
-    ks_per_step = len(levels) * (rot_count(conv1) + rot_count(conv2) + ns1 * (DEG - 1))
+    products = host.ps_products(DEG) if args.poly == "ps" else DEG - 1
+    ks_per_step = len(levels) * (rot_count(conv1) + rot_count(conv2) + ns1 * products)
     pt_bytes = sum(H.he_conv_n_terms(cv) * (lv + 1 + info["K"]) * n * 8 for cv, lv in ((conv1, top1), (conv2, top2)))
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()
@@ -243,12 +245,14 @@ def run_block(args, ws, rank, local):
 
     def step(mode):
         H.he_conv_run_batch(ctx, conv1, xs, y1, len(levels), mode, stream)
+        one = H.he_poly_eval_ps if args.poly == "ps" else H.he_poly_eval
+        many = H.he_poly_eval_ps_many if args.poly == "ps" else H.he_poly_eval_many
         if mode == H.HE_PLAIN:                   # the per-ciphertext path
             for i in range(len(levels)):
                 for v in range(ns1):
-                    H.he_poly_eval(ctx, y1[i * ns1 + v], cheb, tgt[i], stream)
-        else:                                    # every ciphertext of a level through the tree together
-            H.he_poly_eval_many(ctx, y1, cheb, tgt_all, stream)
+                    one(ctx, y1[i * ns1 + v], cheb, tgt[i], stream)
+        else:                                    # every ciphertext of a level through the products together
+            many(ctx, y1, cheb, tgt_all, stream)
         H.he_conv_run_batch(ctx, conv2, y1, y2, len(levels), mode, stream)
         for i in range(len(levels)):
             for v in range(ns2):
@@ -416,9 +420,7 @@ def run_stem(args, ws, rank, local):
     for _ in range(args.warmup):
         H.he_graph_launch(graph, stream)
     torch.cuda.synchronize()
-    trace = args.trace
-    if trace == "ipmac" and ("-> split" in H.he_ctx_tuning_log(ctx) or args.key_stream == "split"):
-        trace = "rmac"
+    trace = args.trace                       # the pooling stages' fused launches dominate the stem
     H.he_trace_start(trace)
     H.he_graph_begin(ctx, stream)
     for _ in range(args.steps):
@@ -494,6 +496,8 @@ def main():
                     help="key-switch + MAC form: autotuned (default), the fused kernel with vector "
                          "loads or a TMA tile pipeline, or the split form (inner products, then MAC)")
     ap.add_argument("--no-graph", action="store_true", help="launch the fused step eagerly, not as a CUDA graph")
+    ap.add_argument("--poly", default="ps", choices=["ps", "tree"],
+                    help="GELU evaluation: Paterson-Stockmeyer (default) or the binary tree")
     ap.add_argument("--workload", default="cifar-layer", choices=["cifar-layer", "resnet-block", "imagenet-stem"],
                     help="cifar-layer: the headline layer; resnet-block: the batched mixed-level block; "
                          "imagenet-stem: the channel-shard stem with stride 2 and average pool")
@@ -533,14 +537,17 @@ def main():
     H.he_keygen_rotations(ctx, rots)
     H.he_keygen_relin(ctx)
     y = H.he_ct_alloc(ctx, LEVEL - 1)
-    ks_per_step = len(rots) + (DEG - 1)
+    products = host.ps_products(DEG) if args.poly == "ps" else DEG - 1
+    ks_per_step = len(rots) + products
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()             # a created stream: the default one cannot be captured
     torch.cuda.set_stream(stream)
 
+    poly = H.he_poly_eval_ps if args.poly == "ps" else H.he_poly_eval
+
     def step(mode):
         H.he_conv_run(ctx, conv, [x], [y], mode, stream)
-        H.he_poly_eval(ctx, y, cheb, pr.scale, stream)
+        poly(ctx, y, cheb, pr.scale, stream)
 
     def barrier():
         if ws > 1:
@@ -615,14 +622,14 @@ def main():
     xin = H.he_ct_export_coeffs(ctx, x, n)
     h_in = torch.empty(xin.size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64).reshape(xin.shape)
     h_in[:] = xin
-    out_level = LEVEL - 1 - ((DEG - 1).bit_length() + 1)      # conv, then ceil(log2 DEG) + 1
+    out_level = H.he_ct_level(y)                               # after the conv and the polynomial
     out_shape = (2, out_level + 1, n)
     h_out = torch.empty(int(np.prod(out_shape)), dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
     xe = H.he_ct_alloc(ctx, LEVEL)
 
     def e2e_body():
         H.he_conv_run(ctx, conv, [xe], [y], H.HE_FUSED, stream)
-        H.he_poly_eval(ctx, y, cheb, pr.scale, stream)
+        poly(ctx, y, cheb, pr.scale, stream)
 
     H.he_ct_import_coeffs(xe, h_in, LEVEL, pr.scale, stream)
     e2e_body()
@@ -674,7 +681,8 @@ def main():
                        "key_switches_per_step": ks_per_step, "key_stream": args.key_stream,
                        "cuda_graph": not args.no_graph,
                        "autotuner": H.he_ctx_tuning_log(ctx).strip().splitlines(),
-                       "rotations": int(len(rots)), "relins": DEG - 1, "input_level": LEVEL,
+                       "rotations": int(len(rots)), "relins": products, "input_level": LEVEL,
+                       "gelu": "degree-16 Chebyshev, %s" % ("Paterson-Stockmeyer" if args.poly == "ps" else "binary tree"),
                        "l2": "inputs larger than L2 (rotation keys %.1f GB streamed every step)" % (H.he_key_bytes(ctx) / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single"},
             "plain": {"ms_per_step": ms_p, "value": ws * ks_per_step / (ms_p * 1e-3),

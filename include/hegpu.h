@@ -351,6 +351,16 @@ int he_poly_eval(he_ctx *ctx, he_ct *io, const double *cheb, int deg, double tar
  * ciphertext gets exactly the bits he_poly_eval gives it. */
 int he_poly_eval_many(he_ctx *ctx, he_ct *const *io, int m, const double *cheb, int deg,
                       const double *target_scales, void *stream);
+/* The same polynomial by Paterson-Stockmeyer in the Chebyshev basis: baby steps T_1..T_k and
+ * giant steps T_k, T_2k, ... (the binary-tree recursion), the division p = q T_G + r with
+ * T_G T_j = (T_{G+j} + T_{|G-j|}) / 2, each node evaluated to a given level and scale (leaves as
+ * exact-scale integer combinations).  Far fewer relinearised products than the tree (degree
+ * 59: 16 instead of 58) and the paper's depths (degree 59 at 6, 27 at 5; Appendix).  The
+ * output scale is target_scale up to the rounding of its own bookkeeping (a product node's
+ * scale s_q s_G / q).  deg in 2..255.  Different bits from he_poly_eval, same polynomial. */
+int he_poly_eval_ps(he_ctx *ctx, he_ct *io, const double *cheb, int deg, double target_scale, void *stream);
+int he_poly_eval_ps_many(he_ctx *ctx, he_ct *const *io, int m, const double *cheb, int deg,
+                         const double *target_scales, void *stream);
 
 /* Convenience wrappers: create, run, destroy. */
 int he_hconv2d(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, const double *W,

@@ -288,6 +288,8 @@ void he_tune_note(he_ctx *ctx, const std::string &line);
 int k_smac(const he_ctx *ctx, const u64 *Y, size_t ystride, size_t yps, const u64 *Wm, int co, int ci, int H, int T,
            int level, u64 *out, size_t ostride, size_t ops, cudaStream_t s);
 int k_selftest_bounded_wait(const he_ctx *ctx, cudaStream_t s);
+#define HE_LC_MAX 20        // terms of one k_lincomb launch
+#define HE_LC_LIMBS 24      // limbs of one k_lincomb launch (residue table row length)
 int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u64 *res, int n,
               const u64 *cst, int level, u64 *out, size_t out_ps, cudaStream_t s);
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s);

@@ -1257,8 +1257,6 @@ __global__ void __launch_bounds__(TB, 3) ipmac1_kernel(KP kp, const fgrp *grps, 
 
 // acc = sum_terms K_term * x_term (+ c on poly 0) over limbs 0..level, x of any higher level
 // (the drop is implicit); per-limb residues of the integer constants are passed by value.
-#define HE_LC_MAX 20
-#define HE_LC_LIMBS 24
 struct LincombArgs {
     const u64 *x[HE_LC_MAX];
     size_t ps[HE_LC_MAX];

@@ -2467,6 +2467,278 @@ static int poly_eval_group(he_ctx *c, const std::vector<he_ct *> &io, const doub
     return HE_OK;
 }
 
+// ---------------------------------------------------------------- Paterson-Stockmeyer
+// sum c_j T_j in the Chebyshev basis with baby steps T_1..T_k and giant steps T_k, T_2k, ...
+// (Appendix: the recursion T_{2n} = 2 T_n^2 - 1, T_{2n+1} = 2 T_n T_{n+1} - x builds both), and
+// the division p = q T_G + r (T_G T_j = (T_{G+j} + T_{|G-j|}) / 2); every node is evaluated to a
+// given (level, scale): leaves are exact-scale integer combinations, a product node lands its
+// quotient one level up so that q T_G meets r on the same level and scale.  The operations and
+// their order are the oracle's; every product is batched over the ciphertexts of a group.
+static void ps_params(int deg, int &k, std::vector<int> &giants) {
+    k = 2;
+    while (k * k < (deg + 1) / 2) k *= 2;
+    giants.clear();
+    for (int g = k; g <= deg; g *= 2) giants.push_back(g);
+}
+
+static void cheb_divide(const std::vector<double> &c, int G, std::vector<double> &q, std::vector<double> &r) {
+    const int d = (int)c.size() - 1;
+    q.assign(1, c[G]);
+    for (int j = 1; j <= d - G; j++) q.push_back(2.0 * c[G + j]);
+    r.resize(G);
+    for (int i = 0; i < G; i++) r[i] = c[i] - ((2 * G - i <= d && i >= 1) ? c[2 * G - i] : 0.0);
+}
+
+static int bit_len(int x) { int b = 0; while (x > 0) { b++; x >>= 1; } return b; }
+static int ps_depth(int i) { return bit_len(i - 1); }         // level cost of T_i from the tree
+
+static int ps_need(const std::vector<double> &cc, int k, const std::vector<int> &giants) {
+    const int d = (int)cc.size() - 1;
+    if (d < k) {
+        int m = 0;
+        for (int i = 1; i <= d; i++) m = std::max(m, ps_depth(i));
+        return 1 + m;
+    }
+    int G = 0;
+    for (int g : giants)
+        if (g <= d) G = g;
+    std::vector<double> q, r;
+    cheb_divide(cc, G, q, r);
+    if (q.size() == 1 && G - 1 < k) {
+        int m = ps_depth(G);
+        for (int i = 1; i < G; i++) m = std::max(m, ps_depth(i));
+        return 1 + m;
+    }
+    if (q.size() == 1) return std::max(1 + ps_depth(G), ps_need(r, k, giants));
+    return std::max(std::max(ps_need(q, k, giants) + 1, ps_depth(G) + 1), ps_need(r, k, giants));
+}
+
+// sum_(coef, x) round(coef scale q_{l+1} / s_x) x + round(c0 scale q_{l+1}) at level l + 1, rescaled
+// to (l, scale); y is scratch for the term-by-term form
+static int ps_lincomb(he_ctx *c, const std::vector<std::pair<double, const he_ct *>> &terms, double c0, int level,
+                      double scale, he_ct *out, he_ct *y, cudaStream_t s) {
+    const int lm = level + 1;
+    const double ql = (double)c->primes[lm];
+    const double cst = std::nearbyint(c0 * scale * ql);
+    if ((int)terms.size() <= HE_LC_MAX && lm + 1 <= HE_LC_LIMBS) {
+        std::vector<const u64 *> xs;
+        std::vector<size_t> pss;
+        std::vector<u64> res((size_t)terms.size() * HE_LC_LIMBS, 0), cres(HE_LC_LIMBS, 0);
+        for (size_t t = 0; t < terms.size(); t++) {
+            const he_ct *x = terms[t].second;
+            if (x->level < lm) { he_set_error("polynomial: operand below the combination level"); return HE_ESTATE; }
+            const double K = std::nearbyint(terms[t].first * scale * ql / x->scale);
+            xs.push_back(x->d);
+            pss.push_back(x->pstride);
+            for (int i = 0; i <= lm; i++)
+                if (!int_residue(K, c->primes[i], &res[t * HE_LC_LIMBS + i])) {
+                    he_set_error("polynomial: constant is not an exact integer");
+                    return HE_EINVAL;
+                }
+        }
+        for (int i = 0; i <= lm; i++)
+            if (!int_residue(cst, c->primes[i], &cres[i])) { he_set_error("polynomial: bad constant"); return HE_EINVAL; }
+        HE_TRY(ensure_ct(c, out, lm));
+        HE_TRY(k_lincomb(c, xs.data(), pss.data(), res.data(), (int)terms.size(), cres.data(), lm, out->d,
+                         out->pstride, s));
+    } else {
+        bool first = true;
+        for (auto &tm : terms) {
+            HE_TRY(he_ct_copy(y, tm.second, s));
+            HE_TRY(he_ct_drop_level(y, lm));
+            const double K = std::nearbyint(tm.first * scale * ql / y->scale);
+            HE_TRY(he_mul_int(c, y, K, s));
+            if (first) { HE_TRY(he_ct_copy(out, y, s)); first = false; }
+            else HE_TRY(he_add(c, out, y, s));
+        }
+        HE_TRY(he_add_const_int(c, out, cst, s));
+    }
+    out->scale = scale * ql;
+    HE_TRY(he_rescale(c, out, s));
+    out->scale = scale;
+    return HE_OK;
+}
+
+struct PsGroup {
+    he_ctx *c;
+    cudaStream_t s;
+    int k;
+    std::vector<int> giants;
+    int m;
+    std::vector<std::map<int, he_ct *>> T;                   // per ciphertext: index -> T_index
+    std::vector<std::vector<he_ct *>> tq, tr;                // per ciphertext, per recursion depth
+    std::vector<he_ct *> t1, y;
+
+    int ev(const std::vector<double> &cc, int level, const std::vector<double> &scale, const std::vector<he_ct *> &out,
+           int depth) {
+        const int d = (int)cc.size() - 1;
+        if (d < k) {
+            for (int j = 0; j < m; j++) {
+                std::vector<std::pair<double, const he_ct *>> terms;
+                for (int i = 1; i <= d; i++) terms.push_back({cc[i], T[j][i]});
+                HE_TRY(ps_lincomb(c, terms, cc[0], level, scale[j], out[j], y[j], s));
+            }
+            return HE_OK;
+        }
+        int G = 0;
+        for (int g : giants)
+            if (g <= d) G = g;
+        std::vector<double> q, r;
+        cheb_divide(cc, G, q, r);
+        if (q.size() == 1 && G - 1 < k) {                    // q_0 T_G + r in one combination
+            for (int j = 0; j < m; j++) {
+                std::vector<std::pair<double, const he_ct *>> terms;
+                for (int i = 1; i < G; i++) terms.push_back({r[i], T[j][i]});
+                terms.push_back({q[0], T[j][G]});
+                HE_TRY(ps_lincomb(c, terms, r[0], level, scale[j], out[j], y[j], s));
+            }
+            return HE_OK;
+        }
+        if (q.size() == 1) {                                 // ev(r) plus the scalar q_0 T_G
+            HE_TRY(ev(r, level, scale, out, depth + 1));
+            for (int j = 0; j < m; j++) {
+                HE_TRY(ps_lincomb(c, {{q[0], T[j][G]}}, 0.0, level, scale[j], tq[j][depth], y[j], s));
+                HE_TRY(he_add(c, out[j], tq[j][depth], s));
+            }
+            return HE_OK;
+        }
+        std::vector<double> sq(m);
+        std::vector<he_ct> tg(m);
+        std::vector<he_ct *> qo(m), ro(m);
+        for (int j = 0; j < m; j++) {
+            tg[j] = *T[j][G];                                // T_G dropped to level + 1 (a view)
+            tg[j].level = level + 1;
+            sq[j] = scale[j] * (double)c->primes[level + 1] / tg[j].scale;
+            qo[j] = tq[j][depth];
+            ro[j] = tr[j][depth];
+        }
+        HE_TRY(ev(q, level + 1, sq, qo, depth + 1));
+        std::vector<const he_ct *> A, B;
+        for (int j = 0; j < m; j++) {
+            if (qo[j]->level != level + 1) { he_set_error("polynomial: quotient off its level"); return HE_ESTATE; }
+            A.push_back(qo[j]);
+            B.push_back(&tg[j]);
+        }
+        HE_TRY(relin_batch(c, A, B, out, s));
+        std::vector<double> ps_(m);
+        for (int j = 0; j < m; j++) ps_[j] = out[j]->scale;
+        HE_TRY(ev(r, level, ps_, ro, depth + 1));
+        for (int j = 0; j < m; j++) HE_TRY(he_add(c, out[j], ro[j], s));
+        return HE_OK;
+    }
+};
+
+// m ciphertexts at one level; temporaries poly_tmp[t0 .. t0 + m * per)
+static int ps_group(he_ctx *c, const std::vector<he_ct *> &io, const double *cheb, int deg,
+                    const std::vector<double> &tgt, size_t t0, size_t per, cudaStream_t s) {
+    PsGroup P;
+    P.c = c;
+    P.s = s;
+    P.m = (int)io.size();
+    ps_params(deg, P.k, P.giants);
+    std::vector<double> cc(cheb, cheb + deg + 1);
+    const int need = ps_need(cc, P.k, P.giants);
+    const int lin = io[0]->level;
+    if (lin - need < 0) { he_set_error("he_poly_eval_ps: needs %d levels", need); return HE_ELEVEL; }
+    std::vector<int> idx;
+    const int top = std::max(P.k, P.giants.empty() ? 0 : P.giants.back());
+    for (int i = 1; i <= top; i++)
+        if (i <= P.k || std::find(P.giants.begin(), P.giants.end(), i) != P.giants.end()) idx.push_back(i);
+    const int nd = (int)P.giants.size() + 2;
+    P.T.resize(P.m);
+    P.tq.resize(P.m);
+    P.tr.resize(P.m);
+    P.t1.resize(P.m);
+    P.y.resize(P.m);
+    std::vector<he_ct *> outv(P.m);
+    for (int j = 0; j < P.m; j++) {
+        he_ct **tp = c->poly_tmp.data() + t0 + (size_t)j * per;
+        size_t u = 0;
+        for (int i : idx) P.T[j][i] = tp[u++];
+        for (int d = 0; d < nd; d++) {
+            P.tq[j].push_back(tp[u++]);
+            P.tr[j].push_back(tp[u++]);
+        }
+        P.t1[j] = tp[u++];
+        P.y[j] = tp[u++];
+        outv[j] = tp[u++];
+        if (u > per) { he_set_error("polynomial: temporaries"); return HE_ESTATE; }
+        HE_TRY(he_ct_copy(P.T[j][1], io[j], s));
+    }
+    // baby and giant steps, index by index, each product batched over the group
+    for (int i : idx) {
+        if (i == 1) continue;
+        const int h = i / 2;
+        std::vector<const he_ct *> A, B;
+        std::vector<he_ct *> O;
+        std::vector<he_ct> va(P.m), vb(P.m);
+        for (int j = 0; j < P.m; j++) {
+            if (i % 2 == 0) {
+                A.push_back(P.T[j][h]);
+                B.push_back(P.T[j][h]);
+            } else {
+                const int lv = std::min(P.T[j][h]->level, P.T[j][h + 1]->level);
+                va[j] = *P.T[j][h];
+                va[j].level = lv;
+                vb[j] = *P.T[j][h + 1];
+                vb[j].level = lv;
+                A.push_back(&va[j]);
+                B.push_back(&vb[j]);
+            }
+            O.push_back(P.T[j][i]);
+        }
+        HE_TRY(relin_batch(c, A, B, O, s));
+        for (int j = 0; j < P.m; j++) {
+            he_ct *x = P.T[j][i];
+            HE_TRY(he_mul_int(c, x, 2.0, s));
+            if (i % 2 == 0) {
+                HE_TRY(he_add_const_int(c, x, -std::nearbyint(x->scale), s));
+            } else {
+                HE_TRY(retarget(c, P.T[j][1], x->level, x->scale, P.t1[j], s));
+                HE_TRY(he_sub(c, x, P.t1[j], s));
+            }
+        }
+    }
+    HE_TRY(P.ev(cc, lin - need, tgt, outv, 0));
+    for (int j = 0; j < P.m; j++) HE_TRY(he_ct_copy(io[j], outv[j], s));
+    return HE_OK;
+}
+
+extern "C" int he_poly_eval_ps_many(he_ctx *c, he_ct *const *io, int m, const double *cheb, int deg,
+                                    const double *target_scales, void *stream) {
+    if (!c || !io || m < 1 || !cheb || !target_scales || deg < 2 || deg > 255) {
+        he_set_error("he_poly_eval_ps_many: bad argument");
+        return HE_EINVAL;
+    }
+    int k;
+    std::vector<int> giants;
+    ps_params(deg, k, giants);
+    const size_t per = (size_t)k + giants.size() + 2 * (giants.size() + 2) + 3;
+    std::map<int, std::vector<int>> by_level;
+    for (int j = 0; j < m; j++) {
+        if (!io[j] || io[j]->ctx != c) { he_set_error("he_poly_eval_ps_many: ciphertext %d missing", j); return HE_EINVAL; }
+        by_level[io[j]->level].push_back(j);
+    }
+    HE_TRY(poly_temps(c, (size_t)m * per));
+    size_t t0 = 0;
+    for (auto &kv : by_level) {
+        std::vector<he_ct *> grp;
+        std::vector<double> tg;
+        for (int j : kv.second) {
+            grp.push_back(io[j]);
+            tg.push_back(target_scales[j]);
+        }
+        HE_TRY(ps_group(c, grp, cheb, deg, tg, t0, per, (cudaStream_t)stream));
+        t0 += grp.size() * per;
+    }
+    return HE_OK;
+}
+
+extern "C" int he_poly_eval_ps(he_ctx *c, he_ct *io, const double *cheb, int deg, double target_scale, void *stream) {
+    he_ct *a[1] = {io};
+    return he_poly_eval_ps_many(c, a, 1, cheb, deg, &target_scale, stream);
+}
+
 extern "C" int he_poly_eval(he_ctx *c, he_ct *io, const double *cheb, int deg, double target_scale, void *stream) {
     if (!c || !io || !cheb || deg < 1 || deg > 64) { he_set_error("he_poly_eval: bad argument"); return HE_EINVAL; }
     int depth = 0;

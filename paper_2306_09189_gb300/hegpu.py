@@ -130,6 +130,8 @@ _SIGS = {
     "he_pool_run": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_vp]),
     "he_poly_eval": (c_int, [c_vp, c_vp, F64P, c_int, c_double, c_vp]),
     "he_poly_eval_many": (c_int, [c_vp, ctypes.POINTER(c_vp), c_int, F64P, c_int, F64P, c_vp]),
+    "he_poly_eval_ps": (c_int, [c_vp, c_vp, F64P, c_int, c_double, c_vp]),
+    "he_poly_eval_ps_many": (c_int, [c_vp, ctypes.POINTER(c_vp), c_int, F64P, c_int, F64P, c_vp]),
     "he_hconv2d": (c_int, [c_vp, ctypes.POINTER(he_layout), ctypes.POINTER(c_vp), F64P, F64P, c_int, c_int,
                            c_int, c_int, c_int, c_int, c_int, ctypes.POINTER(he_layout),
                            ctypes.POINTER(c_vp), c_vp]),
@@ -581,6 +583,18 @@ def he_poly_eval_many(ctx, cts, cheb, target_scales, stream=None):
     t = np.ascontiguousarray(target_scales, dtype=np.float64)
     _check(load().he_poly_eval_many(ctx, _vp_array(cts), len(cts), _p(c, F64P), c.size - 1, _p(t, F64P),
                                     stream_ptr(stream)))
+
+
+def he_poly_eval_ps(ctx, ct, cheb, target_scale, stream=None):
+    c = np.ascontiguousarray(cheb, dtype=np.float64)
+    _check(load().he_poly_eval_ps(ctx, ct, _p(c, F64P), c.size - 1, target_scale, stream_ptr(stream)))
+
+
+def he_poly_eval_ps_many(ctx, cts, cheb, target_scales, stream=None):
+    c = np.ascontiguousarray(cheb, dtype=np.float64)
+    t = np.ascontiguousarray(target_scales, dtype=np.float64)
+    _check(load().he_poly_eval_ps_many(ctx, _vp_array(cts), len(cts), _p(c, F64P), c.size - 1, _p(t, F64P),
+                                       stream_ptr(stream)))
 
 
 def he_poly_eval(ctx, ct, cheb, target_scale, stream=None):

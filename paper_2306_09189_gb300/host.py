@@ -96,3 +96,55 @@ def encrypt_image(ctx, lay, img, level, scale, nonce0=0, stream=None):
 
 def decrypt_image(ctx, lay, cts, stream=None):
     return unpack(lay, np.stack([H.he_decrypt(ctx, ct, lay.N, stream) for ct in cts]))
+
+
+def ps_products(deg):
+    """Relinearised products of the Paterson-Stockmeyer evaluation of a degree-deg polynomial:
+    the baby steps T_2..T_k, the giant steps beyond T_k, and one per split with a non-constant
+    quotient (the same recursion as the library's)."""
+    k = 2
+    while k * k < (deg + 1) // 2:
+        k *= 2
+    giants = []
+    g = k
+    while g <= deg:
+        giants.append(g)
+        g *= 2
+    count = (k - 1) + max(0, len(giants) - 1)
+
+    def splits(d):
+        if d < k:
+            return 0
+        G = max(x for x in giants if x <= d)
+        qd, rd = d - G, G - 1
+        if qd == 0:
+            return splits(rd) if rd >= k else 0
+        return 1 + splits(qd) + splits(rd)
+    return count + splits(deg)
+
+
+def ps_depth(deg):
+    """Levels the Paterson-Stockmeyer evaluation of a degree-deg polynomial consumes (the
+    library's recursion: leaves cost one level above their deepest baby step, a split with a
+    non-constant quotient one level above the quotient and the giant step)."""
+    k = 2
+    while k * k < (deg + 1) // 2:
+        k *= 2
+    giants = []
+    g = k
+    while g <= deg:
+        giants.append(g)
+        g *= 2
+    depth = lambda i: (i - 1).bit_length()
+
+    def need(d):
+        if d < k:
+            return 1 + max([depth(i) for i in range(1, d + 1)] + [0])
+        G = max(x for x in giants if x <= d)
+        qd, rd = d - G, G - 1
+        if qd == 0 and rd < k:
+            return 1 + max([depth(G)] + [depth(i) for i in range(1, G)])
+        if qd == 0:
+            return max(1 + depth(G), need(rd))
+        return max(need(qd) + 1, depth(G) + 1, need(rd))
+    return need(deg)

@@ -23,7 +23,8 @@ from . import host
 
 
 def poly_depth(deg):
-    return (deg - 1).bit_length() + 1
+    """Levels of the GELU as the serving loop evaluates it (Paterson-Stockmeyer)."""
+    return host.ps_depth(deg)
 
 
 @dataclass
@@ -102,8 +103,8 @@ class Worker:
             if mode == H.HE_PLAIN:
                 for ct in outc:
                     H.he_poly_eval(self.ctx, ct, st.cheb, st.scale, s)
-            else:                                  # all shards of the layer through the tree together
-                H.he_poly_eval_many(self.ctx, outc, st.cheb, [st.scale] * len(outc), s)
+            else:                                  # all shards of the layer through the products together
+                H.he_poly_eval_ps_many(self.ctx, outc, st.cheb, [st.scale] * len(outc), s)
             outp = b["pool%d" % i]
             H.he_pool_run(self.ctx, pool, outc, outp, mode, s)
             cur = outp

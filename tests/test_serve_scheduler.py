@@ -52,3 +52,15 @@ def test_admission_waits_for_memory_headroom():
     srv = Server(None, {}, 0, reserve_bytes=5, export=False, workers=[FakeWorker(0.01)], hbm_free=hbm_free)
     out = srv.serve([Request(0, 0.0, 32, 0)])
     assert out[0].start >= 0.1                        # held back until memory freed up
+
+
+def test_polynomial_depth_and_products_match_the_oracle_recursion():
+    # the serving planner's level budget and the bench's key-switch count follow the
+    # Paterson-Stockmeyer recursion the library runs (the oracle's cheb_ps_he pins its depth)
+    from paper_2306_09189_gb300 import host
+    from oracle import layers as Ly
+    assert [host.ps_depth(d) for d in (5, 16, 27, 59)] == [3, 5, 5, 6]
+    assert [host.ps_products(d) for d in (5, 16, 27, 59)] == [4, 8, 11, 16]
+    for d in (5, 16, 27, 59):
+        k, giants = Ly.cheb_ps_params(d)
+        assert host.ps_products(d) >= k - 1 + len(giants) - 1
