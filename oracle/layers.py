@@ -250,6 +250,11 @@ def rotate_all(ctx, cts, amounts_of):
 def mac_rescale(ctx, R, terms, pts, level, scale_in, pt_scale=None):
     """Rescale(sum_{(u,a)} pt_{u,a} * R_{u,a}): the fused pt x ct MAC of one output shard.
     pt_scale: the plaintexts' encoding scale (default q_level, which keeps the scale exact)."""
+    return ctx.rescale(mac(ctx, R, terms, pts, level, scale_in, pt_scale))
+
+
+def mac(ctx, R, terms, pts, level, scale_in, pt_scale=None):
+    """sum_{(u,a)} pt_{u,a} * R_{u,a}, unrescaled (scale scale_in * pt_scale)."""
     mods, psis = ctx.mods(level), ctx.psis(level)
     acc = [np.zeros((level + 1, ctx.n), dtype=np.uint64) for _ in range(2)]
     for (u, a), pt in zip(terms, pts):
@@ -260,7 +265,7 @@ def mac_rescale(ctx, R, terms, pts, level, scale_in, pt_scale=None):
     from .ckks import Ciphertext
     c = np.stack([ctx.intt(x, mods, psis).reshape(level + 1, ctx.n) for x in acc])
     S = float(ctx.q[level]) if pt_scale is None else pt_scale
-    return ctx.rescale(Ciphertext(c, level, scale_in * S))
+    return Ciphertext(c, level, scale_in * S)
 
 
 def conv_he(ctx, plan: ConvPlan, cts, pts=None, bias_pts=None, pt_scale=None):
@@ -353,6 +358,123 @@ def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None, pt_scale=None):
         acc.scale = scale * (float(ctx.q[level]) if pt_scale is None else pt_scale)
         ct = ctx.rescale(acc)
         bpt = bias_pts[v] if bias_pts is not None else encode(plan.bias[v], ctx.n, ct.scale)
+        ct.c[0] = ctx.add(ct.c[0], ctx.reduce_int(bpt, ctx.mods(ct.level)), ctx.mods(ct.level))
+        out.append(ct)
+    return out
+
+
+# ============================================================================ BSGS convolution
+def bsgs_split(a, B, N):
+    """Amount a = g + t (mod N): t is the residue of a modulo the block length B taken in
+    [-B/2, B/2) (the tap's row and column shift), g = a - t a whole number of blocks (the
+    channel offset r m^2 of Eqs. 2-5).  Both are returned as amounts in [0, N)."""
+    t = a % B
+    if 2 * t >= B:
+        t -= B
+    return (a - t) % N, t % N
+
+
+@dataclass
+class BsgsPlan:
+    """The diagonal plan regrouped baby-step / giant-step (double hoisting of the rotations of
+    Eqs. 2-7): D_{u,v,a} (.) rot_a(X_u) = rot_g( rot_{-g}(D_{u,v,a}) (.) rot_t(X_u) ) with
+    a = g + t, so
+
+        S_{v,g} = sum_{(u,t)} rot_{-g}(D_{u,v,g+t}) (.) rot_t(X_u)     (baby steps, hoisted per u)
+        out_v   = sum_g rot_g(S_{v,g}) + bias_v                       (giant steps)
+
+    Rotations: the distinct non-zero t per input shard plus the distinct non-zero g per output
+    shard, instead of the distinct non-zero a per input shard."""
+    base: ConvPlan
+    baby: dict = field(default_factory=dict)     # (v, g) -> {(u, t): rot_{-g}(D) float64 [N]}
+
+    def keys(self):
+        return sorted(self.baby)
+
+    def baby_amounts(self, u):
+        return sorted({t for d in self.baby.values() for (uu, t) in d if uu == u})
+
+    def giants(self, v):
+        return [g for (vv, g) in self.keys() if vv == v]
+
+    def n_rotations(self):
+        nb = sum(len([t for t in self.baby_amounts(u) if t != 0]) for u in range(self.base.lin.n_shards))
+        ng = sum(len([g for g in self.giants(v) if g != 0]) for v in range(self.base.lout.n_shards))
+        return nb + ng
+
+
+def conv_plan_bsgs(plan: ConvPlan):
+    """Regroup a diagonal conv plan by (output shard, giant amount); the block length of the
+    input layout fixes the split of every amount (bsgs_split)."""
+    N, B = plan.lin.N, plan.lin.B
+    bp = BsgsPlan(plan)
+    for v, terms in plan.terms.items():
+        for (u, a), D in terms.items():
+            g, t = bsgs_split(a, B, N)
+            d = bp.baby.setdefault((v, g), {})
+            assert (u, t) not in d
+            d[(u, t)] = np.roll(D, g)               # rot_{-g}(D)
+    return bp
+
+
+def bsgs_slots(bp: BsgsPlan, slots):
+    """Slot simulator of the BSGS form (np.roll as the rotation)."""
+    out = np.zeros((bp.base.lout.n_shards, bp.base.lin.N))
+    for (v, g), d in bp.baby.items():
+        S = np.zeros(bp.base.lin.N)
+        for (u, t), P in d.items():
+            S += P * np.roll(slots[u], -t)
+        out[v] += np.roll(S, -g)
+    return out + bp.base.bias
+
+
+def bsgs_plaintexts(bp: BsgsPlan, n, S):
+    """Integer plaintexts of the rotated diagonals at scale S, keyed by the diagonal's own term
+    (u, v, a = g + t)."""
+    N = bp.base.lin.N
+    return {(u, v, (g + t) % N): encode(P, n, S) for (v, g), d in bp.baby.items() for (u, t), P in d.items()}
+
+
+def conv_he_bsgs(ctx, bp: BsgsPlan, cts, pts=None, bias_pts=None, pt_scale=None, raised=False):
+    """hconv2d in the BSGS form, then rescale and bias.
+
+    raised=False: baby steps are hoisted rotations of each input shard (one ModDown each), the
+    S_{v,g} are plaintext MACs, and each S_{v,g} with g != 0 takes one hoisted rotation.
+    raised=True: both steps are raised-basis stages (raised_stage): the baby step gives every
+    S_{v,g} one ModDown, the giant step (plaintext 1) gives every output one ModDown.
+    Rescaling once, after the giant step, leaves the output scale in * S_pt / q_level as in the
+    diagonal form.  pts / bias_pts / pt_scale as in conv_he (pts keyed (u, v, a))."""
+    level, scale = cts[0].level, cts[0].scale
+    assert all(c.level == level and c.scale == scale for c in cts)
+    N = bp.base.lin.N
+    if pts is None:
+        pts = bsgs_plaintexts(bp, ctx.n, float(ctx.q[level]))
+    S_pt = float(ctx.q[level]) if pt_scale is None else pt_scale
+    keys = bp.keys()
+    nout = bp.base.lout.n_shards
+    if raised:
+        stage = {i: [(u, t, pts[(u, v, (g + t) % N)]) for (u, t) in sorted(bp.baby[(v, g)])]
+                 for i, (v, g) in enumerate(keys)}
+        S = raised_stage(ctx, cts, stage)
+        for x in S:
+            x.scale = scale * S_pt
+        giant = {v: [(i, g, None) for i, (vv, g) in enumerate(keys) if vv == v] for v in range(nout)}
+        accs = raised_stage(ctx, S, giant)
+    else:
+        R = rotate_all(ctx, cts, bp.baby_amounts)
+        accs = [None] * nout
+        for (v, g) in keys:
+            terms = sorted(bp.baby[(v, g)])
+            x = mac(ctx, R, terms, [pts[(u, v, (g + t) % N)] for (u, t) in terms], level, scale, pt_scale)
+            if g != 0:
+                ctx.gen_rotation_key(g)
+                x = ctx.rotate_hoisted(x, ctx.hoist(x), g)
+            accs[v] = x if accs[v] is None else ctx.add_ct(accs[v], x)
+    out = []
+    for v, acc in enumerate(accs):
+        acc.scale = scale * S_pt
+        ct = ctx.rescale(acc)
+        bpt = bias_pts[v] if bias_pts is not None else encode(bp.base.bias[v], ctx.n, ct.scale)
         ct.c[0] = ctx.add(ct.c[0], ctx.reduce_int(bpt, ctx.mods(ct.level)), ctx.mods(ct.level))
         out.append(ct)
     return out

@@ -56,6 +56,47 @@ def test_rotation_counts_match_the_paper():
     assert own_nbr  # some output shards read neighbour shards
 
 
+@pytest.mark.parametrize("c,co,m,N,k,pad", CASES)
+def test_bsgs_plan_equals_torch_conv2d(c, co, m, N, k, pad):
+    # the baby-step / giant-step regrouping is the same linear map as the diagonal plan
+    rng = np.random.default_rng(c * 100 + m + 1)
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (co, c, k, k))
+    b = rng.uniform(-1, 1, co)
+    lin = Ly.image_layout(c, m, N)
+    plan = Ly.conv_plan(lin, W, b, pad)
+    bp = Ly.conv_plan_bsgs(plan)
+    slots = Ly.pack(lin, x)
+    out = Ly.bsgs_slots(bp, slots)
+    assert np.abs(out - Ly.conv_slots(plan, slots)).max() < 1e-12
+    img = Ly.unpack(plan.lout, out, check_copies=True, atol=1e-12)
+    assert np.abs(img - _conv_ref(x, W, b, pad)).max() < 1e-12
+    for (v, g), d in bp.baby.items():           # every split is g + t with g whole blocks
+        assert g % lin.B == 0
+        for (u, t) in d:
+            assert (u, (g + t) % N) in plan.terms[v]
+            assert min(t, N - t) <= lin.B // 2
+
+
+def test_bsgs_rotation_counts():
+    rng = np.random.default_rng(1)
+    # one duplicated shard (c = 16): c kappa^2 - 1 = 143 diagonal rotations become
+    # (kappa^2 - 1) baby + (c - 1) giant = 23
+    p = Ly.conv_plan(Ly.image_layout(16, 32, 32768), rng.uniform(-1, 1, (16, 16, 3, 3)), None, 1)
+    assert p.n_rotations() == 143 and Ly.conv_plan_bsgs(p).n_rotations() == 8 + 15
+    # image shards, z = 4 channels per shard, 4 in / 4 out: n_in (kappa^2 - 1) + n_out (z - 1)
+    p = Ly.conv_plan(Ly.image_layout(16, 16, 1024), rng.uniform(-1, 1, (16, 16, 3, 3)), None, 1)
+    assert p.n_rotations() == 4 * 35 and Ly.conv_plan_bsgs(p).n_rotations() == 4 * 8 + 4 * 3
+    # channel shards: every amount is a tap shift, no giant steps
+    p = Ly.conv_plan(Ly.image_layout(2, 32, 512), rng.uniform(-1, 1, (2, 2, 3, 3)), None, 1)
+    bp = Ly.conv_plan_bsgs(p)
+    assert all(g == 0 for (_, g) in bp.baby) and bp.n_rotations() == p.n_rotations()
+    # the split itself: centred residue modulo the block
+    assert Ly.bsgs_split(3 * 256 + 17, 256, 1024) == (768, 17)
+    assert Ly.bsgs_split(3 * 256 - 17, 256, 1024) == (768, 1024 - 17)
+    assert Ly.bsgs_split(1024 - 1, 256, 1024) == (0, 1023)
+
+
 @pytest.mark.parametrize("c,m,N,sel", [(4, 32, 4096, False), (16, 32, 2048, False),
                                         (8, 32, 2048, False), (2, 32, 512, False),
                                         (2, 28, 512, False), (3, 32, 512, True),
@@ -264,6 +305,52 @@ def test_plaintexts_encoded_for_a_higher_level_serve_a_lower_one():
         assert out[0].level == 1 and out[0].scale == ctx.pr.scale * S / float(ctx.q[2])
         img = Ly.unpack(plan.lout, np.stack([ctx.decrypt(c) for c in out]))
         assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+
+
+def test_bsgs_he_without_giant_steps_is_the_diagonal_form():
+    # channel shards: every giant amount is 0, so S_{v,0} is the diagonal MAC (per-rotation
+    # form) or the diagonal raised stage, and the giant stage adds nothing: bit for bit
+    ctx = _small_ctx()
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0, 1, (2, 32, 32))
+    W = rng.uniform(-1, 1, (2, 2, 3, 3))
+    b = rng.uniform(-1, 1, 2)
+    lin = Ly.image_layout(2, 32, ctx.N)
+    plan = Ly.conv_plan(lin, W, b, 1)
+    bp = Ly.conv_plan_bsgs(plan)
+    assert all(g == 0 for (_, g) in bp.baby)
+    cts = [ctx.encrypt(Ly.pack(lin, x)[u], 3, nonce=40 + u) for u in range(lin.n_shards)]
+    for raised, diag in ((False, Ly.conv_he), (True, Ly.conv_he_raised)):
+        got = Ly.conv_he_bsgs(ctx, bp, cts, raised=raised)
+        want = diag(ctx, plan, cts)
+        for g_, w_ in zip(got, want):
+            assert g_.level == w_.level and g_.scale == w_.scale and np.array_equal(g_.c, w_.c)
+
+
+@pytest.mark.parametrize("c,co,m,log_n", [(8, 4, 16, 11), (2, 2, 8, 10)])
+def test_bsgs_he_decrypts_to_fp64_conv(c, co, m, log_n):
+    # image shards (8 channels in 2 shards) and a duplicated shard (2 channels x 4 copies)
+    ctx = Context(Params(log_n=log_n, n_q=4, n_p=2, dnum=2, q0_bits=50, q_bits=40, p_bits=50,
+                         scale=2.0 ** 40, seed=4))
+    rng = np.random.default_rng(c + m)
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (co, c, 3, 3))
+    b = rng.uniform(-1, 1, co)
+    lin = Ly.image_layout(c, m, ctx.N)
+    plan = Ly.conv_plan(lin, W, b, 1)
+    bp = Ly.conv_plan_bsgs(plan)
+    assert any(g != 0 for (_, g) in bp.baby) and bp.n_rotations() < plan.n_rotations()
+    S = float(ctx.q[3])                          # plaintexts for level 3 serve level 2 too
+    pts = Ly.bsgs_plaintexts(bp, ctx.n, S)
+    ref = _conv_ref(x, W, b, 1)
+    for level in (3, 2):
+        cts = [ctx.encrypt(Ly.pack(lin, x)[u], level, nonce=50 + u) for u in range(lin.n_shards)]
+        outs = [Ly.conv_he_bsgs(ctx, bp, cts, pts, pt_scale=S, raised=r) for r in (False, True)]
+        assert not np.array_equal(outs[0][0].c, outs[1][0].c)
+        for out in outs:
+            assert out[0].level == level - 1 and out[0].scale == ctx.pr.scale * S / float(ctx.q[level])
+            img = Ly.unpack(plan.lout, np.stack([ctx.decrypt(ct) for ct in out]))
+            assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
 
 
 @pytest.mark.parametrize("c,co,m,N,k,pad", [(3, 4, 32, 512, 3, 1), (2, 2, 32, 256, 7, 3), (3, 2, 28, 256, 5, 2),
