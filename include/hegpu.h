@@ -277,6 +277,22 @@ int he_conv_create(he_ctx *ctx, const he_layout *in, const double *W, const doub
 int he_conv_create_factored(he_ctx *ctx, const he_layout *in, const double *W, const double *bias,
                             int co, int ci, int kh, int kw, int stride, int pad, int level,
                             double in_scale, he_conv **out);
+/* The same convolution in baby-step giant-step form (double hoisting of the rotations of
+ * Eqs. 2-7): every diagonal amount a splits as a = g + t, t the residue of a modulo the input
+ * layout's block length taken in [-B/2, B/2) (the tap's row/column shift), g a whole number of
+ * blocks (the channel offset r m^2).  Baby steps: S_{v,g} = sum_{(u,t)} rot_{-g}(D_{u,v,a}) (.)
+ * rot_t(X_u), hoisted per input shard; giant steps: out_v = sum_g rot_g(S_{v,g}), then one
+ * rescale and the bias.  Rotations drop from the distinct a per input shard to the distinct t
+ * per input shard plus the distinct g per output shard (143 -> 23 for 16 duplicated channels
+ * with a 3x3 kernel; 568 -> 120 for 8 shards of 8 channels).  Same levels, plaintext count and
+ * output scale as he_conv_create; different bits.  In HE_FUSED mode both steps are raised-basis
+ * stages (one ModDown per partial sum, one per output); HE_PLAIN and HE_BATCHED give one
+ * hoisted rotation per partial sum.  Terms are ordered by v, then g, u, t; he_conv_export_plan
+ * returns each term's (u, v, a = g + t) and the unrotated diagonal D_{u,v,a};
+ * he_conv_import_plaintexts takes the rotated diagonals rot_{-g}(D) in that order. */
+int he_conv_create_bsgs(he_ctx *ctx, const he_layout *in, const double *W, const double *bias,
+                        int co, int ci, int kh, int kw, int stride, int pad, int level,
+                        double in_scale, he_conv **out);
 void he_conv_destroy(he_conv *conv);
 int he_conv_out_layout(const he_conv *conv, he_layout *out);
 int he_conv_out_level(const he_conv *conv);
@@ -287,7 +303,8 @@ int he_conv_rotations(const he_conv *conv, int32_t *amounts, size_t cap);
  * including the stride-2 select); he_pool_keyswitches the same for a pooling layer. */
 int64_t he_conv_keyswitches(const he_conv *conv);
 /* Number of diagonal terms of the stride-1 stage and their (u, v, a) in plan order
- * (v, then u, then a ascending); diag (optional) receives [n_terms][N] doubles. */
+ * (v, then u, then a ascending; BSGS form: v, then g, u, t); diag (optional) receives
+ * [n_terms][N] doubles. */
 int he_conv_n_terms(const he_conv *conv);
 int he_conv_export_plan(const he_conv *conv, int32_t *u, int32_t *v, int32_t *a, double *diag);
 /* Replace the plan's encoded plaintexts by caller-given integer polynomials (plan order,

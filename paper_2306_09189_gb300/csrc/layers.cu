@@ -1460,11 +1460,30 @@ struct he_conv {
     std::unique_ptr<ConvBatch> batch;            // he_conv_run_batch: buffers of the last signature
     std::unique_ptr<FactoredConv> fc;            // set: the factored channel-shard form
     std::map<std::pair<int, uint64_t>, u64 *> bias_by;   // (level, output scale) -> bias addends
+    // baby-step giant-step form: term t reads rot_{tt[t]}(X_u) into the partial sum ts[t];
+    // partial sum i is S_{sv[i], sg[i]}, rotated by sg[i] into output shard sv[i]
+    bool bsgs = false;
+    std::vector<int> tt, ts, sv, sg, s_off;      // s_off: [nS + 1] term range of each partial sum
+    u64 *Sb = nullptr, *Gb = nullptr;            // [nS][2][pw] partial sums, rotated partial sums
+    RotSet grot;                                 // per-rotation modes: giant rotations
+    bool grot_ready = false;
+    FusedStage fusedG;                           // HE_FUSED: giant stage
+    int term_amt(size_t t) const { return bsgs ? tt[t] : ta[t]; }   // rotation a term's input takes
     u64 *rot_ptr(int u, int a) {
         return a == 0 ? R + (size_t)u * 2 * pw : Rrot + (size_t)slot[(long long)u * c->N + a] * 2 * pw;
     }
     ~he_conv();
 };
+
+// Baby-step giant-step split of a diagonal amount: a = g + t (mod N), t the residue of a
+// modulo the block length B taken in [-B/2, B/2) (the tap's row and column shift), g a whole
+// number of blocks (the channel offset r m^2 of Eqs. 2-5).
+static void bsgs_split(int a, int B, int N, int &g, int &t) {
+    int r = a % B;
+    if (2 * r >= B) r -= B;
+    g = ((a - r) % N + N) % N;
+    t = (r % N + N) % N;
+}
 
 static int conv_bias_int(he_conv *cv, int v, double scale, std::vector<int64_t> &m) {
     std::vector<double> z(cv->c->N, 0.0);
@@ -1741,10 +1760,59 @@ extern "C" int he_conv_create_factored(he_ctx *c, const he_layout *in, const dou
 
 
 // buffers every mode uses: input copies, accumulators, the stride-2 select stage
+// per-rotation BSGS: the giant rotations of every partial sum (amount 0: a copy)
+static void bsgs_giant_set(he_conv *cv, RotSet &g, int level, size_t pw, u64 *Sb, u64 *Gb) {
+    g.c = cv->c;
+    g.level = level;
+    for (size_t i = 0; i < cv->sv.size(); i++) g.src.push_back({Sb + i * 2 * pw, pw});
+    for (size_t i = 0; i < cv->sv.size(); i++) g.add((int)i, cv->sg[i], Gb + i * 2 * pw, pw);
+}
+
+// per-rotation BSGS after the baby rotations: each partial sum's MAC (unrescaled), its giant
+// rotation, and the sum of the rotated partial sums of every output shard into acc
+static int bsgs_rot_tail(he_ctx *c, he_conv *cv, const mac_term *d_terms, u64 *Sb, u64 *Gb, u64 *acc, size_t pw,
+                         int lv, RotSet &grot, int mode, cudaStream_t s) {
+    const size_t nS = cv->sv.size();
+    for (size_t i = 0; i < nS; i++)
+        HE_TRY(k_mac(c, d_terms + cv->s_off[i], cv->s_off[i + 1] - cv->s_off[i], Sb + i * 2 * pw, pw, lv, false, s));
+    if (mode == HE_BATCHED) HE_TRY(grot.prepare_batched());
+    HE_TRY(grot.run(mode, s));
+    std::vector<char> first(cv->lout.ns, 1);
+    for (size_t i = 0; i < nS; i++) {
+        const int v = cv->sv[i];
+        u64 *a = acc + (size_t)v * 2 * pw;
+        const u64 *x = Gb + i * 2 * pw;
+        if (first[v]) HE_TRY(k_copy_limbs(a, pw, x, pw, pw, 2, s));
+        else HE_TRY(k_add_raw(c, a, pw, x, pw, lv + 1, 2, false, s));
+        first[v] = 0;
+    }
+    return HE_OK;
+}
+
+// fused BSGS stages of one image at level l: baby (inputs -> partial sums, one ModDown each)
+// and giant (partial sums -> outputs, plaintext 1, one ModDown per output)
+static int bsgs_fused_stages(he_conv *cv, FusedStage &B, FusedStage &G, int l, int pt_level, size_t pw, u64 *R,
+                             u64 *Sb, u64 *acc, const std::string &name) {
+    B.c = G.c = cv->c;
+    B.level = G.level = l;
+    B.pt_level = pt_level;
+    B.name = name + " baby";
+    G.name = name + " giant";
+    for (int u = 0; u < cv->lin.ns; u++) B.add_src(R + (size_t)u * 2 * pw, pw);
+    for (size_t i = 0; i < cv->sv.size(); i++) B.add_out(Sb + i * 2 * pw, pw);
+    for (size_t t = 0; t < cv->tu.size(); t++) B.add_term(cv->ts[t], cv->tu[t], cv->tt[t], cv->pts + t * cv->pe);
+    for (size_t i = 0; i < cv->sv.size(); i++) G.add_src(Sb + i * 2 * pw, pw);
+    for (int v = 0; v < cv->lout.ns; v++) G.add_out(acc + (size_t)v * 2 * pw, pw);
+    for (size_t i = 0; i < cv->sv.size(); i++) G.add_term(cv->sv[i], (int)i, cv->sg[i], HE_PT_ONE);
+    HE_TRY(B.build());
+    return G.build();
+}
+
 static int conv_runtime(he_conv *cv, const he_pool *pool_src = nullptr) {
     he_ctx *c = cv->c;
     HE_TRY(dev_alloc(&cv->R, (size_t)cv->lin.ns * 2 * cv->pw));
     HE_TRY(dev_alloc(&cv->acc, (size_t)cv->lout.ns * 2 * cv->pw));
+    if (cv->bsgs) HE_TRY(dev_alloc(&cv->Sb, cv->sv.size() * 2 * cv->pw));
     if (cv->stride == 2) {
         if (pool_src) HE_TRY(pool_fork(pool_src, c, &cv->pool));
         else HE_TRY(pool_build(c, cv->lout, cv->level - 1, true, &cv->pool));
@@ -1765,7 +1833,7 @@ static int conv_rot_runtime(he_conv *cv) {
     HE_TRY(dev_alloc(&cv->Rrot, cv->slot.size() * 2 * pw));
     std::vector<mac_term> terms(n_terms);
     for (size_t t = 0; t < n_terms; t++)
-        terms[t] = mac_term{cv->pts + t * cv->pe, cv->rot_ptr(cv->tu[t], cv->ta[t]), pw};
+        terms[t] = mac_term{cv->pts + t * cv->pe, cv->rot_ptr(cv->tu[t], cv->term_amt(t)), pw};
     HE_TRY(dev_alloc(&cv->d_terms, n_terms));
     HE_CHECK_CUDA(cudaMemcpy(cv->d_terms, terms.data(), n_terms * sizeof(mac_term), cudaMemcpyHostToDevice));
     cv->rot.c = c;
@@ -1774,6 +1842,10 @@ static int conv_rot_runtime(he_conv *cv) {
     for (auto &kv : cv->slot) {
         int u = (int)(kv.first / c->N), a = (int)(kv.first % c->N);
         cv->rot.add(u, a, cv->Rrot + (size_t)kv.second * 2 * pw, pw);
+    }
+    if (cv->bsgs) {
+        HE_TRY(dev_alloc(&cv->Gb, cv->sv.size() * 2 * pw));
+        bsgs_giant_set(cv, cv->grot, cv->level, pw, cv->Sb, cv->Gb);
     }
     cv->rot_ready = true;
     return HE_OK;
@@ -1790,6 +1862,8 @@ static int conv_fork(const he_conv *src, he_ctx *c, he_conv **out) {
     cv->in_scale = src->in_scale; cv->mid_scale = src->mid_scale;
     cv->pw = src->pw; cv->pe = src->pe;
     cv->tu = src->tu; cv->tv = src->tv; cv->ta = src->ta; cv->term_off = src->term_off;
+    cv->bsgs = src->bsgs;
+    cv->tt = src->tt; cv->ts = src->ts; cv->sv = src->sv; cv->sg = src->sg; cv->s_off = src->s_off;
     cv->slot = src->slot;
     cv->pts = src->pts;
     cv->bias_pts = src->bias_pts;
@@ -1809,9 +1883,8 @@ extern "C" int he_pool_fork(const he_pool *src, he_ctx *ctx, he_pool **out) {
     return pool_fork(src, ctx, out);
 }
 
-extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, const double *bias,
-                              int co, int ci, int kh, int kw, int stride, int pad, int level,
-                              double in_scale, he_conv **out) {
+static int conv_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int co, int ci, int kh,
+                       int kw, int stride, int pad, int level, double in_scale, bool bsgs, he_conv **out) {
     if (!c || !in || !W || !out || co < 1 || ci < 1 || kh < 1 || kw < 1 || pad < 0 ||
         (stride != 1 && stride != 2)) {
         he_set_error("he_conv_create: bad argument");
@@ -1844,25 +1917,60 @@ extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, c
         plan_conv_v(lin, cv->lout, cv->W.data(), ci, kh, kw, pad, v, maps[v]);
         n_terms += maps[v].size();
     }
-    // rotation slots: every (u, a) with a != 0 that some output needs
+    const int N = c->N;
+    cv->bsgs = bsgs;
+    // rotation slots: every (u, amount) with amount != 0 that some term's input needs (the
+    // diagonal amount a, or in the BSGS form the baby amount t)
     for (int v = 0; v < cv->lout.ns; v++)
-        for (auto &kv : maps[v])
-            if (kv.first % c->N != 0 && !cv->slot.count(kv.first)) {
+        for (auto &kv : maps[v]) {
+            int a = (int)(kv.first % N), g = 0, t = a;
+            if (bsgs) bsgs_split(a, lin.B, N, g, t);
+            const long long key = (kv.first / N) * N + t;
+            if (t != 0 && !cv->slot.count(key)) {
                 int id = (int)cv->slot.size();
-                cv->slot[kv.first] = id;
+                cv->slot[key] = id;
             }
+        }
     HE_TRY(dev_alloc(&cv->pts, n_terms * pe));
     HE_TRY(dev_alloc(&cv->bias_pts, (size_t)cv->lout.ns * level * c->n));
-    // diagonal plaintexts at scale q_level
+    // diagonal plaintexts at scale q_level; in the BSGS form ordered by (g, u, t) within an
+    // output shard, the diagonal rotated by -g: P'[i] = D[(i - g) mod N]
     size_t t0 = 0;
     cv->term_off.push_back(0);
     for (int v = 0; v < cv->lout.ns; v++) {
-        std::vector<const double *> vecs;
+        struct E { int g, u, t, a; const std::vector<double> *D; };
+        std::vector<E> es;
         for (auto &kv : maps[v]) {
-            cv->tu.push_back((int)(kv.first / c->N));
+            int a = (int)(kv.first % N), g = 0, t = a;
+            if (bsgs) bsgs_split(a, lin.B, N, g, t);
+            es.push_back({g, (int)(kv.first / N), t, a, &kv.second});
+        }
+        if (bsgs)
+            std::sort(es.begin(), es.end(), [](const E &x, const E &y) {
+                return x.g != y.g ? x.g < y.g : x.u != y.u ? x.u < y.u : x.t < y.t;
+            });
+        std::vector<std::vector<double>> rolled;
+        std::vector<const double *> vecs;
+        if (bsgs) rolled.reserve(es.size());
+        for (const E &e : es) {
+            cv->tu.push_back(e.u);
             cv->tv.push_back(v);
-            cv->ta.push_back((int)(kv.first % c->N));
-            vecs.push_back(kv.second.data());
+            cv->ta.push_back(e.a);
+            if (bsgs) {
+                if (cv->sv.empty() || cv->sv.back() != v || cv->sg.back() != e.g) {
+                    cv->sv.push_back(v);
+                    cv->sg.push_back(e.g);
+                    cv->s_off.push_back((int)cv->tu.size() - 1);
+                }
+                cv->tt.push_back(e.t);
+                cv->ts.push_back((int)cv->sv.size() - 1);
+                std::vector<double> r(N);
+                for (int i = 0; i < N; i++) r[i] = (*e.D)[((i - e.g) % N + N) % N];
+                rolled.push_back(std::move(r));
+                vecs.push_back(rolled.back().data());
+            } else {
+                vecs.push_back(e.D->data());
+            }
         }
         HE_TRY(upload_plaintexts(c, vecs, vecs.size(), (double)c->primes[level], level, cv->pts + t0 * pe, nullptr,
                                  true));
@@ -1870,6 +1978,7 @@ extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, c
         cv->term_off.push_back((int)t0);
         DiagMap().swap(maps[v]);
     }
+    if (bsgs) cv->s_off.push_back((int)t0);
     // bias at the output scale, normal NTT form at level - 1
     for (int v = 0; v < cv->lout.ns; v++) {
         std::vector<int64_t> m;
@@ -1879,6 +1988,18 @@ extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, c
     HE_TRY(conv_runtime(cv.get()));
     *out = cv.release();
     return HE_OK;
+}
+
+extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, const double *bias,
+                              int co, int ci, int kh, int kw, int stride, int pad, int level,
+                              double in_scale, he_conv **out) {
+    return conv_create(c, in, W, bias, co, ci, kh, kw, stride, pad, level, in_scale, false, out);
+}
+
+extern "C" int he_conv_create_bsgs(he_ctx *c, const he_layout *in, const double *W, const double *bias,
+                                   int co, int ci, int kh, int kw, int stride, int pad, int level,
+                                   double in_scale, he_conv **out) {
+    return conv_create(c, in, W, bias, co, ci, kh, kw, stride, pad, level, in_scale, true, out);
 }
 
 extern "C" void he_conv_destroy(he_conv *cv) {
@@ -1897,6 +2018,7 @@ extern "C" int he_conv_rotations(const he_conv *cv, int32_t *amounts, size_t cap
     if (!cv) return HE_EINVAL;
     std::vector<int> v;
     for (auto &kv : cv->slot) v.push_back((int)(kv.first % cv->c->N));
+    v.insert(v.end(), cv->sg.begin(), cv->sg.end());
     if (cv->fc) v.insert(v.end(), cv->fc->amt.begin(), cv->fc->amt.end());
     if (cv->pool) collect_rotations(cv->pool, v);
     return distinct_nonzero(cv->c, v, amounts, cap);
@@ -1932,6 +2054,7 @@ extern "C" int64_t he_conv_keyswitches(const he_conv *cv) {
         k = (int64_t)r.size();
     } else {
         k = (int64_t)cv->slot.size();
+        for (int g : cv->sg) k += h_galois(cv->c, g) != 1;
     }
     if (cv->pool) k += pool_keyswitches(cv->pool);
     return k;
@@ -1962,13 +2085,13 @@ extern "C" int he_conv_export_plan(const he_conv *cv, int32_t *u, int32_t *v, in
         if (v) v[t] = cv->tv[t];
         if (a) a[t] = cv->ta[t];
     }
-    if (diag) {
+    if (diag) {                                 // the diagonal D_{u,v,a} of every term
         const int N = cv->c->N;
-        size_t t = 0;
         for (int vv = 0; vv < cv->lout.ns; vv++) {
             DiagMap m;
             plan_conv_v(cv->lin, cv->lout, cv->W.data(), cv->ci, cv->kh, cv->kw, cv->pad, vv, m);
-            for (auto &kv : m) memcpy(diag + (t++) * N, kv.second.data(), (size_t)N * 8);
+            for (int t = cv->term_off[vv]; t < cv->term_off[vv + 1]; t++)
+                memcpy(diag + (size_t)t * N, m[(long long)cv->tu[t] * N + cv->ta[t]].data(), (size_t)N * 8);
         }
     }
     return HE_OK;
@@ -1999,10 +2122,11 @@ extern "C" int he_conv_import_plaintexts(he_conv *cv, const int64_t *terms, cons
 static int conv_prepare_fused(he_conv *cv) {
     FusedStage &F = cv->fused;
     if (F.c) return HE_OK;
-    F.c = cv->c;
-    F.level = cv->level;
     char nm[96];
     snprintf(nm, sizeof(nm), "conv %d->%d %dx%d k%dx%d", cv->ci, cv->co, cv->lin.m, cv->lin.m, cv->kh, cv->kw);
+    if (cv->bsgs) return bsgs_fused_stages(cv, F, cv->fusedG, cv->level, cv->level, cv->pw, cv->R, cv->Sb, cv->acc, nm);
+    F.c = cv->c;
+    F.level = cv->level;
     F.name = nm;
     for (int u = 0; u < cv->lin.ns; u++) F.add_src(cv->R + (size_t)u * 2 * cv->pw, cv->pw);
     for (int v = 0; v < cv->lout.ns; v++) F.add_out(cv->acc + (size_t)v * 2 * cv->pw, cv->pw);
@@ -2031,10 +2155,12 @@ extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out
     if (mode == HE_FUSED) {
         HE_TRY(conv_prepare_fused(cv));
         HE_TRY(cv->fused.run(s));
+        if (cv->bsgs) HE_TRY(cv->fusedG.run(s));
     } else {
         HE_TRY(conv_rot_runtime(cv));
         if (mode == HE_BATCHED) HE_TRY(cv->rot.prepare_batched());
         HE_TRY(cv->rot.run(mode, s));
+        if (cv->bsgs) HE_TRY(bsgs_rot_tail(c, cv, cv->d_terms, cv->Sb, cv->Gb, cv->acc, pw, lv, cv->grot, mode, s));
     }
     he_ct **dst = cv->stride == 1 ? out : cv->mid.data();
     for (int v = 0; v < cv->lout.ns; v++) {
@@ -2042,7 +2168,7 @@ extern "C" int he_conv_run(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out
         // add the bias, hand out
         u64 *a = cv->acc + (size_t)v * 2 * pw;
         const int t0 = cv->term_off[v], t1 = cv->term_off[v + 1];
-        if (mode != HE_FUSED) HE_TRY(k_mac(c, cv->d_terms + t0, t1 - t0, a, pw, lv, false, s));
+        if (mode != HE_FUSED && !cv->bsgs) HE_TRY(k_mac(c, cv->d_terms + t0, t1 - t0, a, pw, lv, false, s));
         he_ct t = view(c, a, pw, lv, cv->in_scale * (double)c->primes[lv]);
         HE_TRY(he_rescale(c, &t, stream));
         HE_TRY(k_add_raw(c, a, pw, cv->bias_pts + (size_t)v * lv * c->n, 0, lv, 1, false, s));
@@ -2068,23 +2194,24 @@ struct ConvSlot {                                // one image of a batch: buffer
     int level = 0;
     size_t pw = 0;
     u64 *R = nullptr, *acc = nullptr, *Rrot = nullptr;
+    u64 *Sb = nullptr, *Gb = nullptr;            // BSGS partial sums, rotated partial sums
     mac_term *d_terms = nullptr;
-    RotSet rot;
+    RotSet rot, grot;
     bool rot_ready = false;
-    FusedStage fused;
-    ~ConvSlot() { cudaFree(R); cudaFree(acc); cudaFree(Rrot); cudaFree(d_terms); }
+    FusedStage fused, fusedG;                    // fusedG: BSGS giant stage
+    ~ConvSlot() { cudaFree(R); cudaFree(acc); cudaFree(Rrot); cudaFree(d_terms); cudaFree(Sb); cudaFree(Gb); }
 };
 struct ConvBatch {
     std::vector<int> levels;
     std::vector<std::unique_ptr<ConvSlot>> slots;
-    std::unique_ptr<FusedLaunch> launch;
+    std::unique_ptr<FusedLaunch> launch, launchG;   // launchG: the BSGS giant stages
 };
 
 he_conv::~he_conv() {
     batch.reset();
     fc.reset();
     for (auto &kv : bias_by) cudaFree(kv.second);
-    cudaFree(R); cudaFree(Rrot); cudaFree(d_terms); cudaFree(acc);
+    cudaFree(R); cudaFree(Rrot); cudaFree(d_terms); cudaFree(acc); cudaFree(Sb); cudaFree(Gb);
     if (!shared_pts) { cudaFree(pts); cudaFree(bias_pts); }
     delete pool;
     for (he_ct *x : mid) he_ct_free(x);
@@ -2101,6 +2228,12 @@ static int conv_batch_build(he_conv *cv, const std::vector<int> &levels) {
     snprintf(nm, sizeof(nm), "conv %d->%d %dx%d k%dx%d batch of %zu", cv->ci, cv->co, cv->lin.m, cv->lin.m, cv->kh,
              cv->kw, levels.size());
     B->launch->name = nm;
+    if (cv->bsgs) {
+        B->launchG.reset(new FusedLaunch());
+        B->launchG->c = c;
+        B->launchG->name = std::string(nm) + " giant";
+        B->launch->name += " baby";
+    }
     for (size_t i = 0; i < levels.size(); i++) {
         std::unique_ptr<ConvSlot> S(new ConvSlot());
         const int l = levels[i];
@@ -2108,6 +2241,15 @@ static int conv_batch_build(he_conv *cv, const std::vector<int> &levels) {
         S->pw = (size_t)(l + 1) * c->n;
         HE_TRY(dev_alloc(&S->R, (size_t)cv->lin.ns * 2 * S->pw));
         HE_TRY(dev_alloc(&S->acc, (size_t)cv->lout.ns * 2 * S->pw));
+        if (cv->bsgs) {
+            HE_TRY(dev_alloc(&S->Sb, cv->sv.size() * 2 * S->pw));
+            HE_TRY(bsgs_fused_stages(cv, S->fused, S->fusedG, l, cv->level, S->pw, S->R, S->Sb, S->acc,
+                                     std::string(nm) + " image " + std::to_string(i)));
+            B->launch->st.push_back(&S->fused);
+            B->launchG->st.push_back(&S->fusedG);
+            B->slots.push_back(std::move(S));
+            continue;
+        }
         FusedStage &F = S->fused;
         F.c = c;
         F.level = l;
@@ -2135,7 +2277,7 @@ static int conv_slot_rot(he_conv *cv, ConvSlot &S) {
         return a == 0 ? S.R + (size_t)u * 2 * pw : S.Rrot + (size_t)slot[(long long)u * c->N + a] * 2 * pw;
     };
     std::vector<mac_term> terms(n_terms);
-    for (size_t t = 0; t < n_terms; t++) terms[t] = mac_term{cv->pts + t * cv->pe, rptr(cv->tu[t], cv->ta[t]), pw};
+    for (size_t t = 0; t < n_terms; t++) terms[t] = mac_term{cv->pts + t * cv->pe, rptr(cv->tu[t], cv->term_amt(t)), pw};
     HE_TRY(dev_alloc(&S.d_terms, n_terms));
     HE_CHECK_CUDA(cudaMemcpy(S.d_terms, terms.data(), n_terms * sizeof(mac_term), cudaMemcpyHostToDevice));
     S.rot.c = c;
@@ -2144,6 +2286,10 @@ static int conv_slot_rot(he_conv *cv, ConvSlot &S) {
     for (auto &kv : slot) {
         int u = (int)(kv.first / c->N), a = (int)(kv.first % c->N);
         S.rot.add(u, a, S.Rrot + (size_t)kv.second * 2 * pw, pw);
+    }
+    if (cv->bsgs) {
+        HE_TRY(dev_alloc(&S.Gb, cv->sv.size() * 2 * pw));
+        bsgs_giant_set(cv, S.grot, S.level, pw, S.Sb, S.Gb);
     }
     S.rot_ready = true;
     return HE_OK;
@@ -2228,12 +2374,14 @@ extern "C" int he_conv_run_batch(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct
     }
     if (mode == HE_FUSED) {
         HE_TRY(B.launch->run(s));
+        if (B.launchG) HE_TRY(B.launchG->run(s));
     } else {
         for (int i = 0; i < n_img; i++) {
             ConvSlot &S = *B.slots[i];
             HE_TRY(conv_slot_rot(cv, S));
             if (mode == HE_BATCHED) HE_TRY(S.rot.prepare_batched());
             HE_TRY(S.rot.run(mode, s));
+            if (cv->bsgs) HE_TRY(bsgs_rot_tail(c, cv, S.d_terms, S.Sb, S.Gb, S.acc, S.pw, S.level, S.grot, mode, s));
         }
     }
     const double S_pt = (double)c->primes[cv->level];
@@ -2247,7 +2395,7 @@ extern "C" int he_conv_run_batch(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct
         for (int v = 0; v < no; v++) {
             u64 *a = S.acc + (size_t)v * 2 * S.pw;
             const int t0 = cv->term_off[v], t1 = cv->term_off[v + 1];
-            if (mode != HE_FUSED) HE_TRY(k_mac(c, S.d_terms + t0, t1 - t0, a, S.pw, l, false, s));
+            if (mode != HE_FUSED && !cv->bsgs) HE_TRY(k_mac(c, S.d_terms + t0, t1 - t0, a, S.pw, l, false, s));
             he_ct t = view(c, a, S.pw, l, in_scale * S_pt);
             HE_TRY(he_rescale(c, &t, stream));
             HE_TRY(k_add_raw(c, a, S.pw, bias + (size_t)v * l * c->n, 0, l, 1, false, s));
