@@ -215,9 +215,14 @@ def run_block(args, ws, rank, local):
     top2 = top1 - 1 - gdepth
     t_setup = time.perf_counter()
     lay = H.he_layout_image(c, m, N)
-    conv1 = H.he_conv_create(ctx, lay, W1, b1, 1, 1, top1, pr.scale)
+    if args.conv == "bsgs":
+        def create(*a):
+            return H.he_conv_create_bsgs(*a, args.bsgs_k)
+    else:
+        create = H.he_conv_create
+    conv1 = create(ctx, lay, W1, b1, 1, 1, top1, pr.scale)
     lay1 = H.he_conv_out_layout(conv1)
-    conv2 = H.he_conv_create(ctx, lay1, W2, b2, 1, 1, top2, pr.scale)
+    conv2 = create(ctx, lay1, W2, b2, 1, 1, top2, pr.scale)
     lay2 = H.he_conv_out_layout(conv2)
     H.he_keygen_rotations(ctx, sorted(set(H.he_conv_rotations(conv1)) | set(H.he_conv_rotations(conv2))))
     H.he_keygen_relin(ctx)
@@ -233,11 +238,8 @@ def run_block(args, ws, rank, local):
     tgt_all = [t for t in tgt for _ in range(lay.n_shards)]
     setup_s = time.perf_counter() - t_setup
 
-    def rot_count(conv):
-        u, v, a, _ = H.he_conv_export_plan(conv, N)
-        return len({(int(uu), int(aa)) for uu, aa in zip(u, a) if int(aa) % N != 0})
     products = host.ps_products(DEG) if args.poly == "ps" else DEG - 1
-    ks_per_step = len(levels) * (rot_count(conv1) + rot_count(conv2) + ns1 * products)
+    ks_per_step = len(levels) * (H.he_conv_keyswitches(conv1) + H.he_conv_keyswitches(conv2) + ns1 * products)
     pt_bytes = sum(H.he_conv_n_terms(cv) * (lv + 1 + info["K"]) * n * 8 for cv, lv in ((conv1, top1), (conv2, top2)))
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()
@@ -340,6 +342,9 @@ def run_block(args, ws, rank, local):
                            "input_levels": list(levels),
                            "key_switches_per_step": ks_per_step, "images": len(levels),
                            "mode": "each conv of the batch is one fused launch over all images and levels",
+                           "conv": args.conv,
+                           "bsgs_giant_blocks": [H.he_conv_bsgs_giant(conv1), H.he_conv_bsgs_giant(conv2)],
+                           "conv_keyswitches_per_image": [H.he_conv_keyswitches(conv1), H.he_conv_keyswitches(conv2)],
                            "cuda_graph": True, "key_stream": args.key_stream,
                            "autotuner": H.he_ctx_tuning_log(ctx).strip().splitlines(),
                            "setup_s": setup_s,
@@ -348,7 +353,8 @@ def run_block(args, ws, rank, local):
                            "parallelism": "replicas" if ws > 1 else "single"},
                 "plain": {"ms_per_step": ms_p, "value": ws * ks_per_step / (ms_p * 1e-3),
                           "batched_speedup": ms_p / ms_f,
-                          "note": "image by image, per-ciphertext key switches, same plaintexts"},
+                          "note": "image by image, per-ciphertext key switches, same plaintexts"
+                                  + (" (per-rotation BSGS)" if args.conv == "bsgs" else "")},
                 "check": {"image": 0, "input_level": levels[0], "max_err_rel_range": err,
                           "tolerance": 2.0 ** -20},
                 "gpu_launches": int(launches_f), "roofline": roof, "clocks": clk}
@@ -496,6 +502,11 @@ def main():
                     help="key-switch + MAC form: autotuned (default), the fused kernel with vector "
                          "loads or a TMA tile pipeline, or the split form (inner products, then MAC)")
     ap.add_argument("--no-graph", action="store_true", help="launch the fused step eagerly, not as a CUDA graph")
+    ap.add_argument("--conv", default="diag", choices=["diag", "bsgs"],
+                    help="convolution form of the ResNet block: diagonal (one rotation per amount) or "
+                         "baby-step giant-step")
+    ap.add_argument("--bsgs-k", type=int, default=0,
+                    help="giant stride (blocks) of the baby-step giant-step convolutions; 0 = cost model")
     ap.add_argument("--poly", default="ps", choices=["ps", "tree"],
                     help="GELU evaluation: Paterson-Stockmeyer (default) or the binary tree")
     ap.add_argument("--workload", default="cifar-layer", choices=["cifar-layer", "resnet-block", "imagenet-stem"],
@@ -536,6 +547,9 @@ def main():
     rots = H.he_conv_rotations(conv)
     H.he_keygen_rotations(ctx, rots)
     H.he_keygen_relin(ctx)
+    # the same layer in baby-step giant-step form, timed beside the diagonal form
+    conv_b = H.he_conv_create_bsgs(ctx, lay, wl.W, wl.bias, 1, 1, LEVEL, pr.scale, args.bsgs_k)
+    H.he_keygen_rotations(ctx, H.he_conv_rotations(conv_b))
     y = H.he_ct_alloc(ctx, LEVEL - 1)
     products = host.ps_products(DEG) if args.poly == "ps" else DEG - 1
     ks_per_step = len(rots) + products
@@ -545,8 +559,10 @@ def main():
 
     poly = H.he_poly_eval_ps if args.poly == "ps" else H.he_poly_eval
 
+    cur = {"conv": conv}
+
     def step(mode):
-        H.he_conv_run(ctx, conv, [x], [y], mode, stream)
+        H.he_conv_run(ctx, cur["conv"], [x], [y], mode, stream)
         poly(ctx, y, cheb, pr.scale, stream)
 
     def barrier():
@@ -617,6 +633,17 @@ def main():
     clk = clocks.stop()
     ms_p, _, _ = timed(H.HE_PLAIN, max(1, args.steps // 2))
     ms_u, _, _ = timed(H.HE_BATCHED, max(1, args.steps // 2))
+    # BSGS form: its first run builds and autotunes, then its own graph
+    cur["conv"] = conv_b
+    step(H.HE_FUSED)
+    torch.cuda.synchronize()
+    H.he_graph_destroy(graph)
+    H.he_graph_begin(ctx, stream)
+    step(H.HE_FUSED)
+    graph = H.he_graph_end(ctx, stream)
+    ms_bs, _, _ = timed(H.HE_FUSED, args.steps)
+    ks_bsgs = H.he_conv_keyswitches(conv_b) + products
+    cur["conv"] = conv
 
     # end to end through the C ABI with host buffers: pinned host ciphertext in, result out
     xin = H.he_ct_export_coeffs(ctx, x, n)
@@ -688,6 +715,11 @@ def main():
             "plain": {"ms_per_step": ms_p, "value": ws * ks_per_step / (ms_p * 1e-3),
                       "batched_speedup": ms_p / ms_b,
                       "note": "per-ciphertext launches, one ModDown per rotation"},
+            "bsgs": {"ms_per_step": ms_bs, "key_switches_per_step": ks_bsgs,
+                     "giant_blocks": H.he_conv_bsgs_giant(conv_b),
+                     "speedup_vs_diagonal": ms_b / ms_bs, "speedup_vs_plain": ms_p / ms_bs,
+                     "note": "same layer, baby-step giant-step convolution (tap shifts per input shard, "
+                             "channel offsets per partial sum), both steps raised-basis fused stages"},
             "batched_unfused": {"ms_per_step": ms_u, "value": ws * ks_per_step / (ms_u * 1e-3),
                                 "note": "all rotations per launch, one ModDown per rotation (bits equal plain)"},
             "e2e": {"value": ws * ks_per_step / (e2e_ms * 1e-3), "unit": "key-switches/s",
@@ -705,6 +737,7 @@ def main():
     H.he_graph_destroy(graph)
     H.he_graph_destroy(graph_e2e)
     H.he_conv_destroy(conv)
+    H.he_conv_destroy(conv_b)
     for c in (x, y, xe):
         H.he_ct_free(c)
     H.he_ctx_destroy(ctx)

@@ -278,21 +278,28 @@ int he_conv_create_factored(he_ctx *ctx, const he_layout *in, const double *W, c
                             int co, int ci, int kh, int kw, int stride, int pad, int level,
                             double in_scale, he_conv **out);
 /* The same convolution in baby-step giant-step form (double hoisting of the rotations of
- * Eqs. 2-7): every diagonal amount a splits as a = g + t, t the residue of a modulo the input
- * layout's block length taken in [-B/2, B/2) (the tap's row/column shift), g a whole number of
- * blocks (the channel offset r m^2).  Baby steps: S_{v,g} = sum_{(u,t)} rot_{-g}(D_{u,v,a}) (.)
- * rot_t(X_u), hoisted per input shard; giant steps: out_v = sum_g rot_g(S_{v,g}), then one
- * rescale and the bias.  Rotations drop from the distinct a per input shard to the distinct t
- * per input shard plus the distinct g per output shard (143 -> 23 for 16 duplicated channels
- * with a 3x3 kernel; 568 -> 120 for 8 shards of 8 channels).  Same levels, plaintext count and
- * output scale as he_conv_create; different bits.  In HE_FUSED mode both steps are raised-basis
- * stages (one ModDown per partial sum, one per output); HE_PLAIN and HE_BATCHED give one
- * hoisted rotation per partial sum.  Terms are ordered by v, then g, u, t; he_conv_export_plan
- * returns each term's (u, v, a = g + t) and the unrotated diagonal D_{u,v,a};
- * he_conv_import_plaintexts takes the rotated diagonals rot_{-g}(D) in that order. */
+ * Eqs. 2-7).  Every diagonal amount splits as a = r B + s: s the residue of a modulo the input
+ * layout's block length B taken in [-B/2, B/2) (the tap's row/column shift), r the channel
+ * offset in blocks (r m^2).  With a giant stride of k = giant_blocks blocks the baby amount is
+ * t = (r mod k) B + s and the giant amount g = (r - r mod k) B.  Baby steps: S_{v,g} =
+ * sum_{(u,t)} rot_{-g}(D_{u,v,a}) (.) rot_t(X_u), hoisted per input shard; giant steps:
+ * out_v = sum_g rot_g(S_{v,g}), then one rescale and the bias.  Rotations drop from the
+ * distinct a per input shard to the distinct t per input shard plus the distinct g per output
+ * shard (16 duplicated channels, 3x3: 143 -> 23 at k = 1, 38 at k = 4); k = blocks per shard
+ * gives every g = 0 (the diagonal rotation set).  giant_blocks = 0 picks k by a cost model of
+ * key and digit streaming against the extra ModUps and ModDowns (logged in
+ * he_ctx_tuning_log); otherwise it must be a power of two dividing the blocks per shard
+ * (HE_EINVAL).  Same levels, plaintext count and output scale as he_conv_create; different
+ * bits.  In HE_FUSED mode both steps are raised-basis stages (one ModDown per partial sum, one
+ * per output); HE_PLAIN and HE_BATCHED give one hoisted rotation per partial sum.  Terms are
+ * ordered by v, then g, u, t; he_conv_export_plan returns each term's (u, v, a = g + t) and
+ * the unrotated diagonal D_{u,v,a}; he_conv_import_plaintexts takes the rotated diagonals
+ * rot_{-g}(D) in that order. */
 int he_conv_create_bsgs(he_ctx *ctx, const he_layout *in, const double *W, const double *bias,
                         int co, int ci, int kh, int kw, int stride, int pad, int level,
-                        double in_scale, he_conv **out);
+                        double in_scale, int giant_blocks, he_conv **out);
+/* The giant stride (blocks) of a baby-step giant-step convolution; 0 for the other forms. */
+int he_conv_bsgs_giant(const he_conv *conv);
 void he_conv_destroy(he_conv *conv);
 int he_conv_out_layout(const he_conv *conv, he_layout *out);
 int he_conv_out_level(const he_conv *conv);

@@ -364,14 +364,17 @@ def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None, pt_scale=None):
 
 
 # ============================================================================ BSGS convolution
-def bsgs_split(a, B, N):
-    """Amount a = g + t (mod N): t is the residue of a modulo the block length B taken in
-    [-B/2, B/2) (the tap's row and column shift), g = a - t a whole number of blocks (the
-    channel offset r m^2 of Eqs. 2-5).  Both are returned as amounts in [0, N)."""
-    t = a % B
-    if 2 * t >= B:
-        t -= B
-    return (a - t) % N, t % N
+def bsgs_split(a, B, N, k=1):
+    """Amount a = g + t (mod N).  First a = r B + s with s the residue of a modulo the block
+    length B taken in [-B/2, B/2) (the tap's row and column shift) and r = (a - s)/B mod N/B
+    (the channel offset r m^2 of Eqs. 2-5); then with a giant stride of k blocks the baby step
+    takes t = (r mod k) B + s and the giant step g = (r - r mod k) B.  k = 1: t is the tap
+    shift; k = N/B: g = 0 (the diagonal form).  Both are returned as amounts in [0, N)."""
+    s = a % B
+    if 2 * s >= B:
+        s -= B
+    r = ((a - s) // B) % (N // B)
+    return (r - r % k) * B % N, ((r % k) * B + s) % N
 
 
 @dataclass
@@ -386,6 +389,7 @@ class BsgsPlan:
     Rotations: the distinct non-zero t per input shard plus the distinct non-zero g per output
     shard, instead of the distinct non-zero a per input shard."""
     base: ConvPlan
+    k: int = 1                                   # giant stride in blocks
     baby: dict = field(default_factory=dict)     # (v, g) -> {(u, t): rot_{-g}(D) float64 [N]}
 
     def keys(self):
@@ -403,14 +407,16 @@ class BsgsPlan:
         return nb + ng
 
 
-def conv_plan_bsgs(plan: ConvPlan):
-    """Regroup a diagonal conv plan by (output shard, giant amount); the block length of the
-    input layout fixes the split of every amount (bsgs_split)."""
+def conv_plan_bsgs(plan: ConvPlan, giant_blocks=1):
+    """Regroup a diagonal conv plan by (output shard, giant amount), every amount split with a
+    giant stride of giant_blocks blocks of the input layout (bsgs_split).  giant_blocks = N/B
+    leaves every g = 0: the diagonal form."""
     N, B = plan.lin.N, plan.lin.B
-    bp = BsgsPlan(plan)
+    assert giant_blocks >= 1 and (N // B) % giant_blocks == 0
+    bp = BsgsPlan(plan, giant_blocks)
     for v, terms in plan.terms.items():
         for (u, a), D in terms.items():
-            g, t = bsgs_split(a, B, N)
+            g, t = bsgs_split(a, B, N, giant_blocks)
             d = bp.baby.setdefault((v, g), {})
             assert (u, t) not in d
             d[(u, t)] = np.roll(D, g)               # rot_{-g}(D)

@@ -1463,6 +1463,7 @@ struct he_conv {
     // baby-step giant-step form: term t reads rot_{tt[t]}(X_u) into the partial sum ts[t];
     // partial sum i is S_{sv[i], sg[i]}, rotated by sg[i] into output shard sv[i]
     bool bsgs = false;
+    int bsgs_k = 0;                              // giant stride in blocks
     std::vector<int> tt, ts, sv, sg, s_off;      // s_off: [nS + 1] term range of each partial sum
     u64 *Sb = nullptr, *Gb = nullptr;            // [nS][2][pw] partial sums, rotated partial sums
     RotSet grot;                                 // per-rotation modes: giant rotations
@@ -1475,14 +1476,42 @@ struct he_conv {
     ~he_conv();
 };
 
-// Baby-step giant-step split of a diagonal amount: a = g + t (mod N), t the residue of a
-// modulo the block length B taken in [-B/2, B/2) (the tap's row and column shift), g a whole
-// number of blocks (the channel offset r m^2 of Eqs. 2-5).
-static void bsgs_split(int a, int B, int N, int &g, int &t) {
-    int r = a % B;
-    if (2 * r >= B) r -= B;
-    g = ((a - r) % N + N) % N;
-    t = (r % N + N) % N;
+// Baby-step giant-step split of a diagonal amount: a = r B + s with s the residue of a modulo
+// the block length B taken in [-B/2, B/2) (the tap's row and column shift) and r the channel
+// offset in blocks (r m^2 of Eqs. 2-5); with a giant stride of k blocks the baby amount is
+// t = (r mod k) B + s and the giant amount g = (r - r mod k) B (mod N).
+static void bsgs_split(int a, int B, int N, int k, int &g, int &t) {
+    int s = a % B;
+    if (2 * s >= B) s -= B;
+    const int nb = N / B;
+    const int r = (((a - s) / B) % nb + nb) % nb;
+    g = (int)((long long)(r - r % k) * B % N);
+    t = (((r % k) * B + s) % N + N) % N;
+}
+
+// Modelled time (us) of the BSGS form with giant stride k at a level: the key and raised-digit
+// streams at an effective 4.5 TB/s, and each ModUp (nq INTT + beta ext NTT limbs) and ModDown
+// (2 (K + nq) limbs) at 1.3 us per 2^16-word limb transform with its base conversion (both
+// rates as measured on the CIFAR-layer and ResNet-block convolutions).  terms: (v, u, a).
+static double bsgs_cost(const he_ctx *c, const Lay &lin, int level, const std::vector<std::array<int, 3>> &terms,
+                        int n_out, int k) {
+    std::set<int> amt_b, amt_g, src_b;
+    std::set<std::pair<int, int>> ent_b, S, grot;
+    for (auto &x : terms) {
+        int g, t;
+        bsgs_split(x[2], lin.B, lin.N, k, g, t);
+        S.insert({x[0], g});
+        if (t != 0) { amt_b.insert(t); ent_b.insert({x[1], t}); src_b.insert(x[1]); }
+        if (g != 0) { amt_g.insert(g); grot.insert({x[0], g}); }
+    }
+    const double nq = level + 1, ext = nq + c->K, beta = (level + c->alpha) / c->alpha;
+    const double limb = (double)c->n * 8, tlimb = 1.3e-6 * c->n / 65536.0;
+    const double keys = (double)(amt_b.size() + amt_g.size()) * 2 * beta * ext;
+    const double ents = (double)(ent_b.size() + grot.size()) * 3 * ext + (double)(ent_b.size() + grot.size()) * beta * ext;
+    const double hbm = (keys + ents) * limb / 4.5e12;
+    const double alu = ((double)(src_b.size() + grot.size()) * (nq + beta * ext) +
+                        (double)(S.size() + n_out) * 2 * (c->K + nq)) * tlimb;
+    return (hbm + alu) * 1e6;
 }
 
 static int conv_bias_int(he_conv *cv, int v, double scale, std::vector<int64_t> &m) {
@@ -1863,6 +1892,7 @@ static int conv_fork(const he_conv *src, he_ctx *c, he_conv **out) {
     cv->pw = src->pw; cv->pe = src->pe;
     cv->tu = src->tu; cv->tv = src->tv; cv->ta = src->ta; cv->term_off = src->term_off;
     cv->bsgs = src->bsgs;
+    cv->bsgs_k = src->bsgs_k;
     cv->tt = src->tt; cv->ts = src->ts; cv->sv = src->sv; cv->sg = src->sg; cv->s_off = src->s_off;
     cv->slot = src->slot;
     cv->pts = src->pts;
@@ -1883,8 +1913,11 @@ extern "C" int he_pool_fork(const he_pool *src, he_ctx *ctx, he_pool **out) {
     return pool_fork(src, ctx, out);
 }
 
+// bsgs_k < 0: the diagonal form; 0: baby-step giant-step with the giant stride chosen by
+// bsgs_cost; >= 1: with a giant stride of bsgs_k blocks
 static int conv_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int co, int ci, int kh,
-                       int kw, int stride, int pad, int level, double in_scale, bool bsgs, he_conv **out) {
+                       int kw, int stride, int pad, int level, double in_scale, int bsgs_k, he_conv **out) {
+    const bool bsgs = bsgs_k >= 0;
     if (!c || !in || !W || !out || co < 1 || ci < 1 || kh < 1 || kw < 1 || pad < 0 ||
         (stride != 1 && stride != 2)) {
         he_set_error("he_conv_create: bad argument");
@@ -1919,12 +1952,36 @@ static int conv_create(he_ctx *c, const he_layout *in, const double *W, const do
     }
     const int N = c->N;
     cv->bsgs = bsgs;
+    if (bsgs) {
+        if (bsgs_k > 0 && (bsgs_k > lin.nb || lin.nb % bsgs_k != 0 || (bsgs_k & (bsgs_k - 1)) != 0)) {
+            he_set_error("he_conv_create_bsgs: giant stride %d blocks does not divide the %d blocks of a shard",
+                         bsgs_k, lin.nb);
+            return HE_EINVAL;
+        }
+        if (bsgs_k == 0) {                     // the modelled-fastest giant stride
+            std::vector<std::array<int, 3>> tl;
+            for (int v = 0; v < cv->lout.ns; v++)
+                for (auto &kv : maps[v]) tl.push_back({v, (int)(kv.first / N), (int)(kv.first % N)});
+            std::string note = "conv " + std::to_string(ci) + "->" + std::to_string(co) + " " + std::to_string(lin.m) +
+                               "x" + std::to_string(lin.m) + " bsgs giant stride:";
+            double best = 0;
+            for (int k = 1; k <= lin.nb; k *= 2) {
+                const double t = bsgs_cost(c, lin, level, tl, cv->lout.ns, k);
+                char b[48];
+                snprintf(b, sizeof(b), " k=%d %.0f us;", k, t);
+                note += b;
+                if (bsgs_k == 0 || t < best) { best = t; bsgs_k = k; }
+            }
+            he_tune_note(c, note + " -> k=" + std::to_string(bsgs_k));
+        }
+        cv->bsgs_k = bsgs_k;
+    }
     // rotation slots: every (u, amount) with amount != 0 that some term's input needs (the
     // diagonal amount a, or in the BSGS form the baby amount t)
     for (int v = 0; v < cv->lout.ns; v++)
         for (auto &kv : maps[v]) {
             int a = (int)(kv.first % N), g = 0, t = a;
-            if (bsgs) bsgs_split(a, lin.B, N, g, t);
+            if (bsgs) bsgs_split(a, lin.B, N, bsgs_k, g, t);
             const long long key = (kv.first / N) * N + t;
             if (t != 0 && !cv->slot.count(key)) {
                 int id = (int)cv->slot.size();
@@ -1942,7 +1999,7 @@ static int conv_create(he_ctx *c, const he_layout *in, const double *W, const do
         std::vector<E> es;
         for (auto &kv : maps[v]) {
             int a = (int)(kv.first % N), g = 0, t = a;
-            if (bsgs) bsgs_split(a, lin.B, N, g, t);
+            if (bsgs) bsgs_split(a, lin.B, N, bsgs_k, g, t);
             es.push_back({g, (int)(kv.first / N), t, a, &kv.second});
         }
         if (bsgs)
@@ -1993,13 +2050,19 @@ static int conv_create(he_ctx *c, const he_layout *in, const double *W, const do
 extern "C" int he_conv_create(he_ctx *c, const he_layout *in, const double *W, const double *bias,
                               int co, int ci, int kh, int kw, int stride, int pad, int level,
                               double in_scale, he_conv **out) {
-    return conv_create(c, in, W, bias, co, ci, kh, kw, stride, pad, level, in_scale, false, out);
+    return conv_create(c, in, W, bias, co, ci, kh, kw, stride, pad, level, in_scale, -1, out);
 }
 
 extern "C" int he_conv_create_bsgs(he_ctx *c, const he_layout *in, const double *W, const double *bias,
                                    int co, int ci, int kh, int kw, int stride, int pad, int level,
-                                   double in_scale, he_conv **out) {
-    return conv_create(c, in, W, bias, co, ci, kh, kw, stride, pad, level, in_scale, true, out);
+                                   double in_scale, int giant_blocks, he_conv **out) {
+    if (giant_blocks < 0) { he_set_error("he_conv_create_bsgs: negative giant stride"); return HE_EINVAL; }
+    return conv_create(c, in, W, bias, co, ci, kh, kw, stride, pad, level, in_scale, giant_blocks, out);
+}
+
+extern "C" int he_conv_bsgs_giant(const he_conv *cv) {
+    if (!cv) return HE_EINVAL;
+    return cv->bsgs ? cv->bsgs_k : 0;
 }
 
 extern "C" void he_conv_destroy(he_conv *cv) {

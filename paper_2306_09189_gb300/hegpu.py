@@ -108,7 +108,8 @@ _SIGS = {
     "he_conv_create_factored": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_int, c_int,
                                         c_int, c_int, c_int, c_double, ctypes.POINTER(c_vp)]),
     "he_conv_create_bsgs": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_int, c_int,
-                                    c_int, c_int, c_int, c_double, ctypes.POINTER(c_vp)]),
+                                    c_int, c_int, c_int, c_double, c_int, ctypes.POINTER(c_vp)]),
+    "he_conv_bsgs_giant": (c_int, [c_vp]),
     "he_conv_destroy": (None, [c_vp]),
     "he_conv_fork": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "he_conv_out_layout": (c_int, [c_vp, ctypes.POINTER(he_layout)]),
@@ -465,14 +466,18 @@ def he_conv_create_factored(ctx, layout, W, bias, stride, pad, level, in_scale):
     return h
 
 
-def he_conv_create_bsgs(ctx, layout, W, bias, stride, pad, level, in_scale):
+def he_conv_create_bsgs(ctx, layout, W, bias, stride, pad, level, in_scale, giant_blocks=0):
     W = np.ascontiguousarray(W, dtype=np.float64)
     co, ci, kh, kw = W.shape
     b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
     h = c_vp()
     _check(load().he_conv_create_bsgs(ctx, ctypes.byref(layout), _p(W, F64P), None if b is None else _p(b, F64P),
-                                      co, ci, kh, kw, stride, pad, level, in_scale, ctypes.byref(h)))
+                                      co, ci, kh, kw, stride, pad, level, in_scale, giant_blocks, ctypes.byref(h)))
     return h
+
+
+def he_conv_bsgs_giant(conv):
+    return _check(load().he_conv_bsgs_giant(conv))
 
 
 def he_conv_destroy(conv):

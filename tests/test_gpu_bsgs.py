@@ -42,7 +42,8 @@ def _plan_order(bp, N):
 
 def _create(H, g, o, lin, W, b, level, pad, bp, stride=1):
     lay = H.he_layout_image(lin.c, lin.m, o.N)
-    conv = H.he_conv_create_bsgs(g.h, lay, W, b, stride, pad, level, o.pr.scale)
+    conv = H.he_conv_create_bsgs(g.h, lay, W, b, stride, pad, level, o.pr.scale, bp.k)
+    assert H.he_conv_bsgs_giant(conv) == bp.k
     rots = set(int(r) for r in H.he_conv_rotations(conv))
     H.he_keygen_rotations(g.h, sorted(rots))
     if stride == 1:
@@ -53,12 +54,14 @@ def _create(H, g, o, lin, W, b, level, pad, bp, stride=1):
     return conv
 
 
-@pytest.mark.parametrize("c,co,m,k,pad", [(8, 8, 28, 3, 1),    # 4 image shards of 2 channels
-                                           (16, 24, 16, 3, 1),  # 2 image shards of 8 channels
-                                           (2, 2, 16, 3, 1),    # one shard, 4 copies
-                                           (4, 2, 16, 5, 2),    # one shard, 2 copies, 5x5
-                                           (2, 2, 56, 3, 1)])   # channel shards: no giant step
-def test_bsgs_conv_bit_exact(mid, c, co, m, k, pad):
+@pytest.mark.parametrize("c,co,m,k,pad,gk", [(8, 8, 28, 3, 1, 1),    # 4 image shards of 2 channels
+                                              (16, 24, 16, 3, 1, 1),  # 2 image shards of 8 channels
+                                              (16, 24, 16, 3, 1, 4),  # the same, giant stride 4 blocks
+                                              (2, 2, 16, 3, 1, 1),    # one shard, 4 copies
+                                              (2, 2, 16, 3, 1, 2),    # the same, giant stride 2 blocks
+                                              (4, 2, 16, 5, 2, 1),    # one shard, 2 copies, 5x5
+                                              (2, 2, 56, 3, 1, 1)])   # channel shards: no giant step
+def test_bsgs_conv_bit_exact(mid, c, co, m, k, pad, gk):
     from paper_2306_09189_gb300 import hegpu as H
     from tests._hegpu_util import assert_ct_equal
     o, g = mid
@@ -69,7 +72,7 @@ def test_bsgs_conv_bit_exact(mid, c, co, m, k, pad):
     b = rng.uniform(-1, 1, co)
     lin = Ly.image_layout(c, m, o.N)
     plan = Ly.conv_plan(lin, W, b, pad)
-    bp = Ly.conv_plan_bsgs(plan)
+    bp = Ly.conv_plan_bsgs(plan, gk)
     slots = Ly.pack(lin, x)
     cts = [o.encrypt(slots[u], level, nonce=900 + u) for u in range(lin.n_shards)]
     pts = Ly.bsgs_plaintexts(bp, o.n, float(o.q[level]))
@@ -147,6 +150,25 @@ def test_bsgs_mixed_level_batch_bit_exact(mid):
                 assert H.he_ct_level(oc) == lv - 1 and H.he_ct_scale(oc) == rc.scale
                 assert_ct_equal(g.download(oc), rc)
     H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_AUTO)
+    H.he_conv_destroy(conv)
+
+
+def test_bsgs_giant_stride_choice_and_checks(mid):
+    from paper_2306_09189_gb300 import hegpu as H
+    o, g = mid
+    rng = np.random.default_rng(5)
+    W = rng.uniform(-1, 1, (2, 2, 3, 3))
+    lay = H.he_layout_image(2, 16, o.N)          # one shard of 8 blocks (4 copies)
+    conv = H.he_conv_create_bsgs(g.h, lay, W, None, 1, 1, 3, o.pr.scale, 0)
+    k = H.he_conv_bsgs_giant(conv)
+    assert k in (1, 2, 4, 8) and "bsgs giant stride" in H.he_ctx_tuning_log(g.h)
+    H.he_conv_destroy(conv)
+    for bad in (3, 16):                          # not a power of two / more than the 8 blocks
+        with pytest.raises(H.HEError) as e:
+            H.he_conv_create_bsgs(g.h, lay, W, None, 1, 1, 3, o.pr.scale, bad)
+        assert e.value.code == H.HE_EINVAL
+    conv = H.he_conv_create(g.h, lay, W, None, 1, 1, 3, o.pr.scale)
+    assert H.he_conv_bsgs_giant(conv) == 0
     H.he_conv_destroy(conv)
 
 

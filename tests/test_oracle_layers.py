@@ -75,7 +75,11 @@ def test_bsgs_plan_equals_torch_conv2d(c, co, m, N, k, pad):
         assert g % lin.B == 0
         for (u, t) in d:
             assert (u, (g + t) % N) in plan.terms[v]
-            assert min(t, N - t) <= lin.B // 2
+            assert min(t, N - t) <= lin.B // 2 or lin.B == N
+    k = 2
+    while k * lin.B <= N:                        # wider giant strides: the same linear map
+        assert np.abs(Ly.bsgs_slots(Ly.conv_plan_bsgs(plan, k), slots) - out).max() < 1e-12
+        k *= 2
 
 
 def test_bsgs_rotation_counts():
@@ -84,6 +88,9 @@ def test_bsgs_rotation_counts():
     # (kappa^2 - 1) baby + (c - 1) giant = 23
     p = Ly.conv_plan(Ly.image_layout(16, 32, 32768), rng.uniform(-1, 1, (16, 16, 3, 3)), None, 1)
     assert p.n_rotations() == 143 and Ly.conv_plan_bsgs(p).n_rotations() == 8 + 15
+    # giant stride of k blocks: (k kappa^2 - 1) baby + (c/k - 1) giant; k = c is the diagonal form
+    for k, want in ((2, 17 + 7), (4, 35 + 3), (8, 71 + 1), (16, 143), (32, 143)):
+        assert Ly.conv_plan_bsgs(p, k).n_rotations() == want
     # image shards, z = 4 channels per shard, 4 in / 4 out: n_in (kappa^2 - 1) + n_out (z - 1)
     p = Ly.conv_plan(Ly.image_layout(16, 16, 1024), rng.uniform(-1, 1, (16, 16, 3, 3)), None, 1)
     assert p.n_rotations() == 4 * 35 and Ly.conv_plan_bsgs(p).n_rotations() == 4 * 8 + 4 * 3
@@ -95,6 +102,8 @@ def test_bsgs_rotation_counts():
     assert Ly.bsgs_split(3 * 256 + 17, 256, 1024) == (768, 17)
     assert Ly.bsgs_split(3 * 256 - 17, 256, 1024) == (768, 1024 - 17)
     assert Ly.bsgs_split(1024 - 1, 256, 1024) == (0, 1023)
+    assert Ly.bsgs_split(3 * 256 + 17, 256, 1024, 2) == (512, 256 + 17)
+    assert Ly.bsgs_split(3 * 256 - 17, 256, 1024, 4) == (0, 3 * 256 - 17)
 
 
 @pytest.mark.parametrize("c,m,N,sel", [(4, 32, 4096, False), (16, 32, 2048, False),
@@ -325,6 +334,23 @@ def test_bsgs_he_without_giant_steps_is_the_diagonal_form():
         want = diag(ctx, plan, cts)
         for g_, w_ in zip(got, want):
             assert g_.level == w_.level and g_.scale == w_.scale and np.array_equal(g_.c, w_.c)
+
+
+def test_bsgs_he_with_full_giant_stride_is_the_diagonal_form():
+    # G = N: every g = 0 and t = a, on a duplicated shard that has giant steps at G = B
+    ctx = _small_ctx()
+    rng = np.random.default_rng(13)
+    x = rng.uniform(0, 1, (2, 8, 8))
+    W = rng.uniform(-1, 1, (2, 2, 3, 3))
+    lin = Ly.image_layout(2, 8, ctx.N)
+    plan = Ly.conv_plan(lin, W, None, 1)
+    assert any(g != 0 for (_, g) in Ly.conv_plan_bsgs(plan).baby)
+    bp = Ly.conv_plan_bsgs(plan, lin.nb)
+    assert all(g == 0 for (_, g) in bp.baby) and bp.n_rotations() == plan.n_rotations()
+    cts = [ctx.encrypt(Ly.pack(lin, x)[0], 3, nonce=45)]
+    for raised, diag in ((False, Ly.conv_he), (True, Ly.conv_he_raised)):
+        got, want = Ly.conv_he_bsgs(ctx, bp, cts, raised=raised), diag(ctx, plan, cts)
+        assert all(np.array_equal(a.c, b.c) for a, b in zip(got, want))
 
 
 @pytest.mark.parametrize("c,co,m,log_n", [(8, 4, 16, 11), (2, 2, 8, 10)])
