@@ -486,6 +486,122 @@ def conv_he_bsgs(ctx, bp: BsgsPlan, cts, pts=None, bias_pts=None, pt_scale=None,
     return out
 
 
+# ============================================================================ linear head
+@dataclass
+class LinearPlan:
+    """Linear layer over a sharded image (Sec. 4 "Other Layers", Linear): output j is the dot
+    product of the flattened feature map with row j of the weights.  w[(j, u)] holds row j on the
+    first copy (shard, then block order) of every valid pixel of shard u, zero elsewhere, so
+    duplicated channels are counted once."""
+    lin: Layout
+    n_out: int
+    w: dict = field(default_factory=dict)        # (j, u) -> float64 [N]
+    bias: np.ndarray = None                      # [n_out]
+
+    def amounts(self):
+        """The rotate-and-add shifts N/2, N/4, ..., 1."""
+        out, s = [], self.lin.N // 2
+        while s >= 1:
+            out.append(s)
+            s //= 2
+        return out
+
+
+def _first_copy_mask(lin: Layout):
+    """[n_shards][N] bool: the slot is the first copy of its (channel, row, column)."""
+    seen = set()
+    masks = np.zeros((lin.n_shards, lin.N), dtype=bool)
+    for u in range(lin.n_shards):
+        ch, y, x, valid = slot_coords(lin, u)
+        for i in np.nonzero(valid)[0]:
+            key = (int(ch[i]), int(y[i]), int(x[i]))
+            if key not in seen:
+                seen.add(key)
+                masks[u, i] = True
+    return masks
+
+
+def linear_plan(lin: Layout, W, bias=None):
+    """W [n_out][c][m][m] (the flattened input's weights), bias [n_out] or None."""
+    W = np.asarray(W, dtype=np.float64)
+    n_out = W.shape[0]
+    assert W.shape[1:] == (lin.c, lin.m, lin.m) and n_out <= lin.N
+    first = _first_copy_mask(lin)
+    plan = LinearPlan(lin, n_out, bias=np.zeros(n_out) if bias is None else np.asarray(bias, dtype=np.float64))
+    for u in range(lin.n_shards):
+        ch, y, x, valid = slot_coords(lin, u)
+        sel = first[u]
+        for j in range(n_out):
+            v = np.zeros(lin.N)
+            v[sel] = W[j, ch[sel], y[sel], x[sel]]
+            plan.w[(j, u)] = v
+    return plan
+
+
+def pool_linear_plan(lin: Layout, W, bias=None):
+    """Pool-linear (Sec. 4 "Other Layers"): every m x m channel averaged to one value, then a
+    linear layer W [n_out][c]; the weights are spread over the channel's pixels and divided by
+    the normalisation factor m^2."""
+    W = np.asarray(W, dtype=np.float64)
+    full = np.repeat(np.repeat(W[:, :, None, None], lin.m, 2), lin.m, 3) / float(lin.m * lin.m)
+    return linear_plan(lin, full, bias)
+
+
+def linear_slots(plan: LinearPlan, slots):
+    """Slot simulator: T_j = sum_u w_{j,u} * x_u, summed over all slots by rotate-and-add
+    (T += roll(T, -s) for s = N/2, ..., 1), masked to slot j and summed; plus the bias."""
+    out = np.zeros(plan.lin.N)
+    for j in range(plan.n_out):
+        T = sum(plan.w[(j, u)] * slots[u] for u in range(plan.lin.n_shards))
+        for s in plan.amounts():
+            T = T + np.roll(T, -s)
+        e = np.zeros(plan.lin.N)
+        e[j] = 1.0
+        out += e * T
+    out[: plan.n_out] += plan.bias
+    return out
+
+
+def linear_plaintexts(plan: LinearPlan, n, S_w, S_mask):
+    """Integer plaintexts: weights {(j, u)} at scale S_w, masks e_j {j} at scale S_mask."""
+    w = {k: encode(v, n, S_w) for k, v in plan.w.items()}
+    masks = {}
+    for j in range(plan.n_out):
+        e = np.zeros(plan.lin.N)
+        e[j] = 1.0
+        masks[j] = encode(e, n, S_mask)
+    return w, masks
+
+
+def linear_he(ctx, plan: LinearPlan, cts, w_pts=None, mask_pts=None, bias_pt=None):
+    """The linear layer on oracle ciphertexts (all shards at one level l >= 2, one scale):
+    T_j = Rescale(sum_u w_{j,u} * x_u) with weights at scale q_l; for s = N/2, ..., 1 the
+    hoisted rotation T_j += rot_s(T_j); out = Rescale(sum_j e_j * T_j) with masks at scale
+    q_{l-1}; plus the bias (slots 0..n_out-1) at the output scale.  Output level l - 2."""
+    level, scale = cts[0].level, cts[0].scale
+    assert level >= 2 and all(c.level == level and c.scale == scale for c in cts)
+    if w_pts is None or mask_pts is None:
+        w_pts, mask_pts = linear_plaintexts(plan, ctx.n, float(ctx.q[level]), float(ctx.q[level - 1]))
+    R = {(u, 0): ct for u, ct in enumerate(cts)}
+    terms = [(u, 0) for u in range(plan.lin.n_shards)]
+    T = []
+    for j in range(plan.n_out):
+        t = ctx.rescale(mac(ctx, R, terms, [w_pts[(j, u)] for u in range(plan.lin.n_shards)], level, scale))
+        for s in plan.amounts():
+            ctx.gen_rotation_key(s)
+            t = ctx.add_ct(t, ctx.rotate_hoisted(t, ctx.hoist(t), s))
+        T.append(t)
+    acc = mac(ctx, {(j, 0): t for j, t in enumerate(T)}, [(j, 0) for j in range(plan.n_out)],
+              [mask_pts[j] for j in range(plan.n_out)], level - 1, T[0].scale)
+    out = ctx.rescale(acc)
+    if bias_pt is None:
+        b = np.zeros(plan.lin.N)
+        b[: plan.n_out] = plan.bias
+        bias_pt = encode(b, ctx.n, out.scale)
+    out.c[0] = ctx.add(out.c[0], ctx.reduce_int(bias_pt, ctx.mods(out.level)), ctx.mods(out.level))
+    return out
+
+
 # ============================================================================ factored conv
 @dataclass
 class FactoredPlan:

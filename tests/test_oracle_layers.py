@@ -316,6 +316,52 @@ def test_plaintexts_encoded_for_a_higher_level_serve_a_lower_one():
         assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
 
 
+@pytest.mark.parametrize("c,m,N", [(4, 8, 512), (16, 8, 512), (2, 32, 512), (3, 28, 1024)])
+def test_linear_plan_is_the_dot_product(c, m, N):
+    # one duplicated shard, image shards, channel shards, a padded frame: every pixel counted once
+    rng = np.random.default_rng(c * 31 + m)
+    x = rng.uniform(-1, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (5, c, m, m))
+    b = rng.uniform(-1, 1, 5)
+    lin = Ly.image_layout(c, m, N)
+    plan = Ly.linear_plan(lin, W, b)
+    out = Ly.linear_slots(plan, Ly.pack(lin, x))
+    want = W.reshape(5, -1) @ x.reshape(-1) + b
+    assert np.abs(out[:5] - want).max() < 1e-9 and np.abs(out[5:]).max() < 1e-9
+    assert plan.amounts() == [N >> i for i in range(1, N.bit_length())]
+
+
+def test_pool_linear_is_global_average_pool_then_linear():
+    rng = np.random.default_rng(9)
+    c, m, N = 16, 8, 512                         # a ResNet tail: 8 x 8 channels, one shard
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (10, c))
+    b = rng.uniform(-1, 1, 10)
+    lin = Ly.image_layout(c, m, N)
+    out = Ly.linear_slots(Ly.pool_linear_plan(lin, W, b), Ly.pack(lin, x))
+    pooled = torch.nn.functional.adaptive_avg_pool2d(torch.tensor(x)[None], 1).reshape(-1)
+    want = torch.nn.functional.linear(pooled, torch.tensor(W), torch.tensor(b)).numpy()
+    assert np.abs(out[:10] - want).max() < 1e-12
+
+
+def test_linear_he_decrypts_to_fp64():
+    ctx = _small_ctx()
+    rng = np.random.default_rng(10)
+    c, m = 8, 8
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (4, c))
+    b = rng.uniform(-1, 1, 4)
+    lin = Ly.image_layout(c, m, ctx.N)
+    plan = Ly.pool_linear_plan(lin, W, b)
+    cts = [ctx.encrypt(Ly.pack(lin, x)[u], 3, nonce=70 + u) for u in range(lin.n_shards)]
+    out = Ly.linear_he(ctx, plan, cts)
+    assert out.level == 1 and out.scale == ctx.pr.scale
+    got = ctx.decrypt(out)
+    want = W @ x.mean(axis=(1, 2)) + b
+    assert np.abs(got[:4] - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+    assert np.abs(got[4:]).max() <= 2.0 ** -20 * (want.max() - want.min())
+
+
 def test_bsgs_he_without_giant_steps_is_the_diagonal_form():
     # channel shards: every giant amount is 0, so S_{v,0} is the diagonal MAC (per-rotation
     # form) or the diagonal raised stage, and the giant stage adds nothing: bit for bit
