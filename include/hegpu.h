@@ -57,6 +57,7 @@ typedef struct he_ct he_ct;
 typedef struct he_pt he_pt;
 typedef struct he_conv he_conv;
 typedef struct he_pool he_pool;
+typedef struct he_linear he_linear;
 typedef struct he_poly he_poly;
 
 /* Scheme parameters (Sec. 2; the paper uses ring 2^16 and 59-bit scales, Sec. 5.3).
@@ -345,6 +346,36 @@ int he_conv_import_bias(he_conv *conv, int level, double out_scale, const int64_
  * the plan and the resident plaintexts, and owns its run buffers, so forks run concurrently
  * on their own streams.  Destroy forks before the original. */
 int he_conv_fork(const he_conv *conv, he_ctx *ctx, he_conv **out);
+
+/* ------------------------------------------------------------------ linear head (Sec. 4, Other Layers) */
+/* Linear layer over a sharded image: output j = sum over the flattened (channel, row, column)
+ * features of W[j][c][m][m] x feature, + bias[j] (bias NULL: 0).  Row j is placed on the first
+ * copy (shard, then block order) of every valid pixel, so duplicated channels count once.
+ * Evaluation: T_j = Rescale(sum_u w_{j,u} (.) X_u) with the weights at scale q_level; the slot
+ * sum by rotate-and-add, T_j += rot_s(T_j) for s = N/2, ..., 1 (log2 N hoisted rotations per
+ * output, every output's rotation by s in one fused launch); out = Rescale(sum_j e_j (.) T_j)
+ * with one-hot masks e_j at scale q_{level-1}, plus the bias in slots 0..n_out-1.  The output
+ * is one ciphertext at level - 2 (he_linear_out_level) and scale in_scale, out_j in slot j.
+ * n_out <= N; level >= 2 (HE_ELEVEL).  Rotation keys: he_linear_rotations (the log2 N shifts). */
+int he_linear_create(he_ctx *ctx, const he_layout *in, const double *W, const double *bias, int n_out,
+                     int level, double in_scale, he_linear **out);
+/* Pool-linear: every m x m channel averaged to one value and a linear layer W[n_out][c] applied,
+ * fused as a linear layer whose weights are W[j][f] / m^2 on every pixel of channel f. */
+int he_pool_linear_create(he_ctx *ctx, const he_layout *in, const double *W, const double *bias, int n_out,
+                          int level, double in_scale, he_linear **out);
+void he_linear_destroy(he_linear *lin);
+int he_linear_rotations(const he_linear *lin, int32_t *amounts, size_t cap);
+int he_linear_out_level(const he_linear *lin);
+/* Key switches one run performs: n_out x log2 N. */
+int64_t he_linear_keyswitches(const he_linear *lin);
+/* Replace the encoded plaintexts by integer polynomials: weights [n_out][n_in_shards][n] at
+ * scale q_level, masks [n_out][n] at scale q_{level-1}, bias [n] at the output scale (each
+ * optional, NULL keeps the encoded one). */
+int he_linear_import_plaintexts(he_linear *lin, const int64_t *weights, const int64_t *masks,
+                                const int64_t *bias);
+/* Run on the input shards (level and scale as planned, else HE_ELEVEL); out is allocated by
+ * the caller (any level; resized to level - 2). */
+int he_linear_run(he_ctx *ctx, he_linear *lin, he_ct *const *in, he_ct *out, void *stream);
 
 /* 2x2 average pool (Sec. 4.2): downsample (2x2 ones convolution, horizontal reduction
  * Eq. 10, vertical reduction Eq. 11), consolidate 4 shards into one (Eq. 12, channel order

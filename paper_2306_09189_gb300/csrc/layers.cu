@@ -2989,6 +2989,228 @@ extern "C" int he_poly_eval_many(he_ctx *c, he_ct *const *io, int m, const doubl
     return HE_OK;
 }
 
+// ================================================================================ linear head
+// Linear layer over a sharded image (Sec. 4 "Other Layers", Linear): T_j = Rescale(sum_u w_{j,u}
+// (.) X_u) with row j of the weights on the first copy of every valid pixel (scale q_l); for
+// s = N/2, ..., 1: T_j += rot_s(T_j) (one fused raised-basis stage per shift over every j: the
+// shift key is read once for all outputs, and each output takes one ModDown, which gives the
+// bits of T_j + hoisted rotation); out = Rescale(sum_j e_j (.) T_j) with the one-hot masks at
+// scale q_{l-1}, plus the bias in slots 0..n_out-1.  Pool-linear spreads per-channel weights over
+// the m x m pixels, divided by m^2.
+struct he_linear {
+    he_ctx *c = nullptr;
+    Lay lin;
+    int n_out = 0, level = 0;
+    double in_scale = 1.0;
+    size_t pw = 0;                               // poly stride of every buffer: level l
+    std::vector<double> bias;
+    u64 *R = nullptr;                            // [n_in][2][pw] input copies
+    u64 *w = nullptr;                            // [n_out][n_in][pw] weights, Montgomery NTT form
+    u64 *mask = nullptr;                         // [n_out][l][n] masks at level l - 1
+    u64 *bias_pt = nullptr;                      // [l - 1][n] bias addend at level l - 2
+    u64 *T[2] = {nullptr, nullptr};              // [n_out][2][pw] partial sums (ping-pong)
+    u64 *acc = nullptr;                          // [2][pw]
+    mac_term *d_w = nullptr, *d_m = nullptr;     // weight MACs; mask MACs (over the final T)
+    std::vector<std::unique_ptr<FusedStage>> steps;
+    std::vector<int> shifts;
+    ~he_linear() {
+        cudaDeviceSynchronize();
+        steps.clear();
+        cudaFree(R); cudaFree(w); cudaFree(mask); cudaFree(bias_pt); cudaFree(T[0]); cudaFree(T[1]);
+        cudaFree(acc); cudaFree(d_w); cudaFree(d_m);
+    }
+};
+
+// row j of the weights on the first copy of every valid pixel of shard u; W[j][c][m][m]
+static void linear_weights(const Lay &L, const double *W, int j, int u, const std::vector<char> &first,
+                           std::vector<double> &out) {
+    out.assign(L.N, 0.0);
+    for (int i = 0; i < L.N; i++) {
+        if (!first[(size_t)u * L.N + i]) continue;
+        SlotInfo si = slot_info(L, u, i);
+        out[i] = W[(((size_t)j * L.c + si.ch) * L.m + si.y) * L.m + si.x];
+    }
+}
+
+static int linear_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int n_out, int level,
+                         double in_scale, he_linear **out) {
+    if (!c || !in || !W || !out || n_out < 1) { he_set_error("he_linear_create: bad argument"); return HE_EINVAL; }
+    if (level < 2 || level > c->L) { he_set_error("he_linear_create: level %d, the head takes two levels", level); return HE_ELEVEL; }
+    Lay lin = from_c(*in);
+    HE_TRY(check_layout(lin, c->N));
+    if (n_out > lin.N) { he_set_error("he_linear_create: %d outputs exceed %d slots", n_out, lin.N); return HE_EINVAL; }
+    std::unique_ptr<he_linear> L(new he_linear());
+    L->c = c;
+    L->lin = lin;
+    L->n_out = n_out;
+    L->level = level;
+    L->in_scale = in_scale;
+    L->pw = (size_t)(level + 1) * c->n;
+    L->bias.assign(n_out, 0.0);
+    if (bias) L->bias.assign(bias, bias + n_out);
+    for (int s = lin.N / 2; s >= 1; s /= 2) L->shifts.push_back(s);
+    const int ni = lin.ns, n = c->n;
+    // first copy (shard, then block order) of every (channel, row, column)
+    std::vector<char> first((size_t)ni * lin.N, 0), seen((size_t)lin.c * lin.m * lin.m, 0);
+    for (int u = 0; u < ni; u++)
+        for (int i = 0; i < lin.N; i++) {
+            SlotInfo si = slot_info(lin, u, i);
+            if (!si.valid) continue;
+            char &sn = seen[((size_t)si.ch * lin.m + si.y) * lin.m + si.x];
+            if (!sn) { sn = 1; first[(size_t)u * lin.N + i] = 1; }
+        }
+    HE_TRY(dev_alloc(&L->R, (size_t)ni * 2 * L->pw));
+    HE_TRY(dev_alloc(&L->w, (size_t)n_out * ni * L->pw));
+    HE_TRY(dev_alloc(&L->mask, (size_t)n_out * level * n));
+    HE_TRY(dev_alloc(&L->bias_pt, (size_t)(level - 1) * n));
+    for (int b = 0; b < 2; b++) HE_TRY(dev_alloc(&L->T[b], (size_t)n_out * 2 * L->pw));
+    HE_TRY(dev_alloc(&L->acc, 2 * L->pw));
+    std::vector<std::vector<double>> rows(ni);
+    for (int j = 0; j < n_out; j++) {
+        std::vector<const double *> vecs;
+        for (int u = 0; u < ni; u++) {
+            linear_weights(lin, W, j, u, first, rows[u]);
+            vecs.push_back(rows[u].data());
+        }
+        HE_TRY(upload_plaintexts(c, vecs, ni, (double)c->primes[level], level, L->w + (size_t)j * ni * L->pw, nullptr));
+    }
+    std::vector<double> e(lin.N, 0.0);
+    for (int j = 0; j < n_out; j++) {
+        e.assign(lin.N, 0.0);
+        e[j] = 1.0;
+        std::vector<const double *> vecs{e.data()};
+        HE_TRY(upload_plaintexts(c, vecs, 1, (double)c->primes[level - 1], level - 1, L->mask + (size_t)j * level * n,
+                                 nullptr));
+    }
+    {
+        std::vector<double> z(lin.N, 0.0);
+        for (int j = 0; j < n_out; j++) z[j] = L->bias[j];
+        std::vector<int64_t> m(n);
+        encode_slots(z.data(), n, in_scale, m.data());
+        HE_TRY(upload_addend(c, m.data(), level - 2, L->bias_pt));
+    }
+    // MAC tables: weights over the input copies; masks over the partial sums after the last shift
+    std::vector<mac_term> tw((size_t)n_out * ni), tm(n_out);
+    for (int j = 0; j < n_out; j++)
+        for (int u = 0; u < ni; u++)
+            tw[(size_t)j * ni + u] = mac_term{L->w + ((size_t)j * ni + u) * L->pw, L->R + (size_t)u * 2 * L->pw, L->pw};
+    const int fin = (int)(L->shifts.size() % 2);      // buffer holding T after the last shift
+    for (int j = 0; j < n_out; j++)
+        tm[j] = mac_term{L->mask + (size_t)j * level * n, L->T[fin] + (size_t)j * 2 * L->pw, L->pw};
+    HE_TRY(dev_alloc(&L->d_w, tw.size()));
+    HE_TRY(dev_alloc(&L->d_m, tm.size()));
+    HE_CHECK_CUDA(cudaMemcpy(L->d_w, tw.data(), tw.size() * sizeof(mac_term), cudaMemcpyHostToDevice));
+    HE_CHECK_CUDA(cudaMemcpy(L->d_m, tm.data(), tm.size() * sizeof(mac_term), cudaMemcpyHostToDevice));
+    *out = L.release();
+    return HE_OK;
+}
+
+extern "C" int he_linear_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int n_out,
+                                int level, double in_scale, he_linear **out) {
+    return linear_create(c, in, W, bias, n_out, level, in_scale, out);
+}
+
+extern "C" int he_pool_linear_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int n_out,
+                                     int level, double in_scale, he_linear **out) {
+    if (!in || !W || n_out < 1 || in->c < 1 || in->m < 1) { he_set_error("he_pool_linear_create: bad argument"); return HE_EINVAL; }
+    const int C = in->c, m = in->m;
+    std::vector<double> full((size_t)n_out * C * m * m);
+    const double norm = 1.0 / ((double)m * m);
+    for (int j = 0; j < n_out; j++)
+        for (int f = 0; f < C; f++)
+            for (int k = 0; k < m * m; k++) full[((size_t)j * C + f) * m * m + k] = W[(size_t)j * C + f] * norm;
+    return linear_create(c, in, full.data(), bias, n_out, level, in_scale, out);
+}
+
+extern "C" void he_linear_destroy(he_linear *L) { delete L; }
+
+extern "C" int he_linear_rotations(const he_linear *L, int32_t *amounts, size_t cap) {
+    if (!L) return HE_EINVAL;
+    for (size_t i = 0; i < L->shifts.size() && i < cap; i++) amounts[i] = L->shifts[i];
+    return (int)L->shifts.size();
+}
+
+extern "C" int he_linear_out_level(const he_linear *L) { return L ? L->level - 2 : HE_EINVAL; }
+
+extern "C" int64_t he_linear_keyswitches(const he_linear *L) {
+    return L ? (int64_t)L->n_out * (int64_t)L->shifts.size() : HE_EINVAL;
+}
+
+extern "C" int he_linear_import_plaintexts(he_linear *L, const int64_t *weights, const int64_t *masks,
+                                           const int64_t *bias) {
+    if (!L) return HE_EINVAL;
+    he_ctx *c = L->c;
+    const int ni = L->lin.ns, n = c->n;
+    std::vector<const double *> none;
+    if (weights)
+        for (int j = 0; j < L->n_out; j++)
+            HE_TRY(upload_plaintexts(c, none, ni, 0.0, L->level, L->w + (size_t)j * ni * L->pw,
+                                     weights + (size_t)j * ni * n));
+    if (masks)
+        for (int j = 0; j < L->n_out; j++)
+            HE_TRY(upload_plaintexts(c, none, 1, 0.0, L->level - 1, L->mask + (size_t)j * L->level * n,
+                                     masks + (size_t)j * n));
+    if (bias) HE_TRY(upload_addend(c, bias, L->level - 2, L->bias_pt));
+    return HE_OK;
+}
+
+// one fused stage per shift: sources T[b], outputs T[1-b], terms (j, j, 0, 1) and (j, j, s, 1)
+static int linear_steps(he_linear *L) {
+    if (!L->steps.empty()) return HE_OK;
+    HE_TRY(he_capture_guard("the linear head's first run"));
+    for (size_t k = 0; k < L->shifts.size(); k++) {
+        std::unique_ptr<FusedStage> F(new FusedStage());
+        F->c = L->c;
+        F->level = L->level - 1;
+        F->name = "linear head shift " + std::to_string(L->shifts[k]);
+        u64 *src = L->T[k % 2], *dst = L->T[(k + 1) % 2];
+        for (int j = 0; j < L->n_out; j++) {
+            F->add_src(src + (size_t)j * 2 * L->pw, L->pw);
+            F->add_out(dst + (size_t)j * 2 * L->pw, L->pw);
+        }
+        for (int j = 0; j < L->n_out; j++) {
+            F->add_term(j, j, 0, HE_PT_ONE);
+            F->add_term(j, j, L->shifts[k], HE_PT_ONE);
+        }
+        HE_TRY(F->build());
+        L->steps.push_back(std::move(F));
+    }
+    return HE_OK;
+}
+
+extern "C" int he_linear_run(he_ctx *c, he_linear *L, he_ct *const *in, he_ct *out, void *stream) {
+    if (!c || !L || !in || !out || L->c != c || out->ctx != c) { he_set_error("he_linear_run: bad argument"); return HE_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int lv = L->level, ni = L->lin.ns;
+    const size_t pw = L->pw;
+    for (int u = 0; u < ni; u++) {
+        if (!in[u] || in[u]->ctx != c || in[u]->level != lv || in[u]->scale != L->in_scale) {
+            he_set_error("he_linear_run: input shard %d is not at level %d / the planned scale", u, lv);
+            return HE_ELEVEL;
+        }
+        HE_TRY(k_copy_limbs(L->R + (size_t)u * 2 * pw, pw, in[u]->d, in[u]->pstride, pw, 2, s));
+    }
+    HE_TRY(linear_steps(L));
+    // T_j = Rescale(sum_u w_{j,u} (.) X_u)
+    for (int j = 0; j < L->n_out; j++) {
+        u64 *t = L->T[0] + (size_t)j * 2 * pw;
+        HE_TRY(k_mac(c, L->d_w + (size_t)j * ni, ni, t, pw, lv, false, s));
+        he_ct v = view(c, t, pw, lv, L->in_scale * (double)c->primes[lv]);
+        HE_TRY(he_rescale(c, &v, stream));
+    }
+    for (auto &F : L->steps) HE_TRY(F->run(s));
+    // out = Rescale(sum_j e_j (.) T_j) + bias
+    HE_TRY(k_mac(c, L->d_m, L->n_out, L->acc, pw, lv - 1, false, s));
+    const double t_scale = L->in_scale * (double)c->primes[lv] / (double)c->primes[lv];
+    he_ct v = view(c, L->acc, pw, lv - 1, t_scale * (double)c->primes[lv - 1]);
+    HE_TRY(he_rescale(c, &v, stream));
+    HE_TRY(k_add_raw(c, L->acc, pw, L->bias_pt, 0, lv - 1, 1, false, s));
+    HE_TRY(ensure_ct(c, out, lv - 2));
+    HE_TRY(k_copy_limbs(out->d, out->pstride, L->acc, pw, (size_t)(lv - 1) * c->n, 2, s));
+    out->scale = v.scale;
+    return HE_OK;
+}
+
 // ================================================================================ wrappers
 static int keygen_for(he_ctx *c, const std::vector<int32_t> &amts) {
     return he_keygen_rotations(c, amts.data(), amts.size());

@@ -124,6 +124,16 @@ _SIGS = {
     "he_conv_run_batch": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp), ctypes.POINTER(c_vp), c_int, c_int, c_vp]),
     "he_conv_import_bias": (c_int, [c_vp, c_int, c_double, I64P]),
     "he_pool_create": (c_int, [c_vp, ctypes.POINTER(he_layout), c_int, ctypes.POINTER(c_vp)]),
+    "he_linear_create": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_double,
+                                 ctypes.POINTER(c_vp)]),
+    "he_pool_linear_create": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_double,
+                                      ctypes.POINTER(c_vp)]),
+    "he_linear_destroy": (None, [c_vp]),
+    "he_linear_rotations": (c_int, [c_vp, I32P, c_size_t]),
+    "he_linear_out_level": (c_int, [c_vp]),
+    "he_linear_keyswitches": (ctypes.c_int64, [c_vp]),
+    "he_linear_import_plaintexts": (c_int, [c_vp, I64P, I64P, I64P]),
+    "he_linear_run": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "he_pool_destroy": (None, [c_vp]),
     "he_pool_fork": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "he_pool_out_layout": (c_int, [c_vp, ctypes.POINTER(he_layout)]),
@@ -547,6 +557,54 @@ def he_conv_run_batch(ctx, conv, ins, outs, n_img, mode=HE_FUSED, stream=None):
 def he_conv_import_bias(conv, level, out_scale, bias):
     b = np.ascontiguousarray(bias, dtype=np.int64)
     _check(load().he_conv_import_bias(conv, level, out_scale, _p(b, I64P)))
+
+
+def he_linear_create(ctx, layout, W, bias, level, in_scale):
+    """W [n_out][c][m][m]: a linear layer over the flattened sharded image."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
+    h = c_vp()
+    _check(load().he_linear_create(ctx, ctypes.byref(layout), _p(W, F64P), None if b is None else _p(b, F64P),
+                                   W.shape[0], level, in_scale, ctypes.byref(h)))
+    return h
+
+
+def he_pool_linear_create(ctx, layout, W, bias, level, in_scale):
+    """W [n_out][c]: global average pool of every channel fused with a linear layer."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
+    h = c_vp()
+    _check(load().he_pool_linear_create(ctx, ctypes.byref(layout), _p(W, F64P), None if b is None else _p(b, F64P),
+                                        W.shape[0], level, in_scale, ctypes.byref(h)))
+    return h
+
+
+def he_linear_destroy(lin):
+    load().he_linear_destroy(lin)
+
+
+def he_linear_rotations(lin):
+    n = _check(load().he_linear_rotations(lin, None, 0))
+    out = np.zeros(n, dtype=np.int32)
+    load().he_linear_rotations(lin, _p(out, I32P), n)
+    return out
+
+
+def he_linear_out_level(lin):
+    return _check(load().he_linear_out_level(lin))
+
+
+def he_linear_keyswitches(lin):
+    return int(_check(load().he_linear_keyswitches(lin)))
+
+
+def he_linear_import_plaintexts(lin, weights=None, masks=None, bias=None):
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.int64) for a in (weights, masks, bias)]
+    _check(load().he_linear_import_plaintexts(lin, *[None if a is None else _p(a, I64P) for a in arrs]))
+
+
+def he_linear_run(ctx, lin, ins, out, stream=None):
+    _check(load().he_linear_run(ctx, lin, _vp_array(ins), out, stream_ptr(stream)))
 
 
 def he_pool_create(ctx, layout, level):
