@@ -368,6 +368,97 @@ def run_block(args, ws, rank, local):
     H.he_ctx_destroy(ctx)
 
 
+HEAD_WORKLOAD = ("resnet head: 64x8x8 feature map (one shard, 8 copies), pool-linear to 10 logits "
+                 "(global average pool fused with the linear layer), batch of 8 images at level 4, "
+                 "2N=2^16, 20+5 primes")
+
+
+def run_head(args, ws, rank, local):
+    """Pool-linear head of a ResNet (Sec. 4, Other Layers) over a batch of images: per image one
+    weighted MAC per logit, log2 N rotate-and-add shifts (each one fused launch over the 10
+    logits), the one-hot mask MAC; the batch step is one CUDA graph."""
+    import torch
+    import workloads
+    from paper_2306_09189_gb300 import hegpu as H
+    from paper_2306_09189_gb300 import host
+    pr = host.cifar_params(seed=0)
+    ctx = H.he_ctx_create(pr)
+    N = H.he_ctx_info(ctx)["slots"]
+    level, n_img = 4, 8
+    x0, W, b = workloads.resnet_head(0)
+    c, m = x0.shape[0], x0.shape[1]
+    imgs = [x0] + [workloads.resnet_head(10 + i)[0] for i in range(n_img - 1)]
+    lay = H.he_layout_image(c, m, N)
+    L = H.he_pool_linear_create(ctx, lay, W, b, level, pr.scale)
+    H.he_keygen_rotations(ctx, H.he_linear_rotations(L))
+    xs = [host.encrypt_image(ctx, lay, img, level, pr.scale, nonce0=40 * i) for i, img in enumerate(imgs)]
+    ys = [H.he_ct_alloc(ctx, level - 2) for _ in range(n_img)]
+    ks_per_step = n_img * H.he_linear_keyswitches(L)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    def step():
+        for i in range(n_img):
+            H.he_linear_run(ctx, L, xs[i], ys[i], stream)
+
+    step()
+    torch.cuda.synchronize()
+    trace = args.trace
+    if trace == "ipmac" and "-> split" in H.he_ctx_tuning_log(ctx):
+        trace = "rmac"
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    H.he_trace_start(trace)
+    H.he_graph_begin(ctx, stream)
+    for _ in range(args.steps):
+        step()
+    gk = H.he_graph_end(ctx, stream)
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = H.he_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    H.he_graph_launch(gk, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = H.he_kernel_launches() - l0
+    tr = H.he_trace_stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), ws) / args.steps
+    H.he_graph_destroy(gk)
+    got = H.he_decrypt(ctx, ys[0], N)[:W.shape[0]]
+    want = W @ imgs[0].mean(axis=(1, 2)) + b
+    err = float(np.abs(got - want).max() / (want.max() - want.min()))
+    peaks, src = _peaks()
+    roof = None
+    if tr and tr["launches"]:
+        per_launch_ms = tr["ms"] / tr["launches"]
+        achieved = tr["bytes"] / tr["launches"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": trace, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                "launches": tr["launches"], "ms_per_launch": per_launch_ms,
+                "share_of_step": tr["ms"] / (ms * args.steps)}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": job_value(ks_per_step, ms, ws), "unit": "key-switches/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": HEAD_WORKLOAD, "images": n_img, "input_level": level,
+                       "key_switches_per_step": ks_per_step, "ms_per_image": ms / n_img, "cuda_graph": True,
+                       "autotuner": H.he_ctx_tuning_log(ctx).strip().splitlines()[:3],
+                       "l2": "working set below L2 (level 4: 10 partial sums of 5+5 limbs); keys %.2f GB"
+                             % (H.he_key_bytes(ctx) / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "check": {"image": 0, "max_err_rel_range": err, "tolerance": 2.0 ** -20},
+            "gpu_launches": int(launches), "roofline": roof, "clocks": clk}), flush=True)
+    H.he_ctx_check(ctx, stream)
+    H.he_linear_destroy(L)
+    for ct in [x for xi in xs for x in xi] + ys:
+        H.he_ct_free(ct)
+    H.he_ctx_destroy(ctx)
+
+
 STEM_WORKLOAD = ("imagenet stem: 3x224x224 in channel shards (256 frame, 2 shards per channel), conv7x7/2 "
                  "3->64 pad 3 in the factored form (masks, then integer weights) with the stride-2 select, "
                  "-> 112x112x64 (32 shards) -> 2x2 avgpool -> 56x56x64 (8 shards); 2N=2^16, 20+5 primes")
@@ -509,9 +600,11 @@ def main():
                     help="giant stride (blocks) of the baby-step giant-step convolutions; 0 = cost model")
     ap.add_argument("--poly", default="ps", choices=["ps", "tree"],
                     help="GELU evaluation: Paterson-Stockmeyer (default) or the binary tree")
-    ap.add_argument("--workload", default="cifar-layer", choices=["cifar-layer", "resnet-block", "imagenet-stem"],
+    ap.add_argument("--workload", default="cifar-layer",
+                    choices=["cifar-layer", "resnet-block", "imagenet-stem", "resnet-head"],
                     help="cifar-layer: the headline layer; resnet-block: the batched mixed-level block; "
-                         "imagenet-stem: the channel-shard stem with stride 2 and average pool")
+                         "imagenet-stem: the channel-shard stem with stride 2 and average pool; "
+                         "resnet-head: the pool-linear head")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -523,8 +616,9 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    if args.workload in ("resnet-block", "imagenet-stem"):
-        (run_block if args.workload == "resnet-block" else run_stem)(args, ws, rank, local)
+    if args.workload in ("resnet-block", "imagenet-stem", "resnet-head"):
+        {"resnet-block": run_block, "imagenet-stem": run_stem, "resnet-head": run_head}[args.workload](
+            args, ws, rank, local)
         if ws > 1:
             torch.distributed.destroy_process_group()
         return

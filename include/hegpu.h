@@ -347,6 +347,20 @@ int he_conv_import_bias(he_conv *conv, int level, double out_scale, const int64_
  * on their own streams.  Destroy forks before the original. */
 int he_conv_fork(const he_conv *conv, he_ctx *ctx, he_conv **out);
 
+/* ------------------------------------------------------------------ polynomial approximation (Appendix) */
+/* Activation functions: GELU x Phi(x) (exact erf), ReLU, SiLU x / (1 + e^-x), Softplus. */
+#define HE_FN_GELU 0
+#define HE_FN_RELU 1
+#define HE_FN_SILU 2
+#define HE_FN_SOFTPLUS 3
+/* Minimax (best uniform) polynomial of degree deg to activation fn on [lo, hi] by the Remez
+ * exchange algorithm (the alternative to Chebyshev interpolation in the approximation table of
+ * the Appendix): coeffs[0..deg] (caller-owned) receive c_k with p(x) = sum c_k T_k(t),
+ * t = (2x - lo - hi)/(hi - lo), the form he_poly_eval / he_poly_eval_ps take; err (optional)
+ * the levelled maximum error.  Host only (no device, no context).  HE_EINVAL for a bad
+ * function id, deg outside 0..200 or hi <= lo; HE_ESTATE if the exchange degenerates. */
+int he_cheb_minimax(int fn, int deg, double lo, double hi, double *coeffs, double *err);
+
 /* ------------------------------------------------------------------ linear head (Sec. 4, Other Layers) */
 /* Linear layer over a sharded image: output j = sum over the flattened (channel, row, column)
  * features of W[j][c][m][m] x feature, + bias[j] (bias NULL: 0).  Row j is placed on the first

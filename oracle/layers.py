@@ -946,6 +946,95 @@ def cheb_eval(c, x, lo, hi):
     return acc
 
 
+def minimax_coeffs(f, deg, lo, hi, iters=80, tol=1e-10):
+    """Best uniform (minimax) approximation of degree deg to f on [lo, hi] by the Remez exchange
+    algorithm (Appendix, 'Chebyshev Basis': the alternative to Chebyshev interpolation whose
+    errors the approximation table also lists).  Chebyshev coefficients on [lo, hi] as in
+    cheb_nodes_coeffs; returns (c, E) with E the levelled error.
+
+    Start from the deg+2 Chebyshev extrema; each step solves p(x_i) + (-1)^i E = f(x_i) on the
+    reference, then takes as the new reference one extremum of f - p per run of constant sign
+    (scanned on a fine grid and refined by golden-section search), keeping deg+2 of them with
+    alternating signs; stop when the largest error equals |E| to a relative tol."""
+    n = deg + 2
+    fv = np.vectorize(f, otypes=[np.float64])
+
+    def X(t):
+        return 0.5 * (hi - lo) * np.asarray(t) + 0.5 * (hi + lo)
+
+    def err(t, c):
+        return fv(X(t)) - cheb_eval(c, X(t), lo, hi)
+
+    tg = np.unique(np.concatenate([np.cos(np.pi * np.arange(400 * n + 1) / (400 * n)), [0.0]]))
+    fg = fv(X(tg))
+    ref = np.cos(np.pi * np.arange(n) / (n - 1))[::-1].copy()
+    for _ in range(iters):
+        A = np.zeros((n, n))
+        T0, T1 = np.ones(n), ref.copy()
+        A[:, 0] = T0
+        if deg >= 1:
+            A[:, 1] = T1
+        for k in range(2, deg + 1):
+            T0, T1 = T1, 2.0 * ref * T1 - T0
+            A[:, k] = T1
+        A[:, deg + 1] = (-1.0) ** np.arange(n)
+        sol = np.linalg.solve(A, fv(X(ref)))
+        c, E = sol[: deg + 1], sol[deg + 1]
+        r = fg - cheb_eval(c, X(tg), lo, hi)
+        # one extremum per run of constant sign
+        sg = np.sign(r)
+        ext = []
+        i = 0
+        while i < len(tg):
+            j = i
+            while j + 1 < len(tg) and sg[j + 1] == sg[i]:
+                j += 1
+            k = i + int(np.argmax(np.abs(r[i:j + 1])))
+            ext.append(k)
+            i = j + 1
+        # refine each by golden-section search between its grid neighbours
+        pts, vals = [], []
+        gr = (math.sqrt(5.0) - 1.0) / 2.0
+        for k in ext:
+            a, b = tg[max(k - 1, 0)], tg[min(k + 1, len(tg) - 1)]
+            s_ = np.sign(r[k]) if r[k] != 0 else 1.0
+            x1, x2 = b - gr * (b - a), a + gr * (b - a)
+            f1, f2 = s_ * err(x1, c), s_ * err(x2, c)
+            for _ in range(60):
+                if f1 > f2:
+                    b, x2, f2 = x2, x1, f1
+                    x1 = b - gr * (b - a)
+                    f1 = s_ * err(x1, c)
+                else:
+                    a, x1, f1 = x1, x2, f2
+                    x2 = a + gr * (b - a)
+                    f2 = s_ * err(x2, c)
+            cand = [(s_ * r[k], tg[k]), (f1, x1), (f2, x2)]
+            best = max(cand)
+            pts.append(best[1])
+            vals.append(s_ * best[0])
+        pts, vals = list(pts), list(vals)
+        while len(pts) > n:                      # keep n alternating extrema
+            if len(pts) == n + 1:
+                drop = 0 if abs(vals[0]) < abs(vals[-1]) else len(pts) - 1
+                del pts[drop], vals[drop]
+                continue
+            k = int(np.argmin(np.abs(vals)))
+            if k == 0 or k == len(pts) - 1:
+                del pts[k], vals[k]
+            else:
+                kk = k - 1 if abs(vals[k - 1]) < abs(vals[k + 1]) else k + 1
+                for d in sorted((k, kk), reverse=True):
+                    del pts[d], vals[d]
+        if len(pts) < n:
+            raise RuntimeError("Remez: fewer alternation points than deg + 2")
+        ref = np.array(pts)
+        emax = max(abs(v) for v in vals)
+        if emax - abs(E) <= tol * emax:
+            break
+    return c, abs(E)
+
+
 def gelu(x):
     return 0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0)))
 

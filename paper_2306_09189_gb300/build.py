@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhegpu.so")
-SOURCES = ["kernels.cu", "context.cu", "layers.cu", "encode.cpp", "noalloc.cu"]
+SOURCES = ["kernels.cu", "context.cu", "layers.cu", "encode.cpp", "approx.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "--fmad=false", "-I", os.path.join(ROOT, "include")]

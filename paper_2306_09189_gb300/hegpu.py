@@ -129,6 +129,7 @@ _SIGS = {
     "he_pool_linear_create": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_double,
                                       ctypes.POINTER(c_vp)]),
     "he_linear_destroy": (None, [c_vp]),
+    "he_cheb_minimax": (c_int, [c_int, c_int, c_double, c_double, F64P, F64P]),
     "he_linear_rotations": (c_int, [c_vp, I32P, c_size_t]),
     "he_linear_out_level": (c_int, [c_vp]),
     "he_linear_keyswitches": (ctypes.c_int64, [c_vp]),
@@ -605,6 +606,17 @@ def he_linear_import_plaintexts(lin, weights=None, masks=None, bias=None):
 
 def he_linear_run(ctx, lin, ins, out, stream=None):
     _check(load().he_linear_run(ctx, lin, _vp_array(ins), out, stream_ptr(stream)))
+
+
+HE_FN_GELU, HE_FN_RELU, HE_FN_SILU, HE_FN_SOFTPLUS = 0, 1, 2, 3
+
+
+def he_cheb_minimax(fn, deg, lo, hi):
+    """(coefficients [deg + 1], levelled error) of the minimax polynomial (Remez)."""
+    c = np.zeros(deg + 1, dtype=np.float64)
+    e = np.zeros(1, dtype=np.float64)
+    _check(load().he_cheb_minimax(fn, deg, lo, hi, _p(c, F64P), _p(e, F64P)))
+    return c, float(e[0])
 
 
 def he_pool_create(ctx, layout, level):

@@ -83,6 +83,13 @@ def chebyshev_coeffs(f, deg, lo, hi):
     return c
 
 
+def minimax_coeffs(fn, deg, lo, hi):
+    """The minimax polynomial of an activation ("gelu", "relu", "silu", "softplus") by the
+    library's Remez routine: (c_0..c_deg in the same Chebyshev form, levelled error)."""
+    ids = {"gelu": H.HE_FN_GELU, "relu": H.HE_FN_RELU, "silu": H.HE_FN_SILU, "softplus": H.HE_FN_SOFTPLUS}
+    return H.he_cheb_minimax(ids[fn], deg, lo, hi)
+
+
 # ----------------------------------------------------------------------------- images
 def encrypt_image(ctx, lay, img, level, scale, nonce0=0, stream=None):
     slots = pack(lay, img)

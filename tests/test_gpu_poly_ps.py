@@ -51,3 +51,23 @@ def test_ps_bit_exact(deep, deg, levels):
     want = Ly.cheb_eval(c, 8 * z, -8, 8)
     got = H.he_decrypt(g.h, gcs[0], o.N)
     assert np.abs(got - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+
+
+def test_ps_minimax_gelu_degree_59(deep):
+    # the paper's degree-59 GELU on [-16, 16] in its minimax form (the oracle's Remez routine):
+    # bit for bit against the oracle's evaluator, and within the minimax error of GELU itself
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = deep
+    c, E = Ly.minimax_coeffs(Ly.gelu, 59, -16, 16)
+    z = np.random.default_rng(59).uniform(-1, 1, o.N)
+    ct = o.encrypt(z, 9, nonce=4059)
+    ref = Ly.cheb_ps_he(o, ct, c, target_scale=o.pr.scale)
+    gc = g.upload(ct)
+    H.he_poly_eval_ps(g.h, gc, c, o.pr.scale)
+    H.he_ctx_check(g.h)
+    assert H.he_ct_level(gc) == ref.level == 9 - 6
+    assert_ct_equal(g.download(gc), ref)
+    got = H.he_decrypt(g.h, gc, o.N)
+    want = np.array([Ly.gelu(16 * v) for v in z])
+    assert np.abs(got - want).max() <= E + 2.0 ** -20 * (want.max() - want.min())

@@ -143,15 +143,73 @@ def test_strided_conv_is_conv_then_top_left_select():
     assert np.abs(Ly.unpack(pp.lout, out) - ref).max() < 1e-12
 
 
+def _table(method):
+    return [l.split()[1:] for l in open(os.path.join(GOLD, "poly_approx_table.txt"))
+            if l.strip() and not l.startswith("#") and l.split()[0] == method]
+
+
 def test_chebyshev_nodes_table_from_the_paper():
-    rows = [l.split() for l in open(os.path.join(GOLD, "poly_approx_table.txt"))
-            if l.strip() and not l.startswith("#")]
+    rows = _table("chebyshev")
+    assert len(rows) == 2
     xs = np.linspace(-16, 16, 100001)
-    for _, deg, relu_err, gelu_err in rows:
+    for deg, relu_err, gelu_err in rows:
         for f, want in ((Ly.relu, relu_err), (Ly.gelu, gelu_err)):
             c = Ly.cheb_nodes_coeffs(f, int(deg), -16, 16)
             err = np.abs(Ly.cheb_eval(c, xs, -16, 16) - np.array([f(v) for v in xs])).max()
             assert round(err, 4) == float(want), (deg, f.__name__, err)
+
+
+@pytest.fixture(scope="module")
+def minimax16():
+    return {(f.__name__, d): Ly.minimax_coeffs(f, d, -16, 16) for f in (Ly.relu, Ly.gelu) for d in (27, 59)}
+
+
+def test_minimax_table_from_the_paper(minimax16):
+    # GELU rows: the printed digits.  ReLU rows: the exact minimax error sits at most 2% below
+    # the printed value (a minimax error cannot exceed any approximation's, and the paper's
+    # routine stopped slightly short of the optimum); it is the Bernstein limit
+    # E_{2k}(|x|) ~ beta / 2k with beta = 0.2801694990..., times 16 / 2 for ReLU = (x + |x|)/2
+    rows = _table("minimax")
+    assert len(rows) == 2
+    for deg, relu_err, gelu_err in rows:
+        d = int(deg)
+        _, Eg = minimax16[("gelu", d)]
+        _, Er = minimax16[("relu", d)]
+        assert round(Eg, 4) == float(gelu_err), (d, Eg)
+        assert 0.98 * float(relu_err) <= Er <= float(relu_err), (d, Er)
+        assert abs(Er / 8.0 * (d - 1) / 0.2801694990 - 1.0) < 3e-3
+        # optimality: below the Chebyshev-node interpolant of the same degree
+        for f, E in ((Ly.relu, Er), (Ly.gelu, Eg)):
+            xs = np.linspace(-16, 16, 20001)
+            c = Ly.cheb_nodes_coeffs(f, d, -16, 16)
+            assert E < np.abs(Ly.cheb_eval(c, xs, -16, 16) - np.array([f(v) for v in xs])).max()
+
+
+def test_minimax_equioscillates(minimax16):
+    # the characterisation theorem: the error reaches +-E alternately at deg + 2 points and
+    # nowhere exceeds E
+    for (name, d), (c, E) in minimax16.items():
+        f = getattr(Ly, name)
+        xs = np.linspace(-16, 16, 400001)
+        r = np.array([f(v) for v in xs]) - Ly.cheb_eval(c, xs, -16, 16)
+        assert np.abs(r).max() <= E * (1 + 1e-7)
+        near = np.nonzero(np.abs(r) >= E * (1 - 1e-3))[0]
+        signs = [np.sign(r[near[0]])]
+        for i in near[1:]:
+            if np.sign(r[i]) != signs[-1]:
+                signs.append(np.sign(r[i]))
+        assert len(signs) >= d + 2, (name, d, len(signs))
+
+
+def test_minimax_wide_range_claims():
+    # ReLU is homogeneous, so its minimax error scales with the range; on [-65, 65] GELU's
+    # degree-59 minimax error is only about 1.2x below ReLU's (Appendix), against two orders of
+    # magnitude on [-16, 16]
+    _, Er16 = Ly.minimax_coeffs(Ly.relu, 59, -16, 16)
+    _, Er65 = Ly.minimax_coeffs(Ly.relu, 59, -65, 65)
+    _, Eg65 = Ly.minimax_coeffs(Ly.gelu, 59, -65, 65)
+    assert abs(Er65 / Er16 - 65.0 / 16.0) < 1e-6
+    assert 1.15 <= Er65 / Eg65 <= 1.35
 
 
 def test_binary_tree_chebyshev_recursion_and_depth():

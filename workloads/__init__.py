@@ -87,6 +87,15 @@ def resnet_block(seed=0, c=64, m=56):
     return x, (W1f, b1f), (W2 / 8.0, np.zeros(c))
 
 
+def resnet_head(seed=0, c=64, m=8, n_out=10):
+    """ResNet tail: a c x m x m feature map (post-GELU range), global average pool and a linear
+    layer to n_out logits with PyTorch's default init U[+-1/sqrt(c)]."""
+    rng = np.random.default_rng(seed + 3)
+    x = rng.uniform(-0.2, 1.0, (c, m, m))
+    bound = 1.0 / math.sqrt(c)
+    return x, rng.uniform(-bound, bound, (n_out, c)), rng.uniform(-bound, bound, n_out)
+
+
 def poisson_arrivals(n, rate, seed=0):
     """Arrival times (seconds) of n requests at `rate` requests/second."""
     rng = np.random.default_rng(seed)
