@@ -172,6 +172,15 @@ int k_copy_limbs(u64 *dst, size_t dst_pstride, const u64 *src, size_t src_pstrid
 // Key switching.  D: [beta][level+1+K][n]; u: [2][level+1+K][n]; conv: [2][level+1][n].
 int k_modup(const he_ctx *ctx, const u64 *x_coef, const u64 *x_ntt, u64 *D, int level,
             cudaStream_t s);
+// ModUp of several sources at one level in three launch sets: gather every c1 (NTT form) into
+// tmp [n_src][level+1][n], one INTT, one base-conversion launch writing each source's digits
+// at its D ([beta][level+1+K][n], coefficient form except the digit's own limbs); the digits'
+// forward NTT is the caller's (one job over all of them)
+struct modup_src {
+    const u64 *c1;          // source c1, NTT form, [level+1][n]
+    u64 *D;                 // its raised digits
+};
+int k_modup_batch(const he_ctx *ctx, const modup_src *d_tab, int n_src, u64 *tmp, int level, cudaStream_t s);
 struct ip_item {            // one key-switching inner product
     const u64 *D;           // raised digits
     const u64 *key;         // key [dnum][2][L+1+K][n]

@@ -469,23 +469,23 @@ struct ModupArgs {
     int level, alpha;
     const u64 *tab[16];
 };
-__global__ void __launch_bounds__(TB) modup_kernel(KP kp, ModupArgs A) {
-    const int k = blockIdx.x * TB + threadIdx.x;
-    const int j = blockIdx.y;
+// digit j of one source: x_coef = c1 in coefficient form, x_ntt = c1 in NTT form, D its digits
+__device__ __forceinline__ void modup_digit(const KP &kp, const ModupArgs &A, const u64 *x_coef, const u64 *x_ntt,
+                                            u64 *D, int k, int j) {
     const int nq = A.level + 1;
     const int ext = nq + kp.K;
     const int lo = j * A.alpha;
     const int ns = min(A.alpha, nq - lo);
     const u64 *tab = A.tab[j];
-    u64 *Dj = A.D + (size_t)j * ext * kp.n;
+    u64 *Dj = D + (size_t)j * ext * kp.n;
     u64 y[16];
 #pragma unroll
     for (int i = 0; i < 16; i++) {
         if (i < ns) {
             const int pr = lo + i;
-            u64 xv = A.x_coef[(size_t)pr * kp.n + k];
+            u64 xv = x_coef[(size_t)pr * kp.n + k];
             y[i] = mul_shoup(xv, tab[i], tab[ns + i], kp.q[pr]);
-            Dj[(size_t)pr * kp.n + k] = A.x_ntt[(size_t)pr * kp.n + k];
+            Dj[(size_t)pr * kp.n + k] = x_ntt[(size_t)pr * kp.n + k];
         }
     }
     const u64 *hat = tab + 2 * ns;
@@ -500,6 +500,23 @@ __global__ void __launch_bounds__(TB) modup_kernel(KP kp, ModupArgs A) {
             if (i < ns) acc += (u128)y[i] * h[i];
         Dj[(size_t)limb * kp.n + k] = redc(acc, kp.q[pr], kp.qinv[pr]);
     }
+}
+
+__global__ void __launch_bounds__(TB) modup_kernel(KP kp, ModupArgs A) {
+    modup_digit(kp, A, A.x_coef, A.x_ntt, A.D, blockIdx.x * TB + threadIdx.x, blockIdx.y);
+}
+
+// several sources in one launch (blockIdx.z): coefficient-form c1 at x_coef + z nq n
+__global__ void __launch_bounds__(TB) modup_batch_kernel(KP kp, ModupArgs A, const modup_src *tab) {
+    const int z = blockIdx.z;
+    const size_t nqn = (size_t)(A.level + 1) * kp.n;
+    modup_digit(kp, A, A.x_coef + z * nqn, tab[z].c1, tab[z].D, blockIdx.x * TB + threadIdx.x, blockIdx.y);
+}
+
+// c1 (NTT form) of every source into one contiguous [n_src][words] buffer
+__global__ void gather_c1_kernel(const modup_src *tab, u64 *dst, size_t words) {
+    const size_t k = (size_t)blockIdx.x * TB + threadIdx.x;
+    if (k < words) dst[(size_t)blockIdx.y * words + k] = tab[blockIdx.y].c1[k];
 }
 
 // ------------------------------------------------------------------------------ inner product
@@ -1465,6 +1482,35 @@ int k_copy_limbs(u64 *dst, size_t dps, const u64 *src, size_t sps, size_t words,
                  cudaStream_t s) {
     copy_kernel<<<dim3((unsigned)((words + TB - 1) / TB), npoly), TB, 0, s>>>(dst, dps, src, sps, words);
     LAUNCH_CHECK();
+    return HE_OK;
+}
+
+int k_modup_batch(const he_ctx *ctx, const modup_src *d_tab, int n_src, u64 *tmp, int level, cudaStream_t s) {
+    if (n_src <= 0) return HE_OK;
+    const int nq = level + 1, ext = nq + ctx->K;
+    const int beta = (level + ctx->alpha) / ctx->alpha;
+    if (beta > 16 || ctx->alpha > 16 || n_src > 65535) {
+        he_set_error("modup: at most 16 digits of at most 16 primes, 65535 sources");
+        return HE_EINVAL;
+    }
+    const size_t words = (size_t)nq * ctx->n;
+    gather_c1_kernel<<<dim3((unsigned)((words + TB - 1) / TB), n_src), TB, 0, s>>>(d_tab, tmp, words);
+    LAUNCH_CHECK();
+    ntt_job ji{tmp, words, 0, nq, nq, 0, n_src, 0};
+    HE_TRY(k_ntt(ctx, ji, true, s));
+    ModupArgs A;
+    A.x_coef = tmp;
+    A.x_ntt = nullptr;
+    A.D = nullptr;
+    A.level = level;
+    A.alpha = ctx->alpha;
+    for (int j = 0; j < beta; j++) A.tab[j] = ctx->modup[level][j].d;
+    {
+        TraceScope tr("modup", s, (double)n_src * (nq + beta * ext) * ctx->n * 8,
+                      (double)n_src * (nq + (double)beta * (ext - ctx->alpha) * ctx->alpha) * ctx->n);
+        modup_batch_kernel<<<dim3(ctx->n / TB, beta, n_src), TB, 0, s>>>(ctx->kp, A, d_tab);
+        LAUNCH_CHECK();
+    }
     return HE_OK;
 }
 

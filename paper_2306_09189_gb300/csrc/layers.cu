@@ -354,12 +354,15 @@ struct RotSet {
     std::vector<const DeviceKey *> keys;
     size_t chunk = 0;
     u64 *D_all = nullptr, *u_all = nullptr, *conv_all = nullptr;
+    u64 *htmp = nullptr;                                       // [src][nq][n] gathered c1
+    modup_src *d_hsrc = nullptr;
     ip_item *d_ip = nullptr;
     md_item *d_md = nullptr;
     bool batched_ready = false;
 
     ~RotSet() {
         cudaFree(D_all); cudaFree(u_all); cudaFree(conv_all); cudaFree(d_ip); cudaFree(d_md);
+        cudaFree(htmp); cudaFree(d_hsrc);
     }
     size_t nq() const { return (size_t)level + 1; }
     size_t pw() const { return nq() * c->n; }
@@ -383,6 +386,13 @@ struct RotSet {
         if (batched_ready || items.empty()) { batched_ready = true; return HE_OK; }
         chunk = autotune_chunk(c, level, items.size());
         HE_TRY(dev_alloc(&D_all, src.size() * (size_t)beta() * ext()));
+        HE_TRY(dev_alloc(&htmp, src.size() * pw()));
+        {
+            std::vector<modup_src> hs(src.size());
+            for (size_t u = 0; u < src.size(); u++) hs[u] = modup_src{src[u].d + src[u].ps, D_all + u * (size_t)beta() * ext()};
+            HE_TRY(dev_alloc(&d_hsrc, hs.size()));
+            HE_CHECK_CUDA(cudaMemcpy(d_hsrc, hs.data(), hs.size() * sizeof(modup_src), cudaMemcpyHostToDevice));
+        }
         HE_TRY(dev_alloc(&u_all, chunk * 2 * ext()));
         HE_TRY(dev_alloc(&conv_all, chunk * 2 * pw()));
         std::vector<ip_item> ip(items.size());
@@ -423,9 +433,11 @@ struct RotSet {
             return HE_OK;
         }
         if (!batched_ready) HE_TRY(prepare_batched());
-        for (size_t u = 0; u < src.size(); u++) {
-            he_ct t = view(c, src[u].d, src[u].ps, level, 1.0);
-            HE_TRY(hoist_modup(c, &t, D_all + u * (size_t)beta() * ext(), s));
+        // every source's ModUp in one launch set
+        HE_TRY(k_modup_batch(c, d_hsrc, (int)src.size(), htmp, level, s));
+        {
+            ntt_job jd{D_all, ext(), 0, (int)nq() + c->K, (int)nq(), c->alpha, beta() * (int)src.size(), beta()};
+            HE_TRY(k_ntt(c, jd, false, s));
         }
         const int nqi = (int)nq();
         for (size_t i0 = 0; i0 < items.size(); i0 += chunk) {
@@ -469,7 +481,10 @@ struct FusedStage {
     };
     std::vector<Group> groups;                        // for outputs-per-key-pass Vg
     std::vector<int> hslot;                           // source -> slot in D_all (-1: not rotated)
+    int nh = 0;                                       // rotated sources
     u64 *D_all = nullptr;
+    u64 *htmp = nullptr;                              // [nh][nq][n] c1 of the rotated sources
+    modup_src *d_hsrc = nullptr;                      // [nh] their c1 and digit slots
     u64 *facc = nullptr, *fconv = nullptr;            // [nout][2][ext|nq][n]
     md_item *d_md = nullptr;
     bool ready = false;
@@ -522,10 +537,19 @@ struct FusedStage {
         for (auto &t : terms)
             if (h_galois(c, t.a) != 1) srcs[t.s].rotated = true;
         hslot.assign(srcs.size(), -1);
-        int nh = 0;
+        nh = 0;
         for (size_t i = 0; i < srcs.size(); i++)
             if (srcs[i].rotated) hslot[i] = nh++;
         HE_TRY(dev_alloc(&D_all, (size_t)nh * beta() * ext() * n));
+        if (nh > 0) {
+            HE_TRY(dev_alloc(&htmp, (size_t)nh * nq() * n));
+            std::vector<modup_src> hs(nh);
+            for (size_t i = 0; i < srcs.size(); i++)
+                if (hslot[i] >= 0)
+                    hs[hslot[i]] = modup_src{srcs[i].d + srcs[i].ps, D_all + (size_t)hslot[i] * beta() * ext() * n};
+            HE_TRY(dev_alloc(&d_hsrc, hs.size()));
+            HE_CHECK_CUDA(cudaMemcpy(d_hsrc, hs.data(), hs.size() * sizeof(modup_src), cudaMemcpyHostToDevice));
+        }
         // a group stores only the outputs it has (fgrp.nv, rgrp.nv): no padding needed
         const size_t nslot = nout;
         HE_TRY(dev_alloc(&facc, nslot * 2 * ext() * n));
@@ -550,8 +574,6 @@ struct FusedStage {
         Vg = V;
         const int nq_ = nq(), ext_ = ext(), beta_ = beta();
         const size_t n = c->n;
-        int nh = 0;
-        for (int h : hslot) nh += h >= 0;
         std::vector<const u64 *> Dp(srcs.size());
         for (size_t i = 0; i < srcs.size(); i++)
             Dp[i] = hslot[i] >= 0 ? D_all + (size_t)hslot[i] * beta_ * ext_ * n : nullptr;
@@ -612,13 +634,13 @@ struct FusedStage {
         return HE_OK;
     }
 
+    // ModUp of every rotated source: one gather, one INTT, one base conversion and one NTT
+    // launch set for all of them (the bits of a ModUp per source)
     int hoist(cudaStream_t s) {
-        for (size_t i = 0; i < srcs.size(); i++)
-            if (hslot[i] >= 0) {
-                he_ct t = view(c, srcs[i].d, srcs[i].ps, level, 1.0);
-                HE_TRY(hoist_modup(c, &t, D_all + (size_t)hslot[i] * beta() * ext() * c->n, s));
-            }
-        return HE_OK;
+        if (nh == 0) return HE_OK;
+        HE_TRY(k_modup_batch(c, d_hsrc, nh, htmp, level, s));
+        ntt_job j{D_all, (size_t)ext() * c->n, 0, ext(), nq(), c->alpha, beta() * nh, beta()};
+        return k_ntt(c, j, false, s);
     }
 
     // one ModDown pipeline for every output of the stage
@@ -1006,7 +1028,7 @@ FusedStage::~FusedStage() {
     own.reset();
     free_split();
     free_groups();
-    cudaFree(D_all); cudaFree(facc); cudaFree(fconv); cudaFree(d_md);
+    cudaFree(D_all); cudaFree(facc); cudaFree(fconv); cudaFree(d_md); cudaFree(htmp); cudaFree(d_hsrc);
 }
 
 int FusedStage::run(cudaStream_t s) {
