@@ -129,6 +129,11 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  *   HE_KEY_STREAM_CP (4): every word of an (amount, source) item (key words, gathered digits,
  *     plaintexts, source words) copied by each thread with cp.async into its own shared-memory
  *     slots, two items ahead of the one it computes (no block barrier).  Up to 4 digits;
+ *   HE_KEY_STREAM_PK (6): pre-keyed: for stages where every output takes at most one source
+ *     per rotation amount, each amount's key is multiplied by the output's plaintext once
+ *     (K (.) pt, built on first use; the key itself when the plaintext is 1), and the kernel
+ *     accumulates sum_j D_j (K (.) pt)_j without per-amount reductions or a plaintext stream.
+ *     Other stages fall back to the LDG form;
  *   HE_KEY_STREAM_SPLIT (3): the split form: the raised inner product of every (source,
  *     amount) is written to HBM once (each key read once), then a raised-basis MAC forms the
  *     plaintext-weighted sums of 4 outputs per pass; amounts go in chunks of at most 2 GB of
@@ -144,6 +149,7 @@ int he_ctx_check(he_ctx *ctx, void *stream);
 #define HE_KEY_STREAM_SPLIT 3
 #define HE_KEY_STREAM_CP 4
 #define HE_KEY_STREAM_LDG1 5
+#define HE_KEY_STREAM_PK 6
 int he_ctx_set_option(he_ctx *ctx, int option, int value);
 int he_ctx_get_option(const he_ctx *ctx, int option, int *value);
 /* The autotuner's decisions so far (one line per tuned stage: the candidates' times and the

@@ -180,6 +180,9 @@ struct modup_src {
     const u64 *c1;          // source c1, NTT form, [level+1][n]
     u64 *D;                 // its raised digits
 };
+// K' = key (.) pt on the limbs of Q_level u P (key layout) and Ppt = [P]_q (.) pt on the q-limbs
+int k_prekey(const he_ctx *ctx, const u64 *key, const u64 *pt, int level, int pt_level, int beta, u64 *Kp, u64 *Ppt,
+             cudaStream_t s);
 int k_modup_batch(const he_ctx *ctx, const modup_src *d_tab, int n_src, u64 *tmp, int level, cudaStream_t s);
 struct ip_item {            // one key-switching inner product
     const u64 *D;           // raised digits

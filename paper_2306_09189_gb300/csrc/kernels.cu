@@ -1270,6 +1270,103 @@ __global__ void __launch_bounds__(TB, 3) ipmac1_kernel(KP kp, const fgrp *grps, 
             P.acc[((size_t)(2 * v + 1) * ext) * kp.n + off] = redc(a1[v], q, qi);
         }
 }
+// ---- pre-keyed form: for a group whose every amount has one (source, output) term, the
+// plaintext is folded into the key once (K' = K (.) pt, Montgomery) and into the unrotated part
+// (P pt on the q-limbs), so per amount and coefficient the thread forms sum_j D_j K'_j plus
+// c0 P pt directly into its 128-bit accumulators: no per-amount Montgomery reduction and no
+// plaintext stream.  Terms are below p^2 < 2^100; a launch adds at most (beta + 1) per
+// amount, far below 2^28 terms, so the 128-bit sums cannot wrap.  fent.pt[0] holds P pt
+// ([l+1][n], Montgomery) or HE_PT_ONE for the integer 1 (then K' is the key itself).
+template <int B>
+__global__ void __launch_bounds__(TB, 2) ipmac_pk_kernel(KP kp, const fgrp *grps, int n_grp, int gb, const u64 *pmod) {
+    fgrp P;
+    int tile, t, ptl;
+    if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl)) return;
+    const int k = 2 * (tile * TB + threadIdx.x);
+    const int kl = blockIdx.y;
+    const int nq = P.level + 1;
+    const int ext = nq + kp.K;
+    const int beta = P.beta;
+    const bool isq = t < nq;
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 Pm = isq ? to_mont(pmod[kl], q, qi, r2) : 0;
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    const size_t off = (size_t)t * kp.n + k;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    u128 a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+    const int n_amt = P.n_amt;
+    famt A = n_amt > 0 ? P.amts[0] : famt{};
+    fent E = (n_amt > 0 && A.e0 < A.e1) ? P.ents[A.e0] : fent{};
+    for (int i = 0; i < n_amt; i++) {
+        famt An{};
+        fent En{};
+        if (i + 1 < n_amt) {
+            An = P.amts[i + 1];
+            if (An.e0 < An.e1) En = P.ents[An.e0];
+        }
+        if (A.e0 < A.e1) {
+            const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
+            const int sw = ks & 1, kb = ks & ~1;
+            if (A.key) {
+                ulonglong2 kk0[B], kk1[B];
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+                        kk0[j] = ld2_hint(kp0, stream);
+                        kk1[j] = ld2_hint(kp0 + kstride, stream);
+                    }
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        const ulonglong2 d = ld2_hint(E.D + ((size_t)j * ext + t) * kp.n + kb, keep);
+                        const u64 d0 = sw ? d.y : d.x, d1 = sw ? d.x : d.y;
+                        a00 += (u128)d0 * kk0[j].x;
+                        a01 += (u128)d1 * kk0[j].y;
+                        a10 += (u128)d0 * kk1[j].x;
+                        a11 += (u128)d1 * kk1[j].y;
+                    }
+            }
+            if (isq) {
+                const ulonglong2 pp = E.pt[0] == HE_PT_ONE ? make_ulonglong2(Pm, Pm)
+                                                           : ld2_hint(E.pt[0] + (size_t)t * kp.n + k, stream);
+                const ulonglong2 cc = ld2_hint(E.src + (size_t)t * kp.n + kb, keep);
+                a00 += (u128)(sw ? cc.y : cc.x) * pp.x;
+                a01 += (u128)(sw ? cc.x : cc.y) * pp.y;
+                if (!A.key) {
+                    const ulonglong2 c1 = ld2_hint(E.src + E.ps + off, keep);
+                    a10 += (u128)c1.x * pp.x;
+                    a11 += (u128)c1.y * pp.y;
+                }
+            }
+        }
+        A = An;
+        E = En;
+    }
+    st2(P.acc + off, redc(a00, q, qi), redc(a01, q, qi));
+    st2(P.acc + (size_t)ext * kp.n + off, redc(a10, q, qi), redc(a11, q, qi));
+}
+
+// K'[2j + c] = K[2j + c] (.) pt on the limbs of Q_l u P (key layout: global prime index) and
+// Ppt = [P]_q (.) pt on the q-limbs ([l+1][n]); pt holds pt_level + 1 q-limbs then the p-limbs.
+__global__ void prekey_kernel(KP kp, const u64 *key, const u64 *pt, int level, int pt_level, int beta, u64 *Kp,
+                              u64 *Ppt, const u64 *pmod) {
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int t = blockIdx.y, z = blockIdx.z;
+    const int nq = level + 1;
+    const int kl = t < nq ? t : kp.L + 1 + (t - nq);
+    const int ptl = t < nq ? t : pt_level + 1 + (t - nq);
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 p = pt[(size_t)ptl * kp.n + k];
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    if (z < 2 * beta) {
+        const size_t i = (size_t)z * kstride + (size_t)kl * kp.n + k;
+        Kp[i] = mul_mont(key[i], p, q, qi);
+    } else if (t < nq) {
+        Ppt[(size_t)t * kp.n + k] = mul_mont(to_mont(pmod[kl], q, qi, r2), p, q, qi);
+    }
+}
+
 // ==== fused key-switch + MAC kernels: end
 
 // acc = sum_terms K_term * x_term (+ c on poly 0) over limbs 0..level, x of any higher level
@@ -1680,6 +1777,14 @@ int k_tensor(const he_ctx *ctx, const he_ct *a, const he_ct *b, u64 *d, cudaStre
     return HE_OK;
 }
 
+int k_prekey(const he_ctx *ctx, const u64 *key, const u64 *pt, int level, int pt_level, int beta, u64 *Kp, u64 *Ppt,
+             cudaStream_t s) {
+    dim3 g(ctx->n / TB, level + 1 + ctx->K, 2 * beta + 1);
+    prekey_kernel<<<g, TB, 0, s>>>(ctx->kp, key, pt, level, pt_level, beta, Kp, Ppt, ctx->d_consts);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
 int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta, double bytes, double mulmods,
             int form, int gb, cudaStream_t s) {
     if (n_grp <= 0) return HE_OK;
@@ -1704,6 +1809,14 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
             ipmac_tma_kernel<1><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
         else
             ipmac_tma_kernel<2><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
+        LAUNCH_CHECK();
+        return HE_OK;
+    }
+    if (form == HE_KEY_STREAM_PK) {
+        if (V != 1) { he_set_error("k_ipmac: the pre-keyed form takes one output per group"); return HE_EINVAL; }
+        dim3 gp(gx, primes);
+        if (max_beta <= 4) ipmac_pk_kernel<4><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else ipmac_pk_kernel<8><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
         LAUNCH_CHECK();
         return HE_OK;
     }

@@ -503,8 +503,43 @@ struct FusedStage {
     std::vector<Chunk> chunks;
     u64 *U = nullptr;                                 // [slots][2][ext][n] of the largest chunk
     bool split_ready = false;
+    // pre-keyed form (ipmac_pk_kernel): one group per output; per (output, keyed amount) with a
+    // plaintext K' = key (.) pt in the key layout, per (output, amount) with a plaintext P pt
+    struct PkGroup { famt *d_amt = nullptr; fent *d_ent = nullptr; fgrp desc{}; double bytes = 0, mulmods = 0; };
+    std::vector<PkGroup> pk_groups;
+    std::vector<u64 *> pk_bufs;
+    bool pk_built = false;
+    int pk_state = 0;                                 // 0: not checked, 1: eligible, -1: not
 
     ~FusedStage();
+    void free_pk() {
+        for (auto &g : pk_groups) { cudaFree(g.d_amt); cudaFree(g.d_ent); }
+        for (u64 *b : pk_bufs) cudaFree(b);
+        pk_groups.clear();
+        pk_bufs.clear();
+        pk_built = false;
+    }
+    // every output takes at most one source per amount
+    bool pk_eligible() {
+        if (pk_state == 0) {
+            std::set<std::pair<int, int>> seen;
+            pk_state = beta() <= 8 ? 1 : -1;
+            for (auto &t : terms)
+                if (!seen.insert({t.v, t.a}).second) { pk_state = -1; break; }
+        }
+        return pk_state > 0;
+    }
+    size_t pk_bytes() const {                         // device memory of the pre-keyed tables
+        const size_t kst = (size_t)(c->L + 1 + c->K) * c->n;
+        size_t b = 0;
+        for (auto &t : terms)
+            if (t.pt && t.pt != HE_PT_ONE) {
+                b += (size_t)nq() * c->n * 8;
+                if (h_galois(c, t.a) != 1) b += (size_t)2 * beta() * kst * 8;
+            }
+        return b;
+    }
+    int build_pk();
     void free_split() {
         for (auto &ch : chunks) {
             cudaFree(ch.d_amt); cudaFree(ch.d_ent);
@@ -684,8 +719,51 @@ struct FusedLaunch {
     std::vector<int> n_ugrp, n_rgrp;
     std::vector<double> ubytes, rbytes, rmm;
     bool split_built = false;
+    // pre-keyed form: one group per output of every stage
+    fgrp *d_pk = nullptr;
+    int G_pk = 0;
+    double pk_b = 0, pk_mm = 0;
+    bool use_pk = false;
 
-    ~FusedLaunch() { cudaFree(d_grps); free_split_tables(); }
+    ~FusedLaunch() { cudaFree(d_grps); cudaFree(d_pk); free_split_tables(); }
+    bool pk_ok() {
+        for (auto *f : st)
+            if (!f->pk_eligible()) return false;
+        return !st.empty();
+    }
+    size_t pk_need() const {
+        size_t b = 0;
+        for (auto *f : st) b += f->pk_built ? 0 : f->pk_bytes();
+        return b;
+    }
+    int build_pk() {
+        if (d_pk) return HE_OK;
+        std::vector<fgrp> h;
+        pk_b = pk_mm = 0;
+        for (auto *f : st) {
+            HE_TRY(f->build_pk());
+            for (auto &g : f->pk_groups) {
+                h.push_back(g.desc);
+                pk_b += g.bytes;
+                pk_mm += g.mulmods;
+            }
+        }
+        HE_TRY(dev_alloc(&d_pk, std::max<size_t>(1, h.size())));
+        if (!h.empty()) HE_CHECK_CUDA(cudaMemcpy(d_pk, h.data(), h.size() * sizeof(fgrp), cudaMemcpyHostToDevice));
+        G_pk = (int)h.size();
+        return HE_OK;
+    }
+    void free_pk() {
+        cudaFree(d_pk);
+        d_pk = nullptr;
+        G_pk = 0;
+        for (auto *f : st) f->free_pk();
+    }
+    int launch_pk(cudaStream_t s) {
+        int mb = 0;
+        for (auto *f : st) mb = std::max(mb, f->beta());
+        return k_ipmac(c, d_pk, G_pk, 1, mb, pk_b, pk_mm, HE_KEY_STREAM_PK, 0, s);
+    }
     void free_split_tables() {
         for (auto *p : d_ugrps) cudaFree(p);
         for (auto *p : d_rgrps) cudaFree(p);
@@ -785,13 +863,16 @@ struct FusedLaunch {
         forms.push_back(HE_KEY_STREAM_LDG1);
         std::vector<int> Vs = {vmax()};
         if (vmax() == 2) Vs.push_back(1);
-        bool try_split = false;
+        bool try_split = false, try_pk = false;
         if (!he_capturing()) {
             size_t fr = 0, tot = 0;
-            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && split_need() + ((size_t)4 << 30) < fr) try_split = true;
+            if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
+                try_split = split_need() + ((size_t)4 << 30) < fr;
+                try_pk = pk_ok() && pk_need() + ((size_t)4 << 30) < fr;
+            }
             cudaGetLastError();
         }
-        if ((forms.size() == 1 && Vs.size() == 1 && !try_split) || he_capturing()) {
+        if ((forms.size() == 1 && Vs.size() == 1 && !try_split && !try_pk) || he_capturing()) {
             // nothing to choose, or no timing possible inside a graph capture: keep the built
             // groups (a captured graph refers to them, so they are never rebuilt afterwards)
             form = forms[0];
@@ -854,6 +935,17 @@ struct FusedLaunch {
                 if (t < best) { best = t; bestGb = gbc; }
             }
         }
+        bool bestPk = false;
+        if (rc == HE_OK && try_pk) {
+            float t;
+            rc = build_pk();
+            if (rc == HE_OK) rc = time_it([&]() { return launch_pk(s); }, t);
+            if (rc == HE_OK) {
+                if (pos < (int)sizeof(line))
+                    pos += snprintf(line + pos, sizeof(line) - pos, " pk %.3f ms;", t);
+                if (t < best) { best = t; bestPk = true; bestSplit = false; }
+            }
+        }
         if (rc == HE_OK && try_split) {
             float t;
             rc = build_split();
@@ -861,13 +953,20 @@ struct FusedLaunch {
             if (rc == HE_OK) {
                 if (pos < (int)sizeof(line))
                     pos += snprintf(line + pos, sizeof(line) - pos, " split (%zu chunk(s)) %.3f ms;", d_ugrps.size(), t);
-                if (t < best) { best = t; bestSplit = true; }
+                if (t < best) { best = t; bestSplit = true; bestPk = false; }
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         HE_TRY(rc);
-        if (bestSplit) {
+        if (!bestPk && d_pk) free_pk();                 // give the pre-keyed tables' memory back
+        if (bestPk) {
+            use_pk = true;
+            if (split_built) {
+                free_split_tables();
+                for (auto *f : st) f->free_split();
+            }
+        } else if (bestSplit) {
             use_split = true;
             cudaFree(d_grps);                         // the fused tables are not needed
             d_grps = nullptr;
@@ -882,7 +981,8 @@ struct FusedLaunch {
         }
         tuned = true;
         if (pos < (int)sizeof(line)) {
-            if (bestSplit) snprintf(line + pos, sizeof(line) - pos, " -> split");
+            if (bestPk) snprintf(line + pos, sizeof(line) - pos, " -> pk");
+            else if (bestSplit) snprintf(line + pos, sizeof(line) - pos, " -> split");
             else snprintf(line + pos, sizeof(line) - pos, " -> V=%d %s gb=%d", bestV, form_name(bestF),
                           bestGb ? bestGb : G);
         }
@@ -896,13 +996,18 @@ struct FusedLaunch {
         if (opt == HE_KEY_STREAM_SPLIT) {                       // explicit split form
             HE_TRY(build_split());
             HE_TRY(launch_split(s));
-        } else if (opt != HE_KEY_STREAM_AUTO) {                 // explicit fused form
+        } else if (opt == HE_KEY_STREAM_PK && pk_ok()) {        // explicit pre-keyed form
+            HE_TRY(build_pk());
+            HE_TRY(launch_pk(s));
+        } else if (opt != HE_KEY_STREAM_AUTO) {                 // explicit fused form (PK: not eligible)
+            const int fm = opt == HE_KEY_STREAM_PK ? HE_KEY_STREAM_LDG : opt;
             if (!d_grps) HE_TRY(build(V ? V : vmax()));
-            HE_TRY(launch(opt, s));
+            HE_TRY(launch(fm, s));
         } else {
-            if (!d_grps && !use_split) HE_TRY(build(vmax()));
+            if (!d_grps && !use_split && !use_pk) HE_TRY(build(vmax()));
             if (!tuned) HE_TRY(tune(s));
-            if (use_split) HE_TRY(launch_split(s));
+            if (use_pk) HE_TRY(launch_pk(s));
+            else if (use_split) HE_TRY(launch_split(s));
             else HE_TRY(launch(form, s));
         }
         for (auto *f : st) HE_TRY(f->moddown(s));
@@ -1024,10 +1129,74 @@ int FusedStage::build_split(size_t cap_bytes) {
     return HE_OK;
 }
 
+int FusedStage::build_pk() {
+    if (pk_built) return HE_OK;
+    HE_TRY(build());
+    HE_TRY(he_capture_guard("pre-keyed tables"));
+    const size_t n = c->n, kst = (size_t)(c->L + 1 + c->K) * n;
+    const int nq_ = nq(), ext_ = ext(), beta_ = beta();
+    std::vector<std::map<int, const Term *>> by_out(outs.size());
+    for (auto &t : terms) by_out[t.v][t.a] = &t;
+    for (size_t v = 0; v < outs.size(); v++) {
+        std::vector<famt> ha;
+        std::vector<fent> he;
+        double bytes = 0, mm = 0;
+        for (auto &am : by_out[v]) {
+            const Term &T = *am.second;
+            famt A{};
+            A.g = h_galois(c, am.first);
+            const DeviceKey *key = nullptr;
+            if (A.g != 1) HE_TRY(get_key(c, (int)A.g, &key));
+            fent E{};
+            E.s = T.s;
+            E.D = hslot[T.s] >= 0 ? D_all + (size_t)hslot[T.s] * beta_ * ext_ * n : nullptr;
+            E.src = srcs[T.s].d;
+            E.ps = srcs[T.s].ps;
+            E.pt[0] = HE_PT_ONE;
+            E.pt[1] = nullptr;
+            A.key = key ? key->d : nullptr;
+            if (T.pt && T.pt != HE_PT_ONE) {
+                u64 *Ppt = nullptr, *Kp = nullptr;
+                HE_TRY(dev_alloc(&Ppt, (size_t)nq_ * n));
+                pk_bufs.push_back(Ppt);
+                if (key) {
+                    HE_TRY(dev_alloc(&Kp, 2 * beta_ * kst));
+                    pk_bufs.push_back(Kp);
+                }
+                HE_TRY(k_prekey(c, key ? key->d : nullptr, T.pt, level, pt_level, key ? beta_ : 0, Kp, Ppt, 0));
+                A.key = key ? Kp : nullptr;
+                E.pt[0] = Ppt;
+                bytes += (double)nq_ * n * 8;
+            }
+            if (A.key) bytes += (double)2 * beta_ * ext_ * n * 8;
+            mm += (double)ext_ * n * (A.key ? 2 * beta_ : 0) + (double)nq_ * n * 2;
+            A.e0 = (int)he.size();
+            he.push_back(E);
+            A.e1 = (int)he.size();
+            ha.push_back(A);
+        }
+        bytes += (double)nh * beta_ * ext_ * n * 8 / std::max<size_t>(1, outs.size()) +
+                 (double)srcs.size() * 2 * nq_ * n * 8 / std::max<size_t>(1, outs.size()) + (double)2 * ext_ * n * 8;
+        PkGroup G;
+        HE_TRY(dev_alloc(&G.d_amt, std::max<size_t>(1, ha.size())));
+        HE_TRY(dev_alloc(&G.d_ent, std::max<size_t>(1, he.size())));
+        if (!ha.empty()) HE_CHECK_CUDA(cudaMemcpy(G.d_amt, ha.data(), ha.size() * sizeof(famt), cudaMemcpyHostToDevice));
+        if (!he.empty()) HE_CHECK_CUDA(cudaMemcpy(G.d_ent, he.data(), he.size() * sizeof(fent), cudaMemcpyHostToDevice));
+        G.desc = fgrp{G.d_amt, G.d_ent, (int)ha.size(), level, beta_, pt_level, 1, facc + v * 2 * ext_ * n};
+        G.bytes = bytes;
+        G.mulmods = mm;
+        pk_groups.push_back(G);
+    }
+    HE_CHECK_CUDA(cudaStreamSynchronize(0));
+    pk_built = true;
+    return HE_OK;
+}
+
 FusedStage::~FusedStage() {
     own.reset();
     free_split();
     free_groups();
+    free_pk();
     cudaFree(D_all); cudaFree(facc); cudaFree(fconv); cudaFree(d_md); cudaFree(htmp); cudaFree(d_hsrc);
 }
 

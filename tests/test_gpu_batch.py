@@ -55,6 +55,7 @@ def test_mixed_level_batch_bit_exact():
         runs = [(H.HE_FUSED, H.HE_KEY_STREAM_AUTO, refs_f), (H.HE_FUSED, H.HE_KEY_STREAM_LDG, refs_f),
                 (H.HE_FUSED, H.HE_KEY_STREAM_TMA, refs_f), (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT, refs_f),
                 (H.HE_FUSED, H.HE_KEY_STREAM_CP, refs_f), (H.HE_FUSED, H.HE_KEY_STREAM_LDG1, refs_f),
+                (H.HE_FUSED, H.HE_KEY_STREAM_PK, refs_f),
                 (H.HE_PLAIN, H.HE_KEY_STREAM_AUTO, refs_p), (H.HE_BATCHED, H.HE_KEY_STREAM_AUTO, refs_p)]
         for mode, ks, refs in runs:
             H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)

@@ -72,11 +72,13 @@ def test_linear_head_bit_exact(mid, c, m, n_out, pool, level):
     H.he_linear_import_plaintexts(L, np.stack([np.stack([w_pts[(j, u)] for u in range(lin.n_shards)])
                                                for j in range(n_out)]),
                                   np.stack([m_pts[j] for j in range(n_out)]), b_pt)
-    for _ in range(2):                           # a second run reuses the built stages
+    for ks in (H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_PK, H.HE_KEY_STREAM_LDG):
+        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)   # a second run reuses the built stages
         H.he_linear_run(g.h, L, ins, out)
         H.he_ctx_check(g.h)
         assert H.he_ct_level(out) == ref.level and H.he_ct_scale(out) == ref.scale
         assert_ct_equal(g.download(out), ref)
+    H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_AUTO)
     # a shard at another level is refused
     bad = [g.ct(level - 1) for _ in range(lin.n_shards)]
     with pytest.raises(H.HEError) as e:
