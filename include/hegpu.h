@@ -133,7 +133,9 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  *     per rotation amount, each amount's key is multiplied by the output's plaintext once
  *     (K (.) pt, built on first use; the key itself when the plaintext is 1), and the kernel
  *     accumulates sum_j D_j (K (.) pt)_j without per-amount reductions or a plaintext stream.
- *     Other stages fall back to the LDG form;
+ *     Other stages fall back to the LDG form.  HE_KEY_STREAM_PK3 (7): the same kernel at three
+ *     blocks per SM; HE_KEY_STREAM_PKP (8): at two blocks per SM with the next amount's key words
+ *     requested before the current amount computes;
  *   HE_KEY_STREAM_SPLIT (3): the split form: the raised inner product of every (source,
  *     amount) is written to HBM once (each key read once), then a raised-basis MAC forms the
  *     plaintext-weighted sums of 4 outputs per pass; amounts go in chunks of at most 2 GB of
@@ -150,6 +152,8 @@ int he_ctx_check(he_ctx *ctx, void *stream);
 #define HE_KEY_STREAM_CP 4
 #define HE_KEY_STREAM_LDG1 5
 #define HE_KEY_STREAM_PK 6
+#define HE_KEY_STREAM_PK3 7
+#define HE_KEY_STREAM_PKP 8
 int he_ctx_set_option(he_ctx *ctx, int option, int value);
 int he_ctx_get_option(const he_ctx *ctx, int option, int *value);
 /* The autotuner's decisions so far (one line per tuned stage: the candidates' times and the

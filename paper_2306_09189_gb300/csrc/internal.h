@@ -180,6 +180,9 @@ struct modup_src {
     const u64 *c1;          // source c1, NTT form, [level+1][n]
     u64 *D;                 // its raised digits
 };
+// the pre-keyed kernel's variants (public key-stream values)
+#define HE_FORM_PK3 HE_KEY_STREAM_PK3
+#define HE_FORM_PKP HE_KEY_STREAM_PKP
 // K' = key (.) pt on the limbs of Q_level u P (key layout) and Ppt = [P]_q (.) pt on the q-limbs
 int k_prekey(const he_ctx *ctx, const u64 *key, const u64 *pt, int level, int pt_level, int beta, u64 *Kp, u64 *Ppt,
              cudaStream_t s);

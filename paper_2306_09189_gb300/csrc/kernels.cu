@@ -1277,8 +1277,9 @@ __global__ void __launch_bounds__(TB, 3) ipmac1_kernel(KP kp, const fgrp *grps, 
 // plaintext stream.  Terms are below p^2 < 2^100; a launch adds at most (beta + 1) per
 // amount, far below 2^28 terms, so the 128-bit sums cannot wrap.  fent.pt[0] holds P pt
 // ([l+1][n], Montgomery) or HE_PT_ONE for the integer 1 (then K' is the key itself).
-template <int B>
-__global__ void __launch_bounds__(TB, 2) ipmac_pk_kernel(KP kp, const fgrp *grps, int n_grp, int gb, const u64 *pmod) {
+template <int B, int MINB, bool PIPE>
+__global__ void __launch_bounds__(TB, MINB) ipmac_pk_kernel(KP kp, const fgrp *grps, int n_grp, int gb,
+                                                            const u64 *pmod) {
     fgrp P;
     int tile, t, ptl;
     if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl)) return;
@@ -1297,6 +1298,20 @@ __global__ void __launch_bounds__(TB, 2) ipmac_pk_kernel(KP kp, const fgrp *grps
     const int n_amt = P.n_amt;
     famt A = n_amt > 0 ? P.amts[0] : famt{};
     fent E = (n_amt > 0 && A.e0 < A.e1) ? P.ents[A.e0] : fent{};
+    // PIPE: the next amount's key words are requested before this amount computes
+    ulonglong2 kk0[B], kk1[B];
+    auto load_key = [&](const famt &X, ulonglong2 (&k0)[B], ulonglong2 (&k1)[B]) {
+        if (X.key) {
+#pragma unroll
+            for (int j = 0; j < B; j++)
+                if (j < beta) {
+                    const u64 *kp0 = X.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+                    k0[j] = ld2_hint(kp0, stream);
+                    k1[j] = ld2_hint(kp0 + kstride, stream);
+                }
+        }
+    };
+    if (PIPE && n_amt > 0) load_key(A, kk0, kk1);
     for (int i = 0; i < n_amt; i++) {
         famt An{};
         fent En{};
@@ -1304,18 +1319,13 @@ __global__ void __launch_bounds__(TB, 2) ipmac_pk_kernel(KP kp, const fgrp *grps
             An = P.amts[i + 1];
             if (An.e0 < An.e1) En = P.ents[An.e0];
         }
+        ulonglong2 kn0[B], kn1[B];
+        if (PIPE) load_key(An, kn0, kn1);
+        else load_key(A, kk0, kk1);
         if (A.e0 < A.e1) {
             const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
             const int sw = ks & 1, kb = ks & ~1;
             if (A.key) {
-                ulonglong2 kk0[B], kk1[B];
-#pragma unroll
-                for (int j = 0; j < B; j++)
-                    if (j < beta) {
-                        const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
-                        kk0[j] = ld2_hint(kp0, stream);
-                        kk1[j] = ld2_hint(kp0 + kstride, stream);
-                    }
 #pragma unroll
                 for (int j = 0; j < B; j++)
                     if (j < beta) {
@@ -1339,6 +1349,10 @@ __global__ void __launch_bounds__(TB, 2) ipmac_pk_kernel(KP kp, const fgrp *grps
                     a11 += (u128)c1.y * pp.y;
                 }
             }
+        }
+        if (PIPE) {
+#pragma unroll
+            for (int j = 0; j < B; j++) { kk0[j] = kn0[j]; kk1[j] = kn1[j]; }
         }
         A = An;
         E = En;
@@ -1812,11 +1826,15 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
         LAUNCH_CHECK();
         return HE_OK;
     }
-    if (form == HE_KEY_STREAM_PK) {
+    if (form == HE_KEY_STREAM_PK || form == HE_FORM_PK3 || form == HE_FORM_PKP) {
         if (V != 1) { he_set_error("k_ipmac: the pre-keyed form takes one output per group"); return HE_EINVAL; }
         dim3 gp(gx, primes);
-        if (max_beta <= 4) ipmac_pk_kernel<4><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
-        else ipmac_pk_kernel<8><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        if (form == HE_FORM_PK3 && max_beta <= 4)
+            ipmac_pk_kernel<4, 3, false><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else if (form == HE_FORM_PKP && max_beta <= 4)
+            ipmac_pk_kernel<4, 2, true><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else if (max_beta <= 4) ipmac_pk_kernel<4, 2, false><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else ipmac_pk_kernel<8, 2, false><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
         LAUNCH_CHECK();
         return HE_OK;
     }

@@ -698,6 +698,8 @@ struct FusedStage {
 // launch (one warm-up pass, then the best of two timed passes, CUDA events on the launch's
 // stream) and keeps the fastest.  Needs the raised digits in place: called after the hoisted
 // ModUps of the first run.
+static bool is_pk(int fm) { return fm == HE_KEY_STREAM_PK || fm == HE_KEY_STREAM_PK3 || fm == HE_KEY_STREAM_PKP; }
+static const char *pk_name(int fm) { return fm == HE_FORM_PK3 ? "pk3" : fm == HE_FORM_PKP ? "pkp" : "pk"; }
 static const char *form_name(int fm) {
     return fm == HE_KEY_STREAM_TMA ? "tma" : fm == HE_KEY_STREAM_CP ? "cp" : fm == HE_KEY_STREAM_LDG1 ? "ldg1" : "ldg";
 }
@@ -759,10 +761,11 @@ struct FusedLaunch {
         G_pk = 0;
         for (auto *f : st) f->free_pk();
     }
-    int launch_pk(cudaStream_t s) {
+    int pk_form = HE_KEY_STREAM_PK;                   // or HE_FORM_PK3 (three blocks per SM)
+    int launch_pk(cudaStream_t s, int fm = 0) {
         int mb = 0;
         for (auto *f : st) mb = std::max(mb, f->beta());
-        return k_ipmac(c, d_pk, G_pk, 1, mb, pk_b, pk_mm, HE_KEY_STREAM_PK, 0, s);
+        return k_ipmac(c, d_pk, G_pk, 1, mb, pk_b, pk_mm, fm ? fm : pk_form, 0, s);
     }
     void free_split_tables() {
         for (auto *p : d_ugrps) cudaFree(p);
@@ -937,13 +940,14 @@ struct FusedLaunch {
         }
         bool bestPk = false;
         if (rc == HE_OK && try_pk) {
-            float t;
             rc = build_pk();
-            if (rc == HE_OK) rc = time_it([&]() { return launch_pk(s); }, t);
-            if (rc == HE_OK) {
+            for (int fm : {(int)HE_KEY_STREAM_PK, (int)HE_FORM_PK3, (int)HE_FORM_PKP}) {
+                float t;
+                if (rc == HE_OK) rc = time_it([&]() { return launch_pk(s, fm); }, t);
+                if (rc != HE_OK) break;
                 if (pos < (int)sizeof(line))
-                    pos += snprintf(line + pos, sizeof(line) - pos, " pk %.3f ms;", t);
-                if (t < best) { best = t; bestPk = true; bestSplit = false; }
+                    pos += snprintf(line + pos, sizeof(line) - pos, " %s %.3f ms;", pk_name(fm), t);
+                if (t < best) { best = t; bestPk = true; bestSplit = false; pk_form = fm; }
             }
         }
         if (rc == HE_OK && try_split) {
@@ -981,7 +985,7 @@ struct FusedLaunch {
         }
         tuned = true;
         if (pos < (int)sizeof(line)) {
-            if (bestPk) snprintf(line + pos, sizeof(line) - pos, " -> pk");
+            if (bestPk) snprintf(line + pos, sizeof(line) - pos, " -> %s", pk_name(pk_form));
             else if (bestSplit) snprintf(line + pos, sizeof(line) - pos, " -> split");
             else snprintf(line + pos, sizeof(line) - pos, " -> V=%d %s gb=%d", bestV, form_name(bestF),
                           bestGb ? bestGb : G);
@@ -996,11 +1000,11 @@ struct FusedLaunch {
         if (opt == HE_KEY_STREAM_SPLIT) {                       // explicit split form
             HE_TRY(build_split());
             HE_TRY(launch_split(s));
-        } else if (opt == HE_KEY_STREAM_PK && pk_ok()) {        // explicit pre-keyed form
+        } else if (is_pk(opt) && pk_ok()) {                     // explicit pre-keyed form
             HE_TRY(build_pk());
-            HE_TRY(launch_pk(s));
+            HE_TRY(launch_pk(s, opt));
         } else if (opt != HE_KEY_STREAM_AUTO) {                 // explicit fused form (PK: not eligible)
-            const int fm = opt == HE_KEY_STREAM_PK ? HE_KEY_STREAM_LDG : opt;
+            const int fm = is_pk(opt) ? HE_KEY_STREAM_LDG : opt;
             if (!d_grps) HE_TRY(build(V ? V : vmax()));
             HE_TRY(launch(fm, s));
         } else {

@@ -19,6 +19,8 @@ HE_OPT_KEY_STREAM = 1
 HE_KEY_STREAM_LDG, HE_KEY_STREAM_TMA, HE_KEY_STREAM_AUTO, HE_KEY_STREAM_SPLIT, HE_KEY_STREAM_CP = 0, 1, 2, 3, 4
 HE_KEY_STREAM_LDG1 = 5
 HE_KEY_STREAM_PK = 6
+HE_KEY_STREAM_PK3 = 7
+HE_KEY_STREAM_PKP = 8
 
 c_int, c_double, c_size_t, c_u64, c_i32, c_vp = (ctypes.c_int, ctypes.c_double, ctypes.c_size_t,
                                                  ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p)

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 MID = Params(log_n=12, n_q=6, n_p=2, dnum=3, q0_bits=50, q_bits=40, p_bits=50,
              scale=2.0 ** 40, seed=5)
 
-FORMS = ("LDG", "TMA", "CP", "LDG1", "SPLIT", "PK")
+FORMS = ("LDG", "TMA", "CP", "LDG1", "SPLIT", "PK", "PK3", "PKP")
 
 
 @pytest.fixture(scope="module")

@@ -72,7 +72,8 @@ def test_linear_head_bit_exact(mid, c, m, n_out, pool, level):
     H.he_linear_import_plaintexts(L, np.stack([np.stack([w_pts[(j, u)] for u in range(lin.n_shards)])
                                                for j in range(n_out)]),
                                   np.stack([m_pts[j] for j in range(n_out)]), b_pt)
-    for ks in (H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_PK, H.HE_KEY_STREAM_LDG):
+    for ks in (H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_PK, H.HE_KEY_STREAM_PK3,
+               H.HE_KEY_STREAM_PKP, H.HE_KEY_STREAM_LDG):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)   # a second run reuses the built stages
         H.he_linear_run(g.h, L, ins, out)
         H.he_ctx_check(g.h)
