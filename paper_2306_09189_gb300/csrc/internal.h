@@ -210,6 +210,9 @@ struct md_item {            // out_c = base_c[phi_g] + (u_c - conv_c) * P^{-1}
 };
 int k_moddown_combine(const he_ctx *ctx, const md_item *items_dev, int n_items, int level,
                       cudaStream_t s);
+// ModDown fused with the rescale that follows it (m relinearised products, see kernels.cu)
+int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, size_t b_ps, u64 *w,
+                      u64 *const *out, const size_t *out_ps, int m, int level, cudaStream_t s);
 int k_rescale_prep(const he_ctx *ctx, const u64 *top_coef, size_t top_pstride, u64 *t, int level,
                    cudaStream_t s);
 int k_rescale_combine(const he_ctx *ctx, he_ct *ct, const u64 *t, cudaStream_t s);

@@ -603,6 +603,103 @@ __global__ void __launch_bounds__(TB) moddown_combine_kernel(KP kp, const md_ite
     }
 }
 
+// ------------------------------------------------------------------------------ ModDown + rescale
+// A key switch whose output is rescaled at once (a relinearised product): with y = ModDown(u)
+// + base and c' = Rescale(y), the top limb y_l is formed in coefficient form directly,
+// y_l = (INTT(u_l + P base_l) - conv_l) P^-1 mod q_l (INTT is linear, so folding P base_l into
+// u_l before its INTT adds base_l after it), and for i < l
+//   c'_i = (u_i P^-1 + base_i - NTT(conv_i P^-1 + [y_l]_{q_i})) q_l^-1,
+// one forward NTT of l limbs instead of the ModDown's l+1 and the rescale's l, and no INTT of
+// y_l.  Every step is exact mod q_i: the bits of ModDown then rescale.
+
+// u[i][c][l] += P base[i][c][l]  (NTT form, c = 0, 1; item i = blockIdx.z)
+__global__ void fold_top_kernel(KP kp, u64 *u, size_t u_is, size_t u_ps, const u64 *base, size_t b_is, size_t b_ps,
+                                int level, const u64 *pmod) {
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int c = blockIdx.y, i = blockIdx.z;
+    const u64 q = kp.q[level], qi = kp.qinv[level], r2 = kp.r2[level];
+    const u64 Pm = to_mont(pmod[level], q, qi, r2);
+    u64 *x = u + (size_t)i * u_is + (size_t)c * u_ps + (size_t)level * kp.n + k;
+    const u64 b = base[(size_t)i * b_is + (size_t)c * b_ps + (size_t)level * kp.n + k];
+    *x = add_mod(*x, mul_mont(b, Pm, q, qi), q);
+}
+
+// per poly (blockIdx.y): u = [ext][n] with limbs l..l+K in coefficient form; w = [l][n]
+__global__ void __launch_bounds__(TB) moddown_rescale_fbc_kernel(KP kp, const u64 *u, u64 *w, int level,
+                                                                 const u64 *tab, const u64 *pinv, const u64 *pinvs) {
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int c = blockIdx.y;
+    const int nq = level + 1;
+    const int ext = nq + kp.K;
+    const int K = kp.K;
+    const u64 *uc = u + (size_t)c * ext * kp.n;
+    u64 v[16];
+    bool neg[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        if (i < K) {
+            const int pr = kp.L + 1 + i;
+            const u64 p = kp.q[pr];
+            u64 y = mul_shoup(uc[(size_t)(nq + i) * kp.n + k], tab[i], tab[K + i], p);
+            neg[i] = 2 * y > p;
+            v[i] = neg[i] ? p - y : y;
+        }
+    }
+    const u64 *hat = tab + 2 * K;
+    const u64 *nhat = hat + (size_t)nq * K;
+    auto fbc = [&](int t) {
+        u128 acc = 0;
+#pragma unroll
+        for (int i = 0; i < 16; i++)
+            if (i < K) acc += (u128)v[i] * (neg[i] ? nhat[t * K + i] : hat[t * K + i]);
+        return redc(acc, kp.q[t], kp.qinv[t]);
+    };
+    // y_l in coefficient form, then its centred representative reduced mod every lower prime
+    const u64 ql = kp.q[level];
+    const u64 yl = mul_shoup(sub_mod(uc[(size_t)level * kp.n + k], fbc(level), ql), pinv[level], pinvs[level], ql);
+    const bool yneg = 2 * yl > ql;
+    for (int t = 0; t < level; t++) {
+        const u64 q = kp.q[t];
+        u64 r;
+        if (yneg) {
+            const u64 m = reduce64(ql - yl, q, kp.mu[t]);
+            r = m == 0 ? 0 : q - m;
+        } else {
+            r = reduce64(yl, q, kp.mu[t]);
+        }
+        w[((size_t)c * level + t) * kp.n + k] = add_mod(mul_shoup(fbc(t), pinv[t], pinvs[t], q), r, q);
+    }
+}
+
+struct mdr_item {            // one key switch of a fused ModDown + rescale
+    const u64 *u;            // [2][l+1+K][n]
+    const u64 *base;         // base polys (NTT form), poly c at base + c base_ps
+    size_t base_ps;
+    const u64 *w;            // [2][l][n], NTT form
+    u64 *out;                // output at level l-1, poly c at out + c out_ps
+    size_t out_ps;
+};
+struct MdrInline {
+    mdr_item it[HE_INLINE_ITEMS];
+};
+
+__global__ void __launch_bounds__(TB) moddown_rescale_combine_kernel(KP kp, MdrInline inl, int level,
+                                                                     const u64 *pinv, const u64 *pinvs,
+                                                                     const u64 *linv, const u64 *linvs) {
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int i = blockIdx.y;
+    const mdr_item it = inl.it[blockIdx.z];
+    const int ext = level + 1 + kp.K;
+    const u64 q = kp.q[i];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        u64 x = mul_shoup(it.u[((size_t)c * ext + i) * kp.n + k], pinv[i], pinvs[i], q);
+        x = add_mod(x, it.base[c * it.base_ps + (size_t)i * kp.n + k], q);
+        x = sub_mod(x, it.w[((size_t)c * level + i) * kp.n + k], q);
+        it.out[c * it.out_ps + (size_t)i * kp.n + k] = mul_shoup(x, linv[i], linvs[i], q);
+    }
+}
+
 // ------------------------------------------------------------------------------ rescale
 // t[c][i][k] = [centred c_l]_{q_i}, from the coefficient-form top limb of poly c
 __global__ void rescale_prep_kernel(KP kp, const u64 *top, size_t top_pstride, u64 *t, int level) {
@@ -1723,6 +1820,50 @@ int k_moddown_combine_inline(const he_ctx *ctx, const md_item *items, int n, int
 
 int k_moddown_combine_one(const he_ctx *ctx, const md_item &it, int level, cudaStream_t s) {
     return k_moddown_combine_inline(ctx, &it, 1, level, s);
+}
+
+// Relinearisation tail of m products at level l, fused with their rescale: u [m][2][l+1+K][n]
+// (inner products, NTT form), base [m] polys 0, 1 at base + i b_is + c b_ps, w scratch
+// [m][2][l][n]; outputs out[i] at level l - 1 (poly c at out[i] + c out_ps[i]).
+int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, size_t b_ps, u64 *w,
+                      u64 *const *out, const size_t *out_ps, int m, int level, cudaStream_t s) {
+    if (m <= 0) return HE_OK;
+    if (ctx->K > 16 || level < 1) { he_set_error("moddown-rescale: bad level or special primes"); return HE_EINVAL; }
+    const int nq = level + 1, ext = nq + ctx->K;
+    const size_t we = (size_t)ext * ctx->n;
+    fold_top_kernel<<<dim3(ctx->n / TB, 2, m), TB, 0, s>>>(ctx->kp, u, 2 * we, we, base, b_is, b_ps, level,
+                                                           ctx->d_consts);
+    LAUNCH_CHECK();
+    ntt_job ju{u, we, level, ctx->K + 1, nq, 0, 2 * m, 0};
+    HE_TRY(k_ntt(ctx, ju, true, s));
+    const u64 *pinv = ctx->d_consts + ctx->np;
+    const u64 *pinvs = pinv + (ctx->L + 1);
+    {
+        TraceScope tr("moddown_fbc", s, (double)2 * m * (ctx->K + 1 + level) * ctx->n * 8,
+                      (double)2 * m * (ctx->K + nq * ctx->K + level) * ctx->n);
+        moddown_rescale_fbc_kernel<<<dim3(ctx->n / TB, 2 * m), TB, 0, s>>>(ctx->kp, u, w, level,
+                                                                          ctx->moddown[level].d, pinv, pinvs);
+        LAUNCH_CHECK();
+    }
+    ntt_job jw{w, (size_t)level * ctx->n, 0, level, nq, 0, 2 * m, 0};
+    HE_TRY(k_ntt(ctx, jw, false, s));
+    const u64 *cb = ctx->d_consts + ctx->np + 2 * (ctx->L + 1);
+    const u64 *linv = cb + (size_t)level * 2 * (ctx->L + 1);
+    const u64 *linvs = linv + (ctx->L + 1);
+    for (int i0 = 0; i0 < m; i0 += HE_INLINE_ITEMS) {
+        const int cnt = std::min(HE_INLINE_ITEMS, m - i0);
+        MdrInline inl;
+        for (int i = 0; i < cnt; i++) {
+            const int j = i0 + i;
+            inl.it[i] = mdr_item{u + (size_t)j * 2 * we, base + (size_t)j * b_is, b_ps, w + (size_t)j * 2 * level * ctx->n,
+                                 out[j], out_ps[j]};
+        }
+        TraceScope tr("moddown_combine", s, (double)cnt * level * ctx->n * 8 * 9, (double)cnt * level * ctx->n * 4);
+        moddown_rescale_combine_kernel<<<dim3(ctx->n / TB, level, cnt), TB, 0, s>>>(ctx->kp, inl, level, pinv, pinvs,
+                                                                                   linv, linvs);
+        LAUNCH_CHECK();
+    }
+    return HE_OK;
 }
 
 int k_rescale_prep(const he_ctx *ctx, const u64 *top, size_t top_pstride, u64 *t, int level,

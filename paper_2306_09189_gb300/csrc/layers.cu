@@ -2690,8 +2690,7 @@ static int relin_batch(he_ctx *c, const std::vector<const he_ct *> &A, const std
     u64 *xc = d + (size_t)m * 3 * wq;             // [m][nq][n]
     u64 *D = xc + (size_t)m * wq;                 // [m][beta][ext][n]
     u64 *u = D + (size_t)m * beta * we;           // [m][2][ext][n]
-    u64 *conv = u + (size_t)m * 2 * we;           // [m][2][nq][n]
-    u64 *rt = conv + (size_t)m * 2 * wq;          // [m][2][nq][n] rescale scratch
+    u64 *conv = u + (size_t)m * 2 * we;           // [m][2][nq][n] (the fused ModDown-rescale's w)
     for (int i = 0; i < m; i++) {
         he_ct ta = *A[i], tb = *B[i];
         HE_TRY(k_tensor(c, &ta, &tb, d + (size_t)i * 3 * wq, s));
@@ -2704,32 +2703,20 @@ static int relin_batch(he_ctx *c, const std::vector<const he_ct *> &A, const std
     ntt_job jd{D, we, 0, ext, nq, c->alpha, beta * m, beta};
     HE_TRY(k_ntt(c, jd, false, s));
     std::vector<ip_item> ip(m);
-    std::vector<md_item> md(m);
     for (int i = 0; i < m; i++) {
         HE_TRY(ensure_ct(c, out[i], l));
         ip[i] = ip_item{D + (size_t)i * beta * we, key->d, u + (size_t)i * 2 * we, 1, beta};
-        md[i] = md_item{u + (size_t)i * 2 * we, conv + (size_t)i * 2 * wq, d + (size_t)i * 3 * wq, wq, 2, 1,
-                        out[i]->d, out[i]->pstride};
     }
     HE_TRY(k_inner_product_inline(c, ip.data(), m, l, s));
-    ntt_job jp{u, we, nq, c->K, nq, 0, 2 * m, 0};
-    HE_TRY(k_ntt(c, jp, true, s));
-    HE_TRY(k_moddown_fbc(c, u, conv, l, 2 * m, s));
-    ntt_job jc{conv, wq, 0, nq, nq, 0, 2 * m, 0};
-    HE_TRY(k_ntt(c, jc, false, s));
-    HE_TRY(k_moddown_combine_inline(c, md.data(), m, l, s));
-    bool uniform = true;
-    for (int i = 1; i < m; i++)
-        uniform = uniform && out[i]->pstride == out[0]->pstride && out[i]->d == out[0]->d + 2 * (size_t)i * out[0]->pstride;
-    if (uniform) HE_TRY(k_rescale_many(c, out[0]->d, out[0]->pstride, m, l, rt, s));
+    // ModDown fused with the rescale: the bits of ModDown, then rescale
+    std::vector<u64 *> op(m);
+    std::vector<size_t> ops(m);
+    for (int i = 0; i < m; i++) { op[i] = out[i]->d; ops[i] = out[i]->pstride; }
+    HE_TRY(k_moddown_rescale(c, u, d, 3 * wq, wq, conv, op.data(), ops.data(), m, l, s));
     for (int i = 0; i < m; i++) {
         out[i]->scale = A[i]->scale * B[i]->scale;
-        if (uniform) {
-            out[i]->level = l - 1;
-            out[i]->scale = out[i]->scale / (double)c->primes[l];
-        } else {
-            HE_TRY(he_rescale(c, out[i], s));
-        }
+        out[i]->level = l - 1;
+        out[i]->scale = out[i]->scale / (double)c->primes[l];
     }
     return HE_OK;
 }
