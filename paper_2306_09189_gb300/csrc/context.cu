@@ -301,6 +301,7 @@ static void free_ctx(he_ctx *c) {
         if (t.d) cudaFree(t.d);
     for (auto &kv : c->keys)
         if (kv.second.d) cudaFree(kv.second.d);
+    for (auto &kv : c->pk_cache) { cudaFree(kv.second.Kp); cudaFree(kv.second.Ppt); }
     if (c->d_tables) cudaFree(c->d_tables);
     if (c->d_consts) cudaFree(c->d_consts);
     if (c->d_s) cudaFree(c->d_s);

@@ -5,6 +5,7 @@
 
 #include <map>
 #include <memory>
+#include <array>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -123,6 +124,11 @@ struct he_ctx {
     int *d_err = nullptr;                // set by a bounded device wait that gave up
     int key_stream = HE_KEY_STREAM_AUTO; // HE_OPT_KEY_STREAM
     std::mutex tune_mu;                  // root only: the autotuner's log
+    // root only: pre-keyed tables (key (.) plaintext and [P]_q plaintext), shared by every
+    // fork and stage that uses the same key and plaintext at the same levels; refcounted
+    struct PkEntry { u64 *Kp = nullptr, *Ppt = nullptr; int refs = 0; };
+    std::mutex pk_mu;
+    std::map<std::array<uintptr_t, 4>, PkEntry> pk_cache;   // (key, plaintext, level, pt_level)
     std::vector<std::string> tune_log;
     he_ctx *parent = nullptr;            // forks share tables, secret and keys with their root
     he_ctx *root() { return parent ? parent : this; }

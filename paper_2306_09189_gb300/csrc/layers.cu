@@ -507,17 +507,31 @@ struct FusedStage {
     // plaintext K' = key (.) pt in the key layout, per (output, amount) with a plaintext P pt
     struct PkGroup { famt *d_amt = nullptr; fent *d_ent = nullptr; fgrp desc{}; double bytes = 0, mulmods = 0; };
     std::vector<PkGroup> pk_groups;
-    std::vector<u64 *> pk_bufs;
+    std::vector<std::array<uintptr_t, 4>> pk_refs;   // entries of the root's pre-keyed cache held
     bool pk_built = false;
     int pk_state = 0;                                 // 0: not checked, 1: eligible, -1: not
 
     ~FusedStage();
     void free_pk() {
         for (auto &g : pk_groups) { cudaFree(g.d_amt); cudaFree(g.d_ent); }
-        for (u64 *b : pk_bufs) cudaFree(b);
+        if (!pk_refs.empty()) {
+            he_ctx *r = c->root();
+            std::lock_guard<std::mutex> lk(r->pk_mu);
+            for (auto &key : pk_refs) {
+                auto it = r->pk_cache.find(key);
+                if (it != r->pk_cache.end() && --it->second.refs == 0) {
+                    cudaFree(it->second.Kp);
+                    cudaFree(it->second.Ppt);
+                    r->pk_cache.erase(it);
+                }
+            }
+        }
         pk_groups.clear();
-        pk_bufs.clear();
+        pk_refs.clear();
         pk_built = false;
+    }
+    std::array<uintptr_t, 4> pk_key(const u64 *key, const u64 *pt) const {
+        return {(uintptr_t)key, (uintptr_t)pt, (uintptr_t)level, (uintptr_t)pt_level};
     }
     // every output takes at most one source per amount
     bool pk_eligible() {
@@ -529,13 +543,19 @@ struct FusedStage {
         }
         return pk_state > 0;
     }
-    size_t pk_bytes() const {                         // device memory of the pre-keyed tables
+    size_t pk_bytes() const {                         // new device memory the pre-keyed tables need
         const size_t kst = (size_t)(c->L + 1 + c->K) * c->n;
         size_t b = 0;
+        he_ctx *r = c->root();
+        std::lock_guard<std::mutex> lk(r->pk_mu);
         for (auto &t : terms)
             if (t.pt && t.pt != HE_PT_ONE) {
+                const u64 g = h_galois(c, t.a);
+                auto kit = r->keys.find((int)g);
+                const u64 *kd = (g != 1 && kit != r->keys.end()) ? kit->second.d : nullptr;
+                if (r->pk_cache.count(pk_key(kd, t.pt))) continue;
                 b += (size_t)nq() * c->n * 8;
-                if (h_galois(c, t.a) != 1) b += (size_t)2 * beta() * kst * 8;
+                if (g != 1) b += (size_t)2 * beta() * kst * 8;
             }
         return b;
     }
@@ -871,7 +891,8 @@ struct FusedLaunch {
             size_t fr = 0, tot = 0;
             if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) {
                 try_split = split_need() + ((size_t)4 << 30) < fr;
-                try_pk = pk_ok() && pk_need() + ((size_t)4 << 30) < fr;
+                const size_t pn = pk_ok() ? pk_need() : 0;
+                try_pk = pk_ok() && pn + ((size_t)4 << 30) < fr && pn <= fr / 4;
             }
             cudaGetLastError();
         }
@@ -1160,16 +1181,24 @@ int FusedStage::build_pk() {
             E.pt[1] = nullptr;
             A.key = key ? key->d : nullptr;
             if (T.pt && T.pt != HE_PT_ONE) {
-                u64 *Ppt = nullptr, *Kp = nullptr;
-                HE_TRY(dev_alloc(&Ppt, (size_t)nq_ * n));
-                pk_bufs.push_back(Ppt);
-                if (key) {
-                    HE_TRY(dev_alloc(&Kp, 2 * beta_ * kst));
-                    pk_bufs.push_back(Kp);
+                const auto ck = pk_key(key ? key->d : nullptr, T.pt);
+                he_ctx *r = c->root();
+                std::lock_guard<std::mutex> lk(r->pk_mu);
+                auto it = r->pk_cache.find(ck);
+                if (it == r->pk_cache.end()) {
+                    he_ctx::PkEntry e;
+                    int rc = dev_alloc(&e.Ppt, (size_t)nq_ * n);
+                    if (rc == HE_OK && key) rc = dev_alloc(&e.Kp, 2 * beta_ * kst);
+                    if (rc == HE_OK)
+                        rc = k_prekey(c, key ? key->d : nullptr, T.pt, level, pt_level, key ? beta_ : 0, e.Kp, e.Ppt, 0);
+                    if (rc == HE_OK && cudaStreamSynchronize(0) != cudaSuccess) { cudaGetLastError(); rc = HE_ECUDA; }
+                    if (rc != HE_OK) { cudaFree(e.Kp); cudaFree(e.Ppt); return rc; }
+                    it = r->pk_cache.emplace(ck, e).first;
                 }
-                HE_TRY(k_prekey(c, key ? key->d : nullptr, T.pt, level, pt_level, key ? beta_ : 0, Kp, Ppt, 0));
-                A.key = key ? Kp : nullptr;
-                E.pt[0] = Ppt;
+                it->second.refs++;
+                pk_refs.push_back(ck);
+                A.key = key ? it->second.Kp : nullptr;
+                E.pt[0] = it->second.Ppt;
                 bytes += (double)nq_ * n * 8;
             }
             if (A.key) bytes += (double)2 * beta_ * ext_ * n * 8;
