@@ -548,12 +548,14 @@ struct FusedStage {
         size_t b = 0;
         he_ctx *r = c->root();
         std::lock_guard<std::mutex> lk(r->pk_mu);
+        std::set<std::array<uintptr_t, 4>> fresh;     // distinct (key, plaintext) pairs to build
         for (auto &t : terms)
             if (t.pt && t.pt != HE_PT_ONE) {
                 const u64 g = h_galois(c, t.a);
                 auto kit = r->keys.find((int)g);
                 const u64 *kd = (g != 1 && kit != r->keys.end()) ? kit->second.d : nullptr;
-                if (r->pk_cache.count(pk_key(kd, t.pt))) continue;
+                const auto ck = pk_key(kd, t.pt);
+                if (r->pk_cache.count(ck) || !fresh.insert(ck).second) continue;
                 b += (size_t)nq() * c->n * 8;
                 if (g != 1) b += (size_t)2 * beta() * kst * 8;
             }

@@ -160,7 +160,7 @@ def test_pool_bit_exact(mid, c, m):
     # every stage with one ModDown per output shard: equals the oracle's raised-basis pool
     ref_r = Ly.pool_he_raised(o, plan, cts, list(hm), list(vm))
     for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_LDG1,
-               H.HE_KEY_STREAM_SPLIT):
+               H.HE_KEY_STREAM_SPLIT, H.HE_KEY_STREAM_PK, H.HE_KEY_STREAM_PK3, H.HE_KEY_STREAM_AUTO):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 2) for _ in range(len(ref_r))]
         H.he_pool_run(g.h, pool, ins, outs, H.HE_FUSED)
