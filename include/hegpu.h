@@ -154,6 +154,11 @@ int he_ctx_check(he_ctx *ctx, void *stream);
 #define HE_KEY_STREAM_PK 6
 #define HE_KEY_STREAM_PK3 7
 #define HE_KEY_STREAM_PKP 8
+/* HE_OPT_PDL (0 default, or 1; process-wide, whichever context sets it): launch every kernel
+ * with programmatic dependent launch, so each grid is set up while its predecessor on the
+ * stream finishes (every kernel waits for the predecessor's writes before it reads).  Same
+ * bits either way; on the graph-launched CIFAR-layer step it measured neutral. */
+#define HE_OPT_PDL 2
 int he_ctx_set_option(he_ctx *ctx, int option, int value);
 int he_ctx_get_option(const he_ctx *ctx, int option, int *value);
 /* The autotuner's decisions so far (one line per tuned stage: the candidates' times and the

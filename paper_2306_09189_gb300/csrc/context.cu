@@ -684,6 +684,10 @@ extern "C" int he_selftest_bounded_wait(he_ctx *c, void *stream) {
 
 extern "C" int he_ctx_set_option(he_ctx *c, int option, int value) {
     if (!c) { he_set_error("null context"); return HE_EINVAL; }
+    if (option == HE_OPT_PDL && (value == 0 || value == 1)) {
+        he_set_pdl(value);
+        return HE_OK;
+    }
     if (option == HE_OPT_KEY_STREAM &&
         (value == HE_KEY_STREAM_LDG || value == HE_KEY_STREAM_TMA || value == HE_KEY_STREAM_AUTO ||
          value == HE_KEY_STREAM_SPLIT || value == HE_KEY_STREAM_CP || value == HE_KEY_STREAM_LDG1 ||
@@ -698,6 +702,7 @@ extern "C" int he_ctx_set_option(he_ctx *c, int option, int value) {
 extern "C" int he_ctx_get_option(const he_ctx *c, int option, int *value) {
     if (!c || !value) { he_set_error("he_ctx_get_option: null argument"); return HE_EINVAL; }
     if (option == HE_OPT_KEY_STREAM) { *value = c->key_stream; return HE_OK; }
+    if (option == HE_OPT_PDL) { *value = he_get_pdl(); return HE_OK; }
     he_set_error("he_ctx_get_option: unknown option %d", option);
     return HE_EINVAL;
 }

@@ -34,6 +34,8 @@ void he_set_error(const char *fmt, ...);
     } while (0)
 
 void he_count_launch(int k = 1);
+void he_set_pdl(int on);                 // programmatic dependent launch of every kernel (process-wide)
+int he_get_pdl();
 // True while this thread is capturing a CUDA graph (he_graph_begin .. he_graph_end): no device
 // allocation, synchronous copy or event timing may happen then.
 bool he_capturing();

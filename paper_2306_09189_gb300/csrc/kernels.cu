@@ -4,6 +4,9 @@
 // coefficient index of one limb, so every global access is a coalesced 8-byte stream.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <utility>
+
 #include <algorithm>
 #include <string.h>
 
@@ -35,14 +38,23 @@ __device__ __forceinline__ int job_limb(const ntt_job &j, int y, int p) {
     return limb;
 }
 
+// Programmatic dependent launch: every kernel is launched with the programmatic-serialisation
+// attribute (when enabled), so its grid is set up while the predecessor on the stream
+// finishes; each kernel's first statement, griddepcontrol.wait, holds it until the predecessor
+// has completed and its writes are visible (a no-op for a normal launch).  The predecessor
+// never waits for the dependent, so no launch can deadlock; results are unchanged.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------------------------ NTT
 // Forward: Cooley-Tukey with twiddles psi^{brev(k)}, natural order in, bit-reversed out.
 // Inverse: Gentleman-Sande with psi^{-brev(k)}, bit-reversed in, natural out, times n^-1.
 // n = R * 256: phase A runs the log2(R) stages whose butterfly distance is a multiple of 256
 // on a tile of R rows x NTT_TC columns in shared memory; phase B runs the last 8 stages on
 // 256-word rows, one warp per row.
+
 template <bool INV>
 __global__ void __launch_bounds__(256) ntt_cols(KP kp, ntt_job job) {
+    pdl_wait();
     extern __shared__ u64 sm[];
     const int p = blockIdx.z;
     const int limb = job_limb(job, blockIdx.y, p);
@@ -98,6 +110,7 @@ __global__ void __launch_bounds__(256) ntt_cols(KP kp, ntt_job job) {
 
 template <bool INV>
 __global__ void __launch_bounds__(256) ntt_rows(KP kp, ntt_job job) {
+    pdl_wait();
     __shared__ u64 sm[8][ROW];
     const int p = blockIdx.z;
     const int limb = job_limb(job, blockIdx.y, p);
@@ -212,6 +225,7 @@ __device__ __forceinline__ void reg_pass(u64 (&x)[16], int base, int ls, int log
 
 template <bool INV>
 __global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job) {
+    pdl_wait();
     __shared__ u64 sm[4096];
     const int p = blockIdx.z;
     const int limb = job_limb(job, blockIdx.y, p);
@@ -262,6 +276,7 @@ __device__ __forceinline__ int pad17(int k) { return k + (k >> 4); }
 
 template <bool INV>
 __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job) {
+    pdl_wait();
     __shared__ u64 sm[16][272];
     const int p = blockIdx.z;
     const int limb = job_limb(job, blockIdx.y, p);
@@ -312,6 +327,7 @@ __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job) {
 
 // ------------------------------------------------------------------------------ sampling
 __global__ void sample_uniform_kernel(KP kp, u64 seed, u64 stream, u64 *out, int nq) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int l = blockIdx.y;
     const int pr = prime_of(kp, l, nq);
@@ -325,6 +341,7 @@ __global__ void sample_uniform_kernel(KP kp, u64 seed, u64 stream, u64 *out, int
 }
 
 __global__ void sample_cbd_kernel(int n, u64 seed, u64 stream, int64_t *out) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     if (k >= n) return;
     u64 r = sm64_word(seed, stream, k);
@@ -332,6 +349,7 @@ __global__ void sample_cbd_kernel(int n, u64 seed, u64 stream, int64_t *out) {
 }
 
 __global__ void sample_ternary_kernel(int n, u64 seed, u64 stream, int64_t *out) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     if (k >= n) return;
     u64 r = sm64_word(seed, stream, k) % 3;
@@ -339,6 +357,7 @@ __global__ void sample_ternary_kernel(int n, u64 seed, u64 stream, int64_t *out)
 }
 
 __global__ void reduce_int_kernel(KP kp, const int64_t *m, u64 *out, int nq, int mont) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int l = blockIdx.y;
     const int pr = prime_of(kp, l, nq);
@@ -356,6 +375,7 @@ __global__ void reduce_int_kernel(KP kp, const int64_t *m, u64 *out, int nq, int
 }
 
 __global__ void mont_kernel(KP kp, u64 *x, int nq, size_t pstride, int to) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int l = blockIdx.y;
     const int pr = prime_of(kp, l, nq);
@@ -365,6 +385,7 @@ __global__ void mont_kernel(KP kp, u64 *x, int nq, size_t pstride, int to) {
 }
 
 __global__ void permute_kernel(KP kp, const u64 *in, u64 *out, u64 g) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const size_t off = (size_t)blockIdx.y * kp.n;
     out[off + k] = in[off + autom_index(k, g, kp.logn)];
@@ -374,6 +395,7 @@ __global__ void permute_kernel(KP kp, const u64 *in, u64 *out, u64 g) {
 // then (b, a) go to Montgomery form.  All inputs NTT form over Q_L u P (global order).
 __global__ void keygen_combine_kernel(KP kp, u64 *b, u64 *a, const u64 *e, const u64 *s,
                                       const u64 *sp, const u64 *pmod, int lo, int hi) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     const u64 q = kp.q[t], qi = kp.qinv[t], r2 = kp.r2[t];
@@ -388,6 +410,7 @@ __global__ void keygen_combine_kernel(KP kp, u64 *b, u64 *a, const u64 *e, const
 // c0 = e - a s + m over Q_l (NTT form)
 __global__ void encrypt_combine_kernel(KP kp, u64 *c0, const u64 *a, const u64 *e, const u64 *m,
                                        const u64 *s) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     const u64 q = kp.q[t], qi = kp.qinv[t], r2 = kp.r2[t];
@@ -397,6 +420,7 @@ __global__ void encrypt_combine_kernel(KP kp, u64 *c0, const u64 *a, const u64 *
 }
 
 __global__ void decrypt_dot_kernel(KP kp, const u64 *c, size_t pstride, const u64 *s, u64 *out) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     const u64 q = kp.q[t], qi = kp.qinv[t], r2 = kp.r2[t];
@@ -405,6 +429,7 @@ __global__ void decrypt_dot_kernel(KP kp, const u64 *c, size_t pstride, const u6
 }
 
 __global__ void addsub_kernel(KP kp, u64 *a, size_t pa, const u64 *b, size_t pb, int sub) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     const u64 q = kp.q[t];
@@ -414,6 +439,7 @@ __global__ void addsub_kernel(KP kp, u64 *a, size_t pa, const u64 *b, size_t pb,
 }
 
 __global__ void mul_scalar_kernel(KP kp, u64 *a, size_t pa, const u64 *res, const u64 *sh) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     u64 *x = a + blockIdx.z * pa + (size_t)t * kp.n + k;
@@ -425,6 +451,7 @@ struct Res64 {
 };
 
 __global__ void mul_scalar_v_kernel(KP kp, u64 *a, size_t pa, Res64 r) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     u64 *x = a + blockIdx.z * pa + (size_t)t * kp.n + k;
@@ -432,6 +459,7 @@ __global__ void mul_scalar_v_kernel(KP kp, u64 *a, size_t pa, Res64 r) {
 }
 
 __global__ void add_const_v_kernel(KP kp, u64 *a, Res64 r) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     u64 *x = a + (size_t)t * kp.n + k;
@@ -439,6 +467,7 @@ __global__ void add_const_v_kernel(KP kp, u64 *a, Res64 r) {
 }
 
 __global__ void mul_pointwise_kernel(KP kp, const u64 *a, const u64 *b, u64 *out) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     const size_t i = (size_t)t * kp.n + k;
@@ -446,6 +475,7 @@ __global__ void mul_pointwise_kernel(KP kp, const u64 *a, const u64 *b, u64 *out
 }
 
 __global__ void add_const_kernel(KP kp, u64 *a, const u64 *res) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     u64 *x = a + (size_t)t * kp.n + k;
@@ -453,6 +483,7 @@ __global__ void add_const_kernel(KP kp, u64 *a, const u64 *res) {
 }
 
 __global__ void zero_kernel(u64 *p, size_t words) {
+    pdl_wait();
     size_t i = (size_t)blockIdx.x * TB + threadIdx.x;
     if (i < words) p[i] = 0;
 }
@@ -503,11 +534,13 @@ __device__ __forceinline__ void modup_digit(const KP &kp, const ModupArgs &A, co
 }
 
 __global__ void __launch_bounds__(TB) modup_kernel(KP kp, ModupArgs A) {
+    pdl_wait();
     modup_digit(kp, A, A.x_coef, A.x_ntt, A.D, blockIdx.x * TB + threadIdx.x, blockIdx.y);
 }
 
 // several sources in one launch (blockIdx.z): coefficient-form c1 at x_coef + z nq n
 __global__ void __launch_bounds__(TB) modup_batch_kernel(KP kp, ModupArgs A, const modup_src *tab) {
+    pdl_wait();
     const int z = blockIdx.z;
     const size_t nqn = (size_t)(A.level + 1) * kp.n;
     modup_digit(kp, A, A.x_coef + z * nqn, tab[z].c1, tab[z].D, blockIdx.x * TB + threadIdx.x, blockIdx.y);
@@ -515,6 +548,7 @@ __global__ void __launch_bounds__(TB) modup_batch_kernel(KP kp, ModupArgs A, con
 
 // c1 (NTT form) of every source into one contiguous [n_src][words] buffer
 __global__ void gather_c1_kernel(const modup_src *tab, u64 *dst, size_t words) {
+    pdl_wait();
     const size_t k = (size_t)blockIdx.x * TB + threadIdx.x;
     if (k < words) dst[(size_t)blockIdx.y * words + k] = tab[blockIdx.y].c1[k];
 }
@@ -529,6 +563,7 @@ struct MdInline {
 };
 
 __global__ void __launch_bounds__(TB) ip_kernel(KP kp, const ip_item *items, IpInline inl, int level) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y;
     const ip_item it = items ? items[blockIdx.z] : inl.it[blockIdx.z];
@@ -554,6 +589,7 @@ __global__ void __launch_bounds__(TB) ip_kernel(KP kp, const ip_item *items, IpI
 // centred (y - p when 2y > p), so (u - conv) / P rounds instead of flooring.
 __global__ void __launch_bounds__(TB) moddown_fbc_kernel(KP kp, const u64 *u, u64 *conv,
                                                          int level, const u64 *tab) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int c = blockIdx.y;
     const int nq = level + 1;
@@ -587,6 +623,7 @@ __global__ void __launch_bounds__(TB) moddown_fbc_kernel(KP kp, const u64 *u, u6
 __global__ void __launch_bounds__(TB) moddown_combine_kernel(KP kp, const md_item *items, MdInline inl,
                                                              int level, const u64 *pinv,
                                                              const u64 *pinvs) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y;
     const md_item it = items ? items[blockIdx.z] : inl.it[blockIdx.z];
@@ -615,6 +652,7 @@ __global__ void __launch_bounds__(TB) moddown_combine_kernel(KP kp, const md_ite
 // u[i][c][l] += P base[i][c][l]  (NTT form, c = 0, 1; item i = blockIdx.z)
 __global__ void fold_top_kernel(KP kp, u64 *u, size_t u_is, size_t u_ps, const u64 *base, size_t b_is, size_t b_ps,
                                 int level, const u64 *pmod) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int c = blockIdx.y, i = blockIdx.z;
     const u64 q = kp.q[level], qi = kp.qinv[level], r2 = kp.r2[level];
@@ -627,6 +665,7 @@ __global__ void fold_top_kernel(KP kp, u64 *u, size_t u_is, size_t u_ps, const u
 // per poly (blockIdx.y): u = [ext][n] with limbs l..l+K in coefficient form; w = [l][n]
 __global__ void __launch_bounds__(TB) moddown_rescale_fbc_kernel(KP kp, const u64 *u, u64 *w, int level,
                                                                  const u64 *tab, const u64 *pinv, const u64 *pinvs) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int c = blockIdx.y;
     const int nq = level + 1;
@@ -686,6 +725,7 @@ struct MdrInline {
 __global__ void __launch_bounds__(TB) moddown_rescale_combine_kernel(KP kp, MdrInline inl, int level,
                                                                      const u64 *pinv, const u64 *pinvs,
                                                                      const u64 *linv, const u64 *linvs) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y;
     const mdr_item it = inl.it[blockIdx.z];
@@ -703,6 +743,7 @@ __global__ void __launch_bounds__(TB) moddown_rescale_combine_kernel(KP kp, MdrI
 // ------------------------------------------------------------------------------ rescale
 // t[c][i][k] = [centred c_l]_{q_i}, from the coefficient-form top limb of poly c
 __global__ void rescale_prep_kernel(KP kp, const u64 *top, size_t top_pstride, u64 *t, int level) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y;
     const int c = blockIdx.z;
@@ -721,6 +762,7 @@ __global__ void rescale_prep_kernel(KP kp, const u64 *top, size_t top_pstride, u
 
 __global__ void rescale_combine_kernel(KP kp, u64 *c, size_t pstride, const u64 *t, int level,
                                        const u64 *inv, const u64 *invs) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y;
     const int p = blockIdx.z;
@@ -735,6 +777,7 @@ __global__ void rescale_combine_kernel(KP kp, u64 *c, size_t pstride, const u64 
 __global__ void __launch_bounds__(TB) mac_kernel(KP kp, const mac_term *terms, mac_term one,
                                                  int n_terms, u64 *out, size_t out_pstride,
                                                  int accumulate) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y;
     const u64 q = kp.q[i], qi = kp.qinv[i];
@@ -828,6 +871,7 @@ __device__ __forceinline__ bool grp_pos(const KP &kp, const fgrp *grps, int n_gr
 template <int V, int B>
 __global__ void __launch_bounds__(TB, (V == 1 && B == 4) ? 2 : 1) ipmac_kernel(KP kp, const fgrp *grps, int n_grp,
                                                                                int gb, const u64 *pmod) {
+    pdl_wait();
     fgrp P;
     int tile, t, ptl;
     if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl)) return;
@@ -976,6 +1020,7 @@ __device__ __forceinline__ void tma_load(unsigned dst, const void *src, unsigned
 template <int V>
 __global__ void __launch_bounds__(TB) ipmac_tma_kernel(KP kp, const fgrp *grps, int n_grp, int gb, int *err,
                                                        const u64 *pmod) {
+    pdl_wait();
     constexpr int NS = TMA_STAGES;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     fgrp P;
@@ -1140,6 +1185,7 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 
 template <int V>
 __global__ void __launch_bounds__(TB) ipmac_cp_kernel(KP kp, const fgrp *grps, int n_grp, int gb, const u64 *pmod) {
+    pdl_wait();
     constexpr int RS = CP_STAGES, B = 4;
     constexpr int NW = 2 * B + B + V + 2;            // 16-byte words per item: keys, D, pt, c0, c1
     extern __shared__ ulonglong2 csm[];              // [RS][NW][TB]
@@ -1282,6 +1328,7 @@ __global__ void __launch_bounds__(TB) ipmac_cp_kernel(KP kp, const fgrp *grps, i
 // SM (24 warps to cover the key stream's latency).  Same arithmetic, same bits.
 template <int V, int B>
 __global__ void __launch_bounds__(TB, 3) ipmac1_kernel(KP kp, const fgrp *grps, int n_grp, int gb, const u64 *pmod) {
+    pdl_wait();
     fgrp P;
     int tile, t, ptl;
     if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl, TB)) return;
@@ -1377,6 +1424,7 @@ __global__ void __launch_bounds__(TB, 3) ipmac1_kernel(KP kp, const fgrp *grps, 
 template <int B, int MINB, bool PIPE>
 __global__ void __launch_bounds__(TB, MINB) ipmac_pk_kernel(KP kp, const fgrp *grps, int n_grp, int gb,
                                                             const u64 *pmod) {
+    pdl_wait();
     fgrp P;
     int tile, t, ptl;
     if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl)) return;
@@ -1462,6 +1510,7 @@ __global__ void __launch_bounds__(TB, MINB) ipmac_pk_kernel(KP kp, const fgrp *g
 // Ppt = [P]_q (.) pt on the q-limbs ([l+1][n]); pt holds pt_level + 1 q-limbs then the p-limbs.
 __global__ void prekey_kernel(KP kp, const u64 *key, const u64 *pt, int level, int pt_level, int beta, u64 *Kp,
                               u64 *Ppt, const u64 *pmod) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int t = blockIdx.y, z = blockIdx.z;
     const int nq = level + 1;
@@ -1490,6 +1539,7 @@ struct LincombArgs {
     int n_terms;
 };
 __global__ void lincomb_kernel(KP kp, LincombArgs A, u64 *out, size_t out_ps) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y;
     const int c = blockIdx.z;
@@ -1506,6 +1556,7 @@ __global__ void lincomb_kernel(KP kp, LincombArgs A, u64 *out, size_t out_ps) {
 
 __global__ void tensor_kernel(KP kp, const u64 *a, size_t pa, const u64 *b, size_t pb, u64 *d,
                               int level) {
+    pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y;
     const u64 q = kp.q[i], qi = kp.qinv[i], r2 = kp.r2[i];
@@ -1519,12 +1570,14 @@ __global__ void tensor_kernel(KP kp, const u64 *a, size_t pa, const u64 *b, size
 }
 
 __global__ void copy_kernel(u64 *dst, size_t dps, const u64 *src, size_t sps, size_t words) {
+    pdl_wait();
     size_t i = (size_t)blockIdx.x * TB + threadIdx.x;
     if (i >= words) return;
     dst[blockIdx.y * dps + i] = src[blockIdx.y * sps + i];
 }
 
 __global__ void bench_modmul_kernel(u64 q, u64 qinv, int iters, u64 *sink) {
+    pdl_wait();
     u64 x = threadIdx.x + 12345, y = blockIdx.x + 777;
     for (int it = 0; it < iters; it++) {
         x = redc((u128)x * y, q, qinv);
@@ -1536,6 +1589,27 @@ __global__ void bench_modmul_kernel(u64 q, u64 qinv, int iters, u64 *sink) {
 }  // namespace
 
 // ================================================================================= launchers
+// Every launch goes through cudaLaunchKernelEx with the programmatic-serialisation attribute
+// (process-wide switch, HE_OPT_PDL); errors surface through cudaGetLastError as for <<<>>>.
+static std::atomic<int> g_pdl{0};
+void he_set_pdl(int on) { g_pdl.store(on ? 1 : 0); }
+int he_get_pdl() { return g_pdl.load(); }
+template <typename... KArgs, typename... Args>
+static cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = g_pdl.load();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 #define LAUNCH_CHECK()                                        \
     do {                                                      \
         he_count_launch();                                    \
@@ -1555,14 +1629,14 @@ int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
         const int TC = 4096 / R;
         dim3 gA(ROW / TC, job.nl, job.npoly), gB(R / 16, job.nl, job.npoly);
         if (!inverse) {
-            ntt16_cols<false><<<gA, 256, 0, s>>>(ctx->kp, job);
+            pdl_launch(ntt16_cols<false>, gA, 256, 0, s, ctx->kp, job);
             LAUNCH_CHECK();
-            ntt16_rows<false><<<gB, 256, 0, s>>>(ctx->kp, job);
+            pdl_launch(ntt16_rows<false>, gB, 256, 0, s, ctx->kp, job);
             LAUNCH_CHECK();
         } else {
-            ntt16_rows<true><<<gB, 256, 0, s>>>(ctx->kp, job);
+            pdl_launch(ntt16_rows<true>, gB, 256, 0, s, ctx->kp, job);
             LAUNCH_CHECK();
-            ntt16_cols<true><<<gA, 256, 0, s>>>(ctx->kp, job);
+            pdl_launch(ntt16_cols<true>, gA, 256, 0, s, ctx->kp, job);
             LAUNCH_CHECK();
         }
         return HE_OK;
@@ -1572,14 +1646,14 @@ int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
     const double limbs = (double)job.nl * job.npoly;
     TraceScope tr("ntt", s, limbs * 2.0 * ctx->n * 8, limbs * (ctx->n / 2) * ctx->logn);
     if (!inverse) {
-        ntt_cols<false><<<gA, 256, smA, s>>>(ctx->kp, job);
+        pdl_launch(ntt_cols<false>, gA, 256, smA, s, ctx->kp, job);
         LAUNCH_CHECK();
-        ntt_rows<false><<<gB, 256, 0, s>>>(ctx->kp, job);
+        pdl_launch(ntt_rows<false>, gB, 256, 0, s, ctx->kp, job);
         LAUNCH_CHECK();
     } else {
-        ntt_rows<true><<<gB, 256, 0, s>>>(ctx->kp, job);
+        pdl_launch(ntt_rows<true>, gB, 256, 0, s, ctx->kp, job);
         LAUNCH_CHECK();
-        ntt_cols<true><<<gA, 256, smA, s>>>(ctx->kp, job);
+        pdl_launch(ntt_cols<true>, gA, 256, smA, s, ctx->kp, job);
         LAUNCH_CHECK();
     }
     return HE_OK;
@@ -1587,46 +1661,46 @@ int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
 
 int k_reduce_int(const he_ctx *ctx, const int64_t *m, u64 *out, int nlimbs, int nq, bool mont,
                  cudaStream_t s) {
-    reduce_int_kernel<<<dim3(ctx->n / TB, nlimbs), TB, 0, s>>>(ctx->kp, m, out, nq, mont ? 1 : 0);
+    pdl_launch(reduce_int_kernel, dim3(ctx->n / TB, nlimbs), TB, 0, s, ctx->kp, m, out, nq, mont ? 1 : 0);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_to_mont(const he_ctx *ctx, u64 *x, int nlimbs, int nq, int npoly, size_t pstride,
               cudaStream_t s) {
-    mont_kernel<<<dim3(ctx->n / TB, nlimbs, npoly), TB, 0, s>>>(ctx->kp, x, nq, pstride, 1);
+    pdl_launch(mont_kernel, dim3(ctx->n / TB, nlimbs, npoly), TB, 0, s, ctx->kp, x, nq, pstride, 1);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_from_mont(const he_ctx *ctx, u64 *x, int nlimbs, int nq, int npoly, size_t pstride,
                 cudaStream_t s) {
-    mont_kernel<<<dim3(ctx->n / TB, nlimbs, npoly), TB, 0, s>>>(ctx->kp, x, nq, pstride, 0);
+    pdl_launch(mont_kernel, dim3(ctx->n / TB, nlimbs, npoly), TB, 0, s, ctx->kp, x, nq, pstride, 0);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_sample_uniform(const he_ctx *ctx, u64 seed, u64 stream, u64 *out, int nlimbs, int nq,
                      cudaStream_t s) {
-    sample_uniform_kernel<<<dim3(ctx->n / TB, nlimbs), TB, 0, s>>>(ctx->kp, seed, stream, out, nq);
+    pdl_launch(sample_uniform_kernel, dim3(ctx->n / TB, nlimbs), TB, 0, s, ctx->kp, seed, stream, out, nq);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_sample_cbd(const he_ctx *ctx, u64 seed, u64 stream, int64_t *out, cudaStream_t s) {
-    sample_cbd_kernel<<<ctx->n / TB, TB, 0, s>>>(ctx->n, seed, stream, out);
+    pdl_launch(sample_cbd_kernel, ctx->n / TB, TB, 0, s, ctx->n, seed, stream, out);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_sample_ternary(const he_ctx *ctx, u64 seed, u64 stream, int64_t *out, cudaStream_t s) {
-    sample_ternary_kernel<<<ctx->n / TB, TB, 0, s>>>(ctx->n, seed, stream, out);
+    pdl_launch(sample_ternary_kernel, ctx->n / TB, TB, 0, s, ctx->n, seed, stream, out);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_permute(const he_ctx *ctx, const u64 *in, u64 *out, int nlimbs, u64 g, cudaStream_t s) {
-    permute_kernel<<<dim3(ctx->n / TB, nlimbs), TB, 0, s>>>(ctx->kp, in, out, g);
+    pdl_launch(permute_kernel, dim3(ctx->n / TB, nlimbs), TB, 0, s, ctx->kp, in, out, g);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1634,7 +1708,7 @@ int k_permute(const he_ctx *ctx, const u64 *in, u64 *out, int nlimbs, u64 g, cud
 int k_keygen_combine(const he_ctx *ctx, u64 *b, u64 *a, const u64 *e, const u64 *s_eval,
                      const u64 *sp_eval, int digit, cudaStream_t s) {
     int lo = digit * ctx->alpha, hi = std::min(lo + ctx->alpha, ctx->L + 1);
-    keygen_combine_kernel<<<dim3(ctx->n / TB, ctx->np), TB, 0, s>>>(
+    pdl_launch(keygen_combine_kernel, dim3(ctx->n / TB, ctx->np), TB, 0, s, 
         ctx->kp, b, a, e, s_eval, sp_eval, ctx->d_consts, lo, hi);
     LAUNCH_CHECK();
     return HE_OK;
@@ -1642,19 +1716,19 @@ int k_keygen_combine(const he_ctx *ctx, u64 *b, u64 *a, const u64 *e, const u64 
 
 int k_encrypt_combine(const he_ctx *ctx, u64 *c0, const u64 *a, const u64 *e, const u64 *m,
                       int level, cudaStream_t s) {
-    encrypt_combine_kernel<<<dim3(ctx->n / TB, level + 1), TB, 0, s>>>(ctx->kp, c0, a, e, m, ctx->d_s);
+    pdl_launch(encrypt_combine_kernel, dim3(ctx->n / TB, level + 1), TB, 0, s, ctx->kp, c0, a, e, m, ctx->d_s);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_decrypt_dot(const he_ctx *ctx, const he_ct *ct, u64 *out, int nlimbs, cudaStream_t s) {
-    decrypt_dot_kernel<<<dim3(ctx->n / TB, nlimbs), TB, 0, s>>>(ctx->kp, ct->d, ct->pstride, ctx->d_s, out);
+    pdl_launch(decrypt_dot_kernel, dim3(ctx->n / TB, nlimbs), TB, 0, s, ctx->kp, ct->d, ct->pstride, ctx->d_s, out);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_add(const he_ctx *ctx, he_ct *acc, const he_ct *b, bool sub, cudaStream_t s) {
-    addsub_kernel<<<dim3(ctx->n / TB, acc->level + 1, 2), TB, 0, s>>>(
+    pdl_launch(addsub_kernel, dim3(ctx->n / TB, acc->level + 1, 2), TB, 0, s, 
         ctx->kp, acc->d, acc->pstride, b->d, b->pstride, sub ? 1 : 0);
     LAUNCH_CHECK();
     return HE_OK;
@@ -1662,33 +1736,33 @@ int k_add(const he_ctx *ctx, he_ct *acc, const he_ct *b, bool sub, cudaStream_t 
 
 int k_add_raw(const he_ctx *ctx, u64 *a, size_t pa, const u64 *b, size_t pb, int nlimbs, int npoly,
               bool sub, cudaStream_t s) {
-    addsub_kernel<<<dim3(ctx->n / TB, nlimbs, npoly), TB, 0, s>>>(ctx->kp, a, pa, b, pb, sub ? 1 : 0);
+    pdl_launch(addsub_kernel, dim3(ctx->n / TB, nlimbs, npoly), TB, 0, s, ctx->kp, a, pa, b, pb, sub ? 1 : 0);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_mul_scalar(const he_ctx *ctx, he_ct *ct, const u64 *res, const u64 *shoup, cudaStream_t s) {
-    mul_scalar_kernel<<<dim3(ctx->n / TB, ct->level + 1, 2), TB, 0, s>>>(ctx->kp, ct->d, ct->pstride, res, shoup);
+    pdl_launch(mul_scalar_kernel, dim3(ctx->n / TB, ct->level + 1, 2), TB, 0, s, ctx->kp, ct->d, ct->pstride, res, shoup);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_add_const(const he_ctx *ctx, he_ct *ct, const u64 *res_dev, cudaStream_t s) {
-    add_const_kernel<<<dim3(ctx->n / TB, ct->level + 1), TB, 0, s>>>(ctx->kp, ct->d, res_dev);
+    pdl_launch(add_const_kernel, dim3(ctx->n / TB, ct->level + 1), TB, 0, s, ctx->kp, ct->d, res_dev);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_zero(u64 *p, size_t words, cudaStream_t s) {
     if (!words) return HE_OK;
-    zero_kernel<<<(unsigned)((words + TB - 1) / TB), TB, 0, s>>>(p, words);
+    pdl_launch(zero_kernel, (unsigned)((words + TB - 1) / TB), TB, 0, s, p, words);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_copy_limbs(u64 *dst, size_t dps, const u64 *src, size_t sps, size_t words, int npoly,
                  cudaStream_t s) {
-    copy_kernel<<<dim3((unsigned)((words + TB - 1) / TB), npoly), TB, 0, s>>>(dst, dps, src, sps, words);
+    pdl_launch(copy_kernel, dim3((unsigned)((words + TB - 1) / TB), npoly), TB, 0, s, dst, dps, src, sps, words);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1702,7 +1776,7 @@ int k_modup_batch(const he_ctx *ctx, const modup_src *d_tab, int n_src, u64 *tmp
         return HE_EINVAL;
     }
     const size_t words = (size_t)nq * ctx->n;
-    gather_c1_kernel<<<dim3((unsigned)((words + TB - 1) / TB), n_src), TB, 0, s>>>(d_tab, tmp, words);
+    pdl_launch(gather_c1_kernel, dim3((unsigned)((words + TB - 1) / TB), n_src), TB, 0, s, d_tab, tmp, words);
     LAUNCH_CHECK();
     ntt_job ji{tmp, words, 0, nq, nq, 0, n_src, 0};
     HE_TRY(k_ntt(ctx, ji, true, s));
@@ -1716,7 +1790,7 @@ int k_modup_batch(const he_ctx *ctx, const modup_src *d_tab, int n_src, u64 *tmp
     {
         TraceScope tr("modup", s, (double)n_src * (nq + beta * ext) * ctx->n * 8,
                       (double)n_src * (nq + (double)beta * (ext - ctx->alpha) * ctx->alpha) * ctx->n);
-        modup_batch_kernel<<<dim3(ctx->n / TB, beta, n_src), TB, 0, s>>>(ctx->kp, A, d_tab);
+        pdl_launch(modup_batch_kernel, dim3(ctx->n / TB, beta, n_src), TB, 0, s, ctx->kp, A, d_tab);
         LAUNCH_CHECK();
     }
     return HE_OK;
@@ -1738,7 +1812,7 @@ int k_modup(const he_ctx *ctx, const u64 *x_coef, const u64 *x_ntt, u64 *D, int 
     for (int j = 0; j < beta; j++) A.tab[j] = ctx->modup[level][j].d;
     const double nq = level + 1, ext = nq + ctx->K;
     TraceScope tr("modup", s, (nq + beta * ext) * ctx->n * 8, (nq + (double)beta * (ext - ctx->alpha) * ctx->alpha) * ctx->n);
-    modup_kernel<<<dim3(ctx->n / TB, beta), TB, 0, s>>>(ctx->kp, A);
+    pdl_launch(modup_kernel, dim3(ctx->n / TB, beta), TB, 0, s, ctx->kp, A);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1755,7 +1829,7 @@ static double ip_mulmods(const he_ctx *ctx, int level, int items) {
 int k_inner_product(const he_ctx *ctx, const ip_item *items_dev, int n_items, int level,
                     cudaStream_t s) {
     TraceScope tr("ip", s, ip_bytes(ctx, level, n_items), ip_mulmods(ctx, level, n_items));
-    ip_kernel<<<dim3(ctx->n / TB, level + 1 + ctx->K, n_items), TB, 0, s>>>(ctx->kp, items_dev, IpInline{},
+    pdl_launch(ip_kernel, dim3(ctx->n / TB, level + 1 + ctx->K, n_items), TB, 0, s, ctx->kp, items_dev, IpInline{},
                                                                              level);
     LAUNCH_CHECK();
     return HE_OK;
@@ -1767,7 +1841,7 @@ int k_inner_product_inline(const he_ctx *ctx, const ip_item *items, int n, int l
         IpInline inl;
         for (int i = 0; i < cnt; i++) inl.it[i] = items[i0 + i];
         TraceScope tr("ip", s, ip_bytes(ctx, level, cnt), ip_mulmods(ctx, level, cnt));
-        ip_kernel<<<dim3(ctx->n / TB, level + 1 + ctx->K, cnt), TB, 0, s>>>(ctx->kp, nullptr, inl, level);
+        pdl_launch(ip_kernel, dim3(ctx->n / TB, level + 1 + ctx->K, cnt), TB, 0, s, ctx->kp, nullptr, inl, level);
         LAUNCH_CHECK();
     }
     return HE_OK;
@@ -1785,7 +1859,7 @@ int k_moddown_fbc(const he_ctx *ctx, const u64 *u, u64 *conv, int level, int npo
     }
     const double nq = level + 1;
     TraceScope tr("moddown_fbc", s, (double)npoly * (ctx->K + nq) * ctx->n * 8, (double)npoly * (ctx->K + nq * ctx->K) * ctx->n);
-    moddown_fbc_kernel<<<dim3(ctx->n / TB, npoly), TB, 0, s>>>(ctx->kp, u, conv, level,
+    pdl_launch(moddown_fbc_kernel, dim3(ctx->n / TB, npoly), TB, 0, s, ctx->kp, u, conv, level,
                                                               ctx->moddown[level].d);
     LAUNCH_CHECK();
     return HE_OK;
@@ -1796,7 +1870,7 @@ int k_moddown_combine(const he_ctx *ctx, const md_item *items_dev, int n_items, 
     const u64 *pinv = ctx->d_consts + ctx->np;
     const u64 *pinvs = pinv + (ctx->L + 1);
     TraceScope tr("moddown_combine", s, (double)n_items * (level + 1) * ctx->n * 8 * 7, (double)n_items * (level + 1) * ctx->n * 2);
-    moddown_combine_kernel<<<dim3(ctx->n / TB, level + 1, n_items), TB, 0, s>>>(
+    pdl_launch(moddown_combine_kernel, dim3(ctx->n / TB, level + 1, n_items), TB, 0, s, 
         ctx->kp, items_dev, MdInline{}, level, pinv, pinvs);
     LAUNCH_CHECK();
     return HE_OK;
@@ -1811,7 +1885,7 @@ int k_moddown_combine_inline(const he_ctx *ctx, const md_item *items, int n, int
         for (int i = 0; i < cnt; i++) inl.it[i] = items[i0 + i];
         TraceScope tr("moddown_combine", s, (double)cnt * (level + 1) * ctx->n * 8 * 7,
                       (double)cnt * (level + 1) * ctx->n * 2);
-        moddown_combine_kernel<<<dim3(ctx->n / TB, level + 1, cnt), TB, 0, s>>>(ctx->kp, nullptr, inl, level,
+        pdl_launch(moddown_combine_kernel, dim3(ctx->n / TB, level + 1, cnt), TB, 0, s, ctx->kp, nullptr, inl, level,
                                                                                pinv, pinvs);
         LAUNCH_CHECK();
     }
@@ -1831,7 +1905,7 @@ int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, s
     if (ctx->K > 16 || level < 1) { he_set_error("moddown-rescale: bad level or special primes"); return HE_EINVAL; }
     const int nq = level + 1, ext = nq + ctx->K;
     const size_t we = (size_t)ext * ctx->n;
-    fold_top_kernel<<<dim3(ctx->n / TB, 2, m), TB, 0, s>>>(ctx->kp, u, 2 * we, we, base, b_is, b_ps, level,
+    pdl_launch(fold_top_kernel, dim3(ctx->n / TB, 2, m), TB, 0, s, ctx->kp, u, 2 * we, we, base, b_is, b_ps, level,
                                                            ctx->d_consts);
     LAUNCH_CHECK();
     ntt_job ju{u, we, level, ctx->K + 1, nq, 0, 2 * m, 0};
@@ -1841,7 +1915,7 @@ int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, s
     {
         TraceScope tr("moddown_fbc", s, (double)2 * m * (ctx->K + 1 + level) * ctx->n * 8,
                       (double)2 * m * (ctx->K + nq * ctx->K + level) * ctx->n);
-        moddown_rescale_fbc_kernel<<<dim3(ctx->n / TB, 2 * m), TB, 0, s>>>(ctx->kp, u, w, level,
+        pdl_launch(moddown_rescale_fbc_kernel, dim3(ctx->n / TB, 2 * m), TB, 0, s, ctx->kp, u, w, level,
                                                                           ctx->moddown[level].d, pinv, pinvs);
         LAUNCH_CHECK();
     }
@@ -1859,7 +1933,7 @@ int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, s
                                  out[j], out_ps[j]};
         }
         TraceScope tr("moddown_combine", s, (double)cnt * level * ctx->n * 8 * 9, (double)cnt * level * ctx->n * 4);
-        moddown_rescale_combine_kernel<<<dim3(ctx->n / TB, level, cnt), TB, 0, s>>>(ctx->kp, inl, level, pinv, pinvs,
+        pdl_launch(moddown_rescale_combine_kernel, dim3(ctx->n / TB, level, cnt), TB, 0, s, ctx->kp, inl, level, pinv, pinvs,
                                                                                    linv, linvs);
         LAUNCH_CHECK();
     }
@@ -1868,7 +1942,7 @@ int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, s
 
 int k_rescale_prep(const he_ctx *ctx, const u64 *top, size_t top_pstride, u64 *t, int level,
                    cudaStream_t s) {
-    rescale_prep_kernel<<<dim3(ctx->n / TB, level, 2), TB, 0, s>>>(ctx->kp, top, top_pstride, t, level);
+    pdl_launch(rescale_prep_kernel, dim3(ctx->n / TB, level, 2), TB, 0, s, ctx->kp, top, top_pstride, t, level);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1879,7 +1953,7 @@ int k_rescale_combine(const he_ctx *ctx, he_ct *ct, const u64 *t, cudaStream_t s
     const u64 *inv = base + (size_t)l * 2 * (ctx->L + 1);
     const u64 *invs = inv + (ctx->L + 1);
     TraceScope tr("rescale", s, (double)l * ctx->n * 8 * 6, (double)l * ctx->n * 2);
-    rescale_combine_kernel<<<dim3(ctx->n / TB, l, 2), TB, 0, s>>>(ctx->kp, ct->d, ct->pstride, t, l, inv, invs);
+    pdl_launch(rescale_combine_kernel, dim3(ctx->n / TB, l, 2), TB, 0, s, ctx->kp, ct->d, ct->pstride, t, l, inv, invs);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1887,7 +1961,7 @@ int k_rescale_combine(const he_ctx *ctx, he_ct *ct, const u64 *t, cudaStream_t s
 int k_mac(const he_ctx *ctx, const mac_term *terms_dev, int n_terms, u64 *out, size_t out_pstride,
           int level, bool accumulate, cudaStream_t s) {
     TraceScope tr("mac", s, (double)(level + 1) * ctx->n * 8 * (3.0 * n_terms + 2), (double)(level + 1) * ctx->n * 2.0 * n_terms);
-    mac_kernel<<<dim3(ctx->n / TB, level + 1), TB, 0, s>>>(ctx->kp, terms_dev, mac_term{}, n_terms, out,
+    pdl_launch(mac_kernel, dim3(ctx->n / TB, level + 1), TB, 0, s, ctx->kp, terms_dev, mac_term{}, n_terms, out,
                                                           out_pstride, accumulate ? 1 : 0);
     LAUNCH_CHECK();
     return HE_OK;
@@ -1895,7 +1969,7 @@ int k_mac(const he_ctx *ctx, const mac_term *terms_dev, int n_terms, u64 *out, s
 
 int k_mac_one(const he_ctx *ctx, const mac_term &t, u64 *out, size_t out_pstride, int level,
               bool accumulate, cudaStream_t s) {
-    mac_kernel<<<dim3(ctx->n / TB, level + 1), TB, 0, s>>>(ctx->kp, nullptr, t, 1, out, out_pstride,
+    pdl_launch(mac_kernel, dim3(ctx->n / TB, level + 1), TB, 0, s, ctx->kp, nullptr, t, 1, out, out_pstride,
                                                           accumulate ? 1 : 0);
     LAUNCH_CHECK();
     return HE_OK;
@@ -1905,7 +1979,7 @@ int k_mul_scalar_v(const he_ctx *ctx, he_ct *ct, const u64 *res, const u64 *shou
                    cudaStream_t s) {
     Res64 r;
     for (int i = 0; i <= ct->level; i++) { r.v[i] = res[i]; r.s[i] = shoup[i]; }
-    mul_scalar_v_kernel<<<dim3(ctx->n / TB, ct->level + 1, polys), TB, 0, s>>>(ctx->kp, ct->d, ct->pstride, r);
+    pdl_launch(mul_scalar_v_kernel, dim3(ctx->n / TB, ct->level + 1, polys), TB, 0, s, ctx->kp, ct->d, ct->pstride, r);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1913,20 +1987,20 @@ int k_mul_scalar_v(const he_ctx *ctx, he_ct *ct, const u64 *res, const u64 *shou
 int k_add_const_v(const he_ctx *ctx, he_ct *ct, const u64 *res, cudaStream_t s) {
     Res64 r;
     for (int i = 0; i <= ct->level; i++) { r.v[i] = res[i]; r.s[i] = 0; }
-    add_const_v_kernel<<<dim3(ctx->n / TB, ct->level + 1), TB, 0, s>>>(ctx->kp, ct->d, r);
+    pdl_launch(add_const_v_kernel, dim3(ctx->n / TB, ct->level + 1), TB, 0, s, ctx->kp, ct->d, r);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_mul_pointwise(const he_ctx *ctx, const u64 *a, const u64 *b, u64 *out, int nlimbs,
                     cudaStream_t s) {
-    mul_pointwise_kernel<<<dim3(ctx->n / TB, nlimbs), TB, 0, s>>>(ctx->kp, a, b, out);
+    pdl_launch(mul_pointwise_kernel, dim3(ctx->n / TB, nlimbs), TB, 0, s, ctx->kp, a, b, out);
     LAUNCH_CHECK();
     return HE_OK;
 }
 
 int k_tensor(const he_ctx *ctx, const he_ct *a, const he_ct *b, u64 *d, cudaStream_t s) {
-    tensor_kernel<<<dim3(ctx->n / TB, a->level + 1), TB, 0, s>>>(ctx->kp, a->d, a->pstride, b->d, b->pstride, d,
+    pdl_launch(tensor_kernel, dim3(ctx->n / TB, a->level + 1), TB, 0, s, ctx->kp, a->d, a->pstride, b->d, b->pstride, d,
                                                                 a->level);
     LAUNCH_CHECK();
     return HE_OK;
@@ -1935,7 +2009,7 @@ int k_tensor(const he_ctx *ctx, const he_ct *a, const he_ct *b, u64 *d, cudaStre
 int k_prekey(const he_ctx *ctx, const u64 *key, const u64 *pt, int level, int pt_level, int beta, u64 *Kp, u64 *Ppt,
              cudaStream_t s) {
     dim3 g(ctx->n / TB, level + 1 + ctx->K, 2 * beta + 1);
-    prekey_kernel<<<g, TB, 0, s>>>(ctx->kp, key, pt, level, pt_level, beta, Kp, Ppt, ctx->d_consts);
+    pdl_launch(prekey_kernel, g, TB, 0, s, ctx->kp, key, pt, level, pt_level, beta, Kp, Ppt, ctx->d_consts);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1961,9 +2035,9 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
         if (!attr_ok) { he_set_error("fused kernel: shared-memory opt-in failed"); return HE_ECUDA; }
         dim3 gt(gx, primes);
         if (V == 1)
-            ipmac_tma_kernel<1><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
+            pdl_launch(ipmac_tma_kernel<1>, gt, TB, smem, s, ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
         else
-            ipmac_tma_kernel<2><<<gt, TB, smem, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
+            pdl_launch(ipmac_tma_kernel<2>, gt, TB, smem, s, ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
         LAUNCH_CHECK();
         return HE_OK;
     }
@@ -1971,17 +2045,17 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
         if (V != 1) { he_set_error("k_ipmac: the pre-keyed form takes one output per group"); return HE_EINVAL; }
         dim3 gp(gx, primes);
         if (form == HE_FORM_PK3 && max_beta <= 4)
-            ipmac_pk_kernel<4, 3, false><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+            pdl_launch(ipmac_pk_kernel<4, 3, false>, gp, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
         else if (form == HE_FORM_PKP && max_beta <= 4)
-            ipmac_pk_kernel<4, 2, true><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
-        else if (max_beta <= 4) ipmac_pk_kernel<4, 2, false><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
-        else ipmac_pk_kernel<8, 2, false><<<gp, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+            pdl_launch(ipmac_pk_kernel<4, 2, true>, gp, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else if (max_beta <= 4) pdl_launch(ipmac_pk_kernel<4, 2, false>, gp, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else pdl_launch(ipmac_pk_kernel<8, 2, false>, gp, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
         LAUNCH_CHECK();
         return HE_OK;
     }
     if (form == HE_KEY_STREAM_LDG1) {
         dim3 g1((unsigned)((n_grp + gb - 1) / gb) * gb * (ctx->n / TB), primes);
-#define IPM1(VV, BB) ipmac1_kernel<VV, BB><<<g1, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts)
+#define IPM1(VV, BB) pdl_launch(ipmac1_kernel<VV, BB>, g1, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts)
         if (V == 1) { if (max_beta <= 4) IPM1(1, 4); else IPM1(1, 8); }
         else { if (max_beta <= 4) IPM1(2, 4); else IPM1(2, 8); }
 #undef IPM1
@@ -1998,13 +2072,13 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
                 cudaSuccess;
         if (!attr_ok) { he_set_error("fused kernel: shared-memory opt-in failed"); return HE_ECUDA; }
         dim3 gc(gx, primes);
-        if (V == 1) ipmac_cp_kernel<1><<<gc, TB, smem1, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
-        else ipmac_cp_kernel<2><<<gc, TB, smem2, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        if (V == 1) pdl_launch(ipmac_cp_kernel<1>, gc, TB, smem1, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else pdl_launch(ipmac_cp_kernel<2>, gc, TB, smem2, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
         LAUNCH_CHECK();
         return HE_OK;
     }
     dim3 g(gx, primes);
-#define IPM(VV, BB) ipmac_kernel<VV, BB><<<g, TB, 0, s>>>(ctx->kp, grps, n_grp, gb, ctx->d_consts)
+#define IPM(VV, BB) pdl_launch(ipmac_kernel<VV, BB>, g, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts)
     if (V == 1) { if (max_beta <= 4) IPM(1, 4); else IPM(1, 8); }
     else { if (max_beta <= 4) IPM(2, 4); else IPM(2, 8); }
 #undef IPM
@@ -2040,6 +2114,7 @@ constexpr int IPA_STAGES = 4;
 
 template <int B>
 __global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps, int n_grp, const u64 *pmod) {
+    pdl_wait();
     constexpr int RS = IPA_STAGES, NW = B + 2;        // words per entry: D[B], c0, c1
     extern __shared__ u64 ism[];                      // [RS][NW][TB]
     const ugrp P = grps[blockIdx.x % n_grp];
@@ -2127,6 +2202,7 @@ constexpr int RMAC_STAGES = 4;
 constexpr int RMAC_WORDS = 2 + HE_RV;               // u0, u1, pt[HE_RV]
 
 __global__ void __launch_bounds__(TB, 2) rmac_kernel(KP kp, const rgrp *grps, int n_grp) {
+    pdl_wait();
     constexpr int RV = HE_RV, RS = RMAC_STAGES;
     extern __shared__ u64 rsm[];                     // [RS][RMAC_WORDS][TB]
     const rgrp P = grps[blockIdx.x % n_grp];
@@ -2203,8 +2279,8 @@ int k_ip_amounts(const he_ctx *ctx, const ugrp *grps, int n_grp, int max_beta, d
         cudaFuncSetAttribute(ip_amounts_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem4) == cudaSuccess &&
         cudaFuncSetAttribute(ip_amounts_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem8) == cudaSuccess;
     if (!attr_ok) { he_set_error("ip_amounts: shared-memory opt-in failed"); return HE_ECUDA; }
-    if (max_beta <= 4) ip_amounts_kernel<4><<<g, TB, smem4, s>>>(ctx->kp, grps, n_grp, ctx->d_consts);
-    else ip_amounts_kernel<8><<<g, TB, smem8, s>>>(ctx->kp, grps, n_grp, ctx->d_consts);
+    if (max_beta <= 4) pdl_launch(ip_amounts_kernel<4>, g, TB, smem4, s, ctx->kp, grps, n_grp, ctx->d_consts);
+    else pdl_launch(ip_amounts_kernel<8>, g, TB, smem8, s, ctx->kp, grps, n_grp, ctx->d_consts);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -2217,7 +2293,7 @@ int k_rmac(const he_ctx *ctx, const rgrp *grps, int n_grp, double bytes, double 
     static const bool attr_ok =
         cudaFuncSetAttribute(rmac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
     if (!attr_ok) { he_set_error("rmac: shared-memory opt-in failed"); return HE_ECUDA; }
-    rmac_kernel<<<g, TB, smem, s>>>(ctx->kp, grps, n_grp);
+    pdl_launch(rmac_kernel, g, TB, smem, s, ctx->kp, grps, n_grp);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -2231,6 +2307,7 @@ constexpr int SM_OB = 16;
 __global__ void __launch_bounds__(TB) smac_kernel(KP kp, const u64 *Y, size_t ystride, size_t yps, const u64 *Wm,
                                                   int co, int ci, int H, int T, u64 *out, size_t ostride,
                                                   size_t ops) {
+    pdl_wait();
     extern __shared__ u64 wsm[];                                   // [SM_OB][nin]
     const int nin = ci * T;
     const int k = blockIdx.x * TB + threadIdx.x;
@@ -2284,7 +2361,7 @@ int k_smac(const he_ctx *ctx, const u64 *Y, size_t ystride, size_t yps, const u6
                                  (double)co * H * 2 * nl * ctx->n * 8,
                   (double)co * H * ci * T * 2 * nl * ctx->n);
     dim3 g(ctx->n / TB, 2 * (level + 1), H * ((co + SM_OB - 1) / SM_OB));
-    smac_kernel<<<g, TB, smem, s>>>(ctx->kp, Y, ystride, yps, Wm, co, ci, H, T, out, ostride, ops);
+    pdl_launch(smac_kernel, g, TB, smem, s, ctx->kp, Y, ystride, yps, Wm, co, ci, H, T, out, ostride, ops);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -2293,6 +2370,7 @@ int k_smac(const he_ctx *ctx, const u64 *Y, size_t ystride, size_t yps, const u6
 // that nothing will ever arrive on; the wait gives up, the kernel records the timeout in the
 // context's error word and returns, leaving the context usable.
 __global__ void bounded_wait_selftest_kernel(int *err) {
+    pdl_wait();
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
         mbar_init(smem_u32(&bar), 1);
@@ -2305,7 +2383,7 @@ __global__ void bounded_wait_selftest_kernel(int *err) {
 
 int k_selftest_bounded_wait(const he_ctx *ctx, cudaStream_t s) {
     if (!ctx->d_err) { he_set_error("context has no error word"); return HE_ESTATE; }
-    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>(ctx->d_err);
+    pdl_launch(bounded_wait_selftest_kernel, 1, 32, 0, s, ctx->d_err);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -2325,7 +2403,7 @@ int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u6
     }
     for (int i = 0; i <= level; i++) A.cst[i] = cst[i];
     A.n_terms = n;
-    lincomb_kernel<<<dim3(ctx->n / TB, level + 1, 2), TB, 0, s>>>(ctx->kp, A, out, out_ps);
+    pdl_launch(lincomb_kernel, dim3(ctx->n / TB, level + 1, 2), TB, 0, s, ctx->kp, A, out, out_ps);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -2334,7 +2412,7 @@ int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u6
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s) {
     ntt_job top{base, ps, level, 1, level + 1, 0, 2 * m, 0};
     HE_TRY(k_ntt(ctx, top, true, s));
-    rescale_prep_kernel<<<dim3(ctx->n / TB, level, 2 * m), TB, 0, s>>>(ctx->kp, base + (size_t)level * ctx->n, ps, t, level);
+    pdl_launch(rescale_prep_kernel, dim3(ctx->n / TB, level, 2 * m), TB, 0, s, ctx->kp, base + (size_t)level * ctx->n, ps, t, level);
     LAUNCH_CHECK();
     ntt_job tj{t, (size_t)level * ctx->n, 0, level, level, 0, 2 * m, 0};
     HE_TRY(k_ntt(ctx, tj, false, s));
@@ -2342,7 +2420,7 @@ int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u6
     const u64 *inv = cb + (size_t)level * 2 * (ctx->L + 1);
     const u64 *invs = inv + (ctx->L + 1);
     TraceScope tr("rescale", s, (double)m * level * ctx->n * 8 * 6, (double)m * level * ctx->n * 2);
-    rescale_combine_kernel<<<dim3(ctx->n / TB, level, 2 * m), TB, 0, s>>>(ctx->kp, base, ps, t, level, inv, invs);
+    pdl_launch(rescale_combine_kernel, dim3(ctx->n / TB, level, 2 * m), TB, 0, s, ctx->kp, base, ps, t, level, inv, invs);
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -2354,9 +2432,9 @@ double k_bench_modmul(const he_ctx *ctx, int blocks, int iters, cudaStream_t s) 
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const u64 q = ctx->primes[0];
-    bench_modmul_kernel<<<blocks, 256, 0, s>>>(q, ctx->h_qinv[0], 16, sink);   // warm-up
+    pdl_launch(bench_modmul_kernel, blocks, 256, 0, s, q, ctx->h_qinv[0], 16, sink);   // warm-up
     cudaEventRecord(e0, s);
-    bench_modmul_kernel<<<blocks, 256, 0, s>>>(q, ctx->h_qinv[0], iters, sink);
+    pdl_launch(bench_modmul_kernel, blocks, 256, 0, s, q, ctx->h_qinv[0], iters, sink);
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
     he_count_launch(2);

@@ -19,6 +19,7 @@ HE_OPT_KEY_STREAM = 1
 HE_KEY_STREAM_LDG, HE_KEY_STREAM_TMA, HE_KEY_STREAM_AUTO, HE_KEY_STREAM_SPLIT, HE_KEY_STREAM_CP = 0, 1, 2, 3, 4
 HE_KEY_STREAM_LDG1 = 5
 HE_KEY_STREAM_PK = 6
+HE_OPT_PDL = 2
 HE_KEY_STREAM_PK3 = 7
 HE_KEY_STREAM_PKP = 8
 
