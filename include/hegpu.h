@@ -205,6 +205,14 @@ size_t he_key_bytes(const he_ctx *ctx);
 
 /* ------------------------------------------------------------------ ciphertexts */
 int he_ct_alloc(he_ctx *ctx, int level, he_ct **out);
+/* Device-side range sanitizer: the number of words of ct (both polynomials, limbs 0..level)
+ * that are not below their prime (0 for a well-formed ciphertext); counts instead of
+ * trapping.  Synchronises the stream; refused inside a graph capture (HE_ESTATE). */
+long long he_ct_check_range(he_ctx *ctx, const he_ct *ct, void *stream);
+/* Test hook, host side only: after `after` more successful device allocations the next one
+ * fails with HE_ENOMEM (the hook then disarms); a negative value disarms it.  Lets tests drive
+ * allocation failures without exhausting a shared GPU. */
+int he_debug_fail_alloc(long after);
 /* Wrap caller-owned device memory of at least 2*(level+1)*n*8 bytes (not freed by us). */
 int he_ct_wrap(he_ctx *ctx, void *dev_ptr, size_t bytes, int level, he_ct **out);
 void he_ct_free(he_ct *ct);

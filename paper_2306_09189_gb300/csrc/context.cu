@@ -29,6 +29,21 @@ void he_count_launch(int k) {
 
 bool he_capturing() { return g_capturing; }
 static thread_local bool g_capture_failed = false;
+// Fault injection for tests (host side only): after g_fail_after more successful device
+// allocations, the next one fails with HE_ENOMEM and the injection disarms (-1: disarmed).
+static std::atomic<long> g_fail_after{-1};
+bool he_alloc_should_fail() {
+    long v = g_fail_after.load();
+    while (v >= 0) {
+        if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+extern "C" int he_debug_fail_alloc(long after) {
+    g_fail_after.store(after < 0 ? -1 : after);
+    return HE_OK;
+}
+
 int he_capture_guard(const char *what) {
     if (!g_capturing) return HE_OK;
     g_capture_failed = true;                     // the graph would be incomplete: discard it
@@ -236,7 +251,7 @@ int Scratch::ensure(size_t w) {
     if (p) cudaFree(p);
     p = nullptr;
     words = 0;
-    if (cudaMalloc(&p, w * 8) != cudaSuccess) {
+    if (he_alloc_should_fail() || cudaMalloc(&p, w * 8) != cudaSuccess) {
         cudaGetLastError();
         he_set_error("scratch allocation of %zu bytes failed", w * 8);
         return HE_ENOMEM;
@@ -807,7 +822,7 @@ extern "C" int he_ct_alloc(he_ctx *c, int level, he_ct **out) {
     ct->cap = ct->level = level;
     ct->pstride = (size_t)(level + 1) * c->n;
     if (he_capturing()) { delete ct; return he_capture_guard("ciphertext allocation"); }
-    if (cudaMalloc(&ct->d, 2 * ct->pstride * 8) != cudaSuccess) {
+    if (he_alloc_should_fail() || cudaMalloc(&ct->d, 2 * ct->pstride * 8) != cudaSuccess) {
         cudaGetLastError();
         delete ct;
         he_set_error("ciphertext allocation failed");
@@ -816,6 +831,19 @@ extern "C" int he_ct_alloc(he_ctx *c, int level, he_ct **out) {
     ct->scale = c->pr.scale;
     *out = ct;
     return HE_OK;
+}
+
+extern "C" long long he_ct_check_range(he_ctx *c, const he_ct *ct, void *stream) {
+    if (!c || !ct || ct->ctx != c || !ct->d) { he_set_error("he_ct_check_range: bad argument"); return HE_EINVAL; }
+    HE_TRY(he_capture_guard("a range check"));
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *bad = (unsigned long long *)c->sc_tmp.p;   // one word of scratch
+    HE_CHECK_CUDA(cudaMemsetAsync(bad, 0, 8, s));
+    HE_TRY(k_range_check(c, ct->d, ct->pstride, ct->level, bad, s));
+    unsigned long long h = 0;
+    HE_CHECK_CUDA(cudaMemcpyAsync(&h, bad, 8, cudaMemcpyDeviceToHost, s));
+    HE_CHECK_CUDA(cudaStreamSynchronize(s));
+    return (long long)h;
 }
 
 extern "C" int he_ct_wrap(he_ctx *c, void *dev_ptr, size_t bytes, int level, he_ct **out) {

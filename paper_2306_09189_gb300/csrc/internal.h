@@ -34,6 +34,7 @@ void he_set_error(const char *fmt, ...);
     } while (0)
 
 void he_count_launch(int k = 1);
+bool he_alloc_should_fail();             // test fault injection (he_debug_fail_alloc)
 void he_set_pdl(int on);                 // programmatic dependent launch of every kernel (process-wide)
 int he_get_pdl();
 // True while this thread is capturing a CUDA graph (he_graph_begin .. he_graph_end): no device
@@ -221,6 +222,7 @@ int k_moddown_combine(const he_ctx *ctx, const md_item *items_dev, int n_items, 
 // ModDown fused with the rescale that follows it (m relinearised products, see kernels.cu)
 int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, size_t b_ps, u64 *w,
                       u64 *const *out, const size_t *out_ps, int m, int level, cudaStream_t s);
+int k_range_check(const he_ctx *ctx, const u64 *d, size_t ps, int level, unsigned long long *bad, cudaStream_t s);
 int k_rescale_prep(const he_ctx *ctx, const u64 *top_coef, size_t top_pstride, u64 *t, int level,
                    cudaStream_t s);
 int k_rescale_combine(const he_ctx *ctx, he_ct *ct, const u64 *t, cudaStream_t s);

@@ -325,6 +325,18 @@ __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job) {
     }
 }
 
+// ------------------------------------------------------------------------------ range check
+// counts the words of a ciphertext (both polynomials, limbs 0..level) that are not below their
+// prime: a device-side sanitizer that records instead of trapping
+__global__ void range_check_kernel(KP kp, const u64 *d, size_t ps, unsigned long long *bad) {
+    pdl_wait();
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int i = blockIdx.y, c = blockIdx.z;
+    const u64 v = d[c * ps + (size_t)i * kp.n + k];
+    const unsigned m = __ballot_sync(0xffffffffu, v >= kp.q[i]);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(bad, (unsigned long long)__popc(m));
+}
+
 // ------------------------------------------------------------------------------ sampling
 __global__ void sample_uniform_kernel(KP kp, u64 seed, u64 stream, u64 *out, int nq) {
     pdl_wait();
@@ -1937,6 +1949,12 @@ int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, s
                                                                                    linv, linvs);
         LAUNCH_CHECK();
     }
+    return HE_OK;
+}
+
+int k_range_check(const he_ctx *ctx, const u64 *d, size_t ps, int level, unsigned long long *bad, cudaStream_t s) {
+    pdl_launch(range_check_kernel, dim3(ctx->n / TB, level + 1, 2), TB, 0, s, ctx->kp, d, ps, bad);
+    LAUNCH_CHECK();
     return HE_OK;
 }
 

@@ -270,7 +270,7 @@ int dev_alloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) return HE_OK;
     HE_TRY(he_capture_guard("device allocation"));
-    if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+    if (he_alloc_should_fail() || cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         he_set_error("device allocation of %zu bytes failed", count * sizeof(T));

@@ -133,6 +133,8 @@ _SIGS = {
     "he_pool_linear_create": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_double,
                                       ctypes.POINTER(c_vp)]),
     "he_linear_destroy": (None, [c_vp]),
+    "he_ct_check_range": (ctypes.c_longlong, [c_vp, c_vp, c_vp]),
+    "he_debug_fail_alloc": (c_int, [ctypes.c_long]),
     "he_cheb_minimax": (c_int, [c_int, c_int, c_double, c_double, F64P, F64P]),
     "he_linear_rotations": (c_int, [c_vp, I32P, c_size_t]),
     "he_linear_out_level": (c_int, [c_vp]),
@@ -610,6 +612,15 @@ def he_linear_import_plaintexts(lin, weights=None, masks=None, bias=None):
 
 def he_linear_run(ctx, lin, ins, out, stream=None):
     _check(load().he_linear_run(ctx, lin, _vp_array(ins), out, stream_ptr(stream)))
+
+
+def he_ct_check_range(ctx, ct, stream=None):
+    """Words of ct not below their prime (0: well formed)."""
+    return int(_check(load().he_ct_check_range(ctx, ct, stream_ptr(stream))))
+
+
+def he_debug_fail_alloc(after):
+    _check(load().he_debug_fail_alloc(after))
 
 
 HE_FN_GELU, HE_FN_RELU, HE_FN_SILU, HE_FN_SOFTPLUS = 0, 1, 2, 3
