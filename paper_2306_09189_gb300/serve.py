@@ -43,7 +43,7 @@ class Stage:
 class Stack:
     """The layer programs for one input resolution, planned on the root context."""
 
-    def __init__(self, ctx, m, layers, cheb, level, scale, channels=4):
+    def __init__(self, ctx, m, layers, cheb, level, scale, channels=4, conv_form="diag"):
         self.ctx, self.m, self.cheb, self.scale = ctx, m, np.asarray(cheb, dtype=np.float64), scale
         info = H.he_ctx_info(ctx)
         self.n, self.N = info["n"], info["slots"]
@@ -53,7 +53,10 @@ class Stack:
         lv = level
         depth = poly_depth(len(cheb) - 1)
         for (W, b) in layers:
-            conv = H.he_conv_create(ctx, lay, W, b, 1, 1, lv, scale)
+            if conv_form == "bsgs":                 # giant stride from the library's cost model
+                conv = H.he_conv_create_bsgs(ctx, lay, W, b, 1, 1, lv, scale, 0)
+            else:
+                conv = H.he_conv_create(ctx, lay, W, b, 1, 1, lv, scale)
             H.he_keygen_rotations(ctx, H.he_conv_rotations(conv))
             lay_c = H.he_conv_out_layout(conv)
             lv_c = lv - 1
@@ -252,6 +255,8 @@ def main():
     ap.add_argument("--sizes", default="32,64")
     ap.add_argument("--rates", default="0.5,0.8,1.0", help="fractions of the measured capacity")
     ap.add_argument("--widths", default="4,8,8,8,8")
+    ap.add_argument("--conv", default="diag", choices=["diag", "bsgs"],
+                    help="convolution form: diagonal, or baby-step giant-step")
     args = ap.parse_args()
     sizes = [int(x) for x in args.sizes.split(",")]
     widths = tuple(int(x) for x in args.widths.split(","))
@@ -262,7 +267,7 @@ def main():
     layers = workloads.serving_stack(0, widths=widths, m=32)
     cheb = host.chebyshev_coeffs(host.gelu, workloads.GELU_DEGREE, -8.0, 8.0)
     level = pr.n_q - 1
-    stacks = {m: Stack(root, m, layers, cheb, level, pr.scale) for m in sizes}
+    stacks = {m: Stack(root, m, layers, cheb, level, pr.scale, conv_form=args.conv) for m in sizes}
     setup_s = time.perf_counter() - t
     server = Server(root, stacks, args.workers)
     rng = np.random.default_rng(0)
@@ -309,6 +314,7 @@ def main():
         results.append(st)
     line = {"workload": "serving: Poisson stream of %s images through 4 x [conv3x3+BN, deg-16 GELU, "
                         "avgpool], widths %s, 2N=2^16, 33+11 primes" % ("/".join(map(str, sizes)), widths),
+            "conv": args.conv,
             "workers": len(server.workers), "setup_s": setup_s, "key_bytes": H.he_key_bytes(root),
             "service_ms_alone": {str(m): v * 1e3 for m, v in alone.items()},
             "capacity_images_per_s": capacity,
