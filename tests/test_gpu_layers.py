@@ -253,20 +253,38 @@ def test_cifar_layer_full_ring():
             img = Ly.unpack(lin, H.he_decrypt(g.h, oc, N)[None])
             assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
         assert np.array_equal(outs[0], outs[1])
-        # the TMA key-tile pipeline and the split form reproduce the fused output at full size
-        for ks in (H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_LDG1, H.HE_KEY_STREAM_SPLIT):
+        # every other fused form (TMA key tiles, cp.async ring, one coefficient per thread, split,
+        # the pre-keyed kernels the bench's autotuner picks) reproduces the output at full size
+        for ks in (H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_LDG1, H.HE_KEY_STREAM_SPLIT,
+                   H.HE_KEY_STREAM_PK, H.HE_KEY_STREAM_PK3, H.HE_KEY_STREAM_PKP, H.HE_KEY_STREAM_AUTO):
             H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
             ot = g.ct(level - 1)
             H.he_conv_run(g.h, conv, [ct], [ot], H.HE_FUSED)
             H.he_ctx_check(g.h)
             assert np.array_equal(g.download(ot), outs[H.HE_FUSED])
-        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_LDG)
+        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_AUTO)
         cheb = Ly.cheb_nodes_coeffs(Ly.gelu, workloads.GELU_DEGREE, -8, 8)
-        H.he_poly_eval(g.h, oc, cheb, C20.scale)
-        assert H.he_ct_level(oc) == level - 1 - 5
-        act = Ly.unpack(lin, H.he_decrypt(g.h, oc, N)[None])
         want = Ly.cheb_eval(cheb, 8 * ref, -8, 8)
-        assert np.abs(act - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+        op = g.ct(level - 1)
+        H.he_ct_copy(op, oc)
+        H.he_poly_eval(g.h, oc, cheb, C20.scale)                 # binary tree
+        H.he_poly_eval_ps(g.h, op, cheb, C20.scale)              # Paterson-Stockmeyer (the bench's)
+        for y in (oc, op):
+            assert H.he_ct_level(y) == level - 1 - 5 and H.he_ct_check_range(g.h, y) == 0
+            act = Ly.unpack(lin, H.he_decrypt(g.h, y, N)[None])
+            assert np.abs(act - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+        # the same layer in BSGS form (the bench's bsgs object) decrypts to the same convolution,
+        # fused and per-rotation
+        cb = H.he_conv_create_bsgs(g.h, lay, wl.W, wl.bias, 1, 1, level, C20.scale, 0)
+        assert H.he_conv_bsgs_giant(cb) == 4 and H.he_conv_keyswitches(cb) == 35 + 3
+        H.he_keygen_rotations(g.h, H.he_conv_rotations(cb))
+        for mode in (H.HE_BATCHED, H.HE_FUSED):
+            ob = g.ct(level - 1)
+            H.he_conv_run(g.h, cb, [ct], [ob], mode)
+            H.he_ctx_check(g.h)
+            img = Ly.unpack(lin, H.he_decrypt(g.h, ob, N)[None])
+            assert np.abs(img - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+        H.he_conv_destroy(cb)
         H.he_conv_destroy(conv)
     finally:
         g.close()
