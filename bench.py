@@ -789,6 +789,13 @@ def main():
                 "peak_source": src, "launches": tr["launches"], "ms_per_launch": per_launch_ms,
                 "share_of_step": tr["ms"] / (ms_b * args.steps)}
     mm_rate = H.he_bench_modmul(ctx, 152 * 8, 2048)
+    if roof is not None and tr.get("mulmods"):
+        # integer pipe: the library counts the kernel's 64x64->128-bit multiply-accumulates; the
+        # microbenchmark's dependent Montgomery products each take three such products
+        mm = tr["mulmods"] / tr["launches"] / (roof["ms_per_launch"] * 1e-3)
+        roof["int"] = {"unit": "64-bit products/s", "achieved": mm, "peak": 3.0 * mm_rate,
+                       "frac": mm / (3.0 * mm_rate),
+                       "peak_source": "he_bench_modmul: dependent Montgomery products at full occupancy, x3"}
 
     if rank == 0:
         line = {
