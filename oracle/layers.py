@@ -602,6 +602,88 @@ def linear_he(ctx, plan: LinearPlan, cts, w_pts=None, mask_pts=None, bias_pt=Non
     return out
 
 
+# ---------------------------------------------------------------------------- packed head
+def linear_packed_width(n_out):
+    """n' = the smallest power of two >= n_out: output j is gathered in slot j of n'-periodic sums."""
+    return 1 << max(0, (int(n_out) - 1).bit_length())
+
+
+def linear_packed_weights(plan: LinearPlan):
+    """Q_{u,d}[i] = w_{i mod n', u}[(i + d) mod N] (zero where i mod n' >= n_out), d < n'.
+
+    Sum_u Sum_d Q_{u,d} (.) rot_d(X_u) puts, in every slot i, the terms of output j = i mod n'
+    at the slots i + d; summing the slots of one residue class mod n' (rotate-and-add by N/2,
+    ..., n') then covers every slot of every shard exactly once: out_j in slot j.  The same
+    dot products as the per-output form with n' hoisted rotations per shard and log2(N/n')
+    shifts instead of n_out log2 N."""
+    N = plan.lin.N
+    npk = linear_packed_width(plan.n_out)
+    i = np.arange(N)
+    j = i % npk
+    Q = {}
+    for u in range(plan.lin.n_shards):
+        W = np.stack([plan.w[(jj, u)] for jj in range(plan.n_out)] +
+                     [np.zeros(N)] * (npk - plan.n_out))            # [n'][N]
+        for d in range(npk):
+            Q[(u, d)] = W[j, (i + d) % N]
+    return Q
+
+
+def linear_packed_shifts(plan: LinearPlan):
+    npk, out, s = linear_packed_width(plan.n_out), [], plan.lin.N // 2
+    while s >= npk:
+        out.append(s)
+        s //= 2
+    return out
+
+
+def linear_packed_slots(plan: LinearPlan, slots):
+    """Slot simulator of the packed head."""
+    N = plan.lin.N
+    C = np.zeros(N)
+    for (u, d), q in linear_packed_weights(plan).items():
+        C += q * np.roll(slots[u], -d)
+    for s in linear_packed_shifts(plan):
+        C = C + np.roll(C, -s)
+    e = np.zeros(N)
+    e[: plan.n_out] = 1.0
+    out = e * C
+    out[: plan.n_out] += plan.bias
+    return out
+
+
+def linear_packed_plaintexts(plan: LinearPlan, n, S_w, S_mask):
+    """Integer plaintexts: packed weights {(u, d)} at scale S_w, the first-n_out mask at S_mask."""
+    e = np.zeros(plan.lin.N)
+    e[: plan.n_out] = 1.0
+    return {k: encode(v, n, S_w) for k, v in linear_packed_weights(plan).items()}, encode(e, n, S_mask)
+
+
+def linear_packed_he(ctx, plan: LinearPlan, cts, w_pts=None, mask_pt=None, bias_pt=None):
+    """The packed head on oracle ciphertexts: C = Rescale(raised stage sum_{(u,d)} Q_{u,d} (.)
+    rot_d(X_u)) (one ModDown), C += hoisted rot_s(C) for s = N/2, ..., n', out =
+    Rescale(mask (.) C) + bias.  Levels and scales as in linear_he; different bits."""
+    level, scale = cts[0].level, cts[0].scale
+    assert level >= 2 and all(c.level == level and c.scale == scale for c in cts)
+    npk = linear_packed_width(plan.n_out)
+    if w_pts is None or mask_pt is None:
+        w_pts, mask_pt = linear_packed_plaintexts(plan, ctx.n, float(ctx.q[level]), float(ctx.q[level - 1]))
+    terms = {0: [(u, d, w_pts[(u, d)]) for u in range(plan.lin.n_shards) for d in range(npk)]}
+    C = raised_stage(ctx, cts, terms)[0]
+    C.scale = scale * float(ctx.q[level])
+    C = ctx.rescale(C)
+    for s in linear_packed_shifts(plan):
+        ctx.gen_rotation_key(s)
+        C = ctx.add_ct(C, ctx.rotate_hoisted(C, ctx.hoist(C), s))
+    out = ctx.rescale(mac(ctx, {(0, 0): C}, [(0, 0)], [mask_pt], level - 1, C.scale))
+    if bias_pt is None:
+        b = np.zeros(plan.lin.N)
+        b[: plan.n_out] = plan.bias
+        bias_pt = encode(b, ctx.n, out.scale)
+    out.c[0] = ctx.add(out.c[0], ctx.reduce_int(bias_pt, ctx.mods(out.level)), ctx.mods(out.level))
+    return out
+
+
 # ============================================================================ factored conv
 @dataclass
 class FactoredPlan:

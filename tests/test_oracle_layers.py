@@ -420,6 +420,44 @@ def test_linear_he_decrypts_to_fp64():
     assert np.abs(got[4:]).max() <= 2.0 ** -20 * (want.max() - want.min())
 
 
+@pytest.mark.parametrize("c,m,N,n_out", [(4, 8, 512, 5), (16, 8, 512, 10), (2, 32, 512, 3), (3, 28, 1024, 16),
+                                         (8, 16, 1024, 1)])
+def test_packed_head_equals_the_per_output_head(c, m, N, n_out):
+    # the packed regrouping computes the same dot products in slots 0..n_out-1 and zeros elsewhere
+    rng = np.random.default_rng(c + m + n_out)
+    x = rng.uniform(-1, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (n_out, c, m, m))
+    b = rng.uniform(-1, 1, n_out)
+    lin = Ly.image_layout(c, m, N)
+    plan = Ly.linear_plan(lin, W, b)
+    slots = Ly.pack(lin, x)
+    got = Ly.linear_packed_slots(plan, slots)
+    assert np.abs(got - Ly.linear_slots(plan, slots)).max() < 1e-9
+    npk = Ly.linear_packed_width(n_out)
+    assert npk >= n_out and npk & (npk - 1) == 0 and npk < 2 * max(n_out, 1)
+    # rotations: n' - 1 hoisted per shard and log2(N / n') shifts, against n_out log2 N
+    assert len(Ly.linear_packed_shifts(plan)) == (N // npk).bit_length() - 1
+
+
+def test_packed_head_he_decrypts_to_fp64():
+    ctx = _small_ctx()
+    rng = np.random.default_rng(11)
+    c, m = 8, 8
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (6, c))
+    b = rng.uniform(-1, 1, 6)
+    lin = Ly.image_layout(c, m, ctx.N)
+    plan = Ly.pool_linear_plan(lin, W, b)
+    cts = [ctx.encrypt(Ly.pack(lin, x)[u], 3, nonce=80 + u) for u in range(lin.n_shards)]
+    out = Ly.linear_packed_he(ctx, plan, cts)
+    ref = Ly.linear_he(ctx, plan, cts)
+    assert out.level == ref.level == 1 and out.scale == ref.scale and not np.array_equal(out.c, ref.c)
+    got = ctx.decrypt(out)
+    want = W @ x.mean(axis=(1, 2)) + b
+    tol = 2.0 ** -20 * (want.max() - want.min())
+    assert np.abs(got[:6] - want).max() <= tol and np.abs(got[6:]).max() <= tol
+
+
 def test_bsgs_he_without_giant_steps_is_the_diagonal_form():
     # channel shards: every giant amount is 0, so S_{v,0} is the diagonal MAC (per-rotation
     # form) or the diagonal raised stage, and the giant stage adds nothing: bit for bit
