@@ -388,10 +388,12 @@ int he_cheb_minimax(int fn, int deg, double lo, double hi, double *coeffs, doubl
 /* Linear layer over a sharded image: output j = sum over the flattened (channel, row, column)
  * features of W[j][c][m][m] x feature, + bias[j] (bias NULL: 0).  Row j is placed on the first
  * copy (shard, then block order) of every valid pixel, so duplicated channels count once.
- * Evaluation: T_j = Rescale(sum_u w_{j,u} (.) X_u) with the weights at scale q_level; the slot
- * sum by rotate-and-add, T_j += rot_s(T_j) for s = N/2, ..., 1 (log2 N hoisted rotations per
+ * Evaluation: T_j = Rescale(sum_u w_{j,u} (.) X_u) with the weights at scale q_level 2^12; the
+ * slot sum by rotate-and-add, T_j += rot_s(T_j) for s = N/2, ..., 1 (log2 N hoisted rotations per
  * output, every output's rotation by s in one fused launch); out = Rescale(sum_j e_j (.) T_j)
- * with one-hot masks e_j at scale q_{level-1}, plus the bias in slots 0..n_out-1.  The output
+ * with one-hot masks e_j at scale q_{level-1} / 2^12, plus the bias in slots 0..n_out-1 (the
+ * sum runs 2^12 above the input scale because each of its steps doubles the key-switch noise
+ * before it; the output is at in_scale exactly).  The output
  * is one ciphertext at level - 2 (he_linear_out_level) and scale in_scale, out_j in slot j.
  * n_out <= N; level >= 2 (HE_ELEVEL).  Rotation keys: he_linear_rotations (the log2 N shifts). */
 int he_linear_create(he_ctx *ctx, const he_layout *in, const double *W, const double *bias, int n_out,
@@ -400,13 +402,25 @@ int he_linear_create(he_ctx *ctx, const he_layout *in, const double *W, const do
  * fused as a linear layer whose weights are W[j][f] / m^2 on every pixel of channel f. */
 int he_pool_linear_create(he_ctx *ctx, const he_layout *in, const double *W, const double *bias, int n_out,
                           int level, double in_scale, he_linear **out);
+/* The same heads in packed form: with n' the smallest power of two >= n_out, the plaintexts
+ * Q_{u,d}[i] = w_{i mod n', u}[(i + d) mod N] (d < n') make C = sum_{(u,d)} Q_{u,d} (.) rot_d(X_u)
+ * (one raised-basis stage: n' - 1 hoisted rotations per shard, one ModDown) hold the terms of
+ * output j = i mod n' around slot i; C += rot_s(C) for s = N/2, ..., n' sums each residue class
+ * mod n', leaving out_j in slot j; then the first-n_out mask, rescale and bias as above.  Same
+ * levels, scale and outputs; n_in (n' - 1) + log2(N/n') key switches instead of n_out log2 N;
+ * different bits.  he_linear_import_plaintexts takes weights [n_in][n'][n] (the Q_{u,d}) and
+ * one mask [n]. */
+int he_linear_create_packed(he_ctx *ctx, const he_layout *in, const double *W, const double *bias, int n_out,
+                            int level, double in_scale, he_linear **out);
+int he_pool_linear_create_packed(he_ctx *ctx, const he_layout *in, const double *W, const double *bias,
+                                 int n_out, int level, double in_scale, he_linear **out);
 void he_linear_destroy(he_linear *lin);
 int he_linear_rotations(const he_linear *lin, int32_t *amounts, size_t cap);
 int he_linear_out_level(const he_linear *lin);
 /* Key switches one run performs: n_out x log2 N. */
 int64_t he_linear_keyswitches(const he_linear *lin);
 /* Replace the encoded plaintexts by integer polynomials: weights [n_out][n_in_shards][n] at
- * scale q_level, masks [n_out][n] at scale q_{level-1}, bias [n] at the output scale (each
+ * scale q_level 2^12, masks [n_out][n] at scale q_{level-1} / 2^12, bias [n] at the output scale (each
  * optional, NULL keeps the encoded one). */
 int he_linear_import_plaintexts(he_linear *lin, const int64_t *weights, const int64_t *masks,
                                 const int64_t *bias);

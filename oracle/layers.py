@@ -573,26 +573,40 @@ def linear_plaintexts(plan: LinearPlan, n, S_w, S_mask):
     return w, masks
 
 
+HEAD_BOOST_BITS = 12
+
+
+def linear_scales(ctx, level):
+    """(weight scale, mask scale) of the head at input level l: q_l 2^b and q_{l-1} / 2^b.
+
+    The slot sum adds every slot of a partial sum, and each of its log2 steps doubles the noise
+    of the key switches before it (up to N/2 times at the first one), so the sum runs at scale
+    Delta 2^b; the masks take the 2^b back out, leaving the output at Delta exactly."""
+    return float(ctx.q[level]) * 2.0 ** HEAD_BOOST_BITS, float(ctx.q[level - 1]) / 2.0 ** HEAD_BOOST_BITS
+
+
 def linear_he(ctx, plan: LinearPlan, cts, w_pts=None, mask_pts=None, bias_pt=None):
     """The linear layer on oracle ciphertexts (all shards at one level l >= 2, one scale):
-    T_j = Rescale(sum_u w_{j,u} * x_u) with weights at scale q_l; for s = N/2, ..., 1 the
+    T_j = Rescale(sum_u w_{j,u} * x_u) with weights at scale S_w; for s = N/2, ..., 1 the
     hoisted rotation T_j += rot_s(T_j); out = Rescale(sum_j e_j * T_j) with masks at scale
-    q_{l-1}; plus the bias (slots 0..n_out-1) at the output scale.  Output level l - 2."""
+    S_mask; plus the bias (slots 0..n_out-1) at the output scale.  (S_w, S_mask) =
+    linear_scales.  Output level l - 2, output scale the input scale."""
     level, scale = cts[0].level, cts[0].scale
     assert level >= 2 and all(c.level == level and c.scale == scale for c in cts)
+    S_w, S_mask = linear_scales(ctx, level)
     if w_pts is None or mask_pts is None:
-        w_pts, mask_pts = linear_plaintexts(plan, ctx.n, float(ctx.q[level]), float(ctx.q[level - 1]))
+        w_pts, mask_pts = linear_plaintexts(plan, ctx.n, S_w, S_mask)
     R = {(u, 0): ct for u, ct in enumerate(cts)}
     terms = [(u, 0) for u in range(plan.lin.n_shards)]
     T = []
     for j in range(plan.n_out):
-        t = ctx.rescale(mac(ctx, R, terms, [w_pts[(j, u)] for u in range(plan.lin.n_shards)], level, scale))
+        t = ctx.rescale(mac(ctx, R, terms, [w_pts[(j, u)] for u in range(plan.lin.n_shards)], level, scale, S_w))
         for s in plan.amounts():
             ctx.gen_rotation_key(s)
             t = ctx.add_ct(t, ctx.rotate_hoisted(t, ctx.hoist(t), s))
         T.append(t)
     acc = mac(ctx, {(j, 0): t for j, t in enumerate(T)}, [(j, 0) for j in range(plan.n_out)],
-              [mask_pts[j] for j in range(plan.n_out)], level - 1, T[0].scale)
+              [mask_pts[j] for j in range(plan.n_out)], level - 1, T[0].scale, S_mask)
     out = ctx.rescale(acc)
     if bias_pt is None:
         b = np.zeros(plan.lin.N)
@@ -666,16 +680,17 @@ def linear_packed_he(ctx, plan: LinearPlan, cts, w_pts=None, mask_pt=None, bias_
     level, scale = cts[0].level, cts[0].scale
     assert level >= 2 and all(c.level == level and c.scale == scale for c in cts)
     npk = linear_packed_width(plan.n_out)
+    S_w, S_mask = linear_scales(ctx, level)
     if w_pts is None or mask_pt is None:
-        w_pts, mask_pt = linear_packed_plaintexts(plan, ctx.n, float(ctx.q[level]), float(ctx.q[level - 1]))
+        w_pts, mask_pt = linear_packed_plaintexts(plan, ctx.n, S_w, S_mask)
     terms = {0: [(u, d, w_pts[(u, d)]) for u in range(plan.lin.n_shards) for d in range(npk)]}
     C = raised_stage(ctx, cts, terms)[0]
-    C.scale = scale * float(ctx.q[level])
+    C.scale = scale * S_w
     C = ctx.rescale(C)
     for s in linear_packed_shifts(plan):
         ctx.gen_rotation_key(s)
         C = ctx.add_ct(C, ctx.rotate_hoisted(C, ctx.hoist(C), s))
-    out = ctx.rescale(mac(ctx, {(0, 0): C}, [(0, 0)], [mask_pt], level - 1, C.scale))
+    out = ctx.rescale(mac(ctx, {(0, 0): C}, [(0, 0)], [mask_pt], level - 1, C.scale, S_mask))
     if bias_pt is None:
         b = np.zeros(plan.lin.N)
         b[: plan.n_out] = plan.bias

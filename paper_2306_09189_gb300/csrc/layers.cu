@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <cmath>
 #include <thread>
@@ -510,6 +511,7 @@ struct FusedStage {
     std::vector<std::array<uintptr_t, 4>> pk_refs;   // entries of the root's pre-keyed cache held
     bool pk_built = false;
     int pk_state = 0;                                 // 0: not checked, 1: eligible, -1: not
+    uint64_t pk_epoch = 0;                            // bumped when the plaintexts are re-imported
 
     ~FusedStage();
     void free_pk() {
@@ -531,8 +533,9 @@ struct FusedStage {
         pk_built = false;
     }
     std::array<uintptr_t, 4> pk_key(const u64 *key, const u64 *pt) const {
-        return {(uintptr_t)key, (uintptr_t)pt, (uintptr_t)level, (uintptr_t)pt_level};
+        return {(uintptr_t)key, (uintptr_t)pt, (uintptr_t)level * 4096 + (uintptr_t)pt_level, (uintptr_t)pk_epoch};
     }
+    void invalidate_pk();                             // plaintext contents changed
     // every output takes at most one source per amount
     bool pk_eligible() {
         if (pk_state == 0) {
@@ -782,6 +785,16 @@ struct FusedLaunch {
         d_pk = nullptr;
         G_pk = 0;
         for (auto *f : st) f->free_pk();
+    }
+    // after a stage's plaintexts changed: drop the pre-keyed tables and tune again on next run
+    void reset_pk() {
+        cudaFree(d_pk);
+        d_pk = nullptr;
+        G_pk = 0;
+        if (use_pk) {
+            use_pk = false;
+            tuned = false;
+        }
     }
     int pk_form = HE_KEY_STREAM_PK;                   // or HE_FORM_PK3 (three blocks per SM)
     int launch_pk(cudaStream_t s, int fm = 0) {
@@ -1227,6 +1240,16 @@ int FusedStage::build_pk() {
     return HE_OK;
 }
 
+// Pre-keyed tables hold key (.) plaintext products, so new plaintext contents make them stale:
+// release this stage's tables, key any new ones by a fresh epoch, and let the stage's own
+// launch tune again (a launch over several stages is reset by its owner).
+static std::atomic<uint64_t> g_pk_epoch{0};
+void FusedStage::invalidate_pk() {
+    free_pk();
+    pk_epoch = ++g_pk_epoch;
+    if (own) own->reset_pk();
+}
+
 FusedStage::~FusedStage() {
     own.reset();
     free_split();
@@ -1648,6 +1671,7 @@ extern "C" int he_pool_import_plaintexts(he_pool *p, const int64_t *h, const int
     if (!p) return HE_EINVAL;
     if (h) HE_TRY(import_masks(p, h, p->P.h_amt.size(), p->h_idx, p->n_hpt, p->level, p->hpts));
     if (v) HE_TRY(import_masks(p, v, p->P.v_amt.size(), p->v_idx, p->n_vpt, p->level - 1, p->vpts));
+    for (FusedStage *f : {&p->f_S, &p->f_H, &p->f_V, &p->f_C, &p->f_D}) f->invalidate_pk();
     return HE_OK;
 }
 
@@ -2386,6 +2410,8 @@ extern "C" int he_conv_export_plan(const he_conv *cv, int32_t *u, int32_t *v, in
     return HE_OK;
 }
 
+static void conv_invalidate_pk(he_conv *cv);
+
 extern "C" int he_conv_import_plaintexts(he_conv *cv, const int64_t *terms, const int64_t *bias) {
     if (!cv) return HE_EINVAL;
     he_ctx *c = cv->c;
@@ -2396,11 +2422,13 @@ extern "C" int he_conv_import_plaintexts(he_conv *cv, const int64_t *terms, cons
             for (int v = 0; v < cv->lout.ns; v++)
                 HE_TRY(upload_addend(c, bias + (size_t)v * c->n, cv->level - 2,
                                      cv->bias_pts + (size_t)v * (cv->level - 1) * c->n));
+        if (terms) conv_invalidate_pk(cv);
         return HE_OK;
     }
     if (terms) {
         std::vector<const double *> none;
         HE_TRY(upload_plaintexts(c, none, cv->tu.size(), 0.0, cv->level, cv->pts, terms, true));
+        conv_invalidate_pk(cv);
     }
     if (bias)
         for (int v = 0; v < cv->lout.ns; v++)
@@ -2623,6 +2651,22 @@ extern "C" int he_conv_import_bias(he_conv *cv, int level, double out_scale, con
     for (int v = 0; v < cv->lout.ns; v++)
         HE_TRY(upload_addend(cv->c, bias + (size_t)v * cv->c->n, level - 1, d + (size_t)v * level * cv->c->n));
     return HE_OK;
+}
+
+// new plaintext contents: every stage of this convolution (single run, image batch, factored
+// stage 1) drops its pre-keyed tables
+static void conv_invalidate_pk(he_conv *cv) {
+    cv->fused.invalidate_pk();
+    cv->fusedG.invalidate_pk();
+    if (cv->fc) cv->fc->fy.invalidate_pk();
+    if (cv->batch) {
+        for (auto &S : cv->batch->slots) {
+            S->fused.invalidate_pk();
+            S->fusedG.invalidate_pk();
+        }
+        if (cv->batch->launch) cv->batch->launch->reset_pk();
+        if (cv->batch->launchG) cv->batch->launchG->reset_pk();
+    }
 }
 
 extern "C" int he_conv_run_batch(he_ctx *c, he_conv *cv, he_ct *const *in, he_ct **out, int n_img, int mode,
@@ -3210,6 +3254,13 @@ extern "C" int he_poly_eval_many(he_ctx *c, he_ct *const *io, int m, const doubl
 // bits of T_j + hoisted rotation); out = Rescale(sum_j e_j (.) T_j) with the one-hot masks at
 // scale q_{l-1}, plus the bias in slots 0..n_out-1.  Pool-linear spreads per-channel weights over
 // the m x m pixels, divided by m^2.
+// The slot sum adds every slot of a partial sum, each of its steps doubling the noise of the key
+// switches before it, so it runs at scale Delta 2^12: weights at q_l 2^12, masks at
+// q_{l-1} / 2^12 (the output is back at Delta exactly).
+constexpr int HEAD_BOOST_BITS = 12;
+static double head_w_scale(const he_ctx *c, int l) { return (double)c->primes[l] * std::ldexp(1.0, HEAD_BOOST_BITS); }
+static double head_mask_scale(const he_ctx *c, int l) { return (double)c->primes[l - 1] / std::ldexp(1.0, HEAD_BOOST_BITS); }
+
 struct he_linear {
     he_ctx *c = nullptr;
     Lay lin;
@@ -3226,9 +3277,17 @@ struct he_linear {
     mac_term *d_w = nullptr, *d_m = nullptr;     // weight MACs; mask MACs (over the final T)
     std::vector<std::unique_ptr<FusedStage>> steps;
     std::vector<int> shifts;
+    // packed form: one sum C = sum_{(u,d)} Q_{u,d} (.) rot_d(X_u) (a raised-basis stage, d < npk)
+    // whose slot classes mod npk are summed by the shifts N/2, ..., npk; w holds the Q_{u,d}
+    // ([n_in][npk][l+1+K][n]), mask the single first-n_out mask, T one partial sum
+    bool packed = false;
+    int npk = 0;
+    std::unique_ptr<FusedStage> stage1;
+    int n_T() const { return packed ? 1 : n_out; }    // partial sums held
     ~he_linear() {
         cudaDeviceSynchronize();
         steps.clear();
+        stage1.reset();
         cudaFree(R); cudaFree(w); cudaFree(mask); cudaFree(bias_pt); cudaFree(T[0]); cudaFree(T[1]);
         cudaFree(acc); cudaFree(d_w); cudaFree(d_m);
     }
@@ -3246,7 +3305,7 @@ static void linear_weights(const Lay &L, const double *W, int j, int u, const st
 }
 
 static int linear_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int n_out, int level,
-                         double in_scale, he_linear **out) {
+                         double in_scale, bool packed, he_linear **out) {
     if (!c || !in || !W || !out || n_out < 1) { he_set_error("he_linear_create: bad argument"); return HE_EINVAL; }
     if (level < 2 || level > c->L) { he_set_error("he_linear_create: level %d, the head takes two levels", level); return HE_ELEVEL; }
     Lay lin = from_c(*in);
@@ -3261,7 +3320,10 @@ static int linear_create(he_ctx *c, const he_layout *in, const double *W, const 
     L->pw = (size_t)(level + 1) * c->n;
     L->bias.assign(n_out, 0.0);
     if (bias) L->bias.assign(bias, bias + n_out);
-    for (int s = lin.N / 2; s >= 1; s /= 2) L->shifts.push_back(s);
+    L->packed = packed;
+    L->npk = 1;
+    while (L->npk < n_out) L->npk *= 2;
+    for (int s = lin.N / 2; s >= (packed ? L->npk : 1); s /= 2) L->shifts.push_back(s);
     const int ni = lin.ns, n = c->n;
     // first copy (shard, then block order) of every (channel, row, column)
     std::vector<char> first((size_t)ni * lin.N, 0), seen((size_t)lin.c * lin.m * lin.m, 0);
@@ -3273,11 +3335,49 @@ static int linear_create(he_ctx *c, const he_layout *in, const double *W, const 
             if (!sn) { sn = 1; first[(size_t)u * lin.N + i] = 1; }
         }
     HE_TRY(dev_alloc(&L->R, (size_t)ni * 2 * L->pw));
+    HE_TRY(dev_alloc(&L->bias_pt, (size_t)(level - 1) * n));
+    for (int b = 0; b < 2; b++) HE_TRY(dev_alloc(&L->T[b], (size_t)L->n_T() * 2 * L->pw));
+    HE_TRY(dev_alloc(&L->acc, 2 * L->pw));
+    {
+        std::vector<double> z(lin.N, 0.0);
+        for (int j = 0; j < n_out; j++) z[j] = L->bias[j];
+        std::vector<int64_t> m(n);
+        encode_slots(z.data(), n, in_scale, m.data());
+        HE_TRY(upload_addend(c, m.data(), level - 2, L->bias_pt));
+    }
+    if (packed) {
+        // Q_{u,d}[i] = w_{i mod npk, u}[(i + d) mod N] (zero rows past n_out), raised layout
+        const int np = L->npk, N = lin.N;
+        const size_t pe = (size_t)(level + 1 + c->K) * n;
+        HE_TRY(dev_alloc(&L->w, (size_t)ni * np * pe));
+        HE_TRY(dev_alloc(&L->mask, (size_t)level * n));
+        std::vector<std::vector<double>> rows(n_out);
+        std::vector<std::vector<double>> Q(np, std::vector<double>(N));
+        for (int u = 0; u < ni; u++) {
+            for (int j = 0; j < n_out; j++) linear_weights(lin, W, j, u, first, rows[j]);
+            std::vector<const double *> vecs;
+            for (int d = 0; d < np; d++) {
+                for (int i = 0; i < N; i++) {
+                    const int j = i % np;
+                    Q[d][i] = j < n_out ? rows[j][(i + d) % N] : 0.0;
+                }
+                vecs.push_back(Q[d].data());
+            }
+            HE_TRY(upload_plaintexts(c, vecs, np, head_w_scale(c, level), level, L->w + (size_t)u * np * pe, nullptr,
+                                     true));
+        }
+        std::vector<double> e(N, 0.0);
+        for (int j = 0; j < n_out; j++) e[j] = 1.0;
+        std::vector<const double *> vecs{e.data()};
+        HE_TRY(upload_plaintexts(c, vecs, 1, head_mask_scale(c, level), level - 1, L->mask, nullptr));
+        mac_term tm{L->mask, L->T[L->shifts.size() % 2], L->pw};
+        HE_TRY(dev_alloc(&L->d_m, 1));
+        HE_CHECK_CUDA(cudaMemcpy(L->d_m, &tm, sizeof(mac_term), cudaMemcpyHostToDevice));
+        *out = L.release();
+        return HE_OK;
+    }
     HE_TRY(dev_alloc(&L->w, (size_t)n_out * ni * L->pw));
     HE_TRY(dev_alloc(&L->mask, (size_t)n_out * level * n));
-    HE_TRY(dev_alloc(&L->bias_pt, (size_t)(level - 1) * n));
-    for (int b = 0; b < 2; b++) HE_TRY(dev_alloc(&L->T[b], (size_t)n_out * 2 * L->pw));
-    HE_TRY(dev_alloc(&L->acc, 2 * L->pw));
     std::vector<std::vector<double>> rows(ni);
     for (int j = 0; j < n_out; j++) {
         std::vector<const double *> vecs;
@@ -3285,22 +3385,15 @@ static int linear_create(he_ctx *c, const he_layout *in, const double *W, const 
             linear_weights(lin, W, j, u, first, rows[u]);
             vecs.push_back(rows[u].data());
         }
-        HE_TRY(upload_plaintexts(c, vecs, ni, (double)c->primes[level], level, L->w + (size_t)j * ni * L->pw, nullptr));
+        HE_TRY(upload_plaintexts(c, vecs, ni, head_w_scale(c, level), level, L->w + (size_t)j * ni * L->pw, nullptr));
     }
     std::vector<double> e(lin.N, 0.0);
     for (int j = 0; j < n_out; j++) {
         e.assign(lin.N, 0.0);
         e[j] = 1.0;
         std::vector<const double *> vecs{e.data()};
-        HE_TRY(upload_plaintexts(c, vecs, 1, (double)c->primes[level - 1], level - 1, L->mask + (size_t)j * level * n,
+        HE_TRY(upload_plaintexts(c, vecs, 1, head_mask_scale(c, level), level - 1, L->mask + (size_t)j * level * n,
                                  nullptr));
-    }
-    {
-        std::vector<double> z(lin.N, 0.0);
-        for (int j = 0; j < n_out; j++) z[j] = L->bias[j];
-        std::vector<int64_t> m(n);
-        encode_slots(z.data(), n, in_scale, m.data());
-        HE_TRY(upload_addend(c, m.data(), level - 2, L->bias_pt));
     }
     // MAC tables: weights over the input copies; masks over the partial sums after the last shift
     std::vector<mac_term> tw((size_t)n_out * ni), tm(n_out);
@@ -3320,11 +3413,29 @@ static int linear_create(he_ctx *c, const he_layout *in, const double *W, const 
 
 extern "C" int he_linear_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int n_out,
                                 int level, double in_scale, he_linear **out) {
-    return linear_create(c, in, W, bias, n_out, level, in_scale, out);
+    return linear_create(c, in, W, bias, n_out, level, in_scale, false, out);
 }
+
+extern "C" int he_linear_create_packed(he_ctx *c, const he_layout *in, const double *W, const double *bias, int n_out,
+                                       int level, double in_scale, he_linear **out) {
+    return linear_create(c, in, W, bias, n_out, level, in_scale, true, out);
+}
+
+static int pool_linear_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int n_out,
+                              int level, double in_scale, bool packed, he_linear **out);
 
 extern "C" int he_pool_linear_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int n_out,
                                      int level, double in_scale, he_linear **out) {
+    return pool_linear_create(c, in, W, bias, n_out, level, in_scale, false, out);
+}
+
+extern "C" int he_pool_linear_create_packed(he_ctx *c, const he_layout *in, const double *W, const double *bias,
+                                            int n_out, int level, double in_scale, he_linear **out) {
+    return pool_linear_create(c, in, W, bias, n_out, level, in_scale, true, out);
+}
+
+static int pool_linear_create(he_ctx *c, const he_layout *in, const double *W, const double *bias, int n_out,
+                              int level, double in_scale, bool packed, he_linear **out) {
     if (!in || !W || n_out < 1 || in->c < 1 || in->m < 1) { he_set_error("he_pool_linear_create: bad argument"); return HE_EINVAL; }
     const int C = in->c, m = in->m;
     std::vector<double> full((size_t)n_out * C * m * m);
@@ -3332,21 +3443,27 @@ extern "C" int he_pool_linear_create(he_ctx *c, const he_layout *in, const doubl
     for (int j = 0; j < n_out; j++)
         for (int f = 0; f < C; f++)
             for (int k = 0; k < m * m; k++) full[((size_t)j * C + f) * m * m + k] = W[(size_t)j * C + f] * norm;
-    return linear_create(c, in, full.data(), bias, n_out, level, in_scale, out);
+    return linear_create(c, in, full.data(), bias, n_out, level, in_scale, packed, out);
 }
 
 extern "C" void he_linear_destroy(he_linear *L) { delete L; }
 
 extern "C" int he_linear_rotations(const he_linear *L, int32_t *amounts, size_t cap) {
     if (!L) return HE_EINVAL;
-    for (size_t i = 0; i < L->shifts.size() && i < cap; i++) amounts[i] = L->shifts[i];
-    return (int)L->shifts.size();
+    std::vector<int> v;
+    if (L->packed)
+        for (int d = 1; d < L->npk; d++) v.push_back(d);
+    v.insert(v.end(), L->shifts.begin(), L->shifts.end());
+    for (size_t i = 0; i < v.size() && i < cap; i++) amounts[i] = v[i];
+    return (int)v.size();
 }
 
 extern "C" int he_linear_out_level(const he_linear *L) { return L ? L->level - 2 : HE_EINVAL; }
 
 extern "C" int64_t he_linear_keyswitches(const he_linear *L) {
-    return L ? (int64_t)L->n_out * (int64_t)L->shifts.size() : HE_EINVAL;
+    if (!L) return HE_EINVAL;
+    if (L->packed) return (int64_t)L->lin.ns * (L->npk - 1) + (int64_t)L->shifts.size();
+    return (int64_t)L->n_out * (int64_t)L->shifts.size();
 }
 
 extern "C" int he_linear_import_plaintexts(he_linear *L, const int64_t *weights, const int64_t *masks,
@@ -3355,6 +3472,17 @@ extern "C" int he_linear_import_plaintexts(he_linear *L, const int64_t *weights,
     he_ctx *c = L->c;
     const int ni = L->lin.ns, n = c->n;
     std::vector<const double *> none;
+    if (L->packed) {                              // weights [n_in][npk][n], mask [1][n]
+        const size_t pe = (size_t)(L->level + 1 + c->K) * n;
+        if (weights)
+            for (int u = 0; u < ni; u++)
+                HE_TRY(upload_plaintexts(c, none, L->npk, 0.0, L->level, L->w + (size_t)u * L->npk * pe,
+                                         weights + (size_t)u * L->npk * n, true));
+        if (masks) HE_TRY(upload_plaintexts(c, none, 1, 0.0, L->level - 1, L->mask, masks));
+        if (bias) HE_TRY(upload_addend(c, bias, L->level - 2, L->bias_pt));
+        if (weights && L->stage1) L->stage1->invalidate_pk();
+        return HE_OK;
+    }
     if (weights)
         for (int j = 0; j < L->n_out; j++)
             HE_TRY(upload_plaintexts(c, none, ni, 0.0, L->level, L->w + (size_t)j * ni * L->pw,
@@ -3377,16 +3505,29 @@ static int linear_steps(he_linear *L) {
         F->level = L->level - 1;
         F->name = "linear head shift " + std::to_string(L->shifts[k]);
         u64 *src = L->T[k % 2], *dst = L->T[(k + 1) % 2];
-        for (int j = 0; j < L->n_out; j++) {
+        for (int j = 0; j < L->n_T(); j++) {
             F->add_src(src + (size_t)j * 2 * L->pw, L->pw);
             F->add_out(dst + (size_t)j * 2 * L->pw, L->pw);
         }
-        for (int j = 0; j < L->n_out; j++) {
+        for (int j = 0; j < L->n_T(); j++) {
             F->add_term(j, j, 0, HE_PT_ONE);
             F->add_term(j, j, L->shifts[k], HE_PT_ONE);
         }
         HE_TRY(F->build());
         L->steps.push_back(std::move(F));
+    }
+    if (L->packed) {                              // C = sum_{(u,d)} Q_{u,d} (.) rot_d(X_u), raised
+        std::unique_ptr<FusedStage> F(new FusedStage());
+        F->c = L->c;
+        F->level = L->level;
+        F->name = "packed linear head";
+        const size_t pe = (size_t)(L->level + 1 + L->c->K) * L->c->n;
+        for (int u = 0; u < L->lin.ns; u++) F->add_src(L->R + (size_t)u * 2 * L->pw, L->pw);
+        F->add_out(L->T[0], L->pw);
+        for (int u = 0; u < L->lin.ns; u++)
+            for (int d = 0; d < L->npk; d++) F->add_term(0, u, d, L->w + ((size_t)u * L->npk + d) * pe);
+        HE_TRY(F->build());
+        L->stage1 = std::move(F);
     }
     return HE_OK;
 }
@@ -3404,18 +3545,23 @@ extern "C" int he_linear_run(he_ctx *c, he_linear *L, he_ct *const *in, he_ct *o
         HE_TRY(k_copy_limbs(L->R + (size_t)u * 2 * pw, pw, in[u]->d, in[u]->pstride, pw, 2, s));
     }
     HE_TRY(linear_steps(L));
+    if (L->packed) {                              // C, rescaled
+        HE_TRY(L->stage1->run(s));
+        he_ct v = view(c, L->T[0], pw, lv, L->in_scale * head_w_scale(c, lv));
+        HE_TRY(he_rescale(c, &v, stream));
+    }
     // T_j = Rescale(sum_u w_{j,u} (.) X_u)
-    for (int j = 0; j < L->n_out; j++) {
+    for (int j = 0; j < (L->packed ? 0 : L->n_out); j++) {
         u64 *t = L->T[0] + (size_t)j * 2 * pw;
         HE_TRY(k_mac(c, L->d_w + (size_t)j * ni, ni, t, pw, lv, false, s));
-        he_ct v = view(c, t, pw, lv, L->in_scale * (double)c->primes[lv]);
+        he_ct v = view(c, t, pw, lv, L->in_scale * head_w_scale(c, lv));
         HE_TRY(he_rescale(c, &v, stream));
     }
     for (auto &F : L->steps) HE_TRY(F->run(s));
     // out = Rescale(sum_j e_j (.) T_j) + bias
-    HE_TRY(k_mac(c, L->d_m, L->n_out, L->acc, pw, lv - 1, false, s));
-    const double t_scale = L->in_scale * (double)c->primes[lv] / (double)c->primes[lv];
-    he_ct v = view(c, L->acc, pw, lv - 1, t_scale * (double)c->primes[lv - 1]);
+    HE_TRY(k_mac(c, L->d_m, L->n_T(), L->acc, pw, lv - 1, false, s));
+    const double t_scale = L->in_scale * head_w_scale(c, lv) / (double)c->primes[lv];
+    he_ct v = view(c, L->acc, pw, lv - 1, t_scale * head_mask_scale(c, lv));
     HE_TRY(he_rescale(c, &v, stream));
     HE_TRY(k_add_raw(c, L->acc, pw, L->bias_pt, 0, lv - 1, 1, false, s));
     HE_TRY(ensure_ct(c, out, lv - 2));

@@ -132,6 +132,10 @@ _SIGS = {
                                  ctypes.POINTER(c_vp)]),
     "he_pool_linear_create": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_double,
                                       ctypes.POINTER(c_vp)]),
+    "he_linear_create_packed": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_double,
+                                        ctypes.POINTER(c_vp)]),
+    "he_pool_linear_create_packed": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_double,
+                                             ctypes.POINTER(c_vp)]),
     "he_linear_destroy": (None, [c_vp]),
     "he_ct_check_range": (ctypes.c_longlong, [c_vp, c_vp, c_vp]),
     "he_debug_fail_alloc": (c_int, [ctypes.c_long]),
@@ -583,6 +587,25 @@ def he_pool_linear_create(ctx, layout, W, bias, level, in_scale):
     h = c_vp()
     _check(load().he_pool_linear_create(ctx, ctypes.byref(layout), _p(W, F64P), None if b is None else _p(b, F64P),
                                         W.shape[0], level, in_scale, ctypes.byref(h)))
+    return h
+
+
+def he_linear_create_packed(ctx, layout, W, bias, level, in_scale):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
+    h = c_vp()
+    _check(load().he_linear_create_packed(ctx, ctypes.byref(layout), _p(W, F64P), None if b is None else _p(b, F64P),
+                                          W.shape[0], level, in_scale, ctypes.byref(h)))
+    return h
+
+
+def he_pool_linear_create_packed(ctx, layout, W, bias, level, in_scale):
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
+    h = c_vp()
+    _check(load().he_pool_linear_create_packed(ctx, ctypes.byref(layout), _p(W, F64P),
+                                               None if b is None else _p(b, F64P), W.shape[0], level, in_scale,
+                                               ctypes.byref(h)))
     return h
 
 

@@ -429,3 +429,39 @@ def test_conv_edge_cases_bit_exact(mid, c, co, m, k, pad, level):
             assert_ct_equal(g.download(oc), rc)
     H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_AUTO)
     H.he_conv_destroy(conv)
+
+
+def test_reimported_plaintexts_refresh_the_prekeyed_tables(mid):
+    # the pre-keyed form folds the plaintexts into the keys; after a run on the library's own
+    # encoding, importing other plaintexts must give the oracle's bits on the next run
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = mid
+    c, co, m, level = 4, 4, 16, 3
+    rng = np.random.default_rng(77)
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (co, c, 3, 3))
+    lin = Ly.image_layout(c, m, o.N)
+    assert lin.n_shards == 1                     # one source per amount: pre-keyed eligible
+    plan = Ly.conv_plan(lin, W, None, 1)
+    cts = [o.encrypt(Ly.pack(lin, x)[0], level, nonce=77)]
+    pts = Ly.conv_plaintexts(plan, o.n, float(o.q[level]) * 0.75)    # deliberately other integers
+    bias = {v: encode(plan.bias[v], o.n, o.pr.scale * 0.75) for v in range(plan.lout.n_shards)}
+    ref = Ly.conv_he_raised(o, plan, cts, pts, bias, pt_scale=float(o.q[level]) * 0.75)
+    lay = H.he_layout_image(c, m, o.N)
+    conv = H.he_conv_create(g.h, lay, W, None, 1, 1, level, o.pr.scale)
+    H.he_keygen_rotations(g.h, H.he_conv_rotations(conv))
+    ins = [g.upload(ct) for ct in cts]
+    for ks in (H.HE_KEY_STREAM_PK3, H.HE_KEY_STREAM_AUTO):
+        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
+        out = [g.ct(level - 1)]
+        H.he_conv_run(g.h, conv, ins, out, H.HE_FUSED)          # builds tables from its own plaintexts
+        keys = [(vv, uu, aa) for vv in sorted(plan.terms) for (uu, aa) in sorted(plan.terms[vv])]
+        H.he_conv_import_plaintexts(conv, np.stack([pts[(uu, vv, aa)] for (vv, uu, aa) in keys]),
+                                    np.stack([bias[v] for v in range(plan.lout.n_shards)]))
+        H.he_conv_run(g.h, conv, ins, out, H.HE_FUSED)
+        H.he_ctx_check(g.h)
+        assert_ct_equal(g.download(out[0]), ref[0])
+        H.he_conv_import_plaintexts(conv, np.stack([Ly.conv_plaintexts(plan, o.n, float(o.q[level]))[(uu, vv, aa)]
+                                                    for (vv, uu, aa) in keys]), None)
+    H.he_conv_destroy(conv)

@@ -42,7 +42,7 @@ def test_linear_head_bit_exact(mid, c, m, n_out, pool, level):
     lin = Ly.image_layout(c, m, o.N)
     plan = (Ly.pool_linear_plan if pool else Ly.linear_plan)(lin, W, b)
     cts = [o.encrypt(Ly.pack(lin, x)[u], level, nonce=300 + u) for u in range(lin.n_shards)]
-    w_pts, m_pts = Ly.linear_plaintexts(plan, o.n, float(o.q[level]), float(o.q[level - 1]))
+    w_pts, m_pts = Ly.linear_plaintexts(plan, o.n, *Ly.linear_scales(o, level))
     zb = np.zeros(o.N)
     zb[:n_out] = b
     b_pt = encode(zb, o.n, o.pr.scale)
@@ -66,7 +66,7 @@ def test_linear_head_bit_exact(mid, c, m, n_out, pool, level):
     else:
         want = W.reshape(n_out, -1) @ x.reshape(-1) + b
     got = H.he_decrypt(g.h, out, o.N)
-    tol = 2.0 ** -20 * max(1.0, want.max() - want.min())
+    tol = 2.0 ** -20 * (want.max() - want.min())
     assert np.abs(got[:n_out] - want).max() <= tol and np.abs(got[n_out:]).max() <= tol
     # the oracle's integer plaintexts: bit for bit
     H.he_linear_import_plaintexts(L, np.stack([np.stack([w_pts[(j, u)] for u in range(lin.n_shards)])
@@ -98,3 +98,48 @@ def test_linear_head_refuses_bad_plans(mid):
     with pytest.raises(H.HEError) as e:                 # more outputs than slots
         H.he_pool_linear_create(g.h, lay, np.ones((o.N + 1, 4)), None, 3, o.pr.scale)
     assert e.value.code == H.HE_EINVAL
+
+
+@pytest.mark.parametrize("c,m,n_out,pool,level", [(16, 8, 10, True, 4), (8, 16, 4, True, 3),
+                                                  (2, 64, 3, False, 2), (3, 28, 5, False, 3)])
+def test_packed_head_bit_exact(mid, c, m, n_out, pool, level):
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = mid
+    rng = np.random.default_rng(c * 17 + m)
+    x = rng.uniform(0, 1, (c, m, m))
+    W = rng.uniform(-1, 1, (n_out, c) if pool else (n_out, c, m, m))
+    b = rng.uniform(-1, 1, n_out)
+    lin = Ly.image_layout(c, m, o.N)
+    plan = (Ly.pool_linear_plan if pool else Ly.linear_plan)(lin, W, b)
+    cts = [o.encrypt(Ly.pack(lin, x)[u], level, nonce=500 + u) for u in range(lin.n_shards)]
+    w_pts, m_pt = Ly.linear_packed_plaintexts(plan, o.n, *Ly.linear_scales(o, level))
+    zb = np.zeros(o.N)
+    zb[:n_out] = b
+    b_pt = encode(zb, o.n, o.pr.scale)
+    ref = Ly.linear_packed_he(o, plan, cts, w_pts, m_pt, b_pt)
+    lay = H.he_layout_image(c, m, o.N)
+    create = H.he_pool_linear_create_packed if pool else H.he_linear_create_packed
+    L = create(g.h, lay, W, b, level, o.pr.scale)
+    npk = Ly.linear_packed_width(n_out)
+    assert sorted(H.he_linear_rotations(L)) == sorted(list(range(1, npk)) + Ly.linear_packed_shifts(plan))
+    assert H.he_linear_keyswitches(L) == lin.n_shards * (npk - 1) + len(Ly.linear_packed_shifts(plan))
+    H.he_keygen_rotations(g.h, H.he_linear_rotations(L))
+    ins = [g.upload(ct) for ct in cts]
+    out = g.ct(level)
+    H.he_linear_run(g.h, L, ins, out)                  # the library's own encoding
+    H.he_ctx_check(g.h)
+    want = W @ x.mean(axis=(1, 2)) + b if pool else W.reshape(n_out, -1) @ x.reshape(-1) + b
+    got = H.he_decrypt(g.h, out, o.N)
+    tol = 2.0 ** -20 * (want.max() - want.min())
+    assert np.abs(got[:n_out] - want).max() <= tol and np.abs(got[n_out:]).max() <= tol
+    H.he_linear_import_plaintexts(L, np.stack([np.stack([w_pts[(u, d)] for d in range(npk)])
+                                               for u in range(lin.n_shards)]), m_pt[None], b_pt)
+    for ks in (H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_PK3, H.HE_KEY_STREAM_SPLIT):
+        H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
+        H.he_linear_run(g.h, L, ins, out)
+        H.he_ctx_check(g.h)
+        assert H.he_ct_level(out) == ref.level and H.he_ct_scale(out) == ref.scale
+        assert_ct_equal(g.download(out), ref)
+    H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, H.HE_KEY_STREAM_AUTO)
+    H.he_linear_destroy(L)
