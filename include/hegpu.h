@@ -340,7 +340,9 @@ int he_conv_n_terms(const he_conv *conv);
 int he_conv_export_plan(const he_conv *conv, int32_t *u, int32_t *v, int32_t *a, double *diag);
 /* Replace the plan's encoded plaintexts by caller-given integer polynomials (plan order,
  * [n_terms][n]) and bias plaintexts ([n_out][n]); used to run on plaintexts encoded
- * elsewhere, e.g. for bit-exact comparison. */
+ * elsewhere, e.g. for bit-exact comparison.  The plan's pre-keyed tables (key x plaintext,
+ * HE_KEY_STREAM_PK*) are rebuilt on its next run; forks share the plaintext memory but not
+ * those tables, so import before forking (a fork made earlier keeps the old tables). */
 int he_conv_import_plaintexts(he_conv *conv, const int64_t *terms, const int64_t *bias);
 /* Run: out[v] (allocated by the caller at he_conv_out_level) for v < out layout n_shards.
  * mode HE_PLAIN = per-ciphertext launches; HE_BATCHED = every rotation of a stage in one
