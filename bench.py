@@ -200,7 +200,8 @@ def run_block(args, ws, rank, local):
     ctx = H.he_ctx_create(pr)
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
-                                                   "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK}[args.key_stream])
+                                                   "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
+                                                   "splitm": H.HE_KEY_STREAM_SPLITM}[args.key_stream])
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]
     q = info["q"]
@@ -309,7 +310,7 @@ def run_block(args, ws, rank, local):
         return
     # the roofline follows the kernel that carries the key switches of this step
     trace = args.trace
-    if trace == "ipmac" and ("-> split" in H.he_ctx_tuning_log(ctx) or args.key_stream == "split"):
+    if trace == "ipmac" and ("-> split" in H.he_ctx_tuning_log(ctx) or args.key_stream in ("split", "splitm")):
         trace = "rmac"
     clocks = Clocks(local)
     clocks.start()
@@ -506,7 +507,8 @@ def run_stem(args, ws, rank, local):
     ctx = H.he_ctx_create(pr)
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
-                                                   "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK}[args.key_stream])
+                                                   "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
+                                                   "splitm": H.HE_KEY_STREAM_SPLITM}[args.key_stream])
     N = H.he_ctx_info(ctx)["slots"]
     wl = workloads.imagenet_stem(0)
     c, m = wl.x.shape[0], wl.x.shape[1]
@@ -618,7 +620,7 @@ def main():
                     help="profiling case: same ring, 2-channel 32x32 conv (17 rotations, ~2 GB of keys)")
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, warm up, then run one batched step between cudaProfilerStart/Stop")
-    ap.add_argument("--key-stream", default="auto", choices=["auto", "ldg", "tma", "split", "pk"],
+    ap.add_argument("--key-stream", default="auto", choices=["auto", "ldg", "tma", "split", "pk", "splitm"],
                     help="key-switch + MAC form: autotuned (default), the fused kernel with vector "
                          "loads or a TMA tile pipeline, or the split form (inner products, then MAC)")
     ap.add_argument("--no-graph", action="store_true", help="launch the fused step eagerly, not as a CUDA graph")
@@ -659,7 +661,8 @@ def main():
     ctx = H.he_ctx_create(pr)
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
-                                                   "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK}[args.key_stream])
+                                                   "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
+                                                   "splitm": H.HE_KEY_STREAM_SPLITM}[args.key_stream])
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]
     wl = workloads.cifar_conv_bn(0, c=2) if args.small else workloads.cifar_conv_bn(0)

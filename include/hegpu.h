@@ -136,6 +136,9 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  *     Other stages fall back to the LDG form.  HE_KEY_STREAM_PK3 (7): the same kernel at three
  *     blocks per SM; HE_KEY_STREAM_PKP (8): at two blocks per SM with the next amount's key words
  *     requested before the current amount computes;
+ *   HE_KEY_STREAM_SPLITM (9): the split form with the raised MAC batched over the images of a
+ *     mixed-level batch (he_conv_run_batch): each plaintext word is read once for up to 4 images
+ *     x 4 outputs; a single image falls back to HE_KEY_STREAM_SPLIT;
  *   HE_KEY_STREAM_SPLIT (3): the split form: the raised inner product of every (source,
  *     amount) is written to HBM once (each key read once), then a raised-basis MAC forms the
  *     plaintext-weighted sums of 4 outputs per pass; amounts go in chunks of at most 2 GB of
@@ -154,6 +157,7 @@ int he_ctx_check(he_ctx *ctx, void *stream);
 #define HE_KEY_STREAM_PK 6
 #define HE_KEY_STREAM_PK3 7
 #define HE_KEY_STREAM_PKP 8
+#define HE_KEY_STREAM_SPLITM 9
 /* HE_OPT_PDL (0 default, or 1; process-wide, whichever context sets it): launch every kernel
  * with programmatic dependent launch, so each grid is set up while its predecessor on the
  * stream finishes (every kernel waits for the predecessor's writes before it reads).  Same

@@ -309,6 +309,21 @@ struct rgrp {               // HE_RV outputs of one stage
     int accumulate;         // add to acc (mod q) instead of overwriting: later amount chunks
     u64 *acc;               // [2 HE_RV][l+1+K][n]
 };
+// Image-batched raised MAC: HE_RNI stages (images of one batch, same plan, any levels) and
+// HE_RVM outputs per pass, so each plaintext word is read once for every image.
+#define HE_RVM 4
+#define HE_RNI 4
+struct rterm_m {
+    const u64 *U[HE_RNI];   // the term's inner product in each image (null: image absent)
+    const u64 *pt[HE_RVM];  // per output: plaintext, HE_PT_ONE or null
+};
+struct rgrp_m {
+    const rterm_m *terms;
+    int n_terms, ni, pt_level, nv, accumulate;
+    int level[HE_RNI];
+    u64 *acc[HE_RNI];       // per image: [2 HE_RVM][level+1+K][n] at the group's first output
+};
+int k_rmac_m(const he_ctx *ctx, const rgrp_m *grps, int n_grp, double bytes, double mulmods, cudaStream_t s);
 int k_ip_amounts(const he_ctx *ctx, const ugrp *grps_dev, int n_grp, int max_beta, double bytes, cudaStream_t s);
 int k_rmac(const he_ctx *ctx, const rgrp *grps_dev, int n_grp, double bytes, double mulmods, cudaStream_t s);
 void he_tune_note(he_ctx *ctx, const std::string &line);

@@ -2178,8 +2178,8 @@ __global__ void __launch_bounds__(TB) ip_amounts_kernel(KP kp, const ugrp *grps,
             for (int j = 0; j < B; j++)
                 if (j < beta) {
                     const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
-                    k0[j] = ld_hint(kp0, stream);
-                    k1[j] = ld_hint(kp0 + kstride, stream);
+                    k0[j] = ld_hint(kp0, keep);
+                    k1[j] = ld_hint(kp0 + kstride, keep);
                 }
         }
         for (int e = A.e0; e < A.e1; e++) {
@@ -2299,6 +2299,114 @@ int k_ip_amounts(const he_ctx *ctx, const ugrp *grps, int n_grp, int max_beta, d
     if (!attr_ok) { he_set_error("ip_amounts: shared-memory opt-in failed"); return HE_ECUDA; }
     if (max_beta <= 4) pdl_launch(ip_amounts_kernel<4>, g, TB, smem4, s, ctx->kp, grps, n_grp, ctx->d_consts);
     else pdl_launch(ip_amounts_kernel<8>, g, TB, smem8, s, ctx->kp, grps, n_grp, ctx->d_consts);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+// Image-batched form: per term, HE_RVM plaintext words (read once) meet the inner products of up
+// to HE_RNI images, each at its own level (an image without the block's q-prime sits out); the
+// same cp.async ring as rmac_kernel, HE_RVM + 2 HE_RNI words per term per thread.
+constexpr int RMACM_WORDS = HE_RVM + 2 * HE_RNI;
+
+__global__ void __launch_bounds__(TB, 1) rmac_m_kernel(KP kp, const rgrp_m *grps, int n_grp) {
+    pdl_wait();
+    constexpr int RV = HE_RVM, NI = HE_RNI, RS = RMAC_STAGES;
+    extern __shared__ u64 rsm[];                     // [RS][RMACM_WORDS][TB]
+    const rgrp_m P = grps[blockIdx.x % n_grp];
+    const int tile = blockIdx.x / n_grp;
+    const int kl = blockIdx.y;
+    int t[NI];
+    bool in[NI];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < NI; i++) {
+        in[i] = i < P.ni && (kl > kp.L || kl <= P.level[i]);
+        t[i] = kl <= kp.L ? kl : P.level[i] + 1 + (kl - kp.L - 1);
+        any = any || in[i];
+    }
+    if (!any) return;
+    const int k = tile * TB + threadIdx.x;
+    const int ptl = kl <= kp.L ? kl : P.pt_level + 1 + (kl - kp.L - 1);
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 one = to_mont(1, q, qi, r2);
+    const size_t ptoff = (size_t)ptl * kp.n + k;
+    const u64 stream = policy_evict_first();
+    const unsigned sbase = smem_u32(rsm);
+    auto slot = [&](int st, int w) -> int { return (st * RMACM_WORDS + w) * TB + threadIdx.x; };
+    auto issue = [&](int e, int st) {
+        const rterm_m T = P.terms[e];
+#pragma unroll
+        for (int v = 0; v < RV; v++)
+            if (T.pt[v] && T.pt[v] != HE_PT_ONE) cp_async8(sbase + 8u * slot(st, v), T.pt[v] + ptoff, stream);
+#pragma unroll
+        for (int i = 0; i < NI; i++)
+            if (in[i] && T.U[i]) {
+                const size_t ext = (size_t)(P.level[i] + 1 + kp.K) * kp.n;
+                cp_async8(sbase + 8u * slot(st, RV + 2 * i), T.U[i] + (size_t)t[i] * kp.n + k, stream);
+                cp_async8(sbase + 8u * slot(st, RV + 2 * i + 1), T.U[i] + ext + (size_t)t[i] * kp.n + k, stream);
+            }
+    };
+    u128 a0[RV][NI], a1[RV][NI];
+#pragma unroll
+    for (int v = 0; v < RV; v++)
+#pragma unroll
+        for (int i = 0; i < NI; i++) a0[v][i] = a1[v][i] = 0;
+    const int nt = P.n_terms;
+#pragma unroll
+    for (int e = 0; e < RS - 1; e++) {
+        if (e < nt) issue(e, e);
+        cp_async_commit();
+    }
+    for (int e = 0; e < nt; e++) {
+        if (e + RS - 1 < nt) issue(e + RS - 1, (e + RS - 1) % RS);
+        cp_async_commit();
+        cp_async_wait<RS - 1>();
+        const int st = e % RS;
+        const rterm_m T = P.terms[e];
+#pragma unroll
+        for (int v = 0; v < RV; v++)
+            if (T.pt[v]) {                           // block-uniform
+                const u64 p = T.pt[v] == HE_PT_ONE ? one : rsm[slot(st, v)];
+#pragma unroll
+                for (int i = 0; i < NI; i++)
+                    if (in[i] && T.U[i]) {
+                        a0[v][i] += (u128)p * rsm[slot(st, RV + 2 * i)];
+                        a1[v][i] += (u128)p * rsm[slot(st, RV + 2 * i + 1)];
+                    }
+            }
+    }
+    cp_async_wait<0>();
+    auto put = [&](u64 *dst, u128 acc) {
+        u64 r = redc(acc, q, qi);
+        if (P.accumulate) {
+            r += *dst;
+            if (r >= q) r -= q;
+        }
+        *dst = r;
+    };
+#pragma unroll
+    for (int i = 0; i < NI; i++)
+        if (in[i]) {
+            const size_t ext = (size_t)(P.level[i] + 1 + kp.K) * kp.n;
+            const size_t off = (size_t)t[i] * kp.n + k;
+#pragma unroll
+            for (int v = 0; v < RV; v++)
+                if (v < P.nv) {
+                    put(P.acc[i] + (size_t)(2 * v) * ext + off, a0[v][i]);
+                    put(P.acc[i] + (size_t)(2 * v + 1) * ext + off, a1[v][i]);
+                }
+        }
+}
+
+int k_rmac_m(const he_ctx *ctx, const rgrp_m *grps, int n_grp, double bytes, double mulmods, cudaStream_t s) {
+    if (n_grp <= 0) return HE_OK;
+    TraceScope tr("rmac", s, bytes, mulmods);
+    dim3 g((unsigned)(ctx->n / TB) * n_grp, ctx->L + 1 + ctx->K);
+    const int smem = RMAC_STAGES * RMACM_WORDS * TB * 8;
+    static const bool attr_ok =
+        cudaFuncSetAttribute(rmac_m_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+    if (!attr_ok) { he_set_error("rmac_m: shared-memory opt-in failed"); return HE_ECUDA; }
+    pdl_launch(rmac_m_kernel, g, TB, smem, s, ctx->kp, grps, n_grp);
     LAUNCH_CHECK();
     return HE_OK;
 }

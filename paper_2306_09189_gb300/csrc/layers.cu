@@ -500,6 +500,7 @@ struct FusedStage {
         std::vector<rterm *> d_terms;                 // per output group of HE_RV
         std::vector<rgrp> rdesc;
         double ubytes = 0, rbytes = 0, rmm = 0;
+        std::vector<std::pair<std::pair<int, int>, u64 *>> ukeys;   // (amount, source) -> U, ordered
     };
     std::vector<Chunk> chunks;
     u64 *U = nullptr;                                 // [slots][2][ext][n] of the largest chunk
@@ -576,7 +577,7 @@ struct FusedStage {
         split_ready = false;
     }
     size_t split_bytes() const;                       // device memory the split form needs
-    int build_split(size_t cap_bytes);
+    int build_split(size_t cap_bytes, size_t plan_slot_bytes = 0);
     void free_groups() {
         for (auto &g : groups) { cudaFree(g.d_amt); cudaFree(g.d_ent); }
         groups.clear();
@@ -746,6 +747,12 @@ struct FusedLaunch {
     std::vector<int> n_ugrp, n_rgrp;
     std::vector<double> ubytes, rbytes, rmm;
     bool split_built = false;
+    // image-batched split form: per amount chunk, groups of HE_RNI stages x HE_RVM outputs
+    std::vector<rgrp_m *> d_mgrps;
+    std::vector<std::vector<rterm_m *>> d_mterms;
+    std::vector<int> n_mgrp;
+    std::vector<double> mbytes, mmm;
+    bool splitm_built = false, use_split_m = false;
     // pre-keyed form: one group per output of every stage
     fgrp *d_pk = nullptr;
     int G_pk = 0;
@@ -753,6 +760,111 @@ struct FusedLaunch {
     bool use_pk = false;
 
     ~FusedLaunch() { cudaFree(d_grps); cudaFree(d_pk); free_split_tables(); }
+    // the stages of a batch share one plan (the same terms, sources and outputs; plaintexts and
+    // their level): the image-batched split form applies
+    bool splitm_ok() const {
+        if (st.size() < 2) return false;
+        const FusedStage *a = st[0];
+        for (auto *f : st) {
+            if (f->terms.size() != a->terms.size() || f->outs.size() != a->outs.size() ||
+                f->srcs.size() != a->srcs.size() || f->pt_level != a->pt_level)
+                return false;
+            for (size_t i = 0; i < f->terms.size(); i++)
+                if (f->terms[i].v != a->terms[i].v || f->terms[i].s != a->terms[i].s || f->terms[i].a != a->terms[i].a ||
+                    f->terms[i].pt != a->terms[i].pt)
+                    return false;
+        }
+        return true;
+    }
+    int build_split_m() {
+        if (splitm_built) return HE_OK;
+        HE_TRY(build_split());
+        const size_t nch = st[0]->chunks.size();
+        for (auto *f : st)
+            if (f->chunks.size() != nch) { he_set_error("image-batched split: chunk plans differ"); return HE_ESTATE; }
+        const FusedStage *a = st[0];
+        const int nout = (int)a->outs.size();
+        std::map<std::array<int, 3>, const u64 *> ptm;            // (amount, source, output) -> plaintext
+        for (auto &t : a->terms) ptm[{h_galois(c, t.a) == 1 ? 0 : t.a, t.s, t.v}] = t.pt;
+        const size_t n = c->n;
+        for (size_t ci = 0; ci < nch; ci++) {
+            std::vector<rgrp_m> hg;
+            std::vector<rterm_m *> owned;
+            double b = 0, mm = 0;
+            for (size_t g0 = 0; g0 < st.size(); g0 += HE_RNI) {
+                const int ni = (int)std::min<size_t>(HE_RNI, st.size() - g0);
+                const auto &keys = st[g0]->chunks[ci].ukeys;
+                for (int i = 1; i < ni; i++)
+                    if (st[g0 + i]->chunks[ci].ukeys.size() != keys.size()) {
+                        he_set_error("image-batched split: chunk terms differ");
+                        return HE_ESTATE;
+                    }
+                for (int v0 = 0; v0 < nout; v0 += HE_RVM) {
+                    std::vector<rterm_m> ht;
+                    for (size_t r = 0; r < keys.size(); r++) {
+                        rterm_m T{};
+                        bool used = false;
+                        for (int v = 0; v < HE_RVM && v0 + v < nout; v++) {
+                            auto it = ptm.find({keys[r].first.first, keys[r].first.second, v0 + v});
+                            if (it != ptm.end()) { T.pt[v] = it->second; used = true; }
+                        }
+                        if (!used) continue;
+                        for (int i = 0; i < ni; i++) {
+                            const auto &kk = st[g0 + i]->chunks[ci].ukeys[r];
+                            if (kk.first != keys[r].first) { he_set_error("image-batched split: term order differs"); return HE_ESTATE; }
+                            T.U[i] = kk.second;
+                        }
+                        ht.push_back(T);
+                    }
+                    rterm_m *d = nullptr;
+                    HE_TRY(dev_alloc(&d, std::max<size_t>(1, ht.size())));
+                    if (!ht.empty()) HE_CHECK_CUDA(cudaMemcpy(d, ht.data(), ht.size() * sizeof(rterm_m), cudaMemcpyHostToDevice));
+                    owned.push_back(d);
+                    rgrp_m G{};
+                    G.terms = d;
+                    G.n_terms = (int)ht.size();
+                    G.ni = ni;
+                    G.pt_level = a->pt_level;
+                    G.nv = std::min(HE_RVM, nout - v0);
+                    G.accumulate = ci > 0 ? 1 : 0;
+                    int maxext = 0;
+                    for (int i = 0; i < ni; i++) {
+                        const FusedStage *f = st[g0 + i];
+                        G.level[i] = f->level;
+                        G.acc[i] = f->facc + (size_t)v0 * 2 * f->ext() * n;
+                        maxext = std::max(maxext, f->ext());
+                    }
+                    hg.push_back(G);
+                    for (auto &T : ht) {
+                        for (int v = 0; v < HE_RVM; v++)
+                            if (T.pt[v]) {
+                                if (T.pt[v] != HE_PT_ONE) b += (double)maxext * n * 8;
+                                for (int i = 0; i < ni; i++) mm += (double)2 * st[g0 + i]->ext() * n;
+                            }
+                        for (int i = 0; i < ni; i++) b += (double)2 * st[g0 + i]->ext() * n * 8;
+                    }
+                    for (int i = 0; i < ni; i++) b += (double)G.nv * 2 * st[g0 + i]->ext() * n * 8;
+                }
+            }
+            rgrp_m *dg = nullptr;
+            HE_TRY(dev_alloc(&dg, std::max<size_t>(1, hg.size())));
+            if (!hg.empty()) HE_CHECK_CUDA(cudaMemcpy(dg, hg.data(), hg.size() * sizeof(rgrp_m), cudaMemcpyHostToDevice));
+            d_mgrps.push_back(dg);
+            d_mterms.push_back(owned);
+            n_mgrp.push_back((int)hg.size());
+            mbytes.push_back(b);
+            mmm.push_back(mm);
+        }
+        splitm_built = true;
+        return HE_OK;
+    }
+    void free_split_m_tables() {
+        for (auto *p : d_mgrps) cudaFree(p);
+        for (auto &v : d_mterms)
+            for (auto *p : v) cudaFree(p);
+        d_mgrps.clear(); d_mterms.clear(); n_mgrp.clear(); mbytes.clear(); mmm.clear();
+        splitm_built = false;
+    }
     bool pk_ok() {
         for (auto *f : st)
             if (!f->pk_eligible()) return false;
@@ -808,6 +920,7 @@ struct FusedLaunch {
         d_ugrps.clear(); d_rgrps.clear(); n_ugrp.clear(); n_rgrp.clear();
         ubytes.clear(); rbytes.clear(); rmm.clear();
         split_built = false;
+        free_split_m_tables();
     }
     int vmax() const {
         for (auto *f : st)
@@ -846,9 +959,10 @@ struct FusedLaunch {
 
     int build_split() {
         if (split_built) return HE_OK;
-        size_t nch = 0;
+        size_t nch = 0, plan_slot = 0;
+        for (auto *f : st) plan_slot = std::max(plan_slot, (size_t)2 * f->ext() * c->n * 8);
         for (auto *f : st) {
-            HE_TRY(f->build_split((size_t)2 << 30));
+            HE_TRY(f->build_split((size_t)2 << 30, plan_slot));
             nch = std::max(nch, f->chunks.size());
         }
         for (size_t ci = 0; ci < nch; ci++) {
@@ -883,12 +997,13 @@ struct FusedLaunch {
     }
 
     int launch(int fm, cudaStream_t s) { return k_ipmac(c, d_grps, G, V, max_beta, bytes, mulmods, fm, gb, s); }
-    int launch_split(cudaStream_t s) {
+    int launch_split(cudaStream_t s, bool multi = false) {
         int mb = 0;
         for (auto *f : st) mb = std::max(mb, f->beta());
         for (size_t ci = 0; ci < d_ugrps.size(); ci++) {
             HE_TRY(k_ip_amounts(c, d_ugrps[ci], n_ugrp[ci], mb, ubytes[ci], s));
-            HE_TRY(k_rmac(c, d_rgrps[ci], n_rgrp[ci], rbytes[ci], rmm[ci], s));
+            if (multi) HE_TRY(k_rmac_m(c, d_mgrps[ci], n_mgrp[ci], mbytes[ci], mmm[ci], s));
+            else HE_TRY(k_rmac(c, d_rgrps[ci], n_rgrp[ci], rbytes[ci], rmm[ci], s));
         }
         return HE_OK;
     }
@@ -995,6 +1110,16 @@ struct FusedLaunch {
                     pos += snprintf(line + pos, sizeof(line) - pos, " split (%zu chunk(s)) %.3f ms;", d_ugrps.size(), t);
                 if (t < best) { best = t; bestSplit = true; bestPk = false; }
             }
+            if (rc == HE_OK && splitm_ok()) {
+                rc = build_split_m();
+                if (rc == HE_OK) rc = time_it([&]() { return launch_split(s, true); }, t);
+                if (rc == HE_OK) {
+                    if (pos < (int)sizeof(line))
+                        pos += snprintf(line + pos, sizeof(line) - pos, " split-m %.3f ms;", t);
+                    if (t < best) { best = t; bestSplit = true; bestPk = false; use_split_m = true; }
+                }
+            }
+            if (!use_split_m) free_split_m_tables();
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
@@ -1022,7 +1147,7 @@ struct FusedLaunch {
         tuned = true;
         if (pos < (int)sizeof(line)) {
             if (bestPk) snprintf(line + pos, sizeof(line) - pos, " -> %s", pk_name(pk_form));
-            else if (bestSplit) snprintf(line + pos, sizeof(line) - pos, " -> split");
+            else if (bestSplit) snprintf(line + pos, sizeof(line) - pos, use_split_m ? " -> split-m" : " -> split");
             else snprintf(line + pos, sizeof(line) - pos, " -> V=%d %s gb=%d", bestV, form_name(bestF),
                           bestGb ? bestGb : G);
         }
@@ -1033,9 +1158,12 @@ struct FusedLaunch {
     int run(cudaStream_t s) {
         const int opt = c->key_stream;
         for (auto *f : st) HE_TRY(f->hoist(s));
-        if (opt == HE_KEY_STREAM_SPLIT) {                       // explicit split form
+        if (opt == HE_KEY_STREAM_SPLIT || (opt == HE_KEY_STREAM_SPLITM && !splitm_ok())) {   // explicit split form
             HE_TRY(build_split());
             HE_TRY(launch_split(s));
+        } else if (opt == HE_KEY_STREAM_SPLITM) {              // explicit image-batched split form
+            HE_TRY(build_split_m());
+            HE_TRY(launch_split(s, true));
         } else if (is_pk(opt) && pk_ok()) {                     // explicit pre-keyed form
             HE_TRY(build_pk());
             HE_TRY(launch_pk(s, opt));
@@ -1047,7 +1175,7 @@ struct FusedLaunch {
             if (!d_grps && !use_split && !use_pk) HE_TRY(build(vmax()));
             if (!tuned) HE_TRY(tune(s));
             if (use_pk) HE_TRY(launch_pk(s));
-            else if (use_split) HE_TRY(launch_split(s));
+            else if (use_split) HE_TRY(launch_split(s, use_split_m));
             else HE_TRY(launch(form, s));
         }
         for (auto *f : st) HE_TRY(f->moddown(s));
@@ -1086,7 +1214,9 @@ size_t FusedStage::split_bytes() const {
     return best;
 }
 
-int FusedStage::build_split(size_t cap_bytes) {
+// plan_slot_bytes: the U slot size the amount chunks are planned with (a batch passes its
+// largest, so every image of it gets the same chunk boundaries)
+int FusedStage::build_split(size_t cap_bytes, size_t plan_slot_bytes) {
     if (split_ready) return HE_OK;
     HE_TRY(build());
     const int nq_ = nq(), ext_ = ext(), beta_ = beta();
@@ -1094,7 +1224,7 @@ int FusedStage::build_split(size_t cap_bytes) {
     std::vector<const u64 *> Dp(srcs.size());
     for (size_t i = 0; i < srcs.size(); i++)
         Dp[i] = hslot[i] >= 0 ? D_all + (size_t)hslot[i] * beta_ * ext_ * n : nullptr;
-    auto plan = split_plan(*this, slot * 8, cap_bytes);
+    auto plan = split_plan(*this, plan_slot_bytes ? plan_slot_bytes : slot * 8, cap_bytes);
     size_t max_slots = 0;
     for (auto &ch : plan) {
         size_t k = 0;
@@ -1133,6 +1263,7 @@ int FusedStage::build_split(size_t cap_bytes) {
         if (!ha.empty()) HE_CHECK_CUDA(cudaMemcpy(ch.d_amt, ha.data(), ha.size() * sizeof(famt), cudaMemcpyHostToDevice));
         if (!he.empty()) HE_CHECK_CUDA(cudaMemcpy(ch.d_ent, he.data(), he.size() * sizeof(uent), cudaMemcpyHostToDevice));
         ch.udesc = ugrp{ch.d_amt, ch.d_ent, (int)ha.size(), (int)he.size(), level, beta_};
+        for (auto &kv : uslot) ch.ukeys.push_back(kv);
         // raised MAC terms per group of HE_RV outputs: this chunk's (a, s) pairs
         for (int v0 = 0; v0 < nout; v0 += HE_RV) {
             std::map<std::pair<int, int>, rterm> tm;

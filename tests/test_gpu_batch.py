@@ -39,7 +39,7 @@ def test_mixed_level_batch_bit_exact():
         conv = H.he_conv_create(g.h, lay, W, b, 1, pad, top, o.pr.scale)
         H.he_keygen_rotations(g.h, H.he_conv_rotations(conv))
         H.he_conv_import_plaintexts(conv, np.stack([pts[(uu, vv, aa)] for (vv, uu, aa) in keys]), None)
-        levels = [5, 3, 4]
+        levels = [5, 3, 4, 2, 5]                  # two image groups of the image-batched MAC
         imgs, cts, refs_f, refs_p, ins = [], [], [], [], []
         for i, lv in enumerate(levels):
             x = rng.uniform(0, 1, (c, m, m))
@@ -55,7 +55,7 @@ def test_mixed_level_batch_bit_exact():
         runs = [(H.HE_FUSED, H.HE_KEY_STREAM_AUTO, refs_f), (H.HE_FUSED, H.HE_KEY_STREAM_LDG, refs_f),
                 (H.HE_FUSED, H.HE_KEY_STREAM_TMA, refs_f), (H.HE_FUSED, H.HE_KEY_STREAM_SPLIT, refs_f),
                 (H.HE_FUSED, H.HE_KEY_STREAM_CP, refs_f), (H.HE_FUSED, H.HE_KEY_STREAM_LDG1, refs_f),
-                (H.HE_FUSED, H.HE_KEY_STREAM_PK, refs_f),
+                (H.HE_FUSED, H.HE_KEY_STREAM_PK, refs_f), (H.HE_FUSED, H.HE_KEY_STREAM_SPLITM, refs_f),
                 (H.HE_PLAIN, H.HE_KEY_STREAM_AUTO, refs_p), (H.HE_BATCHED, H.HE_KEY_STREAM_AUTO, refs_p)]
         for mode, ks, refs in runs:
             H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)

@@ -136,7 +136,7 @@ def test_bsgs_mixed_level_batch_bit_exact(mid):
         refs_f.append(Ly.conv_he_bsgs(o, bp, ci, pts, bias, pt_scale=S_pt, raised=True))
         refs_p.append(Ly.conv_he_bsgs(o, bp, ci, pts, bias, pt_scale=S_pt, raised=False))
         ins += [g.upload(ct) for ct in ci]
-    runs = [(H.HE_FUSED, f, refs_f) for f in ("AUTO", "LDG", "TMA", "SPLIT", "PK")]
+    runs = [(H.HE_FUSED, f, refs_f) for f in ("AUTO", "LDG", "TMA", "SPLIT", "SPLITM", "PK")]
     runs += [(H.HE_PLAIN, "AUTO", refs_p), (H.HE_BATCHED, "AUTO", refs_p)]
     no = plan.lout.n_shards
     for mode, form, refs in runs:
