@@ -12,6 +12,7 @@
 #include <atomic>
 #include <array>
 #include <cmath>
+#include <functional>
 #include <thread>
 #include <unordered_map>
 #include <set>
@@ -3158,6 +3159,88 @@ static int ps_lincomb(he_ctx *c, const std::vector<std::pair<double, const he_ct
     return HE_OK;
 }
 
+// Deferred Paterson-Stockmeyer evaluation.  The plan is recorded as operations, each with the
+// ciphertexts it reads and writes; a scheduler then issues, round by round, every ready operation
+// that is not a product (in program order), then every ready product of one level as one batched
+// relinearisation.  An operation is ready when no earlier unfinished operation writes what it
+// reads or touches what it writes, so every ciphertext gets the bits of the program-order
+// evaluation; independent products of equal level (T_3 and T_4; the last giant step and the
+// product inside a quotient; two sibling quotients' products) share one set of launches.
+struct PsOp {
+    bool prod = false;
+    std::vector<const he_ct *> rd, wr;
+    std::function<int()> fn;                                  // not a product
+    std::function<void(he_ct &, he_ct &)> views;              // product operands, built at issue
+    he_ct *out = nullptr;
+    std::function<double()> expect;                           // product: predicted output scale
+    bool done = false;
+};
+
+// A scale that is known once the ciphertexts in deps are computed.
+struct PsScale {
+    std::function<double()> f;
+    std::vector<const he_ct *> deps;
+};
+
+static int ps_run(he_ctx *c, std::vector<PsOp> &ops, cudaStream_t s) {
+    auto hit = [](const std::vector<const he_ct *> &a, const std::vector<const he_ct *> &b) {
+        for (const he_ct *x : a)
+            for (const he_ct *y : b)
+                if (x == y) return true;
+        return false;
+    };
+    auto ready = [&](size_t i) {
+        for (size_t j = 0; j < i; j++)
+            if (!ops[j].done && (hit(ops[j].wr, ops[i].rd) || hit(ops[j].wr, ops[i].wr) || hit(ops[j].rd, ops[i].wr)))
+                return false;
+        return true;
+    };
+    size_t left = ops.size();
+    while (left) {
+        bool moved = false;
+        for (size_t i = 0; i < ops.size(); i++)
+            if (!ops[i].done && !ops[i].prod && ready(i)) {
+                HE_TRY(ops[i].fn());
+                ops[i].done = true;
+                left--;
+                moved = true;
+            }
+        std::vector<size_t> P;
+        std::vector<he_ct> va, vb;
+        int lv = -1;
+        for (size_t i = 0; i < ops.size(); i++) {
+            if (ops[i].done || !ops[i].prod || !ready(i)) continue;
+            he_ct a, b;
+            ops[i].views(a, b);
+            if (a.level != b.level) { he_set_error("polynomial: product operands at levels %d and %d", a.level, b.level); return HE_ESTATE; }
+            if (lv < 0) lv = a.level;
+            if (a.level != lv) continue;
+            P.push_back(i);
+            va.push_back(a);
+            vb.push_back(b);
+        }
+        if (!P.empty()) {
+            std::vector<const he_ct *> A, B;
+            std::vector<he_ct *> O;
+            for (size_t k = 0; k < P.size(); k++) {
+                A.push_back(&va[k]);
+                B.push_back(&vb[k]);
+                O.push_back(ops[P[k]].out);
+            }
+            HE_TRY(relin_batch(c, A, B, O, s));
+            for (size_t k = 0; k < P.size(); k++) {
+                PsOp &o = ops[P[k]];
+                if (o.expect && o.out->scale != o.expect()) { he_set_error("polynomial: product scale off its prediction"); return HE_ESTATE; }
+                o.done = true;
+                left--;
+            }
+            moved = true;
+        }
+        if (!moved) { he_set_error("polynomial: schedule stalled"); return HE_ESTATE; }
+    }
+    return HE_OK;
+}
+
 struct PsGroup {
     he_ctx *c;
     cudaStream_t s;
@@ -3167,17 +3250,46 @@ struct PsGroup {
     std::vector<std::map<int, he_ct *>> T;                   // per ciphertext: index -> T_index
     std::vector<std::vector<he_ct *>> tq, tr;                // per ciphertext, per recursion depth
     std::vector<he_ct *> t1, y;
+    std::vector<PsOp> ops;
 
-    int ev(const std::vector<double> &cc, int level, const std::vector<double> &scale, const std::vector<he_ct *> &out,
-           int depth) {
+    // a linear combination of T's (scratch y only where ps_lincomb takes its term-by-term form)
+    void lincomb(int j, std::vector<std::pair<double, int>> terms, double c0, int level, const PsScale &sc,
+                 he_ct *out) {
+        PsOp o;
+        for (auto &t : terms) o.rd.push_back(T[j][t.second]);
+        for (auto *d : sc.deps) o.rd.push_back(d);
+        o.wr.push_back(out);
+        if (!((int)terms.size() <= HE_LC_MAX && level + 2 <= HE_LC_LIMBS)) o.wr.push_back(y[j]);
+        he_ctx *cc = c;
+        cudaStream_t st = s;
+        std::vector<std::pair<double, const he_ct *>> tv;
+        for (auto &t : terms) tv.push_back({t.first, T[j][t.second]});
+        he_ct *yj = y[j];
+        std::function<double()> f = sc.f;
+        o.fn = [cc, st, tv, c0, level, f, out, yj]() { return ps_lincomb(cc, tv, c0, level, f(), out, yj, st); };
+        ops.push_back(std::move(o));
+    }
+    void add(he_ct *acc, he_ct *b) {
+        PsOp o;
+        o.rd = {acc, b};
+        o.wr = {acc};
+        he_ctx *cc = c;
+        cudaStream_t st = s;
+        o.fn = [cc, st, acc, b]() { return he_add(cc, acc, b, st); };
+        ops.push_back(std::move(o));
+    }
+
+    // records the evaluation of sum cc_i T_i into out at (level, sc); returns the result's scale
+    std::vector<PsScale> ev(const std::vector<double> &cc, int level, const std::vector<PsScale> &sc,
+                            const std::vector<he_ct *> &out, int depth) {
         const int d = (int)cc.size() - 1;
         if (d < k) {
             for (int j = 0; j < m; j++) {
-                std::vector<std::pair<double, const he_ct *>> terms;
-                for (int i = 1; i <= d; i++) terms.push_back({cc[i], T[j][i]});
-                HE_TRY(ps_lincomb(c, terms, cc[0], level, scale[j], out[j], y[j], s));
+                std::vector<std::pair<double, int>> terms;
+                for (int i = 1; i <= d; i++) terms.push_back({cc[i], i});
+                lincomb(j, terms, cc[0], level, sc[j], out[j]);
             }
-            return HE_OK;
+            return sc;
         }
         int G = 0;
         for (int g : giants)
@@ -3186,44 +3298,65 @@ struct PsGroup {
         cheb_divide(cc, G, q, r);
         if (q.size() == 1 && G - 1 < k) {                    // q_0 T_G + r in one combination
             for (int j = 0; j < m; j++) {
-                std::vector<std::pair<double, const he_ct *>> terms;
-                for (int i = 1; i < G; i++) terms.push_back({r[i], T[j][i]});
-                terms.push_back({q[0], T[j][G]});
-                HE_TRY(ps_lincomb(c, terms, r[0], level, scale[j], out[j], y[j], s));
+                std::vector<std::pair<double, int>> terms;
+                for (int i = 1; i < G; i++) terms.push_back({r[i], i});
+                terms.push_back({q[0], G});
+                lincomb(j, terms, r[0], level, sc[j], out[j]);
             }
-            return HE_OK;
+            return sc;
         }
         if (q.size() == 1) {                                 // ev(r) plus the scalar q_0 T_G
-            HE_TRY(ev(r, level, scale, out, depth + 1));
+            std::vector<PsScale> res = ev(r, level, sc, out, depth + 1);
             for (int j = 0; j < m; j++) {
-                HE_TRY(ps_lincomb(c, {{q[0], T[j][G]}}, 0.0, level, scale[j], tq[j][depth], y[j], s));
-                HE_TRY(he_add(c, out[j], tq[j][depth], s));
+                lincomb(j, {{q[0], G}}, 0.0, level, sc[j], tq[j][depth]);
+                add(out[j], tq[j][depth]);
             }
-            return HE_OK;
+            return res;
         }
-        std::vector<double> sq(m);
-        std::vector<he_ct> tg(m);
+        // q T_G + r: the quotient one level up, its product with T_G (dropped to level + 1), then
+        // the remainder at the product's scale
+        const double ql1 = (double)c->primes[level + 1];
+        std::vector<PsScale> sq(m);
         std::vector<he_ct *> qo(m), ro(m);
         for (int j = 0; j < m; j++) {
-            tg[j] = *T[j][G];                                // T_G dropped to level + 1 (a view)
-            tg[j].level = level + 1;
-            sq[j] = scale[j] * (double)c->primes[level + 1] / tg[j].scale;
+            const he_ct *TG = T[j][G];
+            std::function<double()> f = sc[j].f;
+            sq[j].f = [f, ql1, TG]() { return f() * ql1 / TG->scale; };
+            sq[j].deps = sc[j].deps;
+            sq[j].deps.push_back(TG);
             qo[j] = tq[j][depth];
             ro[j] = tr[j][depth];
         }
-        HE_TRY(ev(q, level + 1, sq, qo, depth + 1));
-        std::vector<const he_ct *> A, B;
+        std::vector<PsScale> resq = ev(q, level + 1, sq, qo, depth + 1);
+        std::vector<PsScale> ps_(m);
         for (int j = 0; j < m; j++) {
-            if (qo[j]->level != level + 1) { he_set_error("polynomial: quotient off its level"); return HE_ESTATE; }
-            A.push_back(qo[j]);
-            B.push_back(&tg[j]);
+            const he_ct *TG = T[j][G];
+            he_ct *a = qo[j];
+            const int lp1 = level + 1;
+            PsOp o;
+            o.prod = true;
+            o.rd = {a, TG};
+            o.wr = {out[j]};
+            o.out = out[j];
+            o.views = [a, TG, lp1](he_ct &A, he_ct &B) {
+                A = *a;
+                B = *TG;                                     // T_G dropped to level + 1 (a view)
+                B.level = lp1;
+            };
+            std::function<double()> fq = resq[j].f;
+            // relin_batch's own arithmetic: (s_A s_B) / q_{level+1}
+            o.expect = [fq, TG, ql1]() {
+                double t = fq() * TG->scale;
+                return t / ql1;
+            };
+            ps_[j].f = o.expect;
+            ps_[j].deps = resq[j].deps;
+            ps_[j].deps.push_back(TG);
+            ops.push_back(std::move(o));
         }
-        HE_TRY(relin_batch(c, A, B, out, s));
-        std::vector<double> ps_(m);
-        for (int j = 0; j < m; j++) ps_[j] = out[j]->scale;
-        HE_TRY(ev(r, level, ps_, ro, depth + 1));
-        for (int j = 0; j < m; j++) HE_TRY(he_add(c, out[j], ro[j], s));
-        return HE_OK;
+        ev(r, level, ps_, ro, depth + 1);
+        for (int j = 0; j < m; j++) add(out[j], ro[j]);
+        return ps_;
     }
 };
 
@@ -3264,41 +3397,53 @@ static int ps_group(he_ctx *c, const std::vector<he_ct *> &io, const double *che
         if (u > per) { he_set_error("polynomial: temporaries"); return HE_ESTATE; }
         HE_TRY(he_ct_copy(P.T[j][1], io[j], s));
     }
-    // baby and giant steps, index by index, each product batched over the group
+    // baby and giant steps: T_2h = 2 T_h^2 - 1, T_2h+1 = 2 T_h T_h+1 - T_1 (operands dropped to the
+    // lower of their levels)
     for (int i : idx) {
         if (i == 1) continue;
         const int h = i / 2;
-        std::vector<const he_ct *> A, B;
-        std::vector<he_ct *> O;
-        std::vector<he_ct> va(P.m), vb(P.m);
         for (int j = 0; j < P.m; j++) {
+            he_ct *Th = P.T[j][h], *Ti = P.T[j][i], *T1 = P.T[j][1], *t1 = P.t1[j];
+            he_ct *Th1 = i % 2 ? P.T[j][h + 1] : nullptr;
+            PsOp o;
+            o.prod = true;
+            o.out = Ti;
+            o.wr = {Ti};
             if (i % 2 == 0) {
-                A.push_back(P.T[j][h]);
-                B.push_back(P.T[j][h]);
+                o.rd = {Th};
+                o.views = [Th](he_ct &A, he_ct &B) { A = *Th; B = *Th; };
             } else {
-                const int lv = std::min(P.T[j][h]->level, P.T[j][h + 1]->level);
-                va[j] = *P.T[j][h];
-                va[j].level = lv;
-                vb[j] = *P.T[j][h + 1];
-                vb[j].level = lv;
-                A.push_back(&va[j]);
-                B.push_back(&vb[j]);
+                o.rd = {Th, Th1};
+                o.views = [Th, Th1](he_ct &A, he_ct &B) {
+                    const int lv = std::min(Th->level, Th1->level);
+                    A = *Th;
+                    A.level = lv;
+                    B = *Th1;
+                    B.level = lv;
+                };
             }
-            O.push_back(P.T[j][i]);
-        }
-        HE_TRY(relin_batch(c, A, B, O, s));
-        for (int j = 0; j < P.m; j++) {
-            he_ct *x = P.T[j][i];
-            HE_TRY(he_mul_int(c, x, 2.0, s));
-            if (i % 2 == 0) {
-                HE_TRY(he_add_const_int(c, x, -std::nearbyint(x->scale), s));
-            } else {
-                HE_TRY(retarget(c, P.T[j][1], x->level, x->scale, P.t1[j], s));
-                HE_TRY(he_sub(c, x, P.t1[j], s));
-            }
+            P.ops.push_back(std::move(o));
+            PsOp f;
+            f.rd = {Ti, T1};
+            f.wr = {Ti};
+            if (i % 2) f.wr.push_back(t1);
+            const bool even = i % 2 == 0;
+            f.fn = [c, s, Ti, T1, t1, even]() {
+                HE_TRY(he_mul_int(c, Ti, 2.0, s));
+                if (even) return he_add_const_int(c, Ti, -std::nearbyint(Ti->scale), s);
+                HE_TRY(retarget(c, T1, Ti->level, Ti->scale, t1, s));
+                return he_sub(c, Ti, t1, s);
+            };
+            P.ops.push_back(std::move(f));
         }
     }
-    HE_TRY(P.ev(cc, lin - need, tgt, outv, 0));
+    std::vector<PsScale> sc(P.m);
+    for (int j = 0; j < P.m; j++) {
+        const double v = tgt[j];
+        sc[j].f = [v]() { return v; };
+    }
+    P.ev(cc, lin - need, sc, outv, 0);
+    HE_TRY(ps_run(c, P.ops, s));
     for (int j = 0; j < P.m; j++) HE_TRY(he_ct_copy(io[j], outv[j], s));
     return HE_OK;
 }

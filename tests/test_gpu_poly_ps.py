@@ -71,3 +71,26 @@ def test_ps_minimax_gelu_degree_59(deep):
     got = H.he_decrypt(g.h, gc, o.N)
     want = np.array([Ly.gelu(16 * v) for v in z])
     assert np.abs(got - want).max() <= E + 2.0 ** -20 * (want.max() - want.min())
+
+
+def test_ps_batches_independent_products(deep):
+    # degree 16 (k = 4, giants 4, 8, 16) has eight products at five operand levels: T_2 | T_3, T_4
+    # | T_8 | T_16 with the product inside the T_8 quotient | the two products of the T_8 and T_4
+    # quotients of the remainder.  The scheduler issues one batched relinearisation per level
+    # (five inner-product launches for one ciphertext), and the bits stay the oracle's.
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = deep
+    c = Ly.cheb_nodes_coeffs(Ly.gelu, 16, -8, 8)
+    ct = o.encrypt(np.random.default_rng(16).uniform(-1, 1, o.N), 9, nonce=4016)
+    ref = Ly.cheb_ps_he(o, ct, c, target_scale=o.pr.scale)
+    gc = g.upload(ct)
+    H.he_poly_eval_ps(g.h, gc, c, o.pr.scale)          # warm (temporaries, scratch)
+    gc = g.upload(ct)
+    H.he_trace_start("ip")
+    H.he_poly_eval_ps(g.h, gc, c, o.pr.scale)
+    tr = H.he_trace_stop()
+    H.he_ctx_check(g.h)
+    assert tr["launches"] == 5
+    assert H.he_ct_level(gc) == ref.level == 9 - 5
+    assert_ct_equal(g.download(gc), ref)
