@@ -105,17 +105,17 @@ def test_autotuner_choice_keeps_bits():
         outs = {}
         for ks in (H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_SPLIT,
                    H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_LDG1, H.HE_KEY_STREAM_PK, H.HE_KEY_STREAM_PK3,
-                   H.HE_KEY_STREAM_PKP):
+                   H.HE_KEY_STREAM_PKP, H.HE_KEY_STREAM_SPLITM):
             H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, ks)
             assert H.he_ctx_get_option(ctx, H.HE_OPT_KEY_STREAM) == ks
             H.he_conv_run(ctx, conv, [x], [y], H.HE_FUSED)
             H.he_ctx_check(ctx)
             outs[ks] = H.he_ct_export_coeffs(ctx, y, 4096)
-        assert all(np.array_equal(outs[0], outs[k]) for k in (1, 2, 3, 4, 5, 6, 7, 8))
+        assert all(np.array_equal(outs[H.HE_KEY_STREAM_AUTO], v) for v in outs.values())
         log = H.he_ctx_tuning_log(ctx)
         assert "conv 4->4 16x16" in log and "->" in log
         with pytest.raises(H.HEError):
-            H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, 9)
+            H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, 99)
     finally:
         H.he_conv_destroy(conv)
         H.he_ct_free(x)
