@@ -196,6 +196,13 @@ struct modup_src {
 int k_prekey(const he_ctx *ctx, const u64 *key, const u64 *pt, int level, int pt_level, int beta, u64 *Kp, u64 *Ppt,
              cudaStream_t s);
 int k_modup_batch(const he_ctx *ctx, const modup_src *d_tab, int n_src, u64 *tmp, int level, cudaStream_t s);
+// ModUp of m sources at fixed strides (coefficient form x_coef + i xs, NTT form x_ntt + i ns,
+// digits D + i ds): one launch, no table
+int k_modup_strided(const he_ctx *ctx, const u64 *x_coef, size_t xs, const u64 *x_ntt, size_t ns, u64 *D, size_t ds,
+                    int m, int level, cudaStream_t s);
+// tensor products (d0, d1, d2) of m pairs at one level into d + i dstride
+int k_tensor_batch(const he_ctx *ctx, const he_ct *const *a, const he_ct *const *b, int m, u64 *d, size_t dstride,
+                   int level, cudaStream_t s);
 struct ip_item {            // one key-switching inner product
     const u64 *D;           // raised digits
     const u64 *key;         // key [dnum][2][L+1+K][n]

@@ -550,6 +550,14 @@ __global__ void __launch_bounds__(TB) modup_kernel(KP kp, ModupArgs A) {
     modup_digit(kp, A, A.x_coef, A.x_ntt, A.D, blockIdx.x * TB + threadIdx.x, blockIdx.y);
 }
 
+// several sources at fixed strides in one launch (blockIdx.z): no table, so it is safe to
+// capture in a graph
+__global__ void __launch_bounds__(TB) modup_strided_kernel(KP kp, ModupArgs A, size_t xs, size_t ns, size_t ds) {
+    pdl_wait();
+    const size_t z = blockIdx.z;
+    modup_digit(kp, A, A.x_coef + z * xs, A.x_ntt + z * ns, A.D + z * ds, blockIdx.x * TB + threadIdx.x, blockIdx.y);
+}
+
 // several sources in one launch (blockIdx.z): coefficient-form c1 at x_coef + z nq n
 __global__ void __launch_bounds__(TB) modup_batch_kernel(KP kp, ModupArgs A, const modup_src *tab) {
     pdl_wait();
@@ -1566,6 +1574,27 @@ __global__ void lincomb_kernel(KP kp, LincombArgs A, u64 *out, size_t out_ps) {
     out[c * out_ps + (size_t)i * kp.n + k] = r;
 }
 
+// tensor products of several pairs at one level (blockIdx.z), operands passed by value
+struct TensorInline {
+    const u64 *a[HE_INLINE_ITEMS], *b[HE_INLINE_ITEMS];
+    size_t pa[HE_INLINE_ITEMS], pb[HE_INLINE_ITEMS];
+};
+__global__ void tensor_batch_kernel(KP kp, TensorInline T, u64 *d, size_t dstride, int level) {
+    pdl_wait();
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int i = blockIdx.y, z = blockIdx.z;
+    const u64 q = kp.q[i], qi = kp.qinv[i], r2 = kp.r2[i];
+    const size_t off = (size_t)i * kp.n + k;
+    const size_t ps = (size_t)(level + 1) * kp.n;
+    const u64 *a = T.a[z], *b = T.b[z];
+    u64 *dz = d + z * dstride;
+    u64 a0 = a[off], a1 = a[T.pa[z] + off];
+    u64 b0 = to_mont(b[off], q, qi, r2), b1 = to_mont(b[T.pb[z] + off], q, qi, r2);
+    dz[off] = redc((u128)a0 * b0, q, qi);
+    dz[ps + off] = redc((u128)a0 * b1 + (u128)a1 * b0, q, qi);
+    dz[2 * ps + off] = redc((u128)a1 * b1, q, qi);
+}
+
 __global__ void tensor_kernel(KP kp, const u64 *a, size_t pa, const u64 *b, size_t pb, u64 *d,
                               int level) {
     pdl_wait();
@@ -1829,6 +1858,29 @@ int k_modup(const he_ctx *ctx, const u64 *x_coef, const u64 *x_ntt, u64 *D, int 
     return HE_OK;
 }
 
+int k_modup_strided(const he_ctx *ctx, const u64 *x_coef, size_t xs, const u64 *x_ntt, size_t ns, u64 *D, size_t ds,
+                    int m, int level, cudaStream_t s) {
+    if (m <= 0) return HE_OK;
+    ModupArgs A;
+    A.x_coef = x_coef;
+    A.x_ntt = x_ntt;
+    A.D = D;
+    A.level = level;
+    A.alpha = ctx->alpha;
+    const int beta = (level + ctx->alpha) / ctx->alpha;
+    if (beta > 16 || ctx->alpha > 16 || m > 65535) {
+        he_set_error("modup: at most 16 digits of at most 16 primes, 65535 sources");
+        return HE_EINVAL;
+    }
+    for (int j = 0; j < beta; j++) A.tab[j] = ctx->modup[level][j].d;
+    const double nq = level + 1, ext = nq + ctx->K;
+    TraceScope tr("modup", s, (double)m * (nq + beta * ext) * ctx->n * 8,
+                  (double)m * (nq + (double)beta * (ext - ctx->alpha) * ctx->alpha) * ctx->n);
+    pdl_launch(modup_strided_kernel, dim3(ctx->n / TB, beta, m), TB, 0, s, ctx->kp, A, xs, ns, ds);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
 static double ip_bytes(const he_ctx *ctx, int level, int items) {
     const double ext = level + 1 + ctx->K, beta = (level + ctx->alpha) / ctx->alpha;
     return (double)items * ext * ctx->n * 8 * (3 * beta + 2);
@@ -2014,6 +2066,24 @@ int k_mul_pointwise(const he_ctx *ctx, const u64 *a, const u64 *b, u64 *out, int
                     cudaStream_t s) {
     pdl_launch(mul_pointwise_kernel, dim3(ctx->n / TB, nlimbs), TB, 0, s, ctx->kp, a, b, out);
     LAUNCH_CHECK();
+    return HE_OK;
+}
+
+int k_tensor_batch(const he_ctx *ctx, const he_ct *const *a, const he_ct *const *b, int m, u64 *d, size_t dstride,
+                   int level, cudaStream_t s) {
+    for (int i0 = 0; i0 < m; i0 += HE_INLINE_ITEMS) {
+        const int cnt = std::min(HE_INLINE_ITEMS, m - i0);
+        TensorInline T;
+        for (int i = 0; i < cnt; i++) {
+            T.a[i] = a[i0 + i]->d;
+            T.b[i] = b[i0 + i]->d;
+            T.pa[i] = a[i0 + i]->pstride;
+            T.pb[i] = b[i0 + i]->pstride;
+        }
+        pdl_launch(tensor_batch_kernel, dim3(ctx->n / TB, level + 1, cnt), TB, 0, s, ctx->kp, T, d + (size_t)i0 * dstride,
+                   dstride, level);
+        LAUNCH_CHECK();
+    }
     return HE_OK;
 }
 

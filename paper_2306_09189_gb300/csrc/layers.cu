@@ -2898,15 +2898,11 @@ static int relin_batch(he_ctx *c, const std::vector<const he_ct *> &A, const std
     u64 *D = xc + (size_t)m * wq;                 // [m][beta][ext][n]
     u64 *u = D + (size_t)m * beta * we;           // [m][2][ext][n]
     u64 *conv = u + (size_t)m * 2 * we;           // [m][2][nq][n] (the fused ModDown-rescale's w)
-    for (int i = 0; i < m; i++) {
-        he_ct ta = *A[i], tb = *B[i];
-        HE_TRY(k_tensor(c, &ta, &tb, d + (size_t)i * 3 * wq, s));
-    }
+    HE_TRY(k_tensor_batch(c, A.data(), B.data(), m, d, 3 * wq, l, s));
     HE_TRY(k_copy_limbs(xc, wq, d + 2 * wq, 3 * wq, wq, m, s));
     ntt_job ji{xc, wq, 0, nq, nq, 0, m, 0};
     HE_TRY(k_ntt(c, ji, true, s));
-    for (int i = 0; i < m; i++)
-        HE_TRY(k_modup(c, xc + i * wq, d + (size_t)i * 3 * wq + 2 * wq, D + (size_t)i * beta * we, l, s));
+    HE_TRY(k_modup_strided(c, xc, wq, d + 2 * wq, 3 * wq, D, (size_t)beta * we, m, l, s));
     ntt_job jd{D, we, 0, ext, nq, c->alpha, beta * m, beta};
     HE_TRY(k_ntt(c, jd, false, s));
     std::vector<ip_item> ip(m);
@@ -3183,16 +3179,38 @@ struct PsScale {
 };
 
 static int ps_run(he_ctx *c, std::vector<PsOp> &ops, cudaStream_t s) {
-    auto hit = [](const std::vector<const he_ct *> &a, const std::vector<const he_ct *> &b) {
-        for (const he_ct *x : a)
-            for (const he_ct *y : b)
-                if (x == y) return true;
-        return false;
-    };
+    // dependencies from program order: an operation waits for the last writer of what it reads or
+    // writes and, for what it writes, for the readers since that write.  Each of those waited in
+    // turn for the writers and readers before it, so every earlier conflicting operation is done
+    // once these are.
+    std::vector<std::vector<size_t>> deps(ops.size());
+    {
+        std::map<const he_ct *, size_t> last_w;
+        std::map<const he_ct *, std::vector<size_t>> readers;
+        for (size_t i = 0; i < ops.size(); i++) {
+            auto &d = deps[i];
+            for (const he_ct *x : ops[i].rd) {
+                auto w = last_w.find(x);
+                if (w != last_w.end()) d.push_back(w->second);
+            }
+            for (const he_ct *x : ops[i].wr) {
+                auto w = last_w.find(x);
+                if (w != last_w.end()) d.push_back(w->second);
+                auto r = readers.find(x);
+                if (r != readers.end())
+                    for (size_t j : r->second)
+                        if (j != i) d.push_back(j);
+            }
+            for (const he_ct *x : ops[i].rd) readers[x].push_back(i);
+            for (const he_ct *x : ops[i].wr) {
+                last_w[x] = i;
+                readers[x].clear();
+            }
+        }
+    }
     auto ready = [&](size_t i) {
-        for (size_t j = 0; j < i; j++)
-            if (!ops[j].done && (hit(ops[j].wr, ops[i].rd) || hit(ops[j].wr, ops[i].wr) || hit(ops[j].rd, ops[i].wr)))
-                return false;
+        for (size_t j : deps[i])
+            if (!ops[j].done) return false;
         return true;
     };
     size_t left = ops.size();
