@@ -68,3 +68,14 @@ def test_bad_parameters_are_rejected_on_host():
         H.he_params_primes(params_of(Params(12, 4, 1, 1, 70, 40, 50, 1.0, 0)))  # 70-bit prime
     with pytest.raises(H.HEError):
         H.he_layout_image(3, 30, 500)                                           # N not 2^k
+
+
+def test_header_constants_match_the_binding():
+    # every integer constant the header defines (error codes, modes, options, key-stream forms,
+    # activation ids) exists in the Python binding with the same value
+    from paper_2306_09189_gb300 import hegpu as H
+    src = open(os.path.join(ROOT, "include", "hegpu.h")).read()
+    defs = dict(re.findall(r"^#define\s+(HE_[A-Z0-9_]+)\s+(-?\d+)\b", src, flags=re.M))
+    assert len(defs) >= 15 and "HE_KEY_STREAM_SPLITM" in defs
+    for name, value in defs.items():
+        assert getattr(H, name) == int(value), name
