@@ -512,7 +512,10 @@ struct ModupArgs {
     int level, alpha;
     const u64 *tab[16];
 };
-// digit j of one source: x_coef = c1 in coefficient form, x_ntt = c1 in NTT form, D its digits
+// digit j of one source: x_coef = c1 in coefficient form, x_ntt = c1 in NTT form, D its digits.
+// CAP >= the digit's prime count ns (alpha, or fewer for the last digit): the launchers pick
+// CAP = alpha for alpha <= 8, so the loops unroll to the digit size instead of a fixed 16.
+template <int CAP>
 __device__ __forceinline__ void modup_digit(const KP &kp, const ModupArgs &A, const u64 *x_coef, const u64 *x_ntt,
                                             u64 *D, int k, int j) {
     const int nq = A.level + 1;
@@ -521,9 +524,9 @@ __device__ __forceinline__ void modup_digit(const KP &kp, const ModupArgs &A, co
     const int ns = min(A.alpha, nq - lo);
     const u64 *tab = A.tab[j];
     u64 *Dj = D + (size_t)j * ext * kp.n;
-    u64 y[16];
+    u64 y[CAP];
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
+    for (int i = 0; i < CAP; i++) {
         if (i < ns) {
             const int pr = lo + i;
             u64 xv = x_coef[(size_t)pr * kp.n + k];
@@ -539,32 +542,50 @@ __device__ __forceinline__ void modup_digit(const KP &kp, const ModupArgs &A, co
         const u64 *h = hat + (size_t)d * ns;
         u128 acc = 0;
 #pragma unroll
-        for (int i = 0; i < 16; i++)
+        for (int i = 0; i < CAP; i++)
             if (i < ns) acc += (u128)y[i] * h[i];
         Dj[(size_t)limb * kp.n + k] = redc(acc, kp.q[pr], kp.qinv[pr]);
     }
 }
 
+template <int CAP>
 __global__ void __launch_bounds__(TB) modup_kernel(KP kp, ModupArgs A) {
     pdl_wait();
-    modup_digit(kp, A, A.x_coef, A.x_ntt, A.D, blockIdx.x * TB + threadIdx.x, blockIdx.y);
-}
-
-// several sources at fixed strides in one launch (blockIdx.z): no table, so it is safe to
-// capture in a graph
-__global__ void __launch_bounds__(TB) modup_strided_kernel(KP kp, ModupArgs A, size_t xs, size_t ns, size_t ds) {
-    pdl_wait();
-    const size_t z = blockIdx.z;
-    modup_digit(kp, A, A.x_coef + z * xs, A.x_ntt + z * ns, A.D + z * ds, blockIdx.x * TB + threadIdx.x, blockIdx.y);
+    modup_digit<CAP>(kp, A, A.x_coef, A.x_ntt, A.D, blockIdx.x * TB + threadIdx.x, blockIdx.y);
 }
 
 // several sources in one launch (blockIdx.z): coefficient-form c1 at x_coef + z nq n
+template <int CAP>
 __global__ void __launch_bounds__(TB) modup_batch_kernel(KP kp, ModupArgs A, const modup_src *tab) {
     pdl_wait();
     const int z = blockIdx.z;
     const size_t nqn = (size_t)(A.level + 1) * kp.n;
-    modup_digit(kp, A, A.x_coef + z * nqn, tab[z].c1, tab[z].D, blockIdx.x * TB + threadIdx.x, blockIdx.y);
+    modup_digit<CAP>(kp, A, A.x_coef + z * nqn, tab[z].c1, tab[z].D, blockIdx.x * TB + threadIdx.x, blockIdx.y);
 }
+
+// several sources at fixed strides in one launch (blockIdx.z): no table, so it is safe to
+// capture in a graph
+template <int CAP>
+__global__ void __launch_bounds__(TB) modup_strided_kernel(KP kp, ModupArgs A, size_t xs, size_t ns, size_t ds) {
+    pdl_wait();
+    const size_t z = blockIdx.z;
+    modup_digit<CAP>(kp, A, A.x_coef + z * xs, A.x_ntt + z * ns, A.D + z * ds, blockIdx.x * TB + threadIdx.x,
+                     blockIdx.y);
+}
+
+// instantiation for a prime count n <= 16: exact for n <= 8, else 16
+#define CAP_SWITCH(n, GO)                                                                         \
+    switch (n) {                                                                                  \
+        case 1: GO(1); break;                                                                     \
+        case 2: GO(2); break;                                                                     \
+        case 3: GO(3); break;                                                                     \
+        case 4: GO(4); break;                                                                     \
+        case 5: GO(5); break;                                                                     \
+        case 6: GO(6); break;                                                                     \
+        case 7: GO(7); break;                                                                     \
+        case 8: GO(8); break;                                                                     \
+        default: GO(16);                                                                          \
+    }
 
 // c1 (NTT form) of every source into one contiguous [n_src][words] buffer
 __global__ void gather_c1_kernel(const modup_src *tab, u64 *dst, size_t words) {
@@ -607,19 +628,14 @@ __global__ void __launch_bounds__(TB) ip_kernel(KP kp, const ip_item *items, IpI
 // ------------------------------------------------------------------------------ ModDown
 // conv[c][i][k] = sum_k' y~_k' (P/p_k') mod q_i with y_k' = [u_P,k' (P/p_k')^-1]_{p_k'} taken
 // centred (y - p when 2y > p), so (u - conv) / P rounds instead of flooring.
-__global__ void __launch_bounds__(TB) moddown_fbc_kernel(KP kp, const u64 *u, u64 *conv,
-                                                         int level, const u64 *tab) {
-    pdl_wait();
-    const int k = blockIdx.x * TB + threadIdx.x;
-    const int c = blockIdx.y;
-    const int nq = level + 1;
-    const int ext = nq + kp.K;
+// centred y_k' of the K special primes for one coefficient; CAP >= K (the launchers pick
+// CAP = K for K <= 8)
+template <int CAP>
+__device__ __forceinline__ void fbc_centred(const KP &kp, const u64 *uc, int nq, int k, const u64 *tab, u64 (&v)[CAP],
+                                            bool (&neg)[CAP]) {
     const int K = kp.K;
-    const u64 *uc = u + (size_t)c * ext * kp.n;
-    u64 v[16];
-    bool neg[16];
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
+    for (int i = 0; i < CAP; i++) {
         if (i < K) {
             const int pr = kp.L + 1 + i;
             const u64 p = kp.q[pr];
@@ -628,15 +644,33 @@ __global__ void __launch_bounds__(TB) moddown_fbc_kernel(KP kp, const u64 *u, u6
             v[i] = neg[i] ? p - y : y;
         }
     }
+}
+template <int CAP>
+__device__ __forceinline__ u64 fbc_sum(const KP &kp, int t, const u64 (&v)[CAP], const bool (&neg)[CAP],
+                                       const u64 *hat, const u64 *nhat) {
+    const int K = kp.K;
+    u128 acc = 0;
+#pragma unroll
+    for (int i = 0; i < CAP; i++)
+        if (i < K) acc += (u128)v[i] * (neg[i] ? nhat[t * K + i] : hat[t * K + i]);
+    return redc(acc, kp.q[t], kp.qinv[t]);
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(TB) moddown_fbc_kernel(KP kp, const u64 *u, u64 *conv, int level, const u64 *tab) {
+    pdl_wait();
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int c = blockIdx.y;
+    const int nq = level + 1;
+    const int ext = nq + kp.K;
+    const int K = kp.K;
+    const u64 *uc = u + (size_t)c * ext * kp.n;
+    u64 v[CAP];
+    bool neg[CAP];
+    fbc_centred<CAP>(kp, uc, nq, k, tab, v, neg);
     const u64 *hat = tab + 2 * K;
     const u64 *nhat = hat + (size_t)nq * K;
-    for (int t = 0; t < nq; t++) {
-        u128 acc = 0;
-#pragma unroll
-        for (int i = 0; i < 16; i++)
-            if (i < K) acc += (u128)v[i] * (neg[i] ? nhat[t * K + i] : hat[t * K + i]);
-        conv[((size_t)c * nq + t) * kp.n + k] = redc(acc, kp.q[t], kp.qinv[t]);
-    }
+    for (int t = 0; t < nq; t++) conv[((size_t)c * nq + t) * kp.n + k] = fbc_sum<CAP>(kp, t, v, neg, hat, nhat);
 }
 
 // out_c[i][k] = base_c[i][phi_g(k)] + (u_c[i][k] - conv_c[i][k]) * P^-1
@@ -683,6 +717,7 @@ __global__ void fold_top_kernel(KP kp, u64 *u, size_t u_is, size_t u_ps, const u
 }
 
 // per poly (blockIdx.y): u = [ext][n] with limbs l..l+K in coefficient form; w = [l][n]
+template <int CAP>
 __global__ void __launch_bounds__(TB) moddown_rescale_fbc_kernel(KP kp, const u64 *u, u64 *w, int level,
                                                                  const u64 *tab, const u64 *pinv, const u64 *pinvs) {
     pdl_wait();
@@ -692,30 +727,15 @@ __global__ void __launch_bounds__(TB) moddown_rescale_fbc_kernel(KP kp, const u6
     const int ext = nq + kp.K;
     const int K = kp.K;
     const u64 *uc = u + (size_t)c * ext * kp.n;
-    u64 v[16];
-    bool neg[16];
-#pragma unroll
-    for (int i = 0; i < 16; i++) {
-        if (i < K) {
-            const int pr = kp.L + 1 + i;
-            const u64 p = kp.q[pr];
-            u64 y = mul_shoup(uc[(size_t)(nq + i) * kp.n + k], tab[i], tab[K + i], p);
-            neg[i] = 2 * y > p;
-            v[i] = neg[i] ? p - y : y;
-        }
-    }
+    u64 v[CAP];
+    bool neg[CAP];
+    fbc_centred<CAP>(kp, uc, nq, k, tab, v, neg);
     const u64 *hat = tab + 2 * K;
     const u64 *nhat = hat + (size_t)nq * K;
-    auto fbc = [&](int t) {
-        u128 acc = 0;
-#pragma unroll
-        for (int i = 0; i < 16; i++)
-            if (i < K) acc += (u128)v[i] * (neg[i] ? nhat[t * K + i] : hat[t * K + i]);
-        return redc(acc, kp.q[t], kp.qinv[t]);
-    };
     // y_l in coefficient form, then its centred representative reduced mod every lower prime
     const u64 ql = kp.q[level];
-    const u64 yl = mul_shoup(sub_mod(uc[(size_t)level * kp.n + k], fbc(level), ql), pinv[level], pinvs[level], ql);
+    const u64 yl = mul_shoup(sub_mod(uc[(size_t)level * kp.n + k], fbc_sum<CAP>(kp, level, v, neg, hat, nhat), ql),
+                             pinv[level], pinvs[level], ql);
     const bool yneg = 2 * yl > ql;
     for (int t = 0; t < level; t++) {
         const u64 q = kp.q[t];
@@ -726,7 +746,8 @@ __global__ void __launch_bounds__(TB) moddown_rescale_fbc_kernel(KP kp, const u6
         } else {
             r = reduce64(yl, q, kp.mu[t]);
         }
-        w[((size_t)c * level + t) * kp.n + k] = add_mod(mul_shoup(fbc(t), pinv[t], pinvs[t], q), r, q);
+        w[((size_t)c * level + t) * kp.n + k] =
+            add_mod(mul_shoup(fbc_sum<CAP>(kp, t, v, neg, hat, nhat), pinv[t], pinvs[t], q), r, q);
     }
 }
 
@@ -1831,7 +1852,9 @@ int k_modup_batch(const he_ctx *ctx, const modup_src *d_tab, int n_src, u64 *tmp
     {
         TraceScope tr("modup", s, (double)n_src * (nq + beta * ext) * ctx->n * 8,
                       (double)n_src * (nq + (double)beta * (ext - ctx->alpha) * ctx->alpha) * ctx->n);
-        pdl_launch(modup_batch_kernel, dim3(ctx->n / TB, beta, n_src), TB, 0, s, ctx->kp, A, d_tab);
+#define GO(C) pdl_launch(modup_batch_kernel<C>, dim3(ctx->n / TB, beta, n_src), TB, 0, s, ctx->kp, A, d_tab)
+        CAP_SWITCH(ctx->alpha, GO)
+#undef GO
         LAUNCH_CHECK();
     }
     return HE_OK;
@@ -1853,7 +1876,9 @@ int k_modup(const he_ctx *ctx, const u64 *x_coef, const u64 *x_ntt, u64 *D, int 
     for (int j = 0; j < beta; j++) A.tab[j] = ctx->modup[level][j].d;
     const double nq = level + 1, ext = nq + ctx->K;
     TraceScope tr("modup", s, (nq + beta * ext) * ctx->n * 8, (nq + (double)beta * (ext - ctx->alpha) * ctx->alpha) * ctx->n);
-    pdl_launch(modup_kernel, dim3(ctx->n / TB, beta), TB, 0, s, ctx->kp, A);
+#define GO(C) pdl_launch(modup_kernel<C>, dim3(ctx->n / TB, beta), TB, 0, s, ctx->kp, A)
+    CAP_SWITCH(ctx->alpha, GO)
+#undef GO
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1876,7 +1901,9 @@ int k_modup_strided(const he_ctx *ctx, const u64 *x_coef, size_t xs, const u64 *
     const double nq = level + 1, ext = nq + ctx->K;
     TraceScope tr("modup", s, (double)m * (nq + beta * ext) * ctx->n * 8,
                   (double)m * (nq + (double)beta * (ext - ctx->alpha) * ctx->alpha) * ctx->n);
-    pdl_launch(modup_strided_kernel, dim3(ctx->n / TB, beta, m), TB, 0, s, ctx->kp, A, xs, ns, ds);
+#define GO(C) pdl_launch(modup_strided_kernel<C>, dim3(ctx->n / TB, beta, m), TB, 0, s, ctx->kp, A, xs, ns, ds)
+    CAP_SWITCH(ctx->alpha, GO)
+#undef GO
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1923,8 +1950,10 @@ int k_moddown_fbc(const he_ctx *ctx, const u64 *u, u64 *conv, int level, int npo
     }
     const double nq = level + 1;
     TraceScope tr("moddown_fbc", s, (double)npoly * (ctx->K + nq) * ctx->n * 8, (double)npoly * (ctx->K + nq * ctx->K) * ctx->n);
-    pdl_launch(moddown_fbc_kernel, dim3(ctx->n / TB, npoly), TB, 0, s, ctx->kp, u, conv, level,
-                                                              ctx->moddown[level].d);
+#define GO(C) pdl_launch(moddown_fbc_kernel<C>, dim3(ctx->n / TB, npoly), TB, 0, s, ctx->kp, u, conv, level, \
+                         ctx->moddown[level].d)
+    CAP_SWITCH(ctx->K, GO)
+#undef GO
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1979,8 +2008,10 @@ int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, s
     {
         TraceScope tr("moddown_fbc", s, (double)2 * m * (ctx->K + 1 + level) * ctx->n * 8,
                       (double)2 * m * (ctx->K + nq * ctx->K + level) * ctx->n);
-        pdl_launch(moddown_rescale_fbc_kernel, dim3(ctx->n / TB, 2 * m), TB, 0, s, ctx->kp, u, w, level,
-                                                                          ctx->moddown[level].d, pinv, pinvs);
+#define GO(C) pdl_launch(moddown_rescale_fbc_kernel<C>, dim3(ctx->n / TB, 2 * m), TB, 0, s, ctx->kp, u, w, level, \
+                         ctx->moddown[level].d, pinv, pinvs)
+        CAP_SWITCH(ctx->K, GO)
+#undef GO
         LAUNCH_CHECK();
     }
     ntt_job jw{w, (size_t)level * ctx->n, 0, level, nq, 0, 2 * m, 0};
