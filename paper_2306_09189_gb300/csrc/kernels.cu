@@ -603,6 +603,8 @@ struct MdInline {
     md_item it[HE_INLINE_ITEMS];
 };
 
+// CAP >= beta (the launchers pick CAP = beta for beta <= 8): every digit's loads issue together
+template <int CAP>
 __global__ void __launch_bounds__(TB) ip_kernel(KP kp, const ip_item *items, IpInline inl, int level) {
     pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
@@ -615,12 +617,14 @@ __global__ void __launch_bounds__(TB) ip_kernel(KP kp, const ip_item *items, IpI
     const int ks = it.g == 1 ? k : autom_index(k, it.g, kp.logn);
     const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
     u128 a0 = 0, a1 = 0;
-    for (int j = 0; j < it.beta; j++) {
-        u64 d = it.D[((size_t)j * ext + t) * kp.n + ks];
-        const u64 *key = it.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
-        a0 += (u128)d * key[0];
-        a1 += (u128)d * key[kstride];
-    }
+#pragma unroll
+    for (int j = 0; j < CAP; j++)
+        if (j < it.beta) {
+            u64 d = it.D[((size_t)j * ext + t) * kp.n + ks];
+            const u64 *key = it.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+            a0 += (u128)d * key[0];
+            a1 += (u128)d * key[kstride];
+        }
     it.u[(size_t)t * kp.n + k] = redc(a0, q, qi);
     it.u[((size_t)ext + t) * kp.n + k] = redc(a1, q, qi);
 }
@@ -1920,8 +1924,11 @@ static double ip_mulmods(const he_ctx *ctx, int level, int items) {
 int k_inner_product(const he_ctx *ctx, const ip_item *items_dev, int n_items, int level,
                     cudaStream_t s) {
     TraceScope tr("ip", s, ip_bytes(ctx, level, n_items), ip_mulmods(ctx, level, n_items));
-    pdl_launch(ip_kernel, dim3(ctx->n / TB, level + 1 + ctx->K, n_items), TB, 0, s, ctx->kp, items_dev, IpInline{},
-                                                                             level);
+    const int beta = (level + ctx->alpha) / ctx->alpha;
+#define GO(C) pdl_launch(ip_kernel<C>, dim3(ctx->n / TB, level + 1 + ctx->K, n_items), TB, 0, s, ctx->kp, items_dev, \
+                         IpInline{}, level)
+    CAP_SWITCH(beta, GO)
+#undef GO
     LAUNCH_CHECK();
     return HE_OK;
 }
@@ -1932,7 +1939,11 @@ int k_inner_product_inline(const he_ctx *ctx, const ip_item *items, int n, int l
         IpInline inl;
         for (int i = 0; i < cnt; i++) inl.it[i] = items[i0 + i];
         TraceScope tr("ip", s, ip_bytes(ctx, level, cnt), ip_mulmods(ctx, level, cnt));
-        pdl_launch(ip_kernel, dim3(ctx->n / TB, level + 1 + ctx->K, cnt), TB, 0, s, ctx->kp, nullptr, inl, level);
+        int beta = 0;
+        for (int i = 0; i < cnt; i++) beta = std::max(beta, inl.it[i].beta);
+#define GO(C) pdl_launch(ip_kernel<C>, dim3(ctx->n / TB, level + 1 + ctx->K, cnt), TB, 0, s, ctx->kp, nullptr, inl, level)
+        CAP_SWITCH(beta, GO)
+#undef GO
         LAUNCH_CHECK();
     }
     return HE_OK;
