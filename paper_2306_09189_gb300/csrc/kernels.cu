@@ -1575,7 +1575,8 @@ __global__ void prekey_kernel(KP kp, const u64 *key, const u64 *pt, int level, i
 // ==== fused key-switch + MAC kernels: end
 
 // acc = sum_terms K_term * x_term (+ c on poly 0) over limbs 0..level, x of any higher level
-// (the drop is implicit); per-limb residues of the integer constants are passed by value.
+// (the drop is implicit); per-limb residues of the integer constants are passed by value, already
+// in Montgomery form, so one REDC of the 128-bit sum finishes it.
 struct LincombArgs {
     const u64 *x[HE_LC_MAX];
     size_t ps[HE_LC_MAX];
@@ -1588,11 +1589,11 @@ __global__ void lincomb_kernel(KP kp, LincombArgs A, u64 *out, size_t out_ps) {
     const int k = blockIdx.x * TB + threadIdx.x;
     const int i = blockIdx.y;
     const int c = blockIdx.z;
-    const u64 q = kp.q[i], qi = kp.qinv[i], r2 = kp.r2[i];
+    const u64 q = kp.q[i], qi = kp.qinv[i];
     u128 acc = 0;
     for (int t = 0; t < A.n_terms; t++) {
         const u64 x = A.x[t][c * A.ps[t] + (size_t)i * kp.n + k];
-        acc += (u128)x * to_mont(A.res[t][i], q, qi, r2);
+        acc += (u128)x * A.res[t][i];
     }
     u64 r = redc(acc, q, qi);
     if (c == 0) r = add_mod(r, A.cst[i], q);
@@ -2637,7 +2638,10 @@ int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u6
     for (int t = 0; t < n; t++) {
         A.x[t] = x[t];
         A.ps[t] = ps[t];
-        for (int i = 0; i <= level; i++) A.res[t][i] = res[t * HE_LC_LIMBS + i];
+        for (int i = 0; i <= level; i++) {                   // Montgomery form, once on the host
+            const u64 q = ctx->primes[i];
+            A.res[t][i] = (u64)((((u128)(res[t * HE_LC_LIMBS + i] % q)) << 64) % q);
+        }
     }
     for (int i = 0; i <= level; i++) A.cst[i] = cst[i];
     A.n_terms = n;
