@@ -254,3 +254,46 @@ def test_small_ring_rotation_and_relin_bit_exact(log_n):
         assert_ct_equal(g.download(m), o.mul_relin(ct, ct2))
     finally:
         g.close()
+
+
+def test_wide_digits_and_many_special_primes_bit_exact():
+    """alpha = 12 and K = 10 (the serving parameters have alpha = K = 11): the base conversions
+    and the inner product run their general instantiations, bit for bit against the oracle."""
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import GpuCtx, assert_ct_equal
+    from oracle import layers as Ly
+    pr = Params(log_n=12, n_q=12, n_p=10, dnum=1, q0_bits=50, q_bits=40, p_bits=50,
+                scale=2.0 ** 40, seed=13)
+    o = Context(pr)
+    g = GpuCtx(pr)
+    try:
+        assert o.alpha == 12 and len(o.p) == 10
+        level = 11
+        ct, z = _rand_ct(o, level, 500)
+        ct2, _ = _rand_ct(o, level, 501)
+        rots = [3, -40]
+        for r in rots:
+            o.gen_rotation_key(r)
+        o.gen_relin_key()
+        H.he_keygen_rotations(g.h, rots)
+        H.he_keygen_relin(g.h)
+        out = g.ct(level)
+        H.he_rotate(g.h, g.upload(ct), rots[0], out)
+        assert_ct_equal(g.download(out), o.rotate(ct, rots[0]))
+        outs = [g.ct(level) for _ in rots]
+        H.he_rotate_hoisted(g.h, g.upload(ct), rots, outs)
+        D = o.hoist(ct)
+        for r, c in zip(rots, outs):
+            assert_ct_equal(g.download(c), o.rotate_hoisted(ct, D, r))
+        m = g.ct(level)
+        H.he_mul_relin(g.h, g.upload(ct), g.upload(ct2), m)
+        assert_ct_equal(g.download(m), o.mul_relin(ct, ct2))
+        c = Ly.cheb_nodes_coeffs(Ly.gelu, 8, -8, 8)
+        ref = Ly.cheb_ps_he(o, ct, c, target_scale=o.pr.scale)
+        gc = g.upload(ct)
+        H.he_poly_eval_ps(g.h, gc, c, o.pr.scale)
+        H.he_ctx_check(g.h)
+        assert H.he_ct_level(gc) == ref.level
+        assert_ct_equal(g.download(gc), ref)
+    finally:
+        g.close()
