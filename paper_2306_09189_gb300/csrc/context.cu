@@ -1151,11 +1151,9 @@ extern "C" int he_rescale(he_ctx *c, he_ct *ct, void *stream) {
     const int l = ct->level;
     if (l < 1) { he_set_error("he_rescale: no level left"); return HE_ELEVEL; }
     cudaStream_t s = (cudaStream_t)stream;
-    HE_TRY(ntt_poly(c, ct->d, ct->pstride, l, 1, l + 1, 2, true, s));    // top limb -> coeff
-    u64 *t = c->sc_tmp.p;
-    HE_TRY(k_rescale_prep(c, ct->d + (size_t)l * c->n, ct->pstride, t, l, s));
-    HE_TRY(ntt_poly(c, t, (size_t)l * c->n, 0, l, l, 2, false, s));
-    HE_TRY(k_rescale_combine(c, ct, t, s));
+    // top limb to coefficient form, its centred residues mod q_0..q_{l-1} to NTT form, then
+    // c_i = (c_i - t_i) q_l^-1 (both polynomials, pstride apart)
+    HE_TRY(k_rescale_many(c, ct->d, ct->pstride, 1, l, c->sc_tmp.p, s));
     ct->level = l - 1;
     ct->scale = ct->scale / (double)c->primes[l];
     return HE_OK;

@@ -223,8 +223,26 @@ __device__ __forceinline__ void reg_pass(u64 (&x)[16], int base, int ls, int log
     }
 }
 
-template <bool INV>
-__global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job) {
+// A rescale fused into the forward NTT of its correction term t: RS in the column pass loads
+// t[i] = [centred c_l]_{q_i} straight from the coefficient-form top limb of poly p (at
+// c + p ps + level n); RS in the row pass stores c_i = (c_i - NTT(t)_i) q_l^-1 into the
+// ciphertext instead of NTT(t).  Same words as rescale_prep / rescale_combine around the NTT.
+struct RescaleFuse {
+    u64 *c;
+    size_t ps;
+    int level;
+    const u64 *inv, *invs;
+};
+__device__ __forceinline__ u64 centred_mod(u64 v, u64 ql, u64 q, u64 mu) {
+    if (2 * v > ql) {
+        const u64 m = reduce64(ql - v, q, mu);
+        return m == 0 ? 0 : q - m;
+    }
+    return reduce64(v, q, mu);
+}
+
+template <bool INV, bool RS = false>
+__global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job, RescaleFuse F) {
     pdl_wait();
     __shared__ u64 sm[4096];
     const int p = blockIdx.z;
@@ -242,8 +260,15 @@ __global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job) {
     const int n2 = lr - 4;                           // pass-2 stages
     u64 x[16];
     if (!INV) {
+        if (RS) {
+            const u64 *top = F.c + (size_t)p * F.ps + (size_t)F.level * kp.n;
+            const u64 ql = kp.q[F.level], mu = kp.mu[pr];
 #pragma unroll
-        for (int j = 0; j < 16; j++) x[j] = a[(size_t)(r + R16 * j) * ROW + c];
+            for (int j = 0; j < 16; j++) x[j] = centred_mod(top[(size_t)(r + R16 * j) * ROW + c], ql, q, mu);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++) x[j] = a[(size_t)(r + R16 * j) * ROW + c];
+        }
         reg_pass<false>(x, r * ROW + c, lr + 4, kp.logn, 4, W, q, q2);
 #pragma unroll
         for (int j = 0; j < 16; j++) sm[(r + R16 * j) * TC + tc] = x[j];
@@ -274,8 +299,8 @@ __global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job) {
 
 __device__ __forceinline__ int pad17(int k) { return k + (k >> 4); }
 
-template <bool INV>
-__global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job) {
+template <bool INV, bool RS = false>
+__global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job, RescaleFuse F) {
     pdl_wait();
     __shared__ u64 sm[16][272];
     const int p = blockIdx.z;
@@ -305,8 +330,18 @@ __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job) {
             s[pad17(16 * l + e)] = v >= q ? v - q : v;
         }
         __syncthreads();
+        if (RS) {
+            u64 *cr = F.c + (size_t)p * F.ps + (size_t)limb * kp.n + (size_t)row * ROW;
+            const u64 iv = F.inv[pr], ivs = F.invs[pr];
 #pragma unroll
-        for (int j = 0; j < 16; j++) a[l + 16 * j] = s[pad17(l + 16 * j)];
+            for (int j = 0; j < 16; j++) {
+                u64 *xp = cr + l + 16 * j;
+                *xp = mul_shoup(sub_mod(*xp, s[pad17(l + 16 * j)], q), iv, ivs, q);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++) a[l + 16 * j] = s[pad17(l + 16 * j)];
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < 16; j++) s[pad17(l + 16 * j)] = a[l + 16 * j];
@@ -1696,14 +1731,14 @@ int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
         const int TC = 4096 / R;
         dim3 gA(ROW / TC, job.nl, job.npoly), gB(R / 16, job.nl, job.npoly);
         if (!inverse) {
-            pdl_launch(ntt16_cols<false>, gA, 256, 0, s, ctx->kp, job);
+            pdl_launch(ntt16_cols<false>, gA, 256, 0, s, ctx->kp, job, RescaleFuse{});
             LAUNCH_CHECK();
-            pdl_launch(ntt16_rows<false>, gB, 256, 0, s, ctx->kp, job);
+            pdl_launch(ntt16_rows<false>, gB, 256, 0, s, ctx->kp, job, RescaleFuse{});
             LAUNCH_CHECK();
         } else {
-            pdl_launch(ntt16_rows<true>, gB, 256, 0, s, ctx->kp, job);
+            pdl_launch(ntt16_rows<true>, gB, 256, 0, s, ctx->kp, job, RescaleFuse{});
             LAUNCH_CHECK();
-            pdl_launch(ntt16_cols<true>, gA, 256, 0, s, ctx->kp, job);
+            pdl_launch(ntt16_cols<true>, gA, 256, 0, s, ctx->kp, job, RescaleFuse{});
             LAUNCH_CHECK();
         }
         return HE_OK;
@@ -2654,6 +2689,21 @@ int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u6
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s) {
     ntt_job top{base, ps, level, 1, level + 1, 0, 2 * m, 0};
     HE_TRY(k_ntt(ctx, top, true, s));
+    if (ctx->logn >= 12 && ctx->logn <= 16) {
+        // the correction term's reduction and the final combine ride in the NTT's two passes
+        const u64 *cb = ctx->d_consts + ctx->np + 2 * (ctx->L + 1);
+        const u64 *inv = cb + (size_t)level * 2 * (ctx->L + 1);
+        RescaleFuse F{base, ps, level, inv, inv + (ctx->L + 1)};
+        ntt_job tj{t, (size_t)level * ctx->n, 0, level, level, 0, 2 * m, 0};
+        const int R = ctx->n / ROW, TC = 4096 / R;
+        dim3 gA(ROW / TC, level, 2 * m), gB(R / 16, level, 2 * m);
+        TraceScope tr("rescale", s, (double)m * level * ctx->n * 8 * 6, (double)m * level * ctx->n * 2);
+        pdl_launch(ntt16_cols<false, true>, gA, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+        pdl_launch(ntt16_rows<false, true>, gB, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+        return HE_OK;
+    }
     pdl_launch(rescale_prep_kernel, dim3(ctx->n / TB, level, 2 * m), TB, 0, s, ctx->kp, base + (size_t)level * ctx->n, ps, t, level);
     LAUNCH_CHECK();
     ntt_job tj{t, (size_t)level * ctx->n, 0, level, level, 0, 2 * m, 0};

@@ -60,14 +60,9 @@ extern "C" int he_rescale_noalloc(he_ctx *c, he_ct *ct, void *stream) {
     HE_TRY(scratch_address(&t));
     cudaStream_t s = (cudaStream_t)stream;
     // same steps as he_rescale: top limb to coefficient form, centred residues of it modulo
-    // every remaining prime (every scratch word is written here, nothing needs zeroing),
-    // back to NTT form, then (c_i - t_i) * q_l^{-1}
-    ntt_job top{ct->d, ct->pstride, l, 1, l + 1, 0, 2};
-    HE_TRY(k_ntt(c, top, true, s));
-    HE_TRY(k_rescale_prep(c, ct->d + (size_t)l * c->n, ct->pstride, t, l, s));
-    ntt_job tj{t, (size_t)l * c->n, 0, l, l, 0, 2};
-    HE_TRY(k_ntt(c, tj, false, s));
-    HE_TRY(k_rescale_combine(c, ct, t, s));
+    // every remaining prime (every scratch word is written before it is read, nothing needs
+    // zeroing), back to NTT form, then (c_i - t_i) * q_l^{-1}
+    HE_TRY(k_rescale_many(c, ct->d, ct->pstride, 1, l, t, s));
     ct->level = l - 1;
     ct->scale = ct->scale / (double)c->primes[l];
     return HE_OK;
