@@ -230,9 +230,6 @@ int k_moddown_combine(const he_ctx *ctx, const md_item *items_dev, int n_items, 
 int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, size_t b_ps, u64 *w,
                       u64 *const *out, const size_t *out_ps, int m, int level, cudaStream_t s);
 int k_range_check(const he_ctx *ctx, const u64 *d, size_t ps, int level, unsigned long long *bad, cudaStream_t s);
-int k_rescale_prep(const he_ctx *ctx, const u64 *top_coef, size_t top_pstride, u64 *t, int level,
-                   cudaStream_t s);
-int k_rescale_combine(const he_ctx *ctx, he_ct *ct, const u64 *t, cudaStream_t s);
 struct mac_term {
     const u64 *pt;          // [level+1][n] Montgomery
     const u64 *ct;          // ct data
@@ -342,6 +339,8 @@ int k_selftest_bounded_wait(const he_ctx *ctx, cudaStream_t s);
 #define HE_LC_LIMBS 24      // limbs of one k_lincomb launch (residue table row length)
 int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u64 *res, int n,
               const u64 *cst, int level, u64 *out, size_t out_ps, cudaStream_t s);
+// Rescale of m ciphertexts at one level, poly p of ciphertext i at base + (2i + p) ps, in place;
+// t is scratch of 2 m level n words.  Every rescale goes through here (he_rescale with m = 1).
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s);
 double k_bench_modmul(const he_ctx *ctx, int blocks, int iters, cudaStream_t s);
 

@@ -2088,24 +2088,6 @@ int k_range_check(const he_ctx *ctx, const u64 *d, size_t ps, int level, unsigne
     return HE_OK;
 }
 
-int k_rescale_prep(const he_ctx *ctx, const u64 *top, size_t top_pstride, u64 *t, int level,
-                   cudaStream_t s) {
-    pdl_launch(rescale_prep_kernel, dim3(ctx->n / TB, level, 2), TB, 0, s, ctx->kp, top, top_pstride, t, level);
-    LAUNCH_CHECK();
-    return HE_OK;
-}
-
-int k_rescale_combine(const he_ctx *ctx, he_ct *ct, const u64 *t, cudaStream_t s) {
-    const int l = ct->level;   // level before the drop
-    const u64 *base = ctx->d_consts + ctx->np + 2 * (ctx->L + 1);
-    const u64 *inv = base + (size_t)l * 2 * (ctx->L + 1);
-    const u64 *invs = inv + (ctx->L + 1);
-    TraceScope tr("rescale", s, (double)l * ctx->n * 8 * 6, (double)l * ctx->n * 2);
-    pdl_launch(rescale_combine_kernel, dim3(ctx->n / TB, l, 2), TB, 0, s, ctx->kp, ct->d, ct->pstride, t, l, inv, invs);
-    LAUNCH_CHECK();
-    return HE_OK;
-}
-
 int k_mac(const he_ctx *ctx, const mac_term *terms_dev, int n_terms, u64 *out, size_t out_pstride,
           int level, bool accumulate, cudaStream_t s) {
     TraceScope tr("mac", s, (double)(level + 1) * ctx->n * 8 * (3.0 * n_terms + 2), (double)(level + 1) * ctx->n * 2.0 * n_terms);
