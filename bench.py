@@ -837,7 +837,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": "batched+fused: every rotation key streamed once "
                                                       "into a raised-basis MAC, one ModDown per output; "
-                                                      "relinearisations batched per tree depth",
+                                                      "relinearised products of one operand level "
+                                                      "batched",
                        "key_switches_per_step": ks_per_step, "key_stream": args.key_stream,
                        "cuda_graph": not args.no_graph,
                        "autotuner": H.he_ctx_tuning_log(ctx).strip().splitlines(),
