@@ -2656,8 +2656,11 @@ int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u6
         A.x[t] = x[t];
         A.ps[t] = ps[t];
         for (int i = 0; i <= level; i++) {                   // Montgomery form, once on the host
-            const u64 q = ctx->primes[i];
-            A.res[t][i] = (u64)((((u128)(res[t * HE_LC_LIMBS + i] % q)) << 64) % q);
+            // x R mod q as the device forms it: REDC(x (R^2 mod q)), three products
+            const u64 q = ctx->primes[i], qinv = ctx->h_qinv[i];
+            const u128 T = (u128)res[t * HE_LC_LIMBS + i] * ctx->h_r2[i];
+            const u64 lo = (u64)T, hi = (u64)(T >> 64), mh = (u64)(((u128)(lo * qinv) * q) >> 64);
+            A.res[t][i] = hi >= mh ? hi - mh : hi + (q - mh);
         }
     }
     for (int i = 0; i <= level; i++) A.cst[i] = cst[i];
