@@ -3156,7 +3156,7 @@ static int ps_lincomb(he_ctx *c, const std::vector<std::pair<double, const he_ct
 }
 
 // Deferred Paterson-Stockmeyer evaluation.  The plan is recorded as operations, each with the
-// ciphertexts it reads and writes; a scheduler then issues, round by round, every ready operation
+// ciphertexts it reads and writes; a scheduler then issues, pass after pass, every ready operation
 // that is not a product (in program order), then every ready product of one level as one batched
 // relinearisation.  An operation is ready when no earlier unfinished operation writes what it
 // reads or touches what it writes, so every ciphertext gets the bits of the program-order
