@@ -616,3 +616,28 @@ def test_paterson_stockmeyer_he_depth_and_accuracy(deep, deg, depth):
     assert count[0] < deg - 1
     ref = Ly.cheb_eval(c, 8 * z, -8, 8)
     assert np.abs(ctx.decrypt(out) - ref).max() <= 2.0 ** -20 * (ref.max() - ref.min())
+
+
+def test_paterson_stockmeyer_degree_16_products_by_operand_level(deep):
+    """Degree 16 (k = 4, giant steps 4, 8, 16): the evaluation takes 8 relinearised products
+    whose operands sit at 5 distinct levels, two products at every level but the first and the
+    third: T_2 | T_3, T_4 | T_8 | T_16 and the product inside the T_8 quotient | the two
+    products of the remainder's quotients.  Products at one level are independent, so 5 is the
+    fewest batches of equal-level products the evaluation can be issued in."""
+    ctx = deep
+    c = Ly.cheb_nodes_coeffs(Ly.gelu, 16, -8, 8)
+    ct = ctx.encrypt(np.random.default_rng(16).uniform(-1, 1, ctx.N), 9, nonce=316)
+    levels = []
+    orig = ctx.mul_relin
+
+    def recorded(a, b):
+        assert a.level == b.level
+        levels.append(a.level)
+        return orig(a, b)
+    ctx.mul_relin = recorded
+    try:
+        Ly.cheb_ps_he(ctx, ct, c)
+    finally:
+        ctx.mul_relin = orig
+    from collections import Counter
+    assert Counter(levels) == Counter({9: 1, 8: 2, 7: 1, 6: 2, 5: 2})
