@@ -268,21 +268,24 @@ def mac(ctx, R, terms, pts, level, scale_in, pt_scale=None):
     return Ciphertext(c, level, scale_in * S)
 
 
-def conv_he(ctx, plan: ConvPlan, cts, pts=None, bias_pts=None, pt_scale=None):
+def conv_he(ctx, plan: ConvPlan, cts, pts=None, bias_pts=None, pt_scale=None, outputs=None):
     """hconv2d on oracle ciphertexts (all inputs at one level and scale).
 
     pts: optional {(u, v, a): int64 plaintext} at scale q_level (else encoded here);
     bias_pts: optional {v: int64 plaintext} at the input scale (else encoded here).
     pt_scale: the scale pts were encoded at, when they were encoded for another (higher)
     level: an integer plaintext is the same at every level, only its residues are fewer.
+    outputs: the output shards to compute (default: all of them), returned in ascending
+    order; only the rotations those shards read are formed.
     """
     level, scale = cts[0].level, cts[0].scale
     assert all(c.level == level and c.scale == scale for c in cts)
+    vs = list(range(plan.lout.n_shards)) if outputs is None else sorted(set(outputs))
     if pts is None:
         pts = conv_plaintexts(plan, ctx.n, float(ctx.q[level]))
-    R = rotate_all(ctx, cts, plan.amounts)
+    R = rotate_all(ctx, cts, lambda u: sorted({a for v in vs for (uu, a) in plan.terms[v] if uu == u}))
     out = []
-    for v in range(plan.lout.n_shards):
+    for v in vs:
         keys = sorted(plan.terms[v].keys())
         ct = mac_rescale(ctx, R, keys, [pts[(u, v, a)] for (u, a) in keys], level, scale, pt_scale)
         bpt = bias_pts[v] if bias_pts is not None else encode(plan.bias[v], ctx.n, ct.scale)
@@ -343,18 +346,18 @@ def raised_stage(ctx, srcs, terms_by_v):
     return [out[v] for v in sorted(out)]
 
 
-def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None, pt_scale=None):
+def conv_he_raised(ctx, plan, cts, pts=None, bias_pts=None, pt_scale=None, outputs=None):
     """hconv2d with one ModDown per output shard (raised_stage), then rescale and bias.
-    Same plan and plaintexts as conv_he; decrypts like it, different bits.  pt_scale as in
-    conv_he."""
+    Same plan and plaintexts as conv_he; decrypts like it, different bits.  pt_scale and
+    outputs as in conv_he."""
     level, scale = cts[0].level, cts[0].scale
     assert all(c.level == level and c.scale == scale for c in cts)
+    vs = list(range(plan.lout.n_shards)) if outputs is None else sorted(set(outputs))
     if pts is None:
         pts = conv_plaintexts(plan, ctx.n, float(ctx.q[level]))
-    terms = {v: [(u, a, pts[(u, v, a)]) for (u, a) in sorted(plan.terms[v].keys())]
-             for v in range(plan.lout.n_shards)}
+    terms = {v: [(u, a, pts[(u, v, a)]) for (u, a) in sorted(plan.terms[v].keys())] for v in vs}
     out = []
-    for v, acc in enumerate(raised_stage(ctx, cts, terms)):
+    for v, acc in zip(vs, raised_stage(ctx, cts, terms)):
         acc.scale = scale * (float(ctx.q[level]) if pt_scale is None else pt_scale)
         ct = ctx.rescale(acc)
         bpt = bias_pts[v] if bias_pts is not None else encode(plan.bias[v], ctx.n, ct.scale)
@@ -919,12 +922,16 @@ def pool_plan(lin: Layout, weights=(0.25, 0.25, 0.25, 0.25), select_top_left=Fal
         f = 4 // t
         step = t * Bn
         dup = [(-k * step) % N for k in range(f)]
+        # Eq. 13: block b of the duplicated shard sums the consolidated blocks b - k t (k < f);
+        # it holds the channel of whichever of them holds data, so the table before
+        # duplication is the one read (an empty block stays empty)
+        chan0, row00 = chan[0].copy(), row0[0].copy()
         for k in range(1, f):
             for b in range(nbn):
                 src = b - k * (step // Bn)
-                if src >= 0 and chan[0, src] >= 0 and chan[0, b] < 0:
-                    chan[0, b] = chan[0, src]
-                    row0[0, b] = row0[0, src]
+                if src >= 0 and chan0[src] >= 0 and chan[0, b] < 0:
+                    chan[0, b] = chan0[src]
+                    row0[0, b] = row00[src]
     lout = Layout(lin.c, m // 2, Mh, N, Bn, chan, row0)
     return PoolPlan(lin, lout, pre, h_terms, v_terms, groups, dup)
 

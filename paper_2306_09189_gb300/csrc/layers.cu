@@ -253,12 +253,16 @@ int plan_pool(const Lay &lin, bool select, PoolPlanH &P) {
         const int f = 4 / t, step = t * Bn;
         P.dup.clear();
         for (int k = 0; k < f; k++) P.dup.push_back(((-k * step) % N + N) % N);
+        // block b of the duplicated shard is the sum of the consolidated blocks b - k t (k < f):
+        // its channel is the one of those consolidated blocks that holds data, so read the
+        // table as it was before duplication (an empty block stays empty)
+        const std::vector<int> chan0 = lo.chan, row00 = lo.row0;
         for (int k = 1; k < f; k++)
             for (int b = 0; b < nbn; b++) {
                 int src = b - k * (step / Bn);
-                if (src >= 0 && lo.chan[src] >= 0 && lo.chan[b] < 0) {
-                    lo.chan[b] = lo.chan[src];
-                    lo.row0[b] = lo.row0[src];
+                if (src >= 0 && chan0[src] >= 0 && lo.chan[b] < 0) {
+                    lo.chan[b] = chan0[src];
+                    lo.row0[b] = row00[src];
                 }
             }
     }
@@ -2453,6 +2457,16 @@ extern "C" void he_conv_destroy(he_conv *cv) {
 extern "C" int he_conv_out_layout(const he_conv *cv, he_layout *out) {
     if (!cv || !out) return HE_EINVAL;
     return to_c(cv->pool ? cv->pool->P.lout : cv->lout, out);
+}
+extern "C" int he_conv_select_pool(const he_conv *cv, he_pool **out) {
+    if (!cv || !out) { he_set_error("he_conv_select_pool: null argument"); return HE_EINVAL; }
+    *out = nullptr;
+    if (cv->stride != 2 || !cv->pool) {
+        he_set_error("he_conv_select_pool: only a stride-2 convolution has a select stage");
+        return HE_EINVAL;
+    }
+    *out = cv->pool;
+    return HE_OK;
 }
 extern "C" int he_conv_out_level(const he_conv *cv) {
     if (!cv) return HE_EINVAL;

@@ -125,7 +125,7 @@ def test_conv_sharded_bit_exact(mid, c, co, m, k, pad):
     _conv_case(mid, c, co, m, k, pad, level=3, seed=c * 10 + m)
 
 
-@pytest.mark.parametrize("c,m", [(8, 32), (2, 32), (4, 32), (2, 64), (6, 28)])
+@pytest.mark.parametrize("c,m", [(8, 32), (2, 32), (4, 32), (2, 64), (6, 28), (3, 32)])
 def test_pool_bit_exact(mid, c, m):
     from paper_2306_09189_gb300 import hegpu as H
     from tests._hegpu_util import assert_ct_equal

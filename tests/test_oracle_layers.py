@@ -109,7 +109,11 @@ def test_bsgs_rotation_counts():
 @pytest.mark.parametrize("c,m,N,sel", [(4, 32, 4096, False), (16, 32, 2048, False),
                                         (8, 32, 2048, False), (2, 32, 512, False),
                                         (2, 28, 512, False), (3, 32, 512, True),
-                                        (64, 56, 32768, False)])
+                                        (64, 56, 32768, False),
+                                        # 2 shards or 1 with an empty block: duplication (Eq. 13)
+                                        # must leave the empty block's copies empty
+                                        (3, 32, 2048, False), (3, 32, 2048, True),
+                                        (5, 32, 4096, False), (3, 32, 4096, False)])
 def test_pool_plan_equals_torch_avg_pool(c, m, N, sel):
     rng = np.random.default_rng(m + c)
     x = rng.uniform(0, 1, (c, m, m))
