@@ -331,6 +331,14 @@ int he_conv_bsgs_giant(const he_conv *conv);
 void he_conv_destroy(he_conv *conv);
 int he_conv_out_layout(const he_conv *conv, he_layout *out);
 int he_conv_out_level(const he_conv *conv);
+/* The select stage of a stride-2 convolution (Sec. 4.1 "Strided convolutions": the unstrided
+ * convolution, then the pooling program of Sec. 4.2 with weights (1, 0, 0, 0) and no ones-
+ * convolution, keeping the top-left pixel of every 2x2 window; masks of Eqs. 10-11 at weight
+ * 1).  *out is borrowed: it belongs to `conv` and is destroyed with it.  Its masks can be read
+ * with he_pool_n_masks and replaced with he_pool_import_plaintexts (horizontal masks at the
+ * conv's output level, vertical one level lower), for instance by another encoder's integers.
+ * HE_EINVAL for a stride-1 convolution. */
+int he_conv_select_pool(const he_conv *conv, he_pool **out);
 /* Distinct non-zero rotation amounts the plan needs (all stages); returns the count,
  * writes up to cap of them. */
 int he_conv_rotations(const he_conv *conv, int32_t *amounts, size_t cap);
@@ -487,9 +495,11 @@ int he_havgpool(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, he_layou
  * has no counterpart; this is a property of this library's memory handling.
  * Its scratch is a fixed device array inside the library (24 MiB, 3 * 2^20 words), held on
  * every GPU that loads the library until the process exits; it rejects a ciphertext whose
- * 2 * level * n exceeds that with HE_EINVAL.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current: make that first
- * call before any stream capture.  All calls share the one array and every call overwrites
+ * 2 * level * n exceeds that with HE_EINVAL.  The array belongs to a module that CUDA may load
+ * lazily; he_ctx_create loads it and looks up the array's device address (cudaGetSymbolAddress)
+ * with the context's device current, so the array is reserved while the context is set up and
+ * a later call allocates nothing.  (A call on a device that has no context yet does that look-up
+ * itself: make it during set-up, before any stream capture.)  All calls share the one array and every call overwrites
  * it completely before reading it; calls whose work overlaps on the GPU (different streams,
  * or different host threads) race on it and must be serialised by the caller. */
 int he_rescale_noalloc(he_ctx *ctx, he_ct *ct, void *stream);

@@ -526,7 +526,15 @@ static int create(const he_params *pr, he_ctx **out) {
 extern "C" int he_ctx_create(const he_params *params, he_ctx **out) {
     if (!out) { he_set_error("null output"); return HE_EINVAL; }
     *out = nullptr;
-    return create(params, out);
+    int rc = create(params, out);
+    if (rc != HE_OK) return rc;
+    // reserve the no-allocation rescale's fixed scratch now, during set-up (see noalloc.cu)
+    rc = he_noalloc_setup();
+    if (rc != HE_OK) {
+        he_ctx_destroy(*out);
+        *out = nullptr;
+    }
+    return rc;
 }
 extern "C" void he_ctx_destroy(he_ctx *ctx) {
     if (ctx) cudaDeviceSynchronize();

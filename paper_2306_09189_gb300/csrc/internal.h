@@ -342,6 +342,8 @@ int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u6
 // Rescale of m ciphertexts at one level, poly p of ciphertext i at base + (2i + p) ps, in place;
 // t is scratch of 2 m level n words.  Every rescale goes through here (he_rescale with m = 1).
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s);
+// Loads the no-allocation rescale's module on the current device and caches its scratch address.
+int he_noalloc_setup();
 double k_bench_modmul(const he_ctx *ctx, int blocks, int iters, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- host helpers

@@ -7,6 +7,12 @@
 // This variant keeps its scratch in a fixed device array that is part of the library image,
 // reserved on every GPU that loads the library until the process exits.  The caller still
 // passes the ciphertext, which is rescaled in place exactly like he_rescale does.
+//
+// The array lives in this translation unit's module.  Under CUDA's lazy module loading that
+// module (and with it the array's device memory) is loaded the first time its address is
+// asked for, so the address is looked up when a context is created (he_ctx_create calls
+// he_noalloc_setup with the context's device current): the reservation then happens during
+// set-up, not on the first no-allocation call.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -37,6 +43,7 @@ static int scratch_address(u64 **out) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
+            cudaGetLastError();   // do not leave the error for a later launch check
             he_set_error("he_rescale_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
             return HE_ECUDA;
         }
@@ -44,6 +51,12 @@ static int scratch_address(u64 **out) {
     }
     *out = g_addr[dev];
     return HE_OK;
+}
+
+// Set-up: load this module on the current device and cache the scratch array's address.
+int he_noalloc_setup() {
+    u64 *t = nullptr;
+    return scratch_address(&t);
 }
 
 extern "C" int he_rescale_noalloc(he_ctx *c, he_ct *ct, void *stream) {
