@@ -119,6 +119,7 @@ _SIGS = {
     "he_conv_fork": (c_int, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "he_conv_out_layout": (c_int, [c_vp, ctypes.POINTER(he_layout)]),
     "he_conv_out_level": (c_int, [c_vp]),
+    "he_conv_select_pool": (c_int, [c_vp, ctypes.POINTER(c_vp)]),
     "he_conv_rotations": (c_int, [c_vp, I32P, c_size_t]),
     "he_conv_n_terms": (c_int, [c_vp]),
     "he_conv_export_plan": (c_int, [c_vp, I32P, I32P, I32P, F64P]),
@@ -520,6 +521,13 @@ def he_conv_out_layout(conv):
 
 def he_conv_out_level(conv):
     return _check(load().he_conv_out_level(conv))
+
+
+def he_conv_select_pool(conv):
+    """The stride-2 convolution's select stage (a pool handle owned by the convolution)."""
+    p = c_vp()
+    _check(load().he_conv_select_pool(conv, ctypes.byref(p)))
+    return p
 
 
 def he_conv_rotations(conv):
