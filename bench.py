@@ -227,7 +227,7 @@ def run_block(args, ws, rank, local):
     lay2 = H.he_conv_out_layout(conv2)
     H.he_keygen_rotations(ctx, sorted(set(H.he_conv_rotations(conv1)) | set(H.he_conv_rotations(conv2))))
     H.he_keygen_relin(ctx)
-    cheb = host.chebyshev_coeffs(host.gelu, DEG, -8.0, 8.0)
+    cheb = host.chebyshev_coeffs("gelu", DEG, -8.0, 8.0)
     ns1, ns2 = lay.n_shards, lay1.n_shards
     xs = []
     for i, (img, lv) in enumerate(zip(imgs, levels)):
@@ -667,7 +667,7 @@ def main():
     n, N = info["n"], info["slots"]
     wl = workloads.cifar_conv_bn(0, c=2) if args.small else workloads.cifar_conv_bn(0)
     lay = H.he_layout_image(wl.x.shape[0], 32, N)
-    cheb = host.chebyshev_coeffs(host.gelu, DEG, -8.0, 8.0)
+    cheb = host.chebyshev_coeffs("gelu", DEG, -8.0, 8.0)
     x = host.encrypt_image(ctx, lay, wl.x, LEVEL, pr.scale, nonce0=1)[0]
     conv = H.he_conv_create(ctx, lay, wl.W, wl.bias, 1, 1, LEVEL, pr.scale)
     rots = H.he_conv_rotations(conv)

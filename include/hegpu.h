@@ -397,6 +397,11 @@ int he_conv_fork(const he_conv *conv, he_ctx *ctx, he_conv **out);
  * the levelled maximum error.  Host only (no device, no context).  HE_EINVAL for a bad
  * function id, deg outside 0..200 or hi <= lo; HE_ESTATE if the exchange degenerates. */
 int he_cheb_minimax(int fn, int deg, double lo, double hi, double *coeffs, double *err);
+/* Chebyshev interpolant of activation fn on [lo, hi] at the deg + 1 first-kind nodes (Appendix,
+ * "Chebyshev Basis"; the interpolation rows of the approximation table): coeffs[0..deg]
+ * (caller-owned) in the same form as he_cheb_minimax.  Host only.  HE_EINVAL for a bad function
+ * id, deg outside 0..1000 or hi <= lo. */
+int he_cheb_interp(int fn, int deg, double lo, double hi, double *coeffs);
 
 /* ------------------------------------------------------------------ linear head (Sec. 4, Other Layers) */
 /* Linear layer over a sharded image: output j = sum over the flattened (channel, row, column)
@@ -481,6 +486,11 @@ int he_poly_eval_many(he_ctx *ctx, he_ct *const *io, int m, const double *cheb, 
 int he_poly_eval_ps(he_ctx *ctx, he_ct *io, const double *cheb, int deg, double target_scale, void *stream);
 int he_poly_eval_ps_many(he_ctx *ctx, he_ct *const *io, int m, const double *cheb, int deg,
                          const double *target_scales, void *stream);
+/* What he_poly_eval_ps costs for a degree-deg polynomial (the plan depends on the degree only):
+ * *products = relinearised products (baby steps T_2..T_k, giant steps beyond T_k, one per
+ * division with a non-constant quotient), *depth = levels consumed (degree 59: 16 products at
+ * depth 6; 27: 11 at 5; 16: 8 at 5).  Host only.  HE_EINVAL for deg outside 2..255. */
+int he_poly_ps_plan(int deg, int *products, int *depth);
 
 /* Convenience wrappers: create, run, destroy. */
 int he_hconv2d(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, const double *W,

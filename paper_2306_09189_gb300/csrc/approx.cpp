@@ -1,6 +1,6 @@
 // Host-side polynomial approximation of activation functions in the Chebyshev basis (Appendix
-// "Polynomial Approximation"): the minimax (best uniform) polynomial by the Remez exchange
-// algorithm.  The coefficients feed he_poly_eval / he_poly_eval_ps, which evaluate
+// "Polynomial Approximation"): interpolation at the Chebyshev nodes (Appendix "Chebyshev
+// Basis") and the minimax (best uniform) polynomial by the Remez exchange algorithm.  The coefficients feed he_poly_eval / he_poly_eval_ps, which evaluate
 // sum c_k T_k(t) on t in [-1, 1].
 #include <math.h>
 #include <string.h>
@@ -61,6 +61,30 @@ bool solve(std::vector<double> A, std::vector<double> b, int m, std::vector<doub
 }
 
 }  // namespace
+
+extern "C" int he_cheb_interp(int fn, int deg, double lo, double hi, double *coeffs) {
+    if (deg < 0 || deg > 1000 || !(hi > lo) || !coeffs || std::isnan(activation(fn, 0.5 * (lo + hi)))) {
+        he_set_error("he_cheb_interp: bad argument");
+        return HE_EINVAL;
+    }
+    // p interpolates f at the deg + 1 first-kind nodes t_j = cos(theta_j), theta_j =
+    // pi (j + 1/2) / (deg + 1); discrete orthogonality of T_k over these nodes gives
+    // c_k = (2 / (deg + 1)) sum_j f(t_j) cos(k theta_j), halved for k = 0
+    const int K = deg + 1;
+    const double half = 0.5 * (hi - lo), mid = 0.5 * (hi + lo);
+    std::vector<double> theta(K), fv(K);
+    for (int j = 0; j < K; j++) {
+        theta[j] = M_PI * (j + 0.5) / K;
+        fv[j] = activation(fn, half * cos(theta[j]) + mid);
+    }
+    for (int k = 0; k < K; k++) {
+        double sum = 0.0;
+        for (int j = 0; j < K; j++) sum += fv[j] * cos(k * theta[j]);
+        coeffs[k] = (2.0 / K) * sum;
+    }
+    coeffs[0] *= 0.5;
+    return HE_OK;
+}
 
 extern "C" int he_cheb_minimax(int fn, int deg, double lo, double hi, double *coeffs, double *err) {
     if (deg < 0 || deg > 200 || !(hi > lo) || !coeffs || std::isnan(activation(fn, 0.5 * (lo + hi)))) {

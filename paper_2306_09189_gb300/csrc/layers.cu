@@ -3123,6 +3123,32 @@ static int ps_need(const std::vector<double> &cc, int k, const std::vector<int> 
     return std::max(std::max(ps_need(q, k, giants) + 1, ps_depth(G) + 1), ps_need(r, k, giants));
 }
 
+// relinearised products of ev on a polynomial of degree d (the recursion of PsGroup::ev below):
+// a split with a non-constant quotient costs its product plus the quotient's and remainder's
+static int ps_split_products(int d, int k, const std::vector<int> &giants) {
+    if (d < k) return 0;
+    int G = 0;
+    for (int g : giants)
+        if (g <= d) G = g;
+    if (d == G && G - 1 < k) return 0;                       // q_0 T_G + r in one combination
+    if (d == G) return ps_split_products(G - 1, k, giants);  // scalar q_0 T_G plus ev(r)
+    return 1 + ps_split_products(d - G, k, giants) + ps_split_products(G - 1, k, giants);
+}
+
+extern "C" int he_poly_ps_plan(int deg, int *products, int *depth) {
+    if (deg < 2 || deg > 255) { he_set_error("he_poly_ps_plan: degree %d outside 2..255", deg); return HE_EINVAL; }
+    int k;
+    std::vector<int> giants;
+    ps_params(deg, k, giants);
+    int steps = 0;                                           // T_2..T_k and the giant steps beyond T_k
+    const int top = std::max(k, giants.empty() ? 0 : giants.back());
+    for (int i = 2; i <= top; i++)
+        if (i <= k || std::find(giants.begin(), giants.end(), i) != giants.end()) steps++;
+    if (products) *products = steps + ps_split_products(deg, k, giants);
+    if (depth) *depth = ps_need(std::vector<double>(deg + 1, 1.0), k, giants);
+    return HE_OK;
+}
+
 // sum_(coef, x) round(coef scale q_{l+1} / s_x) x + round(c0 scale q_{l+1}) at level l + 1, rescaled
 // to (l, scale); y is scratch for the term-by-term form
 static int ps_lincomb(he_ctx *c, const std::vector<std::pair<double, const he_ct *>> &terms, double c0, int level,

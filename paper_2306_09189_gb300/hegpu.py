@@ -142,6 +142,8 @@ _SIGS = {
     "he_ct_check_range": (ctypes.c_longlong, [c_vp, c_vp, c_vp]),
     "he_debug_fail_alloc": (c_int, [ctypes.c_long]),
     "he_cheb_minimax": (c_int, [c_int, c_int, c_double, c_double, F64P, F64P]),
+    "he_cheb_interp": (c_int, [c_int, c_int, c_double, c_double, F64P]),
+    "he_poly_ps_plan": (c_int, [c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "he_linear_rotations": (c_int, [c_vp, I32P, c_size_t]),
     "he_linear_out_level": (c_int, [c_vp]),
     "he_linear_keyswitches": (ctypes.c_int64, [c_vp]),
@@ -664,6 +666,20 @@ def he_cheb_minimax(fn, deg, lo, hi):
     e = np.zeros(1, dtype=np.float64)
     _check(load().he_cheb_minimax(fn, deg, lo, hi, _p(c, F64P), _p(e, F64P)))
     return c, float(e[0])
+
+
+def he_cheb_interp(fn, deg, lo, hi):
+    """Coefficients [deg + 1] of the Chebyshev interpolant at the first-kind nodes."""
+    c = np.zeros(deg + 1, dtype=np.float64)
+    _check(load().he_cheb_interp(fn, deg, lo, hi, _p(c, F64P)))
+    return c
+
+
+def he_poly_ps_plan(deg):
+    """(relinearised products, levels consumed) of the Paterson-Stockmeyer evaluation."""
+    p, d = c_int(), c_int()
+    _check(load().he_poly_ps_plan(deg, ctypes.byref(p), ctypes.byref(d)))
+    return p.value, d.value
 
 
 def he_pool_create(ctx, layout, level):

@@ -67,27 +67,22 @@ def unpack(lay, slots):
 
 
 # ----------------------------------------------------------------------------- activation
-def gelu(x):
-    return 0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0)))
+def _fn_id(fn):
+    ids = {"gelu": H.HE_FN_GELU, "relu": H.HE_FN_RELU, "silu": H.HE_FN_SILU, "softplus": H.HE_FN_SOFTPLUS}
+    return ids[fn]
 
 
-def chebyshev_coeffs(f, deg, lo, hi):
-    """c_0..c_deg with f(x) ~ sum_k c_k T_k((2x - lo - hi)/(hi - lo)), interpolating at the
-    nodes t_j = cos(pi (j + 1/2) / (deg + 1)) (discrete orthogonality of T_k there)."""
-    K = deg + 1
-    j = np.arange(K)
-    theta = np.pi * (j + 0.5) / K
-    fv = np.array([f(0.5 * (hi - lo) * math.cos(t) + 0.5 * (hi + lo)) for t in theta])
-    c = np.array([(2.0 / K) * np.dot(fv, np.cos(k * theta)) for k in range(K)])
-    c[0] /= 2.0
-    return c
+def chebyshev_coeffs(fn, deg, lo, hi):
+    """c_0..c_deg with f(x) ~ sum_k c_k T_k((2x - lo - hi)/(hi - lo)): the library's interpolation
+    at the deg + 1 first-kind Chebyshev nodes, for an activation "gelu", "relu", "silu" or
+    "softplus"."""
+    return H.he_cheb_interp(_fn_id(fn), deg, lo, hi)
 
 
 def minimax_coeffs(fn, deg, lo, hi):
     """The minimax polynomial of an activation ("gelu", "relu", "silu", "softplus") by the
     library's Remez routine: (c_0..c_deg in the same Chebyshev form, levelled error)."""
-    ids = {"gelu": H.HE_FN_GELU, "relu": H.HE_FN_RELU, "silu": H.HE_FN_SILU, "softplus": H.HE_FN_SOFTPLUS}
-    return H.he_cheb_minimax(ids[fn], deg, lo, hi)
+    return H.he_cheb_minimax(_fn_id(fn), deg, lo, hi)
 
 
 # ----------------------------------------------------------------------------- images
@@ -106,52 +101,11 @@ def decrypt_image(ctx, lay, cts, stream=None):
 
 
 def ps_products(deg):
-    """Relinearised products of the Paterson-Stockmeyer evaluation of a degree-deg polynomial:
-    the baby steps T_2..T_k, the giant steps beyond T_k, and one per split with a non-constant
-    quotient (the same recursion as the library's)."""
-    k = 2
-    while k * k < (deg + 1) // 2:
-        k *= 2
-    giants = []
-    g = k
-    while g <= deg:
-        giants.append(g)
-        g *= 2
-    count = (k - 1) + max(0, len(giants) - 1)
-
-    def splits(d):
-        if d < k:
-            return 0
-        G = max(x for x in giants if x <= d)
-        qd, rd = d - G, G - 1
-        if qd == 0:
-            return splits(rd) if rd >= k else 0
-        return 1 + splits(qd) + splits(rd)
-    return count + splits(deg)
+    """Relinearised products of the library's Paterson-Stockmeyer evaluation of a degree-deg
+    polynomial."""
+    return H.he_poly_ps_plan(deg)[0]
 
 
 def ps_depth(deg):
-    """Levels the Paterson-Stockmeyer evaluation of a degree-deg polynomial consumes (the
-    library's recursion: leaves cost one level above their deepest baby step, a split with a
-    non-constant quotient one level above the quotient and the giant step)."""
-    k = 2
-    while k * k < (deg + 1) // 2:
-        k *= 2
-    giants = []
-    g = k
-    while g <= deg:
-        giants.append(g)
-        g *= 2
-    depth = lambda i: (i - 1).bit_length()
-
-    def need(d):
-        if d < k:
-            return 1 + max([depth(i) for i in range(1, d + 1)] + [0])
-        G = max(x for x in giants if x <= d)
-        qd, rd = d - G, G - 1
-        if qd == 0 and rd < k:
-            return 1 + max([depth(G)] + [depth(i) for i in range(1, G)])
-        if qd == 0:
-            return max(1 + depth(G), need(rd))
-        return max(need(qd) + 1, depth(G) + 1, need(rd))
-    return need(deg)
+    """Levels the library's Paterson-Stockmeyer evaluation of a degree-deg polynomial consumes."""
+    return H.he_poly_ps_plan(deg)[1]

@@ -265,7 +265,7 @@ def main():
     t = time.perf_counter()
     H.he_keygen_relin(root)
     layers = workloads.serving_stack(0, widths=widths, m=32)
-    cheb = host.chebyshev_coeffs(host.gelu, workloads.GELU_DEGREE, -8.0, 8.0)
+    cheb = host.chebyshev_coeffs("gelu", workloads.GELU_DEGREE, -8.0, 8.0)
     level = pr.n_q - 1
     stacks = {m: Stack(root, m, layers, cheb, level, pr.scale, conv_form=args.conv) for m in sizes}
     setup_s = time.perf_counter() - t

@@ -25,7 +25,7 @@ def _setup(H, host):
     H.he_keygen_relin(ctx)
     x = host.encrypt_image(ctx, lay, rng.uniform(0, 1, (c, m, m)), 9, pr.scale, nonce0=3)[0]
     y = H.he_ct_alloc(ctx, 8)
-    cheb = host.chebyshev_coeffs(host.gelu, 8, -8.0, 8.0)
+    cheb = host.chebyshev_coeffs("gelu", 8, -8.0, 8.0)
     return pr, ctx, conv, x, y, cheb
 
 

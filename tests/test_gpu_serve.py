@@ -18,7 +18,7 @@ def test_results_identical_alone_and_in_the_mix():
     try:
         H.he_keygen_relin(root)
         layers = workloads.serving_stack(0, widths=(4, 8, 8), m=16)
-        cheb = host.chebyshev_coeffs(host.gelu, 16, -8.0, 8.0)
+        cheb = host.chebyshev_coeffs("gelu", 16, -8.0, 8.0)
         stacks = {m: Stack(root, m, layers, cheb, 16, pr.scale) for m in (8, 16)}
         rng = np.random.default_rng(1)
         imgs, reqs = [], []
