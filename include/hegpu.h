@@ -21,8 +21,9 @@
  *     limbs); floating point appears only in encoding and in scale bookkeeping.
  *   - One context is driven from one host thread and one stream at a time: the context owns
  *     the scratch buffers that key switching uses.
- *   - Device memory: the library allocates with cudaMalloc; he_ct_wrap lets a caller hand
- *     in its own device buffer (for instance a torch tensor's storage).
+ *   - Device memory: the library allocates with cudaMalloc, or through the caller's allocator
+ *     once he_set_allocator has installed one (for instance PyTorch's caching allocator);
+ *     he_ct_wrap lets a caller hand in its own device buffer (a torch tensor's storage).
  */
 #ifndef HEGPU_H
 #define HEGPU_H
@@ -105,6 +106,24 @@ int he_params_primes(const he_params *params, uint64_t *q, uint64_t *p);
  * permutation; one shard with tiled duplication when c M^2 <= N, image shards when
  * M^2 <= N < c M^2, channel shards of N/M rows when M^2 > N). */
 int he_layout_image(int c, int m, int N, he_layout *out);
+
+/* ------------------------------------------------------------------ device memory */
+/* Caller-provided device allocator (the paper has no counterpart: this is how a host framework
+ * that owns the GPU's memory, such as PyTorch's caching allocator, lends it to the library).
+ * Once installed, every device block the library needs (tables, keys, ciphertexts, plaintexts,
+ * scratch) comes from alloc(bytes, user), which returns a device pointer of the current device
+ * aligned to at least 256 bytes, or NULL when it cannot (the library then reports HE_ENOMEM);
+ * every block goes back through free_fn(ptr, user), after the library has synchronised the
+ * device (the allocator may reuse the block on any stream at once).  Process-wide; both NULL
+ * restores cudaMalloc / cudaFree.  HE_EINVAL if exactly one function is NULL; HE_ESTATE while
+ * any block the library allocated is still live (destroy every context and object first), so
+ * that a block is always returned to the allocator that made it.  Not during graph capture
+ * (no allocation happens there).  The fixed scratch of he_rescale_noalloc is not affected. */
+typedef void *(*he_device_alloc_fn)(size_t bytes, void *user);
+typedef void (*he_device_free_fn)(void *ptr, void *user);
+int he_set_allocator(he_device_alloc_fn alloc, he_device_free_fn free_fn, void *user);
+/* Device blocks the library currently holds (from either allocator). */
+int64_t he_live_allocations(void);
 
 /* ------------------------------------------------------------------ context and keys */
 int he_ctx_create(const he_params *params, he_ctx **out);
@@ -492,7 +511,17 @@ int he_poly_eval_ps_many(he_ctx *ctx, he_ct *const *io, int m, const double *che
  * depth 6; 27: 11 at 5; 16: 8 at 5).  Host only.  HE_EINVAL for deg outside 2..255. */
 int he_poly_ps_plan(int deg, int *products, int *depth);
 
-/* Convenience wrappers: create, run, destroy. */
+/* One-call layers: plan, generate the missing rotation keys, run, synchronise the stream and
+ * release the plan.  he_hconv2d is the paper's hconv2d (Sec. 4.1: shift operator Eq. 1, partial
+ * convolutions Eqs. 2-5, image shards Eq. 6, channel shards Eq. 7; stride 2 as the unstrided
+ * convolution plus the downsampling of Sec. 4.2) on the ciphertexts in_cts (all at one level and
+ * scale; the plan is made at that level); he_havgpool is havgpool (Sec. 4.2, Eqs. 10-13: the 2x2
+ * ones-convolution, horizontal and vertical reductions, consolidation or duplication).  W is
+ * [co][ci][kh][kw], bias [co] or NULL.  out_cts: caller-allocated handles, one per output shard
+ * of the output layout, allocated at the output level or above; out_layout (optional) receives that
+ * layout.  The plaintexts are encoded by the library (within one integer per coefficient of any
+ * other encoder of the same values), so the result decrypts to the layer; for bit-level control
+ * of the plaintexts use he_conv_create / he_pool_create and their import calls. */
 int he_hconv2d(he_ctx *ctx, const he_layout *in, he_ct *const *in_cts, const double *W,
                const double *bias, int co, int ci, int kh, int kw, int stride, int pad,
                int mode, he_layout *out_layout, he_ct **out_cts, void *stream);

@@ -44,6 +44,77 @@ extern "C" int he_debug_fail_alloc(long after) {
     return HE_OK;
 }
 
+// ================================================================================ allocator
+namespace {
+std::mutex g_alloc_mu;
+he_device_alloc_fn g_alloc_fn = nullptr;
+he_device_free_fn g_free_fn = nullptr;
+void *g_alloc_user = nullptr;
+std::atomic<long long> g_live{0};     // device blocks the library holds (either allocator)
+}  // namespace
+
+cudaError_t he_malloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return cudaSuccess;
+    he_device_alloc_fn fn;
+    void *user;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        fn = g_alloc_fn;
+        user = g_alloc_user;
+    }
+    if (fn) {
+        void *q = fn(bytes, user);
+        if (!q) return cudaErrorMemoryAllocation;
+        *p = q;
+        g_live++;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess && *p) g_live++;
+    return e;
+}
+
+cudaError_t he_free(void *p) {
+    if (!p) return cudaSuccess;
+    he_device_free_fn fn;
+    void *user;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        fn = g_free_fn;
+        user = g_alloc_user;
+    }
+    g_live--;
+    if (fn) {
+        // cudaFree waits for the device; a caller's allocator may hand the block to other work
+        // on any stream at once, so the library's work on it must be finished first
+        cudaError_t e = cudaDeviceSynchronize();
+        fn(p, user);
+        return e;
+    }
+    return cudaFree(p);
+}
+
+extern "C" int he_set_allocator(he_device_alloc_fn alloc, he_device_free_fn free_fn, void *user) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        he_set_error("he_set_allocator: give both functions, or neither for cudaMalloc / cudaFree");
+        return HE_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    const long long live = g_live.load();
+    if (live != 0) {
+        he_set_error("he_set_allocator: %lld device blocks of the library are still allocated; free every "
+                     "context and object first", live);
+        return HE_ESTATE;
+    }
+    g_alloc_fn = alloc;
+    g_free_fn = free_fn;
+    g_alloc_user = alloc ? user : nullptr;
+    return HE_OK;
+}
+
+extern "C" int64_t he_live_allocations(void) { return (int64_t)g_live.load(); }
+
 int he_capture_guard(const char *what) {
     if (!g_capturing) return HE_OK;
     g_capture_failed = true;                     // the graph would be incomplete: discard it
@@ -248,10 +319,10 @@ u64 h_galois(const he_ctx *ctx, int32_t r) {
 int Scratch::ensure(size_t w) {
     if (w <= words) return HE_OK;
     HE_TRY(he_capture_guard("scratch allocation"));
-    if (p) cudaFree(p);
+    if (p) he_free(p);
     p = nullptr;
     words = 0;
-    if (he_alloc_should_fail() || cudaMalloc(&p, w * 8) != cudaSuccess) {
+    if (he_alloc_should_fail() || he_malloc(&p, w * 8) != cudaSuccess) {
         cudaGetLastError();
         he_set_error("scratch allocation of %zu bytes failed", w * 8);
         return HE_ENOMEM;
@@ -260,7 +331,7 @@ int Scratch::ensure(size_t w) {
     return HE_OK;
 }
 Scratch::~Scratch() {
-    if (p) cudaFree(p);
+    if (p) he_free(p);
 }
 
 int upload_async(void *dst, const void *src, size_t bytes, cudaStream_t s) {
@@ -295,7 +366,7 @@ static int build_fbc(he_ctx *c, const std::vector<int> &src, const std::vector<i
     t.n_dst = nd;
     t.src_prime = src;
     t.dst_prime = dst;
-    HE_CHECK_CUDA(cudaMalloc(&t.d, h.size() * 8));
+    HE_CHECK_CUDA(he_malloc(&t.d, h.size() * 8));
     HE_CHECK_CUDA(cudaMemcpy(t.d, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
     return HE_OK;
 }
@@ -303,23 +374,23 @@ static int build_fbc(he_ctx *c, const std::vector<int> &src, const std::vector<i
 static void free_ctx(he_ctx *c) {
     if (!c) return;
     for (he_ct *t : c->poly_tmp) he_ct_free(t);
-    if (c->poly_block) cudaFree(c->poly_block);
-    if (c->d_err) cudaFree(c->d_err);
+    if (c->poly_block) he_free(c->poly_block);
+    if (c->d_err) he_free(c->d_err);
     if (c->parent) {                       // a fork owns only its scratch
         delete c;
         return;
     }
     for (auto &lv : c->modup)
         for (auto &t : lv)
-            if (t.d) cudaFree(t.d);
+            if (t.d) he_free(t.d);
     for (auto &t : c->moddown)
-        if (t.d) cudaFree(t.d);
+        if (t.d) he_free(t.d);
     for (auto &kv : c->keys)
-        if (kv.second.d) cudaFree(kv.second.d);
-    for (auto &kv : c->pk_cache) { cudaFree(kv.second.Kp); cudaFree(kv.second.Ppt); }
-    if (c->d_tables) cudaFree(c->d_tables);
-    if (c->d_consts) cudaFree(c->d_consts);
-    if (c->d_s) cudaFree(c->d_s);
+        if (kv.second.d) he_free(kv.second.d);
+    for (auto &kv : c->pk_cache) { he_free(kv.second.Kp); he_free(kv.second.Ppt); }
+    if (c->d_tables) he_free(c->d_tables);
+    if (c->d_consts) he_free(c->d_consts);
+    if (c->d_s) he_free(c->d_s);
     delete c;
 }
 
@@ -405,7 +476,7 @@ static int create(const he_params *pr, he_ctx **out) {
         itw2[2 * k + 1] = itws[k];
     }
     size_t words = 4 * (size_t)np + 8 * (size_t)np * n + 2 * (size_t)np;
-    if (cudaMalloc(&c->d_tables, words * 8) != cudaSuccess) {
+    if (he_malloc(&c->d_tables, words * 8) != cudaSuccess) {
         cudaGetLastError();
         free_ctx(c);
         he_set_error("table allocation failed");
@@ -475,7 +546,7 @@ static int create(const he_params *pr, he_ctx **out) {
             cst[np + 2 * Q + (size_t)l * 2 * Q + i] = v;
             cst[np + 2 * Q + (size_t)l * 2 * Q + Q + i] = h_shoup(v, qi);
         }
-    if (cudaMalloc(&c->d_consts, cst.size() * 8) != cudaSuccess) {
+    if (he_malloc(&c->d_consts, cst.size() * 8) != cudaSuccess) {
         cudaGetLastError();
         free_ctx(c);
         he_set_error("constant allocation failed");
@@ -493,17 +564,17 @@ static int create(const he_params *pr, he_ctx **out) {
     if (rc != HE_OK) { free_ctx(c); return rc; }
     // ---- secret key: ternary s, NTT form over every prime
     int64_t *s_int = nullptr;
-    if (cudaMalloc(&c->d_s, (size_t)np * n * 8) != cudaSuccess ||
-        cudaMalloc(&s_int, (size_t)n * 8) != cudaSuccess) {
+    if (he_malloc(&c->d_s, (size_t)np * n * 8) != cudaSuccess ||
+        he_malloc(&s_int, (size_t)n * 8) != cudaSuccess) {
         cudaGetLastError();
-        if (s_int) cudaFree(s_int);
+        if (s_int) he_free(s_int);
         free_ctx(c);
         he_set_error("secret allocation failed");
         return HE_ENOMEM;
     }
-    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
+    if (he_malloc(&c->d_err, sizeof(int)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(s_int);
+        he_free(s_int);
         free_ctx(c);
         he_set_error("error-word allocation failed");
         return HE_ENOMEM;
@@ -512,7 +583,7 @@ static int create(const he_params *pr, he_ctx **out) {
     if (rc == HE_OK) rc = k_reduce_int(c, s_int, c->d_s, np, Q, false, 0);
     if (rc == HE_OK) rc = ntt_poly(c, c->d_s, 0, 0, np, Q, 1, false, 0);
     cudaDeviceSynchronize();
-    cudaFree(s_int);
+    he_free(s_int);
     cudaError_t e = cudaGetLastError();
     if (rc != HE_OK || e != cudaSuccess) {
         if (e != cudaSuccess) he_set_error("context setup: %s", cudaGetErrorString(e));
@@ -561,7 +632,7 @@ static int gen_key(he_ctx *c, int id, const u64 *sp_eval, cudaStream_t s) {
     DeviceKey key;
     key.id = id;
     HE_TRY(he_capture_guard("key generation"));
-    if (cudaMalloc(&key.d, (size_t)c->dnum * 2 * limbs * 8) != cudaSuccess) {
+    if (he_malloc(&key.d, (size_t)c->dnum * 2 * limbs * 8) != cudaSuccess) {
         cudaGetLastError();
         he_set_error("key allocation failed (%zu bytes)", (size_t)c->dnum * 2 * limbs * 8);
         return HE_ENOMEM;
@@ -582,7 +653,7 @@ static int gen_key(he_ctx *c, int id, const u64 *sp_eval, cudaStream_t s) {
         if (rc == HE_OK) rc = k_keygen_combine(c, b, a, e_eval, c->d_s, sp_eval, j, s);
     }
     if (rc != HE_OK) {
-        cudaFree(key.d);
+        he_free(key.d);
         return rc;
     }
     c->root()->keys[id] = key;
@@ -674,7 +745,7 @@ extern "C" int he_ctx_fork(he_ctx *parent, he_ctx **out) {
     if (rc == HE_OK) rc = c->sc_conv.ensure(2 * (size_t)(c->L + 1) * c->n);
     if (rc == HE_OK) rc = c->sc_tmp.ensure(3 * ext);
     if (rc == HE_OK) rc = c->sc_tmp2.ensure(ext);
-    if (rc == HE_OK && (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+    if (rc == HE_OK && (he_malloc(&c->d_err, sizeof(int)) != cudaSuccess ||
                         cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)) {
         cudaGetLastError();
         c->d_err = nullptr;
@@ -831,7 +902,7 @@ extern "C" int he_ct_alloc(he_ctx *c, int level, he_ct **out) {
     ct->cap = ct->level = level;
     ct->pstride = (size_t)(level + 1) * c->n;
     if (he_capturing()) { delete ct; return he_capture_guard("ciphertext allocation"); }
-    if (he_alloc_should_fail() || cudaMalloc(&ct->d, 2 * ct->pstride * 8) != cudaSuccess) {
+    if (he_alloc_should_fail() || he_malloc(&ct->d, 2 * ct->pstride * 8) != cudaSuccess) {
         cudaGetLastError();
         delete ct;
         he_set_error("ciphertext allocation failed");
@@ -874,7 +945,7 @@ extern "C" int he_ct_wrap(he_ctx *c, void *dev_ptr, size_t bytes, int level, he_
 
 extern "C" void he_ct_free(he_ct *ct) {
     if (!ct) return;
-    if (ct->owned && ct->d) cudaFree(ct->d);
+    if (ct->owned && ct->d) he_free(ct->d);
     delete ct;
 }
 extern "C" int he_ct_level(const he_ct *ct) { return ct ? ct->level : HE_EINVAL; }
@@ -1011,7 +1082,7 @@ extern "C" int he_pt_import_coeffs(he_ctx *c, const int64_t *m, int level, doubl
     pt->level = level;
     pt->scale = scale;
     const size_t w = (size_t)(level + 1) * c->n;
-    if (cudaMalloc(&pt->d, w * 8) != cudaSuccess) {
+    if (he_malloc(&pt->d, w * 8) != cudaSuccess) {
         cudaGetLastError();
         delete pt;
         he_set_error("plaintext allocation failed");
@@ -1024,7 +1095,7 @@ extern "C" int he_pt_import_coeffs(he_ctx *c, const int64_t *m, int level, doubl
     if (rc == HE_OK) rc = k_to_mont(c, pt->d, level + 1, level + 1, 1, 0, 0);
     if (rc == HE_OK && cudaStreamSynchronize(0) != cudaSuccess) rc = HE_ECUDA;
     if (rc != HE_OK) {
-        cudaFree(pt->d);
+        he_free(pt->d);
         delete pt;
         return rc;
     }
@@ -1042,7 +1113,7 @@ extern "C" int he_pt_encode(he_ctx *c, const double *slots, size_t n_slots, int 
 
 extern "C" void he_pt_free(he_pt *pt) {
     if (!pt) return;
-    if (pt->d) cudaFree(pt->d);
+    if (pt->d) he_free(pt->d);
     delete pt;
 }
 

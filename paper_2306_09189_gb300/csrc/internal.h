@@ -35,6 +35,12 @@ void he_set_error(const char *fmt, ...);
 
 void he_count_launch(int k = 1);
 bool he_alloc_should_fail();             // test fault injection (he_debug_fail_alloc)
+// Every device allocation of the library goes through these: the caller's allocator when one
+// is installed (he_set_allocator), else cudaMalloc / cudaFree.  he_free(nullptr) is a no-op.
+cudaError_t he_malloc(void **p, size_t bytes);
+cudaError_t he_free(void *p);
+template <class T>
+inline cudaError_t he_malloc(T **p, size_t bytes) { return he_malloc((void **)p, bytes); }
 void he_set_pdl(int on);                 // programmatic dependent launch of every kernel (process-wide)
 int he_get_pdl();
 // True while this thread is capturing a CUDA graph (he_graph_begin .. he_graph_end): no device

@@ -2704,7 +2704,7 @@ int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u6
 
 double k_bench_modmul(const he_ctx *ctx, int blocks, int iters, cudaStream_t s) {
     u64 *sink;
-    if (cudaMalloc(&sink, 8) != cudaSuccess) return -1.0;
+    if (he_malloc(&sink, 8) != cudaSuccess) return -1.0;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -2719,6 +2719,6 @@ double k_bench_modmul(const he_ctx *ctx, int blocks, int iters, cudaStream_t s) 
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(sink);
+    he_free(sink);
     return (double)blocks * 256.0 * 2.0 * iters / (ms * 1e-3);
 }

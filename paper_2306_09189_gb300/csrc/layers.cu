@@ -276,7 +276,7 @@ int dev_alloc(T **p, size_t count) {
     *p = nullptr;
     if (count == 0) return HE_OK;
     HE_TRY(he_capture_guard("device allocation"));
-    if (he_alloc_should_fail() || cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+    if (he_alloc_should_fail() || he_malloc((void **)p, count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         he_set_error("device allocation of %zu bytes failed", count * sizeof(T));
@@ -367,8 +367,8 @@ struct RotSet {
     bool batched_ready = false;
 
     ~RotSet() {
-        cudaFree(D_all); cudaFree(u_all); cudaFree(conv_all); cudaFree(d_ip); cudaFree(d_md);
-        cudaFree(htmp); cudaFree(d_hsrc);
+        he_free(D_all); he_free(u_all); he_free(conv_all); he_free(d_ip); he_free(d_md);
+        he_free(htmp); he_free(d_hsrc);
     }
     size_t nq() const { return (size_t)level + 1; }
     size_t pw() const { return nq() * c->n; }
@@ -521,15 +521,15 @@ struct FusedStage {
 
     ~FusedStage();
     void free_pk() {
-        for (auto &g : pk_groups) { cudaFree(g.d_amt); cudaFree(g.d_ent); }
+        for (auto &g : pk_groups) { he_free(g.d_amt); he_free(g.d_ent); }
         if (!pk_refs.empty()) {
             he_ctx *r = c->root();
             std::lock_guard<std::mutex> lk(r->pk_mu);
             for (auto &key : pk_refs) {
                 auto it = r->pk_cache.find(key);
                 if (it != r->pk_cache.end() && --it->second.refs == 0) {
-                    cudaFree(it->second.Kp);
-                    cudaFree(it->second.Ppt);
+                    he_free(it->second.Kp);
+                    he_free(it->second.Ppt);
                     r->pk_cache.erase(it);
                 }
             }
@@ -573,18 +573,18 @@ struct FusedStage {
     int build_pk();
     void free_split() {
         for (auto &ch : chunks) {
-            cudaFree(ch.d_amt); cudaFree(ch.d_ent);
-            for (auto *t : ch.d_terms) cudaFree(t);
+            he_free(ch.d_amt); he_free(ch.d_ent);
+            for (auto *t : ch.d_terms) he_free(t);
         }
         chunks.clear();
-        cudaFree(U);
+        he_free(U);
         U = nullptr;
         split_ready = false;
     }
     size_t split_bytes() const;                       // device memory the split form needs
     int build_split(size_t cap_bytes, size_t plan_slot_bytes = 0);
     void free_groups() {
-        for (auto &g : groups) { cudaFree(g.d_amt); cudaFree(g.d_ent); }
+        for (auto &g : groups) { he_free(g.d_amt); he_free(g.d_ent); }
         groups.clear();
         Vg = 0;
     }
@@ -764,7 +764,7 @@ struct FusedLaunch {
     double pk_b = 0, pk_mm = 0;
     bool use_pk = false;
 
-    ~FusedLaunch() { cudaFree(d_grps); cudaFree(d_pk); free_split_tables(); }
+    ~FusedLaunch() { he_free(d_grps); he_free(d_pk); free_split_tables(); }
     // the stages of a batch share one plan (the same terms, sources and outputs; plaintexts and
     // their level): the image-batched split form applies
     bool splitm_ok() const {
@@ -864,9 +864,9 @@ struct FusedLaunch {
         return HE_OK;
     }
     void free_split_m_tables() {
-        for (auto *p : d_mgrps) cudaFree(p);
+        for (auto *p : d_mgrps) he_free(p);
         for (auto &v : d_mterms)
-            for (auto *p : v) cudaFree(p);
+            for (auto *p : v) he_free(p);
         d_mgrps.clear(); d_mterms.clear(); n_mgrp.clear(); mbytes.clear(); mmm.clear();
         splitm_built = false;
     }
@@ -898,14 +898,14 @@ struct FusedLaunch {
         return HE_OK;
     }
     void free_pk() {
-        cudaFree(d_pk);
+        he_free(d_pk);
         d_pk = nullptr;
         G_pk = 0;
         for (auto *f : st) f->free_pk();
     }
     // after a stage's plaintexts changed: drop the pre-keyed tables and tune again on next run
     void reset_pk() {
-        cudaFree(d_pk);
+        he_free(d_pk);
         d_pk = nullptr;
         G_pk = 0;
         if (use_pk) {
@@ -920,8 +920,8 @@ struct FusedLaunch {
         return k_ipmac(c, d_pk, G_pk, 1, mb, pk_b, pk_mm, fm ? fm : pk_form, 0, s);
     }
     void free_split_tables() {
-        for (auto *p : d_ugrps) cudaFree(p);
-        for (auto *p : d_rgrps) cudaFree(p);
+        for (auto *p : d_ugrps) he_free(p);
+        for (auto *p : d_rgrps) he_free(p);
         d_ugrps.clear(); d_rgrps.clear(); n_ugrp.clear(); n_rgrp.clear();
         ubytes.clear(); rbytes.clear(); rmm.clear();
         split_built = false;
@@ -947,7 +947,7 @@ struct FusedLaunch {
             }
             max_beta = std::max(max_beta, f->beta());
         }
-        cudaFree(d_grps);
+        he_free(d_grps);
         d_grps = nullptr;
         HE_TRY(dev_alloc(&d_grps, std::max<size_t>(1, h.size())));
         if (!h.empty()) HE_CHECK_CUDA(cudaMemcpy(d_grps, h.data(), h.size() * sizeof(fgrp), cudaMemcpyHostToDevice));
@@ -1138,7 +1138,7 @@ struct FusedLaunch {
             }
         } else if (bestSplit) {
             use_split = true;
-            cudaFree(d_grps);                         // the fused tables are not needed
+            he_free(d_grps);                         // the fused tables are not needed
             d_grps = nullptr;
         } else {
             HE_TRY(build(bestV));
@@ -1343,7 +1343,7 @@ int FusedStage::build_pk() {
                     if (rc == HE_OK)
                         rc = k_prekey(c, key ? key->d : nullptr, T.pt, level, pt_level, key ? beta_ : 0, e.Kp, e.Ppt, 0);
                     if (rc == HE_OK && cudaStreamSynchronize(0) != cudaSuccess) { cudaGetLastError(); rc = HE_ECUDA; }
-                    if (rc != HE_OK) { cudaFree(e.Kp); cudaFree(e.Ppt); return rc; }
+                    if (rc != HE_OK) { he_free(e.Kp); he_free(e.Ppt); return rc; }
                     it = r->pk_cache.emplace(ck, e).first;
                 }
                 it->second.refs++;
@@ -1391,7 +1391,7 @@ FusedStage::~FusedStage() {
     free_split();
     free_groups();
     free_pk();
-    cudaFree(D_all); cudaFree(facc); cudaFree(fconv); cudaFree(d_md); cudaFree(htmp); cudaFree(d_hsrc);
+    he_free(D_all); he_free(facc); he_free(fconv); he_free(d_md); he_free(htmp); he_free(d_hsrc);
 }
 
 int FusedStage::run(cudaStream_t s) {
@@ -1425,10 +1425,10 @@ struct he_pool {
     bool shared_masks = false;               // forks share the parent's mask plaintexts
     bool rot_ready = false;                  // per-rotation buffers of HE_PLAIN / HE_BATCHED
     ~he_pool() {
-        cudaFree(X); cudaFree(Wb); cudaFree(Yb); cudaFree(Zb); cudaFree(Sb);
-        cudaFree(rotS); cudaFree(rotH); cudaFree(rotV); cudaFree(rotC); cudaFree(rotD);
-        cudaFree(d_hterms); cudaFree(d_vterms);
-        if (!shared_masks) { cudaFree(hpts); cudaFree(vpts); }
+        he_free(X); he_free(Wb); he_free(Yb); he_free(Zb); he_free(Sb);
+        he_free(rotS); he_free(rotH); he_free(rotV); he_free(rotC); he_free(rotD);
+        he_free(d_hterms); he_free(d_vterms);
+        if (!shared_masks) { he_free(hpts); he_free(vpts); }
     }
 };
 
@@ -1935,7 +1935,7 @@ struct FactoredConv {
     std::map<int, int> rslot;                    // (u * N + a) -> rotation slot
     mac_term *d_terms = nullptr;
     bool rot_ready = false;
-    ~FactoredConv() { cudaFree(masks); cudaFree(Wm); cudaFree(Y); cudaFree(rt); cudaFree(Rrot); cudaFree(d_terms); }
+    ~FactoredConv() { he_free(masks); he_free(Wm); he_free(Y); he_free(rt); he_free(Rrot); he_free(d_terms); }
 };
 
 // the masks B_{h,h',t} (sorted by key) and the tap amounts
@@ -2662,7 +2662,7 @@ struct ConvSlot {                                // one image of a batch: buffer
     RotSet rot, grot;
     bool rot_ready = false;
     FusedStage fused, fusedG;                    // fusedG: BSGS giant stage
-    ~ConvSlot() { cudaFree(R); cudaFree(acc); cudaFree(Rrot); cudaFree(d_terms); cudaFree(Sb); cudaFree(Gb); }
+    ~ConvSlot() { he_free(R); he_free(acc); he_free(Rrot); he_free(d_terms); he_free(Sb); he_free(Gb); }
 };
 struct ConvBatch {
     std::vector<int> levels;
@@ -2673,9 +2673,9 @@ struct ConvBatch {
 he_conv::~he_conv() {
     batch.reset();
     fc.reset();
-    for (auto &kv : bias_by) cudaFree(kv.second);
-    cudaFree(R); cudaFree(Rrot); cudaFree(d_terms); cudaFree(acc); cudaFree(Sb); cudaFree(Gb);
-    if (!shared_pts) { cudaFree(pts); cudaFree(bias_pts); }
+    for (auto &kv : bias_by) he_free(kv.second);
+    he_free(R); he_free(Rrot); he_free(d_terms); he_free(acc); he_free(Sb); he_free(Gb);
+    if (!shared_pts) { he_free(pts); he_free(bias_pts); }
     delete pool;
     for (he_ct *x : mid) he_ct_free(x);
 }
@@ -2776,7 +2776,7 @@ static int conv_bias_for(he_conv *cv, int l, double out_scale, const u64 **out) 
             std::vector<int64_t> m;
             conv_bias_int(cv, v, out_scale, m);
             int rc = upload_addend(cv->c, m.data(), l - 1, d + (size_t)v * l * cv->c->n);
-            if (rc != HE_OK) { cudaFree(d); return rc; }
+            if (rc != HE_OK) { he_free(d); return rc; }
         }
         it = cv->bias_by.emplace(key, d).first;
     }
@@ -2960,7 +2960,7 @@ static int poly_temps(he_ctx *c, size_t need) {
     HE_TRY(he_capture_guard("polynomial temporaries"));
     for (he_ct *t : c->poly_tmp) he_ct_free(t);
     c->poly_tmp.clear();
-    if (c->poly_block) cudaFree(c->poly_block);
+    if (c->poly_block) he_free(c->poly_block);
     c->poly_block = nullptr;
     const size_t ps = (size_t)(c->L + 1) * c->n;
     HE_TRY(dev_alloc(&c->poly_block, need * 2 * ps));
@@ -3622,8 +3622,8 @@ struct he_linear {
         cudaDeviceSynchronize();
         steps.clear();
         stage1.reset();
-        cudaFree(R); cudaFree(w); cudaFree(mask); cudaFree(bias_pt); cudaFree(T[0]); cudaFree(T[1]);
-        cudaFree(acc); cudaFree(d_w); cudaFree(d_m);
+        he_free(R); he_free(w); he_free(mask); he_free(bias_pt); he_free(T[0]); he_free(T[1]);
+        he_free(acc); he_free(d_w); he_free(d_m);
     }
 };
 

@@ -1,9 +1,10 @@
 // Rescale that performs no device allocation at call time.
 //
-// he_rescale works in scratch buffers that the context allocates with cudaMalloc.  Some
-// callers cannot rely on that: an embedding application whose device memory is entirely
-// owned by its own allocator (a framework's caching pool holding all of HBM), or a process
-// running under a memory cap or policy that forbids driver allocations once it is set up.
+// he_rescale works in scratch buffers that the context allocates (cudaMalloc, or the allocator
+// installed with he_set_allocator).  Some callers cannot rely on that: an embedding application
+// whose device memory is entirely owned by its own allocator (a framework's caching pool holding
+// all of HBM), or a process running under a memory cap or policy that forbids driver
+// allocations once it is set up.
 // This variant keeps its scratch in a fixed device array that is part of the library image,
 // reserved on every GPU that loads the library until the process exits.  The caller still
 // passes the ciphertext, which is rescaled in place exactly like he_rescale does.

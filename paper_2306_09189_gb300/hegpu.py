@@ -56,7 +56,12 @@ class he_layout(ctypes.Structure):
         return chan, row0
 
 
+HE_DEVICE_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+HE_DEVICE_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
 _SIGS = {
+    "he_set_allocator": (c_int, [HE_DEVICE_ALLOC_FN, HE_DEVICE_FREE_FN, c_vp]),
+    "he_live_allocations": (ctypes.c_int64, []),
     "he_last_error": (ctypes.c_char_p, []),
     "he_version": (ctypes.c_char_p, []),
     "he_kernel_launches": (c_u64, []),
@@ -563,6 +568,27 @@ def he_conv_run(ctx, conv, ins, outs, mode=HE_PLAIN, stream=None):
     _check(load().he_conv_run(ctx, conv, _vp_array(ins), _vp_array(outs), mode, stream_ptr(stream)))
 
 
+def he_hconv2d(ctx, layout, ins, W, bias, stride, pad, mode, outs, stream=None):
+    """One-call convolution (plan, rotation keys, run, release); returns the output layout.
+    outs: allocated output handles, one per output shard."""
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    co, ci, kh, kw = W.shape
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.float64)
+    lay = he_layout()
+    _check(load().he_hconv2d(ctx, ctypes.byref(layout), _vp_array(ins), _p(W, F64P),
+                             None if b is None else _p(b, F64P), co, ci, kh, kw, stride, pad, mode,
+                             ctypes.byref(lay), _vp_array(outs), stream_ptr(stream)))
+    return lay
+
+
+def he_havgpool(ctx, layout, ins, mode, outs, stream=None):
+    """One-call 2x2 average pool; returns the output layout."""
+    lay = he_layout()
+    _check(load().he_havgpool(ctx, ctypes.byref(layout), _vp_array(ins), ctypes.byref(lay), _vp_array(outs),
+                              mode, stream_ptr(stream)))
+    return lay
+
+
 def he_conv_keyswitches(conv):
     return int(_check(load().he_conv_keyswitches(conv)))
 
@@ -766,3 +792,45 @@ def he_trace_stop():
     ms, n, b, m = c_double(), c_u64(), c_double(), c_double()
     _check(load().he_trace_stop(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b), ctypes.byref(m)))
     return dict(ms=ms.value, launches=int(n.value), bytes=b.value, mulmods=m.value)
+
+
+# ----------------------------------------------------------------------------- device memory
+_allocator = None          # the installed callbacks, kept alive while the library may call them
+
+
+def he_set_allocator(alloc=None, free=None):
+    """Install Python callables alloc(nbytes) -> device pointer (int, 0 on failure) and
+    free(ptr) as the library's device allocator; no arguments restores cudaMalloc / cudaFree."""
+    global _allocator
+    if alloc is None and free is None:
+        _check(load().he_set_allocator(HE_DEVICE_ALLOC_FN(), HE_DEVICE_FREE_FN(), None))
+        _allocator = None
+        return
+
+    def _a(nbytes, _user):
+        try:
+            return int(alloc(int(nbytes))) or None
+        except Exception:                     # out of memory: the library reports HE_ENOMEM
+            return None
+
+    def _f(ptr, _user):
+        free(int(ptr))
+    cbs = (HE_DEVICE_ALLOC_FN(_a), HE_DEVICE_FREE_FN(_f))
+    _check(load().he_set_allocator(cbs[0], cbs[1], None))
+    _allocator = cbs
+
+
+def he_live_allocations():
+    return int(load().he_live_allocations())
+
+
+def use_torch_allocator():
+    """Take every device block the library needs from PyTorch's caching allocator (on the
+    current device and stream), so that the library's memory is part of torch's pool."""
+    import torch
+    he_set_allocator(lambda nbytes: torch.cuda.caching_allocator_alloc(nbytes),
+                     lambda ptr: torch.cuda.caching_allocator_delete(ptr))
+
+
+def use_default_allocator():
+    he_set_allocator()

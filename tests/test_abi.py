@@ -79,3 +79,14 @@ def test_header_constants_match_the_binding():
     assert len(defs) >= 15 and "HE_KEY_STREAM_SPLITM" in defs
     for name, value in defs.items():
         assert getattr(H, name) == int(value), name
+
+
+def test_allocator_hook_arguments_are_checked():
+    """he_set_allocator (host only): both functions or neither."""
+    from paper_2306_09189_gb300 import hegpu as H
+    L = H.load()
+    with pytest.raises(H.HEError) as e:
+        H._check(L.he_set_allocator(H.HE_DEVICE_ALLOC_FN(lambda n, u: None), H.HE_DEVICE_FREE_FN(), None))
+    assert e.value.code == H.HE_EINVAL
+    assert H.he_live_allocations() == 0
+    H.use_default_allocator()                     # nothing live: accepted
