@@ -198,6 +198,7 @@ def run_block(args, ws, rank, local):
     from paper_2306_09189_gb300 import host
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
+    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS}[args.ntt])
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
@@ -384,6 +385,7 @@ def run_head(args, ws, rank, local):
     from paper_2306_09189_gb300 import host
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
+    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS}[args.ntt])
     N = H.he_ctx_info(ctx)["slots"]
     level, n_img = 4, 8
     x0, W, b = workloads.resnet_head(0)
@@ -505,6 +507,7 @@ def run_stem(args, ws, rank, local):
     from paper_2306_09189_gb300 import host
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
+    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS}[args.ntt])
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
@@ -629,6 +632,9 @@ def main():
                          "baby-step giant-step")
     ap.add_argument("--bsgs-k", type=int, default=0,
                     help="giant stride (blocks) of the baby-step giant-step convolutions; 0 = cost model")
+    ap.add_argument("--ntt", default="twopass", choices=["onepass", "onepass8", "twopass"],
+                    help="NTT at n = 2^16: one launch per limb on a 16-CTA cluster (onepass), on an "
+                         "8-CTA cluster (onepass8), or the two-pass column/row form")
     ap.add_argument("--poly", default="ps", choices=["ps", "tree"],
                     help="GELU evaluation: Paterson-Stockmeyer (default) or the binary tree")
     ap.add_argument("--workload", default="cifar-layer",
@@ -659,6 +665,7 @@ def main():
 
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
+    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS}[args.ntt])
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
@@ -840,7 +847,7 @@ def main():
                                                       "relinearised products of one operand level "
                                                       "batched",
                        "key_switches_per_step": ks_per_step, "key_stream": args.key_stream,
-                       "cuda_graph": not args.no_graph,
+                       "ntt": args.ntt, "cuda_graph": not args.no_graph,
                        "autotuner": H.he_ctx_tuning_log(ctx).strip().splitlines(),
                        "rotations": int(len(rots)), "relins": products, "input_level": LEVEL,
                        "gelu": "degree-16 Chebyshev, %s" % ("Paterson-Stockmeyer" if args.poly == "ps" else "binary tree"),

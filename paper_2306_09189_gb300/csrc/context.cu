@@ -738,6 +738,7 @@ extern "C" int he_ctx_fork(he_ctx *parent, he_ctx **out) {
     c->d_consts = r->d_consts;
     c->d_s = r->d_s;
     c->key_stream = parent->key_stream;
+    c->ntt_form = parent->ntt_form;
     c->parent = r;
     const size_t ext = (size_t)(c->L + 1 + c->K) * c->n;
     int rc = c->sc_digits.ensure((size_t)c->dnum * ext);
@@ -790,6 +791,10 @@ extern "C" int he_ctx_set_option(he_ctx *c, int option, int value) {
         c->key_stream = value;
         return HE_OK;
     }
+    if (option == HE_OPT_NTT && (value == HE_NTT_ONEPASS || value == HE_NTT_TWOPASS || value == HE_NTT_ONEPASS8)) {
+        c->ntt_form = value;
+        return HE_OK;
+    }
     he_set_error("he_ctx_set_option: unknown option %d or value %d", option, value);
     return HE_EINVAL;
 }
@@ -798,6 +803,7 @@ extern "C" int he_ctx_get_option(const he_ctx *c, int option, int *value) {
     if (!c || !value) { he_set_error("he_ctx_get_option: null argument"); return HE_EINVAL; }
     if (option == HE_OPT_KEY_STREAM) { *value = c->key_stream; return HE_OK; }
     if (option == HE_OPT_PDL) { *value = he_get_pdl(); return HE_OK; }
+    if (option == HE_OPT_NTT) { *value = c->ntt_form; return HE_OK; }
     he_set_error("he_ctx_get_option: unknown option %d", option);
     return HE_EINVAL;
 }

@@ -360,6 +360,170 @@ __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job, Rescale
     }
 }
 
+// ------------------------------------------------------------------------------ one-pass NTT
+// n = 2^16 in ONE launch: each limb is transformed by a cluster of CL CTAs (CL = 8 or 16, 16 words
+// per thread), so the data crosses HBM/L2 once each way instead of twice.  View the limb as CL
+// blocks of BLK = 2^16 / CL words, one per CTA.  Forward (Cooley-Tukey, butterfly distances
+// 2^15 .. 1, four stages per radix-16 round):
+//   A  CTA r, thread t holds the 16 words b0 + k 2^12 (b0 = r T + t, T = BLK / 16 threads): the
+//      four stages of distance >= 4096, which mix the blocks, run in registers;
+//   -> every word is stored into the shared memory of the CTA owning its block (distributed
+//      shared memory across the cluster), then one cluster barrier;
+//   B  offsets (t >> 8) 4096 + (t & 255) + 256 k     distances 2048 .. 256
+//   C  offsets (t >> 4) 256 + (t & 15) + 16 k        distances 128 .. 16
+//   D  offsets 16 t + k                              distances 8 .. 1, then stored contiguously
+// with a shared-memory transpose between rounds (padded one word in 16: conflict-free).  The
+// inverse (Gentleman-Sande) runs D, C, B on the CTA's own block, scatters into the layout of A
+// on the destination CTAs, and finishes with A and the factor n^-1.  Same words as the two-pass
+// ntt16_cols / ntt16_rows pair.
+template <int CL> struct NcShape {
+    static constexpr int BLK = 65536 / CL;       // words per CTA
+    static constexpr int T = BLK / 16;           // threads per CTA
+    static constexpr int SMEM = BLK + BLK / 16;  // padded block (also holds round A's [16][T] layout)
+    static constexpr int PER = BLK / 4096;       // 4096-word halves per block (2 or 1)
+    static constexpr int MINB = CL == 8 ? 1 : 3; // resident CTAs per SM the register budget targets
+};
+
+__device__ __forceinline__ int pad16(int b) { return b + (b >> 4); }
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of `local` (this CTA's shared memory) in the CTA of cluster rank `rank`
+__device__ __forceinline__ unsigned dsmem_addr(const void *local, unsigned rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void dsmem_st(unsigned addr, u64 v) {
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+
+// one radix-16 round on the CTA's block: 16 words at sm[pad16(b + (k << ls))]
+template <bool INV>
+__device__ __forceinline__ void nc_round(u64 (&x)[16], u64 *sm, int b, int ls, int gbase,
+                                         const ulonglong2 *__restrict__ W, u64 q, u64 q2) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) x[k] = sm[pad16(b + (k << ls))];
+    reg_pass<INV>(x, gbase + b, ls, 16, 4, W, q, q2);
+#pragma unroll
+    for (int k = 0; k < 16; k++) sm[pad16(b + (k << ls))] = x[k];
+}
+
+template <bool INV, bool RS, int CL>
+__global__ void __launch_bounds__(NcShape<CL>::T, NcShape<CL>::MINB)
+    ntt16_cluster(KP kp, ntt_job job, RescaleFuse F) {
+    using S = NcShape<CL>;
+    pdl_wait();
+    extern __shared__ u64 sm[];
+    const int p = blockIdx.z;
+    const int limb = job_limb(job, blockIdx.y, p);   // one limb per cluster: all its CTAs agree
+    if (limb < 0) return;
+    const int pr = prime_of(kp, limb, job.nq);
+    const u64 q = kp.q[pr], q2 = 2 * q;
+    const int t = threadIdx.x;
+    const int r = blockIdx.x;                         // cluster rank: the grid is one cluster wide
+    const int blk = r * S::BLK;                       // this CTA's block in rounds B, C, D
+    const int b0 = r * S::T + t;                      // round A: words b0 + (k << 12), b0 < 4096
+    u64 *a = job.base + (size_t)p * job.poly_stride + (size_t)limb * kp.n;
+    const ulonglong2 *W = (const ulonglong2 *)(INV ? kp.itw2 : kp.tw2) + (size_t)pr * kp.n;
+    u64 x[16];
+    if (!INV) {
+        cluster_arrive_relaxed();                     // this CTA has started
+        if (RS) {
+            const u64 *top = F.c + (size_t)p * F.ps + (size_t)F.level * kp.n;
+            const u64 ql = kp.q[F.level], mu = kp.mu[pr];
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = centred_mod(top[b0 + (k << 12)], ql, q, mu);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; k++) x[k] = a[b0 + (k << 12)];
+        }
+        reg_pass<false>(x, b0, 12, 16, 4, W, q, q2);
+        cluster_wait();                               // every CTA has started: remote stores are safe
+        // word b0 + (k << 12) lies in block k / PER at offset b0 + (k mod PER) 4096
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+            dsmem_st(dsmem_addr(&sm[pad16(b0 + ((k % S::PER) << 12))], k / S::PER), x[k]);
+        cluster_arrive();
+        cluster_wait();                               // the block is complete in this CTA
+        nc_round<false>(x, sm, ((t >> 8) << 12) + (t & 255), 8, blk, W, q, q2);
+        __syncthreads();
+        nc_round<false>(x, sm, ((t >> 4) << 8) + (t & 15), 4, blk, W, q, q2);
+        __syncthreads();
+        const int bD = t << 4;
+#pragma unroll
+        for (int k = 0; k < 16; k++) x[k] = sm[pad16(bD + k)];
+        reg_pass<false>(x, blk + bD, 0, 16, 4, W, q, q2);
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const u64 v = x[k] >= q2 ? x[k] - q2 : x[k];
+            x[k] = v >= q ? v - q : v;
+        }
+        if (RS) {
+            ulonglong2 *cr = (ulonglong2 *)(F.c + (size_t)p * F.ps + (size_t)limb * kp.n + blk + bD);
+            const u64 iv = F.inv[pr], ivs = F.invs[pr];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                ulonglong2 v = cr[k];
+                v.x = mul_shoup(sub_mod(v.x, x[2 * k], q), iv, ivs, q);
+                v.y = mul_shoup(sub_mod(v.y, x[2 * k + 1], q), iv, ivs, q);
+                cr[k] = v;
+            }
+        } else {
+            ulonglong2 *o = (ulonglong2 *)(a + blk + bD);
+#pragma unroll
+            for (int k = 0; k < 8; k++) o[k] = make_ulonglong2(x[2 * k], x[2 * k + 1]);
+        }
+    } else {
+        const int bD = t << 4;
+        const ulonglong2 *in = (const ulonglong2 *)(a + blk + bD);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const ulonglong2 v = in[k];
+            x[2 * k] = v.x;
+            x[2 * k + 1] = v.y;
+        }
+        reg_pass<true>(x, blk + bD, 0, 16, 4, W, q, q2);
+#pragma unroll
+        for (int k = 0; k < 16; k++) sm[pad16(bD + k)] = x[k];
+        __syncthreads();
+        nc_round<true>(x, sm, ((t >> 4) << 8) + (t & 15), 4, blk, W, q, q2);
+        __syncthreads();
+        const int bB = ((t >> 8) << 12) + (t & 255);
+#pragma unroll
+        for (int k = 0; k < 16; k++) x[k] = sm[pad16(bB + (k << 8))];
+        cluster_arrive();                             // this CTA's block is read: it may be overwritten
+        reg_pass<true>(x, blk + bB, 8, 16, 4, W, q, q2);
+        cluster_wait();
+        // word blk + bB + 256 k is word w + (j << 12) of round A's layout, w = (t & 255) + 256 k
+        // and j = r PER + (t >> 8): thread w mod T of CTA w / T, slot j
+        const int j = r * S::PER + (t >> 8);
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const int w = (t & 255) + (k << 8);
+            dsmem_st(dsmem_addr(&sm[j * S::T + w % S::T], w / S::T), x[k]);
+        }
+        cluster_arrive();
+        cluster_wait();
+#pragma unroll
+        for (int k = 0; k < 16; k++) x[k] = sm[k * S::T + t];
+        reg_pass<true>(x, b0, 12, 16, 4, W, q, q2);
+        const u64 ni = kp.ninv[pr], nis = kp.ninvs[pr];
+#pragma unroll
+        for (int k = 0; k < 16; k++) {
+            const u64 v = x[k] * ni - __umul64hi(x[k], nis) * q;
+            a[b0 + (k << 12)] = v >= q ? v - q : v;
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------ range check
 // counts the words of a ciphertext (both polynomials, limbs 0..level) that are not below their
 // prime: a device-side sanitizer that records instead of trapping
@@ -1722,9 +1886,63 @@ static cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
         }                                                     \
     } while (0)
 
+// the one-pass cluster NTT of a 2^16 ring: cluster dimension at launch (16 is a non-portable
+// size the kernel opts in to), dynamic shared memory opted in once per device
+template <bool INV, bool RS, int CL>
+static int ntt_cluster(const he_ctx *ctx, const ntt_job &job, const RescaleFuse &F, cudaStream_t s) {
+    using S = NcShape<CL>;
+    static std::mutex mu;
+    static bool ready[64] = {};
+    int dev = 0;
+    HE_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { he_set_error("device ordinal %d out of range", dev); return HE_EINVAL; }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!ready[dev]) {
+            HE_CHECK_CUDA(cudaFuncSetAttribute(ntt16_cluster<INV, RS, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               S::SMEM * (int)sizeof(u64)));
+            if (CL > 8)
+                HE_CHECK_CUDA(cudaFuncSetAttribute(ntt16_cluster<INV, RS, CL>,
+                                                   cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            ready[dev] = true;
+        }
+    }
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = g_pdl.load();
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = CL;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(CL, job.nl, job.npoly);
+    cfg.blockDim = dim3(S::T);
+    cfg.dynamicSmemBytes = S::SMEM * sizeof(u64);
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    cudaLaunchKernelEx(&cfg, ntt16_cluster<INV, RS, CL>, ctx->kp, job, F);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+template <bool INV, bool RS>
+static int ntt_onepass_launch(const he_ctx *ctx, const ntt_job &job, const RescaleFuse &F, cudaStream_t s) {
+    return ctx->ntt_form == HE_NTT_ONEPASS8 ? ntt_cluster<INV, RS, 8>(ctx, job, F, s)
+                                            : ntt_cluster<INV, RS, 16>(ctx, job, F, s);
+}
+
+static bool ntt_onepass(const he_ctx *ctx) { return ctx->logn == 16 && ctx->ntt_form != HE_NTT_TWOPASS; }
+
 int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
     if (job.nl <= 0 || job.npoly <= 0) return HE_OK;
     const int R = ctx->n / ROW;
+    if (ntt_onepass(ctx)) {
+        const double limbs = (double)job.nl * job.npoly;
+        TraceScope tr("ntt", s, limbs * 2.0 * ctx->n * 8, limbs * (ctx->n / 2) * ctx->logn);
+        return inverse ? ntt_onepass_launch<true, false>(ctx, job, RescaleFuse{}, s)
+                       : ntt_onepass_launch<false, false>(ctx, job, RescaleFuse{}, s);
+    }
     if (ctx->logn >= 12 && ctx->logn <= 16) {
         const double limbs = (double)job.nl * job.npoly;
         TraceScope tr("ntt", s, limbs * 2.0 * ctx->n * 8, limbs * (ctx->n / 2) * ctx->logn);
@@ -2683,6 +2901,7 @@ int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u6
         const int R = ctx->n / ROW, TC = 4096 / R;
         dim3 gA(ROW / TC, level, 2 * m), gB(R / 16, level, 2 * m);
         TraceScope tr("rescale", s, (double)m * level * ctx->n * 8 * 6, (double)m * level * ctx->n * 2);
+        if (ntt_onepass(ctx)) return ntt_onepass_launch<false, true>(ctx, tj, F, s);
         pdl_launch(ntt16_cols<false, true>, gA, 256, 0, s, ctx->kp, tj, F);
         LAUNCH_CHECK();
         pdl_launch(ntt16_rows<false, true>, gB, 256, 0, s, ctx->kp, tj, F);

@@ -213,21 +213,57 @@ def pair20():
     g.close()
 
 
+@pytest.mark.parametrize("form", ["onepass", "onepass8", "twopass"])
 @pytest.mark.parametrize("level", [19, 12])
-def test_full_ring_rotation_bit_exact(pair20, level):
+def test_full_ring_rotation_bit_exact(pair20, level, form):
+    """At n = 2^16 both NTT forms (one launch per limb on a CTA cluster, or two passes) give the
+    oracle's words through a key switch (INTT, ModUp, NTT, ModDown) and a rescale."""
     from paper_2306_09189_gb300 import hegpu as H
     from tests._hegpu_util import assert_ct_equal
     o, g = pair20
-    ct, z = _rand_ct(o, level, 200 + level)
-    o.gen_rotation_key(33)
-    H.he_keygen_rotations(g.h, [33])
-    out = g.ct(level)
-    c = g.upload(ct)
-    H.he_rotate(g.h, c, 33, out)
-    assert_ct_equal(g.download(out), o.rotate(ct, 33))
-    assert np.abs(H.he_decrypt(g.h, out, o.N) - np.roll(z, -33)).max() < 2.0 ** -20
-    H.he_rescale(g.h, c)
-    assert_ct_equal(g.download(c), o.rescale(ct))
+    H.he_ctx_set_option(g.h, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8,
+                                            "twopass": H.HE_NTT_TWOPASS}[form])
+    try:
+        ct, z = _rand_ct(o, level, 200 + level)
+        o.gen_rotation_key(33)
+        H.he_keygen_rotations(g.h, [33])
+        out = g.ct(level)
+        c = g.upload(ct)
+        H.he_rotate(g.h, c, 33, out)
+        assert_ct_equal(g.download(out), o.rotate(ct, 33))
+        assert np.abs(H.he_decrypt(g.h, out, o.N) - np.roll(z, -33)).max() < 2.0 ** -20
+        H.he_rescale(g.h, c)
+        assert_ct_equal(g.download(c), o.rescale(ct))
+    finally:
+        H.he_ctx_set_option(g.h, H.HE_OPT_NTT, H.HE_NTT_TWOPASS)
+
+
+def test_full_ring_ntt_forms_give_the_same_words(pair20):
+    """Forward in one form, inverse in the other, is the identity on random residues (so the two
+    forward transforms agree word for word), and encryption matches the oracle in both forms."""
+    from paper_2306_09189_gb300 import hegpu as H
+    from tests._hegpu_util import assert_ct_equal
+    o, g = pair20
+    level = 19
+    rng = np.random.default_rng(1919)
+    q = np.array([int(v) for v in o.q[:level + 1]], dtype=np.uint64)
+    words = (rng.integers(0, 2 ** 63, (2, level + 1, o.n), dtype=np.uint64) % q[None, :, None])
+    one, two, eight = H.HE_NTT_ONEPASS, H.HE_NTT_TWOPASS, H.HE_NTT_ONEPASS8
+    try:
+        for fwd, inv in ((one, two), (two, one), (one, one), (eight, two), (two, eight)):
+            x = g.ct(level)
+            H.he_ctx_set_option(g.h, H.HE_OPT_NTT, fwd)
+            H.he_ct_import_coeffs(x, words, level, o.pr.scale)
+            H.he_ctx_set_option(g.h, H.HE_OPT_NTT, inv)
+            assert np.array_equal(g.download(x), words)
+        m = rng.integers(-2 ** 40, 2 ** 40, o.n, dtype=np.int64)
+        for form in (one, two, eight):
+            H.he_ctx_set_option(g.h, H.HE_OPT_NTT, form)
+            x = g.ct(level)
+            H.he_encrypt_coeffs(g.h, m, level, o.pr.scale, 77, x)
+            assert_ct_equal(g.download(x), o.encrypt_coeffs(m, level, o.pr.scale, 77))
+    finally:
+        H.he_ctx_set_option(g.h, H.HE_OPT_NTT, two)
 
 
 @pytest.mark.parametrize("log_n", [10, 11, 13])
