@@ -9,8 +9,11 @@ working set is far larger than L2 and no flush is needed.
 
 Prints one JSON line (rank 0).  value = key switches per second (rotations + relins) over all
 ranks; ms_per_step = layer latency.  The batched mode is the headline; the plain
-per-ciphertext path is timed beside it.  N > 1 runs independent replicas (the layer does
-not shard across GPUs).  --impl reference times the CPU oracle instead.
+per-ciphertext path is timed beside it, and the convolution alone (`conv_only`).  At N = 1 the
+line also carries the batched ResNet block (`resnet_block`: 4 images at mixed levels, batched
+vs plain) and the ImageNet stem (`imagenet_stem`), each run on its own context afterwards, and
+the oracle on all host cores and on one (`cpu_baseline`).  N > 1 runs independent replicas
+(the layer does not shard across GPUs).  --impl reference times the CPU oracle instead.
 """
 import argparse
 import json
@@ -158,6 +161,28 @@ def cpu_baseline(sample_rotations=2):
                       "at n=2^16, level 19; %.1f s" % (len(amounts), dt)}
 
 
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_single_thread(sample_rotations=3):
+    """The same oracle sample on one host core (OpenMP limited to one thread in a child process)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", "import json, bench; print(json.dumps(bench.cpu_baseline(%d)))"
+                        % sample_rotations], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode:
+        return {"error": r.stderr.strip().splitlines()[-1:] or ["failed"]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -188,7 +213,7 @@ BLOCK_WORKLOAD = ("resnet basic block: 64x56x56 (64x64 frame, 8 shards of 8 chan
                   "8/12/16/19, 2N=2^16, 20+5 primes")
 
 
-def run_block(args, ws, rank, local):
+def run_block(args, ws, rank, local, emit=True):
     """The batched form: one ResNet basic block over a batch of images at mixed levels.  Each
     conv of the batch is ONE fused-kernel launch over all images (groups of every image and
     level side by side); the GELU runs per ciphertext; the whole step is one CUDA graph."""
@@ -360,7 +385,8 @@ def run_block(args, ws, rank, local):
                 "check": {"image": 0, "input_level": levels[0], "max_err_rel_range": err,
                           "tolerance": 2.0 ** -20},
                 "gpu_launches": int(launches_f), "roofline": roof, "clocks": clk}
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
     H.he_ctx_check(ctx, stream)
     H.he_graph_destroy(graph)
     H.he_conv_destroy(conv1)
@@ -368,6 +394,7 @@ def run_block(args, ws, rank, local):
     for ct in xs + y1 + y2:
         H.he_ct_free(ct)
     H.he_ctx_destroy(ctx)
+    return line if rank == 0 else None
 
 
 HEAD_WORKLOAD = ("resnet head: 64x8x8 feature map (one shard, 8 copies), pool-linear to 10 logits "
@@ -496,7 +523,7 @@ STEM_WORKLOAD = ("imagenet stem: 3x224x224 in channel shards (256 frame, 2 shard
                  "-> 112x112x64 (32 shards) -> 2x2 avgpool -> 56x56x64 (8 shards); 2N=2^16, 20+5 primes")
 
 
-def run_stem(args, ws, rank, local):
+def run_stem(args, ws, rank, local, emit=True):
     """The ImageNet-shaped sharded stem (config 3): the factored channel-shard conv with stride 2
     (the select runs on 128 channel shards), then the 2x2 average pool; one CUDA graph per step.
     The per-rotation modes would hold every rotated shard of the select (hundreds of GB), so
@@ -600,7 +627,8 @@ def run_stem(args, ws, rank, local):
                 "plain": None, "plain_note": "per-rotation modes would hold every rotated shard of the 128-shard select",
                 "check": {"max_err_rel_range": err, "tolerance": 2.0 ** -20},
                 "gpu_launches": int(launches), "roofline": roof, "clocks": clk}
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
     H.he_ctx_check(ctx, stream)
     H.he_graph_destroy(gk)
     H.he_graph_destroy(graph)
@@ -609,6 +637,7 @@ def run_stem(args, ws, rank, local):
     for ct in xs + y + z:
         H.he_ct_free(ct)
     H.he_ctx_destroy(ctx)
+    return line if rank == 0 else None
 
 
 def main():
@@ -619,6 +648,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--trace", default="ipmac", help="kernel whose launches the roofline uses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the ResNet-block and ImageNet-stem figures the default line carries")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: same ring, 2-channel 32x32 conv (17 rotations, ~2 GB of keys)")
     ap.add_argument("--profile-step", action="store_true",
@@ -778,6 +809,7 @@ def main():
     ks_bsgs = H.he_conv_keyswitches(conv_b) + products
     cur["conv"] = conv
 
+
     # end to end through the C ABI with host buffers: pinned host ciphertext in, result out
     xin = H.he_ct_export_coeffs(ctx, x, n)
     h_in = torch.empty(xin.size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64).reshape(xin.shape)
@@ -816,6 +848,28 @@ def main():
     barrier()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
 
+    def conv_only_ms(cv, k):
+        """The convolution alone (rotations, MAC, rescale, bias), K runs as one graph."""
+        H.he_conv_run(ctx, cv, [x], [y], H.HE_FUSED, stream)
+        barrier()
+        H.he_graph_begin(ctx, stream)
+        for _ in range(k):
+            H.he_conv_run(ctx, cv, [x], [y], H.HE_FUSED, stream)
+        g = H.he_graph_end(ctx, stream)
+        for _ in range(args.warmup):
+            H.he_graph_launch(g, stream)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.he_graph_launch(g, stream)
+        e1.record(stream)
+        barrier()
+        H.he_graph_destroy(g)
+        return max_over_ranks(e0.elapsed_time(e1), ws) / k
+
+    conv_ms_bs = conv_only_ms(conv_b, args.steps)
+    conv_ms = conv_only_ms(conv, args.steps)
+
     peaks, src = _peaks()
     roof = None
     if tr and tr["launches"]:
@@ -828,13 +882,15 @@ def main():
                 "peak_source": src, "launches": tr["launches"], "ms_per_launch": per_launch_ms,
                 "share_of_step": tr["ms"] / (ms_b * args.steps)}
     mm_rate = H.he_bench_modmul(ctx, 152 * 8, 2048)
+    mac_rate = H.he_bench_mac(ctx, 152 * 8, 4096)
     if roof is not None and tr.get("mulmods"):
         # integer pipe: the library counts the kernel's 64x64->128-bit multiply-accumulates; the
-        # microbenchmark's dependent Montgomery products each take three such products
+        # peak is the measured throughput of that operation with 8 independent chains per thread
         mm = tr["mulmods"] / tr["launches"] / (roof["ms_per_launch"] * 1e-3)
-        roof["int"] = {"unit": "64-bit products/s", "achieved": mm, "peak": 3.0 * mm_rate,
-                       "frac": mm / (3.0 * mm_rate),
-                       "peak_source": "he_bench_modmul: dependent Montgomery products at full occupancy, x3"}
+        roof["int"] = {"unit": "64x64->128-bit multiply-accumulates/s", "achieved": mm, "peak": mac_rate,
+                       "frac": mm / mac_rate,
+                       "peak_source": "he_bench_mac: 8 independent chains per thread, 152 x 8 blocks of 256 "
+                                      "threads (measured on this GPU in this run)"}
 
     if rank == 0:
         line = {
@@ -869,11 +925,13 @@ def main():
             "gpu_launches": int(launches_b),
             "roofline": roof,
             "modmul_microbench_per_s": mm_rate,
+            "mac_microbench_per_s": mac_rate,
             "clocks": clk,
+            "conv_only": {"ms": conv_ms, "bsgs_ms": conv_ms_bs,
+                          "gelu_ms": ms_b - conv_ms, "key_switches": int(len(rots)),
+                          "note": "the convolution alone (hoisted rotations, fused MAC, one ModDown, "
+                                  "rescale, bias), as one graph of K runs; gelu_ms = step - conv"},
         }
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(48)          # ~10-15 s of oracle work
-        print(json.dumps(line), flush=True)
     H.he_ctx_check(ctx, stream)
     H.he_graph_destroy(graph)
     H.he_graph_destroy(graph_e2e)
@@ -882,8 +940,34 @@ def main():
     for c in (x, y, xe):
         H.he_ct_free(c)
     H.he_ctx_destroy(ctx)
+    if ws == 1 and not args.no_extra:
+        # the batched ResNet block (the survey's headline for batched vs plain) and the ImageNet
+        # stem, each on its own context after the layer's is released
+        for key, fn, k in (("resnet_block", run_block, 5), ("imagenet_stem", run_stem, 3)):
+            sub = argparse.Namespace(**vars(args))
+            sub.steps, sub.warmup, sub.trace, sub.small, sub.profile_step = k, 3, "ipmac", False, False
+            line[key] = _extra_summary(fn(sub, ws, rank, local, emit=False))
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(48)          # ~10 s of oracle work on every core
+            line["cpu_baseline"]["cpu_model"] = cpu_model()
+            line["cpu_baseline"]["single_thread"] = cpu_baseline_single_thread(3)
+        print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def _extra_summary(d):
+    """The figures of a secondary workload's line that the headline line carries."""
+    if d is None:
+        return None
+    keep = ("ms_per_step", "value", "unit", "steps", "plain", "check", "roofline", "clocks", "gpu_launches")
+    out = {k: d[k] for k in keep if k in d}
+    out["workload"] = d["config"]["workload"]
+    for k in ("key_switches_per_step", "input_levels", "setup_s", "l2", "conv_keyswitches_per_image", "shards"):
+        if k in d["config"]:
+            out[k] = d["config"][k]
+    return out
 
 
 if __name__ == "__main__":

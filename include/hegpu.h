@@ -567,6 +567,11 @@ int he_trace_stop(double *total_ms, uint64_t *launches, double *bytes, double *m
 /* Time the integer pipe: `iters` dependent 64-bit Montgomery products per thread over
  * `blocks` x 256 threads; returns modular products per second (device-timed). */
 int he_bench_modmul(he_ctx *ctx, int blocks, int iters, double *mulmods_per_s);
+/* The integer pipe's throughput on the fused key-switch kernels' inner operation: `iters`
+ * 64 x 64 -> 128-bit multiply-accumulates in each of 8 independent chains per thread over
+ * `blocks` x 256 threads (on a 32-bit multiplier each is four 32 x 32 -> 64-bit partial
+ * products and their carries); returns multiply-accumulates per second (device-timed). */
+int he_bench_mac(he_ctx *ctx, int blocks, int iters, double *macs_per_s);
 
 #ifdef __cplusplus
 }

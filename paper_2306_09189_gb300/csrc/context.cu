@@ -1300,6 +1300,12 @@ extern "C" int he_mul_relin(he_ctx *c, const he_ct *a, const he_ct *b, he_ct *ou
     return he_rescale(c, out, stream);
 }
 
+extern "C" int he_bench_mac(he_ctx *c, int blocks, int iters, double *rate) {
+    if (!c || !rate || blocks <= 0 || iters <= 0) { he_set_error("bad argument"); return HE_EINVAL; }
+    *rate = k_bench_mac(blocks, iters, 0);
+    return *rate > 0 ? HE_OK : HE_ECUDA;
+}
+
 extern "C" int he_bench_modmul(he_ctx *c, int blocks, int iters, double *rate) {
     if (!c || !rate || blocks <= 0 || iters <= 0) { he_set_error("bad argument"); return HE_EINVAL; }
     *rate = k_bench_modmul(c, blocks, iters, 0);

@@ -351,6 +351,7 @@ int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u6
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s);
 // Loads the no-allocation rescale's module on the current device and caches its scratch address.
 int he_noalloc_setup();
+double k_bench_mac(int blocks, int iters, cudaStream_t s);
 double k_bench_modmul(const he_ctx *ctx, int blocks, int iters, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- host helpers

@@ -1852,6 +1852,31 @@ __global__ void bench_modmul_kernel(u64 q, u64 qinv, int iters, u64 *sink) {
     if (x == 0xdeadbeef) sink[0] = y;
 }
 
+// Throughput of 64 x 64 -> 128-bit multiply-accumulates (the fused key-switch kernels' inner
+// operation): eight independent chains per thread, acc_c += a_c b with a_c taken from the low
+// word of the chain's last sum, so every chain is a true dependency and nothing can be hoisted.
+__global__ void bench_mac_kernel(u64 b, int iters, u64 *sink) {
+    pdl_wait();
+    u64 a[8];
+    u128 acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        a[c] = (u64)threadIdx.x * 0x9E3779B97F4A7C15ull + c + blockIdx.x;
+        acc[c] = a[c];
+    }
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            acc[c] += (u128)a[c] * b;
+            a[c] = (u64)acc[c] | 1;
+        }
+    }
+    u64 x = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) x ^= (u64)acc[c] ^ (u64)(acc[c] >> 64);
+    if (x == 0x0123456789abcdefull) sink[0] = x;
+}
+
 }  // namespace
 
 // ================================================================================= launchers
@@ -2919,6 +2944,26 @@ int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u6
     pdl_launch(rescale_combine_kernel, dim3(ctx->n / TB, level, 2 * m), TB, 0, s, ctx->kp, base, ps, t, level, inv, invs);
     LAUNCH_CHECK();
     return HE_OK;
+}
+
+double k_bench_mac(int blocks, int iters, cudaStream_t s) {
+    u64 *sink;
+    if (he_malloc(&sink, 8) != cudaSuccess) return -1.0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    pdl_launch(bench_mac_kernel, blocks, 256, 0, s, 0xfedcba9876543211ull, 16, sink);   // warm-up
+    cudaEventRecord(e0, s);
+    pdl_launch(bench_mac_kernel, blocks, 256, 0, s, 0xfedcba9876543211ull, iters, sink);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    he_count_launch(2);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    he_free(sink);
+    return (double)blocks * 256.0 * 8.0 * iters / (ms * 1e-3);
 }
 
 double k_bench_modmul(const he_ctx *ctx, int blocks, int iters, cudaStream_t s) {

@@ -173,6 +173,7 @@ _SIGS = {
     "he_havgpool": (c_int, [c_vp, ctypes.POINTER(he_layout), ctypes.POINTER(c_vp), ctypes.POINTER(he_layout),
                             ctypes.POINTER(c_vp), c_int, c_vp]),
     "he_bench_modmul": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_double)]),
+    "he_bench_mac": (c_int, [c_vp, c_int, c_int, ctypes.POINTER(c_double)]),
     "he_rescale_noalloc": (c_int, [c_vp, c_vp, c_vp]),
     "he_trace_start": (c_int, [ctypes.c_char_p]),
     "he_trace_stop": (c_int, [ctypes.POINTER(c_double), ctypes.POINTER(c_u64), ctypes.POINTER(c_double),
@@ -783,6 +784,12 @@ def he_poly_eval(ctx, ct, cheb, target_scale, stream=None):
 def he_bench_modmul(ctx, blocks, iters):
     r = c_double()
     _check(load().he_bench_modmul(ctx, blocks, iters, ctypes.byref(r)))
+    return r.value
+
+
+def he_bench_mac(ctx, blocks, iters):
+    r = c_double()
+    _check(load().he_bench_mac(ctx, blocks, iters, ctypes.byref(r)))
     return r.value
 
 
