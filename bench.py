@@ -11,8 +11,9 @@ Prints one JSON line (rank 0).  value = key switches per second (rotations + rel
 ranks; ms_per_step = layer latency.  The batched mode is the headline; the plain
 per-ciphertext path is timed beside it, and the convolution alone (`conv_only`).  At N = 1 the
 line also carries the batched ResNet block (`resnet_block`: 4 images at mixed levels, batched
-vs plain) and the ImageNet stem (`imagenet_stem`), each run on its own context afterwards, and
-the oracle on all host cores and on one (`cpu_baseline`).  N > 1 runs independent replicas
+vs plain), the ImageNet stem (`imagenet_stem`) and the serving loop (`serving`: Poisson
+arrivals, p50/p99 latency and images/s), each run on its own context afterwards, and the oracle
+on all host cores and on one (`cpu_baseline`).  N > 1 runs independent replicas
 (the layer does not shard across GPUs).  --impl reference times the CPU oracle instead.
 """
 import argparse
@@ -649,7 +650,7 @@ def main():
     ap.add_argument("--trace", default="ipmac", help="kernel whose launches the roofline uses")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the ResNet-block and ImageNet-stem figures the default line carries")
+                    help="skip the ResNet-block, ImageNet-stem and serving figures the default line carries")
     ap.add_argument("--small", action="store_true",
                     help="profiling case: same ring, 2-channel 32x32 conv (17 rotations, ~2 GB of keys)")
     ap.add_argument("--profile-step", action="store_true",
@@ -947,6 +948,14 @@ def main():
             sub = argparse.Namespace(**vars(args))
             sub.steps, sub.warmup, sub.trace, sub.small, sub.profile_step = k, 3, "ipmac", False, False
             line[key] = _extra_summary(fn(sub, ws, rank, local, emit=False))
+        # serving: Poisson streams of 32x32 and 64x64 requests through the 4-layer stack at
+        # 33 + 11 primes, continuous batching at stage granularity (p50/p99 and images/s)
+        from paper_2306_09189_gb300 import serve
+        sv = serve.run_benchmark(argparse.Namespace(sizes="32,64", widths="4,16,32,64,64", rates="0.5,0.8",
+                                                    requests=32, conv="bsgs", server="batch", workers=4,
+                                                    max_batch=4))
+        line["serving"] = {k: sv[k] for k in ("workload", "server", "max_batch", "conv", "setup_s",
+                                              "service_ms_alone", "capacity_images_per_s", "runs", "memory")}
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(48)          # ~10 s of oracle work on every core

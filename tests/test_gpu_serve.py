@@ -78,3 +78,59 @@ def test_forked_context_shares_keys_and_matches_parent():
         H.he_ctx_destroy(fork)
     finally:
         H.he_ctx_destroy(root)
+
+
+def _batched_vs_alone(pr, level, widths, sizes, order, max_batch):
+    from paper_2306_09189_gb300 import hegpu as H, host
+    from paper_2306_09189_gb300.serve import (Stack, Server, BatchServer, Request, encrypt_request,
+                                              decrypt_result, plaintext_stack)
+    root = H.he_ctx_create(pr)
+    try:
+        H.he_keygen_relin(root)
+        layers = workloads.serving_stack(0, widths=widths, m=max(sizes))
+        cheb = host.chebyshev_coeffs("gelu", 16, -8.0, 8.0)
+        stacks = {m: Stack(root, m, layers, cheb, level, pr.scale) for m in sizes}
+        rng = np.random.default_rng(5)
+        imgs, reqs = [], []
+        for i, m in enumerate(order):
+            img = rng.uniform(0, 1, (4, m, m))
+            img[3] = 0.0
+            imgs.append(img)
+            reqs.append(Request(i, 0.0, m, encrypt_request(root, stacks[m], img, 300 + 10 * i)))
+        alone = Server(root, stacks, 1)
+        solo = []
+        for r in reqs:
+            solo += alone.serve([Request(r.rid, 0.0, r.m, r.coeffs)])
+        batch = BatchServer(root, stacks, max_batch=max_batch, slots_per_res=max_batch)
+        # a burst, then a request arriving while the burst is on the GPU
+        arrivals = [0.0] * (len(reqs) - 1) + [0.002]
+        got = batch.serve([Request(r.rid, a, r.m, r.coeffs) for r, a in zip(reqs, arrivals)])
+        assert max(size for _, _, size in batch.steps) > 1            # requests shared launches
+        for a, b in zip(solo, got):
+            assert a.rid == b.rid and b.finish >= b.start >= b.arrival
+            for x, y in zip(a.result, b.result):
+                assert np.array_equal(x, y)                          # the same bits as alone
+        for r, img in zip(got, imgs):
+            out = decrypt_result(root, stacks[r.m], r.result)
+            want = plaintext_stack(img, layers, cheb)
+            assert np.abs(out - want).max() <= 2.0 ** -20 * (want.max() - want.min())
+        batch.destroy()
+        alone.destroy()
+        for s in stacks.values():
+            s.destroy()
+    finally:
+        H.he_ctx_destroy(root)
+
+
+def test_batched_server_gives_each_request_its_alone_bits():
+    """Stage-granularity batching at ring 2^12: two layers, two resolutions, a burst of five."""
+    from paper_2306_09189_gb300 import host
+    _batched_vs_alone(host.params(12, 17, 5, 4, 50, 40, 50, seed=7), 16, (4, 8, 8), (8, 16),
+                      [16, 8, 16, 16, 8], 4)
+
+
+def test_batched_server_full_ring():
+    """The same at n = 2^16 with the benchmark's parameters (20 + 5 primes): one layer on
+    32 x 32 images, three requests batched."""
+    from paper_2306_09189_gb300 import host
+    _batched_vs_alone(host.cifar_params(seed=0), 19, (4, 8), (32,), [32, 32, 32], 2)

@@ -64,3 +64,27 @@ def test_polynomial_depth_and_products_match_the_oracle_recursion():
     for d in (5, 16, 27, 59):
         k, giants = Ly.cheb_ps_params(d)
         assert host.ps_products(d) >= k - 1 + len(giants) - 1
+
+
+def test_batched_steps_take_the_oldest_requests_stage_in_power_of_two_groups():
+    from paper_2306_09189_gb300.serve import next_group
+    sizes = [1, 2, 4, 8]
+    # (arrival, rid, resolution, stage)
+    waiting = [(0.0, 0, 32, 2), (0.1, 1, 32, 0), (0.2, 2, 32, 0), (0.3, 3, 64, 0), (0.4, 4, 32, 0),
+               (0.5, 5, 32, 0)]
+    assert next_group(waiting, sizes) == ((32, 2), [0])            # the oldest request goes first
+    rest = waiting[1:]
+    assert next_group(rest, sizes) == ((32, 0), [1, 2, 4, 5])      # four of its stage join it
+    assert next_group(rest[:3], sizes) == ((32, 0), [1, 2])        # three waiting: a group of two
+    many = [(0.01 * i, i, 32, 1) for i in range(11)]
+    assert next_group(many, sizes) == ((32, 1), list(range(8)))    # capped at the largest size
+    assert next_group([(0.0, 9, 64, 3)], sizes) == ((64, 3), [9])
+
+
+def test_admission_refuses_to_wait_forever_for_memory():
+    # nothing runs to free memory and none comes free: the server reports it instead of spinning
+    import pytest
+    srv = Server(None, {}, 0, reserve_bytes=5, export=False, workers=[FakeWorker(0.01)], hbm_free=lambda: 1,
+                 admit_timeout=0.2)
+    with pytest.raises(MemoryError):
+        srv.serve([Request(0, 0.0, 32, 0)])
