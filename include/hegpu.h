@@ -163,8 +163,10 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  *     plaintext-weighted sums of 4 outputs per pass; amounts go in chunks of at most 2 GB of
  *     inner products.  Cheaper than the fused kernel when a stage has many output shards;
  *   HE_KEY_STREAM_AUTO (2, default): on the first run of each fused launch an autotuner times
- *     every eligible candidate (fused kernel: key stream x outputs per key pass; split form,
- *     when device memory allows) and keeps the fastest (he_ctx_tuning_log lists them).
+ *     the eligible candidates (fused kernel: the LDG, TMA and LDG1 key streams x outputs per
+ *     key pass; the pre-keyed forms and the split form, when device memory allows) and keeps the
+ *     fastest (he_ctx_tuning_log lists them).  HE_KEY_STREAM_CP and HE_KEY_STREAM_SPLITM run
+ *     only when selected explicitly.
  * Every choice gives the same bits.  Returns HE_EINVAL for an unknown option or value. */
 #define HE_OPT_KEY_STREAM 1
 #define HE_KEY_STREAM_LDG 0

@@ -1013,11 +1013,13 @@ struct FusedLaunch {
         return HE_OK;
     }
 
-    // candidates: the fused kernel (V outputs per key pass, key stream) and the split form
+    // candidates: the fused kernel (V outputs per key pass, key stream) and the split form.  The
+    // per-thread cp.async ring at one block per SM (HE_KEY_STREAM_CP, and the image-batched split
+    // MAC) is left to explicit selection: it shares its construct with kernels that faulted the
+    // GPU, and it was never the fastest candidate
     int tune(cudaStream_t s) {
         std::vector<int> forms = {HE_KEY_STREAM_LDG};
         if (max_beta <= 4 && c->d_err) forms.push_back(HE_KEY_STREAM_TMA);
-        if (max_beta <= 4) forms.push_back(HE_KEY_STREAM_CP);
         forms.push_back(HE_KEY_STREAM_LDG1);
         std::vector<int> Vs = {vmax()};
         if (vmax() == 2) Vs.push_back(1);
@@ -1114,15 +1116,6 @@ struct FusedLaunch {
                 if (pos < (int)sizeof(line))
                     pos += snprintf(line + pos, sizeof(line) - pos, " split (%zu chunk(s)) %.3f ms;", d_ugrps.size(), t);
                 if (t < best) { best = t; bestSplit = true; bestPk = false; }
-            }
-            if (rc == HE_OK && splitm_ok()) {
-                rc = build_split_m();
-                if (rc == HE_OK) rc = time_it([&]() { return launch_split(s, true); }, t);
-                if (rc == HE_OK) {
-                    if (pos < (int)sizeof(line))
-                        pos += snprintf(line + pos, sizeof(line) - pos, " split-m %.3f ms;", t);
-                    if (t < best) { best = t; bestSplit = true; bestPk = false; use_split_m = true; }
-                }
             }
             if (!use_split_m) free_split_m_tables();
         }
