@@ -155,6 +155,8 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  *     Other stages fall back to the LDG form.  HE_KEY_STREAM_PK3 (7): the same kernel at three
  *     blocks per SM; HE_KEY_STREAM_PKP (8): at two blocks per SM with the next amount's key words
  *     requested before the current amount computes;
+ *   HE_KEY_STREAM_PK1 (10): pre-keyed with one coefficient per thread (half the registers of
+ *     the pair form, four blocks per SM);
  *   HE_KEY_STREAM_SPLITM (9): the split form with the raised MAC batched over the images of a
  *     mixed-level batch (he_conv_run_batch): each plaintext word is read once for up to 4 images
  *     x 4 outputs; a single image falls back to HE_KEY_STREAM_SPLIT;
@@ -179,6 +181,7 @@ int he_ctx_check(he_ctx *ctx, void *stream);
 #define HE_KEY_STREAM_PK3 7
 #define HE_KEY_STREAM_PKP 8
 #define HE_KEY_STREAM_SPLITM 9
+#define HE_KEY_STREAM_PK1 10
 /* HE_OPT_PDL (0 default, or 1; process-wide, whichever context sets it): launch every kernel
  * with programmatic dependent launch, so each grid is set up while its predecessor on the
  * stream finishes (every kernel waits for the predecessor's writes before it reads).  Same

@@ -1750,6 +1750,70 @@ __global__ void __launch_bounds__(TB, MINB) ipmac_pk_kernel(KP kp, const fgrp *g
     st2(P.acc + (size_t)ext * kp.n + off, redc(a10, q, qi), redc(a11, q, qi));
 }
 
+// ---- pre-keyed, one coefficient per thread: the pair form's arithmetic with half its registers
+// per thread, so more blocks per SM keep more key words in flight (8-byte loads; a warp still
+// reads 256 contiguous bytes of every key word).  Same terms, same 128-bit sums, same bits.
+template <int B, int MINB>
+__global__ void __launch_bounds__(TB, MINB) ipmac_pk1_kernel(KP kp, const fgrp *grps, int n_grp, int gb,
+                                                             const u64 *pmod) {
+    pdl_wait();
+    fgrp P;
+    int tile, t, ptl;
+    if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl, TB)) return;
+    const int k = tile * TB + threadIdx.x;
+    const int kl = blockIdx.y;
+    const int nq = P.level + 1;
+    const int ext = nq + kp.K;
+    const int beta = P.beta;
+    const bool isq = t < nq;
+    const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+    const u64 Pm = isq ? to_mont(pmod[kl], q, qi, r2) : 0;
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    const size_t off = (size_t)t * kp.n + k;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    u128 a0 = 0, a1 = 0;
+    const int n_amt = P.n_amt;
+    famt A = n_amt > 0 ? P.amts[0] : famt{};
+    fent E = (n_amt > 0 && A.e0 < A.e1) ? P.ents[A.e0] : fent{};
+    for (int i = 0; i < n_amt; i++) {
+        famt An{};
+        fent En{};
+        if (i + 1 < n_amt) {
+            An = P.amts[i + 1];
+            if (An.e0 < An.e1) En = P.ents[An.e0];
+        }
+        if (A.e0 < A.e1) {
+            const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
+            if (A.key) {
+                u64 k0[B], k1[B], d[B];
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        const u64 *kp0 = A.key + (size_t)(2 * j) * kstride + (size_t)kl * kp.n + k;
+                        k0[j] = ld_hint(kp0, stream);
+                        k1[j] = ld_hint(kp0 + kstride, stream);
+                        d[j] = ld_hint(E.D + ((size_t)j * ext + t) * kp.n + ks, keep);
+                    }
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        a0 += (u128)d[j] * k0[j];
+                        a1 += (u128)d[j] * k1[j];
+                    }
+            }
+            if (isq) {
+                const u64 pp = E.pt[0] == HE_PT_ONE ? Pm : ld_hint(E.pt[0] + (size_t)t * kp.n + k, stream);
+                a0 += (u128)ld_hint(E.src + (size_t)t * kp.n + ks, keep) * pp;
+                if (!A.key) a1 += (u128)ld_hint(E.src + E.ps + off, keep) * pp;
+            }
+        }
+        A = An;
+        E = En;
+    }
+    P.acc[off] = redc(a0, q, qi);
+    P.acc[(size_t)ext * kp.n + off] = redc(a1, q, qi);
+}
+
 // K'[2j + c] = K[2j + c] (.) pt on the limbs of Q_l u P (key layout: global prime index) and
 // Ppt = [P]_q (.) pt on the q-limbs ([l+1][n]); pt holds pt_level + 1 q-limbs then the p-limbs.
 __global__ void prekey_kernel(KP kp, const u64 *key, const u64 *pt, int level, int pt_level, int beta, u64 *Kp,
@@ -2429,6 +2493,14 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
             pdl_launch(ipmac_tma_kernel<1>, gt, TB, smem, s, ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
         else
             pdl_launch(ipmac_tma_kernel<2>, gt, TB, smem, s, ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
+        LAUNCH_CHECK();
+        return HE_OK;
+    }
+    if (form == HE_KEY_STREAM_PK1) {
+        if (V != 1) { he_set_error("k_ipmac: the pre-keyed form takes one output per group"); return HE_EINVAL; }
+        dim3 g1((unsigned)((n_grp + gb - 1) / gb) * gb * (ctx->n / TB), primes);
+        if (max_beta <= 4) pdl_launch(ipmac_pk1_kernel<4, 4>, g1, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else pdl_launch(ipmac_pk1_kernel<8, 2>, g1, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
         LAUNCH_CHECK();
         return HE_OK;
     }

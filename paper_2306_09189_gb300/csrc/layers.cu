@@ -729,8 +729,12 @@ struct FusedStage {
 // launch (one warm-up pass, then the best of two timed passes, CUDA events on the launch's
 // stream) and keeps the fastest.  Needs the raised digits in place: called after the hoisted
 // ModUps of the first run.
-static bool is_pk(int fm) { return fm == HE_KEY_STREAM_PK || fm == HE_KEY_STREAM_PK3 || fm == HE_KEY_STREAM_PKP; }
-static const char *pk_name(int fm) { return fm == HE_FORM_PK3 ? "pk3" : fm == HE_FORM_PKP ? "pkp" : "pk"; }
+static bool is_pk(int fm) {
+    return fm == HE_KEY_STREAM_PK || fm == HE_KEY_STREAM_PK3 || fm == HE_KEY_STREAM_PKP || fm == HE_KEY_STREAM_PK1;
+}
+static const char *pk_name(int fm) {
+    return fm == HE_FORM_PK3 ? "pk3" : fm == HE_FORM_PKP ? "pkp" : fm == HE_KEY_STREAM_PK1 ? "pk1" : "pk";
+}
 static const char *form_name(int fm) {
     return fm == HE_KEY_STREAM_TMA ? "tma" : fm == HE_KEY_STREAM_CP ? "cp" : fm == HE_KEY_STREAM_LDG1 ? "ldg1" : "ldg";
 }
@@ -1099,7 +1103,7 @@ struct FusedLaunch {
         bool bestPk = false;
         if (rc == HE_OK && try_pk) {
             rc = build_pk();
-            for (int fm : {(int)HE_KEY_STREAM_PK, (int)HE_FORM_PK3, (int)HE_FORM_PKP}) {
+            for (int fm : {(int)HE_KEY_STREAM_PK, (int)HE_FORM_PK3, (int)HE_FORM_PKP, (int)HE_KEY_STREAM_PK1}) {
                 float t;
                 if (rc == HE_OK) rc = time_it([&]() { return launch_pk(s, fm); }, t);
                 if (rc != HE_OK) break;
