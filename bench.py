@@ -228,6 +228,8 @@ def run_block(args, ws, rank, local, emit=True):
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
+                                                   "pk3": H.HE_KEY_STREAM_PK3, "pk1": H.HE_KEY_STREAM_PK1,
+                                                   "pkt": H.HE_KEY_STREAM_PKT,
                                                    "splitm": H.HE_KEY_STREAM_SPLITM}[args.key_stream])
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]
@@ -539,6 +541,8 @@ def run_stem(args, ws, rank, local, emit=True):
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
+                                                   "pk3": H.HE_KEY_STREAM_PK3, "pk1": H.HE_KEY_STREAM_PK1,
+                                                   "pkt": H.HE_KEY_STREAM_PKT,
                                                    "splitm": H.HE_KEY_STREAM_SPLITM}[args.key_stream])
     N = H.he_ctx_info(ctx)["slots"]
     wl = workloads.imagenet_stem(0)
@@ -655,7 +659,8 @@ def main():
                     help="profiling case: same ring, 2-channel 32x32 conv (17 rotations, ~2 GB of keys)")
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, warm up, then run one batched step between cudaProfilerStart/Stop")
-    ap.add_argument("--key-stream", default="auto", choices=["auto", "ldg", "tma", "split", "pk", "splitm"],
+    ap.add_argument("--key-stream", default="auto",
+                    choices=["auto", "ldg", "tma", "split", "pk", "pk3", "pk1", "pkt", "splitm"],
                     help="key-switch + MAC form: autotuned (default), the fused kernel with vector "
                          "loads or a TMA tile pipeline, or the split form (inner products, then MAC)")
     ap.add_argument("--no-graph", action="store_true", help="launch the fused step eagerly, not as a CUDA graph")
@@ -701,6 +706,8 @@ def main():
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
+                                                   "pk3": H.HE_KEY_STREAM_PK3, "pk1": H.HE_KEY_STREAM_PK1,
+                                                   "pkt": H.HE_KEY_STREAM_PKT,
                                                    "splitm": H.HE_KEY_STREAM_SPLITM}[args.key_stream])
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]

@@ -1750,6 +1750,153 @@ __global__ void __launch_bounds__(TB, MINB) ipmac_pk_kernel(KP kp, const fgrp *g
     st2(P.acc + (size_t)ext * kp.n + off, redc(a10, q, qi), redc(a11, q, qi));
 }
 
+// ---- pre-keyed form fed by a TMA ring with per-stage release: a producer warp copies each
+// keyed amount's K' tile (2 beta segments of 512 words) by cp.async.bulk into one of PKT_STAGES
+// shared-memory stages; the eight consumer warps wait on the stage's "full" mbarrier, take their
+// key words into registers and release the stage on its "empty" mbarrier (one arrival per warp)
+// before they compute, so warps run up to PKT_STAGES amounts apart and no block barrier paces
+// the stream.  The producer waits on "empty" before refilling a stage.  Every wait is bounded:
+// a consumer whose wait gives up sets *err and a shared abort flag that stops every warp; the
+// block then waits (bounded) for the copies it issued before its shared memory goes away.
+constexpr int PKT_STAGES = 3;                       // 3 x 32 KB at beta = 4: two blocks per SM
+constexpr int PKT_THREADS = TB + 32;                // eight consumer warps and the producer warp
+
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(PKT_THREADS, 2) ipmac_pkt_kernel(KP kp, const fgrp *grps, int n_grp, int gb,
+                                                                   int *err, const u64 *pmod) {
+    pdl_wait();
+    constexpr int NS = PKT_STAGES, B = 4;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_abort;
+    __shared__ int s_issued;
+    fgrp P;
+    int tile, t, ptl;
+    if (!grp_pos(kp, grps, n_grp, gb, P, tile, t, ptl)) return;   // block-uniform
+    const int beta = P.beta, n_amt = P.n_amt, seg = 2 * beta;
+    const famt *amts = P.amts;
+    u64 *kbuf = (u64 *)smem_raw;                                // [NS][2 beta][TMA_TILE]
+    uint64_t *full = (uint64_t *)(kbuf + (size_t)NS * 2 * B * TMA_TILE);
+    uint64_t *empty = full + NS;
+    const int k0 = tile * TMA_TILE;
+    const int kl = blockIdx.y;
+    const int nq = P.level + 1;
+    const int ext = nq + kp.K;
+    const size_t kstride = (size_t)(kp.L + 1 + kp.K) * kp.n;
+    const u64 stream = policy_evict_first(), keep = policy_evict_last();
+    const bool producer = threadIdx.x >= TB;
+    if (threadIdx.x == 0) {
+        s_abort = *(volatile int *)err;            // an earlier block already gave up: skip the work
+        s_issued = 0;
+        for (int st = 0; st < NS; st++) {
+            mbar_init(smem_u32(&full[st]), 1);
+            mbar_init(smem_u32(&empty[st]), TB / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (s_abort) return;                           // block-uniform after the barrier
+    if (producer) {
+        if (threadIdx.x == TB) {                   // one lane issues; the rest of the warp idles
+            const unsigned bytes = (unsigned)seg * TMA_TILE * 8;
+            int u = 0;
+            for (int i = 0; i < n_amt; i++) {
+                if (!amts[i].key) continue;
+                const int st = u % NS;
+                if (u >= NS && !mbar_wait_bounded(smem_u32(&empty[st]), ((u / NS) - 1) & 1)) break;
+                if (*(volatile int *)&s_abort) break;
+                const unsigned bar = smem_u32(&full[st]);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(bar, bytes);
+                const u64 *kb = amts[i].key + (size_t)kl * kp.n + k0;
+                for (int sgi = 0; sgi < seg; sgi++)
+                    tma_load(smem_u32(kbuf + ((size_t)st * 2 * B + sgi) * TMA_TILE), kb + (size_t)sgi * kstride,
+                             TMA_TILE * 8, bar, stream);
+                u++;
+                *(volatile int *)&s_issued = u;
+            }
+        }
+    } else {
+        const int k = k0 + 2 * threadIdx.x;
+        const bool isq = t < nq;
+        const u64 q = kp.q[kl], qi = kp.qinv[kl], r2 = kp.r2[kl];
+        const u64 Pm = isq ? to_mont(pmod[kl], q, qi, r2) : 0;
+        const size_t off = (size_t)t * kp.n + k;
+        u128 a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+        int u = 0;
+        for (int i = 0; i < n_amt; i++) {
+            const famt A = amts[i];
+            const bool has = A.e0 < A.e1;
+            if (!A.key && !has) continue;
+            const fent E = has ? P.ents[A.e0] : fent{};
+            const int ks = A.g == 1 ? k : autom_index(k, A.g, kp.logn);
+            const int sw = ks & 1, kb = ks & ~1;
+            if (A.key) {
+                const int st = u % NS;
+                // warp-uniform decisions: every lane waits (each takes the barrier's acquire),
+                // then the warp votes, so no lane leaves the loop alone
+                if (__any_sync(0xffffffffu, *(volatile int *)&s_abort)) break;
+                const bool ok = mbar_wait_bounded(smem_u32(&full[st]), (u / NS) & 1);
+                if (!__all_sync(0xffffffffu, ok)) {
+                    if ((threadIdx.x & 31) == 0) {
+                        atomicExch(err, 1);
+                        *(volatile int *)&s_abort = 1;
+                    }
+                    break;
+                }
+                ulonglong2 kk0[B], kk1[B];
+                const u64 *kt = kbuf + (size_t)st * 2 * B * TMA_TILE + 2 * threadIdx.x;
+#pragma unroll
+                for (int j = 0; j < B; j++)
+                    if (j < beta) {
+                        kk0[j] = *(const ulonglong2 *)(kt + (size_t)(2 * j) * TMA_TILE);
+                        kk1[j] = *(const ulonglong2 *)(kt + (size_t)(2 * j + 1) * TMA_TILE);
+                    }
+                __syncwarp();
+                if ((threadIdx.x & 31) == 0) mbar_arrive(smem_u32(&empty[st]));   // stage released
+                u++;
+                if (has) {
+#pragma unroll
+                    for (int j = 0; j < B; j++)
+                        if (j < beta) {
+                            const ulonglong2 d = ld2_hint(E.D + ((size_t)j * ext + t) * kp.n + kb, keep);
+                            const u64 d0 = sw ? d.y : d.x, d1 = sw ? d.x : d.y;
+                            a00 += (u128)d0 * kk0[j].x;
+                            a01 += (u128)d1 * kk0[j].y;
+                            a10 += (u128)d0 * kk1[j].x;
+                            a11 += (u128)d1 * kk1[j].y;
+                        }
+                }
+            }
+            if (isq && has) {
+                const ulonglong2 pp = E.pt[0] == HE_PT_ONE ? make_ulonglong2(Pm, Pm)
+                                                           : ld2_hint(E.pt[0] + (size_t)t * kp.n + k, stream);
+                const ulonglong2 cc = ld2_hint(E.src + (size_t)t * kp.n + kb, keep);
+                a00 += (u128)(sw ? cc.y : cc.x) * pp.x;
+                a01 += (u128)(sw ? cc.x : cc.y) * pp.y;
+                if (!A.key) {
+                    const ulonglong2 c1 = ld2_hint(E.src + E.ps + off, keep);
+                    a10 += (u128)c1.x * pp.x;
+                    a11 += (u128)c1.y * pp.y;
+                }
+            }
+        }
+        if (!*(volatile int *)&s_abort) {
+            st2(P.acc + off, redc(a00, q, qi), redc(a01, q, qi));
+            st2(P.acc + (size_t)ext * kp.n + off, redc(a10, q, qi), redc(a11, q, qi));
+        }
+    }
+    __syncthreads();
+    if (s_abort && threadIdx.x == 0) {
+        // the last copy issued into each stage lands (bounded) before the shared memory goes away
+        const int issued = s_issued;
+        for (int u = issued - NS < 0 ? 0 : issued - NS; u < issued; u++)
+            mbar_wait_bounded(smem_u32(&full[u % NS]), (u / NS) & 1);
+    }
+}
+
 // ---- pre-keyed, one coefficient per thread: the pair form's arithmetic with half its registers
 // per thread, so more blocks per SM keep more key words in flight (8-byte loads; a warp still
 // reads 256 contiguous bytes of every key word).  Same terms, same 128-bit sums, same bits.
@@ -2493,6 +2640,18 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
             pdl_launch(ipmac_tma_kernel<1>, gt, TB, smem, s, ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
         else
             pdl_launch(ipmac_tma_kernel<2>, gt, TB, smem, s, ctx->kp, grps, n_grp, gb, ctx->d_err, ctx->d_consts);
+        LAUNCH_CHECK();
+        return HE_OK;
+    }
+    if (form == HE_KEY_STREAM_PKT && !(max_beta <= 4 && ctx->d_err)) form = HE_KEY_STREAM_PK;   // pair form
+    if (form == HE_KEY_STREAM_PKT) {
+        if (V != 1) { he_set_error("k_ipmac: the pre-keyed form takes one output per group"); return HE_EINVAL; }
+        const int smem = PKT_STAGES * (2 * 4 * TMA_TILE * 8) + 2 * PKT_STAGES * 8;
+        static const bool attr_ok =
+            cudaFuncSetAttribute(ipmac_pkt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) == cudaSuccess;
+        if (!attr_ok) { he_set_error("fused kernel: shared-memory opt-in failed"); return HE_ECUDA; }
+        pdl_launch(ipmac_pkt_kernel, dim3(gx, primes), PKT_THREADS, smem, s, ctx->kp, grps, n_grp, gb, ctx->d_err,
+                   ctx->d_consts);
         LAUNCH_CHECK();
         return HE_OK;
     }
