@@ -940,7 +940,11 @@ __global__ void __launch_bounds__(TB) moddown_rescale_fbc_kernel(KP kp, const u6
     const u64 yl = mul_shoup(sub_mod(uc[(size_t)level * kp.n + k], fbc_sum<CAP>(kp, level, v, neg, hat, nhat), ql),
                              pinv[level], pinvs[level], ql);
     const bool yneg = 2 * yl > ql;
-    for (int t = 0; t < level; t++) {
+    // blockIdx.z of gridDim.z: this block's share of the target primes (small batches split the
+    // targets so the launch fills the GPU; y_l is recomputed per share, K + 1 products)
+    const int per = (level + gridDim.z - 1) / gridDim.z;
+    const int t0 = blockIdx.z * per, t1 = min(level, t0 + per);
+    for (int t = t0; t < t1; t++) {
         const u64 q = kp.q[t];
         u64 r;
         if (yneg) {
@@ -2509,8 +2513,11 @@ int k_moddown_rescale(const he_ctx *ctx, u64 *u, const u64 *base, size_t b_is, s
     {
         TraceScope tr("moddown_fbc", s, (double)2 * m * (ctx->K + 1 + level) * ctx->n * 8,
                       (double)2 * m * (ctx->K + nq * ctx->K + level) * ctx->n);
-#define GO(C) pdl_launch(moddown_rescale_fbc_kernel<C>, dim3(ctx->n / TB, 2 * m), TB, 0, s, ctx->kp, u, w, level, \
-                         ctx->moddown[level].d, pinv, pinvs)
+        // target-prime shares: enough blocks for about two per SM slot of a 152-SM GPU
+        const int blocks = (ctx->n / TB) * 2 * m;
+        const int shares = std::max(1, std::min(level, std::min(4, (2048 + blocks - 1) / blocks)));
+#define GO(C) pdl_launch(moddown_rescale_fbc_kernel<C>, dim3(ctx->n / TB, 2 * m, shares), TB, 0, s, ctx->kp, u, w, \
+                         level, ctx->moddown[level].d, pinv, pinvs)
         CAP_SWITCH(ctx->K, GO)
 #undef GO
         LAUNCH_CHECK();
