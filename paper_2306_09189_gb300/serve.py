@@ -231,7 +231,8 @@ class BatchServer:
     resolution is free and HBM headroom allows, and join the next step of their stage.  Each
     image's result is the one it gets alone (the batched calls give every image exactly its
     own bits).  Slots (per-request buffers) are allocated up front, so admission allocates
-    nothing."""
+    nothing.  With export=False a finished request's result is the handles of its slot, which
+    then stays with the request instead of returning to the pool."""
 
     def __init__(self, root, stacks, max_batch=4, slots_per_res=4, reserve_bytes=2 << 30, export=True,
                  hbm_free=None, key_stream=H.HE_KEY_STREAM_LDG, admit_timeout=10.0):
@@ -244,6 +245,7 @@ class BatchServer:
         # one fused launch per (stage, group size) lives at once: the register-fed key stream keeps
         # their memory to the batch buffers (the pre-keyed tables each autotuned launch may take,
         # a quarter of what is free at its turn, add up over many launches)
+        self._prev_key_stream = H.he_ctx_get_option(root, H.HE_OPT_KEY_STREAM)
         H.he_ctx_set_option(root, H.HE_OPT_KEY_STREAM, key_stream)
         # one conv object per (stage, group size): each keeps the buffers of its own batch shape
         self.convs = {m: [{b: H.he_conv_fork(stg.conv, root) for b in self.sizes} for stg in st.stages]
@@ -323,6 +325,7 @@ class BatchServer:
         return sorted(done, key=lambda x: x.rid)
 
     def destroy(self):
+        H.he_ctx_set_option(self.root, H.HE_OPT_KEY_STREAM, self._prev_key_stream)
         for m in self.convs:
             for per_stage in self.convs[m]:
                 for cv in per_stage.values():
