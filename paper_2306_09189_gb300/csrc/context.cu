@@ -1245,6 +1245,32 @@ extern "C" int he_rescale(he_ctx *c, he_ct *ct, void *stream) {
     return HE_OK;
 }
 
+int rescale_batch(he_ctx *c, he_ct *const *cts, int m, cudaStream_t s) {
+    if (m <= 0) return HE_OK;
+    const int l = cts[0]->level;
+    for (int j = 0; j < m; j++)
+        if (!cts[j] || cts[j]->ctx != c || cts[j]->level != l || l < 1) {
+            he_set_error("rescale batch: ciphertexts at different levels or no level left");
+            return HE_ELEVEL;
+        }
+    const int per = HE_NTT_TAB / 2;
+    HE_TRY(c->sc_rs.ensure((size_t)2 * std::min(m, per) * l * c->n));
+    for (int j0 = 0; j0 < m; j0 += per) {
+        const int cnt = std::min(per, m - j0);
+        u64 *polys[HE_NTT_TAB];
+        for (int j = 0; j < cnt; j++) {
+            polys[2 * j] = cts[j0 + j]->d;
+            polys[2 * j + 1] = cts[j0 + j]->d + cts[j0 + j]->pstride;
+        }
+        HE_TRY(k_rescale_tab(c, polys, cnt, l, c->sc_rs.p, s));
+    }
+    for (int j = 0; j < m; j++) {
+        cts[j]->level = l - 1;
+        cts[j]->scale = cts[j]->scale / (double)c->primes[l];
+    }
+    return HE_OK;
+}
+
 // b may sit above acc's level: its limbs q_0..q_l are b at level l (dropping limbs is exact)
 extern "C" int he_add(he_ctx *c, he_ct *acc, const he_ct *b, void *stream) {
     if (!c || !acc || !b || acc->level > b->level) { he_set_error("he_add: addend below the accumulator's level"); return HE_ELEVEL; }

@@ -146,8 +146,10 @@ struct he_ctx {
     std::vector<he_ct *> poly_tmp;       // reusable temporaries of he_poly_eval (level L), views
     u64 *poly_block = nullptr;           // one allocation holding them at a uniform stride
     Scratch sc_relin;                    // batched relinearisation buffers
+    Scratch sc_rs;                       // batched rescales: the correction terms
 };
 
+#define HE_NTT_TAB 16
 struct ntt_job {
     u64 *base;               // poly p, limb l at base + p*poly_stride + l*n
     size_t poly_stride;
@@ -157,6 +159,9 @@ struct ntt_job {
                              // j = p mod skip_mod (j = p when skip_mod is 0)
     int npoly;
     int skip_mod;
+    // optional: when tab[0] is set, poly p starts at tab[p] instead of base + p*poly_stride
+    // (npoly <= HE_NTT_TAB): polynomials of ciphertexts at unrelated addresses in one launch
+    u64 *tab[HE_NTT_TAB];
 };
 
 // ----------------------------------------------------------------------------- kernels
@@ -349,6 +354,10 @@ int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u6
 // Rescale of m ciphertexts at one level, poly p of ciphertext i at base + (2i + p) ps, in place;
 // t is scratch of 2 m level n words.  Every rescale goes through here (he_rescale with m = 1).
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s);
+int k_rescale_tab(const he_ctx *ctx, u64 *const *polys, int m, int level, u64 *t, cudaStream_t s);
+// Rescales m ciphertexts of one level as he_rescale does each (same words, same scales), with one
+// launch set per HE_NTT_TAB / 2 of them.
+int rescale_batch(he_ctx *c, he_ct *const *cts, int m, cudaStream_t s);
 // Loads the no-allocation rescale's module on the current device and caches its scratch address.
 int he_noalloc_setup();
 double k_bench_mac(int blocks, int iters, cudaStream_t s);

@@ -38,6 +38,10 @@ __device__ __forceinline__ int job_limb(const ntt_job &j, int y, int p) {
     return limb;
 }
 
+__device__ __forceinline__ u64 *job_poly(const ntt_job &j, int p) {
+    return j.tab[0] ? j.tab[p] : j.base + (size_t)p * j.poly_stride;
+}
+
 // Programmatic dependent launch: every kernel is launched with the programmatic-serialisation
 // attribute (when enabled), so its grid is set up while the predecessor on the stream
 // finishes; each kernel's first statement, griddepcontrol.wait, holds it until the predecessor
@@ -61,7 +65,7 @@ __global__ void __launch_bounds__(256) ntt_cols(KP kp, ntt_job job) {
     if (limb < 0) return;
     const int pr = prime_of(kp, limb, job.nq);
     const u64 q = kp.q[pr];
-    u64 *a = job.base + (size_t)p * job.poly_stride + (size_t)limb * kp.n;
+    u64 *a = job_poly(job, p) + (size_t)limb * kp.n;
     const int R = kp.n / ROW;
     const int c0 = blockIdx.x * NTT_TC;
     const u64 *W = (INV ? kp.itw : kp.tw) + (size_t)pr * kp.n;
@@ -121,7 +125,7 @@ __global__ void __launch_bounds__(256) ntt_rows(KP kp, ntt_job job) {
     if (row >= R) return;                       // warp-uniform; only __syncwarp below
     const int pr = prime_of(kp, limb, job.nq);
     const u64 q = kp.q[pr];
-    u64 *a = job.base + (size_t)p * job.poly_stride + (size_t)limb * kp.n + (size_t)row * ROW;
+    u64 *a = job_poly(job, p) + (size_t)limb * kp.n + (size_t)row * ROW;
     const u64 *W = (INV ? kp.itw : kp.tw) + (size_t)pr * kp.n;
     const u64 *Ws = (INV ? kp.itws : kp.tws) + (size_t)pr * kp.n;
     u64 *s = sm[warp];
@@ -232,7 +236,11 @@ struct RescaleFuse {
     size_t ps;
     int level;
     const u64 *inv, *invs;
+    u64 *ctab[HE_NTT_TAB];   // when ctab[0] is set: poly p of the ciphertexts at ctab[p]
 };
+__device__ __forceinline__ u64 *fuse_poly(const RescaleFuse &F, int p) {
+    return F.ctab[0] ? F.ctab[p] : F.c + (size_t)p * F.ps;
+}
 __device__ __forceinline__ u64 centred_mod(u64 v, u64 ql, u64 q, u64 mu) {
     if (2 * v > ql) {
         const u64 m = reduce64(ql - v, q, mu);
@@ -255,13 +263,13 @@ __global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job, Rescale
     const int ltc = 12 - lr, TC = 1 << ltc;           // columns per block
     const int t = threadIdx.x, tc = t & (TC - 1), r = t >> ltc;
     const int c = blockIdx.x * TC + tc;
-    u64 *a = job.base + (size_t)p * job.poly_stride + (size_t)limb * kp.n;
+    u64 *a = job_poly(job, p) + (size_t)limb * kp.n;
     const ulonglong2 *W = (const ulonglong2 *)(INV ? kp.itw2 : kp.tw2) + (size_t)pr * kp.n;
     const int n2 = lr - 4;                           // pass-2 stages
     u64 x[16];
     if (!INV) {
         if (RS) {
-            const u64 *top = F.c + (size_t)p * F.ps + (size_t)F.level * kp.n;
+            const u64 *top = fuse_poly(F, p) + (size_t)F.level * kp.n;
             const u64 ql = kp.q[F.level], mu = kp.mu[pr];
 #pragma unroll
             for (int j = 0; j < 16; j++) x[j] = centred_mod(top[(size_t)(r + R16 * j) * ROW + c], ql, q, mu);
@@ -310,7 +318,7 @@ __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job, Rescale
     const u64 q = kp.q[pr], q2 = 2 * q;
     const int t = threadIdx.x, rl = t >> 4, l = t & 15;
     const int row = blockIdx.x * 16 + rl;
-    u64 *a = job.base + (size_t)p * job.poly_stride + (size_t)limb * kp.n + (size_t)row * ROW;
+    u64 *a = job_poly(job, p) + (size_t)limb * kp.n + (size_t)row * ROW;
     const ulonglong2 *W = (const ulonglong2 *)(INV ? kp.itw2 : kp.tw2) + (size_t)pr * kp.n;
     u64 *s = sm[rl];
     u64 x[16];
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job, Rescale
         }
         __syncthreads();
         if (RS) {
-            u64 *cr = F.c + (size_t)p * F.ps + (size_t)limb * kp.n + (size_t)row * ROW;
+            u64 *cr = fuse_poly(F, p) + (size_t)limb * kp.n + (size_t)row * ROW;
             const u64 iv = F.inv[pr], ivs = F.invs[pr];
 #pragma unroll
             for (int j = 0; j < 16; j++) {
@@ -431,13 +439,13 @@ __global__ void __launch_bounds__(NcShape<CL>::T, NcShape<CL>::MINB)
     const int r = blockIdx.x;                         // cluster rank: the grid is one cluster wide
     const int blk = r * S::BLK;                       // this CTA's block in rounds B, C, D
     const int b0 = r * S::T + t;                      // round A: words b0 + (k << 12), b0 < 4096
-    u64 *a = job.base + (size_t)p * job.poly_stride + (size_t)limb * kp.n;
+    u64 *a = job_poly(job, p) + (size_t)limb * kp.n;
     const ulonglong2 *W = (const ulonglong2 *)(INV ? kp.itw2 : kp.tw2) + (size_t)pr * kp.n;
     u64 x[16];
     if (!INV) {
         cluster_arrive_relaxed();                     // this CTA has started
         if (RS) {
-            const u64 *top = F.c + (size_t)p * F.ps + (size_t)F.level * kp.n;
+            const u64 *top = fuse_poly(F, p) + (size_t)F.level * kp.n;
             const u64 ql = kp.q[F.level], mu = kp.mu[pr];
 #pragma unroll
             for (int k = 0; k < 16; k++) x[k] = centred_mod(top[b0 + (k << 12)], ql, q, mu);
@@ -467,7 +475,7 @@ __global__ void __launch_bounds__(NcShape<CL>::T, NcShape<CL>::MINB)
             x[k] = v >= q ? v - q : v;
         }
         if (RS) {
-            ulonglong2 *cr = (ulonglong2 *)(F.c + (size_t)p * F.ps + (size_t)limb * kp.n + blk + bD);
+            ulonglong2 *cr = (ulonglong2 *)(fuse_poly(F, p) + (size_t)limb * kp.n + blk + bD);
             const u64 iv = F.inv[pr], ivs = F.invs[pr];
 #pragma unroll
             for (int k = 0; k < 8; k++) {
@@ -3152,6 +3160,35 @@ int k_lincomb(const he_ctx *ctx, const u64 *const *x, const size_t *ps, const u6
 }
 
 // rescale of m ciphertexts laid out at a uniform stride (poly p of ct i at base + (2i + p) ps)
+// The same for m <= HE_NTT_TAB / 2 ciphertexts at unrelated addresses: polys[2j], polys[2j + 1]
+// are c0, c1 of ciphertext j (c1 = c0 + its poly stride); one launch set for all of them.
+int k_rescale_tab(const he_ctx *ctx, u64 *const *polys, int m, int level, u64 *t, cudaStream_t s) {
+    if (m <= 0) return HE_OK;
+    if (m > HE_NTT_TAB / 2) { he_set_error("rescale: at most %d ciphertexts per table", HE_NTT_TAB / 2); return HE_EINVAL; }
+    if (!(ctx->logn >= 12 && ctx->logn <= 16)) {           // small rings: one ciphertext at a time
+        for (int j = 0; j < m; j++)
+            HE_TRY(k_rescale_many(ctx, polys[2 * j], (size_t)(polys[2 * j + 1] - polys[2 * j]), 1, level, t, s));
+        return HE_OK;
+    }
+    ntt_job top{nullptr, 0, level, 1, level + 1, 0, 2 * m, 0};
+    for (int p = 0; p < 2 * m; p++) top.tab[p] = polys[p];
+    HE_TRY(k_ntt(ctx, top, true, s));
+    const u64 *cb = ctx->d_consts + ctx->np + 2 * (ctx->L + 1);
+    const u64 *inv = cb + (size_t)level * 2 * (ctx->L + 1);
+    RescaleFuse F{nullptr, 0, level, inv, inv + (ctx->L + 1)};
+    for (int p = 0; p < 2 * m; p++) F.ctab[p] = polys[p];
+    ntt_job tj{t, (size_t)level * ctx->n, 0, level, level, 0, 2 * m, 0};
+    const int R = ctx->n / ROW, TC = 4096 / R;
+    dim3 gA(ROW / TC, level, 2 * m), gB(R / 16, level, 2 * m);
+    TraceScope tr("rescale", s, (double)m * level * ctx->n * 8 * 6, (double)m * level * ctx->n * 2);
+    if (ntt_onepass(ctx)) return ntt_onepass_launch<false, true>(ctx, tj, F, s);
+    pdl_launch(ntt16_cols<false, true>, gA, 256, 0, s, ctx->kp, tj, F);
+    LAUNCH_CHECK();
+    pdl_launch(ntt16_rows<false, true>, gB, 256, 0, s, ctx->kp, tj, F);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
 int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u64 *t, cudaStream_t s) {
     ntt_job top{base, ps, level, 1, level + 1, 0, 2 * m, 0};
     HE_TRY(k_ntt(ctx, top, true, s));

@@ -3152,8 +3152,10 @@ extern "C" int he_poly_ps_plan(int deg, int *products, int *depth) {
 
 // sum_(coef, x) round(coef scale q_{l+1} / s_x) x + round(c0 scale q_{l+1}) at level l + 1, rescaled
 // to (l, scale); y is scratch for the term-by-term form
+// defer: stop before the rescale (out at level + 1, scale `scale` q_{l+1}); the caller rescales
+// it, possibly together with other combinations of the same level, and sets the scale to `scale`
 static int ps_lincomb(he_ctx *c, const std::vector<std::pair<double, const he_ct *>> &terms, double c0, int level,
-                      double scale, he_ct *out, he_ct *y, cudaStream_t s) {
+                      double scale, he_ct *out, he_ct *y, cudaStream_t s, bool defer = false) {
     const int lm = level + 1;
     const double ql = (double)c->primes[lm];
     const double cst = std::nearbyint(c0 * scale * ql);
@@ -3191,6 +3193,7 @@ static int ps_lincomb(he_ctx *c, const std::vector<std::pair<double, const he_ct
         HE_TRY(he_add_const_int(c, out, cst, s));
     }
     out->scale = scale * ql;
+    if (defer) return HE_OK;
     HE_TRY(he_rescale(c, out, s));
     out->scale = scale;
     return HE_OK;
@@ -3211,6 +3214,10 @@ struct PsOp {
     he_ct *out = nullptr;
     std::function<double()> expect;                           // product: predicted output scale
     bool done = false;
+    // a combination whose final rescale the scheduler batches with the other ready combinations
+    // of that level: fn leaves `rs` one level up and writes its target scale to *rs_scale
+    he_ct *rs = nullptr;
+    std::shared_ptr<double> rs_scale;
 };
 
 // A scale that is known once the ciphertexts in deps are computed.
@@ -3257,13 +3264,35 @@ static int ps_run(he_ctx *c, std::vector<PsOp> &ops, cudaStream_t s) {
     size_t left = ops.size();
     while (left) {
         bool moved = false;
+        std::vector<size_t> rs_pend;                       // combinations awaiting their rescale
         for (size_t i = 0; i < ops.size(); i++)
             if (!ops[i].done && !ops[i].prod && ready(i)) {
                 HE_TRY(ops[i].fn());
+                if (ops[i].rs) {
+                    rs_pend.push_back(i);
+                    continue;
+                }
                 ops[i].done = true;
                 left--;
                 moved = true;
             }
+        // one batched rescale per level for the combinations issued in this pass (ops that read
+        // them were not ready, so nothing has used them yet)
+        while (!rs_pend.empty()) {
+            const int lv = ops[rs_pend[0]].rs->level;
+            std::vector<size_t> here, rest;
+            for (size_t i : rs_pend) (ops[i].rs->level == lv ? here : rest).push_back(i);
+            std::vector<he_ct *> grp;
+            for (size_t i : here) grp.push_back(ops[i].rs);
+            HE_TRY(rescale_batch(c, grp.data(), (int)grp.size(), s));
+            for (size_t i : here) {
+                ops[i].rs->scale = *ops[i].rs_scale;
+                ops[i].done = true;
+                left--;
+            }
+            moved = true;
+            rs_pend = rest;
+        }
         std::vector<size_t> P;
         std::vector<he_ct> va, vb;
         int lv = -1;
@@ -3325,7 +3354,13 @@ struct PsGroup {
         for (auto &t : terms) tv.push_back({t.first, T[j][t.second]});
         he_ct *yj = y[j];
         std::function<double()> f = sc.f;
-        o.fn = [cc, st, tv, c0, level, f, out, yj]() { return ps_lincomb(cc, tv, c0, level, f(), out, yj, st); };
+        auto rs_scale = std::make_shared<double>(0.0);
+        o.rs = out;
+        o.rs_scale = rs_scale;
+        o.fn = [cc, st, tv, c0, level, f, out, yj, rs_scale]() {
+            *rs_scale = f();
+            return ps_lincomb(cc, tv, c0, level, *rs_scale, out, yj, st, true);
+        };
         ops.push_back(std::move(o));
     }
     void add(he_ct *acc, he_ct *b) {
