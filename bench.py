@@ -964,7 +964,7 @@ def main():
         line["serving"] = {k: sv[k] for k in ("workload", "server", "max_batch", "conv", "setup_s",
                                               "service_ms_alone", "capacity_images_per_s", "runs", "memory")}
     if rank == 0:
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and ws == 1:              # the oracle baseline: rank 0 at N = 1 only
             line["cpu_baseline"] = cpu_baseline(48)          # ~10 s of oracle work on every core
             line["cpu_baseline"]["cpu_model"] = cpu_model()
             line["cpu_baseline"]["single_thread"] = cpu_baseline_single_thread(3)
