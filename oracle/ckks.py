@@ -9,7 +9,10 @@ silent on the internals, so the oracle fixes the textbook hybrid-key-switching R
 construction, one convention per step:
 
   storage      coefficient form, limb-major [poly][limb][n], residues in [0, q)
-  secret       uniform ternary (SplitMix64 word mod 3)
+  secret       uniform ternary (SplitMix64 word mod 3), or with secret_hw = h > 0 a sparse
+               ternary secret: a partial Fisher-Yates shuffle of 0..n-1 whose step k swaps
+               position k with k + (word 2k mod (n - k)) and gives the coefficient at the
+               position it lands on the sign + (word 2k+1 even) or - (odd), k < h
   errors       centred binomial eta=21
   uniform a    128-bit word pair mod q, sampled in coefficient form per limb
   encrypt      (c0, c1) = (-a s + e + m, a)  over Q_l
@@ -38,13 +41,14 @@ import numpy as np
 
 from . import _lib
 from .params import Params, gen_primes, primitive_2n_root
-from .encode import encode, decode
+from .encode import encode, decode, decode_complex
 
 STREAM_SECRET = 1
 STREAM_KEY_A = 2 << 56
 STREAM_KEY_E = 3 << 56
 STREAM_ENC_A = 4 << 56
 STREAM_ENC_E = 5 << 56
+STREAM_SECRET_SPARSE = 6 << 56
 
 
 def _u64(a):
@@ -83,11 +87,27 @@ class Context:
         self.lib = _lib.lib()
         self.seed = params.seed
         # ternary secret in Z (int64 coefficients)
-        s = np.zeros(self.n, dtype=np.int64)
-        self.lib.orc_sample_ternary(self.seed, STREAM_SECRET, self.n, s)
+        if params.secret_hw > 0:
+            s = self.sparse_secret(params.secret_hw)
+        else:
+            s = np.zeros(self.n, dtype=np.int64)
+            self.lib.orc_sample_ternary(self.seed, STREAM_SECRET, self.n, s)
         self.s_int = s
         self.keys = {}          # key_id -> list over digits of (b, a) eval form over Q_L u P
         self._s_eval_cache = {}
+
+    def sparse_secret(self, h):
+        """Exactly h coefficients +-1 at distinct positions (partial Fisher-Yates, module doc)."""
+        n = self.n
+        assert 0 < h <= n
+        perm = list(range(n))
+        s = np.zeros(n, dtype=np.int64)
+        for k in range(h):
+            r = int(self.lib.orc_rng(self.seed, STREAM_SECRET_SPARSE, 2 * k)) % (n - k)
+            perm[k], perm[k + r] = perm[k + r], perm[k]
+            odd = int(self.lib.orc_rng(self.seed, STREAM_SECRET_SPARSE, 2 * k + 1)) & 1
+            s[perm[k]] = -1 if odd else 1
+        return s
 
     # ------------------------------------------------------------ prime bookkeeping
     def mods(self, level, ext=False):
@@ -238,6 +258,16 @@ class Context:
             self.keys[g] = self._gen_ksk(g, self.secret_int_automorph(g))
         return g
 
+    def conj_galois(self):
+        """Galois element of complex conjugation of the slots: X -> X^{2n-1} = X^{-1}."""
+        return 2 * self.n - 1
+
+    def gen_conj_key(self):
+        g = self.conj_galois()
+        if g not in self.keys:
+            self.keys[g] = self._gen_ksk(g, self.secret_int_automorph(g))
+        return g
+
     def gen_relin_key(self):
         if 0 not in self.keys:
             L = self.L
@@ -293,6 +323,10 @@ class Context:
     def decrypt(self, ct):
         coeffs = self.decrypt_coeffs(ct)
         return decode(np.array([float(c) for c in coeffs]), self.n, ct.scale)
+
+    def decrypt_complex(self, ct):
+        coeffs = self.decrypt_coeffs(ct)
+        return decode_complex(np.array([float(c) for c in coeffs]), self.n, ct.scale)
 
     # ------------------------------------------------------------ basic ops
     def rescale(self, ct):
@@ -414,6 +448,52 @@ class Context:
         c1 = self.automorph_coeff(ct.c[1], g, mods)
         k0, k1 = self.key_switch(c1, ct.level, g)
         return Ciphertext(np.stack([self.add(c0, k0, mods), k1]), ct.level, ct.scale)
+
+    def conjugate(self, ct):
+        """Slot-wise complex conjugate: phi_g with g = 2n - 1 (zeta^{g_i} -> zeta^{-g_i}), then a
+        non-hoisted key switch from phi_g(s) back to s."""
+        g = self.conj_galois()
+        assert g in self.keys, "conjugation key missing"
+        mods = self.mods(ct.level)
+        c0 = self.automorph_coeff(ct.c[0], g, mods)
+        c1 = self.automorph_coeff(ct.c[1], g, mods)
+        k0, k1 = self.key_switch(c1, ct.level, g)
+        return Ciphertext(np.stack([self.add(c0, k0, mods), k1]), ct.level, ct.scale)
+
+    def mul_monomial(self, ct, k):
+        """Multiply both polynomials by X^k in Z_Q[X]/(X^n + 1) (exact; no level, no noise).
+        Slot i is multiplied by zeta^{k g_i}; k = n/2 multiplies every slot by i, since
+        g_i = 1 mod 4."""
+        n = self.n
+        k %= 2 * n
+        sign = 1
+        if k >= n:
+            k -= n
+            sign = -1
+        mods = self.mods(ct.level)
+        out = np.empty_like(ct.c)
+        for p in range(ct.c.shape[0]):
+            a = ct.c[p]
+            hi = self.neg(a[:, n - k:], mods) if k else a[:, :0]
+            rot = np.concatenate([hi, a[:, :n - k]], axis=1)    # X^k: j -> j + k, wrap negated
+            out[p] = rot if sign > 0 else self.neg(rot, mods)
+        return Ciphertext(out, ct.level, ct.scale)
+
+    def modraise(self, ct, level=None):
+        """A level-0 ciphertext read over Q_level (default L): every residue mod q_0 is lifted to
+        its centred representative in (-q_0/2, q_0/2] and reduced mod q_0..q_level.  The result
+        decrypts to t = [c0 + c1 s]_{q_0} + q_0 I for an integer polynomial I with
+        |I| <= (||s||_1 + 1) / 2 (the centred c0 + c1 s over Z, divided by q_0)."""
+        assert ct.level == 0
+        level = self.L if level is None else level
+        q0 = self.q[0]
+        mods = self.mods(level)
+        out = np.empty((ct.c.shape[0], level + 1, self.n), dtype=np.uint64)
+        for p in range(ct.c.shape[0]):
+            x = ct.c[p, 0].astype(np.int64)
+            x = np.where(2 * x > q0, x - q0, x)
+            out[p] = self.reduce_int(x, mods)
+        return Ciphertext(out, level, ct.scale)
 
     def hoist(self, ct):
         """ModUp(c1) once per ciphertext, digits in eval form."""

@@ -1200,6 +1200,22 @@ def cheb_ps_slots(c, t):
     return ev(list(c))
 
 
+def cheb_ps_need(cc, k, giants):
+    """Levels the Paterson-Stockmeyer evaluation of sum cc_i T_i consumes below its input's
+    level (cheb_ps_he's recursion; T_i of the binary tree costs bit_length(i - 1) levels)."""
+    d = len(cc) - 1
+    depth = lambda i: (i - 1).bit_length()
+    if d < k:
+        return 1 + max([depth(i) for i in range(1, d + 1)] + [0])
+    G = max(g for g in giants if g <= d)
+    q, r = cheb_divide(cc, G)
+    if len(q) == 1 and G - 1 < k:
+        return 1 + max([depth(G)] + [depth(i) for i in range(1, G)])
+    if len(q) == 1:
+        return max(1 + depth(G), cheb_ps_need(r, k, giants))
+    return max(cheb_ps_need(q, k, giants) + 1, depth(G) + 1, cheb_ps_need(r, k, giants))
+
+
 def cheb_ps_he(ctx, ct, c, target_scale=None):
     """Homomorphic Paterson-Stockmeyer evaluation of sum c_k T_k(ct) in the Chebyshev basis.
 
@@ -1257,18 +1273,7 @@ def cheb_ps_he(ctx, ct, c, target_scale=None):
         return out
 
     def need(cc):
-        """levels consumed below the input level by ev(cc)"""
-        d = len(cc) - 1
-        depth = lambda i: (i - 1).bit_length()
-        if d < k:
-            return 1 + max([depth(i) for i in range(1, d + 1)] + [0])
-        G = max(g for g in giants if g <= d)
-        q, r = cheb_divide(cc, G)
-        if len(q) == 1 and G - 1 < k:
-            return 1 + max([depth(G)] + [depth(i) for i in range(1, G)])
-        if len(q) == 1:
-            return max(1 + depth(G), need(r))
-        return max(need(q) + 1, depth(G) + 1, need(r))
+        return cheb_ps_need(cc, k, giants)
 
     def ev(cc, level, scale):
         d = len(cc) - 1

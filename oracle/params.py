@@ -60,6 +60,7 @@ class Params:
     p_bits: int
     scale: float        # Delta
     seed: int
+    secret_hw: int = 0  # 0: uniform ternary secret; h > 0: exactly h non-zero +-1 coefficients
 
     @property
     def n(self):
@@ -108,3 +109,18 @@ C20 = Params(log_n=16, n_q=20, n_p=5, dnum=4, q0_bits=50, q_bits=40, p_bits=50,
              scale=2.0 ** 40, seed=0)
 S33 = Params(log_n=16, n_q=33, n_p=11, dnum=3, q0_bits=50, q_bits=40, p_bits=50,
              scale=2.0 ** 40, seed=0)
+
+# Bootstrapping sets.  The modular reduction of the raised ciphertext is approximated on
+# [-K, K], K a bound on the integer I of t = m + q_0 I.  I is a sum of h + 1 terms in
+# [-1/2, 1/2] (h = the secret's Hamming weight): |I| <= (h + 1) / 2 always, with standard
+# deviation about sqrt((h + 1) / 12).  A uniform ternary secret at n = 2^16 would need K in the
+# hundreds, so these sets use a sparse secret of weight 64 (deviation 2.3; K = 16 is 7 of them).
+# Every prime has 50 bits and the scale is 2^50: the bootstrap's sine step runs at that scale,
+# and a level-0 input at scale 2^40 keeps q_0 / scale = 2^10 for its small-angle reading.
+# B24: ring 2^16, 23 levels (15 for the bootstrap, 8 for the network between bootstraps),
+# log2(QP) = 1500.  BOOT12: ring 2^12 with the same 15-level bootstrap plus one level to spare,
+# small enough for the oracle to run a whole bootstrap in seconds.
+B24 = Params(log_n=16, n_q=24, n_p=6, dnum=4, q0_bits=50, q_bits=50, p_bits=50,
+             scale=2.0 ** 50, seed=0, secret_hw=64)
+BOOT12 = Params(log_n=12, n_q=17, n_p=4, dnum=6, q0_bits=50, q_bits=50, p_bits=50,
+                scale=2.0 ** 50, seed=0, secret_hw=64)
