@@ -68,7 +68,9 @@ typedef struct he_poly he_poly;
  * Key switching is hybrid with dnum digits of alpha = ceil(n_q/dnum) primes; he_ctx_create
  * rejects sets whose special-prime product P is smaller than the largest digit modulus.
  * seed keys the counter-based SplitMix64 generator that draws the secret, key and
- * encryption randomness (stream ids in the design notes). */
+ * encryption randomness (stream ids in the design notes).  A sparse secret (secret_hw = h)
+ * takes, for k < h, word 2k of stream 6 << 56 modulo n - k as the swap offset of step k and
+ * word 2k + 1's low bit as its sign (1: -1). */
 typedef struct {
     int log_n;       /* 9..17 */
     int n_q;         /* ciphertext primes, L = n_q - 1 */
@@ -77,6 +79,9 @@ typedef struct {
     int q0_bits, q_bits, p_bits;   /* each in [20, 61] */
     double scale;    /* Delta */
     uint64_t seed;
+    int secret_hw;   /* 0: uniform ternary secret; h in 1..n: sparse ternary secret with exactly
+                        h coefficients +-1 (bootstrapping's modular reduction needs the small
+                        |I| a sparse secret gives); drawn by a partial Fisher-Yates shuffle */
 } he_params;
 
 /* Image layout metadata (Sec. 4 "Sharding and Encrypting an Image", "Duplicating and
@@ -240,6 +245,9 @@ int he_ctx_info(const he_ctx *ctx, int *n, int *slots, int *L, int *K, int *dnum
 int he_keygen_rotations(he_ctx *ctx, const int32_t *rot, size_t n_rot);
 /* Relinearisation key (switches s^2 to s). */
 int he_keygen_relin(he_ctx *ctx);
+/* Conjugation key: Galois element 2n - 1 (X -> X^-1 maps every slot to its complex
+ * conjugate), the key bootstrapping's real/imaginary split needs. */
+int he_keygen_conjugation(he_ctx *ctx);
 int he_has_rotation_key(const he_ctx *ctx, int32_t rot);
 /* Key in coefficient form, host layout [dnum][2][L+1+K][n]; rot = HE_RELIN_KEY for relin. */
 int he_key_export(he_ctx *ctx, int32_t rot, uint64_t *host);
@@ -318,6 +326,18 @@ int he_mul_int(he_ctx *ctx, he_ct *ct, double c, void *stream);
 int he_add_const_int(he_ctx *ctx, he_ct *ct, double c, void *stream);
 /* Tensor, relinearise, rescale (levels must match; Appendix, Chebyshev evaluation). */
 int he_mul_relin(he_ctx *ctx, const he_ct *a, const he_ct *b, he_ct *out, void *stream);
+/* Slot-wise complex conjugate: phi_g with g = 2n - 1, then a non-hoisted key switch (needs
+ * he_keygen_conjugation).  out may not alias in. */
+int he_conjugate(he_ctx *ctx, const he_ct *in, he_ct *out, void *stream);
+/* Both polynomials times X^e in Z_Q[X]/(X^n + 1), in place (any integer e, taken mod 2n;
+ * X^n = -1).  Exact: no level, no noise.  Slot i is multiplied by zeta^(e g_i); e = n/2
+ * multiplies every slot by the imaginary unit (g_i = 1 mod 4). */
+int he_mul_monomial(he_ctx *ctx, he_ct *ct, int64_t e, void *stream);
+/* ModRaise (bootstrapping's first step): a level-0 ciphertext read over Q_level, every
+ * residue mod q_0 lifted to its centred representative in (-q_0/2, q_0/2].  The result
+ * decrypts to t = m + q_0 I with |I| <= (||s||_1 + 1) / 2; scale unchanged.  out may not
+ * alias in and must be allocated at `level` or above (HE_ELEVEL otherwise). */
+int he_modraise(he_ctx *ctx, const he_ct *in, int level, he_ct *out, void *stream);
 
 /* ------------------------------------------------------------------ layers (Sec. 4) */
 /* Plan a stride-1 'same' convolution (cross-correlation, W[co][ci][kh][kw], bias[co] or
@@ -422,6 +442,61 @@ int he_conv_import_bias(he_conv *conv, int level, double out_scale, const int64_
  * the plan and the resident plaintexts, and owns its run buffers, so forks run concurrently
  * on their own streams.  Destroy forks before the original. */
 int he_conv_fork(const he_conv *conv, he_ctx *ctx, he_conv **out);
+
+/* ------------------------------------------------------------------ bootstrapping */
+/* Restores the level of a level-0 ciphertext (Sec. 2: the level is restored through
+ * bootstrapping; Sec. 5 tables: the Bootstrap rows, the largest cost of the paper's networks;
+ * the paper runs OpenFHE's and does not define it).  This library's construction, in order:
+ *   ModRaise (he_modraise to level L; scale set to q_0 K: slots hold t / (q_0 K));
+ *   CoeffToSlot: the inverse of the encoding map U_ij = zeta^(g_i j) (slots z = U w for the
+ *     complex coefficient vector w_j = t_j + i t_(j+N)), factored as the radix-2 butterfly
+ *     stages 2 S_h^-1, h = N/2 .. 1 (twiddle exp(2 pi i (5^j mod 8h) / 8h)), merged into
+ *     levels_cts levels; each level a baby-step giant-step product with its non-zero
+ *     diagonals: a raised-basis stage with one ModDown per partial sum, a giant stage with
+ *     one ModDown, one rescale (scale times 2^stages); output BR(w) / (q_0 K);
+ *   retarget: times the integer round((Delta / 2) q_l / s), rescale (scale s k / q_l);
+ *   split: c = conj(x); re = x + c, im = (x - c) X^(3n/2), both at twice the scale;
+ *   EvalMod on re and im: cos(2 pi (K u - 1/4) / 2^r) as a degree-deg Chebyshev interpolant
+ *     in u on [-1, 1] (Paterson-Stockmeyer, target scale Delta), then r double angles
+ *     y <- 2 y^2 - 1: sin(2 pi t / q_0) ~ 2 pi m / q_0;
+ *   re + im X^(n/2), scale times 2 pi Delta_in / q_0 (Delta_in: the input's scale);
+ *   SlotToCoeff: S_h, h = 1 .. N/2, merged into levels_stc levels the same way.
+ * Levels used: levels_cts + 1 + (Paterson-Stockmeyer depth of deg) + r + levels_stc
+ * (15 with the defaults); the output sits at L minus that, same slot values, scale as above.
+ * Needs K >= max |I| (|I| <= (h + 1) / 2 for a weight-h secret: he_params.secret_hw), and
+ * q_0 / Delta_in large enough for sin(x) ~ x (2^10 gives about 2^-17 relative). */
+typedef struct he_boot he_boot;
+typedef struct {
+    int K;            /* EvalMod domain [-K, K] (default 16) */
+    int double_angle; /* r (default 2) */
+    int deg;          /* Chebyshev degree of the cosine, 2..255 (default 59) */
+    int levels_cts;   /* merged CoeffToSlot levels (default 3) */
+    int levels_stc;   /* merged SlotToCoeff levels (default 3) */
+} he_boot_config;
+/* Plans the levels (diagonals, baby-step giant-step split), encodes the diagonals at scale
+ * q_level over Q_level u P, and the cosine's coefficients.  cfg NULL or zero fields take the
+ * defaults.  Keys are not generated: he_boot_rotations, he_keygen_conjugation, relin. */
+int he_boot_create(he_ctx *ctx, const he_boot_config *cfg, he_boot **out);
+void he_boot_destroy(he_boot *bt);
+/* Distinct non-zero rotation amounts the linear levels use (count returned; amounts filled
+ * up to cap). */
+int he_boot_rotations(const he_boot *bt, int32_t *amounts, size_t cap);
+/* Levels: the output level, the top level of CoeffToSlot / EvalMod input / SlotToCoeff, and
+ * the key switches of one bootstrap (rotations, conjugation, relinearisations). */
+int he_boot_info(const he_boot *bt, int *out_level, int *cts_level, int *evalmod_level, int *stc_level,
+                 int *keyswitches);
+/* Plaintexts of linear level idx of stage 0 (CoeffToSlot) or 1 (SlotToCoeff): their count,
+ * and a replacement by caller-given integer polynomials ([count][n], giant index ascending,
+ * then baby index ascending, at scale q_level) for a bit-exact comparison with another
+ * encoder; he_boot_import_coeffs replaces the cosine's Chebyshev coefficients likewise. */
+int he_boot_n_plaintexts(const he_boot *bt, int stage, int idx);
+int he_boot_import_plaintexts(he_boot *bt, int stage, int idx, const int64_t *pts);
+int he_boot_import_coeffs(he_boot *bt, const double *cheb, int deg);
+/* One linear level on its own (for tests): in at the level's level, out one level lower. */
+int he_boot_lintrans(he_ctx *ctx, he_boot *bt, int stage, int idx, const he_ct *in, he_ct *out, void *stream);
+/* The whole bootstrap; in at level 0 (any scale), out allocated at the output level or above
+ * (HE_ELEVEL otherwise). */
+int he_bootstrap(he_ctx *ctx, he_boot *bt, const he_ct *in, he_ct *out, void *stream);
 
 /* ------------------------------------------------------------------ polynomial approximation (Appendix) */
 /* Activation functions: GELU x Phi(x) (exact erf), ReLU, SiLU x / (1 + e^-x), Softplus. */

@@ -426,6 +426,10 @@ static int create(const he_params *pr, he_ctx **out) {
             return HE_EINVAL;
         }
     }
+    if (pr->secret_hw < 0 || pr->secret_hw > (1 << pr->log_n)) {
+        he_set_error("parameters: secret_hw must lie in [0, n]");
+        return HE_EINVAL;
+    }
     he_ctx *c = new he_ctx();
     c->pr = *pr;
     c->logn = pr->log_n;
@@ -562,7 +566,7 @@ static int create(const he_params *pr, he_ctx **out) {
     if (rc == HE_OK) rc = c->sc_tmp.ensure(3 * ext);
     if (rc == HE_OK) rc = c->sc_tmp2.ensure(ext);
     if (rc != HE_OK) { free_ctx(c); return rc; }
-    // ---- secret key: ternary s, NTT form over every prime
+    // ---- secret key: ternary s (uniform, or sparse of a given weight), NTT form over every prime
     int64_t *s_int = nullptr;
     if (he_malloc(&c->d_s, (size_t)np * n * 8) != cudaSuccess ||
         he_malloc(&s_int, (size_t)n * 8) != cudaSuccess) {
@@ -579,7 +583,9 @@ static int create(const he_params *pr, he_ctx **out) {
         he_set_error("error-word allocation failed");
         return HE_ENOMEM;
     }
-    rc = k_sample_ternary(c, pr->seed, 1, s_int, 0);
+    // uniform ternary, or sparse of weight secret_hw (stream 6 << 56; the permutation in sc_tmp)
+    if (pr->secret_hw > 0) rc = k_sample_sparse(c, pr->seed, 6ull << 56, pr->secret_hw, (int32_t *)c->sc_tmp.p, s_int, 0);
+    else rc = k_sample_ternary(c, pr->seed, 1, s_int, 0);
     if (rc == HE_OK) rc = k_reduce_int(c, s_int, c->d_s, np, Q, false, 0);
     if (rc == HE_OK) rc = ntt_poly(c, c->d_s, 0, 0, np, Q, 1, false, 0);
     cudaDeviceSynchronize();
@@ -681,6 +687,17 @@ extern "C" int he_keygen_relin(he_ctx *c) {
     u64 *sp = c->sc_tmp2.p;
     HE_TRY(k_mul_pointwise(c, c->d_s, c->d_s, sp, c->np, 0));
     HE_TRY(gen_key(c, 0, sp, 0));
+    HE_CHECK_CUDA(cudaStreamSynchronize(0));
+    return HE_OK;
+}
+
+extern "C" int he_keygen_conjugation(he_ctx *c) {
+    if (!c) { he_set_error("null context"); return HE_EINVAL; }
+    const u64 g = 2ull * c->n - 1;
+    if (c->root()->keys.count((int)g)) return HE_OK;
+    u64 *sp = c->sc_tmp2.p;
+    HE_TRY(k_permute(c, c->d_s, sp, c->np, g, 0));
+    HE_TRY(gen_key(c, (int)g, sp, 0));
     HE_CHECK_CUDA(cudaStreamSynchronize(0));
     return HE_OK;
 }
@@ -1180,6 +1197,47 @@ extern "C" int he_rotate(he_ctx *c, const he_ct *in, int32_t r, he_ct *out, void
     HE_TRY(k_permute(c, in->d + in->pstride, d, in->level + 1, g, s));
     // non-hoisted: d = phi_g(c1) is raised; c0 enters the combine through phi_g
     return keyswitch_core(c, d, in->level, *key, 1, in->d, in->pstride, 1, g, out, s);
+}
+
+extern "C" int he_conjugate(he_ctx *c, const he_ct *in, he_ct *out, void *stream) {
+    if (!c || !in || !out || in == out) { he_set_error("he_conjugate: bad argument"); return HE_EINVAL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const u64 g = 2ull * c->n - 1;
+    const DeviceKey *key;
+    HE_TRY(get_key(c, (int)g, &key));
+    HE_TRY(ensure_ct(c, out, in->level));
+    out->scale = in->scale;
+    u64 *d = c->sc_tmp.p;
+    HE_TRY(k_permute(c, in->d + in->pstride, d, in->level + 1, g, s));
+    return keyswitch_core(c, d, in->level, *key, 1, in->d, in->pstride, 1, g, out, s);
+}
+
+extern "C" int he_mul_monomial(he_ctx *c, he_ct *ct, int64_t e, void *stream) {
+    if (!c || !ct || ct->ctx != c) { he_set_error("he_mul_monomial: bad argument"); return HE_EINVAL; }
+    const int64_t two_n = 2 * (int64_t)c->n;
+    const u64 ee = (u64)(((e % two_n) + two_n) % two_n);
+    if (ee == 0) return HE_OK;
+    return k_monomial(c, ct->d, ct->pstride, ct->level + 1, ee, (cudaStream_t)stream);
+}
+
+extern "C" int he_modraise(he_ctx *c, const he_ct *in, int level, he_ct *out, void *stream) {
+    if (!c || !in || !out || in == out || in->ctx != c) { he_set_error("he_modraise: bad argument"); return HE_EINVAL; }
+    if (in->level != 0 || level < 0 || level > c->L) {
+        he_set_error("he_modraise: input at level %d (needs 0), target level %d", in->level, level);
+        return HE_ELEVEL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    HE_TRY(ensure_ct(c, out, level));
+    const size_t n = c->n;
+    u64 *t = c->sc_tmp.p;                                   // [2][n]: c0, c1 mod q_0, coefficient form
+    HE_TRY(k_copy_limbs(t, n, in->d, in->pstride, n, 2, s));
+    ntt_job ji{t, n, 0, 1, 1, 0, 2};
+    HE_TRY(k_ntt(c, ji, true, s));
+    HE_TRY(k_modraise(c, t, out->d, out->pstride, level + 1, s));
+    ntt_job jf{out->d, out->pstride, 0, level + 1, level + 1, 0, 2};
+    HE_TRY(k_ntt(c, jf, false, s));
+    out->scale = in->scale;
+    return HE_OK;
 }
 
 extern "C" int he_rotate_hoisted(he_ctx *c, const he_ct *in, const int32_t *r, size_t n_r,

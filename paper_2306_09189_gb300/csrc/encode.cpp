@@ -3,6 +3,8 @@
 // zeta^{5^i mod 2n}, zeta = exp(i pi / n); a real slot vector z has the real coefficients
 // m_j = (2S/n) sum_i z_i cos(pi g_i j / n), computed with one complex FFT of length 2n.
 // Encoding is preprocessing: it runs on the host and never touches ciphertext arithmetic.
+// Complex slot values (the diagonals of bootstrapping's linear maps) take the real polynomial
+// with m(zeta^g_i) = S z_i and m(zeta^-g_i) = S conj(z_i): m_j = (2S/n) sum_i Re(z_i zeta^(-g_i j)).
 #include <cmath>
 #include <complex>
 #include <map>
@@ -87,6 +89,21 @@ void encode_slots(const double *z, int n, double S, int64_t *m_out) {
     for (int j = 0; j < n; j++) {
         double v = S / n * A[j].real();
         double r = v >= 0 ? std::floor(v + 0.5) : std::ceil(v - 0.5);   // half away from zero
+        m_out[j] = (int64_t)r;
+    }
+}
+
+void encode_slots_complex(const double *re, const double *im, int n, double S, int64_t *m_out) {
+    std::vector<int> g = slot_exponents(n);
+    std::vector<cd> A(2 * (size_t)n, cd(0, 0));
+    for (int i = 0; i < n / 2; i++) {
+        A[g[i]] = cd(re[i], im[i]);
+        A[2 * n - g[i]] = cd(re[i], -im[i]);
+    }
+    fft(A);
+    for (int j = 0; j < n; j++) {
+        double v = S / n * A[j].real();
+        double r = v >= 0 ? std::floor(v + 0.5) : std::ceil(v - 0.5);
         m_out[j] = (int64_t)r;
     }
 }

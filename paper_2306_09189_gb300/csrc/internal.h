@@ -177,6 +177,13 @@ int k_sample_uniform(const he_ctx *ctx, u64 seed, u64 stream, u64 *out, int nlim
 int k_sample_cbd(const he_ctx *ctx, u64 seed, u64 stream, int64_t *out, cudaStream_t s);
 int k_sample_ternary(const he_ctx *ctx, u64 seed, u64 stream, int64_t *out, cudaStream_t s);
 int k_permute(const he_ctx *ctx, const u64 *in, u64 *out, int nlimbs, u64 g, cudaStream_t s);
+// sparse ternary secret of weight h (perm: n words of scratch)
+int k_sample_sparse(const he_ctx *ctx, u64 seed, u64 stream, int h, int32_t *perm, int64_t *out, cudaStream_t s);
+// ModRaise: in_coef [2][n] coefficient form mod q_0 -> out [2][nlimbs][n] (poly stride pstride),
+// coefficient form mod q_0..q_{nlimbs-1}
+int k_modraise(const he_ctx *ctx, const u64 *in_coef, u64 *out, size_t pstride, int nlimbs, cudaStream_t s);
+// both polynomials (NTT form, q-limbs 0..nlimbs-1) times X^e, 0 <= e < 2n
+int k_monomial(const he_ctx *ctx, u64 *d, size_t pstride, int nlimbs, u64 e, cudaStream_t s);
 int k_keygen_combine(const he_ctx *ctx, u64 *b, u64 *a, const u64 *e, const u64 *s_eval,
                      const u64 *sp_eval, int digit, cudaStream_t s);
 int k_encrypt_combine(const he_ctx *ctx, u64 *c0, const u64 *a, const u64 *e, const u64 *m,
@@ -371,6 +378,7 @@ u64 h_shoup(u64 w, u64 q);
 u64 h_galois(const he_ctx *ctx, int32_t r);
 int prime_index(const he_ctx *ctx, int limb, int nq);   // limb of a Q_l u P polynomial -> prime
 void encode_slots(const double *z, int n, double S, int64_t *m_out);
+void encode_slots_complex(const double *re, const double *im, int n, double S, int64_t *m_out);
 void decode_coeffs(const double *m, int n, double S, double *z_out);
 int ensure_ct(he_ctx *ctx, he_ct *ct, int level);
 bool int_residue(double v, u64 q, u64 *out);   // exact-integer double -> residue mod q

@@ -693,6 +693,65 @@ __global__ void mul_pointwise_kernel(KP kp, const u64 *a, const u64 *b, u64 *out
     out[i] = mul_mod(a[i], b[i], kp.q[t], kp.qinv[t], kp.r2[t]);
 }
 
+// Sparse ternary secret of weight h: a partial Fisher-Yates shuffle of 0..n-1.  Step k swaps
+// position k with k + (word 2k mod (n - k)) and gives the coefficient at the position it lands
+// on the sign + (word 2k + 1 even) or - (odd).  One block: the threads clear the output and
+// lay out the identity permutation, then one thread walks the h steps (h <= n, no waits).
+__global__ void sample_sparse_kernel(int n, u64 seed, u64 stream, int h, int32_t *perm, int64_t *out) {
+    pdl_wait();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        perm[i] = i;
+        out[i] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < h; k++) {
+        const int r = (int)(sm64_word(seed, stream, 2 * (u64)k) % (u64)(n - k));
+        const int32_t t = perm[k];
+        perm[k] = perm[k + r];
+        perm[k + r] = t;
+        const bool odd = sm64_word(seed, stream, 2 * (u64)k + 1) & 1;
+        out[perm[k]] = odd ? -1 : 1;
+    }
+}
+
+// Coefficient-form residues mod q_0 (poly p at in + p n) lifted to their centred
+// representatives in (-q_0/2, q_0/2] and reduced mod q_l, l < nl (ModRaise).
+__global__ void modraise_kernel(KP kp, const u64 *in, u64 *out, size_t pstride) {
+    pdl_wait();
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int l = blockIdx.y;
+    const int p = blockIdx.z;
+    const u64 q0 = kp.q[0], q = kp.q[l], mu = kp.mu[l];
+    const u64 x = in[(size_t)p * kp.n + k];
+    u64 r;
+    if (x > q0 - x) {                           // 2x > q_0: the representative x - q_0 < 0
+        const u64 m = reduce64(q0 - x, q, mu);
+        r = m ? q - m : 0;
+    } else {
+        r = reduce64(x, q, mu);
+    }
+    out[(size_t)p * pstride + (size_t)l * kp.n + k] = r;
+}
+
+// Both polynomials times the monomial X^e (0 <= e < 2n) in NTT form: slot k holds
+// a(psi^(2 brev(k) + 1)), so it is multiplied by psi^(e (2 brev(k) + 1) mod 2n), read from the
+// forward twiddle table (psi^j at position brev(j), j < n; psi^(j + n) = -psi^j).
+__global__ void monomial_kernel(KP kp, u64 *d, size_t pstride, u64 e) {
+    pdl_wait();
+    const int k = blockIdx.x * TB + threadIdx.x;
+    const int l = blockIdx.y;
+    const u64 q = kp.q[l];
+    const unsigned bk = __brev((unsigned)k) >> (32 - kp.logn);
+    const u64 ex = (e * (2 * (u64)bk + 1)) & ((2ull << kp.logn) - 1);
+    const bool neg = ex >= (u64)kp.n;
+    const unsigned j = (unsigned)(neg ? ex - kp.n : ex);
+    const size_t w = (size_t)l * kp.n + (__brev(j) >> (32 - kp.logn));
+    u64 *x = d + (size_t)blockIdx.z * pstride + (size_t)l * kp.n + k;
+    const u64 v = mul_shoup(*x, kp.tw[w], kp.tws[w], q);
+    *x = neg && v ? q - v : v;
+}
+
 __global__ void add_const_kernel(KP kp, u64 *a, const u64 *res) {
     pdl_wait();
     const int k = blockIdx.x * TB + threadIdx.x;
@@ -2311,6 +2370,24 @@ int k_add_raw(const he_ctx *ctx, u64 *a, size_t pa, const u64 *b, size_t pb, int
 
 int k_mul_scalar(const he_ctx *ctx, he_ct *ct, const u64 *res, const u64 *shoup, cudaStream_t s) {
     pdl_launch(mul_scalar_kernel, dim3(ctx->n / TB, ct->level + 1, 2), TB, 0, s, ctx->kp, ct->d, ct->pstride, res, shoup);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+int k_sample_sparse(const he_ctx *ctx, u64 seed, u64 stream, int h, int32_t *perm, int64_t *out, cudaStream_t s) {
+    pdl_launch(sample_sparse_kernel, 1, 1024, 0, s, ctx->n, seed, stream, h, perm, out);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+int k_modraise(const he_ctx *ctx, const u64 *in_coef, u64 *out, size_t pstride, int nlimbs, cudaStream_t s) {
+    pdl_launch(modraise_kernel, dim3(ctx->n / TB, nlimbs, 2), TB, 0, s, ctx->kp, in_coef, out, pstride);
+    LAUNCH_CHECK();
+    return HE_OK;
+}
+
+int k_monomial(const he_ctx *ctx, u64 *d, size_t pstride, int nlimbs, u64 e, cudaStream_t s) {
+    pdl_launch(monomial_kernel, dim3(ctx->n / TB, nlimbs, 2), TB, 0, s, ctx->kp, d, pstride, e);
     LAUNCH_CHECK();
     return HE_OK;
 }

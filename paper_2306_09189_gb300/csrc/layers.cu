@@ -12,6 +12,7 @@
 #include <atomic>
 #include <array>
 #include <cmath>
+#include <complex>
 #include <functional>
 #include <thread>
 #include <unordered_map>
@@ -3986,4 +3987,433 @@ extern "C" int he_layout_image(int c, int m, int N, he_layout *out) {
         return HE_EINVAL;
     }
     return to_c(L, out);
+}
+
+// ================================================================================ bootstrapping
+// ModRaise, CoeffToSlot, EvalMod, SlotToCoeff (the paper restores levels by bootstrapping,
+// Sec. 2 and the Bootstrap rows of the Sec. 5 tables; the construction is documented at
+// he_boot_create in the header).  The linear levels reuse the raised-basis fused stages of the
+// baby-step giant-step convolution: one ModUp of the input, one ModDown per partial sum, one
+// ModUp per partial sum and one ModDown for the output.
+namespace {
+typedef std::complex<double> cplx;
+typedef std::map<int, std::vector<cplx>> Diags;          // offset mod N -> values over rows
+
+// Non-zero diagonals of the butterfly stage S_h (inverse: 2 S_h^-1) on N slots.  Row x sits at
+// p = x mod 2h of its block, j = p mod h, twiddle exp(2 pi i (5^j mod 8h) / 8h):
+//   S_h:       p < h: v[x] + tw v[x+h];   p >= h: v[x-h] - tw v[x]
+//   2 S_h^-1:  p < h: v[x] + v[x+h];      p >= h: conj(tw) (v[x-h] - v[x])
+Diags stage_diags(int N, int h, bool inverse) {
+    std::vector<cplx> tw(h);
+    const u64 m = 8ull * (u64)h;
+    u64 e = 1;
+    for (int j = 0; j < h; j++) {
+        tw[j] = std::polar(1.0, 2.0 * M_PI * (double)e / (double)m);
+        e = e * 5 % m;
+    }
+    std::vector<cplx> d0(N), dp(N), dm(N);
+    for (int x = 0; x < N; x++) {
+        const int p = x % (2 * h);
+        const cplx t = tw[p % h];
+        if (p < h) {
+            d0[x] = 1.0;
+            dp[x] = inverse ? cplx(1.0) : t;
+        } else {
+            d0[x] = inverse ? -std::conj(t) : -t;
+            dm[x] = inverse ? std::conj(t) : cplx(1.0);
+        }
+    }
+    Diags D;
+    D[0] = d0;
+    D[h % N] = dp;
+    auto &v = D[(N - h) % N];                             // h = N/2: +h and -h are one diagonal
+    if (v.empty()) v = dm;
+    else for (int x = 0; x < N; x++) v[x] += dm[x];
+    return D;
+}
+
+// diagonals of A B (B applied first): diag_d(AB)[x] = sum_e diag_e(A)[x] diag_(d-e)(B)[x+e]
+Diags diag_product(const Diags &A, const Diags &B, int N) {
+    Diags out;
+    for (auto &a : A)
+        for (auto &b : B) {
+            const int d = (a.first + b.first) % N;
+            auto &o = out[d];
+            if (o.empty()) o.assign(N, cplx(0.0));
+            for (int x = 0; x < N; x++) o[x] += a.second[x] * b.second[(x + a.first) % N];
+        }
+    for (auto it = out.begin(); it != out.end();) {
+        bool nz = false;
+        for (auto &v : it->second)
+            if (v != cplx(0.0)) { nz = true; break; }
+        it = nz ? std::next(it) : out.erase(it);
+    }
+    return out;
+}
+
+// stage counts of the merged levels: logN stages into `levels` groups, the larger ones first
+std::vector<int> level_groups(int logN, int levels) {
+    std::vector<int> g(levels, logN / levels);
+    for (int i = 0; i < logN % levels; i++) g[i]++;
+    return g;
+}
+
+int floor_div(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+}  // namespace
+
+// One merged level: offset d = (i b1 + j) u, u = the smallest stage half-length, k = d / u
+// taken in (-N/2u, N/2u], i = floor(k / b1), j = k - i b1, b1 the smallest power of two with
+// b1^2 >= k_max - k_min + 1.  Partial sum S_i = sum_j rot_(-i b1 u)(diag_d) (.) rot_(j u)(x),
+// output sum_i rot_(i b1 u)(S_i).
+struct BootLin {
+    he_ctx *c = nullptr;
+    int stage = 0, idx = 0, level = 0;
+    int unit = 1, b1 = 1;
+    double gain = 1.0;
+    std::vector<int> giants;                      // giant indices, ascending
+    std::vector<std::vector<int>> js;             // per giant: baby indices, ascending
+    std::vector<std::vector<cplx>> vals;          // per term (giant-major): the rotated diagonal
+    size_t pw = 0, pe = 0;
+    u64 *pts = nullptr, *R = nullptr, *Sb = nullptr, *acc = nullptr;
+    FusedStage B, G;
+    bool prepared = false;
+    size_t n_terms() const { return vals.size(); }
+    ~BootLin() { he_free(pts); he_free(R); he_free(Sb); he_free(acc); }
+    void amounts(std::set<int> &out) const {
+        const int N = c->N;
+        for (size_t g = 0; g < giants.size(); g++) {
+            const int a = ((giants[g] * b1 * unit) % N + N) % N;
+            if (a) out.insert(a);
+            for (int j : js[g])
+                if ((j * unit) % N) out.insert((j * unit) % N);
+        }
+    }
+};
+
+static int boot_lin_plan(he_ctx *c, BootLin &L, const std::vector<int> &hs, const Diags &D) {
+    const int N = c->N;
+    L.unit = *std::min_element(hs.begin(), hs.end());
+    const int span = N / L.unit;
+    std::map<int, const std::vector<cplx> *> ks;
+    for (auto &d : D) {
+        int k = d.first / L.unit;
+        if (2 * k > span) k -= span;
+        ks[k] = &d.second;
+    }
+    const int kmin = ks.begin()->first, kmax = ks.rbegin()->first;
+    L.b1 = 1;
+    while (L.b1 * L.b1 < kmax - kmin + 1) L.b1 *= 2;
+    std::map<int, std::map<int, const std::vector<cplx> *>> by;
+    for (auto &kv : ks) {
+        const int i = floor_div(kv.first, L.b1);
+        by[i][kv.first - i * L.b1] = kv.second;
+    }
+    for (auto &gi : by) {
+        L.giants.push_back(gi.first);
+        L.js.emplace_back();
+        const int sh = gi.first * L.b1 * L.unit;          // rot_(-sh): value at x is diag[x - sh]
+        for (auto &bj : gi.second) {
+            L.js.back().push_back(bj.first);
+            const std::vector<cplx> &v = *bj.second;
+            std::vector<cplx> r(N);
+            for (int x = 0; x < N; x++) r[x] = v[(((x - sh) % N) + N) % N];
+            L.vals.push_back(std::move(r));
+        }
+    }
+    return HE_OK;
+}
+
+// encode the level's diagonals (or take given integers) at scale q_level over Q_level u P
+static int boot_lin_upload(he_ctx *c, BootLin &L, const int64_t *given) {
+    const size_t n = c->n, T = L.n_terms();
+    if (!L.pts) HE_TRY(dev_alloc(&L.pts, T * L.pe));
+    std::vector<const double *> none;
+    if (given) return upload_plaintexts(c, none, T, 0.0, L.level, L.pts, given, true);
+    std::vector<int64_t> ints(T * n);
+    std::vector<double> re(c->N), im(c->N);
+    const double S = (double)c->primes[L.level];
+    for (size_t t = 0; t < T; t++) {
+        for (int x = 0; x < c->N; x++) {
+            re[x] = L.vals[t][x].real();
+            im[x] = L.vals[t][x].imag();
+        }
+        encode_slots_complex(re.data(), im.data(), (int)n, S, ints.data() + t * n);
+    }
+    return upload_plaintexts(c, none, T, 0.0, L.level, L.pts, ints.data(), true);
+}
+
+static int boot_lin_prepare(BootLin &L) {
+    if (L.prepared) return HE_OK;
+    he_ctx *c = L.c;
+    const size_t ng = L.giants.size();
+    HE_TRY(dev_alloc(&L.R, 2 * L.pw));
+    HE_TRY(dev_alloc(&L.Sb, ng * 2 * L.pw));
+    HE_TRY(dev_alloc(&L.acc, 2 * L.pw));
+    L.B.c = L.G.c = c;
+    L.B.level = L.G.level = L.level;
+    L.B.pt_level = L.level;
+    char nm[64];
+    snprintf(nm, sizeof(nm), "boot %s%d", L.stage ? "stc" : "cts", L.idx);
+    L.B.name = std::string(nm) + " baby";
+    L.G.name = std::string(nm) + " giant";
+    L.B.add_src(L.R, L.pw);
+    for (size_t g = 0; g < ng; g++) L.B.add_out(L.Sb + g * 2 * L.pw, L.pw);
+    size_t t = 0;
+    for (size_t g = 0; g < ng; g++)
+        for (int j : L.js[g]) L.B.add_term((int)g, 0, j * L.unit, L.pts + (t++) * L.pe);
+    for (size_t g = 0; g < ng; g++) L.G.add_src(L.Sb + g * 2 * L.pw, L.pw);
+    L.G.add_out(L.acc, L.pw);
+    for (size_t g = 0; g < ng; g++) L.G.add_term(0, (int)g, L.giants[g] * L.b1 * L.unit, HE_PT_ONE);
+    HE_TRY(L.B.build());
+    HE_TRY(L.G.build());
+    L.prepared = true;
+    return HE_OK;
+}
+
+static int boot_lin_run(he_ctx *c, BootLin &L, const he_ct *in, he_ct *out, cudaStream_t s) {
+    if (!in || in->ctx != c || in->level != L.level || !out || out == in) {
+        he_set_error("bootstrap linear level: input must sit at level %d", L.level);
+        return HE_ELEVEL;
+    }
+    HE_TRY(boot_lin_prepare(L));
+    HE_TRY(k_copy_limbs(L.R, L.pw, in->d, in->pstride, L.pw, 2, s));
+    HE_TRY(L.B.run(s));
+    HE_TRY(L.G.run(s));
+    he_ct t = view(c, L.acc, L.pw, L.level, in->scale * (double)c->primes[L.level]);
+    HE_TRY(he_rescale(c, &t, s));
+    HE_TRY(ensure_ct(c, out, L.level - 1));
+    HE_TRY(k_copy_limbs(out->d, out->pstride, L.acc, L.pw, (size_t)L.level * c->n, 2, s));
+    out->scale = t.scale * L.gain;
+    return HE_OK;
+}
+
+struct he_boot {
+    he_ctx *c = nullptr;
+    he_boot_config cfg{};
+    std::vector<std::unique_ptr<BootLin>> lin[2];     // 0: CoeffToSlot, 1: SlotToCoeff
+    std::vector<double> coeffs;
+    int depth = 0, evalmod_level = 0, top_stc = 0, out_level = 0;
+    he_ct *x = nullptr, *y = nullptr, *cj = nullptr, *re = nullptr, *im = nullptr, *sq = nullptr;
+    ~he_boot() {
+        for (he_ct *t : {x, y, cj, re, im, sq}) he_ct_free(t);
+    }
+};
+
+// Chebyshev interpolant at the deg + 1 first-kind nodes of cos(2 pi (K u - 1/4) / 2^r) on [-1, 1]
+static void boot_cos_coeffs(int K, int r, int deg, std::vector<double> &c) {
+    const int M = deg + 1;
+    std::vector<double> f(M);
+    for (int k = 0; k < M; k++) {
+        const double u = std::cos(M_PI * (k + 0.5) / M);
+        f[k] = std::cos(2.0 * M_PI * (K * u - 0.25) / std::ldexp(1.0, r));
+    }
+    c.assign(M, 0.0);
+    for (int j = 0; j < M; j++) {
+        double acc = 0;
+        for (int k = 0; k < M; k++) acc += f[k] * std::cos(j * M_PI * (k + 0.5) / M);
+        c[j] = 2.0 / M * acc;
+    }
+    c[0] *= 0.5;
+}
+
+extern "C" int he_boot_create(he_ctx *c, const he_boot_config *cfg_in, he_boot **out) {
+    if (!c || !out) { he_set_error("he_boot_create: null argument"); return HE_EINVAL; }
+    *out = nullptr;
+    he_boot_config cfg{16, 2, 59, 3, 3};
+    if (cfg_in) {
+        if (cfg_in->K > 0) cfg.K = cfg_in->K;
+        if (cfg_in->double_angle > 0) cfg.double_angle = cfg_in->double_angle;
+        if (cfg_in->deg > 0) cfg.deg = cfg_in->deg;
+        if (cfg_in->levels_cts > 0) cfg.levels_cts = cfg_in->levels_cts;
+        if (cfg_in->levels_stc > 0) cfg.levels_stc = cfg_in->levels_stc;
+    }
+    const int logN = c->logn - 1;
+    if (cfg.deg < 2 || cfg.deg > 255 || cfg.levels_cts > logN || cfg.levels_stc > logN || cfg.double_angle > 16) {
+        he_set_error("he_boot_create: bad configuration");
+        return HE_EINVAL;
+    }
+    std::unique_ptr<he_boot> bt(new he_boot());
+    bt->c = c;
+    bt->cfg = cfg;
+    boot_cos_coeffs(cfg.K, cfg.double_angle, cfg.deg, bt->coeffs);
+    int k;
+    std::vector<int> giants;
+    ps_params(cfg.deg, k, giants);
+    bt->depth = ps_need(bt->coeffs, k, giants);
+    const int L = c->L;
+    bt->evalmod_level = L - cfg.levels_cts - 1;
+    bt->top_stc = bt->evalmod_level - bt->depth - cfg.double_angle;
+    bt->out_level = bt->top_stc - cfg.levels_stc;
+    if (bt->out_level < 0) {
+        he_set_error("he_boot_create: the bootstrap needs %d levels, the chain has %d",
+                     L - bt->out_level, L);
+        return HE_ELEVEL;
+    }
+    const int N = c->N;
+    for (int st = 0; st < 2; st++) {
+        const int levels = st == 0 ? cfg.levels_cts : cfg.levels_stc;
+        std::vector<int> grp = level_groups(logN, levels);
+        if (st == 1) std::reverse(grp.begin(), grp.end());
+        std::vector<int> hs;                              // CoeffToSlot: N/2 .. 1; SlotToCoeff: 1 .. N/2
+        for (int e = 0; e < logN; e++) hs.push_back(st == 0 ? 1 << (logN - 1 - e) : 1 << e);
+        size_t pos = 0;
+        for (int i = 0; i < levels; i++) {
+            std::vector<int> mine(hs.begin() + pos, hs.begin() + pos + grp[i]);
+            pos += grp[i];
+            Diags D = stage_diags(N, mine[0], st == 0);
+            for (size_t a = 1; a < mine.size(); a++) D = diag_product(stage_diags(N, mine[a], st == 0), D, N);
+            std::unique_ptr<BootLin> Lv(new BootLin());
+            Lv->c = c;
+            Lv->stage = st;
+            Lv->idx = i;
+            Lv->level = st == 0 ? L - i : bt->top_stc - i;
+            Lv->gain = st == 0 ? std::ldexp(1.0, (int)mine.size()) : 1.0;
+            Lv->pw = (size_t)(Lv->level + 1) * c->n;
+            Lv->pe = (size_t)(Lv->level + 1 + c->K) * c->n;
+            HE_TRY(boot_lin_plan(c, *Lv, mine, D));
+            HE_TRY(boot_lin_upload(c, *Lv, nullptr));
+            bt->lin[st].push_back(std::move(Lv));
+        }
+    }
+    for (he_ct **t : {&bt->x, &bt->y, &bt->cj, &bt->re, &bt->im, &bt->sq}) HE_TRY(he_ct_alloc(c, L, t));
+    *out = bt.release();
+    return HE_OK;
+}
+
+extern "C" void he_boot_destroy(he_boot *bt) {
+    if (bt) cudaDeviceSynchronize();
+    delete bt;
+}
+
+extern "C" int he_boot_rotations(const he_boot *bt, int32_t *amounts, size_t cap) {
+    if (!bt) { he_set_error("null argument"); return HE_EINVAL; }
+    std::set<int> a;
+    for (int st = 0; st < 2; st++)
+        for (auto &L : bt->lin[st]) L->amounts(a);
+    size_t i = 0;
+    for (int v : a) {
+        if (amounts && i < cap) amounts[i] = v;
+        i++;
+    }
+    return (int)i;
+}
+
+extern "C" int he_boot_info(const he_boot *bt, int *out_level, int *cts_level, int *evalmod_level, int *stc_level,
+                            int *keyswitches) {
+    if (!bt) { he_set_error("null argument"); return HE_EINVAL; }
+    if (out_level) *out_level = bt->out_level;
+    if (cts_level) *cts_level = bt->c->L;
+    if (evalmod_level) *evalmod_level = bt->evalmod_level;
+    if (stc_level) *stc_level = bt->top_stc;
+    if (keyswitches) {
+        int ks = 1;                                       // the conjugation
+        for (int st = 0; st < 2; st++)
+            for (auto &L : bt->lin[st]) {
+                std::set<int> a;
+                for (size_t g = 0; g < L->giants.size(); g++) {
+                    for (int j : L->js[g])
+                        if ((j * L->unit) % bt->c->N) a.insert(j);
+                    if ((L->giants[g] * L->b1 * L->unit) % bt->c->N) ks++;
+                }
+                ks += (int)a.size();
+            }
+        int products = 0, dpth = 0;
+        he_poly_ps_plan(bt->cfg.deg, &products, &dpth);
+        ks += 2 * (products + bt->cfg.double_angle);
+        *keyswitches = ks;
+    }
+    return HE_OK;
+}
+
+extern "C" int he_boot_n_plaintexts(const he_boot *bt, int stage, int idx) {
+    if (!bt || stage < 0 || stage > 1 || idx < 0 || idx >= (int)bt->lin[stage].size()) {
+        he_set_error("he_boot_n_plaintexts: bad argument");
+        return HE_EINVAL;
+    }
+    return (int)bt->lin[stage][idx]->n_terms();
+}
+
+extern "C" int he_boot_import_plaintexts(he_boot *bt, int stage, int idx, const int64_t *pts) {
+    if (!bt || !pts || stage < 0 || stage > 1 || idx < 0 || idx >= (int)bt->lin[stage].size()) {
+        he_set_error("he_boot_import_plaintexts: bad argument");
+        return HE_EINVAL;
+    }
+    BootLin &L = *bt->lin[stage][idx];
+    HE_TRY(boot_lin_upload(bt->c, L, pts));
+    L.B.invalidate_pk();
+    return HE_OK;
+}
+
+extern "C" int he_boot_import_coeffs(he_boot *bt, const double *cheb, int deg) {
+    if (!bt || !cheb || deg != bt->cfg.deg) { he_set_error("he_boot_import_coeffs: degree must be %d", bt ? bt->cfg.deg : 0); return HE_EINVAL; }
+    bt->coeffs.assign(cheb, cheb + deg + 1);
+    return HE_OK;
+}
+
+extern "C" int he_boot_lintrans(he_ctx *c, he_boot *bt, int stage, int idx, const he_ct *in, he_ct *out, void *stream) {
+    if (!c || !bt || bt->c != c || stage < 0 || stage > 1 || idx < 0 || idx >= (int)bt->lin[stage].size()) {
+        he_set_error("he_boot_lintrans: bad argument");
+        return HE_EINVAL;
+    }
+    return boot_lin_run(c, *bt->lin[stage][idx], in, out, (cudaStream_t)stream);
+}
+
+extern "C" int he_bootstrap(he_ctx *c, he_boot *bt, const he_ct *in, he_ct *out, void *stream) {
+    if (!c || !bt || bt->c != c || !in || !out || in->ctx != c) { he_set_error("he_bootstrap: bad argument"); return HE_EINVAL; }
+    if (in->level != 0) { he_set_error("he_bootstrap: input at level %d, needs 0", in->level); return HE_ELEVEL; }
+    cudaStream_t s = (cudaStream_t)stream;
+    const double q0 = (double)c->primes[0];
+    const double in_scale = in->scale;
+    he_ct *x = bt->x, *y = bt->y;
+    // ModRaise: slots hold t / (q_0 K)
+    HE_TRY(he_modraise(c, in, c->L, x, stream));
+    x->scale = q0 * bt->cfg.K;
+    // CoeffToSlot
+    for (auto &L : bt->lin[0]) {
+        HE_TRY(boot_lin_run(c, *L, x, y, s));
+        std::swap(x, y);
+    }
+    // retarget to about Delta / 2 (exact scale bookkeeping)
+    {
+        const double kk = std::nearbyint(c->pr.scale / 2.0 * (double)c->primes[x->level] / x->scale);
+        HE_TRY(he_mul_int(c, x, kk, stream));
+        x->scale = x->scale * kk;
+        HE_TRY(he_rescale(c, x, stream));
+    }
+    // split: re = x + conj(x), im = (x - conj(x)) X^(3n/2), both at twice the scale
+    HE_TRY(he_conjugate(c, x, bt->cj, stream));
+    HE_TRY(he_ct_copy(bt->re, x, stream));
+    HE_TRY(he_add(c, bt->re, bt->cj, stream));
+    bt->re->scale = x->scale * 2.0;
+    HE_TRY(he_ct_copy(bt->im, x, stream));
+    HE_TRY(he_sub(c, bt->im, bt->cj, stream));
+    HE_TRY(he_mul_monomial(c, bt->im, 3 * (int64_t)c->n / 2, stream));
+    bt->im->scale = x->scale * 2.0;
+    // EvalMod: cosine by Paterson-Stockmeyer, then r double angles
+    he_ct *pair[2] = {bt->re, bt->im};
+    const double tg[2] = {c->pr.scale, c->pr.scale};
+    HE_TRY(he_poly_eval_ps_many(c, pair, 2, bt->coeffs.data(), bt->cfg.deg, tg, stream));
+    for (int r = 0; r < bt->cfg.double_angle; r++)
+        for (int h = 0; h < 2; h++) {
+            HE_TRY(he_mul_relin(c, pair[h], pair[h], bt->sq, stream));
+            HE_TRY(he_mul_int(c, bt->sq, 2.0, stream));
+            HE_TRY(he_add_const_int(c, bt->sq, -std::nearbyint(bt->sq->scale), stream));
+            std::swap(pair[h], bt->sq);
+        }
+    bt->re = pair[0];
+    bt->im = pair[1];
+    // recombine: re + i im, slots m / Delta_in
+    HE_TRY(he_mul_monomial(c, bt->im, (int64_t)c->n / 2, stream));
+    HE_TRY(he_ct_copy(x, bt->re, stream));
+    HE_TRY(he_add(c, x, bt->im, stream));
+    x->scale = x->scale * (2.0 * M_PI * in_scale / q0);
+    // SlotToCoeff
+    for (auto &L : bt->lin[1]) {
+        HE_TRY(boot_lin_run(c, *L, x, y, s));
+        std::swap(x, y);
+    }
+    HE_TRY(ensure_ct(c, out, x->level));
+    HE_TRY(he_ct_copy(out, x, stream));
+    out->scale = x->scale;
+    return HE_OK;
 }

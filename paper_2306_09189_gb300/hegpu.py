@@ -45,7 +45,12 @@ class HEError(RuntimeError):
 class he_params(ctypes.Structure):
     _fields_ = [("log_n", c_int), ("n_q", c_int), ("n_p", c_int), ("dnum", c_int),
                 ("q0_bits", c_int), ("q_bits", c_int), ("p_bits", c_int),
-                ("scale", c_double), ("seed", c_u64)]
+                ("scale", c_double), ("seed", c_u64), ("secret_hw", c_int)]
+
+
+class he_boot_config(ctypes.Structure):
+    _fields_ = [("K", c_int), ("double_angle", c_int), ("deg", c_int), ("levels_cts", c_int),
+                ("levels_stc", c_int)]
 
 
 class he_layout(ctypes.Structure):
@@ -117,6 +122,20 @@ _SIGS = {
     "he_mul_int": (c_int, [c_vp, c_vp, c_double, c_vp]),
     "he_add_const_int": (c_int, [c_vp, c_vp, c_double, c_vp]),
     "he_mul_relin": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "he_keygen_conjugation": (c_int, [c_vp]),
+    "he_conjugate": (c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "he_mul_monomial": (c_int, [c_vp, c_vp, ctypes.c_int64, c_vp]),
+    "he_modraise": (c_int, [c_vp, c_vp, c_int, c_vp, c_vp]),
+    "he_boot_create": (c_int, [c_vp, ctypes.POINTER(he_boot_config), ctypes.POINTER(c_vp)]),
+    "he_boot_destroy": (None, [c_vp]),
+    "he_boot_rotations": (c_int, [c_vp, I32P, c_size_t]),
+    "he_boot_info": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                             ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
+    "he_boot_n_plaintexts": (c_int, [c_vp, c_int, c_int]),
+    "he_boot_import_plaintexts": (c_int, [c_vp, c_int, c_int, I64P]),
+    "he_boot_import_coeffs": (c_int, [c_vp, F64P, c_int]),
+    "he_boot_lintrans": (c_int, [c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_vp]),
+    "he_bootstrap": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
     "he_conv_create": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_int, c_int,
                                c_int, c_int, c_int, c_double, ctypes.POINTER(c_vp)]),
     "he_conv_create_factored": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_int, c_int,
@@ -478,6 +497,71 @@ def he_add_const_int(ctx, ct, c, stream=None):
 
 def he_mul_relin(ctx, a, b, out, stream=None):
     _check(load().he_mul_relin(ctx, a, b, out, stream_ptr(stream)))
+
+
+def he_keygen_conjugation(ctx):
+    _check(load().he_keygen_conjugation(ctx))
+
+
+def he_conjugate(ctx, ct_in, ct_out, stream=None):
+    _check(load().he_conjugate(ctx, ct_in, ct_out, stream_ptr(stream)))
+
+
+def he_mul_monomial(ctx, ct, e, stream=None):
+    _check(load().he_mul_monomial(ctx, ct, int(e), stream_ptr(stream)))
+
+
+def he_modraise(ctx, ct_in, level, ct_out, stream=None):
+    _check(load().he_modraise(ctx, ct_in, level, ct_out, stream_ptr(stream)))
+
+
+# ----------------------------------------------------------------------------- bootstrapping
+def he_boot_create(ctx, K=0, double_angle=0, deg=0, levels_cts=0, levels_stc=0):
+    """Bootstrapping plan (zero fields take the library's defaults: K 16, r 2, degree 59, 3 + 3
+    linear levels)."""
+    cfg = he_boot_config(K, double_angle, deg, levels_cts, levels_stc)
+    h = c_vp()
+    _check(load().he_boot_create(ctx, ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def he_boot_destroy(bt):
+    load().he_boot_destroy(bt)
+
+
+def he_boot_rotations(bt):
+    n = _check(load().he_boot_rotations(bt, None, 0))
+    a = np.zeros(max(n, 1), dtype=np.int32)
+    _check(load().he_boot_rotations(bt, _p(a, I32P), a.size))
+    return a[:n]
+
+
+def he_boot_info(bt):
+    v = [c_int() for _ in range(5)]
+    _check(load().he_boot_info(bt, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("out_level", "cts_level", "evalmod_level", "stc_level", "keyswitches"), [x.value for x in v]))
+
+
+def he_boot_n_plaintexts(bt, stage, idx):
+    return _check(load().he_boot_n_plaintexts(bt, stage, idx))
+
+
+def he_boot_import_plaintexts(bt, stage, idx, pts):
+    a = np.ascontiguousarray(pts, dtype=np.int64)
+    _check(load().he_boot_import_plaintexts(bt, stage, idx, _p(a, I64P)))
+
+
+def he_boot_import_coeffs(bt, cheb):
+    c = np.ascontiguousarray(cheb, dtype=np.float64)
+    _check(load().he_boot_import_coeffs(bt, _p(c, F64P), c.size - 1))
+
+
+def he_boot_lintrans(ctx, bt, stage, idx, ct_in, ct_out, stream=None):
+    _check(load().he_boot_lintrans(ctx, bt, stage, idx, ct_in, ct_out, stream_ptr(stream)))
+
+
+def he_bootstrap(ctx, bt, ct_in, ct_out, stream=None):
+    _check(load().he_bootstrap(ctx, bt, ct_in, ct_out, stream_ptr(stream)))
 
 
 # ----------------------------------------------------------------------------- layers

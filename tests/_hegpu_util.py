@@ -6,7 +6,7 @@ from paper_2306_09189_gb300 import hegpu as H
 
 def params_of(pr):
     return H.he_params(pr.log_n, pr.n_q, pr.n_p, pr.dnum, pr.q0_bits, pr.q_bits, pr.p_bits,
-                       pr.scale, pr.seed)
+                       pr.scale, pr.seed, pr.secret_hw)
 
 
 class GpuCtx:
