@@ -12,7 +12,8 @@ ranks; ms_per_step = layer latency.  The batched mode is the headline; the plain
 per-ciphertext path is timed beside it, and the convolution alone (`conv_only`).  At N = 1 the
 line also carries the batched ResNet block (`resnet_block`: 4 images at mixed levels, batched
 vs plain), the ImageNet stem (`imagenet_stem`) and the serving loop (`serving`: Poisson
-arrivals, p50/p99 latency and images/s), each run on its own context afterwards, and the oracle
+arrivals, p50/p99 latency and images/s) and one full-ring bootstrap (`bootstrap`), each run on its
+own context afterwards, and the oracle
 on all host cores and on one (`cpu_baseline`).  N > 1 runs independent replicas
 (the layer does not shard across GPUs).  --impl reference times the CPU oracle instead.
 """
@@ -526,6 +527,87 @@ STEM_WORKLOAD = ("imagenet stem: 3x224x224 in channel shards (256 frame, 2 shard
                  "-> 112x112x64 (32 shards) -> 2x2 avgpool -> 56x56x64 (8 shards); 2N=2^16, 20+5 primes")
 
 
+BOOT_WORKLOAD = ("bootstrap: one level-0 ciphertext (2^15 real slots, scale 2^40) to level 8 of 23; "
+                 "2N=2^16, 24+6 primes of 50 bits, weight-64 secret; ModRaise, 3 CoeffToSlot levels, "
+                 "EvalMod (degree-59 Chebyshev cosine, 2 double angles), 3 SlotToCoeff levels")
+
+
+def run_bootstrap(args, ws, rank, local, emit=True):
+    """One bootstrap per step (the paper's largest cost, Sec. 5 tables), as a CUDA graph of the
+    whole pipeline; the decrypted output is compared with the input message."""
+    import torch
+    from paper_2306_09189_gb300 import hegpu as H
+    from paper_2306_09189_gb300 import host
+    pr = host.bootstrap_params(seed=0)
+    ctx = H.he_ctx_create(pr)
+    N = H.he_ctx_info(ctx)["slots"]
+    t_setup = time.perf_counter()
+    bt = H.he_boot_create(ctx)
+    H.he_keygen_rotations(ctx, H.he_boot_rotations(bt))
+    H.he_keygen_conjugation(ctx)
+    H.he_keygen_relin(ctx)
+    info = H.he_boot_info(bt)
+    z = np.random.default_rng(7).uniform(-1, 1, N)
+    x = H.he_ct_alloc(ctx, 0)
+    H.he_encrypt(ctx, z, 0, 2.0 ** 40, 1, x)
+    y = H.he_ct_alloc(ctx, info["out_level"])
+    ts = torch.cuda.Stream()                              # graphs capture a created stream
+    stream = ts.cuda_stream
+    for _ in range(args.warmup):                          # first run: autotuner, buffers
+        H.he_bootstrap(ctx, bt, x, y, stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    if args.profile_step:                                 # one eager bootstrap for a profiler
+        torch.cuda.profiler.start()
+        H.he_bootstrap(ctx, bt, x, y, stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        H.he_boot_destroy(bt)
+        H.he_ctx_destroy(ctx)
+        return None
+    H.he_graph_begin(ctx, stream)
+    H.he_bootstrap(ctx, bt, x, y, stream)
+    graph = H.he_graph_end(ctx, stream)
+    H.he_graph_launch(graph, stream)
+    torch.cuda.synchronize()
+    err = float(np.max(np.abs(H.he_decrypt(ctx, y, N) - z)))
+    clocks = Clocks(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0.record(ts)
+    for _ in range(args.steps):
+        H.he_graph_launch(graph, stream)
+    e1.record(ts)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # eager (no graph) for comparison
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        H.he_bootstrap(ctx, bt, x, y, stream)
+    torch.cuda.synchronize()
+    eager_ms = (time.perf_counter() - t0) * 1e3 / 3
+    line = {"metric": "bootstrap ms at 2N=2^16 on 1 GB300", "value": ms, "unit": "ms", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": BOOT_WORKLOAD, "key_switches_per_step": info["keyswitches"],
+                       "input_levels": [0], "output_level": info["out_level"], "setup_s": setup_s,
+                       "key_bytes": H.load().he_key_bytes(ctx)},
+            "eager_ms": eager_ms, "gpu_launches": H.he_graph_kernels(graph),
+            "check": {"max_abs_error": err, "bits": -float(np.log2(err)) if err > 0 else None},
+            "clocks": ck}
+    H.he_graph_destroy(graph)
+    H.he_boot_destroy(bt)
+    for c in (x, y):
+        H.he_ct_free(c)
+    H.he_ctx_destroy(ctx)
+    if emit and rank == 0:
+        print(json.dumps(line), flush=True)
+    return line if rank == 0 else None
+
+
 def run_stem(args, ws, rank, local, emit=True):
     """The ImageNet-shaped sharded stem (config 3): the factored channel-shard conv with stride 2
     (the select runs on 128 channel shards), then the 2x2 average pool; one CUDA graph per step.
@@ -675,10 +757,10 @@ def main():
     ap.add_argument("--poly", default="ps", choices=["ps", "tree"],
                     help="GELU evaluation: Paterson-Stockmeyer (default) or the binary tree")
     ap.add_argument("--workload", default="cifar-layer",
-                    choices=["cifar-layer", "resnet-block", "imagenet-stem", "resnet-head"],
+                    choices=["cifar-layer", "resnet-block", "imagenet-stem", "resnet-head", "bootstrap"],
                     help="cifar-layer: the headline layer; resnet-block: the batched mixed-level block; "
                          "imagenet-stem: the channel-shard stem with stride 2 and average pool; "
-                         "resnet-head: the pool-linear head")
+                         "resnet-head: the pool-linear head; bootstrap: one full-ring bootstrap")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -690,9 +772,9 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    if args.workload in ("resnet-block", "imagenet-stem", "resnet-head"):
-        {"resnet-block": run_block, "imagenet-stem": run_stem, "resnet-head": run_head}[args.workload](
-            args, ws, rank, local)
+    if args.workload in ("resnet-block", "imagenet-stem", "resnet-head", "bootstrap"):
+        {"resnet-block": run_block, "imagenet-stem": run_stem, "resnet-head": run_head,
+         "bootstrap": run_bootstrap}[args.workload](args, ws, rank, local)
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
@@ -951,7 +1033,8 @@ def main():
     if ws == 1 and not args.no_extra:
         # the batched ResNet block (the survey's headline for batched vs plain) and the ImageNet
         # stem, each on its own context after the layer's is released
-        for key, fn, k in (("resnet_block", run_block, 5), ("imagenet_stem", run_stem, 3)):
+        for key, fn, k in (("resnet_block", run_block, 5), ("imagenet_stem", run_stem, 3),
+                           ("bootstrap", run_bootstrap, 20)):
             sub = argparse.Namespace(**vars(args))
             sub.steps, sub.warmup, sub.trace, sub.small, sub.profile_step = k, 3, "ipmac", False, False
             line[key] = _extra_summary(fn(sub, ws, rank, local, emit=False))
@@ -977,10 +1060,12 @@ def _extra_summary(d):
     """The figures of a secondary workload's line that the headline line carries."""
     if d is None:
         return None
-    keep = ("ms_per_step", "value", "unit", "steps", "plain", "check", "roofline", "clocks", "gpu_launches")
+    keep = ("ms_per_step", "value", "unit", "steps", "plain", "check", "roofline", "clocks", "gpu_launches",
+            "eager_ms")
     out = {k: d[k] for k in keep if k in d}
     out["workload"] = d["config"]["workload"]
-    for k in ("key_switches_per_step", "input_levels", "setup_s", "l2", "conv_keyswitches_per_image", "shards"):
+    for k in ("key_switches_per_step", "input_levels", "output_level", "setup_s", "l2",
+              "conv_keyswitches_per_image", "shards"):
         if k in d["config"]:
             out[k] = d["config"][k]
     return out

@@ -4062,9 +4062,10 @@ int floor_div(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
 }  // namespace
 
 // One merged level: offset d = (i b1 + j) u, u = the smallest stage half-length, k = d / u
-// taken in (-N/2u, N/2u], i = floor(k / b1), j = k - i b1, b1 the smallest power of two with
-// b1^2 >= k_max - k_min + 1.  Partial sum S_i = sum_j rot_(-i b1 u)(diag_d) (.) rot_(j u)(x),
-// output sum_i rot_(i b1 u)(S_i).
+// taken in [-N/2u, N/2u), i = floor(k / b1), j = k - i b1, b1 the smallest power of two with
+// 2 b1 >= k_max - k_min + 1 (two giant steps: a giant partial sum costs a ModUp and a ModDown,
+// a baby rotation only a key read).  Partial sum S_i = sum_j rot_(-i b1 u)(diag_d) (.)
+// rot_(j u)(x), output sum_i rot_(i b1 u)(S_i).
 struct BootLin {
     he_ctx *c = nullptr;
     int stage = 0, idx = 0, level = 0;
@@ -4097,12 +4098,12 @@ static int boot_lin_plan(he_ctx *c, BootLin &L, const std::vector<int> &hs, cons
     std::map<int, const std::vector<cplx> *> ks;
     for (auto &d : D) {
         int k = d.first / L.unit;
-        if (2 * k > span) k -= span;
+        if (2 * k >= span) k -= span;
         ks[k] = &d.second;
     }
     const int kmin = ks.begin()->first, kmax = ks.rbegin()->first;
     L.b1 = 1;
-    while (L.b1 * L.b1 < kmax - kmin + 1) L.b1 *= 2;
+    while (2 * L.b1 < kmax - kmin + 1) L.b1 *= 2;
     std::map<int, std::map<int, const std::vector<cplx> *>> by;
     for (auto &kv : ks) {
         const int i = floor_div(kv.first, L.b1);
@@ -4193,9 +4194,9 @@ struct he_boot {
     std::vector<std::unique_ptr<BootLin>> lin[2];     // 0: CoeffToSlot, 1: SlotToCoeff
     std::vector<double> coeffs;
     int depth = 0, evalmod_level = 0, top_stc = 0, out_level = 0;
-    he_ct *x = nullptr, *y = nullptr, *cj = nullptr, *re = nullptr, *im = nullptr, *sq = nullptr;
+    he_ct *x = nullptr, *y = nullptr, *cj = nullptr, *re = nullptr, *im = nullptr, *sq = nullptr, *sq2 = nullptr;
     ~he_boot() {
-        for (he_ct *t : {x, y, cj, re, im, sq}) he_ct_free(t);
+        for (he_ct *t : {x, y, cj, re, im, sq, sq2}) he_ct_free(t);
     }
 };
 
@@ -4275,7 +4276,7 @@ extern "C" int he_boot_create(he_ctx *c, const he_boot_config *cfg_in, he_boot *
             bt->lin[st].push_back(std::move(Lv));
         }
     }
-    for (he_ct **t : {&bt->x, &bt->y, &bt->cj, &bt->re, &bt->im, &bt->sq}) HE_TRY(he_ct_alloc(c, L, t));
+    for (he_ct **t : {&bt->x, &bt->y, &bt->cj, &bt->re, &bt->im, &bt->sq, &bt->sq2}) HE_TRY(he_ct_alloc(c, L, t));
     *out = bt.release();
     return HE_OK;
 }
@@ -4393,15 +4394,20 @@ extern "C" int he_bootstrap(he_ctx *c, he_boot *bt, const he_ct *in, he_ct *out,
     he_ct *pair[2] = {bt->re, bt->im};
     const double tg[2] = {c->pr.scale, c->pr.scale};
     HE_TRY(he_poly_eval_ps_many(c, pair, 2, bt->coeffs.data(), bt->cfg.deg, tg, stream));
-    for (int r = 0; r < bt->cfg.double_angle; r++)
+    he_ct *sq[2] = {bt->sq, bt->sq2};
+    for (int r = 0; r < bt->cfg.double_angle; r++) {
+        // both halves' squares in one batched relinearisation (the bits of he_mul_relin)
+        HE_TRY(relin_batch(c, {pair[0], pair[1]}, {pair[0], pair[1]}, {sq[0], sq[1]}, s));
         for (int h = 0; h < 2; h++) {
-            HE_TRY(he_mul_relin(c, pair[h], pair[h], bt->sq, stream));
-            HE_TRY(he_mul_int(c, bt->sq, 2.0, stream));
-            HE_TRY(he_add_const_int(c, bt->sq, -std::nearbyint(bt->sq->scale), stream));
-            std::swap(pair[h], bt->sq);
+            HE_TRY(he_mul_int(c, sq[h], 2.0, stream));
+            HE_TRY(he_add_const_int(c, sq[h], -std::nearbyint(sq[h]->scale), stream));
+            std::swap(pair[h], sq[h]);
         }
-    bt->re = pair[0];
+    }
+    bt->re = pair[0];                                     // a permutation of the plan's four buffers
     bt->im = pair[1];
+    bt->sq = sq[0];
+    bt->sq2 = sq[1];
     // recombine: re + i im, slots m / Delta_in
     HE_TRY(he_mul_monomial(c, bt->im, (int64_t)c->n / 2, stream));
     HE_TRY(he_ct_copy(x, bt->re, stream));

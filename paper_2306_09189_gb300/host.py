@@ -13,8 +13,8 @@ import numpy as np
 from . import hegpu as H
 
 
-def params(log_n, n_q, n_p, dnum, q0_bits, q_bits, p_bits, scale=2.0 ** 40, seed=0):
-    return H.he_params(log_n, n_q, n_p, dnum, q0_bits, q_bits, p_bits, scale, seed)
+def params(log_n, n_q, n_p, dnum, q0_bits, q_bits, p_bits, scale=2.0 ** 40, seed=0, secret_hw=0):
+    return H.he_params(log_n, n_q, n_p, dnum, q0_bits, q_bits, p_bits, scale, seed, secret_hw)
 
 
 def toy_params(seed=0):
@@ -25,6 +25,14 @@ def toy_params(seed=0):
 def cifar_params(seed=0):
     """2N = 2^16, q_0 of 50 bits + 19 primes of 40 bits, 5 special primes, dnum 4."""
     return params(16, 20, 5, 4, 50, 40, 50, seed=seed)
+
+
+def bootstrap_params(seed=0):
+    """2N = 2^16, 24 ciphertext primes and 6 special primes of 50 bits, dnum 4, scale 2^50, a
+    sparse secret of weight 64: 15 levels for the bootstrap (3 CoeffToSlot, 1 retarget, 6
+    Paterson-Stockmeyer, 2 double angles, 3 SlotToCoeff) and 8 for the network between two
+    bootstraps; log2(QP) = 1500."""
+    return params(16, 24, 6, 4, 50, 50, 50, scale=2.0 ** 50, seed=seed, secret_hw=64)
 
 
 def serving_params(seed=0):
