@@ -459,10 +459,12 @@ int he_conv_fork(const he_conv *conv, he_ctx *ctx, he_conv **out);
  *   EvalMod on re and im: cos(2 pi (K u - 1/4) / 2^r) as a degree-deg Chebyshev interpolant
  *     in u on [-1, 1] (Paterson-Stockmeyer, target scale Delta), then r double angles
  *     y <- 2 y^2 - 1: sin(2 pi t / q_0) ~ 2 pi m / q_0;
- *   re + im X^(n/2), scale times 2 pi Delta_in / q_0 (Delta_in: the input's scale);
+ *   re + im X^(n/2), scale times 2 pi Delta_in / q_0 (Delta_in: the input's scale), then
+ *     times the integer round(Delta / s) (no level: the scale is about Delta again);
  *   SlotToCoeff: S_h, h = 1 .. N/2, merged into levels_stc levels the same way.
  * Levels used: levels_cts + 1 + (Paterson-Stockmeyer depth of deg) + r + levels_stc
- * (15 with the defaults); the output sits at L minus that, same slot values, scale as above.
+ * (15 with the defaults); the output sits at L minus that, same slot values, scale within a
+ * fraction of a percent of Delta (tracked exactly).
  * Needs K >= max |I| (|I| <= (h + 1) / 2 for a weight-h secret: he_params.secret_hw), and
  * q_0 / Delta_in large enough for sin(x) ~ x (2^10 gives about 2^-17 relative). */
 typedef struct he_boot he_boot;
@@ -494,8 +496,10 @@ int he_boot_import_plaintexts(he_boot *bt, int stage, int idx, const int64_t *pt
 int he_boot_import_coeffs(he_boot *bt, const double *cheb, int deg);
 /* One linear level on its own (for tests): in at the level's level, out one level lower. */
 int he_boot_lintrans(he_ctx *ctx, he_boot *bt, int stage, int idx, const he_ct *in, he_ct *out, void *stream);
-/* The whole bootstrap; in at level 0 (any scale), out allocated at the output level or above
- * (HE_ELEVEL otherwise). */
+/* The whole bootstrap; out allocated at the output level or above (HE_ELEVEL otherwise).  A
+ * level-0 input is taken at its scale; an input above level 0 is first brought to level 0 at
+ * scale q_0 / 2^10 (dropped to level 1, times the integer round((q_0 / 2^10) q_1 / s),
+ * rescaled), so a network can bootstrap wherever its levels run out. */
 int he_bootstrap(he_ctx *ctx, he_boot *bt, const he_ct *in, he_ct *out, void *stream);
 
 /* ------------------------------------------------------------------ polynomial approximation (Appendix) */

@@ -34,8 +34,9 @@ notes):
                [-1, 1] (Paterson-Stockmeyer), then r double angles y <- 2 y^2 - 1, giving
                sin(2 pi x) = sin(2 pi m / q_0) ~ 2 pi m / q_0.
   SlotToCoeff  re + i im, scale times 2 pi Delta_in / q_0 (the slots then hold m / Delta_in,
-               m's coefficients in bit-reversed order), then the forward stages S_1 .. S_{N/2}
-               merged into levels as above: the slots hold the message again.
+               m's coefficients in bit-reversed order); times the integer round(Delta / s)
+               (no level) so the scale is about Delta again; then the forward stages
+               S_1 .. S_{N/2} merged into levels as above: the slots hold the message again.
 
 Levels: CoeffToSlot and SlotToCoeff one per merged level, retarget one, EvalMod the
 Paterson-Stockmeyer depth plus r.
@@ -147,11 +148,13 @@ def stc_levels(N, levels):
 @dataclass
 class BsgsLevel:
     """One merged level, regrouped: offset d = (i b1 + j) u (u = the level's smallest stage
-    half-length, k = i b1 + j the offset in units, taken in (-N/2u, N/2u], j = k mod b1):
+    half-length, k = i b1 + j the offset in units, taken in [-N/2u, N/2u), j = k mod b1):
 
         M v = sum_i rot_{i b1 u}( sum_j rot_{-i b1 u}(diag_d) (.) rot_{j u}(v) )
 
-    b1 = the smallest power of two >= sqrt(k_max - k_min + 1)."""
+    b1 = the smallest power of two >= (k_max - k_min + 1) / 2, so there are two giant steps:
+    each giant partial sum costs a ModUp and a ModDown (a few hundred limb NTTs at the top
+    level), a baby rotation only a key read in the raised-basis stage."""
     N: int
     stages: list
     gain: float                                   # scale factor of the level (2^stages for CoeffToSlot)
@@ -179,12 +182,12 @@ def bsgs_level(N, stages, D, gain):
     for d, v in D.items():
         assert d % u == 0
         k = d // u
-        if 2 * k > span:
+        if 2 * k >= span:
             k -= span
         ks[k] = v
     kmin, kmax = min(ks), max(ks)
     b1 = 1
-    while b1 * b1 < kmax - kmin + 1:
+    while 2 * b1 < kmax - kmin + 1:
         b1 *= 2
     L = BsgsLevel(N, list(stages), gain, u, b1)
     for k, v in sorted(ks.items()):
@@ -308,10 +311,22 @@ def gen_boot_keys(ctx, plan: BootPlan):
     ctx.gen_relin_key()
 
 
+def to_level0(ctx, ct, ratio_bits=10):
+    """A ciphertext above level 0 brought to level 0 at scale q_0 / 2^ratio_bits: dropped to
+    level 1, multiplied by the integer round((q_0 / 2^ratio_bits) q_1 / s), rescaled (the scale
+    bookkeeping exact: s k / q_1).  q_0 / scale = 2^ratio_bits is the small-angle margin the sine
+    step of EvalMod reads the message with."""
+    if ct.level == 0:
+        return ct
+    y = ctx.drop_to(ct, 1) if ct.level > 1 else ct
+    return retarget_exact(ctx, y, float(ctx.q[0]) / 2.0 ** ratio_bits)
+
+
 def bootstrap(ctx, ct, plan: BootPlan, trace=None):
-    """The whole bootstrap of a level-0 ciphertext; returns a ciphertext at plan.out_level with
-    the same slot values.  trace (a dict) receives the intermediate ciphertexts by step name."""
-    assert ct.level == 0
+    """The whole bootstrap; returns a ciphertext at plan.out_level with the same slot values.
+    An input above level 0 first goes through to_level0.  trace (a dict) receives the
+    intermediate ciphertexts by step name."""
+    ct = to_level0(ctx, ct)
     K = plan.cfg.K
     q0 = float(ctx.q[0])
     in_scale = ct.scale
@@ -335,6 +350,12 @@ def bootstrap(ctx, ct, plan: BootPlan, trace=None):
         trace["evalmod_re"], trace["evalmod_im"] = re, im
     w = ctx.add_ct(re, ctx.mul_monomial(im, ctx.n // 2))
     w.scale = w.scale * (2.0 * math.pi * in_scale / q0)
+    # back to about Delta without a level: times the integer k = round(Delta / s) (exact scale
+    # s k), so the output can go straight into products whose scales must stay near the primes
+    k = int(round(ctx.pr.scale / w.scale))
+    if k > 1:
+        w = ctx.mul_int(w, k)
+        w.scale = w.scale * k
     if trace is not None:
         trace["combine"] = w
     for i, lv in enumerate(plan.stc):

@@ -4361,12 +4361,22 @@ extern "C" int he_boot_lintrans(he_ctx *c, he_boot *bt, int stage, int idx, cons
 
 extern "C" int he_bootstrap(he_ctx *c, he_boot *bt, const he_ct *in, he_ct *out, void *stream) {
     if (!c || !bt || bt->c != c || !in || !out || in->ctx != c) { he_set_error("he_bootstrap: bad argument"); return HE_EINVAL; }
-    if (in->level != 0) { he_set_error("he_bootstrap: input at level %d, needs 0", in->level); return HE_ELEVEL; }
     cudaStream_t s = (cudaStream_t)stream;
     const double q0 = (double)c->primes[0];
-    const double in_scale = in->scale;
     he_ct *x = bt->x, *y = bt->y;
-    // ModRaise: slots hold t / (q_0 K)
+    if (in->level > 0) {
+        // to level 0 at scale q_0 / 2^10: drop to level 1, times the integer
+        // round((q_0 / 2^10) q_1 / s), rescale (scale s k / q_1, exact bookkeeping)
+        HE_TRY(he_ct_copy(y, in, stream));
+        HE_TRY(he_ct_drop_level(y, 1));
+        const double kk = std::nearbyint(q0 / 1024.0 * (double)c->primes[1] / y->scale);
+        HE_TRY(he_mul_int(c, y, kk, stream));
+        y->scale = y->scale * kk;
+        HE_TRY(he_rescale(c, y, stream));
+        in = y;
+    }
+    const double in_scale = in->scale;
+    // ModRaise: slots hold t / (q_0 K)  (in may be y here: he_modraise reads limb 0 first)
     HE_TRY(he_modraise(c, in, c->L, x, stream));
     x->scale = q0 * bt->cfg.K;
     // CoeffToSlot
@@ -4413,6 +4423,14 @@ extern "C" int he_bootstrap(he_ctx *c, he_boot *bt, const he_ct *in, he_ct *out,
     HE_TRY(he_ct_copy(x, bt->re, stream));
     HE_TRY(he_add(c, x, bt->im, stream));
     x->scale = x->scale * (2.0 * M_PI * in_scale / q0);
+    {
+        // back to about Delta without a level: times the integer round(Delta / s)
+        const double kk = std::nearbyint(c->pr.scale / x->scale);
+        if (kk > 1.0) {
+            HE_TRY(he_mul_int(c, x, kk, stream));
+            x->scale = x->scale * kk;
+        }
+    }
     // SlotToCoeff
     for (auto &L : bt->lin[1]) {
         HE_TRY(boot_lin_run(c, *L, x, y, s));

@@ -123,6 +123,22 @@ def test_bootstrap_bit_exact_ring_2_12(boot12):
     assert err < 2.0 ** -15
 
 
+def test_bootstrap_bit_exact_from_level_3(boot12):
+    # an input above level 0 goes to level 0 at scale q_0 / 2^10 first (exact retarget)
+    o, plan, g, bt = boot12
+    _import_oracle(o, plan, bt)
+    rng = np.random.default_rng(6)
+    z = rng.uniform(-1, 1, o.N)
+    ct = o.encrypt(z, 3, BOOT12.scale, nonce=31)
+    want = B.bootstrap(o, ct, plan)
+    d = g.upload(ct)
+    out = g.ct(plan.out_level)
+    H.he_bootstrap(g.h, bt, d, out)
+    assert H.he_ct_scale(out) == want.scale
+    assert_ct_equal(g.download(out), want)
+    assert np.max(np.abs(o.decrypt(want) - z)) < 2.0 ** -15
+
+
 def test_bootstrap_own_encoding_precision_ring_2_12():
     o = Context(BOOT12)
     g = GpuCtx(BOOT12)
@@ -185,6 +201,66 @@ def test_bootstrap_full_ring_precision_and_first_level_bit_exact():
         y = g.ct(o.L)
         H.he_boot_lintrans(g.h, bt, 0, 0, x, y)
         assert_ct_equal(g.download(y), B.lintrans_he(o, ox, lv, pts))
+        H.he_boot_destroy(bt)
+    finally:
+        g.close()
+
+
+def test_network_deeper_than_the_chain():
+    """conv3x3+BN -> GELU -> bootstrap -> conv3x3+BN -> GELU on a 4x32x32 image at ring 2^16:
+    12 levels of layers on an 8-level budget, decrypted against the FP64 network with the same
+    polynomial."""
+    import workloads
+    from paper_2306_09189_gb300 import host
+    torch = pytest.importorskip("torch")
+    pr = B24
+    wl = workloads.cifar_conv_bn(0, c=4, m=32)
+    cheb = host.chebyshev_coeffs("gelu", 16, -workloads.GELU_BOUND, workloads.GELU_BOUND)
+    act = lambda v: np.polynomial.chebyshev.chebval(v, cheb)
+    conv = lambda x, W, b: torch.nn.functional.conv2d(torch.tensor(x)[None], torch.tensor(W), padding=1)[0].numpy() + b[:, None, None]
+    y1 = act(conv(wl.x, wl.W, wl.bias))
+    rng = np.random.default_rng(11)
+    W2 = rng.uniform(-1 / 6, 1 / 6, (4, 4, 3, 3))
+    W2f, b2f = workloads.fold_bn(y1, W2, 1)
+    y2 = act(conv(y1, W2f, b2f))
+    g = GpuCtx(pr)
+    try:
+        ctx = g.h
+        bt = H.he_boot_create(ctx)
+        info = H.he_boot_info(bt)
+        lay = H.he_layout_image(4, 32, g.N)
+        level = 7
+        xs = host.encrypt_image(ctx, lay, wl.x, level, pr.scale, nonce0=1)
+        c1 = H.he_conv_create(ctx, lay, wl.W, wl.bias, 1, 1, level, pr.scale)
+        lay1 = H.he_conv_out_layout(c1)
+        H.he_keygen_rotations(ctx, sorted(set(H.he_boot_rotations(bt).tolist()) | set(H.he_conv_rotations(c1))))
+        H.he_keygen_conjugation(ctx)
+        H.he_keygen_relin(ctx)
+        a1 = [H.he_ct_alloc(ctx, level - 1) for _ in range(lay1.n_shards)]
+        H.he_conv_run(ctx, c1, xs, a1, H.HE_FUSED)
+        for ct in a1:
+            H.he_poly_eval_ps(ctx, ct, cheb, pr.scale)
+        assert H.he_ct_level(a1[0]) == 1                 # the chain is spent
+        b1 = [H.he_ct_alloc(ctx, info["out_level"]) for _ in a1]
+        for src, dst in zip(a1, b1):
+            H.he_bootstrap(ctx, bt, src, dst)
+        lv2 = H.he_ct_level(b1[0])
+        assert lv2 == info["out_level"]
+        c2 = H.he_conv_create(ctx, lay1, W2f, b2f, 1, 1, lv2, H.he_ct_scale(b1[0]))
+        H.he_keygen_rotations(ctx, H.he_conv_rotations(c2))
+        lay2 = H.he_conv_out_layout(c2)
+        a2 = [H.he_ct_alloc(ctx, lv2 - 1) for _ in range(lay2.n_shards)]
+        H.he_conv_run(ctx, c2, b1, a2, H.HE_FUSED)
+        for ct in a2:
+            H.he_poly_eval_ps(ctx, ct, cheb, pr.scale)
+        got = host.decrypt_image(ctx, lay2, a2)
+        err = np.max(np.abs(got - y2))
+        rng_y = np.max(y2) - np.min(y2)
+        assert err < 2.0 ** -8 * rng_y, (err, rng_y)
+        for ct in xs + a1 + b1 + a2:
+            H.he_ct_free(ct)
+        H.he_conv_destroy(c1)
+        H.he_conv_destroy(c2)
         H.he_boot_destroy(bt)
     finally:
         g.close()

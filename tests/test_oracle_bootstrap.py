@@ -202,3 +202,16 @@ def test_bootstrap_restores_levels_ring_2_12():
     plan = B.BootPlan(ctx)
     B.gen_boot_keys(ctx, plan)
     _check_bootstrap(ctx, plan, 22, 15)
+
+
+def test_bootstrap_from_a_higher_level(tiny):
+    ctx, plan = tiny
+    rng = np.random.default_rng(23)
+    z = rng.uniform(-1, 1, ctx.N)
+    ct = ctx.encrypt(z, 4, TINY.scale, nonce=23)
+    y = B.to_level0(ctx, ct)
+    assert y.level == 0 and abs(y.scale / (ctx.q[0] / 1024.0) - 1) < 2.0 ** -20
+    assert np.max(np.abs(ctx.decrypt(y) - z)) < 2.0 ** -25
+    out = B.bootstrap(ctx, ct, plan)
+    assert out.level == plan.out_level
+    assert np.max(np.abs(ctx.decrypt(out) - z)) < 2.0 ** -17
