@@ -201,12 +201,16 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  * one launch on a cluster of 16 CTAs of 256 threads that exchange the limb's blocks through
  * distributed shared memory (the limb is read and written once); HE_NTT_ONEPASS8 (2) the same on
  * a cluster of 8 CTAs of 512 threads; HE_NTT_TWOPASS (1) runs a column pass and a row pass as
- * two launches with the limb going through memory in between (the default).  Same words in
- * every form; smaller rings always take the two-pass form. */
+ * two launches with the limb going through memory in between (the default).  When every prime
+ * of the context is below 2^57 the two-pass forward transform skips the per-butterfly
+ * correction (values grow by at most 2q per stage and are reduced once at the end);
+ * HE_NTT_TWOPASS_CORRECTED (3) keeps the correction in every butterfly.  Same words in every
+ * form; smaller rings always take a two-pass form. */
 #define HE_OPT_NTT 3
 #define HE_NTT_ONEPASS 0
 #define HE_NTT_TWOPASS 1
 #define HE_NTT_ONEPASS8 2
+#define HE_NTT_TWOPASS_CORRECTED 3
 int he_ctx_set_option(he_ctx *ctx, int option, int value);
 int he_ctx_get_option(const he_ctx *ctx, int option, int *value);
 /* The autotuner's decisions so far (one line per tuned stage: the candidates' times and the

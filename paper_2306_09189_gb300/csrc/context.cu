@@ -432,6 +432,9 @@ static int create(const he_params *pr, he_ctx **out) {
     }
     he_ctx *c = new he_ctx();
     c->pr = *pr;
+    c->small_primes = true;
+    for (u64 x : q) c->small_primes = c->small_primes && x < (1ull << 57);
+    for (u64 x : p) c->small_primes = c->small_primes && x < (1ull << 57);
     c->logn = pr->log_n;
     c->n = 1 << pr->log_n;
     c->N = c->n / 2;
@@ -756,6 +759,7 @@ extern "C" int he_ctx_fork(he_ctx *parent, he_ctx **out) {
     c->d_s = r->d_s;
     c->key_stream = parent->key_stream;
     c->ntt_form = parent->ntt_form;
+    c->small_primes = parent->small_primes;
     c->parent = r;
     const size_t ext = (size_t)(c->L + 1 + c->K) * c->n;
     int rc = c->sc_digits.ensure((size_t)c->dnum * ext);
@@ -809,7 +813,8 @@ extern "C" int he_ctx_set_option(he_ctx *c, int option, int value) {
         c->key_stream = value;
         return HE_OK;
     }
-    if (option == HE_OPT_NTT && (value == HE_NTT_ONEPASS || value == HE_NTT_TWOPASS || value == HE_NTT_ONEPASS8)) {
+    if (option == HE_OPT_NTT && (value == HE_NTT_ONEPASS || value == HE_NTT_TWOPASS || value == HE_NTT_ONEPASS8 ||
+                                 value == HE_NTT_TWOPASS_CORRECTED)) {
         c->ntt_form = value;
         return HE_OK;
     }

@@ -133,6 +133,7 @@ struct he_ctx {
     int *d_err = nullptr;                // set by a bounded device wait that gave up
     int key_stream = HE_KEY_STREAM_AUTO; // HE_OPT_KEY_STREAM
     int ntt_form = HE_NTT_TWOPASS;       // HE_OPT_NTT
+    bool small_primes = false;           // every prime below 2^57 (forward NTT without corrections)
     std::mutex tune_mu;                  // root only: the autotuner's log
     // root only: pre-keyed tables (key (.) plaintext and [P]_q plaintext), shared by every
     // fork and stage that uses the same key and plaintext at the same levels; refcounted

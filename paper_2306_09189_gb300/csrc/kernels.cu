@@ -181,6 +181,16 @@ __device__ __forceinline__ void ct_lazy(u64 &X, u64 &Y, u64 w, u64 ws, u64 q, u6
     X = x + t;
     Y = x - t + q2;
 }
+// Forward butterfly without the correction of X (NC, "no correction"): with every prime below
+// 2^57 the values may grow by 2q per stage instead: from [0, 4q) they stay below 36q < 2^63
+// after the 16 stages of n = 2^16 (the Shoup product accepts any 64-bit word), and the last
+// pass reduces them once (Barrett) instead of once per butterfly.
+__device__ __forceinline__ void ct_lazy_nc(u64 &X, u64 &Y, u64 w, u64 ws, u64 q, u64 q2) {
+    const u64 x = X;
+    const u64 t = Y * w - __umul64hi(Y, ws) * q;    // [0, 2q)
+    X = x + t;
+    Y = x - t + q2;
+}
 __device__ __forceinline__ void gs_lazy(u64 &X, u64 &Y, u64 w, u64 ws, u64 q, u64 q2) {
     u64 s = X + Y;
     s = s >= q2 ? s - q2 : s;
@@ -191,7 +201,7 @@ __device__ __forceinline__ void gs_lazy(u64 &X, u64 &Y, u64 w, u64 ws, u64 q, u6
 
 // stage with butterfly distance `half` words inside x[16]; element j has NTT index
 // base + (j << ls); all butterflies of a group of 2*half consecutive j share one twiddle.
-template <bool INV, int H>
+template <bool INV, int H, bool NC = false>
 __device__ __forceinline__ void reg_stage(u64 (&x)[16], int base, int ls, int logn,
                                           const ulonglong2 *__restrict__ W, u64 q, u64 q2) {
     constexpr int half = 1 << H;
@@ -205,20 +215,21 @@ __device__ __forceinline__ void reg_stage(u64 (&x)[16], int base, int ls, int lo
         for (int k = 0; k < half; k++) {
             const int j = g * 2 * half + k;
             if (INV) gs_lazy(x[j], x[j + half], w.x, w.y, q, q2);
+            else if (NC) ct_lazy_nc(x[j], x[j + half], w.x, w.y, q, q2);
             else ct_lazy(x[j], x[j + half], w.x, w.y, q, q2);
         }
     }
 }
 
 // CT stages H = 3..lo (forward) or GS stages lo..3 (inverse), lo in [0, 4]
-template <bool INV>
+template <bool INV, bool NC = false>
 __device__ __forceinline__ void reg_pass(u64 (&x)[16], int base, int ls, int logn, int nstages,
                                          const ulonglong2 *__restrict__ W, u64 q, u64 q2) {
     if (!INV) {
-        if (nstages >= 4) reg_stage<false, 3>(x, base, ls, logn, W, q, q2);
-        if (nstages >= 3) reg_stage<false, 2>(x, base, ls, logn, W, q, q2);
-        if (nstages >= 2) reg_stage<false, 1>(x, base, ls, logn, W, q, q2);
-        if (nstages >= 1) reg_stage<false, 0>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 4) reg_stage<false, 3, NC>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 3) reg_stage<false, 2, NC>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 2) reg_stage<false, 1, NC>(x, base, ls, logn, W, q, q2);
+        if (nstages >= 1) reg_stage<false, 0, NC>(x, base, ls, logn, W, q, q2);
     } else {
         if (nstages >= 1) reg_stage<true, 0>(x, base, ls, logn, W, q, q2);
         if (nstages >= 2) reg_stage<true, 1>(x, base, ls, logn, W, q, q2);
@@ -249,7 +260,7 @@ __device__ __forceinline__ u64 centred_mod(u64 v, u64 ql, u64 q, u64 mu) {
     return reduce64(v, q, mu);
 }
 
-template <bool INV, bool RS = false>
+template <bool INV, bool RS = false, bool NC = false>
 __global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job, RescaleFuse F) {
     pdl_wait();
     __shared__ u64 sm[4096];
@@ -277,13 +288,13 @@ __global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job, Rescale
 #pragma unroll
             for (int j = 0; j < 16; j++) x[j] = a[(size_t)(r + R16 * j) * ROW + c];
         }
-        reg_pass<false>(x, r * ROW + c, lr + 4, kp.logn, 4, W, q, q2);
+        reg_pass<false, NC>(x, r * ROW + c, lr + 4, kp.logn, 4, W, q, q2);
 #pragma unroll
         for (int j = 0; j < 16; j++) sm[(r + R16 * j) * TC + tc] = x[j];
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < 16; e++) x[e] = sm[(16 * r + e) * TC + tc];
-        reg_pass<false>(x, 16 * r * ROW + c, 8, kp.logn, n2, W, q, q2);
+        reg_pass<false, NC>(x, 16 * r * ROW + c, 8, kp.logn, n2, W, q, q2);
 #pragma unroll
         for (int e = 0; e < 16; e++) a[(size_t)(16 * r + e) * ROW + c] = x[e];
     } else {
@@ -307,7 +318,7 @@ __global__ void __launch_bounds__(256, 3) ntt16_cols(KP kp, ntt_job job, Rescale
 
 __device__ __forceinline__ int pad17(int k) { return k + (k >> 4); }
 
-template <bool INV, bool RS = false>
+template <bool INV, bool RS = false, bool NC = false>
 __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job, RescaleFuse F) {
     pdl_wait();
     __shared__ u64 sm[16][272];
@@ -325,17 +336,23 @@ __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job, Rescale
     if (!INV) {
 #pragma unroll
         for (int j = 0; j < 16; j++) x[j] = a[l + 16 * j];
-        reg_pass<false>(x, row * ROW + l, 4, kp.logn, 4, W, q, q2);
+        reg_pass<false, NC>(x, row * ROW + l, 4, kp.logn, 4, W, q, q2);
 #pragma unroll
         for (int j = 0; j < 16; j++) s[pad17(l + 16 * j)] = x[j];
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < 16; e++) x[e] = s[pad17(16 * l + e)];
-        reg_pass<false>(x, row * ROW + 16 * l, 0, kp.logn, 4, W, q, q2);
+        reg_pass<false, NC>(x, row * ROW + 16 * l, 0, kp.logn, 4, W, q, q2);
+        if (NC) {
+            const u64 mu = kp.mu[pr];
 #pragma unroll
-        for (int e = 0; e < 16; e++) {
-            u64 v = x[e] >= q2 ? x[e] - q2 : x[e];
-            s[pad17(16 * l + e)] = v >= q ? v - q : v;
+            for (int e = 0; e < 16; e++) s[pad17(16 * l + e)] = reduce64(x[e], q, mu);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                u64 v = x[e] >= q2 ? x[e] - q2 : x[e];
+                s[pad17(16 * l + e)] = v >= q ? v - q : v;
+            }
         }
         __syncthreads();
         if (RS) {
@@ -2239,7 +2256,11 @@ static int ntt_onepass_launch(const he_ctx *ctx, const ntt_job &job, const Resca
                                             : ntt_cluster<INV, RS, 16>(ctx, job, F, s);
 }
 
-static bool ntt_onepass(const he_ctx *ctx) { return ctx->logn == 16 && ctx->ntt_form != HE_NTT_TWOPASS; }
+static bool ntt_onepass(const he_ctx *ctx) {
+    return ctx->logn == 16 && (ctx->ntt_form == HE_NTT_ONEPASS || ctx->ntt_form == HE_NTT_ONEPASS8);
+}
+// the two-pass forward transform without per-butterfly corrections (every prime below 2^57)
+static bool ntt_nc(const he_ctx *ctx) { return ctx->small_primes && ctx->ntt_form == HE_NTT_TWOPASS; }
 
 int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
     if (job.nl <= 0 || job.npoly <= 0) return HE_OK;
@@ -2255,7 +2276,12 @@ int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
         TraceScope tr("ntt", s, limbs * 2.0 * ctx->n * 8, limbs * (ctx->n / 2) * ctx->logn);
         const int TC = 4096 / R;
         dim3 gA(ROW / TC, job.nl, job.npoly), gB(R / 16, job.nl, job.npoly);
-        if (!inverse) {
+        if (!inverse && ntt_nc(ctx)) {
+            pdl_launch(ntt16_cols<false, false, true>, gA, 256, 0, s, ctx->kp, job, RescaleFuse{});
+            LAUNCH_CHECK();
+            pdl_launch(ntt16_rows<false, false, true>, gB, 256, 0, s, ctx->kp, job, RescaleFuse{});
+            LAUNCH_CHECK();
+        } else if (!inverse) {
             pdl_launch(ntt16_cols<false>, gA, 256, 0, s, ctx->kp, job, RescaleFuse{});
             LAUNCH_CHECK();
             pdl_launch(ntt16_rows<false>, gB, 256, 0, s, ctx->kp, job, RescaleFuse{});
@@ -3259,10 +3285,17 @@ int k_rescale_tab(const he_ctx *ctx, u64 *const *polys, int m, int level, u64 *t
     dim3 gA(ROW / TC, level, 2 * m), gB(R / 16, level, 2 * m);
     TraceScope tr("rescale", s, (double)m * level * ctx->n * 8 * 6, (double)m * level * ctx->n * 2);
     if (ntt_onepass(ctx)) return ntt_onepass_launch<false, true>(ctx, tj, F, s);
-    pdl_launch(ntt16_cols<false, true>, gA, 256, 0, s, ctx->kp, tj, F);
-    LAUNCH_CHECK();
-    pdl_launch(ntt16_rows<false, true>, gB, 256, 0, s, ctx->kp, tj, F);
-    LAUNCH_CHECK();
+    if (ntt_nc(ctx)) {
+        pdl_launch(ntt16_cols<false, true, true>, gA, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+        pdl_launch(ntt16_rows<false, true, true>, gB, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+    } else {
+        pdl_launch(ntt16_cols<false, true>, gA, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+        pdl_launch(ntt16_rows<false, true>, gB, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+    }
     return HE_OK;
 }
 
@@ -3279,10 +3312,17 @@ int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u6
         dim3 gA(ROW / TC, level, 2 * m), gB(R / 16, level, 2 * m);
         TraceScope tr("rescale", s, (double)m * level * ctx->n * 8 * 6, (double)m * level * ctx->n * 2);
         if (ntt_onepass(ctx)) return ntt_onepass_launch<false, true>(ctx, tj, F, s);
-        pdl_launch(ntt16_cols<false, true>, gA, 256, 0, s, ctx->kp, tj, F);
-        LAUNCH_CHECK();
-        pdl_launch(ntt16_rows<false, true>, gB, 256, 0, s, ctx->kp, tj, F);
-        LAUNCH_CHECK();
+        if (ntt_nc(ctx)) {
+            pdl_launch(ntt16_cols<false, true, true>, gA, 256, 0, s, ctx->kp, tj, F);
+            LAUNCH_CHECK();
+            pdl_launch(ntt16_rows<false, true, true>, gB, 256, 0, s, ctx->kp, tj, F);
+            LAUNCH_CHECK();
+        } else {
+            pdl_launch(ntt16_cols<false, true>, gA, 256, 0, s, ctx->kp, tj, F);
+            LAUNCH_CHECK();
+            pdl_launch(ntt16_rows<false, true>, gB, 256, 0, s, ctx->kp, tj, F);
+            LAUNCH_CHECK();
+        }
         return HE_OK;
     }
     pdl_launch(rescale_prep_kernel, dim3(ctx->n / TB, level, 2 * m), TB, 0, s, ctx->kp, base + (size_t)level * ctx->n, ps, t, level);
