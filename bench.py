@@ -532,9 +532,34 @@ BOOT_WORKLOAD = ("bootstrap: one level-0 ciphertext (2^15 real slots, scale 2^40
                  "EvalMod (degree-59 Chebyshev cosine, 2 double angles), 3 SlotToCoeff levels")
 
 
+def cpu_baseline_bootstrap():
+    """The oracle on this host's cores for a bounded sample of the bootstrap at the full ring:
+    ModRaise and the first CoeffToSlot level (32 diagonals, 16 rotations at level 23) of the B24
+    chain, keys for it generated first (untimed)."""
+    from oracle import bootstrap as OB
+    from oracle.ckks import Context
+    from oracle.params import B24
+    o = Context(B24)
+    plan = OB.BootPlan(o)
+    for a in plan.cts[0].rotations():
+        o.gen_rotation_key(a)
+    z = np.random.default_rng(7).uniform(-1, 1, o.N)
+    ct = o.encrypt(z, 0, 2.0 ** 40, nonce=1)
+    pts = plan.plaintexts(o, "cts", 0)
+    t0 = time.perf_counter()
+    x = o.modraise(ct)
+    x.scale = float(o.q[0]) * plan.cfg.K
+    OB.lintrans_he(o, x, plan.cts[0], pts)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": dt, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": "ModRaise + the first CoeffToSlot level (32 diagonals, 16 hoisted rotations, "
+                      "level 23) at n=2^16"}
+
+
 def run_bootstrap(args, ws, rank, local, emit=True):
-    """One bootstrap per step (the paper's largest cost, Sec. 5 tables), as a CUDA graph of the
-    whole pipeline; the decrypted output is compared with the input message."""
+    """One bootstrap per step (the paper's largest cost, Sec. 5 tables), the whole pipeline
+    captured as a CUDA graph; the decrypted output is compared with the input message."""
     import torch
     from paper_2306_09189_gb300 import hegpu as H
     from paper_2306_09189_gb300 import host
@@ -574,18 +599,36 @@ def run_bootstrap(args, ws, rank, local, emit=True):
     H.he_graph_launch(graph, stream)
     torch.cuda.synchronize()
     err = float(np.max(np.abs(H.he_decrypt(ctx, y, N) - z)))
+    # the timed region: K bootstraps in one graph, the fused key-switch kernel traced
+    trace = args.trace
+    H.he_trace_start(trace)
+    H.he_graph_begin(ctx, stream)
+    for _ in range(args.steps):
+        H.he_bootstrap(ctx, bt, x, y, stream)
+    gk = H.he_graph_end(ctx, stream)
     clocks = Clocks(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks.start()
     torch.cuda.synchronize()
+    l0 = H.he_kernel_launches()
     e0.record(ts)
-    for _ in range(args.steps):
-        H.he_graph_launch(graph, stream)
+    H.he_graph_launch(gk, stream)
     e1.record(ts)
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    # eager (no graph) for comparison
+    launches = (H.he_kernel_launches() - l0) / args.steps
+    tr = H.he_trace_stop()
+    peaks, src = _peaks()
+    roof = None
+    if tr and tr["launches"]:
+        per = tr["ms"] / tr["launches"]
+        ach = tr["bytes"] / tr["launches"] / (per * 1e-3) / 1e9
+        roof = {"kernel": trace, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                "launches": tr["launches"] / args.steps, "ms_per_launch": per,
+                "share_of_step": tr["ms"] / (ms * args.steps)}
+    # eager (no graph) for comparison, and the oracle's sample beside it
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(3):
@@ -597,15 +640,18 @@ def run_bootstrap(args, ws, rank, local, emit=True):
             "dtype": "u64", "data": "synthetic",
             "config": {"workload": BOOT_WORKLOAD, "key_switches_per_step": info["keyswitches"],
                        "input_levels": [0], "output_level": info["out_level"], "setup_s": setup_s,
-                       "key_bytes": H.load().he_key_bytes(ctx)},
-            "eager_ms": eager_ms, "gpu_launches": H.he_graph_kernels(graph),
+                       "key_bytes": H.he_key_bytes(ctx), "cuda_graph": True},
+            "eager_ms": eager_ms, "gpu_launches": int(round(launches)), "roofline": roof,
             "check": {"max_abs_error": err, "bits": -float(np.log2(err)) if err > 0 else None},
             "clocks": ck}
     H.he_graph_destroy(graph)
+    H.he_graph_destroy(gk)
     H.he_boot_destroy(bt)
     for c in (x, y):
         H.he_ct_free(c)
     H.he_ctx_destroy(ctx)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_bootstrap()
     if emit and rank == 0:
         print(json.dumps(line), flush=True)
     return line if rank == 0 else None
@@ -1066,7 +1112,7 @@ def _extra_summary(d):
     if d is None:
         return None
     keep = ("ms_per_step", "value", "unit", "steps", "plain", "check", "roofline", "clocks", "gpu_launches",
-            "eager_ms")
+            "eager_ms", "cpu_baseline")
     out = {k: d[k] for k in keep if k in d}
     out["workload"] = d["config"]["workload"]
     for k in ("key_switches_per_step", "input_levels", "output_level", "setup_s", "l2",
