@@ -225,7 +225,7 @@ def run_block(args, ws, rank, local, emit=True):
     from paper_2306_09189_gb300 import host
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
-    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS, "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED}[args.ntt])
+    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS, "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED, "twopass-shuffle": H.HE_NTT_TWOPASS_SHUFFLE}[args.ntt])
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
@@ -416,7 +416,7 @@ def run_head(args, ws, rank, local):
     from paper_2306_09189_gb300 import host
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
-    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS, "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED}[args.ntt])
+    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS, "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED, "twopass-shuffle": H.HE_NTT_TWOPASS_SHUFFLE}[args.ntt])
     N = H.he_ctx_info(ctx)["slots"]
     level, n_img = 4, 8
     x0, W, b = workloads.resnet_head(0)
@@ -567,7 +567,7 @@ def run_bootstrap(args, ws, rank, local, emit=True):
     ctx = H.he_ctx_create(pr)
     H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8,
                                             "twopass": H.HE_NTT_TWOPASS,
-                                            "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED}[args.ntt])
+                                            "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED, "twopass-shuffle": H.HE_NTT_TWOPASS_SHUFFLE}[args.ntt])
     N = H.he_ctx_info(ctx)["slots"]
     t_setup = time.perf_counter()
     bt = H.he_boot_create(ctx)
@@ -668,7 +668,7 @@ def run_stem(args, ws, rank, local, emit=True):
     from paper_2306_09189_gb300 import host
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
-    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS, "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED}[args.ntt])
+    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS, "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED, "twopass-shuffle": H.HE_NTT_TWOPASS_SHUFFLE}[args.ntt])
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
@@ -800,11 +800,12 @@ def main():
                          "baby-step giant-step")
     ap.add_argument("--bsgs-k", type=int, default=0,
                     help="giant stride (blocks) of the baby-step giant-step convolutions; 0 = cost model")
-    ap.add_argument("--ntt", default="twopass", choices=["onepass", "onepass8", "twopass", "twopass-corrected"],
+    ap.add_argument("--ntt", default="twopass", choices=["onepass", "onepass8", "twopass", "twopass-corrected", "twopass-shuffle"],
                     help="NTT at n = 2^16: one launch per limb on a 16-CTA cluster (onepass), on an "
                          "8-CTA cluster (onepass8), or the two-pass column/row form (its forward "
                          "butterflies without the per-butterfly correction when the primes allow, "
-                         "or with it: twopass-corrected)")
+                         "or with it: twopass-corrected; twopass-shuffle: the row pass's transposes by "
+                         "warp shuffles)")
     ap.add_argument("--poly", default="ps", choices=["ps", "tree"],
                     help="GELU evaluation: Paterson-Stockmeyer (default) or the binary tree")
     ap.add_argument("--workload", default="cifar-layer",
@@ -835,7 +836,7 @@ def main():
 
     pr = host.cifar_params(seed=0)
     ctx = H.he_ctx_create(pr)
-    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS, "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED}[args.ntt])
+    H.he_ctx_set_option(ctx, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8, "twopass": H.HE_NTT_TWOPASS, "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED, "twopass-shuffle": H.HE_NTT_TWOPASS_SHUFFLE}[args.ntt])
     H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, {"auto": H.HE_KEY_STREAM_AUTO, "ldg": H.HE_KEY_STREAM_LDG,
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,

@@ -204,13 +204,15 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  * two launches with the limb going through memory in between (the default).  When every prime
  * of the context is below 2^57 the two-pass forward transform skips the per-butterfly
  * correction (values grow by at most 2q per stage and are reduced once at the end);
- * HE_NTT_TWOPASS_CORRECTED (3) keeps the correction in every butterfly.  Same words in every
- * form; smaller rings always take a two-pass form. */
+ * HE_NTT_TWOPASS_CORRECTED (3) keeps the correction in every butterfly; HE_NTT_TWOPASS_SHUFFLE
+ * (4) does the row pass's two in-row transposes with warp shuffles instead of shared memory
+ * (rings 2^12..2^16).  Same words in every form; smaller rings always take a two-pass form. */
 #define HE_OPT_NTT 3
 #define HE_NTT_ONEPASS 0
 #define HE_NTT_TWOPASS 1
 #define HE_NTT_ONEPASS8 2
 #define HE_NTT_TWOPASS_CORRECTED 3
+#define HE_NTT_TWOPASS_SHUFFLE 4
 int he_ctx_set_option(he_ctx *ctx, int option, int value);
 int he_ctx_get_option(const he_ctx *ctx, int option, int *value);
 /* The autotuner's decisions so far (one line per tuned stage: the candidates' times and the

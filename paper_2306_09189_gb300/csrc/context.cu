@@ -814,7 +814,7 @@ extern "C" int he_ctx_set_option(he_ctx *c, int option, int value) {
         return HE_OK;
     }
     if (option == HE_OPT_NTT && (value == HE_NTT_ONEPASS || value == HE_NTT_TWOPASS || value == HE_NTT_ONEPASS8 ||
-                                 value == HE_NTT_TWOPASS_CORRECTED)) {
+                                 value == HE_NTT_TWOPASS_CORRECTED || value == HE_NTT_TWOPASS_SHUFFLE)) {
         c->ntt_form = value;
         return HE_OK;
     }

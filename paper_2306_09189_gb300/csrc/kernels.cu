@@ -385,6 +385,84 @@ __global__ void __launch_bounds__(256, 3) ntt16_rows(KP kp, ntt_job job, Rescale
     }
 }
 
+// The row pass with the in-row transposes done by warp shuffles instead of shared memory
+// (HE_NTT_TWOPASS_SHUFFLE): the 16 threads of a row are half a warp, so element (lane l,
+// register j) moves to (lane j, register l) in four rounds of xor-shuffles, each swapping the
+// off-diagonal halves of the 2m x 2m blocks (m = 8, 4, 2, 1).  No shared memory and no block
+// barrier; 32 64-bit shuffles and their selects per transpose.  Same words as ntt16_rows.
+__device__ __forceinline__ u64 shfl_xor64(u64 v, int m) {
+    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)v, m);
+    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), m);
+    return ((u64)hi << 32) | lo;
+}
+__device__ __forceinline__ void lane_transpose16(u64 (&x)[16], int l) {
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int m = 8 >> r;
+        const bool b = (l & m) != 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+            if (!(j & m)) {
+                const u64 recv = shfl_xor64(b ? x[j] : x[j + m], m);
+                if (b) x[j] = recv;
+                else x[j + m] = recv;
+            }
+    }
+}
+
+template <bool INV, bool RS = false, bool NC = false>
+__global__ void __launch_bounds__(256, 3) ntt16_rows_shfl(KP kp, ntt_job job, RescaleFuse F) {
+    pdl_wait();
+    const int p = blockIdx.z;
+    const int limb = job_limb(job, blockIdx.y, p);
+    if (limb < 0) return;
+    const int pr = prime_of(kp, limb, job.nq);
+    const u64 q = kp.q[pr], q2 = 2 * q;
+    const int t = threadIdx.x, rl = t >> 4, l = t & 15;
+    const int row = blockIdx.x * 16 + rl;
+    u64 *a = job_poly(job, p) + (size_t)limb * kp.n + (size_t)row * ROW;
+    const ulonglong2 *W = (const ulonglong2 *)(INV ? kp.itw2 : kp.tw2) + (size_t)pr * kp.n;
+    u64 x[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) x[j] = a[l + 16 * j];
+    if (!INV) {
+        reg_pass<false, NC>(x, row * ROW + l, 4, kp.logn, 4, W, q, q2);
+        lane_transpose16(x, l);
+        reg_pass<false, NC>(x, row * ROW + 16 * l, 0, kp.logn, 4, W, q, q2);
+        if (NC) {
+            const u64 mu = kp.mu[pr];
+#pragma unroll
+            for (int e = 0; e < 16; e++) x[e] = reduce64(x[e], q, mu);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; e++) {
+                const u64 v = x[e] >= q2 ? x[e] - q2 : x[e];
+                x[e] = v >= q ? v - q : v;
+            }
+        }
+        lane_transpose16(x, l);
+        if (RS) {
+            u64 *cr = fuse_poly(F, p) + (size_t)limb * kp.n + (size_t)row * ROW;
+            const u64 iv = F.inv[pr], ivs = F.invs[pr];
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                u64 *xp = cr + l + 16 * j;
+                *xp = mul_shoup(sub_mod(*xp, x[j], q), iv, ivs, q);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++) a[l + 16 * j] = x[j];
+        }
+    } else {
+        lane_transpose16(x, l);
+        reg_pass<true>(x, row * ROW + 16 * l, 0, kp.logn, 4, W, q, q2);
+        lane_transpose16(x, l);
+        reg_pass<true>(x, row * ROW + l, 4, kp.logn, 4, W, q, q2);
+#pragma unroll
+        for (int j = 0; j < 16; j++) a[l + 16 * j] = x[j];
+    }
+}
+
 // ------------------------------------------------------------------------------ one-pass NTT
 // n = 2^16 in ONE launch: each limb is transformed by a cluster of CL CTAs (CL = 8 or 16, 16 words
 // per thread), so the data crosses HBM/L2 once each way instead of twice.  View the limb as CL
@@ -2260,7 +2338,11 @@ static bool ntt_onepass(const he_ctx *ctx) {
     return ctx->logn == 16 && (ctx->ntt_form == HE_NTT_ONEPASS || ctx->ntt_form == HE_NTT_ONEPASS8);
 }
 // the two-pass forward transform without per-butterfly corrections (every prime below 2^57)
-static bool ntt_nc(const he_ctx *ctx) { return ctx->small_primes && ctx->ntt_form == HE_NTT_TWOPASS; }
+static bool ntt_nc(const he_ctx *ctx) {
+    return ctx->small_primes && (ctx->ntt_form == HE_NTT_TWOPASS || ctx->ntt_form == HE_NTT_TWOPASS_SHUFFLE);
+}
+// the row pass with its transposes by warp shuffles
+static bool ntt_shfl(const he_ctx *ctx) { return ctx->ntt_form == HE_NTT_TWOPASS_SHUFFLE; }
 
 int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
     if (job.nl <= 0 || job.npoly <= 0) return HE_OK;
@@ -2276,7 +2358,25 @@ int k_ntt(const he_ctx *ctx, const ntt_job &job, bool inverse, cudaStream_t s) {
         TraceScope tr("ntt", s, limbs * 2.0 * ctx->n * 8, limbs * (ctx->n / 2) * ctx->logn);
         const int TC = 4096 / R;
         dim3 gA(ROW / TC, job.nl, job.npoly), gB(R / 16, job.nl, job.npoly);
-        if (!inverse && ntt_nc(ctx)) {
+        if (ntt_shfl(ctx)) {
+            if (!inverse) {
+                if (ntt_nc(ctx)) {
+                    pdl_launch(ntt16_cols<false, false, true>, gA, 256, 0, s, ctx->kp, job, RescaleFuse{});
+                    LAUNCH_CHECK();
+                    pdl_launch(ntt16_rows_shfl<false, false, true>, gB, 256, 0, s, ctx->kp, job, RescaleFuse{});
+                } else {
+                    pdl_launch(ntt16_cols<false>, gA, 256, 0, s, ctx->kp, job, RescaleFuse{});
+                    LAUNCH_CHECK();
+                    pdl_launch(ntt16_rows_shfl<false>, gB, 256, 0, s, ctx->kp, job, RescaleFuse{});
+                }
+                LAUNCH_CHECK();
+            } else {
+                pdl_launch(ntt16_rows_shfl<true>, gB, 256, 0, s, ctx->kp, job, RescaleFuse{});
+                LAUNCH_CHECK();
+                pdl_launch(ntt16_cols<true>, gA, 256, 0, s, ctx->kp, job, RescaleFuse{});
+                LAUNCH_CHECK();
+            }
+        } else if (!inverse && ntt_nc(ctx)) {
             pdl_launch(ntt16_cols<false, false, true>, gA, 256, 0, s, ctx->kp, job, RescaleFuse{});
             LAUNCH_CHECK();
             pdl_launch(ntt16_rows<false, false, true>, gB, 256, 0, s, ctx->kp, job, RescaleFuse{});
@@ -3285,7 +3385,17 @@ int k_rescale_tab(const he_ctx *ctx, u64 *const *polys, int m, int level, u64 *t
     dim3 gA(ROW / TC, level, 2 * m), gB(R / 16, level, 2 * m);
     TraceScope tr("rescale", s, (double)m * level * ctx->n * 8 * 6, (double)m * level * ctx->n * 2);
     if (ntt_onepass(ctx)) return ntt_onepass_launch<false, true>(ctx, tj, F, s);
-    if (ntt_nc(ctx)) {
+    if (ntt_shfl(ctx) && ntt_nc(ctx)) {
+        pdl_launch(ntt16_cols<false, true, true>, gA, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+        pdl_launch(ntt16_rows_shfl<false, true, true>, gB, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+    } else if (ntt_shfl(ctx)) {
+        pdl_launch(ntt16_cols<false, true>, gA, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+        pdl_launch(ntt16_rows_shfl<false, true>, gB, 256, 0, s, ctx->kp, tj, F);
+        LAUNCH_CHECK();
+    } else if (ntt_nc(ctx)) {
         pdl_launch(ntt16_cols<false, true, true>, gA, 256, 0, s, ctx->kp, tj, F);
         LAUNCH_CHECK();
         pdl_launch(ntt16_rows<false, true, true>, gB, 256, 0, s, ctx->kp, tj, F);
@@ -3312,7 +3422,17 @@ int k_rescale_many(const he_ctx *ctx, u64 *base, size_t ps, int m, int level, u6
         dim3 gA(ROW / TC, level, 2 * m), gB(R / 16, level, 2 * m);
         TraceScope tr("rescale", s, (double)m * level * ctx->n * 8 * 6, (double)m * level * ctx->n * 2);
         if (ntt_onepass(ctx)) return ntt_onepass_launch<false, true>(ctx, tj, F, s);
-        if (ntt_nc(ctx)) {
+        if (ntt_shfl(ctx) && ntt_nc(ctx)) {
+            pdl_launch(ntt16_cols<false, true, true>, gA, 256, 0, s, ctx->kp, tj, F);
+            LAUNCH_CHECK();
+            pdl_launch(ntt16_rows_shfl<false, true, true>, gB, 256, 0, s, ctx->kp, tj, F);
+            LAUNCH_CHECK();
+        } else if (ntt_shfl(ctx)) {
+            pdl_launch(ntt16_cols<false, true>, gA, 256, 0, s, ctx->kp, tj, F);
+            LAUNCH_CHECK();
+            pdl_launch(ntt16_rows_shfl<false, true>, gB, 256, 0, s, ctx->kp, tj, F);
+            LAUNCH_CHECK();
+        } else if (ntt_nc(ctx)) {
             pdl_launch(ntt16_cols<false, true, true>, gA, 256, 0, s, ctx->kp, tj, F);
             LAUNCH_CHECK();
             pdl_launch(ntt16_rows<false, true, true>, gB, 256, 0, s, ctx->kp, tj, F);

@@ -21,7 +21,7 @@ HE_KEY_STREAM_LDG1 = 5
 HE_KEY_STREAM_PK = 6
 HE_OPT_PDL = 2
 HE_OPT_NTT = 3
-HE_NTT_ONEPASS, HE_NTT_TWOPASS, HE_NTT_ONEPASS8, HE_NTT_TWOPASS_CORRECTED = 0, 1, 2, 3
+HE_NTT_ONEPASS, HE_NTT_TWOPASS, HE_NTT_ONEPASS8, HE_NTT_TWOPASS_CORRECTED, HE_NTT_TWOPASS_SHUFFLE = 0, 1, 2, 3, 4
 HE_KEY_STREAM_PK3 = 7
 HE_KEY_STREAM_PKP = 8
 HE_KEY_STREAM_SPLITM = 9

@@ -213,7 +213,7 @@ def pair20():
     g.close()
 
 
-@pytest.mark.parametrize("form", ["onepass", "onepass8", "twopass", "twopass-corrected"])
+@pytest.mark.parametrize("form", ["onepass", "onepass8", "twopass", "twopass-corrected", "twopass-shuffle"])
 @pytest.mark.parametrize("level", [19, 12])
 def test_full_ring_rotation_bit_exact(pair20, level, form):
     """At n = 2^16 every NTT form (one launch per limb on a CTA cluster, or two passes with or
@@ -224,7 +224,8 @@ def test_full_ring_rotation_bit_exact(pair20, level, form):
     o, g = pair20
     H.he_ctx_set_option(g.h, H.HE_OPT_NTT, {"onepass": H.HE_NTT_ONEPASS, "onepass8": H.HE_NTT_ONEPASS8,
                                             "twopass": H.HE_NTT_TWOPASS,
-                                            "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED}[form])
+                                            "twopass-corrected": H.HE_NTT_TWOPASS_CORRECTED,
+                                            "twopass-shuffle": H.HE_NTT_TWOPASS_SHUFFLE}[form])
     try:
         ct, z = _rand_ct(o, level, 200 + level)
         o.gen_rotation_key(33)
@@ -251,15 +252,17 @@ def test_full_ring_ntt_forms_give_the_same_words(pair20):
     q = np.array([int(v) for v in o.q[:level + 1]], dtype=np.uint64)
     words = (rng.integers(0, 2 ** 63, (2, level + 1, o.n), dtype=np.uint64) % q[None, :, None])
     one, two, eight, corr = H.HE_NTT_ONEPASS, H.HE_NTT_TWOPASS, H.HE_NTT_ONEPASS8, H.HE_NTT_TWOPASS_CORRECTED
+    shf = H.HE_NTT_TWOPASS_SHUFFLE
     try:
-        for fwd, inv in ((one, two), (two, one), (one, one), (eight, two), (two, eight), (two, corr), (corr, two)):
+        for fwd, inv in ((one, two), (two, one), (one, one), (eight, two), (two, eight), (two, corr), (corr, two),
+                         (shf, two), (two, shf), (shf, shf)):
             x = g.ct(level)
             H.he_ctx_set_option(g.h, H.HE_OPT_NTT, fwd)
             H.he_ct_import_coeffs(x, words, level, o.pr.scale)
             H.he_ctx_set_option(g.h, H.HE_OPT_NTT, inv)
             assert np.array_equal(g.download(x), words)
         m = rng.integers(-2 ** 40, 2 ** 40, o.n, dtype=np.int64)
-        for form in (one, two, eight, corr):
+        for form in (one, two, eight, corr, shf):
             H.he_ctx_set_option(g.h, H.HE_OPT_NTT, form)
             x = g.ct(level)
             H.he_encrypt_coeffs(g.h, m, level, o.pr.scale, 77, x)
