@@ -264,3 +264,33 @@ def test_network_deeper_than_the_chain():
         H.he_boot_destroy(bt)
     finally:
         g.close()
+
+
+def test_bootstrap_errors_leave_the_context_usable(boot12):
+    from oracle.params import TOY
+    o, plan, g, bt = boot12
+    # a chain too short for the 15 levels
+    small = GpuCtx(TOY)
+    try:
+        with pytest.raises(H.HEError) as e:
+            H.he_boot_create(small.h)
+        assert e.value.code == H.HE_ELEVEL
+    finally:
+        small.close()
+    ct = o.encrypt(np.zeros(o.N), 0, 2.0 ** 40, nonce=60)
+    d = g.upload(ct)
+    # an output below the bootstrap's output level
+    low = g.ct(0)
+    if plan.out_level > 0:
+        with pytest.raises(H.HEError) as e:
+            H.he_bootstrap(g.h, bt, d, low)
+        assert e.value.code == H.HE_ELEVEL
+    # a bad linear level index, a wrong coefficient count
+    with pytest.raises(H.HEError):
+        H.he_boot_n_plaintexts(bt, 0, 99)
+    with pytest.raises(H.HEError):
+        H.he_boot_import_coeffs(bt, np.zeros(5))
+    # the plan still runs
+    out = g.ct(plan.out_level)
+    H.he_bootstrap(g.h, bt, d, out)
+    assert H.he_ct_level(out) == plan.out_level
