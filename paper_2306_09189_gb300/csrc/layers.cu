@@ -4361,6 +4361,10 @@ extern "C" int he_boot_lintrans(he_ctx *c, he_boot *bt, int stage, int idx, cons
 
 extern "C" int he_bootstrap(he_ctx *c, he_boot *bt, const he_ct *in, he_ct *out, void *stream) {
     if (!c || !bt || bt->c != c || !in || !out || in->ctx != c) { he_set_error("he_bootstrap: bad argument"); return HE_EINVAL; }
+    if (out->ctx != c || out->cap < bt->out_level) {
+        he_set_error("he_bootstrap: output allocated below level %d", bt->out_level);
+        return HE_ELEVEL;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const double q0 = (double)c->primes[0];
     he_ct *x = bt->x, *y = bt->y;
