@@ -4073,12 +4073,13 @@ struct BootLin {
     double gain = 1.0;
     std::vector<int> giants;                      // giant indices, ascending
     std::vector<std::vector<int>> js;             // per giant: baby indices, ascending
-    std::vector<std::vector<cplx>> vals;          // per term (giant-major): the rotated diagonal
+    std::vector<std::vector<cplx>> vals;          // per term (giant-major): the rotated diagonal (until encoded)
+    size_t terms = 0;
     size_t pw = 0, pe = 0;
     u64 *pts = nullptr, *R = nullptr, *Sb = nullptr, *acc = nullptr;
     FusedStage B, G;
     bool prepared = false;
-    size_t n_terms() const { return vals.size(); }
+    size_t n_terms() const { return terms; }
     ~BootLin() { he_free(pts); he_free(R); he_free(Sb); he_free(acc); }
     void amounts(std::set<int> &out) const {
         const int N = c->N;
@@ -4121,6 +4122,7 @@ static int boot_lin_plan(he_ctx *c, BootLin &L, const std::vector<int> &hs, cons
             L.vals.push_back(std::move(r));
         }
     }
+    L.terms = L.vals.size();
     return HE_OK;
 }
 
@@ -4130,6 +4132,7 @@ static int boot_lin_upload(he_ctx *c, BootLin &L, const int64_t *given) {
     if (!L.pts) HE_TRY(dev_alloc(&L.pts, T * L.pe));
     std::vector<const double *> none;
     if (given) return upload_plaintexts(c, none, T, 0.0, L.level, L.pts, given, true);
+    if (L.vals.size() != T) { he_set_error("bootstrap level: diagonals already released"); return HE_ESTATE; }
     std::vector<int64_t> ints(T * n);
     std::vector<double> re(c->N), im(c->N);
     const double S = (double)c->primes[L.level];
@@ -4273,6 +4276,7 @@ extern "C" int he_boot_create(he_ctx *c, const he_boot_config *cfg_in, he_boot *
             Lv->pe = (size_t)(Lv->level + 1 + c->K) * c->n;
             HE_TRY(boot_lin_plan(c, *Lv, mine, D));
             HE_TRY(boot_lin_upload(c, *Lv, nullptr));
+            std::vector<std::vector<cplx>>().swap(Lv->vals);   // encoded: the host copy goes
             bt->lin[st].push_back(std::move(Lv));
         }
     }
