@@ -507,6 +507,14 @@ int he_boot_lintrans(he_ctx *ctx, he_boot *bt, int stage, int idx, const he_ct *
  * scale q_0 / 2^10 (dropped to level 1, times the integer round((q_0 / 2^10) q_1 / s),
  * rescaled), so a network can bootstrap wherever its levels run out. */
 int he_bootstrap(he_ctx *ctx, he_boot *bt, const he_ct *in, he_ct *out, void *stream);
+/* The bootstrap with its own error removed once more (the paper's Appendix, "Precision and
+ * Bootstrapping Noise": MetaBTS, about twice the bits for one level and a second bootstrap):
+ * c1 = bootstrap(in); the difference of c1 (brought back to level 0 at the input's scale) and
+ * the input encrypts the bootstrap's error E; it is bootstrapped at 2^kb times its size
+ * (kb in 0..30, 10 suits 2^-13 errors) and subtracted.  out (allocated at the bootstrap's
+ * output level or above) receives c1 - E at one level below the bootstrap's output, c1's
+ * scale. */
+int he_bootstrap_meta(he_ctx *ctx, he_boot *bt, const he_ct *in, int kb, he_ct *out, void *stream);
 
 /* ------------------------------------------------------------------ polynomial approximation (Appendix) */
 /* Activation functions: GELU x Phi(x) (exact erf), ReLU, SiLU x / (1 + e^-x), Softplus. */

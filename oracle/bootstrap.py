@@ -363,3 +363,37 @@ def bootstrap(ctx, ct, plan: BootPlan, trace=None):
         if trace is not None:
             trace["stc%d" % i] = w
     return w
+
+
+def meta_bootstrap(ctx, ct, plan: BootPlan, kb=10):
+    """Bootstrapping with its own error removed once more (the paper's Appendix on precision
+    and bootstrapping noise applies MetaBTS for about twice the bits, one level and a second
+    bootstrap more): c1 = bootstrap(ct); the difference of c1 (brought back to level 0 at ct's
+    scale) and ct encrypts the bootstrapping error E; it is bootstrapped at 2^kb times its size
+    and subtracted: c1 - E, at one level below the bootstrap's output.
+
+      y  = c1 dropped to level 1, times round(s0 q_1 / s), rescaled; read at scale s0 (exact to
+           1/(2k) relative, k ~ 2^40)
+      e  = (y - ct) 2^kb                 level 0, value E 2^kb
+      f  = bootstrap(e), scale times 2^kb (value E plus its own error / 2^kb)
+      g  = f times round(s1 q_lv / s_f), rescaled, read at c1's scale s1
+      out = c1 dropped to lv - 1, minus g"""
+    ct = to_level0(ctx, ct)
+    s0 = ct.scale
+    c1 = bootstrap(ctx, ct, plan)
+    y = ctx.drop_to(c1, 1)
+    k = int(round(s0 * float(ctx.q[1]) / y.scale))
+    y = ctx.mul_int(y, k)
+    y.scale = y.scale * k
+    y = ctx.rescale(y)
+    y.scale = s0
+    e = ctx.mul_int(ctx.sub_ct(y, ct), 2 ** kb)
+    f = bootstrap(ctx, e, plan)
+    f.scale = f.scale * 2.0 ** kb
+    lv = f.level
+    kf = int(round(c1.scale * float(ctx.q[lv]) / f.scale))
+    g = ctx.mul_int(f, kf)
+    g.scale = f.scale * kf
+    g = ctx.rescale(g)
+    g.scale = c1.scale
+    return ctx.sub_ct(ctx.drop_to(c1, lv - 1), g)

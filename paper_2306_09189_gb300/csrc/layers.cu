@@ -4198,8 +4198,9 @@ struct he_boot {
     std::vector<double> coeffs;
     int depth = 0, evalmod_level = 0, top_stc = 0, out_level = 0;
     he_ct *x = nullptr, *y = nullptr, *cj = nullptr, *re = nullptr, *im = nullptr, *sq = nullptr, *sq2 = nullptr;
+    he_ct *m0 = nullptr, *m1 = nullptr, *m2 = nullptr;   // the meta-bootstrap's level-0 input, c1, y / e
     ~he_boot() {
-        for (he_ct *t : {x, y, cj, re, im, sq, sq2}) he_ct_free(t);
+        for (he_ct *t : {x, y, cj, re, im, sq, sq2, m0, m1, m2}) he_ct_free(t);
     }
 };
 
@@ -4280,7 +4281,8 @@ extern "C" int he_boot_create(he_ctx *c, const he_boot_config *cfg_in, he_boot *
             bt->lin[st].push_back(std::move(Lv));
         }
     }
-    for (he_ct **t : {&bt->x, &bt->y, &bt->cj, &bt->re, &bt->im, &bt->sq, &bt->sq2}) HE_TRY(he_ct_alloc(c, L, t));
+    for (he_ct **t : {&bt->x, &bt->y, &bt->cj, &bt->re, &bt->im, &bt->sq, &bt->sq2, &bt->m0, &bt->m1, &bt->m2})
+        HE_TRY(he_ct_alloc(c, L, t));
     *out = bt.release();
     return HE_OK;
 }
@@ -4363,6 +4365,17 @@ extern "C" int he_boot_lintrans(he_ctx *c, he_boot *bt, int stage, int idx, cons
     return boot_lin_run(c, *bt->lin[stage][idx], in, out, (cudaStream_t)stream);
 }
 
+// An input above level 0 brought to level 0 at scale q_0 / 2^10: dropped to level 1, times the
+// integer round((q_0 / 2^10) q_1 / s), rescaled (scale s k / q_1, exact bookkeeping).
+static int boot_to_level0(he_ctx *c, const he_ct *in, he_ct *dst, void *stream) {
+    HE_TRY(he_ct_copy(dst, in, stream));
+    HE_TRY(he_ct_drop_level(dst, 1));
+    const double kk = std::nearbyint((double)c->primes[0] / 1024.0 * (double)c->primes[1] / dst->scale);
+    HE_TRY(he_mul_int(c, dst, kk, stream));
+    dst->scale = dst->scale * kk;
+    return he_rescale(c, dst, stream);
+}
+
 extern "C" int he_bootstrap(he_ctx *c, he_boot *bt, const he_ct *in, he_ct *out, void *stream) {
     if (!c || !bt || bt->c != c || !in || !out || in->ctx != c) { he_set_error("he_bootstrap: bad argument"); return HE_EINVAL; }
     if (out->ctx != c || out->cap < bt->out_level) {
@@ -4373,14 +4386,7 @@ extern "C" int he_bootstrap(he_ctx *c, he_boot *bt, const he_ct *in, he_ct *out,
     const double q0 = (double)c->primes[0];
     he_ct *x = bt->x, *y = bt->y;
     if (in->level > 0) {
-        // to level 0 at scale q_0 / 2^10: drop to level 1, times the integer
-        // round((q_0 / 2^10) q_1 / s), rescale (scale s k / q_1, exact bookkeeping)
-        HE_TRY(he_ct_copy(y, in, stream));
-        HE_TRY(he_ct_drop_level(y, 1));
-        const double kk = std::nearbyint(q0 / 1024.0 * (double)c->primes[1] / y->scale);
-        HE_TRY(he_mul_int(c, y, kk, stream));
-        y->scale = y->scale * kk;
-        HE_TRY(he_rescale(c, y, stream));
+        HE_TRY(boot_to_level0(c, in, y, stream));
         in = y;
     }
     const double in_scale = in->scale;
@@ -4447,5 +4453,51 @@ extern "C" int he_bootstrap(he_ctx *c, he_boot *bt, const he_ct *in, he_ct *out,
     HE_TRY(ensure_ct(c, out, x->level));
     HE_TRY(he_ct_copy(out, x, stream));
     out->scale = x->scale;
+    return HE_OK;
+}
+
+// Bootstrapping with its own error removed once more (the paper's Appendix on precision and
+// bootstrapping noise, MetaBTS): c1 = bootstrap(ct); y = c1 brought back to level 0 at ct's
+// scale (dropped to level 1, times round(s0 q_1 / s), rescaled, read at s0); e = (y - ct) 2^kb
+// encrypts the bootstrap's error 2^kb times larger; f = bootstrap(e) with its scale times 2^kb;
+// g = f times round(s1 q_lv / s_f), rescaled, read at c1's scale; out = c1 (dropped) - g, one
+// level below the bootstrap's output.
+extern "C" int he_bootstrap_meta(he_ctx *c, he_boot *bt, const he_ct *in, int kb, he_ct *out, void *stream) {
+    if (!c || !bt || bt->c != c || !in || !out || in->ctx != c || kb < 0 || kb > 30) {
+        he_set_error("he_bootstrap_meta: bad argument");
+        return HE_EINVAL;
+    }
+    if (bt->out_level < 1 || out->ctx != c || out->cap < bt->out_level) {
+        he_set_error("he_bootstrap_meta: needs the bootstrap's output level (%d) and one more", bt->out_level);
+        return HE_ELEVEL;
+    }
+    he_ct *ct0 = bt->m0, *c1 = bt->m1, *y = bt->m2;
+    if (in->level > 0) HE_TRY(boot_to_level0(c, in, ct0, stream));
+    else HE_TRY(he_ct_copy(ct0, in, stream));
+    const double s0 = ct0->scale;
+    HE_TRY(he_bootstrap(c, bt, ct0, c1, stream));
+    // y = c1 at level 0, read at s0
+    HE_TRY(he_ct_copy(y, c1, stream));
+    HE_TRY(he_ct_drop_level(y, 1));
+    const double k = std::nearbyint(s0 * (double)c->primes[1] / y->scale);
+    HE_TRY(he_mul_int(c, y, k, stream));
+    y->scale = y->scale * k;
+    HE_TRY(he_rescale(c, y, stream));
+    y->scale = s0;
+    // e = (y - ct) 2^kb
+    HE_TRY(he_sub(c, y, ct0, stream));
+    HE_TRY(he_mul_int(c, y, std::ldexp(1.0, kb), stream));
+    // f = bootstrap(e), value E (its scale times 2^kb)
+    HE_TRY(he_bootstrap(c, bt, y, out, stream));
+    out->scale = out->scale * std::ldexp(1.0, kb);
+    const int lv = out->level;
+    const double kf = std::nearbyint(c1->scale * (double)c->primes[lv] / out->scale);
+    HE_TRY(he_mul_int(c, out, kf, stream));
+    out->scale = out->scale * kf;
+    HE_TRY(he_rescale(c, out, stream));
+    // out = c1 (dropped to lv - 1) - g
+    HE_TRY(he_ct_drop_level(c1, lv - 1));
+    HE_TRY(he_sub(c, c1, out, stream));
+    HE_TRY(he_ct_copy(out, c1, stream));
     return HE_OK;
 }

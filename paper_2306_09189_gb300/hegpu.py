@@ -136,6 +136,7 @@ _SIGS = {
     "he_boot_import_coeffs": (c_int, [c_vp, F64P, c_int]),
     "he_boot_lintrans": (c_int, [c_vp, c_vp, c_int, c_int, c_vp, c_vp, c_vp]),
     "he_bootstrap": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "he_bootstrap_meta": (c_int, [c_vp, c_vp, c_vp, c_int, c_vp, c_vp]),
     "he_conv_create": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_int, c_int,
                                c_int, c_int, c_int, c_double, ctypes.POINTER(c_vp)]),
     "he_conv_create_factored": (c_int, [c_vp, ctypes.POINTER(he_layout), F64P, F64P, c_int, c_int, c_int, c_int,
@@ -562,6 +563,10 @@ def he_boot_lintrans(ctx, bt, stage, idx, ct_in, ct_out, stream=None):
 
 def he_bootstrap(ctx, bt, ct_in, ct_out, stream=None):
     _check(load().he_bootstrap(ctx, bt, ct_in, ct_out, stream_ptr(stream)))
+
+
+def he_bootstrap_meta(ctx, bt, ct_in, ct_out, kb=10, stream=None):
+    _check(load().he_bootstrap_meta(ctx, bt, ct_in, kb, ct_out, stream_ptr(stream)))
 
 
 # ----------------------------------------------------------------------------- layers

@@ -139,6 +139,23 @@ def test_bootstrap_bit_exact_from_level_3(boot12):
     assert np.max(np.abs(o.decrypt(want) - z)) < 2.0 ** -15
 
 
+def test_meta_bootstrap_bit_exact_ring_2_12(boot12):
+    o, plan, g, bt = boot12
+    _import_oracle(o, plan, bt)
+    rng = np.random.default_rng(7)
+    z = rng.uniform(-1, 1, o.N)
+    ct = o.encrypt(z, 0, 2.0 ** 40, nonce=32)
+    want = B.meta_bootstrap(o, ct, plan)
+    d = g.upload(ct)
+    out = g.ct(plan.out_level)
+    H.he_bootstrap_meta(g.h, bt, d, out, 10)
+    assert H.he_ct_level(out) == plan.out_level - 1
+    assert H.he_ct_scale(out) == want.scale
+    assert_ct_equal(g.download(out), want)
+    one = np.max(np.abs(o.decrypt(B.bootstrap(o, ct, plan)) - z))
+    assert np.max(np.abs(o.decrypt(want) - z)) < one / 16
+
+
 def test_bootstrap_own_encoding_precision_ring_2_12():
     o = Context(BOOT12)
     g = GpuCtx(BOOT12)
@@ -185,6 +202,10 @@ def test_bootstrap_full_ring_precision_and_first_level_bit_exact():
         assert H.he_ct_level(out) == plan.out_level == B24.n_q - 1 - 15
         err = np.max(np.abs(H.he_decrypt(g.h, out, o.N) - z))
         assert err < 2.0 ** -12, err
+        meta = g.ct(plan.out_level)
+        H.he_bootstrap_meta(g.h, bt, d, meta, 10)
+        err2 = np.max(np.abs(H.he_decrypt(g.h, meta, o.N) - z))
+        assert err2 < err / 16, (err, err2)
         # ModRaise and the first CoeffToSlot level at the full ring, word for word
         x = g.ct(o.L)
         H.he_modraise(g.h, d, o.L, x)

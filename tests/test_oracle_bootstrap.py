@@ -215,3 +215,15 @@ def test_bootstrap_from_a_higher_level(tiny):
     out = B.bootstrap(ctx, ct, plan)
     assert out.level == plan.out_level
     assert np.max(np.abs(ctx.decrypt(out) - z)) < 2.0 ** -17
+
+
+def test_meta_bootstrap_removes_most_of_the_error(tiny):
+    ctx, plan = tiny
+    rng = np.random.default_rng(24)
+    z = rng.uniform(-1, 1, ctx.N)
+    ct = ctx.encrypt(z, 0, 2.0 ** 40, nonce=24)
+    one = np.max(np.abs(ctx.decrypt(B.bootstrap(ctx, ct, plan)) - z))
+    out = B.meta_bootstrap(ctx, ct, plan)
+    assert out.level == plan.out_level - 1
+    two = np.max(np.abs(ctx.decrypt(out) - z))
+    assert two < one / 16, (one, two)
