@@ -4371,6 +4371,7 @@ static int boot_to_level0(he_ctx *c, const he_ct *in, he_ct *dst, void *stream) 
     HE_TRY(he_ct_copy(dst, in, stream));
     HE_TRY(he_ct_drop_level(dst, 1));
     const double kk = std::nearbyint((double)c->primes[0] / 1024.0 * (double)c->primes[1] / dst->scale);
+    if (!(kk >= 1.0)) { he_set_error("bootstrap: input scale %g too large for level 0", dst->scale); return HE_EINVAL; }
     HE_TRY(he_mul_int(c, dst, kk, stream));
     dst->scale = dst->scale * kk;
     return he_rescale(c, dst, stream);
@@ -4401,6 +4402,7 @@ extern "C" int he_bootstrap(he_ctx *c, he_boot *bt, const he_ct *in, he_ct *out,
     // retarget to about Delta / 2 (exact scale bookkeeping)
     {
         const double kk = std::nearbyint(c->pr.scale / 2.0 * (double)c->primes[x->level] / x->scale);
+        if (!(kk >= 1.0)) { he_set_error("bootstrap: scale %g too large to retarget", x->scale); return HE_EINVAL; }
         HE_TRY(he_mul_int(c, x, kk, stream));
         x->scale = x->scale * kk;
         HE_TRY(he_rescale(c, x, stream));
@@ -4480,6 +4482,7 @@ extern "C" int he_bootstrap_meta(he_ctx *c, he_boot *bt, const he_ct *in, int kb
     HE_TRY(he_ct_copy(y, c1, stream));
     HE_TRY(he_ct_drop_level(y, 1));
     const double k = std::nearbyint(s0 * (double)c->primes[1] / y->scale);
+    if (!(k >= 1.0)) { he_set_error("he_bootstrap_meta: scale out of range"); return HE_EINVAL; }
     HE_TRY(he_mul_int(c, y, k, stream));
     y->scale = y->scale * k;
     HE_TRY(he_rescale(c, y, stream));
@@ -4492,6 +4495,7 @@ extern "C" int he_bootstrap_meta(he_ctx *c, he_boot *bt, const he_ct *in, int kb
     out->scale = out->scale * std::ldexp(1.0, kb);
     const int lv = out->level;
     const double kf = std::nearbyint(c1->scale * (double)c->primes[lv] / out->scale);
+    if (!(kf >= 1.0)) { he_set_error("he_bootstrap_meta: scale out of range"); return HE_EINVAL; }
     HE_TRY(he_mul_int(c, out, kf, stream));
     out->scale = out->scale * kf;
     HE_TRY(he_rescale(c, out, stream));
