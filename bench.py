@@ -1110,11 +1110,12 @@ def main():
             sub = argparse.Namespace(**vars(args))
             sub.steps, sub.warmup, sub.trace, sub.small, sub.profile_step = k, 3, "ipmac", False, False
             line[key] = _extra_summary(fn(sub, ws, rank, local, emit=False))
-        # serving: Poisson streams of 32x32 and 64x64 requests through the 4-layer stack at
+        # serving: Poisson streams of 32x32 and 64x64 requests (64 per load of 0.5, 0.8 and 1.0 of the
+        # measured capacity) through the 4-layer stack at
         # 33 + 11 primes, continuous batching at stage granularity (p50/p99 and images/s)
         from paper_2306_09189_gb300 import serve
-        sv = serve.run_benchmark(argparse.Namespace(sizes="32,64", widths="4,16,32,64,64", rates="0.5,0.8",
-                                                    requests=32, conv="bsgs", server="batch", workers=4,
+        sv = serve.run_benchmark(argparse.Namespace(sizes="32,64", widths="4,16,32,64,64", rates="0.5,0.8,1.0",
+                                                    requests=64, conv="bsgs", server="batch", workers=4,
                                                     max_batch=4))
         line["serving"] = {k: sv[k] for k in ("workload", "server", "max_batch", "conv", "setup_s",
                                               "service_ms_alone", "capacity_images_per_s", "runs", "memory")}
