@@ -483,7 +483,10 @@ typedef struct {
 } he_boot_config;
 /* Plans the levels (diagonals, baby-step giant-step split), encodes the diagonals at scale
  * q_level over Q_level u P, and the cosine's coefficients.  cfg NULL or zero fields take the
- * defaults.  Keys are not generated: he_boot_rotations, he_keygen_conjugation, relin. */
+ * defaults.  Keys are not generated: he_boot_rotations, he_keygen_conjugation, relin.  A plan
+ * owns its temporaries: one bootstrap at a time per plan (and per context's scratch); the
+ * first run also tunes the fused stages, so it allocates and must come before a graph
+ * capture. */
 int he_boot_create(he_ctx *ctx, const he_boot_config *cfg, he_boot **out);
 void he_boot_destroy(he_boot *bt);
 /* Distinct non-zero rotation amounts the linear levels use (count returned; amounts filled
