@@ -230,7 +230,7 @@ def run_block(args, ws, rank, local, emit=True):
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
                                                    "pk3": H.HE_KEY_STREAM_PK3, "pk1": H.HE_KEY_STREAM_PK1,
-                                                   "pkt": H.HE_KEY_STREAM_PKT,
+                                                   "pkt": H.HE_KEY_STREAM_PKT, "pk3l": H.HE_KEY_STREAM_PK3L,
                                                    "splitm": H.HE_KEY_STREAM_SPLITM}[args.key_stream])
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]
@@ -693,7 +693,7 @@ def run_stem(args, ws, rank, local, emit=True):
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
                                                    "pk3": H.HE_KEY_STREAM_PK3, "pk1": H.HE_KEY_STREAM_PK1,
-                                                   "pkt": H.HE_KEY_STREAM_PKT,
+                                                   "pkt": H.HE_KEY_STREAM_PKT, "pk3l": H.HE_KEY_STREAM_PK3L,
                                                    "splitm": H.HE_KEY_STREAM_SPLITM}[args.key_stream])
     N = H.he_ctx_info(ctx)["slots"]
     wl = workloads.imagenet_stem(0)
@@ -811,7 +811,7 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="set up, warm up, then run one batched step between cudaProfilerStart/Stop")
     ap.add_argument("--key-stream", default="auto",
-                    choices=["auto", "ldg", "tma", "split", "pk", "pk3", "pk1", "pkt", "splitm"],
+                    choices=["auto", "ldg", "tma", "split", "pk", "pk3", "pk1", "pkt", "pk3l", "splitm"],
                     help="key-switch + MAC form: autotuned (default), the fused kernel with vector "
                          "loads or a TMA tile pipeline, or the split form (inner products, then MAC)")
     ap.add_argument("--no-graph", action="store_true", help="launch the fused step eagerly, not as a CUDA graph")
@@ -861,7 +861,7 @@ def main():
                                                    "tma": H.HE_KEY_STREAM_TMA,
                                                    "split": H.HE_KEY_STREAM_SPLIT, "pk": H.HE_KEY_STREAM_PK,
                                                    "pk3": H.HE_KEY_STREAM_PK3, "pk1": H.HE_KEY_STREAM_PK1,
-                                                   "pkt": H.HE_KEY_STREAM_PKT,
+                                                   "pkt": H.HE_KEY_STREAM_PKT, "pk3l": H.HE_KEY_STREAM_PK3L,
                                                    "splitm": H.HE_KEY_STREAM_SPLITM}[args.key_stream])
     info = H.he_ctx_info(ctx)
     n, N = info["n"], info["slots"]

@@ -166,6 +166,9 @@ int he_ctx_check(he_ctx *ctx, void *stream);
  *     cp.async.bulk into a 3-stage ring; consumer warps release each stage on an mbarrier as
  *     soon as they hold its words (no block barrier); bounded waits as for HE_KEY_STREAM_TMA.
  *     Up to 4 digits, else the pair form runs.  Explicit selection only (measured slower);
+ *   HE_KEY_STREAM_PK3L (12): HE_KEY_STREAM_PK3 with the key tiles of the amount two ahead
+ *     requested into L2 by cp.async.bulk.prefetch (up to 4 digits); explicit selection only
+ *     (measured slower);
  *   HE_KEY_STREAM_SPLITM (9): the split form with the raised MAC batched over the images of a
  *     mixed-level batch (he_conv_run_batch): each plaintext word is read once for up to 4 images
  *     x 4 outputs; a single image falls back to HE_KEY_STREAM_SPLIT;
@@ -192,6 +195,7 @@ int he_ctx_check(he_ctx *ctx, void *stream);
 #define HE_KEY_STREAM_SPLITM 9
 #define HE_KEY_STREAM_PK1 10
 #define HE_KEY_STREAM_PKT 11
+#define HE_KEY_STREAM_PK3L 12
 /* HE_OPT_PDL (0 default, or 1; process-wide, whichever context sets it): launch every kernel
  * with programmatic dependent launch, so each grid is set up while its predecessor on the
  * stream finishes (every kernel waits for the predecessor's writes before it reads).  Same

@@ -809,7 +809,7 @@ extern "C" int he_ctx_set_option(he_ctx *c, int option, int value) {
          value == HE_KEY_STREAM_SPLIT || value == HE_KEY_STREAM_CP || value == HE_KEY_STREAM_LDG1 ||
          value == HE_KEY_STREAM_PK || value == HE_KEY_STREAM_PK3 || value == HE_KEY_STREAM_PKP ||
          value == HE_KEY_STREAM_SPLITM || value == HE_KEY_STREAM_PK1 ||
-         value == HE_KEY_STREAM_PKT)) {
+         value == HE_KEY_STREAM_PKT || value == HE_KEY_STREAM_PK3L)) {
         c->key_stream = value;
         return HE_OK;
     }

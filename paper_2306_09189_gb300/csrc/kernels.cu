@@ -1831,7 +1831,10 @@ __global__ void __launch_bounds__(TB, 3) ipmac1_kernel(KP kp, const fgrp *grps, 
 // plaintext stream.  Terms are below p^2 < 2^100; a launch adds at most (beta + 1) per
 // amount, far below 2^28 terms, so the 128-bit sums cannot wrap.  fent.pt[0] holds P pt
 // ([l+1][n], Montgomery) or HE_PT_ONE for the integer 1 (then K' is the key itself).
-template <int B, int MINB, bool PIPE>
+// PF > 0: the K' tile (2 beta segments of 512 words, 4 KB each) of the amount PF ahead is
+// requested into L2 by cp.async.bulk.prefetch (one thread per segment; a hint, no completion),
+// so the amount's loads hit L2 without holding the words in registers.
+template <int B, int MINB, bool PIPE, int PF = 0>
 __global__ void __launch_bounds__(TB, MINB) ipmac_pk_kernel(KP kp, const fgrp *grps, int n_grp, int gb,
                                                             const u64 *pmod) {
     pdl_wait();
@@ -1868,6 +1871,13 @@ __global__ void __launch_bounds__(TB, MINB) ipmac_pk_kernel(KP kp, const fgrp *g
     };
     if (PIPE && n_amt > 0) load_key(A, kk0, kk1);
     for (int i = 0; i < n_amt; i++) {
+        if (PF > 0 && (int)threadIdx.x < 2 * beta && i + PF < n_amt) {
+            const u64 *kf = P.amts[i + PF].key;
+            if (kf) {
+                const u64 *src = kf + (size_t)threadIdx.x * kstride + (size_t)kl * kp.n + (size_t)tile * (2 * TB);
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(2u * TB * 8u) : "memory");
+            }
+        }
         famt An{};
         fent En{};
         if (i + 1 < n_amt) {
@@ -2881,11 +2891,13 @@ int k_ipmac(const he_ctx *ctx, const fgrp *grps, int n_grp, int V, int max_beta,
         LAUNCH_CHECK();
         return HE_OK;
     }
-    if (form == HE_KEY_STREAM_PK || form == HE_FORM_PK3 || form == HE_FORM_PKP) {
+    if (form == HE_KEY_STREAM_PK || form == HE_FORM_PK3 || form == HE_FORM_PKP || form == HE_KEY_STREAM_PK3L) {
         if (V != 1) { he_set_error("k_ipmac: the pre-keyed form takes one output per group"); return HE_EINVAL; }
         dim3 gp(gx, primes);
         if (form == HE_FORM_PK3 && max_beta <= 4)
             pdl_launch(ipmac_pk_kernel<4, 3, false>, gp, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
+        else if (form == HE_KEY_STREAM_PK3L && max_beta <= 4)
+            pdl_launch(ipmac_pk_kernel<4, 3, false, 2>, gp, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
         else if (form == HE_FORM_PKP && max_beta <= 4)
             pdl_launch(ipmac_pk_kernel<4, 2, true>, gp, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);
         else if (max_beta <= 4) pdl_launch(ipmac_pk_kernel<4, 2, false>, gp, TB, 0, s, ctx->kp, grps, n_grp, gb, ctx->d_consts);

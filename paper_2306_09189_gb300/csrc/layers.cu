@@ -732,11 +732,11 @@ struct FusedStage {
 // ModUps of the first run.
 static bool is_pk(int fm) {
     return fm == HE_KEY_STREAM_PK || fm == HE_KEY_STREAM_PK3 || fm == HE_KEY_STREAM_PKP || fm == HE_KEY_STREAM_PK1 ||
-           fm == HE_KEY_STREAM_PKT;
+           fm == HE_KEY_STREAM_PKT || fm == HE_KEY_STREAM_PK3L;
 }
 static const char *pk_name(int fm) {
     return fm == HE_FORM_PK3 ? "pk3" : fm == HE_FORM_PKP ? "pkp" : fm == HE_KEY_STREAM_PK1 ? "pk1"
-         : fm == HE_KEY_STREAM_PKT ? "pkt" : "pk";
+         : fm == HE_KEY_STREAM_PKT ? "pkt" : fm == HE_KEY_STREAM_PK3L ? "pk3l" : "pk";
 }
 static const char *form_name(int fm) {
     return fm == HE_KEY_STREAM_TMA ? "tma" : fm == HE_KEY_STREAM_CP ? "cp" : fm == HE_KEY_STREAM_LDG1 ? "ldg1" : "ldg";
@@ -1106,8 +1106,9 @@ struct FusedLaunch {
         bool bestPk = false;
         if (rc == HE_OK && try_pk) {
             rc = build_pk();
-            // (HE_KEY_STREAM_PKT, the TMA ring with per-stage release, measured slower than pk3 on
-            // every stage of the CIFAR layer: explicit selection only)
+            // (HE_KEY_STREAM_PKT, the TMA ring with per-stage release, and HE_KEY_STREAM_PK3L, the L2
+            // bulk prefetch two amounts ahead, measured slower than pk3 on the CIFAR layer:
+            // explicit selection only)
             for (int fm : {(int)HE_KEY_STREAM_PK, (int)HE_FORM_PK3, (int)HE_FORM_PKP, (int)HE_KEY_STREAM_PK1}) {
                 float t;
                 if (rc == HE_OK) rc = time_it([&]() { return launch_pk(s, fm); }, t);

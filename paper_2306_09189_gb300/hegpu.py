@@ -27,6 +27,7 @@ HE_KEY_STREAM_PKP = 8
 HE_KEY_STREAM_SPLITM = 9
 HE_KEY_STREAM_PK1 = 10
 HE_KEY_STREAM_PKT = 11
+HE_KEY_STREAM_PK3L = 12
 
 c_int, c_double, c_size_t, c_u64, c_i32, c_vp = (ctypes.c_int, ctypes.c_double, ctypes.c_size_t,
                                                  ctypes.c_uint64, ctypes.c_int32, ctypes.c_void_p)

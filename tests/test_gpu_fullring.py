@@ -72,7 +72,7 @@ def test_cifar_layer_full_ring_limbs_equal_oracle(c20):
     ref_f = Ly.conv_he_raised(o, plan, [ct], pts, {0: bias[0]})[0]
     fused = None
     for ks in (H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_PK3, H.HE_KEY_STREAM_PK1, H.HE_KEY_STREAM_PKT,
-               H.HE_KEY_STREAM_LDG):
+               H.HE_KEY_STREAM_PK3L, H.HE_KEY_STREAM_LDG):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         y = g.ct(level - 1)
         H.he_conv_run(g.h, conv, [x], [y], H.HE_FUSED)

@@ -106,7 +106,7 @@ def test_autotuner_choice_keeps_bits():
         for ks in (H.HE_KEY_STREAM_AUTO, H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_SPLIT,
                    H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_LDG1, H.HE_KEY_STREAM_PK, H.HE_KEY_STREAM_PK3,
                    H.HE_KEY_STREAM_PKP, H.HE_KEY_STREAM_SPLITM, H.HE_KEY_STREAM_PK1,
-                   H.HE_KEY_STREAM_PKT):
+                   H.HE_KEY_STREAM_PKT, H.HE_KEY_STREAM_PK3L):
             H.he_ctx_set_option(ctx, H.HE_OPT_KEY_STREAM, ks)
             assert H.he_ctx_get_option(ctx, H.HE_OPT_KEY_STREAM) == ks
             H.he_conv_run(ctx, conv, [x], [y], H.HE_FUSED)

@@ -94,7 +94,7 @@ def _conv_case(pair, c, co, m, k, pad, level, seed, bias=True):
     ref_raised = Ly.conv_he_raised(o, plan, cts, pts, bias_pts)
     for ks in (H.HE_KEY_STREAM_LDG, H.HE_KEY_STREAM_TMA, H.HE_KEY_STREAM_CP, H.HE_KEY_STREAM_LDG1,
                H.HE_KEY_STREAM_SPLIT, H.HE_KEY_STREAM_PK, H.HE_KEY_STREAM_PK3, H.HE_KEY_STREAM_PKP,
-               H.HE_KEY_STREAM_PK1, H.HE_KEY_STREAM_PKT):
+               H.HE_KEY_STREAM_PK1, H.HE_KEY_STREAM_PKT, H.HE_KEY_STREAM_PK3L):
         H.he_ctx_set_option(g.h, H.HE_OPT_KEY_STREAM, ks)
         outs = [g.ct(level - 1) for _ in range(plan.lout.n_shards)]
         H.he_conv_run(g.h, conv, ins, outs, H.HE_FUSED)
