@@ -315,3 +315,44 @@ def test_bootstrap_errors_leave_the_context_usable(boot12):
     out = g.ct(plan.out_level)
     H.he_bootstrap(g.h, bt, d, out)
     assert H.he_ct_level(out) == plan.out_level
+
+
+def test_full_ring_bootstrap_equals_the_oracle_word_for_word():
+    """The whole bootstrap at ring 2^16 on the oracle's plaintexts and coefficients: every output
+    word equals the oracle's (SHA-256 of the words against tests/golden/bootstrap_b24.json, which
+    tests/golden/make_bootstrap_golden.py wrote from the oracle alone on the same input)."""
+    import hashlib
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bootstrap_b24.json")) as f:
+        gold = json.load(f)
+    o = Context(B24)
+    plan = B.BootPlan(o)
+    h = hashlib.sha256()
+    for name, levels in (("cts", plan.cts), ("stc", plan.stc)):
+        for i, lv in enumerate(levels):
+            pts = plan.plaintexts(o, name, i)
+            for gi in lv.giants:
+                for j in sorted(lv.baby[gi]):
+                    h.update(np.ascontiguousarray(pts[(gi, j)], dtype="<i8").tobytes())
+    assert h.hexdigest() == gold["sha256_plaintexts"], \
+        "this machine's numpy encodes the diagonals differently from the one that wrote the golden file"
+    z = np.random.default_rng(gold["seed_z"]).uniform(-1, 1, o.N)
+    ct = o.encrypt(z, 0, gold["input_scale"], nonce=gold["nonce"])
+    g = GpuCtx(B24)
+    try:
+        bt = H.he_boot_create(g.h)
+        H.he_keygen_rotations(g.h, H.he_boot_rotations(bt))
+        H.he_keygen_conjugation(g.h)
+        H.he_keygen_relin(g.h)
+        _import_oracle(o, plan, bt)
+        out = g.ct(plan.out_level)
+        H.he_bootstrap(g.h, bt, g.upload(ct), out)
+        assert H.he_ct_level(out) == gold["out_level"]
+        assert H.he_ct_scale(out) == gold["out_scale"]
+        words = np.ascontiguousarray(g.download(out), dtype="<u8")
+        assert words[:, :, :4].tolist() == gold["first_words"]
+        assert hashlib.sha256(words.tobytes()).hexdigest() == gold["sha256_words"]
+        H.he_boot_destroy(bt)
+    finally:
+        g.close()
