@@ -6,9 +6,10 @@ uniform in [-1, 1] by numpy's default generator with seed 5, encrypted at scale 
 50.  The file records the SHA-256 of the oracle's output words (coefficient form, [2][l+1][n]
 uint64, little-endian), its level and scale, a SHA-256 of the diagonal plaintexts the oracle
 encoded (so a test can tell an encoder difference from an arithmetic one), and the first words
-of every output limb.  Only oracle/ is called.  The plaintexts come from numpy's FFT, whose last
-bits can differ between builds, so the file is written on the machine whose numpy the GPU test
-uses.
+of every output limb; the same for the bootstrap with its error bootstrapped and subtracted
+(meta_bootstrap, kb = 10).  Only oracle/ is called.  The plaintexts come from numpy's FFT, whose
+last bits can differ between builds, so the file is written on the machine whose numpy the GPU
+test uses.
 
     python tests/golden/make_bootstrap_golden.py [out.json]
 """
@@ -54,6 +55,8 @@ def main():
     out = B.bootstrap(ctx, ct, plan)
     words = np.ascontiguousarray(out.c, dtype="<u8")
     err = float(np.max(np.abs(ctx.decrypt(out) - z)))
+    meta = B.meta_bootstrap(ctx, ct, plan, kb=10)
+    mwords = np.ascontiguousarray(meta.c, dtype="<u8")
     rec = {
         "what": "oracle bootstrap of one seeded level-0 ciphertext, ring 2^16, B24 chain",
         "params": "B24", "seed_z": SEED_Z, "nonce": NONCE, "input_scale": 2.0 ** 40,
@@ -62,6 +65,10 @@ def main():
         "sha256_plaintexts": pdig,
         "first_words": words[:, :, :4].tolist(),
         "max_abs_error": err,
+        "meta": {"kb": 10, "out_level": meta.level, "out_scale": meta.scale,
+                 "sha256_words": hashlib.sha256(mwords.tobytes()).hexdigest(),
+                 "first_words": mwords[:, :, :4].tolist(),
+                 "max_abs_error": float(np.max(np.abs(ctx.decrypt(meta) - z)))},
         "numpy": np.__version__,
         "seconds": time.time() - t0,
     }

@@ -353,6 +353,14 @@ def test_full_ring_bootstrap_equals_the_oracle_word_for_word():
         words = np.ascontiguousarray(g.download(out), dtype="<u8")
         assert words[:, :, :4].tolist() == gold["first_words"]
         assert hashlib.sha256(words.tobytes()).hexdigest() == gold["sha256_words"]
+        # the bootstrap with its error bootstrapped and subtracted, word for word too
+        meta = g.ct(plan.out_level)
+        H.he_bootstrap_meta(g.h, bt, g.upload(ct), meta, gold["meta"]["kb"])
+        assert H.he_ct_level(meta) == gold["meta"]["out_level"]
+        assert H.he_ct_scale(meta) == gold["meta"]["out_scale"]
+        mw = np.ascontiguousarray(g.download(meta), dtype="<u8")
+        assert mw[:, :, :4].tolist() == gold["meta"]["first_words"]
+        assert hashlib.sha256(mw.tobytes()).hexdigest() == gold["meta"]["sha256_words"]
         H.he_boot_destroy(bt)
     finally:
         g.close()
