@@ -12,8 +12,9 @@ ranks; ms_per_step = layer latency.  The batched mode is the headline; the plain
 per-ciphertext path is timed beside it, and the convolution alone (`conv_only`).  At N = 1 the
 line also carries the batched ResNet block (`resnet_block`: 4 images at mixed levels, batched
 vs plain), the ImageNet stem (`imagenet_stem`) and the serving loop (`serving`: Poisson
-arrivals, p50/p99 latency and images/s) and one full-ring bootstrap (`bootstrap`), each run on its
-own context afterwards, and the oracle
+arrivals, p50/p99 latency and images/s), one full-ring bootstrap (`bootstrap`) and a whole
+ResNet-20-shaped encrypted inference with bootstrapping (`resnet20`), each run on its own context
+afterwards, and the oracle
 on all host cores and on one (`cpu_baseline`).  N > 1 runs independent replicas
 (the layer does not shard across GPUs).  --impl reference times the CPU oracle instead.
 """
@@ -677,6 +678,55 @@ def run_bootstrap(args, ws, rank, local, emit=True):
     return line if rank == 0 else None
 
 
+RESNET20_WORKLOAD = ("resnet-20 (CIFAR, 3x32x32): 3x3 stem, 3 stages x 3 basic blocks at 16/32/64 channels "
+                     "(stride 2 and 1x1 shortcut at stages 2-3), folded BN, degree-16 GELU, pool-linear head; "
+                     "bootstrapped wherever the levels run out; 2N=2^16, 24+6 primes of 50 bits")
+
+
+def run_resnet20(args, ws, rank, local, emit=True):
+    """One encrypted ResNet-20-shaped inference per step (the paper's Sec. 5 networks, whose CPU
+    latencies it tabulates): the first image plans every layer and generates its keys, the next
+    ones are timed; the logits are compared with the FP64 network with the same polynomial."""
+    import torch
+    import workloads
+    from paper_2306_09189_gb300 import host
+    from paper_2306_09189_gb300 import hegpu as H
+    from paper_2306_09189_gb300.network import EncryptedResNet
+    net = workloads.resnet20(0)
+    cheb = host.chebyshev_coeffs("gelu", workloads.GELU_DEGREE, -workloads.GELU_BOUND, workloads.GELU_BOUND)
+    want = workloads.resnet20_forward(net, cheb)
+    t0 = time.perf_counter()
+    r = EncryptedResNet(host.bootstrap_params(0), net, cheb)
+    r.infer(net["x"])                                      # plans, keys, autotuner
+    setup_s = time.perf_counter() - t0
+    steps = max(1, min(args.steps, 5))
+    r.timing, r.counts = {}, {}
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    for i in range(steps):
+        got = r.infer(net["x"], nonce0=100 * (i + 1))
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / steps
+    ck = clocks.stop()
+    err = float(np.max(np.abs(got - want)))
+    line = {"metric": "encrypted ResNet-20 inference latency on 1 GB300", "value": sec, "unit": "s/image",
+            "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": sec * 1e3, "higher_is_better": False,
+            "dtype": "u64", "data": "synthetic weights and image",
+            "config": {"workload": RESNET20_WORKLOAD, "setup_s": setup_s,
+                       "key_bytes": H.he_key_bytes(r.ctx)},
+            "breakdown_s": {k: v / steps for k, v in r.timing.items()},
+            "counts": {k: v // steps for k, v in r.counts.items()},
+            "check": {"max_abs_logit_error": err, "logit_range": float(np.max(want) - np.min(want))},
+            "paper_context": "multiplexed ResNet-20, CIFAR-10: 486 s per image on a 32-core Threadripper 3970X "
+                             "(OpenFHE, 2^14-slot shards, 59-bit scales)",
+            "clocks": ck}
+    r.close()
+    if emit and rank == 0:
+        print(json.dumps(line), flush=True)
+    return line if rank == 0 else None
+
+
 def run_stem(args, ws, rank, local, emit=True):
     """The ImageNet-shaped sharded stem (config 3): the factored channel-shard conv with stride 2
     (the select runs on 128 channel shards), then the 2x2 average pool; one CUDA graph per step.
@@ -829,10 +879,12 @@ def main():
     ap.add_argument("--poly", default="ps", choices=["ps", "tree"],
                     help="GELU evaluation: Paterson-Stockmeyer (default) or the binary tree")
     ap.add_argument("--workload", default="cifar-layer",
-                    choices=["cifar-layer", "resnet-block", "imagenet-stem", "resnet-head", "bootstrap"],
+                    choices=["cifar-layer", "resnet-block", "imagenet-stem", "resnet-head", "bootstrap",
+                             "resnet20"],
                     help="cifar-layer: the headline layer; resnet-block: the batched mixed-level block; "
                          "imagenet-stem: the channel-shard stem with stride 2 and average pool; "
-                         "resnet-head: the pool-linear head; bootstrap: one full-ring bootstrap")
+                         "resnet-head: the pool-linear head; bootstrap: one full-ring bootstrap; "
+                         "resnet20: a whole ResNet-20-shaped network with bootstrapping")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -844,9 +896,9 @@ def main():
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    if args.workload in ("resnet-block", "imagenet-stem", "resnet-head", "bootstrap"):
+    if args.workload in ("resnet-block", "imagenet-stem", "resnet-head", "bootstrap", "resnet20"):
         {"resnet-block": run_block, "imagenet-stem": run_stem, "resnet-head": run_head,
-         "bootstrap": run_bootstrap}[args.workload](args, ws, rank, local)
+         "bootstrap": run_bootstrap, "resnet20": run_resnet20}[args.workload](args, ws, rank, local)
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
@@ -1106,7 +1158,7 @@ def main():
         # the batched ResNet block (the survey's headline for batched vs plain) and the ImageNet
         # stem, each on its own context after the layer's is released
         for key, fn, k in (("resnet_block", run_block, 5), ("imagenet_stem", run_stem, 3),
-                           ("bootstrap", run_bootstrap, 20)):
+                           ("bootstrap", run_bootstrap, 20), ("resnet20", run_resnet20, 3)):
             sub = argparse.Namespace(**vars(args))
             sub.steps, sub.warmup, sub.trace, sub.small, sub.profile_step = k, 3, "ipmac", False, False
             line[key] = _extra_summary(fn(sub, ws, rank, local, emit=False))
@@ -1134,7 +1186,7 @@ def _extra_summary(d):
     if d is None:
         return None
     keep = ("ms_per_step", "value", "unit", "steps", "plain", "check", "roofline", "clocks", "gpu_launches",
-            "eager_ms", "cpu_baseline", "meta")
+            "eager_ms", "cpu_baseline", "meta", "breakdown_s", "counts", "paper_context")
     out = {k: d[k] for k in keep if k in d}
     out["workload"] = d["config"]["workload"]
     for k in ("key_switches_per_step", "input_levels", "output_level", "setup_s", "l2",

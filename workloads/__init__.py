@@ -129,3 +129,93 @@ def serving_stack(seed=0, widths=(4, 16, 32, 64, 64), m=32, bound=GELU_BOUND, de
         y = torch.nn.functional.gelu(y * bound)
         x = torch.nn.functional.avg_pool2d(y[None], 2)[0].numpy()
     return layers
+
+
+def _gelu(v):
+    from math import erf, sqrt
+    return v * 0.5 * (1.0 + np.vectorize(erf)(v / sqrt(2.0)))
+
+
+def resnet20(seed=0, m=32, bound=GELU_BOUND):
+    """ResNet-20-shaped CIFAR network (the paper's smallest multiplexed ResNet, Sec. 5): a 3x3
+    stem 3->16, three stages of three basic blocks at 16, 32 and 64 channels (the first block of
+    stages 2 and 3 with stride 2 and a 1x1 stride-2 shortcut convolution), GELU activations,
+    global average pool and a linear layer to 10 logits.  PyTorch's default initialisation;
+    every BatchNorm folded into the convolution before it, its statistics taken from a seeded
+    image pushed through the plaintext network (exact GELU) and divided by `bound`, so every
+    activation input lies in [-1, 1] (the polynomial's interval [-bound, bound] folded in; the
+    shortcut adds x / bound).  Reseeds until that holds.  Returns a dict: x [3][m][m], stem
+    (W, b), blocks [{stride, W1, b1, W2, b2, Ws, bs}] (Ws None for the identity shortcut),
+    head (W [10][64], b [10])."""
+    import torch
+    F = torch.nn.functional
+
+    def conv(x, W, stride, pad):
+        return F.conv2d(torch.tensor(x)[None], torch.tensor(W), stride=stride, padding=pad)[0].numpy()
+
+    def fold(x, W, stride, pad, eps=1e-5):
+        y = conv(x, W, stride, pad)
+        mu = y.mean(axis=(1, 2))
+        sd = np.sqrt(y.var(axis=(1, 2)) + eps)
+        return W / (sd[:, None, None, None] * bound), -mu / (sd * bound)
+
+    while True:
+        rng = np.random.default_rng(seed + 11)
+        x = image(3, m, seed)
+        ok = True
+
+        def init(co, ci, k):
+            b = 1.0 / math.sqrt(ci * k * k)
+            return rng.uniform(-b, b, (co, ci, k, k))
+
+        W, b = fold(x, init(16, 3, 3), 1, 1)
+        t = conv(x, W, 1, 1) + b[:, None, None]
+        ok &= np.abs(t).max() <= 1.0
+        a = _gelu(bound * t)
+        stem = (W, b)
+        blocks = []
+        c = 16
+        for stage, co in enumerate((16, 32, 64)):
+            for i in range(3):
+                stride = 2 if (stage > 0 and i == 0) else 1
+                W1, b1 = fold(a, init(co, c, 3), stride, 1)
+                h = _gelu(bound * (conv(a, W1, stride, 1) + b1[:, None, None]))
+                W2, b2 = fold(h, init(co, co, 3), 1, 1)
+                y = conv(h, W2, 1, 1) + b2[:, None, None]
+                if stride == 2 or co != c:
+                    Ws, bs = fold(a, init(co, c, 1), stride, 0)
+                    sc = conv(a, Ws, stride, 0) + bs[:, None, None]
+                else:
+                    Ws, bs = None, None
+                    sc = a / bound
+                t = y + sc
+                ok &= np.abs(t).max() <= 1.0
+                a = _gelu(bound * t)
+                blocks.append(dict(stride=stride, W1=W1, b1=b1, W2=W2, b2=b2, Ws=Ws, bs=bs))
+                c = co
+        hb = 1.0 / math.sqrt(64)
+        head = (rng.uniform(-hb, hb, (10, 64)), rng.uniform(-hb, hb, 10))
+        if ok:
+            return dict(x=x, stem=stem, blocks=blocks, head=head)
+        seed += 1000
+
+
+def resnet20_forward(net, cheb, bound=GELU_BOUND):
+    """The plaintext network in FP64 with the activation a given Chebyshev polynomial (the one
+    the encrypted network evaluates): the reference its decrypted logits are checked against."""
+    import torch
+    F = torch.nn.functional
+    act = lambda t: np.polynomial.chebyshev.chebval(t, cheb)
+
+    def conv(x, W, b, stride, pad):
+        return F.conv2d(torch.tensor(x)[None], torch.tensor(W), stride=stride, padding=pad)[0].numpy() + b[:, None, None]
+
+    a = act(conv(net["x"], *net["stem"], 1, 1))
+    for blk in net["blocks"]:
+        s = blk["stride"]
+        h = act(conv(a, blk["W1"], blk["b1"], s, 1))
+        y = conv(h, blk["W2"], blk["b2"], 1, 1)
+        sc = a / bound if blk["Ws"] is None else conv(a, blk["Ws"], blk["bs"], s, 0)
+        a = act(y + sc)
+    W, b = net["head"]
+    return W @ a.mean(axis=(1, 2)) + b
